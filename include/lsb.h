@@ -1,0 +1,183 @@
+/*
+ * lsb.h - C ABI of the GB300 coupled level-set lattice Boltzmann library.
+ *
+ * The library advances two immiscible fluid phases, each with its own
+ * lattice Boltzmann solver (Sec. 2.1: BGK collision, Eq. feq, Eq. omega,
+ * forcing), coupled at a sharp interface given by a level set phi (Sec. 2.2;
+ * phi < 0 liquid, phi >= 0 gas) through interpolated bounce-back with the
+ * velocity and stress-jump conditions (Sec. 2.3, Eq. bb, bb_cc, Sdecomp),
+ * refill of cells that change phase (Sec. 2.4), on a block-structured
+ * adaptive Cartesian grid with Dupuis-Chopard level coupling (Sec. 2.1 last
+ * paragraph, Sec. 2.5, 2.6).
+ *
+ * Conventions for every entry point:
+ *  - Units are lattice units of the case's FINEST level (dx = dt = 1 there).
+ *  - Dense arrays are row-major with x fastest: index x + nx*(y + ny*z).
+ *  - Pointers marked "device" must be CUDA device memory of the current
+ *    device; pointers marked "host" are ordinary host memory.  The library
+ *    never takes ownership of caller buffers.
+ *  - All device work is enqueued on the stream given at creation; calls that
+ *    return data synchronise that stream.
+ *  - Every call validates its arguments before enqueuing work and returns
+ *    LSB_EINVAL without side effects on bad input.  Errors raised on the
+ *    device (non-finite state, list overflow) are latched and returned by
+ *    the next synchronising call (lsb_get_fields, lsb_observables,
+ *    lsb_sync).  lsb_last_error() gives a human-readable message.
+ *  - A handle is not thread safe: use one handle per host thread/stream.
+ */
+#ifndef LSB_H
+#define LSB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lsb_grid lsb_grid;
+
+typedef enum {
+  LSB_OK = 0,
+  LSB_EINVAL = 1,    /* invalid argument */
+  LSB_ENOMEM = 2,    /* device allocation failed or a work list overflowed */
+  LSB_ECUDA = 3,     /* CUDA runtime error */
+  LSB_EUNSTABLE = 4, /* non-finite density or velocity detected */
+  LSB_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+  LSB_ESTATE = 6     /* call not valid in the handle's current state */
+} lsb_status;
+
+enum { LSB_D2Q9 = 0, LSB_D3Q19 = 1 };           /* velocity sets, Sec. 2.1 / Fig. 1 */
+enum { LSB_PERIODIC = 0, LSB_WALL = 1 };        /* per-axis boundary kind */
+enum { LSB_FP32 = 0, LSB_FP16S = 1 };           /* population storage */
+enum { LSB_SENSOR_BAND = 0, LSB_SENSOR_SIGNED = 1 }; /* refinement sensor, Sec. 2.6, 3.2.2 */
+
+/* Fields for lsb_get_fields (dense arrays of one level of one case). */
+enum {
+  LSB_FIELD_RHO = 0,   /* normalised density rho_hat (float, 1 per cell)           */
+  LSB_FIELD_U = 1,     /* velocity, D floats per cell, component-major (D x cells) */
+  LSB_FIELD_PHI = 2,   /* level set (float, finest level only)                     */
+  LSB_FIELD_PHASE = 3, /* uint8 per cell: 0 liquid, 1 gas                          */
+  LSB_FIELD_F = 4,     /* populations f_i (float, Q x cells, Fig. 1 order)         */
+  LSB_FIELD_TAG = 5,   /* uint8 per cell: bit0 phase, bit1 interface cell,
+                          bit2 flipped at the last step, bit3 previous phase,
+                          bit4 covered cell streamed from by a leaf, bit5 ghost   */
+  LSB_FIELD_BLOCKS = 6,/* int8 per block: 0 inactive, 1 leaf, 2 refined           */
+  LSB_FIELD_CUTMASK = 7,/* uint32 per cell: bit k set when the incoming direction
+                          k's source lies in the other phase (finest level)       */
+  LSB_FIELD_KAPPA = 8, /* curvature at interface cells (float, finest level)      */
+  LSB_FIELD_UEXT = 9   /* extension velocity u~ (D x cells, finest level)         */
+};
+
+/* Geometry and discretisation of one case, fixed for the handle's life. */
+typedef struct {
+  int lattice;          /* LSB_D2Q9 or LSB_D3Q19; all cases of a handle share it     */
+  int base[3];          /* base-level cells per axis (base[2] ignored in 2D)         */
+  int n_levels;         /* total levels including the base (1 = uniform), <= 4       */
+  int block[3];         /* block edge in cells, even, same on every level            */
+  int bc[3];            /* per axis: LSB_PERIODIC or LSB_WALL (walls on cell faces)  */
+  double wall_u[6][3];  /* velocity of faces x-, x+, y-, y+, z-, z+                  */
+  int storage;          /* LSB_FP32 or LSB_FP16S; all cases of a handle share it     */
+  double fp16_scale;    /* LSB_FP16S: populations stored as (f - w) * scale, a power
+                           of two that keeps them out of the half subnormal range   */
+} lsb_grid_desc;
+
+/* Physics and method parameters of one case (lattice units of the finest level). */
+typedef struct {
+  double rho[2];        /* physical densities: [0] liquid (phi < 0), [1] gas        */
+  double nu[2];         /* kinematic viscosities on the finest level (Eq. omega)    */
+  double body_force[3]; /* force density, acts as acceleration body_force/rho_k     */
+  double gravity[3];    /* acceleration acting on both phases                       */
+  double sigma;         /* surface tension (Eq. Sdecomp)                            */
+  double x_ref[3];      /* hydrostatic reference point for the initial density:
+                           rho_hat = 1 - gravity.(x - x_ref)/c_s^2                  */
+  int n_ext;            /* extension sweeps per step (Eq. hyperbolicExtension)      */
+  double dtau_ext;      /* extension pseudo time step                               */
+  int reinit_every;     /* reinitialise every this many finest steps (0 = never)    */
+  int n_reinit;         /* TVD-RK3 pseudo steps per reinitialisation                */
+  double dtau_reinit;   /* reinitialisation pseudo time step                        */
+  double refine_dist[4];/* sensor distance per level l < n_levels-1 (finest cells)  */
+  int sensor;           /* LSB_SENSOR_BAND or LSB_SENSOR_SIGNED                      */
+  int regrid_every;     /* regrid every this many coarse steps (0 = never)          */
+  int ls_active;        /* 0 freezes the level set (no transport, no refill)        */
+} lsb_params;
+
+/*
+ * Create a handle holding n_cases independent cases (an ensemble; n_cases = 1
+ * for a single simulation).  descs/params: arrays of n_cases host structs.
+ * phi0: array of n_cases DEVICE pointers, each the case's initial level set
+ * on its finest level (float, dense, x fastest, base * 2^(n_levels-1) cells
+ * per axis).  stream: a cudaStream_t (NULL = legacy default stream).
+ * The initial grid is refined from phi0 by the sensor (Sec. 2.6), the
+ * populations set to rest equilibrium with the hydrostatic density of
+ * params.gravity / x_ref.  On success *out receives the handle; the caller
+ * frees it with lsb_destroy.  Errors: LSB_EINVAL (bad descriptor or
+ * parameters, e.g. nu <= 0, odd block edge, mismatched lattices),
+ * LSB_ENOMEM, LSB_ECUDA.
+ */
+lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_params *params,
+                           const float *const *phi0, void *stream, lsb_grid **out);
+
+/* Replace the physics parameters of one case (case_idx) or all (-1); takes
+ * effect at the next step.  Grid-shaping fields (refine_dist, sensor) apply
+ * at the next regrid.  Errors: LSB_EINVAL. */
+lsb_status lsb_set_params(lsb_grid *g, int case_idx, const lsb_params *params);
+
+/* Advance every case by n coarse steps (each is 2^(n_levels-1) finest steps
+ * of that case), Sec. 2 method.  Asynchronous on the handle's stream. */
+lsb_status lsb_step(lsb_grid *g, int n);
+
+/* Run the refinement sensor and regrid every case now (Sec. 2.6). */
+lsb_status lsb_refine(lsb_grid *g);
+
+/*
+ * Copy one field of one level of one case into dst (dense over that level's
+ * box; see the LSB_FIELD_* list for element type and count).  dst_bytes must
+ * be at least the field size (lsb_field_bytes); dst_on_host selects a host
+ * or device destination.  Synchronises the stream.  Errors: LSB_EINVAL,
+ * LSB_ECUDA, or a latched device error.
+ */
+lsb_status lsb_get_fields(lsb_grid *g, int case_idx, int field, int level, void *dst,
+                          size_t dst_bytes, int dst_on_host);
+
+/* Bytes lsb_get_fields writes for (case, field, level); 0 for invalid input. */
+size_t lsb_field_bytes(const lsb_grid *g, int case_idx, int field, int level);
+
+/*
+ * Observables of every case in float64 (Sec. 3.2: bubble centroid and
+ * velocity as Heaviside-weighted integrals), written to a host array of
+ * n_cases * (4 + 2*D) doubles per case: mass liquid, mass gas, gas volume,
+ * number of leaf cells updated per coarse step, centroid[D], velocity[D];
+ * lengths in finest cells.  Synchronises.  LSB_EUNSTABLE if a density or
+ * velocity is not finite.
+ */
+lsb_status lsb_observables(lsb_grid *g, double *out_host, size_t n_doubles);
+
+/* Finest-level leaf cell updates one coarse step performs (sum over levels
+ * of leaf cells x 2^level), per case summed; the MLUPS numerator. */
+lsb_status lsb_cell_updates(const lsb_grid *g, double *updates_per_coarse_step);
+
+/*
+ * Adjoint of the bubble observables with respect to the parameters
+ * (Sec. 3.2 observables; no counterpart in the paper): not available in this
+ * build.  Always returns LSB_ESTATE.
+ */
+lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, float *dJ_dphi0);
+
+/* Wait for the handle's stream and return any latched device error. */
+lsb_status lsb_sync(lsb_grid *g);
+
+/* Number of kernels launched by the handle so far (all entry points). */
+uint64_t lsb_kernel_launches(const lsb_grid *g);
+
+/* Last error message of the handle, or of a failed lsb_create_grid when g is NULL. */
+const char *lsb_last_error(const lsb_grid *g);
+
+/* Free every device buffer of the handle.  NULL is ignored. */
+void lsb_destroy(lsb_grid *g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSB_H */

@@ -1,0 +1,1003 @@
+// Host runtime and C ABI of the lsb library (include/lsb.h).
+//
+// Owns every device buffer, builds the per-level block work lists, drives the
+// Dupuis-Chopard recursion over levels (Sec. 2.1 last paragraph) with the
+// finest-level interface, level-set and refill kernels, runs the refinement
+// sensor and regrid (Sec. 2.6) with host-side grading, and exports fields.
+// All cases of a handle (an ensemble) advance together: every launch covers
+// the blocks of all cases that own the level it works on.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lsb.h"
+#include "lsb_kernels.h"
+
+using namespace lsb;
+
+namespace {
+
+constexpr int MAXL = 4;
+
+struct WorkList {
+  int *d = nullptr;
+  int n = 0;
+  int cap = 0;
+  std::vector<int> h;
+};
+
+struct CaseHost {
+  lsb_grid_desc d;
+  lsb_params p;
+  int L = 1;
+  int ld0 = 0;  // first level descriptor of this case
+};
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct lsb_grid {
+  int ncase = 0, Q = 9, D = 2, storage = LSB_FP32, Lmax = 1;
+  int bs[3] = {1, 1, 1};
+  int nthreads = 0;
+  float fp16_scale = 1.f;
+  std::vector<CaseHost> cases;
+  std::vector<LevelDev> lds;
+  std::vector<std::vector<int8_t>> status;  // per ld
+  long long ncell_total = 0, nfine = 0;
+  int nblock_total = 0;
+  // device buffers
+  LevelDev *d_lds = nullptr;
+  int *d_blk_ld = nullptr;
+  int8_t *d_bstat = nullptr, *d_bstat_old = nullptr;
+  uint8_t *d_bflag = nullptr, *d_tag = nullptr, *d_frozen = nullptr;
+  void *d_buf[2] = {nullptr, nullptr};
+  float *d_phi = nullptr, *d_p1 = nullptr, *d_p2 = nullptr, *d_s0 = nullptr;
+  float *d_ut[3] = {nullptr, nullptr, nullptr};
+  uint32_t *d_cmask = nullptr;
+  int *d_cbase = nullptr;
+  float *d_macro = nullptr, *d_nvec = nullptr, *d_kappa = nullptr, *d_linkbuf = nullptr;
+  int *d_counters = nullptr, *d_err = nullptr, *d_band = nullptr;
+  int2 *d_iface = nullptr, *d_flip = nullptr;
+  double *d_obs = nullptr;
+  float *d_sens = nullptr;
+  long long link_cap = 0, list_cap = 0;
+  int band_cap = 0;
+  std::vector<void *> allocs;
+  // work lists per global level
+  WorkList cs[MAXL], rst[MAXL], ghost[MAXL], finest[MAXL], leaf, tags, sens, all_active;
+  std::vector<int> tags_prev;
+  int par[MAXL] = {0, 0, 0, 0};
+  long long fine_steps[MAXL] = {0, 0, 0, 0};
+  long long coarse_steps = 0;
+  // method parameters shared by all cases
+  int n_ext = 8, reinit_every = 1, n_reinit = 1, regrid_every = 0;
+  cudaStream_t stream = nullptr;
+  uint64_t launches = 0;
+  std::string err;
+  int latched = 0;
+};
+
+namespace {
+
+lsb_status fail(lsb_grid *g, lsb_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (g) g->err = buf;
+  else g_create_error = buf;
+  return s;
+}
+
+#define CU(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) return fail(g, LSB_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename P>
+lsb_status dalloc(lsb_grid *g, P **ptr, size_t bytes) {
+  void *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) return fail(g, LSB_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  g->allocs.push_back(p);
+  *ptr = reinterpret_cast<P *>(p);
+  return LSB_OK;
+}
+
+lsb_status upload_list(lsb_grid *g, WorkList &w) {
+  w.n = (int)w.h.size();
+  if (w.n > w.cap) {
+    int cap = std::max(w.n, 64);
+    int *p = nullptr;
+    lsb_status s = dalloc(g, &p, sizeof(int) * (size_t)cap);
+    if (s) return s;
+    w.d = p;
+    w.cap = cap;
+  }
+  if (w.n) CU(cudaMemcpyAsync(w.d, w.h.data(), sizeof(int) * w.n, cudaMemcpyHostToDevice, g->stream));
+  return LSB_OK;
+}
+
+Ctx make_ctx(lsb_grid *g) {
+  Ctx C;
+  memset(&C, 0, sizeof C);
+  C.lds = g->d_lds;
+  C.blk_ld = g->d_blk_ld;
+  C.bstat = g->d_bstat;
+  C.bstat_old = g->d_bstat_old;
+  C.bflag = g->d_bflag;
+  C.tag = g->d_tag;
+  C.buf[0] = g->d_buf[0];
+  C.buf[1] = g->d_buf[1];
+  for (int l = 0; l < MAXL; ++l) C.par[l] = g->par[l];
+  C.phi = g->d_phi;
+  C.p1 = g->d_p1;
+  C.p2 = g->d_p2;
+  C.s0 = g->d_s0;
+  C.frozen = g->d_frozen;
+  C.ut0 = g->d_ut[0];
+  C.ut1 = g->d_ut[1];
+  C.ut2 = g->d_ut[2];
+  C.cmask = g->d_cmask;
+  C.cbase = g->d_cbase;
+  C.macro = g->d_macro;
+  C.nvec = g->d_nvec;
+  C.kappa = g->d_kappa;
+  C.linkbuf = g->d_linkbuf;
+  C.nfine = g->nfine;
+  C.link_cap = g->link_cap;
+  C.counters = g->d_counters;
+  C.iface_list = g->d_iface;
+  C.flip_list = g->d_flip;
+  C.band_list = g->d_band;
+  C.list_cap = g->list_cap;
+  C.band_cap = g->band_cap;
+  C.err = g->d_err;
+  C.fp16_scale = g->fp16_scale;
+  C.fp16_inv = 1.0f / g->fp16_scale;
+  return C;
+}
+
+BlockShape shape(const lsb_grid *g) {
+  BlockShape S;
+  for (int a = 0; a < 3; ++a) S.bs[a] = g->bs[a];
+  return S;
+}
+
+// Count a launch and turn its error into a status.
+lsb_status launched(lsb_grid *g, cudaError_t e) {
+  g->launches++;
+  if (e != cudaSuccess) return fail(g, LSB_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+  return LSB_OK;
+}
+
+Launch LN(const lsb_grid *g, int grid, int block) { return Launch{grid, block, g->stream}; }
+
+#define RUN(grid, block, fn, ...) \
+  do { if ((grid) > 0) TRY(launched(g, fn(__VA_ARGS__))); } while (0)
+
+constexpr int DYN_GRID = 152 * 8;  // CTAs for kernels over device-sized lists
+
+#define TRY(x)                   \
+  do {                           \
+    lsb_status s_ = (x);         \
+    if (s_ != LSB_OK) return s_; \
+  } while (0)
+
+// ------------------------------------------------------------------ block topology helpers
+void block_coords(const LevelDev &L, int lb, int b[3]) {
+  b[0] = lb % L.nb[0];
+  b[1] = (lb / L.nb[0]) % L.nb[1];
+  b[2] = lb / (L.nb[0] * L.nb[1]);
+}
+
+template <typename F>
+void for_block_neighbors(const lsb_grid *g, const LevelDev &L, int lb, F fn) {
+  int b[3];
+  block_coords(L, lb, b);
+  const int zr = g->D == 3 ? 1 : 0;
+  for (int dz = -zr; dz <= zr; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        int c[3] = {b[0] + dx, b[1] + dy, b[2] + dz};
+        bool ok = true;
+        for (int a = 0; a < g->D; ++a) {
+          if (c[a] < 0 || c[a] >= L.nb[a]) {
+            if (L.per[a]) c[a] = (c[a] + L.nb[a]) % L.nb[a];
+            else ok = false;
+          }
+        }
+        if (ok) fn(c[0] + L.nb[0] * (c[1] + L.nb[1] * c[2]));
+      }
+}
+
+int parent_block(const LevelDev &Lc, const LevelDev &Lf, int lbf) {
+  int b[3];
+  block_coords(Lf, lbf, b);
+  return (b[0] / 2) + Lc.nb[0] * ((b[1] / 2) + Lc.nb[1] * (b[2] / 2));
+}
+
+// Grading from the finest level down, then statuses top-down (mirrors the oracle's reading).
+void grade_case(const lsb_grid *g, const CaseHost &ch, std::vector<std::vector<char>> &want,
+                std::vector<std::vector<int8_t>> &st) {
+  const int L = ch.L;
+  for (int l = L - 2; l >= 1; --l) {
+    const LevelDev &Lf = g->lds[ch.ld0 + l];
+    const LevelDev &Lc = g->lds[ch.ld0 + l - 1];
+    for (int b = 0; b < Lf.nblock; ++b) {
+      if (!want[l][b]) continue;
+      for_block_neighbors(g, Lf, b, [&](int nb) { want[l - 1][parent_block(Lc, Lf, nb)] = 1; });
+      want[l - 1][parent_block(Lc, Lf, b)] = 1;
+    }
+  }
+  st.assign(L, {});
+  for (int l = 0; l < L; ++l) {
+    const LevelDev &Ll = g->lds[ch.ld0 + l];
+    st[l].assign(Ll.nblock, BLK_INACTIVE);
+    for (int b = 0; b < Ll.nblock; ++b) {
+      bool act = l == 0 ? true : st[l - 1][parent_block(g->lds[ch.ld0 + l - 1], Ll, b)] == BLK_REFINED;
+      int8_t s = act ? BLK_LEAF : BLK_INACTIVE;
+      if (l < L - 1 && act && want[l][b]) s = BLK_REFINED;
+      st[l][b] = s;
+    }
+  }
+}
+
+bool any_neighbor(const lsb_grid *g, const LevelDev &L, const std::vector<int8_t> &st, int lb, int8_t what,
+                  bool active_any) {
+  bool r = false;
+  for_block_neighbors(g, L, lb, [&](int nb) {
+    if (active_any ? (st[nb] != BLK_INACTIVE) : (st[nb] == what)) r = true;
+  });
+  return r;
+}
+
+// Rebuild every host work list from the statuses and upload them.
+lsb_status build_lists(lsb_grid *g) {
+  for (int l = 0; l < MAXL; ++l) {
+    g->cs[l].h.clear();
+    g->rst[l].h.clear();
+    g->ghost[l].h.clear();
+    g->finest[l].h.clear();
+  }
+  g->leaf.h.clear();
+  g->all_active.h.clear();
+  std::vector<int> tl;
+  for (size_t ld = 0; ld < g->lds.size(); ++ld) {
+    const LevelDev &L = g->lds[ld];
+    const std::vector<int8_t> &st = g->status[ld];
+    const int l = L.level;
+    for (int b = 0; b < L.nblock; ++b) {
+      const int gb = L.block_off + b;
+      const int8_t s = st[b];
+      bool near_leaf = any_neighbor(g, L, st, b, BLK_LEAF, false);
+      bool near_active = any_neighbor(g, L, st, b, 0, true);
+      if (s == BLK_LEAF) {
+        g->cs[l].h.push_back(gb);
+        g->leaf.h.push_back(gb);
+        if (L.finest) g->finest[l].h.push_back(gb);
+      }
+      if (s != BLK_INACTIVE) g->all_active.h.push_back(gb);
+      if (s == BLK_REFINED && near_leaf) {
+        g->cs[l].h.push_back(gb);
+        g->rst[l].h.push_back(gb);
+      }
+      if (s == BLK_INACTIVE && near_active && l > 0) g->ghost[l].h.push_back(gb);
+      if (s != BLK_INACTIVE || near_active) tl.push_back(gb);
+    }
+  }
+  // tags: current relevant blocks plus the previous ones (stale bits get cleared)
+  std::vector<int> u = tl;
+  u.insert(u.end(), g->tags_prev.begin(), g->tags_prev.end());
+  std::sort(u.begin(), u.end());
+  u.erase(std::unique(u.begin(), u.end()), u.end());
+  g->tags.h = u;
+  g->tags_prev = tl;
+  for (int l = 0; l < MAXL; ++l) {
+    TRY(upload_list(g, g->cs[l]));
+    TRY(upload_list(g, g->rst[l]));
+    TRY(upload_list(g, g->ghost[l]));
+    TRY(upload_list(g, g->finest[l]));
+  }
+  TRY(upload_list(g, g->leaf));
+  TRY(upload_list(g, g->tags));
+  TRY(upload_list(g, g->all_active));
+  return LSB_OK;
+}
+
+lsb_status upload_status(lsb_grid *g, const std::vector<std::vector<int8_t>> &st) {
+  std::vector<int8_t> flat(g->nblock_total);
+  for (size_t ld = 0; ld < g->lds.size(); ++ld)
+    std::copy(st[ld].begin(), st[ld].end(), flat.begin() + g->lds[ld].block_off);
+  CU(cudaMemcpyAsync(g->d_bstat, flat.data(), flat.size(), cudaMemcpyHostToDevice, g->stream));
+  CU(cudaStreamSynchronize(g->stream));  // flat is a host temporary
+  return LSB_OK;
+}
+
+lsb_status level_tags(lsb_grid *g) {
+  Ctx C = make_ctx(g);
+  BlockShape S = shape(g);
+  RUN(g->tags.n, g->nthreads, run_level_tags, g->Q, LN(g, g->tags.n, g->nthreads), C, S, (const int *)g->tags.d,
+      g->tags.n);
+  return LSB_OK;
+}
+
+bool has_finest(const lsb_grid *g, int l) {
+  for (const CaseHost &c : g->cases)
+    if (c.L - 1 == l) return true;
+  return false;
+}
+
+// Classification of the finest level l: phases, flips, cut links, band; then geometry.
+lsb_status classify(lsb_grid *g, int l, int init) {
+  if (!has_finest(g, l)) return LSB_OK;
+  CU(cudaMemsetAsync(g->d_counters + l * NCOUNT, 0, sizeof(int) * NCOUNT, g->stream));
+  Ctx C = make_ctx(g);
+  BlockShape S = shape(g);
+  WorkList &F = g->finest[l];
+  const int *fl = F.d;
+  const int Q = g->Q, D = g->D, nt = g->nthreads;
+  RUN(F.n, nt, run_classify_phase, Q, LN(g, F.n, nt), C, S, fl, F.n, l, init);
+  RUN(F.n, nt, run_classify_links, Q, LN(g, F.n, nt), C, S, fl, F.n, l);
+  RUN(F.n, 128, run_band, Q, LN(g, (F.n + 127) / 128, 128), C, S, fl, F.n, l);
+  RUN(1, 128, run_geometry, D, LN(g, DYN_GRID, 128), C, l, 0);
+  RUN(1, 128, run_geometry, D, LN(g, DYN_GRID, 128), C, l, 1);
+  return LSB_OK;
+}
+
+// Level-set update of the finest level l (extension, transport, reinitialisation).
+lsb_status levelset(lsb_grid *g, int l) {
+  Ctx C = make_ctx(g);
+  BlockShape S = shape(g);
+  const int nb = std::max(1, std::min(g->band_cap, 152 * 16));
+  const int nt = g->nthreads;
+  const int Q = g->Q, D = g->D;
+  RUN(1, 128, run_ext_init, Q, LN(g, DYN_GRID, 128), C, l);
+  const float *uin = g->d_ut[0];
+  for (int it = 0; it < g->n_ext; ++it) {
+    float *uout = g->d_ut[1 + (it & 1)];
+    RUN(nb, nt, run_ext_iter, D, LN(g, nb, nt), C, S, l, uin, uout, 0);
+    uin = uout;
+  }
+  if (g->n_ext > 0) {
+    RUN(nb, nt, run_ext_iter, D, LN(g, nb, nt), C, S, l, uin, (float *)nullptr, 1);
+  }
+  for (int st = 1; st <= 3; ++st) {
+    RUN(nb, nt, run_adv_stage, D, LN(g, nb, nt), C, S, l, st);
+  }
+  const bool due = g->reinit_every > 0 && ((g->fine_steps[l] + 1) % g->reinit_every == 0);
+  if (due && g->n_reinit > 0) {
+    RUN(nb, nt, run_reinit_prep, Q, LN(g, nb, nt), C, S, l);
+    for (int r = 0; r < g->n_reinit; ++r)
+      for (int st = 1; st <= 3; ++st) {
+        RUN(nb, nt, run_reinit_stage, D, LN(g, nb, nt), C, S, l, st);
+      }
+  }
+  return LSB_OK;
+}
+
+bool ls_active_any(const lsb_grid *g, int l) {
+  for (const CaseHost &c : g->cases)
+    if (c.L - 1 == l && c.p.ls_active) return true;
+  return false;
+}
+
+// One advance of global level l (recursive over finer levels).
+lsb_status advance(lsb_grid *g, int l) {
+  BlockShape S = shape(g);
+  const int nt = g->nthreads;
+  Ctx C = make_ctx(g);
+  const int Q = g->Q, st = g->storage;
+  RUN(g->rst[l].n, nt, run_restrict, Q, st, LN(g, g->rst[l].n, nt), C, S, (const int *)g->rst[l].d, g->rst[l].n, 0);
+  RUN(g->cs[l].n, nt, run_collide_stream, Q, st, LN(g, g->cs[l].n, nt), C, S, (const int *)g->cs[l].d, g->cs[l].n);
+  if (has_finest(g, l)) {
+    RUN(1, 128, run_interface_bc, Q, st, LN(g, DYN_GRID, 128), C, l);
+    if (ls_active_any(g, l)) TRY(levelset(g, l));
+    TRY(classify(g, l, 0));
+    C = make_ctx(g);
+    RUN(1, 128, run_refill, Q, st, LN(g, DYN_GRID, 128), C, l);
+    g->fine_steps[l]++;
+  }
+  if (l + 1 < g->Lmax) {
+    const WorkList &gh = g->ghost[l + 1];
+    for (int sub = 0; sub < 2; ++sub) {
+      C = make_ctx(g);
+      const float theta = sub == 0 ? 0.0f : 0.5f;
+      RUN(gh.n, nt, run_ghost, Q, st, LN(g, gh.n, nt), C, S, (const int *)gh.d, gh.n, theta);
+      TRY(advance(g, l + 1));
+    }
+  }
+  g->par[l] ^= 1;
+  return LSB_OK;
+}
+
+lsb_status regrid(lsb_grid *g, bool initial);
+
+lsb_status check_params(const lsb_params &p, const lsb_grid_desc &d, std::string &why) {
+  char b[256];
+  for (int k = 0; k < 2; ++k) {
+    if (!(p.rho[k] > 0) || !(p.nu[k] > 0) || !std::isfinite(p.rho[k]) || !std::isfinite(p.nu[k])) {
+      snprintf(b, sizeof b, "rho and nu must be positive (phase %d)", k);
+      why = b;
+      return LSB_EINVAL;
+    }
+  }
+  if (p.n_ext < 0 || p.reinit_every < 0 || p.n_reinit < 0 || p.regrid_every < 0) {
+    why = "negative iteration count";
+    return LSB_EINVAL;
+  }
+  if (!(p.sigma >= 0)) { why = "sigma must be >= 0"; return LSB_EINVAL; }
+  if (p.sensor != LSB_SENSOR_BAND && p.sensor != LSB_SENSOR_SIGNED) { why = "unknown sensor"; return LSB_EINVAL; }
+  (void)d;
+  return LSB_OK;
+}
+
+void fill_physics(lsb_grid *g, LevelDev &L, const CaseHost &ch) {
+  const lsb_params &p = ch.p;
+  const float scale = (float)L.scale;
+  for (int k = 0; k < 2; ++k) {
+    const double nu = p.nu[k] / L.scale;
+    L.tau[k] = (float)(3.0 * nu + 0.5);
+    L.omega[k] = (float)(1.0 / (3.0 * nu + 0.5));
+    for (int a = 0; a < 3; ++a) L.acc[k][a] = (float)((p.gravity[a] + p.body_force[a] / p.rho[k]) * scale);
+    L.rho_phys[k] = (float)p.rho[k];
+    L.eta[k] = (float)(p.rho[k] * p.nu[k]);
+  }
+  for (int f = 0; f < 6; ++f)
+    for (int a = 0; a < 3; ++a) L.wall_u[f][a] = (float)ch.d.wall_u[f][a];
+  L.sigma = (float)p.sigma;
+  L.dtau_ext = (float)p.dtau_ext;
+  L.dtau_reinit = (float)p.dtau_reinit;
+  for (int a = 0; a < 3; ++a) {
+    L.x_ref[a] = (float)p.x_ref[a];
+    L.grav[a] = (float)p.gravity[a];
+  }
+  L.ls_active = p.ls_active;
+  (void)g;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_params *params,
+                           const float *const *phi0, void *stream, lsb_grid **out) {
+  lsb_grid *g = nullptr;
+  if (!out) return fail(nullptr, LSB_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_cases < 1 || !descs || !params || !phi0) return fail(nullptr, LSB_EINVAL, "need n_cases >= 1 and arrays");
+  const lsb_grid_desc &d0 = descs[0];
+  if (d0.lattice != LSB_D2Q9 && d0.lattice != LSB_D3Q19) return fail(nullptr, LSB_EINVAL, "unknown lattice");
+  if (d0.storage != LSB_FP32 && d0.storage != LSB_FP16S) return fail(nullptr, LSB_EINVAL, "unknown storage");
+  const int D = d0.lattice == LSB_D2Q9 ? 2 : 3;
+  int bs[3] = {d0.block[0], d0.block[1], D == 3 ? d0.block[2] : 1};
+  for (int a = 0; a < D; ++a)
+    if (bs[a] < 2 || bs[a] % 2) return fail(nullptr, LSB_EINVAL, "block edges must be even and >= 2");
+  const int nthreads = bs[0] * bs[1] * bs[2];
+  if (nthreads % 32 || nthreads > 1024) return fail(nullptr, LSB_EINVAL, "block must hold 32..1024 cells, a multiple of 32");
+  for (int c = 0; c < n_cases; ++c) {
+    const lsb_grid_desc &d = descs[c];
+    if (d.lattice != d0.lattice || d.storage != d0.storage) return fail(nullptr, LSB_EINVAL, "cases must share lattice and storage");
+    for (int a = 0; a < 3; ++a)
+      if (d.block[a] != d0.block[a] && (a < D)) return fail(nullptr, LSB_EINVAL, "cases must share the block shape");
+    if (d.n_levels < 1 || d.n_levels > MAXL) return fail(nullptr, LSB_EINVAL, "n_levels must be 1..%d", MAXL);
+    for (int a = 0; a < D; ++a) {
+      if (d.base[a] < 1) return fail(nullptr, LSB_EINVAL, "base must be positive");
+      if (d.bc[a] != LSB_PERIODIC && d.bc[a] != LSB_WALL) return fail(nullptr, LSB_EINVAL, "bad bc");
+    }
+    std::string why;
+    if (check_params(params[c], d, why)) return fail(nullptr, LSB_EINVAL, "case %d: %s", c, why.c_str());
+    if (!phi0[c]) return fail(nullptr, LSB_EINVAL, "phi0[%d] is NULL", c);
+    const lsb_params &p = params[c], &p0 = params[0];
+    if (p.n_ext != p0.n_ext || p.reinit_every != p0.reinit_every || p.n_reinit != p0.n_reinit ||
+        p.regrid_every != p0.regrid_every)
+      return fail(nullptr, LSB_EINVAL, "cases must share the level-set iteration counts and regrid period");
+  }
+  if (d0.storage == LSB_FP16S && !(d0.fp16_scale > 0)) return fail(nullptr, LSB_EINVAL, "fp16_scale must be > 0");
+
+  g = new lsb_grid();
+  g->ncase = n_cases;
+  g->Q = D == 2 ? 9 : 19;
+  g->D = D;
+  g->storage = d0.storage;
+  g->fp16_scale = d0.storage == LSB_FP16S ? (float)d0.fp16_scale : 1.0f;
+  for (int a = 0; a < 3; ++a) g->bs[a] = bs[a];
+  g->nthreads = nthreads;
+  g->stream = (cudaStream_t)stream;
+  g->n_ext = params[0].n_ext;
+  g->reinit_every = params[0].reinit_every;
+  g->n_reinit = params[0].n_reinit;
+  g->regrid_every = params[0].regrid_every;
+  // level descriptors
+  long long cell_off = 0, fine_off = 0;
+  int block_off = 0;
+  for (int c = 0; c < n_cases; ++c) {
+    CaseHost ch;
+    ch.d = descs[c];
+    ch.p = params[c];
+    ch.L = descs[c].n_levels;
+    ch.ld0 = (int)g->lds.size();
+    g->Lmax = std::max(g->Lmax, ch.L);
+    for (int l = 0; l < ch.L; ++l) {
+      LevelDev L;
+      memset(&L, 0, sizeof L);
+      L.case_id = c;
+      L.level = l;
+      L.n_levels = ch.L;
+      L.finest = l == ch.L - 1;
+      L.scale = 1 << (ch.L - 1 - l);
+      L.ncell = 1;
+      for (int a = 0; a < 3; ++a) {
+        L.n[a] = a < D ? descs[c].base[a] << l : 1;
+        L.p[a] = ((L.n[a] + bs[a] - 1) / bs[a]) * bs[a];
+        L.nb[a] = L.p[a] / bs[a];
+        L.per[a] = a < D ? (descs[c].bc[a] == LSB_PERIODIC) : 1;
+        L.ncell *= L.p[a];
+      }
+      L.nblock = L.nb[0] * L.nb[1] * L.nb[2];
+      L.cell_off = cell_off;
+      L.block_off = block_off;
+      L.fine_off = L.finest ? fine_off : -1;
+      L.parent_ld = l > 0 ? ch.ld0 + l - 1 : -1;
+      L.child_ld = l < ch.L - 1 ? ch.ld0 + l + 1 : -1;
+      L.fine_ld = ch.ld0 + ch.L - 1;
+      fill_physics(g, L, ch);
+      cell_off += L.ncell;
+      block_off += L.nblock;
+      if (L.finest) fine_off += L.ncell;
+      g->lds.push_back(L);
+    }
+    g->cases.push_back(ch);
+  }
+  g->ncell_total = cell_off;
+  g->nblock_total = block_off;
+  g->nfine = fine_off;
+  const long long nf = g->nfine;
+  const int Q = g->Q;
+  const size_t fsz = g->storage == LSB_FP32 ? 4 : 2;
+  const int MF = 1 + D + D * (D + 1) / 2;
+  g->list_cap = std::min<long long>(nf, std::max<long long>(1 << 16, nf / 4));
+  g->link_cap = std::min<long long>((long long)Q * nf, std::max<long long>(1 << 18, 2 * nf));
+  g->band_cap = 0;
+  for (const LevelDev &L : g->lds)
+    if (L.finest) g->band_cap += L.nblock;
+  lsb_status s = LSB_OK;
+#define ALLOC(ptr, bytes)                              \
+  do {                                             \
+    s = dalloc(g, &(ptr), (size_t)(bytes));        \
+    if (s) { g_create_error = g->err; lsb_destroy(g); return s; } \
+  } while (0)
+  ALLOC(g->d_lds, sizeof(LevelDev) * g->lds.size());
+  ALLOC(g->d_blk_ld, sizeof(int) * g->nblock_total);
+  ALLOC(g->d_bstat, g->nblock_total);
+  ALLOC(g->d_bstat_old, g->nblock_total);
+  ALLOC(g->d_bflag, g->nblock_total);
+  ALLOC(g->d_tag, g->ncell_total);
+  ALLOC(g->d_buf[0], fsz * Q * g->ncell_total);
+  ALLOC(g->d_buf[1], fsz * Q * g->ncell_total);
+  ALLOC(g->d_phi, 4 * nf);
+  ALLOC(g->d_p1, 4 * nf);
+  ALLOC(g->d_p2, 4 * nf);
+  ALLOC(g->d_s0, 4 * nf);
+  ALLOC(g->d_frozen, nf);
+  for (int k = 0; k < 3; ++k) ALLOC(g->d_ut[k], 4 * D * nf);
+  ALLOC(g->d_cmask, 4 * nf);
+  ALLOC(g->d_cbase, 4 * nf);
+  ALLOC(g->d_macro, 4 * (size_t)MF * nf);
+  ALLOC(g->d_nvec, 4 * D * nf);
+  ALLOC(g->d_kappa, 4 * nf);
+  ALLOC(g->d_linkbuf, 8 * g->link_cap);
+  ALLOC(g->d_counters, sizeof(int) * MAXL * NCOUNT);
+  ALLOC(g->d_err, sizeof(int));
+  ALLOC(g->d_iface, sizeof(int2) * MAXL * g->list_cap);
+  ALLOC(g->d_flip, sizeof(int2) * MAXL * g->list_cap);
+  ALLOC(g->d_band, sizeof(int) * MAXL * (size_t)std::max(1, g->band_cap));
+  ALLOC(g->d_obs, sizeof(double) * n_cases * 16);
+  ALLOC(g->d_sens, sizeof(float) * g->nblock_total);
+#undef ALLOC
+  // block -> level descriptor
+  std::vector<int> bl(g->nblock_total);
+  for (size_t ld = 0; ld < g->lds.size(); ++ld)
+    for (int b = 0; b < g->lds[ld].nblock; ++b) bl[g->lds[ld].block_off + b] = (int)ld;
+  auto cuerr = [&](cudaError_t e, const char *what) -> bool {
+    if (e == cudaSuccess) return false;
+    g_create_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return true;
+  };
+  if (cuerr(cudaMemcpy(g->d_lds, g->lds.data(), sizeof(LevelDev) * g->lds.size(), cudaMemcpyHostToDevice), "lds") ||
+      cuerr(cudaMemcpy(g->d_blk_ld, bl.data(), sizeof(int) * bl.size(), cudaMemcpyHostToDevice), "blk_ld") ||
+      cuerr(cudaMemset(g->d_tag, 0, g->ncell_total), "tag") ||
+      cuerr(cudaMemset(g->d_bflag, 0, g->nblock_total), "bflag") ||
+      cuerr(cudaMemset(g->d_err, 0, sizeof(int)), "err") ||
+      cuerr(cudaMemset(g->d_counters, 0, sizeof(int) * MAXL * NCOUNT), "counters") ||
+      cuerr(cudaMemset(g->d_cmask, 0, 4 * nf), "cmask") ||
+      cuerr(cudaMemset(g->d_nvec, 0, 4 * D * nf), "nvec") ||
+      cuerr(cudaMemset(g->d_kappa, 0, 4 * nf), "kappa") ||
+      cuerr(cudaMemset(g->d_macro, 0, 4 * (size_t)MF * nf), "macro") ||
+      cuerr(cudaMemset(g->d_buf[0], 0, fsz * Q * g->ncell_total), "buf0") ||
+      cuerr(cudaMemset(g->d_buf[1], 0, fsz * Q * g->ncell_total), "buf1")) {
+    lsb_destroy(g);
+    return LSB_ECUDA;
+  }
+  for (int k = 0; k < 3; ++k)
+    if (cuerr(cudaMemset(g->d_ut[k], 0, 4 * D * nf), "ut")) { lsb_destroy(g); return LSB_ECUDA; }
+  // phi: dense caller array -> padded finest array
+  for (int c = 0; c < n_cases; ++c) {
+    const LevelDev &F = g->lds[g->cases[c].ld0 + g->cases[c].L - 1];
+    if (cuerr(cudaMemset(g->d_phi + F.fine_off, 0, 4 * F.ncell), "phi")) { lsb_destroy(g); return LSB_ECUDA; }
+    cudaMemcpy3DParms pr;
+    memset(&pr, 0, sizeof pr);
+    pr.srcPtr = make_cudaPitchedPtr((void *)phi0[c], sizeof(float) * F.n[0], F.n[0], F.n[1]);
+    pr.dstPtr = make_cudaPitchedPtr(g->d_phi + F.fine_off, sizeof(float) * F.p[0], F.p[0], F.p[1]);
+    pr.extent = make_cudaExtent(sizeof(float) * F.n[0], F.n[1], F.n[2]);
+    pr.kind = cudaMemcpyDeviceToDevice;
+    if (cuerr(cudaMemcpy3D(&pr), "phi0 copy")) { lsb_destroy(g); return LSB_ECUDA; }
+  }
+  s = regrid(g, true);
+  if (s) { g_create_error = g->err; lsb_destroy(g); return s; }
+  *out = g;
+  return LSB_OK;
+}
+
+lsb_status lsb_set_params(lsb_grid *g, int case_idx, const lsb_params *params) {
+  if (!g || !params) return LSB_EINVAL;
+  if (case_idx < -1 || case_idx >= g->ncase) return fail(g, LSB_EINVAL, "case_idx out of range");
+  for (int c = 0; c < g->ncase; ++c) {
+    if (case_idx != -1 && c != case_idx) continue;
+    std::string why;
+    if (check_params(*params, g->cases[c].d, why)) return fail(g, LSB_EINVAL, "%s", why.c_str());
+  }
+  if (params->n_ext != g->n_ext || params->reinit_every != g->reinit_every || params->n_reinit != g->n_reinit)
+    if (g->ncase > 1 && case_idx != -1) return fail(g, LSB_EINVAL, "level-set iteration counts are shared by all cases");
+  for (int c = 0; c < g->ncase; ++c) {
+    if (case_idx != -1 && c != case_idx) continue;
+    g->cases[c].p = *params;
+    for (int l = 0; l < g->cases[c].L; ++l) fill_physics(g, g->lds[g->cases[c].ld0 + l], g->cases[c]);
+  }
+  g->n_ext = params->n_ext;
+  g->reinit_every = params->reinit_every;
+  g->n_reinit = params->n_reinit;
+  g->regrid_every = params->regrid_every;
+  CU(cudaMemcpyAsync(g->d_lds, g->lds.data(), sizeof(LevelDev) * g->lds.size(), cudaMemcpyHostToDevice, g->stream));
+  CU(cudaStreamSynchronize(g->stream));
+  return LSB_OK;
+}
+
+lsb_status lsb_step(lsb_grid *g, int n) {
+  if (!g || n < 0) return LSB_EINVAL;
+  for (int k = 0; k < n; ++k) {
+    TRY(advance(g, 0));
+    g->coarse_steps++;
+    if (g->regrid_every > 0 && g->Lmax > 1 && g->coarse_steps % g->regrid_every == 0) TRY(regrid(g, false));
+  }
+  return LSB_OK;
+}
+
+lsb_status lsb_refine(lsb_grid *g) {
+  if (!g) return LSB_EINVAL;
+  return regrid(g, false);
+}
+
+lsb_status lsb_sync(lsb_grid *g) {
+  if (!g) return LSB_EINVAL;
+  CU(cudaStreamSynchronize(g->stream));
+  int e = 0;
+  CU(cudaMemcpy(&e, g->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  g->latched |= e;
+  if (g->latched & (ERR_LINK_OVF | ERR_LIST_OVF | ERR_BAND_OVF))
+    return fail(g, LSB_ENOMEM, "device work list overflow (flags %d)", g->latched);
+  if (g->latched & ERR_NONFINITE) return fail(g, LSB_EUNSTABLE, "non-finite density or velocity");
+  return LSB_OK;
+}
+
+size_t lsb_field_bytes(const lsb_grid *g, int case_idx, int field, int level) {
+  if (!g || case_idx < 0 || case_idx >= g->ncase) return 0;
+  const CaseHost &ch = g->cases[case_idx];
+  if (level < 0 || level >= ch.L) return 0;
+  const LevelDev &L = g->lds[ch.ld0 + level];
+  const size_t n = (size_t)L.n[0] * L.n[1] * L.n[2];
+  const bool fine_only = field == LSB_FIELD_PHI || field == LSB_FIELD_CUTMASK || field == LSB_FIELD_KAPPA ||
+                         field == LSB_FIELD_UEXT;
+  if (fine_only && !L.finest) return 0;
+  switch (field) {
+    case LSB_FIELD_RHO: case LSB_FIELD_PHI: case LSB_FIELD_KAPPA: return 4 * n;
+    case LSB_FIELD_U: case LSB_FIELD_UEXT: return 4 * n * g->D;
+    case LSB_FIELD_PHASE: case LSB_FIELD_TAG: return n;
+    case LSB_FIELD_F: return 4 * n * g->Q;
+    case LSB_FIELD_BLOCKS: return (size_t)L.nblock;
+    case LSB_FIELD_CUTMASK: return 4 * n;
+    default: return 0;
+  }
+}
+
+lsb_status lsb_get_fields(lsb_grid *g, int case_idx, int field, int level, void *dst, size_t dst_bytes,
+                          int dst_on_host) {
+  if (!g || !dst) return LSB_EINVAL;
+  const size_t need = lsb_field_bytes(g, case_idx, field, level);
+  if (need == 0) return fail(g, LSB_EINVAL, "invalid case/field/level");
+  if (dst_bytes < need) return fail(g, LSB_EINVAL, "dst too small: %zu < %zu", dst_bytes, need);
+  const CaseHost &ch = g->cases[case_idx];
+  const int ld = ch.ld0 + level;
+  const LevelDev &L = g->lds[ld];
+  const size_t n = (size_t)L.n[0] * L.n[1] * L.n[2];
+  const cudaMemcpyKind kind = dst_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (field == LSB_FIELD_BLOCKS) {
+    if (dst_on_host) memcpy(dst, g->status[ld].data(), L.nblock);
+    else CU(cudaMemcpy(dst, g->status[ld].data(), L.nblock, cudaMemcpyHostToDevice));
+    return lsb_sync(g);
+  }
+  if (field == LSB_FIELD_RHO || field == LSB_FIELD_U || field == LSB_FIELD_F) {
+    float *tmp = nullptr;
+    CU(cudaMalloc(&tmp, need));
+    Ctx C = make_ctx(g);
+    const int fcode = field == LSB_FIELD_RHO ? 0 : (field == LSB_FIELD_U ? 1 : 4);
+    lsb_status s = LSB_OK;
+    s = launched(g, run_export(g->Q, g->storage, LN(g, 1024, 256), C, ld, fcode, tmp));
+    if (s == LSB_OK) {
+      cudaError_t e = cudaMemcpyAsync(dst, tmp, need, kind, g->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+      if (e != cudaSuccess) s = fail(g, LSB_ECUDA, "export copy: %s", cudaGetErrorString(e));
+    }
+    cudaFree(tmp);
+    if (s) return s;
+    return lsb_sync(g);
+  }
+  // plain per-cell arrays: strided 3-D copies from the padded layout
+  const void *src = nullptr;
+  size_t esz = 4;
+  int planes = 1;
+  long long plane_stride = 0;
+  switch (field) {
+    case LSB_FIELD_PHI: src = g->d_phi + L.fine_off; break;
+    case LSB_FIELD_KAPPA: src = g->d_kappa + L.fine_off; break;
+    case LSB_FIELD_CUTMASK: src = g->d_cmask + L.fine_off; break;
+    case LSB_FIELD_UEXT: src = g->d_ut[0] + L.fine_off; planes = g->D; plane_stride = g->nfine; break;
+    case LSB_FIELD_PHASE: case LSB_FIELD_TAG: src = g->d_tag + L.cell_off; esz = 1; break;
+    default: return fail(g, LSB_EINVAL, "field");
+  }
+  CU(cudaStreamSynchronize(g->stream));
+  for (int pl = 0; pl < planes; ++pl) {
+    cudaMemcpy3DParms pr;
+    memset(&pr, 0, sizeof pr);
+    const char *sp = (const char *)src + esz * plane_stride * pl;
+    pr.srcPtr = make_cudaPitchedPtr((void *)sp, esz * L.p[0], L.p[0], L.p[1]);
+    pr.dstPtr = make_cudaPitchedPtr((char *)dst + esz * n * pl, esz * L.n[0], L.n[0], L.n[1]);
+    pr.extent = make_cudaExtent(esz * L.n[0], L.n[1], L.n[2]);
+    pr.kind = kind;
+    CU(cudaMemcpy3D(&pr));
+  }
+  if (field == LSB_FIELD_PHASE) {
+    if (dst_on_host) {
+      uint8_t *p = (uint8_t *)dst;
+      for (size_t i = 0; i < n; ++i) p[i] &= TAG_GAS;
+    } else {
+      std::vector<uint8_t> h(n);
+      CU(cudaMemcpy(h.data(), dst, n, cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < n; ++i) h[i] &= TAG_GAS;
+      CU(cudaMemcpy(dst, h.data(), n, cudaMemcpyHostToDevice));
+    }
+  }
+  return lsb_sync(g);
+}
+
+lsb_status lsb_observables(lsb_grid *g, double *out_host, size_t n_doubles) {
+  if (!g || !out_host) return LSB_EINVAL;
+  const int stride = 4 + 2 * g->D;
+  if (n_doubles < (size_t)stride * g->ncase) return fail(g, LSB_EINVAL, "need %d doubles", stride * g->ncase);
+  CU(cudaMemsetAsync(g->d_obs, 0, sizeof(double) * stride * g->ncase, g->stream));
+  Ctx C = make_ctx(g);
+  BlockShape S = shape(g);
+  RUN(g->leaf.n, g->nthreads, run_observables, g->Q, g->storage, LN(g, g->leaf.n, g->nthreads), C, S,
+      (const int *)g->leaf.d, g->leaf.n, g->d_obs, stride);
+  std::vector<double> h((size_t)stride * g->ncase);
+  CU(cudaMemcpyAsync(h.data(), g->d_obs, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g->stream));
+  lsb_status s = lsb_sync(g);
+  for (int c = 0; c < g->ncase; ++c) {
+    double *o = out_host + (size_t)stride * c;
+    const double *v = h.data() + (size_t)stride * c;
+    o[0] = v[0];
+    o[1] = v[1];
+    o[2] = v[2];
+    o[3] = v[3];
+    for (int a = 0; a < g->D; ++a) {
+      o[4 + a] = v[2] > 0 ? v[4 + a] / v[2] : NAN;
+      o[4 + g->D + a] = v[2] > 0 ? v[4 + g->D + a] / v[2] : NAN;
+    }
+  }
+  return s;
+}
+
+lsb_status lsb_cell_updates(const lsb_grid *g, double *upd) {
+  if (!g || !upd) return LSB_EINVAL;
+  double total = 0;
+  for (size_t ld = 0; ld < g->lds.size(); ++ld) {
+    const LevelDev &L = g->lds[ld];
+    long long leaf_cells = 0;
+    for (int b = 0; b < L.nblock; ++b) {
+      if (g->status[ld][b] != BLK_LEAF) continue;
+      int bc[3];
+      block_coords(L, b, bc);
+      long long cnt = 1;
+      for (int a = 0; a < 3; ++a) cnt *= std::min(g->bs[a], L.n[a] - bc[a] * g->bs[a]);
+      leaf_cells += cnt;
+    }
+    total += (double)leaf_cells * (double)(1LL << L.level);
+  }
+  *upd = total;
+  return LSB_OK;
+}
+
+lsb_status lsb_backward(lsb_grid *g, const double *, double *, float *) {
+  if (!g) return LSB_EINVAL;
+  return fail(g, LSB_ESTATE, "the adjoint is not available in this build");
+}
+
+uint64_t lsb_kernel_launches(const lsb_grid *g) { return g ? g->launches : 0; }
+
+const char *lsb_last_error(const lsb_grid *g) { return g ? g->err.c_str() : g_create_error.c_str(); }
+
+void lsb_destroy(lsb_grid *g) {
+  if (!g) return;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  else cudaDeviceSynchronize();
+  for (void *p : g->allocs) cudaFree(p);
+  delete g;
+}
+
+// Velocity-set tables compiled into the library, for host-side checks:
+// c (Q x 3 ints), w (Q floats), opp (Q ints).  Returns Q, or 0 for an unknown lattice.
+int lsb_lattice_table(int lattice, int *c, float *w, int *opp) {
+  if (lattice == LSB_D2Q9) {
+    for (int i = 0; i < 9; ++i) {
+      if (c) { c[3 * i] = Lat<9>::cx(i); c[3 * i + 1] = Lat<9>::cy(i); c[3 * i + 2] = 0; }
+      if (w) w[i] = Lat<9>::w(i);
+      if (opp) opp[i] = Lat<9>::opp(i);
+    }
+    return 9;
+  }
+  if (lattice == LSB_D3Q19) {
+    for (int i = 0; i < 19; ++i) {
+      if (c) { c[3 * i] = Lat<19>::cx(i); c[3 * i + 1] = Lat<19>::cy(i); c[3 * i + 2] = Lat<19>::cz(i); }
+      if (w) w[i] = Lat<19>::w(i);
+      if (opp) opp[i] = Lat<19>::opp(i);
+    }
+    return 19;
+  }
+  return 0;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ regrid
+namespace {
+
+lsb_status regrid(lsb_grid *g, bool initial) {
+  BlockShape S = shape(g);
+  const int nt = g->nthreads;
+  // sensor over every block of every non-finest level
+  g->sens.h.clear();
+  for (const CaseHost &ch : g->cases)
+    for (int l = 0; l < ch.L - 1; ++l) {
+      const LevelDev &L = g->lds[ch.ld0 + l];
+      for (int b = 0; b < L.nblock; ++b) g->sens.h.push_back(L.block_off + b);
+    }
+  std::vector<float> sv(g->sens.h.size());
+  if (!g->sens.h.empty()) {
+    TRY(upload_list(g, g->sens));
+    Ctx C = make_ctx(g);
+    // mode per case: launch once per mode present (cases with the other mode are overwritten below)
+    for (int mode = 0; mode < 2; ++mode) {
+      bool any = false;
+      for (const CaseHost &ch : g->cases) any |= (ch.p.sensor == mode);
+      if (!any) continue;
+      RUN(g->sens.n, 256, run_sensor, LN(g, g->sens.n, 256), C, S, (const int *)g->sens.d, g->sens.n, mode, g->d_sens);
+      std::vector<float> tmp(g->sens.h.size());
+      CU(cudaMemcpyAsync(tmp.data(), g->d_sens, sizeof(float) * tmp.size(), cudaMemcpyDeviceToHost, g->stream));
+      CU(cudaStreamSynchronize(g->stream));
+      size_t k = 0;
+      for (const CaseHost &ch : g->cases)
+        for (int l = 0; l < ch.L - 1; ++l) {
+          const LevelDev &L = g->lds[ch.ld0 + l];
+          for (int b = 0; b < L.nblock; ++b, ++k)
+            if (ch.p.sensor == mode) sv[k] = tmp[k];
+        }
+    }
+  }
+  // wanted refinement and grading per case
+  std::vector<std::vector<int8_t>> newst(g->lds.size());
+  size_t k = 0;
+  for (const CaseHost &ch : g->cases) {
+    std::vector<std::vector<char>> want(ch.L);
+    for (int l = 0; l < ch.L - 1; ++l) {
+      const LevelDev &L = g->lds[ch.ld0 + l];
+      want[l].assign(L.nblock, 0);
+      const double dref = ch.p.refine_dist[l];
+      for (int b = 0; b < L.nblock; ++b, ++k)
+        want[l][b] = ch.p.sensor == LSB_SENSOR_SIGNED ? (sv[k] >= -dref) : (sv[k] <= dref);
+    }
+    std::vector<std::vector<int8_t>> st;
+    grade_case(g, ch, want, st);
+    for (int l = 0; l < ch.L; ++l) newst[ch.ld0 + l] = st[l];
+  }
+  if (initial) {
+    g->status = newst;
+    TRY(upload_status(g, g->status));
+    TRY(build_lists(g));
+    TRY(level_tags(g));
+    Ctx C = make_ctx(g);
+    RUN(g->all_active.n, nt, run_init, g->Q, g->storage, LN(g, g->all_active.n, nt), C, S,
+        (const int *)g->all_active.d, g->all_active.n);
+  } else {
+    std::vector<std::vector<int8_t>> old = g->status;
+    bool changed = false;
+    for (size_t ld = 0; ld < old.size(); ++ld) changed |= (old[ld] != newst[ld]);
+    if (!changed) return LSB_OK;
+    // coarsening, finest to coarsest: parents of deactivated blocks take the children's mean
+    for (int l = g->Lmax - 2; l >= 0; --l) {
+      WorkList wl;
+      for (const CaseHost &ch : g->cases) {
+        if (l >= ch.L - 1) continue;
+        const int ld = ch.ld0 + l;
+        for (int b = 0; b < g->lds[ld].nblock; ++b)
+          if (old[ld][b] == BLK_REFINED && newst[ld][b] != BLK_REFINED) wl.h.push_back(g->lds[ld].block_off + b);
+      }
+      if (wl.h.empty()) continue;
+      TRY(upload_list(g, wl));
+      Ctx C = make_ctx(g);
+      RUN(wl.n, nt, run_restrict, g->Q, g->storage, LN(g, wl.n, nt), C, S, (const int *)wl.d, wl.n, 1);
+      CU(cudaStreamSynchronize(g->stream));
+      cudaFree(wl.d);
+      g->allocs.erase(std::remove(g->allocs.begin(), g->allocs.end(), (void *)wl.d), g->allocs.end());
+    }
+    // refinement, coarsest to finest: new fine blocks from the coarse data
+    std::vector<std::vector<int8_t>> merged = newst;
+    for (size_t ld = 0; ld < merged.size(); ++ld)
+      for (size_t b = 0; b < merged[ld].size(); ++b)
+        if (old[ld][b] == BLK_LEAF || newst[ld][b] == BLK_LEAF) merged[ld][b] = BLK_LEAF;
+    TRY(upload_status(g, merged));
+    g->status = merged;
+    TRY(build_lists(g));
+    TRY(level_tags(g));
+    for (int l = 0; l < g->Lmax - 1; ++l) {
+      WorkList wl;
+      for (const CaseHost &ch : g->cases) {
+        if (l >= ch.L - 1) continue;
+        const LevelDev &Lc = g->lds[ch.ld0 + l];
+        const LevelDev &Lf = g->lds[ch.ld0 + l + 1];
+        for (int b = 0; b < Lf.nblock; ++b) {
+          int pb = parent_block(Lc, Lf, b);
+          if (newst[ch.ld0 + l][pb] == BLK_REFINED && old[ch.ld0 + l][pb] != BLK_REFINED)
+            wl.h.push_back(Lf.block_off + b);
+        }
+      }
+      if (wl.h.empty()) continue;
+      TRY(upload_list(g, wl));
+      Ctx C = make_ctx(g);
+      RUN(wl.n, nt, run_prolong, g->Q, g->storage, LN(g, wl.n, nt), C, S, (const int *)wl.d, wl.n);
+      CU(cudaStreamSynchronize(g->stream));
+      cudaFree(wl.d);
+      g->allocs.erase(std::remove(g->allocs.begin(), g->allocs.end(), (void *)wl.d), g->allocs.end());
+    }
+    g->status = newst;
+    TRY(upload_status(g, g->status));
+    TRY(build_lists(g));
+    TRY(level_tags(g));
+  }
+  CU(cudaMemsetAsync(g->d_bflag, 0, g->nblock_total, g->stream));
+  for (int l = 0; l < g->Lmax; ++l) TRY(classify(g, l, 1));
+  return LSB_OK;
+}
+
+}  // namespace

@@ -1,0 +1,203 @@
+// Device-side definitions shared by the lsb kernels: velocity sets (Sec. 2.1,
+// Fig. 1), level descriptors of the block-structured grid, storage of the
+// populations as deviations from the rest weights (FP32 or scaled FP16).
+#pragma once
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lsb {
+
+constexpr float CS2 = 1.0f / 3.0f;
+
+// ---------------------------------------------------------------- lattices
+// D2Q9 ordering of Fig. 1a: -x, +x, -y, +y, (-1,-1), (-1,1), (1,1), (1,-1), rest.
+// D3Q19: the axis and edge velocities of Fig. 1b in that order, rest last.
+template <int Q> struct Lat;
+
+template <> struct Lat<9> {
+  static constexpr int D = 2;
+  static constexpr int REST = 8;
+  __host__ __device__ static constexpr int cx(int i) {
+    return (i == 0 || i == 4 || i == 5) ? -1 : ((i == 1 || i == 6 || i == 7) ? 1 : 0);
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    return (i == 2 || i == 4 || i == 7) ? -1 : ((i == 3 || i == 5 || i == 6) ? 1 : 0);
+  }
+  __host__ __device__ static constexpr int cz(int) { return 0; }
+  __host__ __device__ static constexpr float w(int i) {
+    return i < 4 ? 1.0f / 9.0f : (i < 8 ? 1.0f / 36.0f : 4.0f / 9.0f);
+  }
+  __host__ __device__ static constexpr int opp(int i) {
+    return i == 8 ? 8 : (i < 4 ? (i ^ 1) : (i < 6 ? i + 2 : i - 2));
+  }
+};
+
+template <> struct Lat<19> {
+  static constexpr int D = 3;
+  static constexpr int REST = 18;
+  // axis: 0 -x, 1 +x, 2 -y, 3 +y, 4 -z, 5 +z
+  // edges: 6 (-1,-1,0) 7 (-1,1,0) 8 (1,-1,0) 9 (1,1,0)
+  //        10 (-1,0,-1) 11 (-1,0,1) 12 (1,0,-1) 13 (1,0,1)
+  //        14 (0,-1,-1) 15 (0,-1,1) 16 (0,1,-1) 17 (0,1,1)
+  __host__ __device__ static constexpr int cx(int i) {
+    return (i == 0 || (i >= 6 && i <= 7) || (i >= 10 && i <= 11)) ? -1
+         : ((i == 1 || (i >= 8 && i <= 9) || (i >= 12 && i <= 13)) ? 1 : 0);
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    return (i == 2 || i == 6 || i == 8 || i == 14 || i == 15) ? -1
+         : ((i == 3 || i == 7 || i == 9 || i == 16 || i == 17) ? 1 : 0);
+  }
+  __host__ __device__ static constexpr int cz(int i) {
+    return (i == 4 || i == 10 || i == 12 || i == 14 || i == 16) ? -1
+         : ((i == 5 || i == 11 || i == 13 || i == 15 || i == 17) ? 1 : 0);
+  }
+  __host__ __device__ static constexpr float w(int i) {
+    return i < 6 ? 1.0f / 18.0f : (i < 18 ? 1.0f / 36.0f : 1.0f / 3.0f);
+  }
+  __host__ __device__ static constexpr int opp(int i) {
+    return i == 18 ? 18
+         : (i < 6 ? (i ^ 1)
+         : (i < 10 ? 15 - i : (i < 14 ? 23 - i : 31 - i)));
+  }
+};
+
+// ---------------------------------------------------------------- grid descriptors
+enum : int8_t { BLK_INACTIVE = 0, BLK_LEAF = 1, BLK_REFINED = 2 };
+
+// per-cell tag bits
+enum : uint8_t {
+  TAG_GAS = 1,      // current phase (1 gas, 0 liquid)
+  TAG_IFACE = 2,    // finest level: has a cut incoming link
+  TAG_FLIP = 4,     // changed phase at the last classification
+  TAG_PREVGAS = 8,  // phase before the last classification
+  TAG_RLAYER = 16,  // covered cell a leaf streams from (fine-to-coarse target)
+  TAG_GHOST = 32,   // inactive cell a leaf streams from (coarse-to-fine target)
+  TAG_LEAF = 64     // cell of a leaf block inside the box
+};
+
+// per-block flag bits (finest level)
+enum : uint8_t { BF_IFACE = 1, BF_BAND = 2 };
+
+struct LevelDev {
+  int case_id, level, n_levels, finest;
+  int n[3];        // true cells per axis (n[2] = 1 in 2D)
+  int p[3];        // padded to whole blocks
+  int nb[3];       // blocks per axis
+  int per[3];      // periodic axis flags
+  long long ncell; // p0*p1*p2
+  long long cell_off;  // offset in per-cell arrays of all levels (f uses *Q)
+  long long fine_off;  // offset in finest-level arrays, -1 if not finest
+  int block_off, nblock;
+  int parent_ld, child_ld;
+  int scale;       // finest cells per cell edge of this level: 2^(n_levels-1-level)
+  int fine_ld;     // level descriptor of this case's finest level
+  float omega[2], tau[2];
+  float acc[2][3];     // lattice acceleration per phase at this level
+  float wall_u[6][3];  // face velocities
+  // case physics needed on the finest level
+  float rho_phys[2], eta[2], sigma;
+  float dtau_ext, dtau_reinit;
+  float x_ref[3], grav[3];
+  int ls_active;
+};
+
+struct Ctx {
+  const LevelDev *lds;
+  const int *blk_ld;       // global block id -> level descriptor
+  int8_t *bstat;           // block status (per global block)
+  int8_t *bstat_old;       // previous status during regrid
+  uint8_t *bflag;          // finest-level block flags
+  uint8_t *tag;            // per cell, all levels
+  void *buf[2];            // two population buffers; level l reads buf[par[l]] (state A)
+  int par[4];              // and writes buf[1 - par[l]] (state B); SoA by q at cell_off*Q
+  // finest-level arrays (indexed fine_off + cell)
+  float *phi, *p1, *p2, *s0;
+  uint8_t *frozen;
+  float *ut0, *ut1, *ut2;  // extension velocity (D planes of nfine each)
+  uint32_t *cmask;
+  int *cbase;
+  float *macro;            // MF planes of nfine: drho, u[D], S (sym, D(D+1)/2)
+  float *nvec, *kappa;     // geometry at interface cells (D planes + 1)
+  float *linkbuf;          // 2 floats per cut link
+  long long nfine;         // finest-level cells over all cases
+  long long link_cap;
+  int *counters;           // per global level: [0] links, [1] iface cells, [2] flipped, [3] band blocks
+  int2 *iface_list, *flip_list;   // (ld, cell)
+  int *band_list;          // global block ids
+  long long list_cap;      // capacity of iface/flip lists per global level
+  int band_cap;
+  int *err;                // latched error bits
+  float fp16_scale, fp16_inv;
+};
+
+enum : int { ERR_LINK_OVF = 1, ERR_LIST_OVF = 2, ERR_NONFINITE = 4, ERR_BAND_OVF = 8 };
+constexpr int NCOUNT = 4;
+
+// ---------------------------------------------------------------- storage
+template <typename T> struct Store;
+template <> struct Store<float> {
+  __device__ static __forceinline__ float ld(const float *p, float) { return __ldg(p); }
+  __device__ static __forceinline__ void st(float *p, float v, float) { *p = v; }
+};
+template <> struct Store<__half> {
+  __device__ static __forceinline__ float ld(const __half *p, float inv) {
+    return __half2float(__ldg(p)) * inv;
+  }
+  __device__ static __forceinline__ void st(__half *p, float v, float scale) {
+    *p = __float2half_rn(v * scale);
+  }
+};
+
+struct BlockShape {
+  int bs[3];
+};
+
+// Population state A (pre-collision, time t) and B (destination of the push) of a level.
+template <typename T, int Q>
+__device__ __forceinline__ T *fA(const Ctx &C, const LevelDev &L) {
+  return reinterpret_cast<T *>(C.buf[C.par[L.level]]) + L.cell_off * Q;
+}
+template <typename T, int Q>
+__device__ __forceinline__ T *fB(const Ctx &C, const LevelDev &L) {
+  return reinterpret_cast<T *>(C.buf[1 - C.par[L.level]]) + L.cell_off * Q;
+}
+
+// ---------------------------------------------------------------- indexing helpers
+__device__ __forceinline__ void block_cell(const LevelDev &L, int lb, int t, const int bs[3], int &x,
+                                           int &y, int &z) {
+  int bx = lb % L.nb[0];
+  int by = (lb / L.nb[0]) % L.nb[1];
+  int bz = lb / (L.nb[0] * L.nb[1]);
+  int tx = t % bs[0];
+  int ty = (t / bs[0]) % bs[1];
+  int tz = t / (bs[0] * bs[1]);
+  x = bx * bs[0] + tx;
+  y = by * bs[1] + ty;
+  z = bz * bs[2] + tz;
+}
+
+__device__ __forceinline__ long long cidx(const LevelDev &L, int x, int y, int z) {
+  return (long long)x + (long long)L.p[0] * ((long long)y + (long long)L.p[1] * z);
+}
+
+__device__ __forceinline__ int block_of(const LevelDev &L, int x, int y, int z, const int bs[3]) {
+  return (x / bs[0]) + L.nb[0] * ((y / bs[1]) + L.nb[1] * (z / bs[2]));
+}
+
+// Wrap a coordinate on a periodic axis; returns false if it leaves through a wall.
+__device__ __forceinline__ bool wrap(const LevelDev &L, int a, int &v) {
+  int n = L.n[a];
+  if (v >= 0 && v < n) return true;
+  if (!L.per[a]) return false;
+  v = (v % n + n) % n;
+  return true;
+}
+
+// Clamp (walled axes) or wrap (periodic axes): zero-gradient ghost values.
+__device__ __forceinline__ int clampwrap(const LevelDev &L, int a, int v) {
+  int n = L.n[a];
+  if (L.per[a]) return (v % n + n) % n;
+  return v < 0 ? 0 : (v >= n ? n - 1 : v);
+}
+
+}  // namespace lsb

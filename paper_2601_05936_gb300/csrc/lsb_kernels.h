@@ -1,0 +1,41 @@
+// Host launchers of the lsb kernels.  Each is defined in the translation unit
+// that defines its kernel (lsb_lb.cu, lsb_ls.cu), so the launch and the kernel
+// registration live together; (Q, storage) pick the template instance.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "lsb_device.cuh"
+
+namespace lsb {
+
+struct Launch {
+  int grid, block;
+  cudaStream_t stream;
+};
+
+// lsb_lb.cu: lattice Boltzmann, interface bounce-back, level transfers
+cudaError_t run_init(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n);
+cudaError_t run_collide_stream(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n);
+cudaError_t run_interface_bc(int Q, int st, Launch L, Ctx C, int glevel);
+cudaError_t run_restrict(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, int all_cells);
+cudaError_t run_ghost(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, float theta);
+cudaError_t run_prolong(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n);
+cudaError_t run_level_tags(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n);
+cudaError_t run_observables(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, double *out,
+                            int stride);
+cudaError_t run_export(int Q, int st, Launch L, Ctx C, int ld, int field, float *dst);
+
+// lsb_ls.cu: level set, classification, geometry, refill, sensor
+cudaError_t run_classify_phase(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, int glevel, int init);
+cudaError_t run_classify_links(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, int glevel);
+cudaError_t run_band(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, int glevel);
+cudaError_t run_geometry(int D, Launch L, Ctx C, int glevel, int which);
+cudaError_t run_ext_init(int Q, Launch L, Ctx C, int glevel);
+cudaError_t run_ext_iter(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int commit);
+cudaError_t run_adv_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage);
+cudaError_t run_reinit_prep(int Q, Launch L, Ctx C, BlockShape S, int glevel);
+cudaError_t run_reinit_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage);
+cudaError_t run_refill(int Q, int st, Launch L, Ctx C, int glevel);
+cudaError_t run_sensor(Launch L, Ctx C, BlockShape S, const int *list, int n, int mode, float *out);
+
+}  // namespace lsb

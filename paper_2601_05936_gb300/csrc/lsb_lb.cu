@@ -1,0 +1,633 @@
+// Lattice Boltzmann kernels: fused BGK collide + push streaming with wall
+// bounce-back (Sec. 2.1, Eq. 1, feq, omega, forcing, bb at q = 1/2), the
+// interface bounce-back post-pass (Sec. 2.3, Eq. bb, bb_cc, Sdecomp), the
+// Dupuis-Chopard level transfers (Sec. 2.1 last paragraph), initialisation and
+// the float64 observables (Sec. 3.2).
+//
+// Populations are stored as deviations f~ = f - w (per-phase rest density 1),
+// structure of arrays per level: f[q * ncell + cell], x fastest, so a warp of a
+// block row touches consecutive words for every q.  The state between steps is
+// the PRE-collision (post-stream) population; a step reads it once, collides in
+// registers and pushes every population to its destination once: 2*Q*sizeof(T)
+// bytes of HBM traffic per cell update.
+#include "lsb_kernels.h"
+
+namespace lsb {
+
+// ------------------------------------------------------------------ helpers
+template <int Q>
+__device__ __forceinline__ void lb_moments(const float *f, float &drho, float u[3]) {
+  using LT = Lat<Q>;
+  float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    d += f[i];
+    jx += LT::cx(i) * f[i];
+    jy += LT::cy(i) * f[i];
+    if (LT::D == 3) jz += LT::cz(i) * f[i];
+  }
+  float inv = 1.0f / (1.0f + d);
+  drho = d;
+  u[0] = jx * inv;
+  u[1] = jy * inv;
+  u[2] = jz * inv;
+}
+
+template <int Q>
+__device__ __forceinline__ float feq_dev(int i, float drho, const float u[3], float usq) {
+  using LT = Lat<Q>;
+  float cu = LT::cx(i) * u[0] + LT::cy(i) * u[1] + LT::cz(i) * u[2];
+  return LT::w(i) * (drho + (1.0f + drho) * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
+}
+
+// BGK collision with forcing (Eq. 1), in place; optionally returns the strain rate.
+template <int Q, bool WANT_S>
+__device__ __forceinline__ void lb_collide(float *f, float om, const float acc[3], float &drho,
+                                           float u[3], float Sout[6]) {
+  using LT = Lat<Q>;
+  lb_moments<Q>(f, drho, u);
+  float rho = 1.0f + drho;
+  float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  float pxx = 0, pxy = 0, pxz = 0, pyy = 0, pyz = 0, pzz = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
+    float fe = feq_dev<Q>(i, drho, u, usq);
+    if (WANT_S) {
+      float fn = f[i] - fe;
+      pxx += cx * cx * fn;
+      pxy += cx * cy * fn;
+      pyy += cy * cy * fn;
+      if (LT::D == 3) {
+        pxz += cx * cz * fn;
+        pyz += cy * cz * fn;
+        pzz += cz * cz * fn;
+      }
+    }
+    float F = 3.0f * LT::w(i) * rho * (cx * acc[0] + cy * acc[1] + cz * acc[2]);
+    f[i] = f[i] + om * (fe - f[i]) + F;
+  }
+  if (WANT_S) {
+    float s = -1.5f * om / rho;  // -omega / (2 rho c_s^2)
+    Sout[0] = s * pxx; Sout[1] = s * pxy; Sout[2] = s * pxz;
+    Sout[3] = s * pyy; Sout[4] = s * pyz; Sout[5] = s * pzz;
+  }
+}
+
+// ------------------------------------------------------------------ init
+// Rest equilibrium with the hydrostatic density rho_hat = 1 - g.(x - x_ref)/c_s^2.
+template <int Q, typename T>
+__global__ void k_init(Ctx C, BlockShape S, const int *list, int nlist) {
+  using LT = Lat<Q>;
+  for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
+    int gb = list[w];
+    const LevelDev &L = C.lds[C.blk_ld[gb]];
+    int x, y, z;
+    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
+    long long c = cidx(L, x, y, z);
+    float xc[3] = {(x + 0.5f) * L.scale, (y + 0.5f) * L.scale, (z + 0.5f) * L.scale};
+    float drho = 0.f;
+    for (int a = 0; a < LT::D; ++a) drho -= L.grav[a] * (xc[a] - L.x_ref[a]) / CS2;
+    T *A = fA<T, Q>(C, L);
+    float u0[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Store<T>::st(A + i * L.ncell + c, feq_dev<Q>(i, drho, u0, 0.f), C.fp16_scale);
+  }
+}
+
+// ------------------------------------------------------------------ collide + stream
+// One CTA per block of the work list, one thread per cell.  Leaf cells and
+// the covered cells a leaf streams from (TAG_RLAYER) collide and push.  On the
+// finest level, band blocks also write the pre-collision moments and strain
+// rate (input of the interface condition and the level-set velocity), and a
+// push across the interface is parked in the link buffer for the post-pass.
+template <int Q, typename T>
+__global__ void __launch_bounds__(512) k_collide_stream(Ctx C, BlockShape S, const int *__restrict__ list,
+                                                        int nlist) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
+    const int gb = list[w];
+    const LevelDev &L = C.lds[C.blk_ld[gb]];
+    int x, y, z;
+    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
+    const long long c = cidx(L, x, y, z);
+    const uint8_t tg = C.tag[L.cell_off + c];
+    if (!(tg & (TAG_LEAF | TAG_RLAYER))) continue;
+    const long long N = L.ncell;
+    const T *A = fA<T, Q>(C, L);
+    T *B = fB<T, Q>(C, L);
+    float f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = Store<T>::ld(A + i * N + c, C.fp16_inv);
+    const int ph = tg & TAG_GAS;
+    const float acc[3] = {L.acc[ph][0], L.acc[ph][1], L.acc[ph][2]};
+    float drho, u[3], Sm[6];
+    const bool fine = L.finest != 0;
+    const bool want_macro = fine && (C.bflag[gb] & BF_BAND);
+    if (want_macro) {
+      lb_collide<Q, true>(f, L.omega[ph], acc, drho, u, Sm);
+      const long long fc = L.fine_off + c;
+      const long long NF = C.nfine;
+      float *M = C.macro;
+      M[fc] = drho;
+      for (int a = 0; a < D; ++a) M[(1 + a) * NF + fc] = u[a];
+      if (D == 2) {
+        M[3 * NF + fc] = Sm[0]; M[4 * NF + fc] = Sm[1]; M[5 * NF + fc] = Sm[3];
+      } else {
+        M[4 * NF + fc] = Sm[0]; M[5 * NF + fc] = Sm[1]; M[6 * NF + fc] = Sm[2];
+        M[7 * NF + fc] = Sm[3]; M[8 * NF + fc] = Sm[4]; M[9 * NF + fc] = Sm[5];
+      }
+    } else {
+      lb_collide<Q, false>(f, L.omega[ph], acc, drho, u, Sm);
+    }
+    uint32_t cm = 0;
+    int cb = 0;
+    if (fine && (tg & TAG_IFACE)) {
+      cm = C.cmask[L.fine_off + c];
+      cb = C.cbase[L.fine_off + c];
+    }
+    Store<T>::st(B + LT::REST * N + c, f[LT::REST], C.fp16_scale);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (i == LT::REST) continue;
+      const int k = LT::opp(i);
+      if (cm & (1u << k)) {  // x + c_i lies across the interface: park for the post-pass
+        long long li = cb + __popc(cm & ((1u << k) - 1u));
+        if (li < C.link_cap) {
+          C.linkbuf[2 * li] = f[i];
+          C.linkbuf[2 * li + 1] = f[k];
+        }
+        continue;
+      }
+      int tx = x + LT::cx(i), ty = y + LT::cy(i), tz = z + LT::cz(i);
+      bool in = wrap(L, 0, tx) && wrap(L, 1, ty);
+      int face = -1;
+      if (!(0 <= x + LT::cx(i) && x + LT::cx(i) < L.n[0]) && !L.per[0]) face = LT::cx(i) < 0 ? 0 : 1;
+      else if (!(0 <= y + LT::cy(i) && y + LT::cy(i) < L.n[1]) && !L.per[1]) face = LT::cy(i) < 0 ? 2 : 3;
+      if (D == 3) {
+        bool inz = wrap(L, 2, tz);
+        if (face < 0 && !inz) face = LT::cz(i) < 0 ? 4 : 5;
+        in = in && inz;
+      }
+      if (in) {
+        Store<T>::st(B + i * N + cidx(L, tx, ty, tz), f[i], C.fp16_scale);
+      } else {
+        // half-way bounce-back with the moving-wall term, i pointing at the wall
+        const float *uw = L.wall_u[face];
+        float du = LT::cx(i) * uw[0] + LT::cy(i) * uw[1] + LT::cz(i) * uw[2];
+        Store<T>::st(B + k * N + c, f[i] - 6.0f * LT::w(i) * du, C.fp16_scale);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ interface post-pass
+// For every cut link (x, k) of an interface cell: Eq. bb with the momentum term of
+// Eq. bb_cc; i = opp(k) points from x (phase A) to x + c_i (phase B).
+template <int Q, typename T>
+__global__ void k_interface_bc(Ctx C, int glevel) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  const int n = min(C.counters[glevel * NCOUNT + 1], (int)C.list_cap);
+  const int2 *lst = C.iface_list + (long long)glevel * C.list_cap;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 it = lst[e];
+    const LevelDev &L = C.lds[it.x];
+    const long long c = it.y;
+    const int x = (int)(c % L.p[0]);
+    const int y = (int)((c / L.p[0]) % L.p[1]);
+    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    const long long fo = L.fine_off;
+    const long long NF = C.nfine;
+    const uint32_t cm = C.cmask[fo + c];
+    const int cb = C.cbase[fo + c];
+    const uint8_t tg = C.tag[L.cell_off + c];
+    const int A = tg & TAG_GAS;
+    const int Bp = 1 - A;
+    const long long N = L.ncell;
+    T *Bf = fB<T, Q>(C, L);
+    const float *M = C.macro;
+    const float phx = C.phi[fo + c];
+    const float rA = M[fo + c];
+    float uA[3] = {0.f, 0.f, 0.f}, SA[6] = {0, 0, 0, 0, 0, 0}, nx[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < D; ++a) {
+      uA[a] = M[(1 + a) * NF + fo + c];
+      nx[a] = C.nvec[a * NF + fo + c];
+    }
+    const int MS = 1 + D;
+    for (int s = 0; s < D * (D + 1) / 2; ++s) SA[s] = M[(MS + s) * NF + fo + c];
+    const float kx = C.kappa[fo + c];
+    const float etaA = L.eta[A], etaB = L.eta[Bp];
+    const float eta_bar = 0.5f * (etaA + etaB);
+    const float jeta = etaB - etaA;
+    const float sgn = (A == 0) ? 1.0f : -1.0f;
+    for (int k = 0; k < Q; ++k) {
+      if (!(cm & (1u << k))) continue;
+      const int i = LT::opp(k);
+      const long long li = cb + __popc(cm & ((1u << k) - 1u));
+      if (li >= C.link_cap) continue;
+      const float fi = C.linkbuf[2 * li], fk = C.linkbuf[2 * li + 1];
+      int yx = x + LT::cx(i), yy = y + LT::cy(i), yz = z + LT::cz(i);
+      wrap(L, 0, yx); wrap(L, 1, yy); if (D == 3) wrap(L, 2, yz);
+      const long long cy_ = cidx(L, yx, yy, yz);
+      const float phy = C.phi[fo + cy_];
+      const float q = phx / (phx - phy);
+      // u_I, n, kappa along the link; Sbar, [p], eta from the two nodes
+      float uI[3], nv[3], Sb[6];
+      float nn = 0.f;
+      for (int a = 0; a < 3; ++a) { uI[a] = 0.f; nv[a] = 0.f; }
+      for (int a = 0; a < D; ++a) {
+        uI[a] = (1.0f - q) * uA[a] + q * M[(1 + a) * NF + fo + cy_];
+        nv[a] = (1.0f - q) * nx[a] + q * C.nvec[a * NF + fo + cy_];
+        nn += nv[a] * nv[a];
+      }
+      nn = sqrtf(nn);
+      for (int a = 0; a < D; ++a) nv[a] = nn > 0.f ? sgn * nv[a] / nn : 0.f;
+      const float kap = sgn * ((1.0f - q) * kx + q * C.kappa[fo + cy_]);
+      for (int s = 0; s < D * (D + 1) / 2; ++s) Sb[s] = 0.5f * (SA[s] + M[(MS + s) * NF + fo + cy_]);
+      const float rB = M[fo + cy_];
+      const float jp = CS2 * (L.rho_phys[Bp] * rB - L.rho_phys[A] * rA);
+      // symmetric tensor access
+      auto Sget = [&](int a, int b) -> float {
+        if (D == 2) return (a == 0 && b == 0) ? Sb[0] : ((a == 1 && b == 1) ? Sb[2] : Sb[1]);
+        int lo = a < b ? a : b, hi = a < b ? b : a;
+        if (lo == 0) return Sb[hi];            // xx, xy, xz
+        if (lo == 1) return Sb[2 + hi];        // yy, yz
+        return Sb[5];                          // zz
+      };
+      float v[3] = {0.f, 0.f, 0.f};
+      float Snn = 0.f;
+      for (int a = 0; a < D; ++a) {
+        for (int b = 0; b < D; ++b) v[a] += Sget(a, b) * nv[b];
+        Snn += nv[a] * v[a];
+      }
+      float vt[3], cn = 0.f, cvt = 0.f, cuI = 0.f;
+      const float ci[3] = {(float)LT::cx(i), (float)LT::cy(i), (float)LT::cz(i)};
+      for (int a = 0; a < D; ++a) {
+        vt[a] = v[a] - Snn * nv[a];
+        cn += ci[a] * nv[a];
+        cvt += ci[a] * vt[a];
+        cuI += ci[a] * uI[a];
+      }
+      const float alpha = (jp + L.sigma * kap) / (2.0f * eta_bar) - (jeta / eta_bar) * Snn;
+      const float ccS = alpha * cn * cn - 2.0f * (jeta / eta_bar) * cn * cvt;
+      const float df = -6.0f * LT::w(i) * (cuI - q * (1.0f - q) * ccS);
+      // Bouzidi branches (linear); the q < 1/2 branch needs x - c_i in phase A
+      float val;
+      if (q >= 0.5f) {
+        val = fi / (2.0f * q) + (2.0f * q - 1.0f) / (2.0f * q) * fk + df / (2.0f * q);
+      } else {
+        int bx = x - LT::cx(i), by = y - LT::cy(i), bz = z - LT::cz(i);
+        bool ok = wrap(L, 0, bx) && wrap(L, 1, by) && (D == 2 || wrap(L, 2, bz));
+        if (ok) {
+          const long long cbk = cidx(L, bx, by, bz);
+          const uint8_t tb = C.tag[L.cell_off + cbk];
+          ok = (tb & TAG_LEAF) && ((tb & TAG_GAS) == A);
+          if (ok) {
+            const float fb = Store<T>::ld(Bf + i * N + c, C.fp16_inv);
+            val = 2.0f * q * fi + (1.0f - 2.0f * q) * fb + df;
+          }
+        }
+        if (!ok) val = fi + df;
+      }
+      Store<T>::st(Bf + k * N + c, val, C.fp16_scale);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ level transfers
+// f~ -> f~eq(rho, u) + fac * (f~ - f~eq)
+template <int Q>
+__device__ __forceinline__ void rescale_neq(float *f, float fac) {
+  float drho, u[3];
+  lb_moments<Q>(f, drho, u);
+  float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    float fe = feq_dev<Q>(i, drho, u, usq);
+    f[i] = fe + fac * (f[i] - fe);
+  }
+}
+
+// Covered coarse cells (TAG_RLAYER): mean of the 2^D children's pre-collision
+// populations, f^neq scaled by 2 tau_c / tau_f.  mode 1 (regrid coarsening):
+// every cell of the listed blocks.
+template <int Q, typename T>
+__global__ void k_restrict(Ctx C, BlockShape S, const int *list, int nlist, int all_cells) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
+    int gb = list[w];
+    const LevelDev &L = C.lds[C.blk_ld[gb]];
+    int x, y, z;
+    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
+    long long c = cidx(L, x, y, z);
+    uint8_t tg = C.tag[L.cell_off + c];
+    if (!all_cells && !(tg & TAG_RLAYER)) continue;
+    const LevelDev &F = C.lds[L.child_ld];
+    const T *Af = fA<T, Q>(C, F);
+    float f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = 0.f;
+    const int nz = (D == 3) ? 2 : 1;
+    for (int sz = 0; sz < nz; ++sz)
+      for (int sy = 0; sy < 2; ++sy)
+        for (int sx = 0; sx < 2; ++sx) {
+          long long cf = cidx(F, 2 * x + sx, 2 * y + sy, D == 3 ? 2 * z + sz : 0);
+#pragma unroll
+          for (int i = 0; i < Q; ++i) f[i] += Store<T>::ld(Af + i * F.ncell + cf, C.fp16_inv);
+        }
+    const float inv = 1.0f / (float)(4 * nz);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] *= inv;
+    int ph = tg & TAG_GAS;
+    rescale_neq<Q>(f, 2.0f * L.tau[ph] / F.tau[ph]);
+    T *Ac = fA<T, Q>(C, L);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Store<T>::st(Ac + i * L.ncell + c, f[i], C.fp16_scale);
+  }
+}
+
+// Linear interpolation of coarse populations at the centre of fine cell (x,y,z):
+// central gradients where both coarse neighbours are leaves (TAG_LEAF), one-sided
+// where only one is, none otherwise; theta blends the coarse state at t (A) and
+// t+1 (B) for the second fine substep.
+template <int Q, typename T>
+__device__ __forceinline__ void interp_coarse(const Ctx &C, const LevelDev &Lc, int x, int y, int z,
+                                              float theta, float *out) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  const T *Ac = fA<T, Q>(C, Lc);
+  const T *Bc = fB<T, Q>(C, Lc);
+  const int P[3] = {x >> 1, y >> 1, D == 3 ? (z >> 1) : 0};
+  auto load = [&](long long cc, float *dst) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      float a = Store<T>::ld(Ac + i * Lc.ncell + cc, C.fp16_inv);
+      if (theta != 0.f) a = (1.0f - theta) * a + theta * Store<T>::ld(Bc + i * Lc.ncell + cc, C.fp16_inv);
+      dst[i] = a;
+    }
+  };
+  const long long cp = cidx(Lc, P[0], P[1], P[2]);
+  float fp[Q];
+  load(cp, fp);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) out[i] = fp[i];
+  const int fcrd[3] = {x, y, z};
+  for (int a = 0; a < D; ++a) {
+    const float delta = ((fcrd[a] & 1) - 0.5f) * 0.5f;
+    int up[3] = {P[0], P[1], P[2]}, dn[3] = {P[0], P[1], P[2]};
+    up[a] += 1;
+    dn[a] -= 1;
+    bool upok = wrap(Lc, a, up[a]);
+    bool dnok = wrap(Lc, a, dn[a]);
+    long long cu = 0, cd = 0;
+    if (upok) {
+      cu = cidx(Lc, up[0], up[1], up[2]);
+      upok = (C.tag[Lc.cell_off + cu] & TAG_LEAF) != 0;
+    }
+    if (dnok) {
+      cd = cidx(Lc, dn[0], dn[1], dn[2]);
+      dnok = (C.tag[Lc.cell_off + cd] & TAG_LEAF) != 0;
+    }
+    if (!upok && !dnok) continue;
+    float fu[Q], fd[Q];
+    if (upok) load(cu, fu);
+    if (dnok) load(cd, fd);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      float g = (upok && dnok) ? 0.5f * (fu[i] - fd[i]) : (upok ? fu[i] - fp[i] : fp[i] - fd[i]);
+      out[i] += delta * g;
+    }
+  }
+}
+
+// Ghost ring of level F (TAG_GHOST cells): coarse interpolation at time weight
+// theta, f^neq scaled by tau_f / (2 tau_c), fine-level collision, pushed into
+// the fine leaves that stream from it.
+template <int Q, typename T>
+__global__ void k_ghost(Ctx C, BlockShape S, const int *list, int nlist, float theta) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
+    const int gb = list[w];
+    const LevelDev &F = C.lds[C.blk_ld[gb]];
+    int x, y, z;
+    block_cell(F, gb - F.block_off, threadIdx.x, S.bs, x, y, z);
+    if (x >= F.n[0] || y >= F.n[1] || z >= F.n[2]) continue;
+    const long long c = cidx(F, x, y, z);
+    if (!(C.tag[F.cell_off + c] & TAG_GHOST)) continue;
+    const LevelDev &Lc = C.lds[F.parent_ld];
+    float f[Q];
+    interp_coarse<Q, T>(C, Lc, x, y, z, theta, f);
+    const long long cpar = cidx(Lc, x >> 1, y >> 1, D == 3 ? (z >> 1) : 0);
+    const int ph = C.tag[Lc.cell_off + cpar] & TAG_GAS;
+    rescale_neq<Q>(f, F.tau[ph] / (2.0f * Lc.tau[ph]));
+    float drho, u[3], Sm[6];
+    const float acc[3] = {F.acc[ph][0], F.acc[ph][1], F.acc[ph][2]};
+    lb_collide<Q, false>(f, F.omega[ph], acc, drho, u, Sm);
+    T *Bf = fB<T, Q>(C, F);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (i == LT::REST) continue;
+      int tx = x + LT::cx(i), ty = y + LT::cy(i), tz = z + LT::cz(i);
+      if (!(wrap(F, 0, tx) && wrap(F, 1, ty) && (D == 2 || wrap(F, 2, tz)))) continue;
+      const long long ct = cidx(F, tx, ty, tz);
+      if (C.tag[F.cell_off + ct] & TAG_LEAF) Store<T>::st(Bf + i * F.ncell + ct, f[i], C.fp16_scale);
+    }
+  }
+}
+
+// Regrid: fill every cell of the listed (newly active) fine blocks from the
+// coarse level (interpolation + f^neq scaling, no collision).  The coarse
+// TAG_LEAF must mark the cells that hold valid data (old or new leaves).
+template <int Q, typename T>
+__global__ void k_prolong(Ctx C, BlockShape S, const int *list, int nlist) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
+    const int gb = list[w];
+    const LevelDev &F = C.lds[C.blk_ld[gb]];
+    int x, y, z;
+    block_cell(F, gb - F.block_off, threadIdx.x, S.bs, x, y, z);
+    if (x >= F.n[0] || y >= F.n[1] || z >= F.n[2]) continue;
+    const long long c = cidx(F, x, y, z);
+    const LevelDev &Lc = C.lds[F.parent_ld];
+    float f[Q];
+    interp_coarse<Q, T>(C, Lc, x, y, z, 0.f, f);
+    const long long cpar = cidx(Lc, x >> 1, y >> 1, D == 3 ? (z >> 1) : 0);
+    const int ph = C.tag[Lc.cell_off + cpar] & TAG_GAS;
+    rescale_neq<Q>(f, F.tau[ph] / (2.0f * Lc.tau[ph]));
+    T *Af = fA<T, Q>(C, F);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Store<T>::st(Af + i * F.ncell + c, f[i], C.fp16_scale);
+  }
+}
+
+// ------------------------------------------------------------------ tags from block status
+// Per cell: phase from phi at the finest cell under the cell's lowest corner,
+// TAG_LEAF / TAG_RLAYER / TAG_GHOST from the block statuses of the cell and of
+// its lattice neighbours.  Finest-level interface bits are rebuilt by the
+// classification that follows every regrid.
+template <int Q>
+__global__ void k_level_tags(Ctx C, BlockShape S, const int *list, int nlist) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
+    const int gb = list[w];
+    const LevelDev &L = C.lds[C.blk_ld[gb]];
+    int x, y, z;
+    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
+    const long long c = cidx(L, x, y, z);
+    const LevelDev &Fn = C.lds[L.fine_ld];
+    const long long cf = cidx(Fn, x * L.scale, y * L.scale, z * L.scale);
+    uint8_t tg = (C.phi[Fn.fine_off + cf] >= 0.0f) ? TAG_GAS : 0;
+    const int8_t st = C.bstat[gb];
+    bool near_leaf = false;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (i == LT::REST) continue;
+      int tx = x + LT::cx(i), ty = y + LT::cy(i), tz = z + LT::cz(i);
+      if (!(wrap(L, 0, tx) && wrap(L, 1, ty) && (D == 2 || wrap(L, 2, tz)))) continue;
+      if (C.bstat[L.block_off + block_of(L, tx, ty, tz, S.bs)] == BLK_LEAF) near_leaf = true;
+    }
+    if (st == BLK_LEAF) tg |= TAG_LEAF;
+    if (st == BLK_REFINED && near_leaf) tg |= TAG_RLAYER;
+    if (st == BLK_INACTIVE && near_leaf) tg |= TAG_GHOST;
+    if (tg & TAG_GAS) tg |= TAG_PREVGAS;
+    C.tag[L.cell_off + c] = tg;
+  }
+}
+
+// ------------------------------------------------------------------ observables
+// Per case, float64: mass of each phase, gas volume, leaf count, centroid and
+// velocity of the gas (sharp Heaviside, Sec. 3.2), lengths in finest cells.
+template <int Q, typename T>
+__global__ void k_observables(Ctx C, BlockShape S, const int *list, int nlist, double *out, int stride) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
+    const int gb = list[w];
+    const LevelDev &L = C.lds[C.blk_ld[gb]];
+    int x, y, z;
+    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    double v[4 + 2 * 3];
+    for (int k = 0; k < 4 + 2 * D; ++k) v[k] = 0.0;
+    if (x < L.n[0] && y < L.n[1] && z < L.n[2]) {
+      const long long c = cidx(L, x, y, z);
+      const uint8_t tg = C.tag[L.cell_off + c];
+      if (tg & TAG_LEAF) {
+        const T *A = fA<T, Q>(C, L);
+        float f[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i] = Store<T>::ld(A + i * L.ncell + c, C.fp16_inv);
+        float drho, u[3];
+        lb_moments<Q>(f, drho, u);
+        double vol = 1.0;
+        for (int a = 0; a < D; ++a) vol *= (double)L.scale;
+        const int gas = tg & TAG_GAS;
+        v[gas] = vol * (1.0 + (double)drho);
+        v[3] = 1.0;
+        bool finite = isfinite(drho) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
+        if (!finite) atomicOr(C.err, ERR_NONFINITE);
+        if (gas) {
+          v[2] = vol;
+          const int crd[3] = {x, y, z};
+          for (int a = 0; a < D; ++a) {
+            v[4 + a] = vol * ((double)crd[a] + 0.5) * (double)L.scale;
+            v[4 + D + a] = vol * (double)u[a];
+          }
+        }
+      }
+    }
+    // block reduction in float64 (warp shuffles, then one atomic per warp)
+    for (int k = 0; k < 4 + 2 * D; ++k) {
+      double s = v[k];
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+      if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(out + (long long)L.case_id * stride + k, s);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ field export
+// Dense copy of one level: populations (full f = f~ + w), rho_hat, u.
+template <int Q, typename T>
+__global__ void k_export(Ctx C, int ld, int field, float *dst) {
+  using LT = Lat<Q>;
+  const LevelDev &L = C.lds[ld];
+  const long long ntrue = (long long)L.n[0] * L.n[1] * L.n[2];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ntrue;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(e % L.n[0]);
+    const int y = (int)((e / L.n[0]) % L.n[1]);
+    const int z = (int)(e / ((long long)L.n[0] * L.n[1]));
+    const long long c = cidx(L, x, y, z);
+    const T *A = fA<T, Q>(C, L);
+    float f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = Store<T>::ld(A + i * L.ncell + c, C.fp16_inv);
+    if (field == 4) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) dst[i * ntrue + e] = f[i] + LT::w(i);
+    } else {
+      float drho, u[3];
+      lb_moments<Q>(f, drho, u);
+      if (field == 0) dst[e] = 1.0f + drho;
+      else
+        for (int a = 0; a < LT::D; ++a) dst[a * ntrue + e] = u[a];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host launchers
+#define LSB_QT(Q, st, CALL)                                      \
+  do {                                                           \
+    if (Q == 9) {                                                \
+      if (st == 0) { constexpr int Q_ = 9; using T_ = float; CALL; } \
+      else { constexpr int Q_ = 9; using T_ = __half; CALL; }    \
+    } else {                                                     \
+      if (st == 0) { constexpr int Q_ = 19; using T_ = float; CALL; } \
+      else { constexpr int Q_ = 19; using T_ = __half; CALL; }   \
+    }                                                            \
+    return cudaGetLastError();                                   \
+  } while (0)
+
+#define LK(kern) kern<Q_, T_><<<L.grid, L.block, 0, L.stream>>>
+
+cudaError_t run_init(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n) {
+  LSB_QT(Q, st, (LK(k_init)(C, S, list, n)));
+}
+cudaError_t run_collide_stream(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n) {
+  LSB_QT(Q, st, (LK(k_collide_stream)(C, S, list, n)));
+}
+cudaError_t run_interface_bc(int Q, int st, Launch L, Ctx C, int glevel) {
+  LSB_QT(Q, st, (LK(k_interface_bc)(C, glevel)));
+}
+cudaError_t run_restrict(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, int all_cells) {
+  LSB_QT(Q, st, (LK(k_restrict)(C, S, list, n, all_cells)));
+}
+cudaError_t run_ghost(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, float theta) {
+  LSB_QT(Q, st, (LK(k_ghost)(C, S, list, n, theta)));
+}
+cudaError_t run_prolong(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n) {
+  LSB_QT(Q, st, (LK(k_prolong)(C, S, list, n)));
+}
+cudaError_t run_observables(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, double *out,
+                            int stride) {
+  LSB_QT(Q, st, (LK(k_observables)(C, S, list, n, out, stride)));
+}
+cudaError_t run_export(int Q, int st, Launch L, Ctx C, int ld, int field, float *dst) {
+  LSB_QT(Q, st, (LK(k_export)(C, ld, field, dst)));
+}
+cudaError_t run_level_tags(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n) {
+  if (Q == 9) k_level_tags<9><<<L.grid, L.block, 0, L.stream>>>(C, S, list, n);
+  else k_level_tags<19><<<L.grid, L.block, 0, L.stream>>>(C, S, list, n);
+  return cudaGetLastError();
+}
+
+}  // namespace lsb

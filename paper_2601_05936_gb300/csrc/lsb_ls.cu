@@ -1,0 +1,636 @@
+// Level-set kernels on the finest level (Sec. 2.2): phase classification and
+// cut links (Sec. 2.3 radiation theorem), the narrow band, float64
+// least-squares geometry, hyperbolic velocity extension (Eq.
+// hyperbolicExtension), upwind-5 / TVD-RK3 transport, constrained
+// reinitialisation (HJ-WENO5 Godunov, interface cells frozen), refill of cells
+// that change phase (Sec. 2.4) and the refinement sensor (Sec. 2.6, 3.2.2).
+//
+// The narrow band is block granular: finest-level blocks holding an interface
+// cell and their 3^D neighbours (active blocks only).  phi, the RK stage
+// arrays and the extension velocity are dense finest-level arrays; stencil
+// points outside the band read the committed fields.
+#include "lsb_kernels.h"
+
+namespace lsb {
+
+__device__ __forceinline__ bool in_band(const Ctx &C, const LevelDev &L, const BlockShape &S, int x, int y, int z) {
+  return (C.bflag[L.block_off + block_of(L, x, y, z, S.bs)] & BF_BAND) != 0;
+}
+
+// ------------------------------------------------------------------ classification
+// Pass 1: phase of every leaf cell from phi (liquid iff phi < 0); flipped cells
+// are listed.  init = 1 (after creation or regrid): no flips, previous = current.
+template <int Q>
+__global__ void k_classify_phase(Ctx C, BlockShape S, const int *list, int nlist, int glevel, int init) {
+  for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
+    const int gb = list[w];
+    const LevelDev &L = C.lds[C.blk_ld[gb]];
+    if (threadIdx.x == 0) C.bflag[gb] = 0;
+    int x, y, z;
+    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
+    const long long c = cidx(L, x, y, z);
+    const uint8_t tg = C.tag[L.cell_off + c];
+    if (!(tg & TAG_LEAF)) continue;
+    const int gas = C.phi[L.fine_off + c] >= 0.0f ? 1 : 0;
+    const int prev = init ? gas : (tg & TAG_GAS);
+    const bool flip = !init && (gas != prev);
+    uint8_t nt = (tg & (TAG_LEAF | TAG_RLAYER | TAG_GHOST)) | (gas ? TAG_GAS : 0) | (prev ? TAG_PREVGAS : 0) |
+                 (flip ? TAG_FLIP : 0);
+    C.tag[L.cell_off + c] = nt;
+    if (flip) {
+      int e = atomicAdd(&C.counters[glevel * NCOUNT + 2], 1);
+      if (e < C.list_cap) C.flip_list[(long long)glevel * C.list_cap + e] = make_int2(C.blk_ld[gb], (int)c);
+      else atomicOr(C.err, ERR_LIST_OVF);
+    }
+  }
+}
+
+// Pass 2: cut mask of every leaf cell (bit k: source x - c_k is a leaf of the
+// other phase), link base, interface list, block interface flag.
+template <int Q>
+__global__ void k_classify_links(Ctx C, BlockShape S, const int *list, int nlist, int glevel) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
+    const int gb = list[w];
+    const LevelDev &L = C.lds[C.blk_ld[gb]];
+    int x, y, z;
+    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    bool has = false;
+    if (x < L.n[0] && y < L.n[1] && z < L.n[2]) {
+      const long long c = cidx(L, x, y, z);
+      const uint8_t tg = C.tag[L.cell_off + c];
+      if (tg & TAG_LEAF) {
+        uint32_t m = 0;
+        for (int k = 0; k < Q; ++k) {
+          if (k == LT::REST) continue;
+          int sx = x - LT::cx(k), sy = y - LT::cy(k), sz = z - LT::cz(k);
+          if (!(wrap(L, 0, sx) && wrap(L, 1, sy) && (D == 2 || wrap(L, 2, sz)))) continue;
+          const uint8_t ts = C.tag[L.cell_off + cidx(L, sx, sy, sz)];
+          if ((ts & TAG_LEAF) && ((ts & TAG_GAS) != (tg & TAG_GAS))) m |= 1u << k;
+        }
+        C.cmask[L.fine_off + c] = m;
+        if (m) {
+          has = true;
+          int base = atomicAdd(&C.counters[glevel * NCOUNT + 0], __popc(m));
+          if ((long long)base + __popc(m) > C.link_cap) atomicOr(C.err, ERR_LINK_OVF);
+          C.cbase[L.fine_off + c] = base;
+          C.tag[L.cell_off + c] = tg | TAG_IFACE;
+          int e = atomicAdd(&C.counters[glevel * NCOUNT + 1], 1);
+          if (e < C.list_cap) C.iface_list[(long long)glevel * C.list_cap + e] = make_int2(C.blk_ld[gb], (int)c);
+          else atomicOr(C.err, ERR_LIST_OVF);
+        }
+      }
+    }
+    if (__syncthreads_or(has) && threadIdx.x == 0) C.bflag[gb] = BF_IFACE;
+  }
+}
+
+// Pass 3: band flag of every active finest block (itself or a 3^D neighbour
+// holds an interface cell); band blocks are listed.
+template <int Q>
+__global__ void k_band(Ctx C, BlockShape S, const int *list, int nlist, int glevel) {
+  constexpr int D = Lat<Q>::D;
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nlist; w += gridDim.x * blockDim.x) {
+    const int gb = list[w];
+    const LevelDev &L = C.lds[C.blk_ld[gb]];
+    const int lb = gb - L.block_off;
+    const int b[3] = {lb % L.nb[0], (lb / L.nb[0]) % L.nb[1], lb / (L.nb[0] * L.nb[1])};
+    bool band = false;
+    for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          int nb3[3] = {b[0] + dx, b[1] + dy, b[2] + dz};
+          const int d3[3] = {dx, dy, dz};
+          bool ok = true;
+          for (int a = 0; a < D; ++a) {
+            if (nb3[a] < 0 || nb3[a] >= L.nb[a]) {
+              if (L.per[a]) nb3[a] = (nb3[a] + L.nb[a]) % L.nb[a];
+              else ok = false;
+            }
+            (void)d3;
+          }
+          if (!ok) continue;
+          int nbid = L.block_off + nb3[0] + L.nb[0] * (nb3[1] + L.nb[1] * nb3[2]);
+          if (C.bflag[nbid] & BF_IFACE) band = true;
+        }
+    if (band && C.bstat[gb] == BLK_LEAF) {
+      C.bflag[gb] = C.bflag[gb] | BF_BAND;
+      int e = atomicAdd(&C.counters[glevel * NCOUNT + 3], 1);
+      if (e < C.band_cap) C.band_list[(long long)glevel * C.band_cap + e] = gb;
+      else atomicOr(C.err, ERR_BAND_OVF);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ geometry (float64)
+// Unweighted least-squares quadratic over the 3^D stencil.  With offsets in
+// {-1,0,1}^D the odd basis functions decouple: grad_a = sum(o_a phi)/sum(o_a^2),
+// H_ab = sum(o_a o_b phi)/sum(o_a^2 o_b^2) (a != b); the constant and pure
+// quadratic coefficients solve the 1 + D even normal equations in closed form.
+// n = g/|g|, kappa = (|g|^2 tr H - g.H.g)/|g|^3.
+template <int D>
+__global__ void k_geometry(Ctx C, int glevel, int which) {
+  const int n = min(C.counters[glevel * NCOUNT + (which ? 2 : 1)], (int)C.list_cap);
+  const int2 *lst = (which ? C.flip_list : C.iface_list) + (long long)glevel * C.list_cap;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 it = lst[e];
+    const LevelDev &L = C.lds[it.x];
+    const long long c = it.y;
+    const int x = (int)(c % L.p[0]);
+    const int y = (int)((c / L.p[0]) % L.p[1]);
+    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    double P = 0, sx[3] = {0, 0, 0}, sxx[3] = {0, 0, 0}, sxy[3] = {0, 0, 0};
+    for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz)
+      for (int oy = -1; oy <= 1; ++oy)
+        for (int ox = -1; ox <= 1; ++ox) {
+          const int xx = clampwrap(L, 0, x + ox), yy = clampwrap(L, 1, y + oy);
+          const int zz = D == 3 ? clampwrap(L, 2, z + oz) : 0;
+          const double v = (double)C.phi[L.fine_off + cidx(L, xx, yy, zz)];
+          const int o[3] = {ox, oy, oz};
+          P += v;
+          for (int a = 0; a < D; ++a) {
+            sx[a] += o[a] * v;
+            sxx[a] += o[a] * o[a] * v;
+          }
+          sxy[0] += ox * oy * v;
+          if (D == 3) {
+            sxy[1] += ox * oz * v;
+            sxy[2] += oy * oz * v;
+          }
+        }
+    double g[3] = {0, 0, 0}, H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    if (D == 2) {
+      // sums over 9 points: sum o^2 = 6, sum o_x^2 o_y^2 = 4, sum o^4 = 6
+      const double R = sxx[0] + sxx[1];
+      const double s = (3.0 * R - 4.0 * P) / 6.0;
+      const double a0 = (5.0 * P - 3.0 * R) / 9.0;
+      for (int a = 0; a < 2; ++a) {
+        g[a] = sx[a] / 6.0;
+        H[a][a] = 2.0 * (sxx[a] - 6.0 * a0 - 4.0 * s) / 2.0;
+      }
+      H[0][1] = H[1][0] = sxy[0] / 4.0;
+    } else {
+      // sums over 27 points: sum o^2 = 18, sum o_a^2 o_b^2 = 12, sum o^4 = 18
+      const double R = sxx[0] + sxx[1] + sxx[2];
+      const double s = (R - 2.0 * P) / 6.0;
+      const double a0 = (7.0 * P - 3.0 * R) / 27.0;
+      for (int a = 0; a < 3; ++a) {
+        g[a] = sx[a] / 18.0;
+        H[a][a] = 2.0 * (sxx[a] - 18.0 * a0 - 12.0 * s) / 6.0;
+      }
+      H[0][1] = H[1][0] = sxy[0] / 12.0;
+      H[0][2] = H[2][0] = sxy[1] / 12.0;
+      H[1][2] = H[2][1] = sxy[2] / 12.0;
+    }
+    double g2 = 0, tr = 0, gHg = 0;
+    for (int a = 0; a < D; ++a) {
+      g2 += g[a] * g[a];
+      tr += H[a][a];
+      for (int b = 0; b < D; ++b) gHg += g[a] * H[a][b] * g[b];
+    }
+    const double mag = sqrt(g2);
+    const long long fc = L.fine_off + c;
+    if (mag > 1e-12) {
+      for (int a = 0; a < D; ++a) C.nvec[a * C.nfine + fc] = (float)(g[a] / mag);
+      C.kappa[fc] = (float)((g2 * tr - gHg) / (mag * mag * mag));
+    } else {
+      for (int a = 0; a < D; ++a) C.nvec[a * C.nfine + fc] = 0.f;
+      C.kappa[fc] = 0.f;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ velocity extension
+// Interface cells: mean of u_I = (1-q) u(x) + q u(x + c_i) over their cut links.
+template <int Q>
+__global__ void k_ext_init(Ctx C, int glevel) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  const int n = min(C.counters[glevel * NCOUNT + 1], (int)C.list_cap);
+  const int2 *lst = C.iface_list + (long long)glevel * C.list_cap;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 it = lst[e];
+    const LevelDev &L = C.lds[it.x];
+    const long long c = it.y;
+    const int x = (int)(c % L.p[0]);
+    const int y = (int)((c / L.p[0]) % L.p[1]);
+    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    const long long fo = L.fine_off, NF = C.nfine;
+    const uint32_t m = C.cmask[fo + c];
+    const float phx = C.phi[fo + c];
+    float acc[3] = {0.f, 0.f, 0.f};
+    int cnt = 0;
+    for (int k = 0; k < Q; ++k) {
+      if (!(m & (1u << k))) continue;
+      const int i = LT::opp(k);
+      int yx = x + LT::cx(i), yy = y + LT::cy(i), yz = z + LT::cz(i);
+      wrap(L, 0, yx); wrap(L, 1, yy); if (D == 3) wrap(L, 2, yz);
+      const long long cy_ = cidx(L, yx, yy, yz);
+      const float q = phx / (phx - C.phi[fo + cy_]);
+      for (int a = 0; a < D; ++a)
+        acc[a] += (1.0f - q) * C.macro[(1 + a) * NF + fo + c] + q * C.macro[(1 + a) * NF + fo + cy_];
+      ++cnt;
+    }
+    for (int a = 0; a < D; ++a) C.ut0[a * NF + fo + c] = acc[a] / (float)cnt;
+  }
+}
+
+// One Jacobi sweep of first-order upwind extension on the band (interface cells
+// copy their value).  Neighbours outside the band read the committed field ut0.
+// commit = 1: copy uin into ut0 on the band instead.
+template <int D>
+__global__ void k_ext_iter(Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int commit) {
+  const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
+  const int *lst = C.band_list + (long long)glevel * C.band_cap;
+  for (int w = blockIdx.x; w < nl; w += gridDim.x) {
+    const int gb = lst[w];
+    const LevelDev &L = C.lds[C.blk_ld[gb]];
+    int x, y, z;
+    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
+    const long long fo = L.fine_off, NF = C.nfine;
+    const long long c = cidx(L, x, y, z);
+    if (commit) {
+      for (int a = 0; a < D; ++a) C.ut0[a * NF + fo + c] = uin[a * NF + fo + c];
+      continue;
+    }
+    const uint8_t tg = C.tag[L.cell_off + c];
+    if (tg & TAG_IFACE) {
+      for (int a = 0; a < D; ++a) uout[a * NF + fo + c] = uin[a * NF + fo + c];
+      continue;
+    }
+    const int crd[3] = {x, y, z};
+    float nvec[3], gm = 0.f;
+    for (int a = 0; a < D; ++a) {
+      int p[3] = {x, y, z}, m[3] = {x, y, z};
+      p[a] = clampwrap(L, a, crd[a] + 1);
+      m[a] = clampwrap(L, a, crd[a] - 1);
+      nvec[a] = 0.5f * (C.phi[fo + cidx(L, p[0], p[1], p[2])] - C.phi[fo + cidx(L, m[0], m[1], m[2])]);
+      gm += nvec[a] * nvec[a];
+    }
+    gm = sqrtf(gm);
+    const float ph = C.phi[fo + c];
+    const float sg = ph / sqrtf(ph * ph + 1.0f);
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < D; ++a) {
+      const float va = gm > 0.f ? sg * nvec[a] / gm : 0.f;
+      int nb[3] = {x, y, z};
+      nb[a] = clampwrap(L, a, crd[a] + (va > 0.f ? -1 : 1));
+      const long long cn = cidx(L, nb[0], nb[1], nb[2]);
+      const float *src = in_band(C, L, S, nb[0], nb[1], nb[2]) ? uin : C.ut0;
+      for (int b = 0; b < D; ++b) {
+        const float u0 = uin[b * NF + fo + c];
+        const float un = src[b * NF + fo + cn];
+        acc[b] += va * (va > 0.f ? (u0 - un) : (un - u0));
+      }
+    }
+    for (int b = 0; b < D; ++b) uout[b * NF + fo + c] = uin[b * NF + fo + c] - L.dtau_ext * acc[b];
+  }
+}
+
+// ------------------------------------------------------------------ transport
+// Gather phi along axis a at offsets -3..+3; points in the band (and, for the
+// reinitialisation, not frozen) read the stage array, others the committed phi.
+template <int D>
+__device__ __forceinline__ void gather7(const Ctx &C, const LevelDev &L, const BlockShape &S, const float *pin,
+                                        bool use_frozen, int x, int y, int z, int a, float v[7]) {
+  const int crd[3] = {x, y, z};
+  for (int m = 0; m < 7; ++m) {
+    int p[3] = {x, y, z};
+    p[a] = clampwrap(L, a, crd[a] + m - 3);
+    const long long cc = L.fine_off + cidx(L, p[0], p[1], p[2]);
+    bool upd = pin != C.phi && in_band(C, L, S, p[0], p[1], p[2]);
+    if (upd && use_frozen) upd = !C.frozen[cc];
+    v[m] = upd ? pin[cc] : C.phi[cc];
+  }
+}
+
+__device__ __forceinline__ float d5m(const float v[7]) {  // left-biased, offsets -3..+2
+  return (-2.f * v[0] + 15.f * v[1] - 60.f * v[2] + 20.f * v[3] + 30.f * v[4] - 3.f * v[5]) / 60.f;
+}
+__device__ __forceinline__ float d5p(const float v[7]) {  // mirror image
+  return -(-2.f * v[6] + 15.f * v[5] - 60.f * v[4] + 20.f * v[3] + 30.f * v[2] - 3.f * v[1]) / 60.f;
+}
+
+// TVD-RK3 stage of d phi/dt = -u~ . grad phi on the band (dt = 1):
+// stage 1: p1 = phi + L(phi); 2: p2 = 3/4 phi + 1/4 (p1 + L(p1)); 3: phi = 1/3 phi + 2/3 (p2 + L(p2)).
+template <int D>
+__global__ void k_adv_stage(Ctx C, BlockShape S, int glevel, int stage) {
+  const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
+  const int *lst = C.band_list + (long long)glevel * C.band_cap;
+  const float *pin = stage == 1 ? C.phi : (stage == 2 ? C.p1 : C.p2);
+  for (int w = blockIdx.x; w < nl; w += gridDim.x) {
+    const int gb = lst[w];
+    const LevelDev &L = C.lds[C.blk_ld[gb]];
+    int x, y, z;
+    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
+    const long long fc = L.fine_off + cidx(L, x, y, z);
+    float rhs = 0.f;
+    for (int a = 0; a < D; ++a) {
+      float v[7];
+      gather7<D>(C, L, S, pin, false, x, y, z, a, v);
+      const float ua = C.ut0[a * C.nfine + fc];
+      rhs -= ua * (ua >= 0.f ? d5m(v) : d5p(v));
+    }
+    const float p0 = C.phi[fc];
+    if (stage == 1) C.p1[fc] = p0 + rhs;
+    else if (stage == 2) C.p2[fc] = 0.75f * p0 + 0.25f * (C.p1[fc] + rhs);
+    else C.phi[fc] = p0 / 3.0f + (2.0f / 3.0f) * (C.p2[fc] + rhs);
+  }
+}
+
+// ------------------------------------------------------------------ reinitialisation
+// Frozen cells (sign change to any lattice neighbour in the box) and S(phi0).
+template <int Q>
+__global__ void k_reinit_prep(Ctx C, BlockShape S, int glevel) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
+  const int *lst = C.band_list + (long long)glevel * C.band_cap;
+  for (int w = blockIdx.x; w < nl; w += gridDim.x) {
+    const int gb = lst[w];
+    const LevelDev &L = C.lds[C.blk_ld[gb]];
+    int x, y, z;
+    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
+    const long long fc = L.fine_off + cidx(L, x, y, z);
+    const float p = C.phi[fc];
+    const bool g = p >= 0.f;
+    bool fr = false;
+    for (int i = 0; i < Q; ++i) {
+      if (i == LT::REST) continue;
+      int tx = x + LT::cx(i), ty = y + LT::cy(i), tz = z + LT::cz(i);
+      if (!(wrap(L, 0, tx) && wrap(L, 1, ty) && (D == 2 || wrap(L, 2, tz)))) continue;
+      if ((C.phi[L.fine_off + cidx(L, tx, ty, tz)] >= 0.f) != g) fr = true;
+    }
+    C.frozen[fc] = fr ? 1 : 0;
+    C.s0[fc] = p / sqrtf(p * p + 1.0f);
+  }
+}
+
+// HJ-WENO5 one-sided derivative (Jiang & Peng 2000) from the five differences.
+__device__ __forceinline__ float weno5(float v1, float v2, float v3, float v4, float v5) {
+  const float eps = 1e-6f;
+  const float d1 = v1 / 3.f - 7.f * v2 / 6.f + 11.f * v3 / 6.f;
+  const float d2 = -v2 / 6.f + 5.f * v3 / 6.f + v4 / 3.f;
+  const float d3 = v3 / 3.f + 5.f * v4 / 6.f - v5 / 6.f;
+  const float s1 = 13.f / 12.f * (v1 - 2.f * v2 + v3) * (v1 - 2.f * v2 + v3) +
+                   0.25f * (v1 - 4.f * v2 + 3.f * v3) * (v1 - 4.f * v2 + 3.f * v3);
+  const float s2 = 13.f / 12.f * (v2 - 2.f * v3 + v4) * (v2 - 2.f * v3 + v4) + 0.25f * (v2 - v4) * (v2 - v4);
+  const float s3 = 13.f / 12.f * (v3 - 2.f * v4 + v5) * (v3 - 2.f * v4 + v5) +
+                   0.25f * (3.f * v3 - 4.f * v4 + v5) * (3.f * v3 - 4.f * v4 + v5);
+  const float a1 = 0.1f / ((s1 + eps) * (s1 + eps));
+  const float a2 = 0.6f / ((s2 + eps) * (s2 + eps));
+  const float a3 = 0.3f / ((s3 + eps) * (s3 + eps));
+  return (a1 * d1 + a2 * d2 + a3 * d3) / (a1 + a2 + a3);
+}
+
+// TVD-RK3 stage of phi_tau = -S(phi0)(|grad phi|_G - 1) on band cells that are not frozen.
+template <int D>
+__global__ void k_reinit_stage(Ctx C, BlockShape S, int glevel, int stage) {
+  const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
+  const int *lst = C.band_list + (long long)glevel * C.band_cap;
+  const float *pin = stage == 1 ? C.phi : (stage == 2 ? C.p1 : C.p2);
+  for (int w = blockIdx.x; w < nl; w += gridDim.x) {
+    const int gb = lst[w];
+    const LevelDev &L = C.lds[C.blk_ld[gb]];
+    int x, y, z;
+    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
+    const long long fc = L.fine_off + cidx(L, x, y, z);
+    if (C.frozen[fc]) continue;
+    const float s0 = C.s0[fc];
+    float g2 = 0.f;
+    for (int a = 0; a < D; ++a) {
+      float v[7];
+      gather7<D>(C, L, S, pin, true, x, y, z, a, v);
+      const float dm = weno5(v[1] - v[0], v[2] - v[1], v[3] - v[2], v[4] - v[3], v[5] - v[4]);
+      const float dp = weno5(v[6] - v[5], v[5] - v[4], v[4] - v[3], v[3] - v[2], v[2] - v[1]);
+      float ga;
+      if (s0 > 0.f) ga = fmaxf(fmaxf(dm, 0.f) * fmaxf(dm, 0.f), fminf(dp, 0.f) * fminf(dp, 0.f));
+      else ga = fmaxf(fminf(dm, 0.f) * fminf(dm, 0.f), fmaxf(dp, 0.f) * fmaxf(dp, 0.f));
+      g2 += ga;
+    }
+    const float rhs = L.dtau_reinit * (-s0 * (sqrtf(g2) - 1.0f));
+    const float p0 = C.phi[fc];
+    if (stage == 1) C.p1[fc] = p0 + rhs;
+    else if (stage == 2) C.p2[fc] = 0.75f * p0 + 0.25f * (C.p1[fc] + rhs);
+    else C.phi[fc] = p0 / 3.0f + (2.0f / 3.0f) * (C.p2[fc] + rhs);
+  }
+}
+
+// ------------------------------------------------------------------ refill (Sec. 2.4)
+template <int Q>
+__device__ __forceinline__ void moments_q(const float *f, float &drho, float u[3]) {
+  using LT = Lat<Q>;
+  float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+  for (int i = 0; i < Q; ++i) {
+    d += f[i];
+    jx += LT::cx(i) * f[i];
+    jy += LT::cy(i) * f[i];
+    jz += LT::cz(i) * f[i];
+  }
+  drho = d;
+  const float inv = 1.0f / (1.0f + d);
+  u[0] = jx * inv; u[1] = jy * inv; u[2] = jz * inv;
+}
+
+template <int Q>
+__device__ __forceinline__ float feq_q(int i, float drho, const float u[3]) {
+  using LT = Lat<Q>;
+  const float cu = LT::cx(i) * u[0] + LT::cy(i) * u[1] + LT::cz(i) * u[2];
+  const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  return LT::w(i) * (drho + (1.0f + drho) * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
+}
+
+template <int Q, typename T>
+__global__ void k_refill(Ctx C, int glevel) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  const int n = min(C.counters[glevel * NCOUNT + 2], (int)C.list_cap);
+  const int2 *lst = C.flip_list + (long long)glevel * C.list_cap;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 it = lst[e];
+    const LevelDev &L = C.lds[it.x];
+    const long long c = it.y;
+    const int x = (int)(c % L.p[0]);
+    const int y = (int)((c / L.p[0]) % L.p[1]);
+    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    const long long fo = L.fine_off, NF = C.nfine, N = L.ncell;
+    T *Bf = fB<T, Q>(C, L);
+    const uint8_t tg = C.tag[L.cell_off + c];
+    const int Pn = tg & TAG_GAS;
+    const int Po = (tg & TAG_PREVGAS) ? 1 : 0;
+    const float sg = Pn == 0 ? 1.0f : -1.0f;
+    float mvec[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < D; ++a) mvec[a] = -sg * C.nvec[a * NF + fo + c];  // into the new phase
+    auto valid_new = [&](int tx, int ty, int tz, long long &ct) -> bool {
+      if (!(wrap(L, 0, tx) && wrap(L, 1, ty) && (D == 2 || wrap(L, 2, tz)))) return false;
+      ct = cidx(L, tx, ty, tz);
+      const uint8_t tt = C.tag[L.cell_off + ct];
+      const int g = tt & TAG_GAS, pg = (tt & TAG_PREVGAS) ? 1 : 0;
+      return (tt & TAG_LEAF) && g == Pn && pg == Pn;
+    };
+    int best = -1;
+    float bestv = -1e30f;
+    for (int i = 0; i < Q; ++i) {
+      if (i == LT::REST) continue;
+      long long ct;
+      if (!valid_new(x + LT::cx(i), y + LT::cy(i), z + LT::cz(i), ct)) continue;
+      const float nrm = sqrtf((float)(LT::cx(i) * LT::cx(i) + LT::cy(i) * LT::cy(i) + LT::cz(i) * LT::cz(i)));
+      const float v = (LT::cx(i) * mvec[0] + LT::cy(i) * mvec[1] + LT::cz(i) * mvec[2]) / nrm;
+      if (v > bestv) {
+        bestv = v;
+        best = i;
+      }
+    }
+    if (best < 0) {
+      for (int i = 0; i < Q; ++i) Store<T>::st(Bf + i * N + c, 0.0f, C.fp16_scale);
+      continue;
+    }
+    const int ex = LT::cx(best), ey = LT::cy(best), ez = LT::cz(best);
+    const float phr = C.phi[fo + c];
+    float q = 0.5f;
+    {
+      int bx = x - ex, by = y - ey, bz = z - ez;
+      if (wrap(L, 0, bx) && wrap(L, 1, by) && (D == 2 || wrap(L, 2, bz))) {
+        const long long cb = cidx(L, bx, by, bz);
+        if ((C.tag[L.cell_off + cb] & TAG_GAS) != Pn) q = phr / (phr - C.phi[fo + cb]);
+      }
+    }
+    long long c1 = 0, c2 = 0;
+    valid_new(x + ex, y + ey, z + ez, c1);
+    const bool quad = valid_new(x + 2 * ex, y + 2 * ey, z + 2 * ez, c2);
+    float w0, w1, w2;
+    if (quad) {
+      w0 = 2.0f / ((q + 1.0f) * (q + 2.0f));
+      w1 = 2.0f * q / (q + 1.0f);
+      w2 = -q / (q + 2.0f);
+    } else {
+      w0 = 1.0f / (1.0f + q);
+      w1 = q / (1.0f + q);
+      w2 = 0.0f;
+    }
+    float fo_[Q], f1[Q];
+    for (int i = 0; i < Q; ++i) {
+      fo_[i] = Store<T>::ld(Bf + i * N + c, C.fp16_inv);
+      f1[i] = Store<T>::ld(Bf + i * N + c1, C.fp16_inv);
+    }
+    float r_old, u_old[3], r1, u1[3];
+    moments_q<Q>(fo_, r_old, u_old);
+    moments_q<Q>(f1, r1, u1);
+    const float p_gamma = L.rho_phys[Po] * CS2 * r_old + L.sigma * sg * C.kappa[fo + c];
+    const float r_g = p_gamma / (L.rho_phys[Pn] * CS2);
+    float rr = w0 * r_g + w1 * r1;
+    float ur[3];
+    for (int a = 0; a < 3; ++a) ur[a] = w0 * u_old[a] + w1 * u1[a];
+    if (quad) {
+      float f2[Q], r2, u2[3];
+      for (int i = 0; i < Q; ++i) f2[i] = Store<T>::ld(Bf + i * N + c2, C.fp16_inv);
+      moments_q<Q>(f2, r2, u2);
+      rr += w2 * r2;
+      for (int a = 0; a < 3; ++a) ur[a] += w2 * u2[a];
+    }
+    for (int i = 0; i < Q; ++i) {
+      const float v = feq_q<Q>(i, rr, ur) + (f1[i] - feq_q<Q>(i, r1, u1));
+      Store<T>::st(Bf + i * N + c, v, C.fp16_scale);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ refinement sensor
+// Per listed coarse block: min |phi| (mode 0) or max phi (mode 1) over the
+// finest cells under it.
+__global__ void k_sensor(Ctx C, BlockShape S, const int *list, int nlist, int mode, float *out) {
+  __shared__ float red[32];
+  for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
+    const int gb = list[w];
+    const LevelDev &L = C.lds[C.blk_ld[gb]];
+    const LevelDev &F = C.lds[L.fine_ld];
+    const int lb = gb - L.block_off;
+    const int b[3] = {lb % L.nb[0], (lb / L.nb[0]) % L.nb[1], lb / (L.nb[0] * L.nb[1])};
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = b[a] * S.bs[a] * L.scale;
+      hi[a] = min((b[a] + 1) * S.bs[a], L.n[a]) * L.scale;
+      hi[a] = min(hi[a], F.n[a]);
+    }
+    const long long cnt = (long long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+    float acc = mode == 0 ? 3.0e38f : -3.0e38f;
+    for (long long e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int sx = hi[0] - lo[0], sy = hi[1] - lo[1];
+      const int x = lo[0] + (int)(e % sx);
+      const int y = lo[1] + (int)((e / sx) % sy);
+      const int z = lo[2] + (int)(e / ((long long)sx * sy));
+      const float p = C.phi[F.fine_off + cidx(F, x, y, z)];
+      acc = mode == 0 ? fminf(acc, fabsf(p)) : fmaxf(acc, p);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const float o = __shfl_down_sync(0xffffffffu, acc, off);
+      acc = mode == 0 ? fminf(acc, o) : fmaxf(acc, o);
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float r = red[0];
+      for (int k = 1; k < (int)(blockDim.x + 31) / 32; ++k) r = mode == 0 ? fminf(r, red[k]) : fmaxf(r, red[k]);
+      out[w] = r;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ host launchers
+#define LQ(kern, ...)                                                          \
+  do {                                                                         \
+    if (Q == 9) kern<9><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);        \
+    else kern<19><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);              \
+    return cudaGetLastError();                                                 \
+  } while (0)
+#define LD(kern, ...)                                                          \
+  do {                                                                         \
+    if (D == 2) kern<2><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);        \
+    else kern<3><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);               \
+    return cudaGetLastError();                                                 \
+  } while (0)
+
+cudaError_t run_classify_phase(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, int glevel, int init) {
+  LQ(k_classify_phase, C, S, list, n, glevel, init);
+}
+cudaError_t run_classify_links(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, int glevel) {
+  LQ(k_classify_links, C, S, list, n, glevel);
+}
+cudaError_t run_band(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, int glevel) {
+  LQ(k_band, C, S, list, n, glevel);
+}
+cudaError_t run_geometry(int D, Launch L, Ctx C, int glevel, int which) { LD(k_geometry, C, glevel, which); }
+cudaError_t run_ext_init(int Q, Launch L, Ctx C, int glevel) { LQ(k_ext_init, C, glevel); }
+cudaError_t run_ext_iter(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int commit) {
+  LD(k_ext_iter, C, S, glevel, uin, uout, commit);
+}
+cudaError_t run_adv_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage) {
+  LD(k_adv_stage, C, S, glevel, stage);
+}
+cudaError_t run_reinit_prep(int Q, Launch L, Ctx C, BlockShape S, int glevel) { LQ(k_reinit_prep, C, S, glevel); }
+cudaError_t run_reinit_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage) {
+  LD(k_reinit_stage, C, S, glevel, stage);
+}
+cudaError_t run_refill(int Q, int st, Launch L, Ctx C, int glevel) {
+  if (Q == 9) {
+    if (st == 0) k_refill<9, float><<<L.grid, L.block, 0, L.stream>>>(C, glevel);
+    else k_refill<9, __half><<<L.grid, L.block, 0, L.stream>>>(C, glevel);
+  } else {
+    if (st == 0) k_refill<19, float><<<L.grid, L.block, 0, L.stream>>>(C, glevel);
+    else k_refill<19, __half><<<L.grid, L.block, 0, L.stream>>>(C, glevel);
+  }
+  return cudaGetLastError();
+}
+cudaError_t run_sensor(Launch L, Ctx C, BlockShape S, const int *list, int n, int mode, float *out) {
+  k_sensor<<<L.grid, L.block, 0, L.stream>>>(C, S, list, n, mode, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lsb
