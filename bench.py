@@ -1,0 +1,263 @@
+#!/usr/bin/env python
+"""Throughput of the coupled level-set LB step on GB300: MLUPS and HBM roofline.
+
+Workload (default): 3D D3Q19 rising bubble, 128x128x256 base grid, 2 levels
+(finest 256x256x512), bubble radius 16 base cells, density ratio 1000,
+viscosity ratio 100, Eo 10, Re 35, FP32 storage (``--storage fp16s`` for the
+FP16-storage variant).  A step is one coarse time step of the whole method:
+collide-stream on both levels (the finest twice), interface bounce-back,
+level-set extension / transport / reinitialisation, classification, curvature,
+refill, level transfers and the periodic regrid.
+
+MLUPS = leaf cell updates (sum over levels of leaf cells x 2^level) / time.
+The state (2 x 19 x 4 B x ~38 M cells) is far larger than the 129 MB L2, so
+no flush is needed between steps.  The collide-stream kernel's duration is
+measured with CUDA events on the library stream inside the timed region;
+its algorithmic bytes are 2 * Q * sizeof(storage) per leaf cell update.
+
+Multi-GPU: the method is not sharded; with torchrun each rank runs an
+independent replica ("replicas only") and the value is the sum over ranks.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (leaf cell updates / s), 3D D3Q19 rising bubble, 2 AMR levels"
+HBM_FALLBACK = 6800.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return HBM_FALLBACK, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(smax) if smax else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+def cpu_baseline(budget_s=20.0):
+    """The FP64 oracle as it stands on the host cores: bounded sample = the
+    downsampled 32x32x64 copy of the workload (same physics, d scaled by 1/4),
+    as many coarse steps as fit in ~budget_s (at least one)."""
+    from oracle.sim import Sim
+    from paper_2601_05936_gb300 import workloads
+    case = workloads.rising_bubble_3d(scale=0.25)
+    s = Sim(case)
+    t0 = time.perf_counter()
+    n = 0
+    upd = 0.0
+    while True:
+        s.step(1)
+        n += 1
+        upd += sum(float(m[0].sum()) * 2 ** l for l, m in enumerate(s.masks))
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return dict(value=upd / dt / 1e6, unit="MLUPS", cores=1, kind="oracle",
+                sample=f"downsampled 32x32x64 base / 2-level copy of the workload, {n} coarse steps, "
+                       f"{upd:.0f} cell updates in {dt:.1f} s (numpy float64, single thread)")
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    res = cpu_baseline(budget_s=max(10.0, min(120.0, 6.0 * max(args.steps, 1))))
+    line = dict(impl="reference", metric=METRIC, value=res["value"], unit="MLUPS", n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic",
+                config=dict(workload="rising_bubble_3d_32x32x64_L2 (downsampled sample of 128x128x256_L2)",
+                            lattice="D3Q19"),
+                cpu_baseline=res, e2e=dict(value=res["value"], unit="MLUPS", h2d_bytes_per_step=0,
+                                           d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="lsb", choices=["lsb", "reference"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16s"])
+    ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-all", action="store_true", help="print a per-kernel time table to stderr")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2601_05936_gb300 import lsb, workloads
+
+    case = workloads.rising_bubble_3d(storage=args.storage)
+    stream = torch.cuda.Stream()
+    g = lsb.Grid(case, stream=stream, device=local)
+    g.step(args.warmup)
+    g.sync()
+
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    g.profile(2 if args.profile_all else 1)
+    launches0 = g.kernel_launches()
+    upd0 = g.cell_updates(total=True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    g.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = g.profile_read()
+    g.profile(0)
+    clk = clocks.stop()
+    launches = g.kernel_launches() - launches0
+    upd = g.cell_updates(total=True) - upd0
+    g.sync()
+
+    t = torch.tensor([ms, upd], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        tm = t.clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ts = t.clone()
+        dist.all_reduce(ts, op=dist.ReduceOp.SUM)
+        ms_max, upd_sum = float(tm[0]), float(ts[1])
+    else:
+        ms_max, upd_sum = ms, upd
+    value = upd_sum / (ms_max / 1e3) / 1e6
+
+    # roofline of the dominant kernel (collide-and-stream), from events on the library stream
+    cs_ms, cs_n, cs_bytes = prof.get("k_collide_stream", (0.0, 0, 0.0))
+    hbm, src = peaks()
+    achieved = cs_bytes / (cs_ms / 1e3) / 1e9 if cs_ms > 0 else None
+    roof = dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s",
+                frac=(achieved / hbm) if achieved else None, traffic=None, peak_source=src + " (hbm_gbs, of "
+                + src + ")", kernel="k_collide_stream", launches=cs_n,
+                bytes_per_launch=cs_bytes / max(cs_n, 1), avg_launch_ms=cs_ms / max(cs_n, 1),
+                share_of_step=cs_ms / ms if ms > 0 else None)
+    if args.profile_all and rank == 0:
+        for k, (kms, kn, kb) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
+            print(f"{k:20s} {kms:9.2f} ms {kn:7d} launches {100 * kms / ms:5.1f}%", file=sys.stderr)
+
+    # end to end through the public API with host buffers: parameters H2D, step, observables D2H
+    import ctypes
+    E = args.e2e_steps
+    nld = len(g.cases) * int(case["n_levels"])
+    h2d = ctypes.sizeof(lsb.Params) + 0  # the parameter struct the caller hands over each step
+    d2h = 8 * (4 + 2 * g.D) * len(g.cases)
+    g.sync()
+    u0 = g.cell_updates(total=True)
+    t0 = time.perf_counter()
+    for _ in range(E):
+        g.set_params(case)
+        g.step(1)
+        g.observables()
+    t1 = time.perf_counter()
+    e2e = dict(value=(g.cell_updates(total=True) - u0) / (t1 - t0) / 1e6 * world, unit="MLUPS",
+               h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h, steps=E,
+               note=f"lsb_set_params + lsb_step(1) + lsb_observables per step, host wall clock; the "
+                    f"parameter upload also rewrites {nld} level descriptors on the device")
+    obs = g.observables()[0]
+    g.close()
+
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline()
+    line = dict(metric=METRIC, value=value, unit="MLUPS", n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=ms_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32" if args.storage == "fp32" else "f16-store/f32-compute", data="synthetic",
+                config=dict(workload=case["name"], lattice="D3Q19", levels=int(case["n_levels"]),
+                            storage=args.storage, parallelism=f"replicas{world}",
+                            cell_updates_per_step=upd / args.steps, l2_flush="state 5.7 GB >> 129 MB L2",
+                            bubble=dict(centroid=[float(v) for v in obs["centroid"]],
+                                        velocity=[float(v) for v in obs["velocity"]])),
+                roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clk)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

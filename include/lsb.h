@@ -74,7 +74,8 @@ typedef struct {
   int lattice;          /* LSB_D2Q9 or LSB_D3Q19; all cases of a handle share it     */
   int base[3];          /* base-level cells per axis (base[2] ignored in 2D)         */
   int n_levels;         /* total levels including the base (1 = uniform), <= 4       */
-  int block[3];         /* block edge in cells, even, same on every level            */
+  int block[3];         /* block edge in cells, powers of two, same on every level;
+                           their product is a multiple of 32 and at most 1024       */
   int bc[3];            /* per axis: LSB_PERIODIC or LSB_WALL (walls on cell faces)  */
   double wall_u[6][3];  /* velocity of faces x-, x+, y-, y+, z-, z+                  */
   int storage;          /* LSB_FP32 or LSB_FP16S; all cases of a handle share it     */
@@ -90,7 +91,9 @@ typedef struct {
   double gravity[3];    /* acceleration acting on both phases                       */
   double sigma;         /* surface tension (Eq. Sdecomp)                            */
   double x_ref[3];      /* hydrostatic reference point for the initial density:
-                           rho_hat = 1 - gravity.(x - x_ref)/c_s^2                  */
+                           rho_hat = 1 - gravity.(x - x_ref)/c_s^2, plus in the gas
+                           p_gas0 / (rho[1] c_s^2)                                   */
+  double p_gas0;        /* initial gas gauge pressure (e.g. its Laplace pressure)    */
   int n_ext;            /* extension sweeps per step (Eq. hyperbolicExtension)      */
   double dtau_ext;      /* extension pseudo time step                               */
   int reinit_every;     /* reinitialise every this many finest steps (0 = never)    */
@@ -153,9 +156,16 @@ size_t lsb_field_bytes(const lsb_grid *g, int case_idx, int field, int level);
  */
 lsb_status lsb_observables(lsb_grid *g, double *out_host, size_t n_doubles);
 
-/* Finest-level leaf cell updates one coarse step performs (sum over levels
- * of leaf cells x 2^level), per case summed; the MLUPS numerator. */
-lsb_status lsb_cell_updates(const lsb_grid *g, double *updates_per_coarse_step);
+/* Cell updates (the MLUPS numerator): per_coarse_step = sum over levels of
+ * leaf cells x 2^level for the current grid (all cases); total_done = the same
+ * summed over every coarse step taken so far (regrids change the per-step
+ * count).  Either pointer may be NULL.  Needs no synchronisation. */
+lsb_status lsb_cell_updates(const lsb_grid *g, double *per_coarse_step, double *total_done);
+
+/* Velocity-set tables compiled into the library (Sec. 2.1, Fig. 1): c receives
+ * Q x 3 ints, w Q floats, opp Q ints (opposite directions); any may be NULL.
+ * Returns Q, or 0 for an unknown lattice.  Needs no GPU. */
+int lsb_lattice_table(int lattice, int *c, float *w, int *opp);
 
 /*
  * Adjoint of the bubble observables with respect to the parameters
@@ -163,6 +173,22 @@ lsb_status lsb_cell_updates(const lsb_grid *g, double *updates_per_coarse_step);
  * build.  Always returns LSB_ESTATE.
  */
 lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, float *dJ_dphi0);
+
+/* Kernel timing for diagnostics and the bench roofline: mode 0 off, 1 times
+ * every collide-and-stream launch, 2 times every launch.  Timed launches are
+ * bracketed by CUDA events on the handle's stream (a few microseconds each).
+ * Calling it discards earlier records.  Synchronises. */
+lsb_status lsb_profile(lsb_grid *g, int mode);
+
+/* Per kernel class k < n (see lsb_kernel_name): device milliseconds, launches
+ * and algorithmic bytes (collide-and-stream: 2*Q*sizeof(storage) per leaf cell
+ * update) summed over the records since the last lsb_profile or
+ * lsb_profile_read; consumes them.  Any output pointer may be NULL.  Synchronises. */
+lsb_status lsb_profile_read(lsb_grid *g, double *ms, double *bytes, uint64_t *launches, int n);
+
+/* Name of kernel class k, or NULL; lsb_kernel_count() classes exist. */
+const char *lsb_kernel_name(int k);
+int lsb_kernel_count(void);
 
 /* Wait for the handle's stream and return any latched device error. */
 lsb_status lsb_sync(lsb_grid *g);

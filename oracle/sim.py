@@ -29,7 +29,7 @@ from .lattice import CS2, get as get_lattice
 from .lbm import collide, equilibrium, moments, omega_from_nu, strain_rate
 
 DEFAULTS = dict(
-    n_levels=1, sigma=0.0, body_force=None, gravity=None, x_ref=None, wall_u=None,
+    n_levels=1, sigma=0.0, body_force=None, gravity=None, x_ref=None, wall_u=None, p_gas0=0.0,
     n_ext=8, dtau_ext=0.5, reinit_every=1, n_reinit=1, dtau_reinit=0.3,
     refine_dist=None, sensor="band", regrid_every=0, ls_active=True,
 )
@@ -79,6 +79,7 @@ class Sim:
             r = 2.0 ** (self.L - 1 - l)
             xc = g.centers(r)
             drho = -(self.gravity[:, None] * (xc - x_ref[:, None])).sum(0) / CS2
+            drho = drho + np.where(self.phase[l] == 1, float(c["p_gas0"]) / (self.rho_phys[1] * CS2), 0.0)
             self.f.append(equilibrium(lat, 1.0 + drho, np.zeros((D, g.N))))
         self.ghost = [None] * self.L
 

@@ -37,13 +37,19 @@ def _stale():
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False, extra=()):
-    """Compile liblsb.so if any source is newer than it; returns the path."""
-    if not force and not _stale():
+def build(force=False, verbose=False, extra=(), out=None):
+    """Compile liblsb.so if any source is newer than it; returns the path.
+
+    ``extra`` adds nvcc flags and ``out`` writes the library elsewhere (for
+    comparing compile-time variants)."""
+    if out is None and not force and not _stale():
         return LIB
     os.makedirs(LIBDIR, exist_ok=True)
     exe = nvcc()
-    objs = [os.path.join(LIBDIR, s.replace(".cu", ".o")) for s in SOURCES]
+    odir = LIBDIR if out is None else os.path.dirname(os.path.abspath(out))
+    os.makedirs(odir, exist_ok=True)
+    tag = "" if out is None else "_" + os.path.basename(out).replace(".so", "")
+    objs = [os.path.join(odir, s.replace(".cu", tag + ".o")) for s in SOURCES]
 
     def comp(src_obj):
         src, obj = src_obj
@@ -57,12 +63,13 @@ def build(force=False, verbose=False, extra=()):
 
     with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
         list(ex.map(comp, zip(SOURCES, objs)))
-    tmp = LIB + ".tmp"
+    target = LIB if out is None else out
+    tmp = target + ".tmp"
     r = subprocess.run([exe, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, target)
+    return target
 
 
 if __name__ == "__main__":

@@ -24,12 +24,26 @@ using namespace lsb;
 namespace {
 
 constexpr int MAXL = 4;
+const char *const KNAMES[] = {"k_collide_stream", "k_interface_bc", "k_restrict", "k_ghost", "k_prolong", "k_level_tags", "k_observables", "k_export", "k_classify_phase", "k_classify_links", "k_band", "k_geometry", "k_ext_init", "k_ext_iter", "k_adv_stage", "k_reinit_prep", "k_reinit_stage", "k_refill", "k_sensor", "k_init", "k_collect"};
+constexpr int NKERN = sizeof(KNAMES) / sizeof(KNAMES[0]);
+
+struct ProfRec {
+  int kid;
+  cudaEvent_t a, b;
+  double bytes;
+};
 
 struct WorkList {
   int *d = nullptr;
   int n = 0;
   int cap = 0;
   std::vector<int> h;
+};
+
+struct CellList {
+  int2 *d = nullptr;
+  int n = 0;
+  int cap = 0;
 };
 
 struct CaseHost {
@@ -56,6 +70,7 @@ struct lsb_grid {
   // device buffers
   LevelDev *d_lds = nullptr;
   int *d_blk_ld = nullptr;
+  int4 *d_blk_info = nullptr;
   int8_t *d_bstat = nullptr, *d_bstat_old = nullptr;
   uint8_t *d_bflag = nullptr, *d_tag = nullptr, *d_frozen = nullptr;
   void *d_buf[2] = {nullptr, nullptr};
@@ -74,6 +89,8 @@ struct lsb_grid {
   // work lists per global level
   WorkList cs[MAXL], rst[MAXL], ghost[MAXL], finest[MAXL], leaf, tags, sens, all_active;
   std::vector<int> tags_prev;
+  CellList ghost_cells[MAXL], rl_cells[MAXL];
+  int *d_count = nullptr;
   int par[MAXL] = {0, 0, 0, 0};
   long long fine_steps[MAXL] = {0, 0, 0, 0};
   long long coarse_steps = 0;
@@ -83,6 +100,12 @@ struct lsb_grid {
   uint64_t launches = 0;
   std::string err;
   int latched = 0;
+  // kernel timing
+  int prof_mode = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<ProfRec> prof;
+  double leaf_cells[MAXL] = {0, 0, 0, 0};
+  double updates_done = 0;
 };
 
 namespace {
@@ -134,6 +157,7 @@ Ctx make_ctx(lsb_grid *g) {
   memset(&C, 0, sizeof C);
   C.lds = g->d_lds;
   C.blk_ld = g->d_blk_ld;
+  C.blk_info = g->d_blk_info;
   C.bstat = g->d_bstat;
   C.bstat_old = g->d_bstat_old;
   C.bflag = g->d_bflag;
@@ -171,7 +195,12 @@ Ctx make_ctx(lsb_grid *g) {
 
 BlockShape shape(const lsb_grid *g) {
   BlockShape S;
-  for (int a = 0; a < 3; ++a) S.bs[a] = g->bs[a];
+  for (int a = 0; a < 3; ++a) {
+    S.bs[a] = g->bs[a];
+    int lg = 0;
+    while ((1 << lg) < g->bs[a]) ++lg;
+    S.lg[a] = lg;
+  }
   return S;
 }
 
@@ -184,8 +213,38 @@ lsb_status launched(lsb_grid *g, cudaError_t e) {
 
 Launch LN(const lsb_grid *g, int grid, int block) { return Launch{grid, block, g->stream}; }
 
-#define RUN(grid, block, fn, ...) \
-  do { if ((grid) > 0) TRY(launched(g, fn(__VA_ARGS__))); } while (0)
+cudaEvent_t take_event(lsb_grid *g) {
+  if (!g->ev_pool.empty()) {
+    cudaEvent_t e = g->ev_pool.back();
+    g->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+bool profiled(const lsb_grid *g, int kid) { return g->prof_mode == 2 || (g->prof_mode == 1 && kid == 0); }
+
+// Launch through a host launcher; with profiling on, bracket it with events.
+#define RUN(kid, bytes, grid, block, fn, ...)                         \
+  do {                                                                \
+    if ((grid) > 0) {                                                 \
+      ProfRec pr_{kid, nullptr, nullptr, (double)(bytes)};            \
+      const bool on_ = profiled(g, kid);                              \
+      if (on_) {                                                      \
+        pr_.a = take_event(g);                                        \
+        pr_.b = take_event(g);                                        \
+        cudaEventRecord(pr_.a, g->stream);                            \
+      }                                                               \
+      cudaError_t e_ = fn(__VA_ARGS__);                               \
+      if (on_) {                                                      \
+        cudaEventRecord(pr_.b, g->stream);                            \
+        g->prof.push_back(pr_);                                       \
+      }                                                               \
+      TRY(launched(g, e_));                                           \
+    }                                                                 \
+  } while (0)
 
 constexpr int DYN_GRID = 152 * 8;  // CTAs for kernels over device-sized lists
 
@@ -273,6 +332,7 @@ lsb_status build_lists(lsb_grid *g) {
   }
   g->leaf.h.clear();
   g->all_active.h.clear();
+  for (int l = 0; l < MAXL; ++l) g->leaf_cells[l] = 0;
   std::vector<int> tl;
   for (size_t ld = 0; ld < g->lds.size(); ++ld) {
     const LevelDev &L = g->lds[ld];
@@ -284,6 +344,11 @@ lsb_status build_lists(lsb_grid *g) {
       bool near_leaf = any_neighbor(g, L, st, b, BLK_LEAF, false);
       bool near_active = any_neighbor(g, L, st, b, 0, true);
       if (s == BLK_LEAF) {
+        int bc[3];
+        block_coords(L, b, bc);
+        double cnt = 1;
+        for (int a = 0; a < 3; ++a) cnt *= std::min(g->bs[a], L.n[a] - bc[a] * g->bs[a]);
+        g->leaf_cells[l] += cnt;
         g->cs[l].h.push_back(gb);
         g->leaf.h.push_back(gb);
         if (L.finest) g->finest[l].h.push_back(gb);
@@ -328,7 +393,7 @@ lsb_status upload_status(lsb_grid *g, const std::vector<std::vector<int8_t>> &st
 lsb_status level_tags(lsb_grid *g) {
   Ctx C = make_ctx(g);
   BlockShape S = shape(g);
-  RUN(g->tags.n, g->nthreads, run_level_tags, g->Q, LN(g, g->tags.n, g->nthreads), C, S, (const int *)g->tags.d,
+  RUN(5, 0, g->tags.n, g->nthreads, run_level_tags, g->Q, LN(g, g->tags.n, g->nthreads), C, S, (const int *)g->tags.d,
       g->tags.n);
   return LSB_OK;
 }
@@ -348,11 +413,11 @@ lsb_status classify(lsb_grid *g, int l, int init) {
   WorkList &F = g->finest[l];
   const int *fl = F.d;
   const int Q = g->Q, D = g->D, nt = g->nthreads;
-  RUN(F.n, nt, run_classify_phase, Q, LN(g, F.n, nt), C, S, fl, F.n, l, init);
-  RUN(F.n, nt, run_classify_links, Q, LN(g, F.n, nt), C, S, fl, F.n, l);
-  RUN(F.n, 128, run_band, Q, LN(g, (F.n + 127) / 128, 128), C, S, fl, F.n, l);
-  RUN(1, 128, run_geometry, D, LN(g, DYN_GRID, 128), C, l, 0);
-  RUN(1, 128, run_geometry, D, LN(g, DYN_GRID, 128), C, l, 1);
+  RUN(8, 0, F.n, nt, run_classify_phase, Q, LN(g, F.n, nt), C, S, fl, F.n, l, init);
+  RUN(9, 0, F.n, nt, run_classify_links, Q, LN(g, F.n, nt), C, S, fl, F.n, l);
+  RUN(10, 0, F.n, 128, run_band, Q, LN(g, (F.n + 127) / 128, 128), C, S, fl, F.n, l);
+  RUN(11, 0, 1, 128, run_geometry, D, LN(g, DYN_GRID, 128), C, l, 0);
+  RUN(11, 0, 1, 128, run_geometry, D, LN(g, DYN_GRID, 128), C, l, 1);
   return LSB_OK;
 }
 
@@ -363,25 +428,25 @@ lsb_status levelset(lsb_grid *g, int l) {
   const int nb = std::max(1, std::min(g->band_cap, 152 * 16));
   const int nt = g->nthreads;
   const int Q = g->Q, D = g->D;
-  RUN(1, 128, run_ext_init, Q, LN(g, DYN_GRID, 128), C, l);
+  RUN(12, 0, 1, 128, run_ext_init, Q, LN(g, DYN_GRID, 128), C, l);
   const float *uin = g->d_ut[0];
   for (int it = 0; it < g->n_ext; ++it) {
     float *uout = g->d_ut[1 + (it & 1)];
-    RUN(nb, nt, run_ext_iter, D, LN(g, nb, nt), C, S, l, uin, uout, 0);
+    RUN(13, 0, nb, nt, run_ext_iter, D, LN(g, nb, nt), C, S, l, uin, uout, 0);
     uin = uout;
   }
   if (g->n_ext > 0) {
-    RUN(nb, nt, run_ext_iter, D, LN(g, nb, nt), C, S, l, uin, (float *)nullptr, 1);
+    RUN(13, 0, nb, nt, run_ext_iter, D, LN(g, nb, nt), C, S, l, uin, (float *)nullptr, 1);
   }
   for (int st = 1; st <= 3; ++st) {
-    RUN(nb, nt, run_adv_stage, D, LN(g, nb, nt), C, S, l, st);
+    RUN(14, 0, nb, nt, run_adv_stage, D, LN(g, nb, nt), C, S, l, st);
   }
   const bool due = g->reinit_every > 0 && ((g->fine_steps[l] + 1) % g->reinit_every == 0);
   if (due && g->n_reinit > 0) {
-    RUN(nb, nt, run_reinit_prep, Q, LN(g, nb, nt), C, S, l);
+    RUN(15, 0, nb, nt, run_reinit_prep, Q, LN(g, nb, nt), C, S, l);
     for (int r = 0; r < g->n_reinit; ++r)
       for (int st = 1; st <= 3; ++st) {
-        RUN(nb, nt, run_reinit_stage, D, LN(g, nb, nt), C, S, l, st);
+        RUN(16, 0, nb, nt, run_reinit_stage, D, LN(g, nb, nt), C, S, l, st);
       }
   }
   return LSB_OK;
@@ -399,22 +464,23 @@ lsb_status advance(lsb_grid *g, int l) {
   const int nt = g->nthreads;
   Ctx C = make_ctx(g);
   const int Q = g->Q, st = g->storage;
-  RUN(g->rst[l].n, nt, run_restrict, Q, st, LN(g, g->rst[l].n, nt), C, S, (const int *)g->rst[l].d, g->rst[l].n, 0);
-  RUN(g->cs[l].n, nt, run_collide_stream, Q, st, LN(g, g->cs[l].n, nt), C, S, (const int *)g->cs[l].d, g->cs[l].n);
+  const CellList &rc = g->rl_cells[l];
+  RUN(2, 0, rc.n, 128, run_restrict_cells, Q, st, LN(g, (rc.n + 127) / 128, 128), C, (const int2 *)rc.d, rc.n);
+  RUN(0, 2.0 * g->Q * (g->storage == LSB_FP32 ? 4 : 2) * g->leaf_cells[l], g->cs[l].n, nt, run_collide_stream, Q, st, LN(g, g->cs[l].n, nt), C, S, (const int *)g->cs[l].d, g->cs[l].n);
   if (has_finest(g, l)) {
-    RUN(1, 128, run_interface_bc, Q, st, LN(g, DYN_GRID, 128), C, l);
+    RUN(1, 0, 1, 128, run_interface_bc, Q, st, LN(g, DYN_GRID, 128), C, l);
     if (ls_active_any(g, l)) TRY(levelset(g, l));
     TRY(classify(g, l, 0));
     C = make_ctx(g);
-    RUN(1, 128, run_refill, Q, st, LN(g, DYN_GRID, 128), C, l);
+    RUN(17, 0, 1, 128, run_refill, Q, st, LN(g, DYN_GRID, 128), C, l);
     g->fine_steps[l]++;
   }
   if (l + 1 < g->Lmax) {
-    const WorkList &gh = g->ghost[l + 1];
     for (int sub = 0; sub < 2; ++sub) {
       C = make_ctx(g);
       const float theta = sub == 0 ? 0.0f : 0.5f;
-      RUN(gh.n, nt, run_ghost, Q, st, LN(g, gh.n, nt), C, S, (const int *)gh.d, gh.n, theta);
+      const CellList &gc = g->ghost_cells[l + 1];
+      RUN(3, 0, gc.n, 128, run_ghost_cells, Q, st, LN(g, (gc.n + 127) / 128, 128), C, (const int2 *)gc.d, gc.n, theta);
       TRY(advance(g, l + 1));
     }
   }
@@ -423,6 +489,13 @@ lsb_status advance(lsb_grid *g, int l) {
 }
 
 lsb_status regrid(lsb_grid *g, bool initial);
+
+// Leaf cell updates of one coarse step: sum over levels of leaf cells x 2^level.
+double updates_per_step(const lsb_grid *g) {
+  double t = 0;
+  for (int l = 0; l < MAXL; ++l) t += g->leaf_cells[l] * (double)(1 << l);
+  return t;
+}
 
 lsb_status check_params(const lsb_params &p, const lsb_grid_desc &d, std::string &why) {
   char b[256];
@@ -464,6 +537,7 @@ void fill_physics(lsb_grid *g, LevelDev &L, const CaseHost &ch) {
     L.grav[a] = (float)p.gravity[a];
   }
   L.ls_active = p.ls_active;
+  L.p_gas0 = (float)p.p_gas0;
   (void)g;
 }
 
@@ -484,7 +558,7 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
   const int D = d0.lattice == LSB_D2Q9 ? 2 : 3;
   int bs[3] = {d0.block[0], d0.block[1], D == 3 ? d0.block[2] : 1};
   for (int a = 0; a < D; ++a)
-    if (bs[a] < 2 || bs[a] % 2) return fail(nullptr, LSB_EINVAL, "block edges must be even and >= 2");
+    if (bs[a] < 2 || (bs[a] & (bs[a] - 1))) return fail(nullptr, LSB_EINVAL, "block edges must be powers of two >= 2");
   const int nthreads = bs[0] * bs[1] * bs[2];
   if (nthreads % 32 || nthreads > 1024) return fail(nullptr, LSB_EINVAL, "block must hold 32..1024 cells, a multiple of 32");
   for (int c = 0; c < n_cases; ++c) {
@@ -561,6 +635,11 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
     }
     g->cases.push_back(ch);
   }
+  for (const LevelDev &L : g->lds)
+    if ((double)L.ncell * (g->Q + 1) >= 4294967295.0) {
+      lsb_destroy(g);
+      return fail(nullptr, LSB_EINVAL, "a level holds %lld cells; Q x cells must stay below 2^32", L.ncell);
+    }
   g->ncell_total = cell_off;
   g->nblock_total = block_off;
   g->nfine = fine_off;
@@ -581,6 +660,7 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
   } while (0)
   ALLOC(g->d_lds, sizeof(LevelDev) * g->lds.size());
   ALLOC(g->d_blk_ld, sizeof(int) * g->nblock_total);
+  ALLOC(g->d_blk_info, sizeof(int4) * g->nblock_total);
   ALLOC(g->d_bstat, g->nblock_total);
   ALLOC(g->d_bstat_old, g->nblock_total);
   ALLOC(g->d_bflag, g->nblock_total);
@@ -609,8 +689,14 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
 #undef ALLOC
   // block -> level descriptor
   std::vector<int> bl(g->nblock_total);
+  std::vector<int4> binfo(g->nblock_total);
   for (size_t ld = 0; ld < g->lds.size(); ++ld)
-    for (int b = 0; b < g->lds[ld].nblock; ++b) bl[g->lds[ld].block_off + b] = (int)ld;
+    for (int b = 0; b < g->lds[ld].nblock; ++b) {
+      bl[g->lds[ld].block_off + b] = (int)ld;
+      int bc[3];
+      block_coords(g->lds[ld], b, bc);
+      binfo[g->lds[ld].block_off + b] = make_int4((int)ld, bc[0], bc[1], bc[2]);
+    }
   auto cuerr = [&](cudaError_t e, const char *what) -> bool {
     if (e == cudaSuccess) return false;
     g_create_error = std::string(what) + ": " + cudaGetErrorString(e);
@@ -618,6 +704,7 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
   };
   if (cuerr(cudaMemcpy(g->d_lds, g->lds.data(), sizeof(LevelDev) * g->lds.size(), cudaMemcpyHostToDevice), "lds") ||
       cuerr(cudaMemcpy(g->d_blk_ld, bl.data(), sizeof(int) * bl.size(), cudaMemcpyHostToDevice), "blk_ld") ||
+      cuerr(cudaMemcpy(g->d_blk_info, binfo.data(), sizeof(int4) * binfo.size(), cudaMemcpyHostToDevice), "blk_info") ||
       cuerr(cudaMemset(g->d_tag, 0, g->ncell_total), "tag") ||
       cuerr(cudaMemset(g->d_bflag, 0, g->nblock_total), "bflag") ||
       cuerr(cudaMemset(g->d_err, 0, sizeof(int)), "err") ||
@@ -679,6 +766,7 @@ lsb_status lsb_step(lsb_grid *g, int n) {
   if (!g || n < 0) return LSB_EINVAL;
   for (int k = 0; k < n; ++k) {
     TRY(advance(g, 0));
+    g->updates_done += updates_per_step(g);
     g->coarse_steps++;
     if (g->regrid_every > 0 && g->Lmax > 1 && g->coarse_steps % g->regrid_every == 0) TRY(regrid(g, false));
   }
@@ -799,7 +887,7 @@ lsb_status lsb_observables(lsb_grid *g, double *out_host, size_t n_doubles) {
   CU(cudaMemsetAsync(g->d_obs, 0, sizeof(double) * stride * g->ncase, g->stream));
   Ctx C = make_ctx(g);
   BlockShape S = shape(g);
-  RUN(g->leaf.n, g->nthreads, run_observables, g->Q, g->storage, LN(g, g->leaf.n, g->nthreads), C, S,
+  RUN(6, 0, g->leaf.n, g->nthreads, run_observables, g->Q, g->storage, LN(g, g->leaf.n, g->nthreads), C, S,
       (const int *)g->leaf.d, g->leaf.n, g->d_obs, stride);
   std::vector<double> h((size_t)stride * g->ncase);
   CU(cudaMemcpyAsync(h.data(), g->d_obs, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g->stream));
@@ -819,25 +907,51 @@ lsb_status lsb_observables(lsb_grid *g, double *out_host, size_t n_doubles) {
   return s;
 }
 
-lsb_status lsb_cell_updates(const lsb_grid *g, double *upd) {
-  if (!g || !upd) return LSB_EINVAL;
-  double total = 0;
-  for (size_t ld = 0; ld < g->lds.size(); ++ld) {
-    const LevelDev &L = g->lds[ld];
-    long long leaf_cells = 0;
-    for (int b = 0; b < L.nblock; ++b) {
-      if (g->status[ld][b] != BLK_LEAF) continue;
-      int bc[3];
-      block_coords(L, b, bc);
-      long long cnt = 1;
-      for (int a = 0; a < 3; ++a) cnt *= std::min(g->bs[a], L.n[a] - bc[a] * g->bs[a]);
-      leaf_cells += cnt;
-    }
-    total += (double)leaf_cells * (double)(1LL << L.level);
-  }
-  *upd = total;
+lsb_status lsb_cell_updates(const lsb_grid *g, double *per_coarse_step, double *total_done) {
+  if (!g) return LSB_EINVAL;
+  if (per_coarse_step) *per_coarse_step = updates_per_step(g);
+  if (total_done) *total_done = g->updates_done;
   return LSB_OK;
 }
+
+lsb_status lsb_profile(lsb_grid *g, int mode) {
+  if (!g || mode < 0 || mode > 2) return LSB_EINVAL;
+  CU(cudaStreamSynchronize(g->stream));
+  for (ProfRec &r : g->prof) {
+    g->ev_pool.push_back(r.a);
+    g->ev_pool.push_back(r.b);
+  }
+  g->prof.clear();
+  g->prof_mode = mode;
+  return LSB_OK;
+}
+
+lsb_status lsb_profile_read(lsb_grid *g, double *ms, double *bytes, uint64_t *launches, int n) {
+  if (!g || n < 0) return LSB_EINVAL;
+  CU(cudaStreamSynchronize(g->stream));
+  for (int k = 0; k < n; ++k) {
+    if (ms) ms[k] = 0;
+    if (bytes) bytes[k] = 0;
+    if (launches) launches[k] = 0;
+  }
+  for (ProfRec &r : g->prof) {
+    float t = 0.f;
+    CU(cudaEventElapsedTime(&t, r.a, r.b));
+    if (r.kid < n) {
+      if (ms) ms[r.kid] += t;
+      if (bytes) bytes[r.kid] += r.bytes;
+      if (launches) launches[r.kid] += 1;
+    }
+    g->ev_pool.push_back(r.a);
+    g->ev_pool.push_back(r.b);
+  }
+  g->prof.clear();
+  return LSB_OK;
+}
+
+const char *lsb_kernel_name(int k) { return (k >= 0 && k < NKERN) ? KNAMES[k] : nullptr; }
+
+int lsb_kernel_count(void) { return NKERN; }
 
 lsb_status lsb_backward(lsb_grid *g, const double *, double *, float *) {
   if (!g) return LSB_EINVAL;
@@ -853,6 +967,11 @@ void lsb_destroy(lsb_grid *g) {
   if (g->stream) cudaStreamSynchronize(g->stream);
   else cudaDeviceSynchronize();
   for (void *p : g->allocs) cudaFree(p);
+  for (ProfRec &r : g->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
   delete g;
 }
 
@@ -883,6 +1002,35 @@ int lsb_lattice_table(int lattice, int *c, float *w, int *opp) {
 // ------------------------------------------------------------------ regrid
 namespace {
 
+// Compact ghost-ring and restriction-layer cells of every level into cell lists.
+lsb_status collect_cells(lsb_grid *g) {
+  BlockShape S = shape(g);
+  if (!g->d_count) TRY(dalloc(g, &g->d_count, sizeof(int)));
+  for (int l = 0; l < g->Lmax; ++l) {
+    for (int kind = 0; kind < 2; ++kind) {
+      WorkList &bl = kind == 0 ? g->ghost[l] : g->rst[l];
+      CellList &cl = kind == 0 ? g->ghost_cells[l] : g->rl_cells[l];
+      const int bits = kind == 0 ? TAG_GHOST : TAG_RLAYER;
+      cl.n = 0;
+      if (bl.n == 0) continue;
+      const int need = bl.n * g->nthreads;
+      if (need > cl.cap) {
+        TRY(dalloc(g, &cl.d, sizeof(int2) * (size_t)need));
+        cl.cap = need;
+      }
+      CU(cudaMemsetAsync(g->d_count, 0, sizeof(int), g->stream));
+      Ctx C = make_ctx(g);
+      RUN(20, 0, bl.n, g->nthreads, run_collect, LN(g, bl.n, g->nthreads), C, S, (const int *)bl.d, bl.n, bits, cl.d,
+          g->d_count, cl.cap);
+      int n = 0;
+      CU(cudaMemcpyAsync(&n, g->d_count, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+      CU(cudaStreamSynchronize(g->stream));
+      cl.n = std::min(n, cl.cap);
+    }
+  }
+  return LSB_OK;
+}
+
 lsb_status regrid(lsb_grid *g, bool initial) {
   BlockShape S = shape(g);
   const int nt = g->nthreads;
@@ -902,7 +1050,7 @@ lsb_status regrid(lsb_grid *g, bool initial) {
       bool any = false;
       for (const CaseHost &ch : g->cases) any |= (ch.p.sensor == mode);
       if (!any) continue;
-      RUN(g->sens.n, 256, run_sensor, LN(g, g->sens.n, 256), C, S, (const int *)g->sens.d, g->sens.n, mode, g->d_sens);
+      RUN(18, 0, g->sens.n, 256, run_sensor, LN(g, g->sens.n, 256), C, S, (const int *)g->sens.d, g->sens.n, mode, g->d_sens);
       std::vector<float> tmp(g->sens.h.size());
       CU(cudaMemcpyAsync(tmp.data(), g->d_sens, sizeof(float) * tmp.size(), cudaMemcpyDeviceToHost, g->stream));
       CU(cudaStreamSynchronize(g->stream));
@@ -937,7 +1085,7 @@ lsb_status regrid(lsb_grid *g, bool initial) {
     TRY(build_lists(g));
     TRY(level_tags(g));
     Ctx C = make_ctx(g);
-    RUN(g->all_active.n, nt, run_init, g->Q, g->storage, LN(g, g->all_active.n, nt), C, S,
+    RUN(19, 0, g->all_active.n, nt, run_init, g->Q, g->storage, LN(g, g->all_active.n, nt), C, S,
         (const int *)g->all_active.d, g->all_active.n);
   } else {
     std::vector<std::vector<int8_t>> old = g->status;
@@ -956,7 +1104,7 @@ lsb_status regrid(lsb_grid *g, bool initial) {
       if (wl.h.empty()) continue;
       TRY(upload_list(g, wl));
       Ctx C = make_ctx(g);
-      RUN(wl.n, nt, run_restrict, g->Q, g->storage, LN(g, wl.n, nt), C, S, (const int *)wl.d, wl.n, 1);
+      RUN(2, 0, wl.n, nt, run_restrict, g->Q, g->storage, LN(g, wl.n, nt), C, S, (const int *)wl.d, wl.n, 1);
       CU(cudaStreamSynchronize(g->stream));
       cudaFree(wl.d);
       g->allocs.erase(std::remove(g->allocs.begin(), g->allocs.end(), (void *)wl.d), g->allocs.end());
@@ -985,7 +1133,7 @@ lsb_status regrid(lsb_grid *g, bool initial) {
       if (wl.h.empty()) continue;
       TRY(upload_list(g, wl));
       Ctx C = make_ctx(g);
-      RUN(wl.n, nt, run_prolong, g->Q, g->storage, LN(g, wl.n, nt), C, S, (const int *)wl.d, wl.n);
+      RUN(4, 0, wl.n, nt, run_prolong, g->Q, g->storage, LN(g, wl.n, nt), C, S, (const int *)wl.d, wl.n);
       CU(cudaStreamSynchronize(g->stream));
       cudaFree(wl.d);
       g->allocs.erase(std::remove(g->allocs.begin(), g->allocs.end(), (void *)wl.d), g->allocs.end());
@@ -995,6 +1143,7 @@ lsb_status regrid(lsb_grid *g, bool initial) {
     TRY(build_lists(g));
     TRY(level_tags(g));
   }
+  TRY(collect_cells(g));
   CU(cudaMemsetAsync(g->d_bflag, 0, g->nblock_total, g->stream));
   for (int l = 0; l < g->Lmax; ++l) TRY(classify(g, l, 1));
   return LSB_OK;

@@ -98,12 +98,14 @@ struct LevelDev {
   float rho_phys[2], eta[2], sigma;
   float dtau_ext, dtau_reinit;
   float x_ref[3], grav[3];
+  float p_gas0;
   int ls_active;
 };
 
 struct Ctx {
   const LevelDev *lds;
   const int *blk_ld;       // global block id -> level descriptor
+  const int4 *blk_info;    // global block id -> (level descriptor, block x, y, z)
   int8_t *bstat;           // block status (per global block)
   int8_t *bstat_old;       // previous status during regrid
   uint8_t *bflag;          // finest-level block flags
@@ -149,7 +151,8 @@ template <> struct Store<__half> {
 };
 
 struct BlockShape {
-  int bs[3];
+  int bs[3];  // block edge per axis (powers of two)
+  int lg[3];  // log2 of the edges
 };
 
 // Population state A (pre-collision, time t) and B (destination of the push) of a level.
@@ -176,12 +179,35 @@ __device__ __forceinline__ void block_cell(const LevelDev &L, int lb, int t, con
   z = bz * bs[2] + tz;
 }
 
+// Same with power-of-two block edges (shifts and masks for the thread part).
+__device__ __forceinline__ void block_cell2(const LevelDev &L, int lb, int t, const BlockShape &S, int &x,
+                                            int &y, int &z) {
+  const int nb0 = L.nb[0], nb1 = L.nb[1];
+  const int q0 = lb / nb0;
+  const int bx = lb - q0 * nb0;
+  const int bz = q0 / nb1;
+  const int by = q0 - bz * nb1;
+  x = (bx << S.lg[0]) + (t & (S.bs[0] - 1));
+  y = (by << S.lg[1]) + ((t >> S.lg[0]) & (S.bs[1] - 1));
+  z = (bz << S.lg[2]) + (t >> (S.lg[0] + S.lg[1]));
+}
+
 __device__ __forceinline__ long long cidx(const LevelDev &L, int x, int y, int z) {
   return (long long)x + (long long)L.p[0] * ((long long)y + (long long)L.p[1] * z);
 }
 
-__device__ __forceinline__ int block_of(const LevelDev &L, int x, int y, int z, const int bs[3]) {
-  return (x / bs[0]) + L.nb[0] * ((y / bs[1]) + L.nb[1] * (z / bs[2]));
+__device__ __forceinline__ int block_of(const LevelDev &L, int x, int y, int z, const BlockShape &S) {
+  return (x >> S.lg[0]) + L.nb[0] * ((y >> S.lg[1]) + L.nb[1] * (z >> S.lg[2]));
+}
+
+// Level descriptor and cell coordinates of thread t of global block gb.
+__device__ __forceinline__ const LevelDev &blk_cell(const Ctx &C, const BlockShape &S, int gb, int t, int &x, int &y,
+                                                    int &z) {
+  const int4 bi = __ldg(C.blk_info + gb);
+  x = (bi.y << S.lg[0]) + (t & (S.bs[0] - 1));
+  y = (bi.z << S.lg[1]) + ((t >> S.lg[0]) & (S.bs[1] - 1));
+  z = (bi.w << S.lg[2]) + (t >> (S.lg[0] + S.lg[1]));
+  return C.lds[bi.x];
 }
 
 // Wrap a coordinate on a periodic axis; returns false if it leaves through a wall.

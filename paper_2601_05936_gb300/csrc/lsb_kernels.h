@@ -18,9 +18,12 @@ cudaError_t run_init(int Q, int st, Launch L, Ctx C, BlockShape S, const int *li
 cudaError_t run_collide_stream(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n);
 cudaError_t run_interface_bc(int Q, int st, Launch L, Ctx C, int glevel);
 cudaError_t run_restrict(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, int all_cells);
-cudaError_t run_ghost(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, float theta);
 cudaError_t run_prolong(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n);
 cudaError_t run_level_tags(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n);
+cudaError_t run_collect(Launch L, Ctx C, BlockShape S, const int *list, int n, int bits, int2 *out, int *count,
+                        int cap);
+cudaError_t run_restrict_cells(int Q, int st, Launch L, Ctx C, const int2 *cells, int n);
+cudaError_t run_ghost_cells(int Q, int st, Launch L, Ctx C, const int2 *cells, int n, float theta);
 cudaError_t run_observables(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, double *out,
                             int stride);
 cudaError_t run_export(int Q, int st, Launch L, Ctx C, int ld, int field, float *dst);

@@ -81,14 +81,14 @@ __global__ void k_init(Ctx C, BlockShape S, const int *list, int nlist) {
   using LT = Lat<Q>;
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     int gb = list[w];
-    const LevelDev &L = C.lds[C.blk_ld[gb]];
     int x, y, z;
-    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     long long c = cidx(L, x, y, z);
     float xc[3] = {(x + 0.5f) * L.scale, (y + 0.5f) * L.scale, (z + 0.5f) * L.scale};
     float drho = 0.f;
     for (int a = 0; a < LT::D; ++a) drho -= L.grav[a] * (xc[a] - L.x_ref[a]) / CS2;
+    if (C.tag[L.cell_off + c] & TAG_GAS) drho += L.p_gas0 / (L.rho_phys[1] * CS2);
     T *A = fA<T, Q>(C, L);
     float u0[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -97,37 +97,48 @@ __global__ void k_init(Ctx C, BlockShape S, const int *list, int nlist) {
 }
 
 // ------------------------------------------------------------------ collide + stream
+#ifndef LSB_CS_MINB
+#define LSB_CS_MINB 2  // CTAs of 512 threads per SM the register budget is sized for
+#endif
+
 // One CTA per block of the work list, one thread per cell.  Leaf cells and
 // the covered cells a leaf streams from (TAG_RLAYER) collide and push.  On the
 // finest level, band blocks also write the pre-collision moments and strain
 // rate (input of the interface condition and the level-set velocity), and a
 // push across the interface is parked in the link buffer for the post-pass.
+// The neighbour offsets along each axis (-1, +1: plain, wrapped on periodic
+// axes, or a wall) are formed once per cell, so every population's
+// destination is one add and boundary cells take no divergent slow path.
 template <int Q, typename T>
-__global__ void __launch_bounds__(512) k_collide_stream(Ctx C, BlockShape S, const int *__restrict__ list,
-                                                        int nlist) {
+__global__ void __launch_bounds__(512, LSB_CS_MINB) k_collide_stream(Ctx C, BlockShape S,
+                                                                     const int *__restrict__ list, int nlist) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
-    const int gb = list[w];
-    const LevelDev &L = C.lds[C.blk_ld[gb]];
-    int x, y, z;
-    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
-    if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
-    const long long c = cidx(L, x, y, z);
+    const int gb = __ldg(list + w);
+    const int4 bi = __ldg(C.blk_info + gb);
+    const LevelDev &L = C.lds[bi.x];
+    const int t = threadIdx.x;
+    const int x = (bi.y << S.lg[0]) + (t & (S.bs[0] - 1));
+    const int y = (bi.z << S.lg[1]) + ((t >> S.lg[0]) & (S.bs[1] - 1));
+    const int z = (bi.w << S.lg[2]) + (t >> (S.lg[0] + S.lg[1]));
+    const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
+    if (x >= n0 || y >= n1 || z >= n2) continue;
+    const unsigned p0 = (unsigned)L.p[0], p01 = (unsigned)(L.p[0] * L.p[1]);
+    const unsigned c = x + p0 * y + p01 * z;
     const uint8_t tg = C.tag[L.cell_off + c];
     if (!(tg & (TAG_LEAF | TAG_RLAYER))) continue;
-    const long long N = L.ncell;
-    const T *A = fA<T, Q>(C, L);
-    T *B = fB<T, Q>(C, L);
+    const unsigned N = (unsigned)L.ncell;
+    const T *__restrict__ A = fA<T, Q>(C, L);
+    T *__restrict__ B = fB<T, Q>(C, L);
     float f[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = Store<T>::ld(A + i * N + c, C.fp16_inv);
+    for (int i = 0; i < Q; ++i) f[i] = Store<T>::ld(A + (i * N + c), C.fp16_inv);
     const int ph = tg & TAG_GAS;
     const float acc[3] = {L.acc[ph][0], L.acc[ph][1], L.acc[ph][2]};
     float drho, u[3], Sm[6];
     const bool fine = L.finest != 0;
-    const bool want_macro = fine && (C.bflag[gb] & BF_BAND);
-    if (want_macro) {
+    if (fine && (C.bflag[gb] & BF_BAND)) {
       lb_collide<Q, true>(f, L.omega[ph], acc, drho, u, Sm);
       const long long fc = L.fine_off + c;
       const long long NF = C.nfine;
@@ -143,42 +154,46 @@ __global__ void __launch_bounds__(512) k_collide_stream(Ctx C, BlockShape S, con
     } else {
       lb_collide<Q, false>(f, L.omega[ph], acc, drho, u, Sm);
     }
+    // per-axis neighbour offsets and wall flags
+    const bool wxm = x == 0 && !L.per[0], wxp = x == n0 - 1 && !L.per[0];
+    const bool wym = y == 0 && !L.per[1], wyp = y == n1 - 1 && !L.per[1];
+    const bool wzm = D == 3 && z == 0 && !L.per[2], wzp = D == 3 && z == n2 - 1 && !L.per[2];
+    const int dxm = x > 0 ? -1 : n0 - 1, dxp = x < n0 - 1 ? 1 : 1 - n0;
+    const int dym = y > 0 ? -(int)p0 : (n1 - 1) * (int)p0, dyp = y < n1 - 1 ? (int)p0 : (1 - n1) * (int)p0;
+    const int dzm = z > 0 ? -(int)p01 : (n2 - 1) * (int)p01, dzp = z < n2 - 1 ? (int)p01 : (1 - n2) * (int)p01;
     uint32_t cm = 0;
     int cb = 0;
     if (fine && (tg & TAG_IFACE)) {
       cm = C.cmask[L.fine_off + c];
       cb = C.cbase[L.fine_off + c];
     }
-    Store<T>::st(B + LT::REST * N + c, f[LT::REST], C.fp16_scale);
+    Store<T>::st(B + (LT::REST * N + c), f[LT::REST], C.fp16_scale);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if (i == LT::REST) continue;
+      const int cxi = LT::cx(i), cyi = LT::cy(i), czi = LT::cz(i);
       const int k = LT::opp(i);
       if (cm & (1u << k)) {  // x + c_i lies across the interface: park for the post-pass
-        long long li = cb + __popc(cm & ((1u << k) - 1u));
+        const long long li = cb + __popc(cm & ((1u << k) - 1u));
         if (li < C.link_cap) {
           C.linkbuf[2 * li] = f[i];
           C.linkbuf[2 * li + 1] = f[k];
         }
         continue;
       }
-      int tx = x + LT::cx(i), ty = y + LT::cy(i), tz = z + LT::cz(i);
-      bool in = wrap(L, 0, tx) && wrap(L, 1, ty);
-      int face = -1;
-      if (!(0 <= x + LT::cx(i) && x + LT::cx(i) < L.n[0]) && !L.per[0]) face = LT::cx(i) < 0 ? 0 : 1;
-      else if (!(0 <= y + LT::cy(i) && y + LT::cy(i) < L.n[1]) && !L.per[1]) face = LT::cy(i) < 0 ? 2 : 3;
-      if (D == 3) {
-        bool inz = wrap(L, 2, tz);
-        if (face < 0 && !inz) face = LT::cz(i) < 0 ? 4 : 5;
-        in = in && inz;
-      }
-      if (in) {
-        Store<T>::st(B + i * N + cidx(L, tx, ty, tz), f[i], C.fp16_scale);
+      const bool wx = (cxi < 0 && wxm) || (cxi > 0 && wxp);
+      const bool wy = (cyi < 0 && wym) || (cyi > 0 && wyp);
+      const bool wz = (czi < 0 && wzm) || (czi > 0 && wzp);
+      if (!(wx || wy || wz)) {
+        const int off = (cxi < 0 ? dxm : (cxi > 0 ? dxp : 0)) + (cyi < 0 ? dym : (cyi > 0 ? dyp : 0)) +
+                        (czi < 0 ? dzm : (czi > 0 ? dzp : 0));
+        Store<T>::st(B + (i * N + (unsigned)((int)c + off)), f[i], C.fp16_scale);
       } else {
         // half-way bounce-back with the moving-wall term, i pointing at the wall
+        const int face = wx ? (cxi < 0 ? 0 : 1) : (wy ? (cyi < 0 ? 2 : 3) : (czi < 0 ? 4 : 5));
         const float *uw = L.wall_u[face];
-        float du = LT::cx(i) * uw[0] + LT::cy(i) * uw[1] + LT::cz(i) * uw[2];
-        Store<T>::st(B + k * N + c, f[i] - 6.0f * LT::w(i) * du, C.fp16_scale);
+        const float du = cxi * uw[0] + cyi * uw[1] + czi * uw[2];
+        Store<T>::st(B + (k * N + c), f[i] - 6.0f * LT::w(i) * du, C.fp16_scale);
       }
     }
   }
@@ -321,9 +336,8 @@ __global__ void k_restrict(Ctx C, BlockShape S, const int *list, int nlist, int 
   constexpr int D = LT::D;
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     int gb = list[w];
-    const LevelDev &L = C.lds[C.blk_ld[gb]];
     int x, y, z;
-    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     long long c = cidx(L, x, y, z);
     uint8_t tg = C.tag[L.cell_off + c];
@@ -406,42 +420,6 @@ __device__ __forceinline__ void interp_coarse(const Ctx &C, const LevelDev &Lc, 
   }
 }
 
-// Ghost ring of level F (TAG_GHOST cells): coarse interpolation at time weight
-// theta, f^neq scaled by tau_f / (2 tau_c), fine-level collision, pushed into
-// the fine leaves that stream from it.
-template <int Q, typename T>
-__global__ void k_ghost(Ctx C, BlockShape S, const int *list, int nlist, float theta) {
-  using LT = Lat<Q>;
-  constexpr int D = LT::D;
-  for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
-    const int gb = list[w];
-    const LevelDev &F = C.lds[C.blk_ld[gb]];
-    int x, y, z;
-    block_cell(F, gb - F.block_off, threadIdx.x, S.bs, x, y, z);
-    if (x >= F.n[0] || y >= F.n[1] || z >= F.n[2]) continue;
-    const long long c = cidx(F, x, y, z);
-    if (!(C.tag[F.cell_off + c] & TAG_GHOST)) continue;
-    const LevelDev &Lc = C.lds[F.parent_ld];
-    float f[Q];
-    interp_coarse<Q, T>(C, Lc, x, y, z, theta, f);
-    const long long cpar = cidx(Lc, x >> 1, y >> 1, D == 3 ? (z >> 1) : 0);
-    const int ph = C.tag[Lc.cell_off + cpar] & TAG_GAS;
-    rescale_neq<Q>(f, F.tau[ph] / (2.0f * Lc.tau[ph]));
-    float drho, u[3], Sm[6];
-    const float acc[3] = {F.acc[ph][0], F.acc[ph][1], F.acc[ph][2]};
-    lb_collide<Q, false>(f, F.omega[ph], acc, drho, u, Sm);
-    T *Bf = fB<T, Q>(C, F);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if (i == LT::REST) continue;
-      int tx = x + LT::cx(i), ty = y + LT::cy(i), tz = z + LT::cz(i);
-      if (!(wrap(F, 0, tx) && wrap(F, 1, ty) && (D == 2 || wrap(F, 2, tz)))) continue;
-      const long long ct = cidx(F, tx, ty, tz);
-      if (C.tag[F.cell_off + ct] & TAG_LEAF) Store<T>::st(Bf + i * F.ncell + ct, f[i], C.fp16_scale);
-    }
-  }
-}
-
 // Regrid: fill every cell of the listed (newly active) fine blocks from the
 // coarse level (interpolation + f^neq scaling, no collision).  The coarse
 // TAG_LEAF must mark the cells that hold valid data (old or new leaves).
@@ -451,9 +429,8 @@ __global__ void k_prolong(Ctx C, BlockShape S, const int *list, int nlist) {
   constexpr int D = LT::D;
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     const int gb = list[w];
-    const LevelDev &F = C.lds[C.blk_ld[gb]];
     int x, y, z;
-    block_cell(F, gb - F.block_off, threadIdx.x, S.bs, x, y, z);
+    const LevelDev &F = blk_cell(C, S, gb, threadIdx.x, x, y, z);
     if (x >= F.n[0] || y >= F.n[1] || z >= F.n[2]) continue;
     const long long c = cidx(F, x, y, z);
     const LevelDev &Lc = C.lds[F.parent_ld];
@@ -479,9 +456,8 @@ __global__ void k_level_tags(Ctx C, BlockShape S, const int *list, int nlist) {
   constexpr int D = LT::D;
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     const int gb = list[w];
-    const LevelDev &L = C.lds[C.blk_ld[gb]];
     int x, y, z;
-    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long c = cidx(L, x, y, z);
     const LevelDev &Fn = C.lds[L.fine_ld];
@@ -494,7 +470,7 @@ __global__ void k_level_tags(Ctx C, BlockShape S, const int *list, int nlist) {
       if (i == LT::REST) continue;
       int tx = x + LT::cx(i), ty = y + LT::cy(i), tz = z + LT::cz(i);
       if (!(wrap(L, 0, tx) && wrap(L, 1, ty) && (D == 2 || wrap(L, 2, tz)))) continue;
-      if (C.bstat[L.block_off + block_of(L, tx, ty, tz, S.bs)] == BLK_LEAF) near_leaf = true;
+      if (C.bstat[L.block_off + block_of(L, tx, ty, tz, S)] == BLK_LEAF) near_leaf = true;
     }
     if (st == BLK_LEAF) tg |= TAG_LEAF;
     if (st == BLK_REFINED && near_leaf) tg |= TAG_RLAYER;
@@ -513,9 +489,8 @@ __global__ void k_observables(Ctx C, BlockShape S, const int *list, int nlist, d
   constexpr int D = LT::D;
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     const int gb = list[w];
-    const LevelDev &L = C.lds[C.blk_ld[gb]];
     int x, y, z;
-    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
     double v[4 + 2 * 3];
     for (int k = 0; k < 4 + 2 * D; ++k) v[k] = 0.0;
     if (x < L.n[0] && y < L.n[1] && z < L.n[2]) {
@@ -584,6 +559,95 @@ __global__ void k_export(Ctx C, int ld, int field, float *dst) {
   }
 }
 
+// ------------------------------------------------------------------ compact cell lists
+// Append (ld, cell) of every cell of the listed blocks whose tag has any bit of
+// `bits` (ghost ring or restriction layer), so that the level transfers run
+// one thread per cell instead of one CTA per mostly idle block.
+__global__ void k_collect(Ctx C, BlockShape S, const int *list, int nlist, int bits, int2 *out, int *count,
+                          int cap) {
+  for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
+    const int gb = list[w];
+    int x, y, z;
+    const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
+    if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
+    const long long c = cidx(L, x, y, z);
+    if (!(C.tag[L.cell_off + c] & bits)) continue;
+    const int e = atomicAdd(count, 1);
+    if (e < cap) out[e] = make_int2(C.blk_ld[gb], (int)c);
+    else atomicOr(C.err, ERR_LIST_OVF);
+  }
+}
+
+// Restriction layer from a cell list (one thread per covered cell).
+template <int Q, typename T>
+__global__ void k_restrict_cells(Ctx C, const int2 *cells, int n) {
+  constexpr int D = Lat<Q>::D;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 it = cells[e];
+    const LevelDev &L = C.lds[it.x];
+    const long long c = it.y;
+    const int x = (int)(c % L.p[0]);
+    const int y = (int)((c / L.p[0]) % L.p[1]);
+    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    const LevelDev &F = C.lds[L.child_ld];
+    const T *Af = fA<T, Q>(C, F);
+    float f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = 0.f;
+    const int nz = (D == 3) ? 2 : 1;
+    for (int sz = 0; sz < nz; ++sz)
+      for (int sy = 0; sy < 2; ++sy)
+        for (int sx = 0; sx < 2; ++sx) {
+          const long long cf = cidx(F, 2 * x + sx, 2 * y + sy, D == 3 ? 2 * z + sz : 0);
+#pragma unroll
+          for (int i = 0; i < Q; ++i) f[i] += Store<T>::ld(Af + i * F.ncell + cf, C.fp16_inv);
+        }
+    const float inv = 1.0f / (float)(4 * nz);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] *= inv;
+    const int ph = C.tag[L.cell_off + c] & TAG_GAS;
+    rescale_neq<Q>(f, 2.0f * L.tau[ph] / F.tau[ph]);
+    T *Ac = fA<T, Q>(C, L);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Store<T>::st(Ac + i * L.ncell + c, f[i], C.fp16_scale);
+  }
+}
+
+// Ghost ring of level F (TAG_GHOST cells), one thread per listed cell: coarse
+// interpolation at time weight theta, f^neq scaled by tau_f / (2 tau_c), a
+// fine-level collision, pushed into the fine leaves that stream from it.
+template <int Q, typename T>
+__global__ void k_ghost_cells(Ctx C, const int2 *cells, int n, float theta) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 it = cells[e];
+    const LevelDev &F = C.lds[it.x];
+    const long long c = it.y;
+    const int x = (int)(c % F.p[0]);
+    const int y = (int)((c / F.p[0]) % F.p[1]);
+    const int z = (int)(c / ((long long)F.p[0] * F.p[1]));
+    const LevelDev &Lc = C.lds[F.parent_ld];
+    float f[Q];
+    interp_coarse<Q, T>(C, Lc, x, y, z, theta, f);
+    const long long cpar = cidx(Lc, x >> 1, y >> 1, D == 3 ? (z >> 1) : 0);
+    const int ph = C.tag[Lc.cell_off + cpar] & TAG_GAS;
+    rescale_neq<Q>(f, F.tau[ph] / (2.0f * Lc.tau[ph]));
+    float drho, u[3], Sm[6];
+    const float acc[3] = {F.acc[ph][0], F.acc[ph][1], F.acc[ph][2]};
+    lb_collide<Q, false>(f, F.omega[ph], acc, drho, u, Sm);
+    T *Bf = fB<T, Q>(C, F);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (i == LT::REST) continue;
+      int tx = x + LT::cx(i), ty = y + LT::cy(i), tz = z + LT::cz(i);
+      if (!(wrap(F, 0, tx) && wrap(F, 1, ty) && (D == 2 || wrap(F, 2, tz)))) continue;
+      const long long ct = cidx(F, tx, ty, tz);
+      if (C.tag[F.cell_off + ct] & TAG_LEAF) Store<T>::st(Bf + i * F.ncell + ct, f[i], C.fp16_scale);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ host launchers
 #define LSB_QT(Q, st, CALL)                                      \
   do {                                                           \
@@ -611,9 +675,6 @@ cudaError_t run_interface_bc(int Q, int st, Launch L, Ctx C, int glevel) {
 cudaError_t run_restrict(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, int all_cells) {
   LSB_QT(Q, st, (LK(k_restrict)(C, S, list, n, all_cells)));
 }
-cudaError_t run_ghost(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, float theta) {
-  LSB_QT(Q, st, (LK(k_ghost)(C, S, list, n, theta)));
-}
 cudaError_t run_prolong(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n) {
   LSB_QT(Q, st, (LK(k_prolong)(C, S, list, n)));
 }
@@ -623,6 +684,17 @@ cudaError_t run_observables(int Q, int st, Launch L, Ctx C, BlockShape S, const 
 }
 cudaError_t run_export(int Q, int st, Launch L, Ctx C, int ld, int field, float *dst) {
   LSB_QT(Q, st, (LK(k_export)(C, ld, field, dst)));
+}
+cudaError_t run_collect(Launch L, Ctx C, BlockShape S, const int *list, int n, int bits, int2 *out, int *count,
+                        int cap) {
+  k_collect<<<L.grid, L.block, 0, L.stream>>>(C, S, list, n, bits, out, count, cap);
+  return cudaGetLastError();
+}
+cudaError_t run_restrict_cells(int Q, int st, Launch L, Ctx C, const int2 *cells, int n) {
+  LSB_QT(Q, st, (LK(k_restrict_cells)(C, cells, n)));
+}
+cudaError_t run_ghost_cells(int Q, int st, Launch L, Ctx C, const int2 *cells, int n, float theta) {
+  LSB_QT(Q, st, (LK(k_ghost_cells)(C, cells, n, theta)));
 }
 cudaError_t run_level_tags(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n) {
   if (Q == 9) k_level_tags<9><<<L.grid, L.block, 0, L.stream>>>(C, S, list, n);

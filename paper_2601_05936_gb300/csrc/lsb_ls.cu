@@ -14,7 +14,7 @@
 namespace lsb {
 
 __device__ __forceinline__ bool in_band(const Ctx &C, const LevelDev &L, const BlockShape &S, int x, int y, int z) {
-  return (C.bflag[L.block_off + block_of(L, x, y, z, S.bs)] & BF_BAND) != 0;
+  return (C.bflag[L.block_off + block_of(L, x, y, z, S)] & BF_BAND) != 0;
 }
 
 // ------------------------------------------------------------------ classification
@@ -24,10 +24,9 @@ template <int Q>
 __global__ void k_classify_phase(Ctx C, BlockShape S, const int *list, int nlist, int glevel, int init) {
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     const int gb = list[w];
-    const LevelDev &L = C.lds[C.blk_ld[gb]];
     if (threadIdx.x == 0) C.bflag[gb] = 0;
     int x, y, z;
-    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long c = cidx(L, x, y, z);
     const uint8_t tg = C.tag[L.cell_off + c];
@@ -54,9 +53,8 @@ __global__ void k_classify_links(Ctx C, BlockShape S, const int *list, int nlist
   constexpr int D = LT::D;
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     const int gb = list[w];
-    const LevelDev &L = C.lds[C.blk_ld[gb]];
     int x, y, z;
-    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
     bool has = false;
     if (x < L.n[0] && y < L.n[1] && z < L.n[2]) {
       const long long c = cidx(L, x, y, z);
@@ -246,9 +244,8 @@ __global__ void k_ext_iter(Ctx C, BlockShape S, int glevel, const float *uin, fl
   const int *lst = C.band_list + (long long)glevel * C.band_cap;
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
     const int gb = lst[w];
-    const LevelDev &L = C.lds[C.blk_ld[gb]];
     int x, y, z;
-    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long fo = L.fine_off, NF = C.nfine;
     const long long c = cidx(L, x, y, z);
@@ -323,9 +320,8 @@ __global__ void k_adv_stage(Ctx C, BlockShape S, int glevel, int stage) {
   const float *pin = stage == 1 ? C.phi : (stage == 2 ? C.p1 : C.p2);
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
     const int gb = lst[w];
-    const LevelDev &L = C.lds[C.blk_ld[gb]];
     int x, y, z;
-    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long fc = L.fine_off + cidx(L, x, y, z);
     float rhs = 0.f;
@@ -352,9 +348,8 @@ __global__ void k_reinit_prep(Ctx C, BlockShape S, int glevel) {
   const int *lst = C.band_list + (long long)glevel * C.band_cap;
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
     const int gb = lst[w];
-    const LevelDev &L = C.lds[C.blk_ld[gb]];
     int x, y, z;
-    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long fc = L.fine_off + cidx(L, x, y, z);
     const float p = C.phi[fc];
@@ -396,9 +391,8 @@ __global__ void k_reinit_stage(Ctx C, BlockShape S, int glevel, int stage) {
   const float *pin = stage == 1 ? C.phi : (stage == 2 ? C.p1 : C.p2);
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
     const int gb = lst[w];
-    const LevelDev &L = C.lds[C.blk_ld[gb]];
     int x, y, z;
-    block_cell(L, gb - L.block_off, threadIdx.x, S.bs, x, y, z);
+    const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long fc = L.fine_off + cidx(L, x, y, z);
     if (C.frozen[fc]) continue;

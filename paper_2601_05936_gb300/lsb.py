@@ -12,7 +12,7 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_lib", "liblsb.so")
+LIB_PATH = os.environ.get("LSB_LIBRARY") or os.path.join(HERE, "_lib", "liblsb.so")
 
 D2Q9, D3Q19 = 0, 1
 PERIODIC, WALL = 0, 1
@@ -32,6 +32,7 @@ class GridDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double * 2), ("nu", ctypes.c_double * 2), ("body_force", ctypes.c_double * 3),
                 ("gravity", ctypes.c_double * 3), ("sigma", ctypes.c_double), ("x_ref", ctypes.c_double * 3),
+                ("p_gas0", ctypes.c_double),
                 ("n_ext", ctypes.c_int), ("dtau_ext", ctypes.c_double), ("reinit_every", ctypes.c_int),
                 ("n_reinit", ctypes.c_int), ("dtau_reinit", ctypes.c_double), ("refine_dist", ctypes.c_double * 4),
                 ("sensor", ctypes.c_int), ("regrid_every", ctypes.c_int), ("ls_active", ctypes.c_int)]
@@ -64,7 +65,7 @@ def load():
     lib.lsb_field_bytes.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.lsb_field_bytes.restype = ctypes.c_size_t
     lib.lsb_observables.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]
-    lib.lsb_cell_updates.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    lib.lsb_cell_updates.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.lsb_backward.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
     lib.lsb_sync.argtypes = [vp]
     lib.lsb_kernel_launches.argtypes = [vp]
@@ -75,7 +76,14 @@ def load():
     lib.lsb_destroy.restype = None
     lib.lsb_lattice_table.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
                                       ctypes.POINTER(ctypes.c_int)]
-    for name in ("lsb_create_grid", "lsb_set_params", "lsb_step", "lsb_refine", "lsb_get_fields",
+    lib.lsb_profile.argtypes = [vp, ctypes.c_int]
+    lib.lsb_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]
+    lib.lsb_kernel_name.argtypes = [ctypes.c_int]
+    lib.lsb_kernel_name.restype = ctypes.c_char_p
+    lib.lsb_kernel_count.argtypes = []
+    lib.lsb_kernel_count.restype = ctypes.c_int
+    for name in ("lsb_profile", "lsb_profile_read", "lsb_create_grid", "lsb_set_params", "lsb_step", "lsb_refine", "lsb_get_fields",
                  "lsb_observables", "lsb_cell_updates", "lsb_backward", "lsb_sync"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -125,6 +133,7 @@ def _params(case, D):
         for a in range(3):
             getattr(p, name)[a] = float(v[a]) if a < D else 0.0
     p.sigma = float(case.get("sigma", 0.0))
+    p.p_gas0 = float(case.get("p_gas0", 0.0))
     p.n_ext = int(case.get("n_ext", 8))
     p.dtau_ext = float(case.get("dtau_ext", 0.5))
     p.reinit_every = int(case.get("reinit_every", 1))
@@ -239,10 +248,25 @@ class Grid:
         return [dict(mass=r[0:2], volume=r[2], leaf_cells=r[3], centroid=r[4:4 + D], velocity=r[4 + D:4 + 2 * D])
                 for r in a]
 
-    def cell_updates(self):
+    def cell_updates(self, total=False):
+        """Leaf cell updates per coarse step now, or (total=True) done since creation."""
         v = ctypes.c_double()
-        self._check(self.lib.lsb_cell_updates(self.h, ctypes.byref(v)))
-        return v.value
+        t = ctypes.c_double()
+        self._check(self.lib.lsb_cell_updates(self.h, ctypes.byref(v), ctypes.byref(t)))
+        return t.value if total else v.value
+
+    def profile(self, mode):
+        """0 off, 1 time collide-and-stream launches, 2 time every launch."""
+        self._check(self.lib.lsb_profile(self.h, int(mode)))
+
+    def profile_read(self):
+        """{kernel name: (ms, launches, algorithmic bytes)} since the last profile/read."""
+        n = self.lib.lsb_kernel_count()
+        ms = (ctypes.c_double * n)()
+        by = (ctypes.c_double * n)()
+        la = (ctypes.c_uint64 * n)()
+        self._check(self.lib.lsb_profile_read(self.h, ms, by, la, n))
+        return {self.lib.lsb_kernel_name(k).decode(): (ms[k], int(la[k]), by[k]) for k in range(n) if la[k]}
 
     def kernel_launches(self):
         return int(self.lib.lsb_kernel_launches(self.h))

@@ -38,5 +38,6 @@ def compare_levels(g, s, case_idx=0):
         m = leaf_o
         out.append(dict(level=l, leaf_equal=bool(np.array_equal(leaf_o, leaf_g)),
                         drho=rel_l2(rho_g[m] - 1, rho_o[m] - 1), u=rel_l2(u_g[:, m], u_o[:, m]),
+                        drho_abs=float(np.abs(rho_g[m] - rho_o[m]).max()) if m.any() else 0.0,
                         umax_abs=float(np.abs(u_g[:, m] - u_o[:, m]).max()) if m.any() else 0.0))
     return out
