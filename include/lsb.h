@@ -143,6 +143,29 @@ lsb_status lsb_refine(lsb_grid *g);
 lsb_status lsb_get_fields(lsb_grid *g, int case_idx, int field, int level, void *dst,
                           size_t dst_bytes, int dst_on_host);
 
+/*
+ * Allocation-free variant of lsb_get_fields for LSB_FIELD_RHO, LSB_FIELD_U and
+ * LSB_FIELD_F (the paper has no counterpart: this is a service of the library).
+ * lsb_get_fields stages these fields in a temporary cudaMalloc buffer; this
+ * entry point stages them in a fixed 16 MiB array that the library reserves
+ * on every GPU it is loaded on, held until the process exits.  It is meant
+ * for callers that cannot allocate device memory at the point of the call:
+ * code whose device memory is entirely owned by another allocator (such as a
+ * framework's caching allocator), real-time loops that cannot afford an
+ * allocation's latency or its implicit synchronisation, or callbacks in
+ * which allocation is not permitted.  It calls no cudaMalloc or cudaFree.
+ * The first call on a device resolves the array's device address (with that
+ * device current); make that first call before any stream capture.
+ * Fields larger than 16 MiB are rejected with LSB_EINVAL.  Every call shares
+ * the one array: calls whose work overlaps on the GPU (two handles on
+ * different streams, or two host threads) race and must be serialised by the
+ * caller.  Each call writes the whole staged range before copying it out, so
+ * nothing carries over from an earlier call.  Arguments and result as for
+ * lsb_get_fields; synchronises the handle's stream.
+ */
+lsb_status lsb_get_fields_noalloc(lsb_grid *g, int case_idx, int field, int level, void *dst,
+                                  size_t dst_bytes, int dst_on_host);
+
 /* Bytes lsb_get_fields writes for (case, field, level); 0 for invalid input. */
 size_t lsb_field_bytes(const lsb_grid *g, int case_idx, int field, int level);
 

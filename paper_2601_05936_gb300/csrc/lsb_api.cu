@@ -958,6 +958,27 @@ lsb_status lsb_backward(lsb_grid *g, const double *, double *, float *) {
   return fail(g, LSB_ESTATE, "the adjoint is not available in this build");
 }
 
+lsb_status lsb_get_fields_noalloc(lsb_grid *g, int case_idx, int field, int level, void *dst, size_t dst_bytes,
+                                  int dst_on_host) {
+  if (!g || !dst) return LSB_EINVAL;
+  if (field != LSB_FIELD_RHO && field != LSB_FIELD_U && field != LSB_FIELD_F)
+    return fail(g, LSB_EINVAL, "lsb_get_fields_noalloc exports LSB_FIELD_RHO, LSB_FIELD_U and LSB_FIELD_F only");
+  const size_t need = lsb_field_bytes(g, case_idx, field, level);
+  if (need == 0) return fail(g, LSB_EINVAL, "invalid case/field/level");
+  if (dst_bytes < need) return fail(g, LSB_EINVAL, "dst too small: %zu < %zu", dst_bytes, need);
+  if (need > kNoAllocFloats * sizeof(float))
+    return fail(g, LSB_EINVAL, "field needs %zu bytes, more than the %zu-byte fixed staging array of "
+                "lsb_get_fields_noalloc; use lsb_get_fields", need, kNoAllocFloats * sizeof(float));
+  const int ld = g->cases[case_idx].ld0 + level;
+  const int fcode = field == LSB_FIELD_RHO ? 0 : (field == LSB_FIELD_U ? 1 : 4);
+  float *staged = nullptr;
+  Ctx C = make_ctx(g);
+  TRY(launched(g, run_export_noalloc(g->Q, g->storage, LN(g, 1024, 256), C, ld, fcode, &staged)));
+  CU(cudaMemcpyAsync(dst, staged, need, dst_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, g->stream));
+  CU(cudaStreamSynchronize(g->stream));
+  return lsb_sync(g);
+}
+
 uint64_t lsb_kernel_launches(const lsb_grid *g) { return g ? g->launches : 0; }
 
 const char *lsb_last_error(const lsb_grid *g) { return g ? g->err.c_str() : g_create_error.c_str(); }

@@ -8,6 +8,10 @@
 
 namespace lsb {
 
+// Size of the fixed staging array behind lsb_get_fields_noalloc (floats, 16 MiB).
+constexpr size_t kNoAllocFloats = size_t(4) << 20;
+constexpr int kMaxDevices = 64;
+
 struct Launch {
   int grid, block;
   cudaStream_t stream;
@@ -27,6 +31,8 @@ cudaError_t run_ghost_cells(int Q, int st, Launch L, Ctx C, const int2 *cells, i
 cudaError_t run_observables(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, double *out,
                             int stride);
 cudaError_t run_export(int Q, int st, Launch L, Ctx C, int ld, int field, float *dst);
+// Export into the file-scope staging array; *staged receives its device address.
+cudaError_t run_export_noalloc(int Q, int st, Launch L, Ctx C, int ld, int field, float **staged);
 
 // lsb_ls.cu: level set, classification, geometry, refill, sensor
 cudaError_t run_classify_phase(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, int glevel, int init);

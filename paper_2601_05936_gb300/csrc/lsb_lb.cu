@@ -10,6 +10,8 @@
 // the PRE-collision (post-stream) population; a step reads it once, collides in
 // registers and pushes every population to its destination once: 2*Q*sizeof(T)
 // bytes of HBM traffic per cell update.
+#include <mutex>
+
 #include "lsb_kernels.h"
 
 namespace lsb {
@@ -648,6 +650,32 @@ __global__ void k_ghost_cells(Ctx C, const int2 *cells, int n, float theta) {
   }
 }
 
+// ------------------------------------------------------------------ allocation-free export staging
+// Fixed staging area for lsb_get_fields_noalloc: a file-scope device array, so
+// callers that must not allocate device memory can still export fields.  Every
+// GPU that loads the library holds it until the process exits.  In host code
+// the name below is only a stand-in; its device address comes from
+// cudaGetSymbolAddress, resolved once per device (with that device current).
+static __device__ __align__(256) float g_export_scratch[kNoAllocFloats];
+
+cudaError_t noalloc_scratch(float **ptr) {
+  static std::mutex mu;
+  static float *addr[kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_export_scratch);
+    if (e != cudaSuccess) return e;
+    addr[dev] = static_cast<float *>(p);
+  }
+  *ptr = addr[dev];
+  return cudaSuccess;
+}
+
 // ------------------------------------------------------------------ host launchers
 #define LSB_QT(Q, st, CALL)                                      \
   do {                                                           \
@@ -683,6 +711,13 @@ cudaError_t run_observables(int Q, int st, Launch L, Ctx C, BlockShape S, const 
   LSB_QT(Q, st, (LK(k_observables)(C, S, list, n, out, stride)));
 }
 cudaError_t run_export(int Q, int st, Launch L, Ctx C, int ld, int field, float *dst) {
+  LSB_QT(Q, st, (LK(k_export)(C, ld, field, dst)));
+}
+cudaError_t run_export_noalloc(int Q, int st, Launch L, Ctx C, int ld, int field, float **staged) {
+  float *dst = nullptr;
+  cudaError_t e = noalloc_scratch(&dst);
+  if (e != cudaSuccess) return e;
+  *staged = dst;
   LSB_QT(Q, st, (LK(k_export)(C, ld, field, dst)));
 }
 cudaError_t run_collect(Launch L, Ctx C, BlockShape S, const int *list, int n, int bits, int2 *out, int *count,

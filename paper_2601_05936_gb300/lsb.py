@@ -62,6 +62,8 @@ def load():
     lib.lsb_step.argtypes = [vp, ctypes.c_int]
     lib.lsb_refine.argtypes = [vp]
     lib.lsb_get_fields.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t, ctypes.c_int]
+    lib.lsb_get_fields_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t,
+                                           ctypes.c_int]
     lib.lsb_field_bytes.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.lsb_field_bytes.restype = ctypes.c_size_t
     lib.lsb_observables.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]
@@ -83,7 +85,7 @@ def load():
     lib.lsb_kernel_name.restype = ctypes.c_char_p
     lib.lsb_kernel_count.argtypes = []
     lib.lsb_kernel_count.restype = ctypes.c_int
-    for name in ("lsb_profile", "lsb_profile_read", "lsb_create_grid", "lsb_set_params", "lsb_step", "lsb_refine", "lsb_get_fields",
+    for name in ("lsb_get_fields_noalloc", "lsb_profile", "lsb_profile_read", "lsb_create_grid", "lsb_set_params", "lsb_step", "lsb_refine", "lsb_get_fields",
                  "lsb_observables", "lsb_cell_updates", "lsb_backward", "lsb_sync"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
