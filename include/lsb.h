@@ -130,6 +130,14 @@ lsb_status lsb_set_params(lsb_grid *g, int case_idx, const lsb_params *params);
  * of that case), Sec. 2 method.  Asynchronous on the handle's stream. */
 lsb_status lsb_step(lsb_grid *g, int n);
 
+/* Replay steps from CUDA graphs (enable = 1) instead of launching each kernel.
+ * Two coarse steps are captured at a time (one graph per starting buffer
+ * parity), re-captured after every regrid; steps next to a regrid, steps while
+ * kernel timing is on, and handles whose reinitialisation period is above 1
+ * run eagerly.  Needs the handle to use a non-default stream (LSB_EINVAL
+ * otherwise).  Results are identical to eager stepping. */
+lsb_status lsb_use_graphs(lsb_grid *g, int enable);
+
 /* Run the refinement sensor and regrid every case now (Sec. 2.6). */
 lsb_status lsb_refine(lsb_grid *g);
 

@@ -6,6 +6,7 @@
 // sensor and regrid (Sec. 2.6) with host-side grading, and exports fields.
 // All cases of a handle (an ensemble) advance together: every launch covers
 // the blocks of all cases that own the level it works on.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -106,6 +107,13 @@ struct lsb_grid {
   std::vector<ProfRec> prof;
   double leaf_cells[MAXL] = {0, 0, 0, 0};
   double updates_done = 0;
+  // CUDA graphs of two coarse steps, one per starting parity of level 0
+  int use_graphs = 0;
+  // TMA tensor maps of every level's population buffers (2 per level descriptor)
+  CUtensorMap *d_tmaps = nullptr;
+  int tma_grid = 0;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  uint64_t gnodes[2] = {0, 0};
 };
 
 namespace {
@@ -466,7 +474,15 @@ lsb_status advance(lsb_grid *g, int l) {
   const int Q = g->Q, st = g->storage;
   const CellList &rc = g->rl_cells[l];
   RUN(2, 0, rc.n, 128, run_restrict_cells, Q, st, LN(g, (rc.n + 127) / 128, 128), C, (const int2 *)rc.d, rc.n);
-  RUN(0, 2.0 * g->Q * (g->storage == LSB_FP32 ? 4 : 2) * g->leaf_cells[l], g->cs[l].n, nt, run_collide_stream, Q, st, LN(g, g->cs[l].n, nt), C, S, (const int *)g->cs[l].d, g->cs[l].n);
+  const double cs_bytes = 2.0 * g->Q * (g->storage == LSB_FP32 ? 4 : 2) * g->leaf_cells[l];
+  if (g->d_tmaps) {
+    const int grid = std::min(g->cs[l].n, g->tma_grid);
+    RUN(0, cs_bytes, g->cs[l].n, nt, run_collide_stream_tma, Q, st, LN(g, grid, nt), C, S, (const int *)g->cs[l].d,
+        g->cs[l].n, (const CUtensorMap *)g->d_tmaps);
+  } else {
+    RUN(0, cs_bytes, g->cs[l].n, nt, run_collide_stream, Q, st, LN(g, g->cs[l].n, nt), C, S, (const int *)g->cs[l].d,
+        g->cs[l].n);
+  }
   if (has_finest(g, l)) {
     RUN(1, 0, 1, 128, run_interface_bc, Q, st, LN(g, DYN_GRID, 128), C, l);
     if (ls_active_any(g, l)) TRY(levelset(g, l));
@@ -539,6 +555,129 @@ void fill_physics(lsb_grid *g, LevelDev &L, const CaseHost &ch) {
   L.ls_active = p.ls_active;
   L.p_gas0 = (float)p.p_gas0;
   (void)g;
+}
+
+// Tensor maps for the TMA-staged collide kernel: per level descriptor and
+// buffer, a (x, y, [z,] q) view of that level's populations with a box of one
+// block x all Q populations.  Returns false (and leaves d_tmaps NULL) when the
+// driver entry point is unavailable; the plain kernel is used then.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+lsb_status build_tensor_maps(lsb_grid *g) {
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return LSB_OK;
+  }
+  EncodeTiledFn encode = reinterpret_cast<EncodeTiledFn>(fn);
+  const size_t es = g->storage == LSB_FP32 ? 4 : 2;
+  // A box row must be whole 16-byte units: then every block's x origin is 16-byte aligned too.
+  if ((g->bs[0] * es) % 16 != 0 || g->bs[0] > 256 || g->bs[1] > 256 || g->bs[2] > 256) return LSB_OK;
+  const CUtensorMapDataType dt =
+      g->storage == LSB_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  std::vector<CUtensorMap> maps(2 * g->lds.size());
+  for (size_t ld = 0; ld < g->lds.size(); ++ld) {
+    const LevelDev &L = g->lds[ld];
+    for (int b = 0; b < 2; ++b) {
+      char *base = static_cast<char *>(g->d_buf[b]) + (size_t)L.cell_off * g->Q * es;
+      cuuint64_t dims[4], strides[3];
+      cuuint32_t box[4], estr[4] = {1, 1, 1, 1};
+      cuuint32_t rank;
+      if (g->D == 3) {
+        rank = 4;
+        dims[0] = L.p[0]; dims[1] = L.p[1]; dims[2] = L.p[2]; dims[3] = g->Q;
+        strides[0] = (cuuint64_t)L.p[0] * es;
+        strides[1] = (cuuint64_t)L.p[0] * L.p[1] * es;
+        strides[2] = (cuuint64_t)L.ncell * es;
+        box[0] = g->bs[0]; box[1] = g->bs[1]; box[2] = g->bs[2]; box[3] = g->Q;
+      } else {
+        rank = 3;
+        dims[0] = L.p[0]; dims[1] = L.p[1]; dims[2] = g->Q;
+        strides[0] = (cuuint64_t)L.p[0] * es;
+        strides[1] = (cuuint64_t)L.ncell * es;
+        box[0] = g->bs[0]; box[1] = g->bs[1]; box[2] = g->Q;
+      }
+      CUresult r = encode(&maps[2 * ld + b], dt, rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return LSB_OK;  // keep the plain kernel
+    }
+  }
+  int per_sm = 0, nsm = 0, dev = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  if (prepare_collide_stream_tma(g->Q, g->storage, g->nthreads, &per_sm) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return LSB_OK;
+  }
+  TRY(dalloc(g, &g->d_tmaps, sizeof(CUtensorMap) * maps.size()));
+  CU(cudaMemcpy(g->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
+  g->tma_grid = per_sm * nsm;
+  return LSB_OK;
+}
+
+void drop_graphs(lsb_grid *g) {
+  for (int p = 0; p < 2; ++p)
+    if (g->gexec[p]) {
+      cudaGraphExecDestroy(g->gexec[p]);
+      g->gexec[p] = nullptr;
+    }
+}
+
+// Graph replay needs a non-default stream, no kernel timing, and a fixed
+// launch sequence (reinitialisation every finest step or never).
+bool graphs_usable(const lsb_grid *g) {
+  return g->use_graphs && g->stream && g->prof_mode == 0 && g->reinit_every <= 1;
+}
+
+// Two coarse steps as one CUDA graph: every level's buffer parity returns to
+// its starting value, so the captured kernel arguments stay valid until the
+// next regrid rebuilds the work lists.
+lsb_status replay_two_steps(lsb_grid *g) {
+  const int p0 = g->par[0];
+  if (!g->gexec[p0]) {
+    int par[MAXL];
+    long long fs[MAXL];
+    std::copy(g->par, g->par + MAXL, par);
+    std::copy(g->fine_steps, g->fine_steps + MAXL, fs);
+    const uint64_t l0 = g->launches;
+    CU(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    lsb_status s = advance(g, 0);
+    if (s == LSB_OK) s = advance(g, 0);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
+    std::copy(par, par + MAXL, g->par);
+    std::copy(fs, fs + MAXL, g->fine_steps);
+    g->gnodes[p0] = g->launches - l0;
+    g->launches = l0;
+    if (s != LSB_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    if (e != cudaSuccess) return fail(g, LSB_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&g->gexec[p0], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(g, LSB_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  CU(cudaGraphLaunch(g->gexec[p0], g->stream));
+  g->launches += g->gnodes[p0];
+  for (int l = 0; l < MAXL; ++l) {
+    // level l advances 2^(l+1) times in two coarse steps; its parity flips that often
+    const long long adv = 2LL << l;
+    if (l < g->Lmax) {
+      if (adv & 1) g->par[l] ^= 1;
+      if (has_finest(g, l)) g->fine_steps[l] += adv;
+    }
+  }
+  for (int k = 0; k < 2; ++k) {
+    g->updates_done += updates_per_step(g);
+    g->coarse_steps++;
+  }
+  return LSB_OK;
 }
 
 }  // namespace
@@ -732,7 +871,8 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
     pr.kind = cudaMemcpyDeviceToDevice;
     if (cuerr(cudaMemcpy3D(&pr), "phi0 copy")) { lsb_destroy(g); return LSB_ECUDA; }
   }
-  s = regrid(g, true);
+  s = build_tensor_maps(g);
+  if (s == LSB_OK) s = regrid(g, true);
   if (s) { g_create_error = g->err; lsb_destroy(g); return s; }
   *out = g;
   return LSB_OK;
@@ -764,12 +904,30 @@ lsb_status lsb_set_params(lsb_grid *g, int case_idx, const lsb_params *params) {
 
 lsb_status lsb_step(lsb_grid *g, int n) {
   if (!g || n < 0) return LSB_EINVAL;
-  for (int k = 0; k < n; ++k) {
+  int k = 0;
+  while (k < n) {
+    const bool regrid_on = g->regrid_every > 0 && g->Lmax > 1;
+    const bool regrid_soon =
+        regrid_on && ((g->coarse_steps + 1) % g->regrid_every == 0 || (g->coarse_steps + 2) % g->regrid_every == 0);
+    if (n - k >= 2 && !regrid_soon && graphs_usable(g)) {
+      TRY(replay_two_steps(g));
+      k += 2;
+      continue;
+    }
     TRY(advance(g, 0));
     g->updates_done += updates_per_step(g);
     g->coarse_steps++;
-    if (g->regrid_every > 0 && g->Lmax > 1 && g->coarse_steps % g->regrid_every == 0) TRY(regrid(g, false));
+    ++k;
+    if (regrid_on && g->coarse_steps % g->regrid_every == 0) TRY(regrid(g, false));
   }
+  return LSB_OK;
+}
+
+lsb_status lsb_use_graphs(lsb_grid *g, int enable) {
+  if (!g || (enable != 0 && enable != 1)) return LSB_EINVAL;
+  if (enable && !g->stream) return fail(g, LSB_EINVAL, "CUDA graphs need a non-default stream");
+  g->use_graphs = enable;
+  if (!enable) drop_graphs(g);
   return LSB_OK;
 }
 
@@ -786,6 +944,7 @@ lsb_status lsb_sync(lsb_grid *g) {
   g->latched |= e;
   if (g->latched & (ERR_LINK_OVF | ERR_LIST_OVF | ERR_BAND_OVF))
     return fail(g, LSB_ENOMEM, "device work list overflow (flags %d)", g->latched);
+  if (g->latched & ERR_TIMEOUT) return fail(g, LSB_ETIMEOUT, "a bounded device-side wait gave up");
   if (g->latched & ERR_NONFINITE) return fail(g, LSB_EUNSTABLE, "non-finite density or velocity");
   return LSB_OK;
 }
@@ -987,6 +1146,7 @@ void lsb_destroy(lsb_grid *g) {
   if (!g) return;
   if (g->stream) cudaStreamSynchronize(g->stream);
   else cudaDeviceSynchronize();
+  drop_graphs(g);
   for (void *p : g->allocs) cudaFree(p);
   for (ProfRec &r : g->prof) {
     cudaEventDestroy(r.a);
@@ -1165,6 +1325,7 @@ lsb_status regrid(lsb_grid *g, bool initial) {
     TRY(level_tags(g));
   }
   TRY(collect_cells(g));
+  drop_graphs(g);
   CU(cudaMemsetAsync(g->d_bflag, 0, g->nblock_total, g->stream));
   for (int l = 0; l < g->Lmax; ++l) TRY(classify(g, l, 1));
   return LSB_OK;

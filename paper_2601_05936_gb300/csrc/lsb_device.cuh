@@ -132,7 +132,7 @@ struct Ctx {
   float fp16_scale, fp16_inv;
 };
 
-enum : int { ERR_LINK_OVF = 1, ERR_LIST_OVF = 2, ERR_NONFINITE = 4, ERR_BAND_OVF = 8 };
+enum : int { ERR_LINK_OVF = 1, ERR_LIST_OVF = 2, ERR_NONFINITE = 4, ERR_BAND_OVF = 8, ERR_TIMEOUT = 16 };
 constexpr int NCOUNT = 4;
 
 // ---------------------------------------------------------------- storage

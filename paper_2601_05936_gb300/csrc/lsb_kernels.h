@@ -2,6 +2,7 @@
 // that defines its kernel (lsb_lb.cu, lsb_ls.cu), so the launch and the kernel
 // registration live together; (Q, storage) pick the template instance.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "lsb_device.cuh"
@@ -20,6 +21,10 @@ struct Launch {
 // lsb_lb.cu: lattice Boltzmann, interface bounce-back, level transfers
 cudaError_t run_init(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n);
 cudaError_t run_collide_stream(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n);
+cudaError_t run_collide_stream_tma(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n,
+                                   const CUtensorMap *tmaps);
+size_t tma_smem_bytes(int Q, int st, int nthreads);
+cudaError_t prepare_collide_stream_tma(int Q, int st, int nthreads, int *ctas_per_sm);
 cudaError_t run_interface_bc(int Q, int st, Launch L, Ctx C, int glevel);
 cudaError_t run_restrict(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, int all_cells);
 cudaError_t run_prolong(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n);

@@ -10,6 +10,8 @@
 // the PRE-collision (post-stream) population; a step reads it once, collides in
 // registers and pushes every population to its destination once: 2*Q*sizeof(T)
 // bytes of HBM traffic per cell update.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "lsb_kernels.h"
@@ -198,6 +200,184 @@ __global__ void __launch_bounds__(512, LSB_CS_MINB) k_collide_stream(Ctx C, Bloc
         Store<T>::st(B + (k * N + c), f[i] - 6.0f * LT::w(i) * du, C.fp16_scale);
       }
     }
+  }
+}
+
+// ------------------------------------------------------------------ collide + stream, TMA-staged
+// Same update as k_collide_stream, with the A populations of each block
+// brought into shared memory by one TMA tensor load (a box of
+// bs0 x bs1 x bs2 cells x Q populations), double buffered: while a CTA
+// collides block w, the load of its next block is in flight.  Persistent CTAs
+// walk the work list; one thread issues the loads, every thread waits on the
+// stage's mbarrier with an iteration limit (on expiry the error word gets
+// ERR_TIMEOUT and the CTA stops).
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const void *tmap, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int c0, int c1, int c2, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(smem_u32(dst)),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+constexpr unsigned kWaitLimit = 1u << 24;
+
+template <typename T>
+__device__ __forceinline__ float stage_ld(const T *p, float inv);
+template <>
+__device__ __forceinline__ float stage_ld<float>(const float *p, float) {
+  return *p;
+}
+template <>
+__device__ __forceinline__ float stage_ld<__half>(const __half *p, float inv) {
+  return __half2float(*p) * inv;
+}
+
+template <int Q, typename T>
+__global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape S, const int *__restrict__ list,
+                                                               int nlist, const CUtensorMap *__restrict__ tmaps) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  const int nt = blockDim.x;
+  const unsigned stage_bytes = (unsigned)(Q * nt * sizeof(T));
+  const unsigned stage_stride = (stage_bytes + 127u) & ~127u;  // TMA destinations 128-byte aligned
+  T *stage[2] = {reinterpret_cast<T *>(smem_raw), reinterpret_cast<T *>(smem_raw + stage_stride)};
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int w, int st) {
+    const int gb = __ldg(list + w);
+    const int4 bi = __ldg(C.blk_info + gb);
+    const LevelDev &L = C.lds[bi.x];
+    const CUtensorMap *tm = tmaps + 2 * bi.x + C.par[L.level];
+    mbar_expect_tx(&bar[st], stage_bytes);
+    if (D == 3) tma_load_4d(stage[st], tm, bi.y << S.lg[0], bi.z << S.lg[1], bi.w << S.lg[2], 0, &bar[st]);
+    else tma_load_3d(stage[st], tm, bi.y << S.lg[0], bi.z << S.lg[1], 0, &bar[st]);
+  };
+  if (threadIdx.x == 0 && (int)blockIdx.x < nlist) issue(blockIdx.x, 0);
+  int it = 0;
+  for (int w = blockIdx.x; w < nlist; w += gridDim.x, ++it) {
+    const int st = it & 1;
+    if (threadIdx.x == 0 && w + (int)gridDim.x < nlist) issue(w + gridDim.x, st ^ 1);
+    unsigned spins = 0;
+    while (!mbar_try_wait(&bar[st], (it >> 1) & 1)) {
+      if (++spins > kWaitLimit) {
+        atomicOr(C.err, ERR_TIMEOUT);
+        return;
+      }
+    }
+    do {
+      const int gb = __ldg(list + w);
+      const int4 bi = __ldg(C.blk_info + gb);
+      const LevelDev &L = C.lds[bi.x];
+      const int t = threadIdx.x;
+      const int x = (bi.y << S.lg[0]) + (t & (S.bs[0] - 1));
+      const int y = (bi.z << S.lg[1]) + ((t >> S.lg[0]) & (S.bs[1] - 1));
+      const int z = (bi.w << S.lg[2]) + (t >> (S.lg[0] + S.lg[1]));
+      const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
+      if (x >= n0 || y >= n1 || z >= n2) break;
+      const unsigned p0 = (unsigned)L.p[0], p01 = (unsigned)(L.p[0] * L.p[1]);
+      const unsigned c = x + p0 * y + p01 * z;
+      const uint8_t tg = C.tag[L.cell_off + c];
+      if (!(tg & (TAG_LEAF | TAG_RLAYER))) break;
+      const unsigned N = (unsigned)L.ncell;
+      T *__restrict__ B = fB<T, Q>(C, L);
+      const T *sp = stage[st];
+      float f[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) f[i] = stage_ld<T>(sp + i * nt + t, C.fp16_inv);
+      const int ph = tg & TAG_GAS;
+      const float acc[3] = {L.acc[ph][0], L.acc[ph][1], L.acc[ph][2]};
+      float drho, u[3], Sm[6];
+      const bool fine = L.finest != 0;
+      if (fine && (C.bflag[gb] & BF_BAND)) {
+        lb_collide<Q, true>(f, L.omega[ph], acc, drho, u, Sm);
+        const long long fc = L.fine_off + c;
+        const long long NF = C.nfine;
+        float *M = C.macro;
+        M[fc] = drho;
+        for (int a = 0; a < D; ++a) M[(1 + a) * NF + fc] = u[a];
+        if (D == 2) {
+          M[3 * NF + fc] = Sm[0]; M[4 * NF + fc] = Sm[1]; M[5 * NF + fc] = Sm[3];
+        } else {
+          M[4 * NF + fc] = Sm[0]; M[5 * NF + fc] = Sm[1]; M[6 * NF + fc] = Sm[2];
+          M[7 * NF + fc] = Sm[3]; M[8 * NF + fc] = Sm[4]; M[9 * NF + fc] = Sm[5];
+        }
+      } else {
+        lb_collide<Q, false>(f, L.omega[ph], acc, drho, u, Sm);
+      }
+      const bool wxm = x == 0 && !L.per[0], wxp = x == n0 - 1 && !L.per[0];
+      const bool wym = y == 0 && !L.per[1], wyp = y == n1 - 1 && !L.per[1];
+      const bool wzm = D == 3 && z == 0 && !L.per[2], wzp = D == 3 && z == n2 - 1 && !L.per[2];
+      const int dxm = x > 0 ? -1 : n0 - 1, dxp = x < n0 - 1 ? 1 : 1 - n0;
+      const int dym = y > 0 ? -(int)p0 : (n1 - 1) * (int)p0, dyp = y < n1 - 1 ? (int)p0 : (1 - n1) * (int)p0;
+      const int dzm = z > 0 ? -(int)p01 : (n2 - 1) * (int)p01, dzp = z < n2 - 1 ? (int)p01 : (1 - n2) * (int)p01;
+      uint32_t cm = 0;
+      int cb = 0;
+      if (fine && (tg & TAG_IFACE)) {
+        cm = C.cmask[L.fine_off + c];
+        cb = C.cbase[L.fine_off + c];
+      }
+      Store<T>::st(B + (LT::REST * N + c), f[LT::REST], C.fp16_scale);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if (i == LT::REST) continue;
+        const int cxi = LT::cx(i), cyi = LT::cy(i), czi = LT::cz(i);
+        const int k = LT::opp(i);
+        if (cm & (1u << k)) {
+          const long long li = cb + __popc(cm & ((1u << k) - 1u));
+          if (li < C.link_cap) {
+            C.linkbuf[2 * li] = f[i];
+            C.linkbuf[2 * li + 1] = f[k];
+          }
+          continue;
+        }
+        const bool wx = (cxi < 0 && wxm) || (cxi > 0 && wxp);
+        const bool wy = (cyi < 0 && wym) || (cyi > 0 && wyp);
+        const bool wz = (czi < 0 && wzm) || (czi > 0 && wzp);
+        if (!(wx || wy || wz)) {
+          const int off = (cxi < 0 ? dxm : (cxi > 0 ? dxp : 0)) + (cyi < 0 ? dym : (cyi > 0 ? dyp : 0)) +
+                          (czi < 0 ? dzm : (czi > 0 ? dzp : 0));
+          Store<T>::st(B + (i * N + (unsigned)((int)c + off)), f[i], C.fp16_scale);
+        } else {
+          const int face = wx ? (cxi < 0 ? 0 : 1) : (wy ? (cyi < 0 ? 2 : 3) : (czi < 0 ? 4 : 5));
+          const float *uw = L.wall_u[face];
+          const float du = cxi * uw[0] + cyi * uw[1] + czi * uw[2];
+          Store<T>::st(B + (k * N + c), f[i] - 6.0f * LT::w(i) * du, C.fp16_scale);
+        }
+      }
+    } while (false);
+    __syncthreads();  // stage st is refilled at iteration it + 2's issue (one iteration from now)
   }
 }
 
@@ -696,6 +876,38 @@ cudaError_t run_init(int Q, int st, Launch L, Ctx C, BlockShape S, const int *li
 }
 cudaError_t run_collide_stream(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n) {
   LSB_QT(Q, st, (LK(k_collide_stream)(C, S, list, n)));
+}
+// Dynamic shared memory of the TMA-staged kernel: two stages of Q x block cells.
+size_t tma_smem_bytes(int Q, int st, int nthreads) {
+  const size_t stage = (size_t)Q * nthreads * (st == 0 ? 4 : 2);
+  return 2 * ((stage + 127) & ~size_t(127));
+}
+// Raise the kernel's dynamic shared-memory limit (once, outside any capture) and
+// report how many CTAs of nthreads fit on one SM.
+cudaError_t prepare_collide_stream_tma(int Q, int st, int nthreads, int *ctas_per_sm) {
+  const size_t smem = tma_smem_bytes(Q, st, nthreads);
+  cudaError_t e = cudaSuccess;
+  int nb = 0;
+  if (Q == 9 && st == 0) {
+    e = cudaFuncSetAttribute(k_collide_stream_tma<9, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_collide_stream_tma<9, float>, nthreads, smem);
+  } else if (Q == 9) {
+    e = cudaFuncSetAttribute(k_collide_stream_tma<9, __half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_collide_stream_tma<9, __half>, nthreads, smem);
+  } else if (st == 0) {
+    e = cudaFuncSetAttribute(k_collide_stream_tma<19, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_collide_stream_tma<19, float>, nthreads, smem);
+  } else {
+    e = cudaFuncSetAttribute(k_collide_stream_tma<19, __half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_collide_stream_tma<19, __half>, nthreads, smem);
+  }
+  *ctas_per_sm = nb;
+  return e;
+}
+cudaError_t run_collide_stream_tma(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n,
+                                   const CUtensorMap *tmaps) {
+  const size_t smem = tma_smem_bytes(Q, st, L.block);
+  LSB_QT(Q, st, (k_collide_stream_tma<Q_, T_><<<L.grid, L.block, smem, L.stream>>>(C, S, list, n, tmaps)));
 }
 cudaError_t run_interface_bc(int Q, int st, Launch L, Ctx C, int glevel) {
   LSB_QT(Q, st, (LK(k_interface_bc)(C, glevel)));

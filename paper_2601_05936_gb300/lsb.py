@@ -60,6 +60,7 @@ def load():
                                     ctypes.POINTER(ctypes.c_void_p), vp, ctypes.POINTER(vp)]
     lib.lsb_set_params.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Params)]
     lib.lsb_step.argtypes = [vp, ctypes.c_int]
+    lib.lsb_use_graphs.argtypes = [vp, ctypes.c_int]
     lib.lsb_refine.argtypes = [vp]
     lib.lsb_get_fields.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t, ctypes.c_int]
     lib.lsb_get_fields_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t,
@@ -85,7 +86,7 @@ def load():
     lib.lsb_kernel_name.restype = ctypes.c_char_p
     lib.lsb_kernel_count.argtypes = []
     lib.lsb_kernel_count.restype = ctypes.c_int
-    for name in ("lsb_get_fields_noalloc", "lsb_profile", "lsb_profile_read", "lsb_create_grid", "lsb_set_params", "lsb_step", "lsb_refine", "lsb_get_fields",
+    for name in ("lsb_use_graphs", "lsb_get_fields_noalloc", "lsb_profile", "lsb_profile_read", "lsb_create_grid", "lsb_set_params", "lsb_step", "lsb_refine", "lsb_get_fields",
                  "lsb_observables", "lsb_cell_updates", "lsb_backward", "lsb_sync"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -199,6 +200,10 @@ class Grid:
 
     def step(self, n=1):
         self._check(self.lib.lsb_step(self.h, int(n)))
+
+    def use_graphs(self, enable=True):
+        """Replay two coarse steps at a time from CUDA graphs (needs a non-default stream)."""
+        self._check(self.lib.lsb_use_graphs(self.h, 1 if enable else 0))
 
     def refine(self):
         self._check(self.lib.lsb_refine(self.h))

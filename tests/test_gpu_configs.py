@@ -1,0 +1,107 @@
+"""GPU checks on the benchmark workloads' shapes: the 3D two-level bubble against
+the oracle on its 32x32x64 copy (FP32 and FP16 storage), the Laplace pressure
+jump of the static drop on the GPU path, and ensembles of uneven cases giving
+bit-identical results to the same cases run alone."""
+import numpy as np
+import pytest
+
+from tests.gpu_util import as_fp32_phi, compare_levels, run_both
+
+pytestmark = pytest.mark.gpu
+
+
+def _phi_err(g, s):
+    return float(np.abs(g.get("phi").reshape(-1).astype(np.float64) - s.phi).max())
+
+
+def test_bubble3d_downsampled_fp32_parity():
+    from paper_2601_05936_gb300 import workloads
+    case = workloads.rising_bubble_3d(scale=0.25)
+    g, s = run_both(case, 2)
+    res = compare_levels(g, s)
+    for r in res:
+        assert r["leaf_equal"], r
+        assert r["u"] < 1e-4 and r["drho_abs"] < 1e-5, r
+    for l in range(2):
+        assert np.array_equal(g.get("blocks", 0, l), s.status[l])
+    assert _phi_err(g, s) < 1e-4
+    assert np.array_equal(g.get("phase").reshape(-1), s.phase[-1].astype(np.uint8))
+
+
+def test_bubble3d_downsampled_fp16_storage_error():
+    """FP16 storage (scaled deviations, FP32 arithmetic): error against FP64 stated per field."""
+    from paper_2601_05936_gb300 import workloads
+    case = workloads.rising_bubble_3d(scale=0.25, storage="fp16s")
+    g, s = run_both(case, 2)
+    res = compare_levels(g, s)
+    U = case["Ma"] / np.sqrt(3.0)  # velocity scale of the case
+    for r in res:
+        assert r["leaf_equal"], r
+        # the field is still nearly at rest after two steps, so bound the error by the velocity scale
+        assert r["umax_abs"] < 2e-3 * U and r["drho_abs"] < 2e-4, r
+    assert _phi_err(g, s) < 1e-3
+
+
+def test_stratified_channel_fp16_storage_error():
+    from paper_2601_05936_gb300 import workloads
+    case = workloads.stratified_channel()
+    case["storage"] = "fp16s"
+    g, s = run_both(case, 1000)
+    r = compare_levels(g, s)[0]
+    assert r["u"] < 5e-3, r
+
+
+def test_static_drop_laplace_jump_gpu():
+    """Closed form on the GPU path: p_in - p_out = sigma / R (2D), two levels."""
+    from paper_2601_05936_gb300 import lsb, workloads
+    case = workloads.static_drop(n=64, radius_base=10.0, band=4.0)
+    g = lsb.Grid(case)
+    g.step(1500)
+    rho = g.get("rho").reshape(-1).astype(np.float64)
+    phase = g.get("phase").reshape(-1)
+    phi = g.get("phi").reshape(-1)
+    rp = np.asarray(case["rho_phys"])
+    p = rp[phase] / 3.0 * (rho - 1.0)
+    dp = p[(phase == 1) & (phi > 3)].mean() - p[(phase == 0) & (phi < -3)].mean()
+    ratio = dp / (case["sigma"] / case["R"])
+    assert abs(ratio - 1.0) < 0.1, ratio
+
+
+def test_ensemble_matches_solo_bit_identical():
+    from paper_2601_05936_gb300 import lsb, workloads
+    cases = workloads.ensemble(n_cases=3, w_range=(64, 96), steps=10)
+    for c in cases:
+        c["regrid_every"] = 4
+    ens = lsb.Grid(cases)
+    ens.step(9)
+    for k, c in enumerate(cases):
+        solo = lsb.Grid(c)
+        solo.step(9)
+        for l in range(int(c["n_levels"])):
+            for field in ("rho", "u"):
+                assert np.array_equal(ens.get(field, k, l), solo.get(field, 0, l)), (k, l, field)
+            assert np.array_equal(ens.get("blocks", k, l), solo.get("blocks", 0, l))
+        assert np.array_equal(ens.get("phi", k), solo.get("phi", 0))
+        solo.close()
+    ens.close()
+
+
+def test_graph_replay_matches_eager_bit_identical():
+    import torch
+
+    from paper_2601_05936_gb300 import lsb
+    from tests.test_gpu_parity import _bubble2d
+    case = _bubble2d(N=64, R=6.0, levels=2, rr=100.0, nu=(0.06, 0.6), g=2e-5, sigma=2e-3)
+    case["refine_dist"] = [8.0]
+    case["regrid_every"] = 6
+    out = []
+    for graphs in (False, True):
+        st = torch.cuda.Stream()
+        g = lsb.Grid(case, stream=st)
+        if graphs:
+            g.use_graphs(True)
+        g.step(15)
+        out.append([g.get(f, 0, l) for l in range(2) for f in ("rho", "u")] + [g.get("phi")])
+        g.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
