@@ -144,6 +144,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-all", action="store_true", help="print a per-kernel time table to stderr")
+    ap.add_argument("--workload", default="bubble3d", choices=["bubble3d", "box3d", "ensemble"],
+                    help="bubble3d: the benchmark configuration; box3d: uniform periodic 128^3 box "
+                         "(collide-and-stream only, for profiling captures); ensemble: 64 uneven 2D bubbles")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -168,9 +171,19 @@ def main():
     __graft_entry__.build()
     from paper_2601_05936_gb300 import lsb, workloads
 
-    case = workloads.rising_bubble_3d(storage=args.storage)
+    if args.workload == "bubble3d":
+        case = workloads.rising_bubble_3d(storage=args.storage)
+        cases = [case]
+    elif args.workload == "box3d":
+        case = workloads.uniform_box(storage=args.storage)
+        cases = [case]
+    else:
+        cases = workloads.ensemble()
+        for c in cases:
+            c["storage"] = args.storage
+        case = cases[0]
     stream = torch.cuda.Stream()
-    g = lsb.Grid(case, stream=stream, device=local)
+    g = lsb.Grid(cases, stream=stream, device=local)
     g.step(args.warmup)
     g.sync()
 
@@ -209,14 +222,19 @@ def main():
     value = upd_sum / (ms_max / 1e3) / 1e6
 
     # roofline of the dominant kernel (collide-and-stream), from events on the library stream
-    cs_ms, cs_n, cs_bytes = prof.get("k_collide_stream", (0.0, 0, 0.0))
+    cs = [v for k, v in prof.items() if k.startswith("k_collide_stream")]
+    cs_ms = sum(v[0] for v in cs)
+    cs_n = sum(v[1] for v in cs)
+    cs_bytes = sum(v[2] for v in cs)
+    per_level = {k: dict(ms=v[0], launches=v[1], gbs=(v[2] / (v[0] / 1e3) / 1e9 if v[0] > 0 else None))
+                 for k, v in prof.items() if k.startswith("k_collide_stream")}
     hbm, src = peaks()
     achieved = cs_bytes / (cs_ms / 1e3) / 1e9 if cs_ms > 0 else None
     roof = dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s",
                 frac=(achieved / hbm) if achieved else None, traffic=None, peak_source=src + " (hbm_gbs, of "
                 + src + ")", kernel="k_collide_stream", launches=cs_n,
                 bytes_per_launch=cs_bytes / max(cs_n, 1), avg_launch_ms=cs_ms / max(cs_n, 1),
-                share_of_step=cs_ms / ms if ms > 0 else None)
+                share_of_step=cs_ms / ms if ms > 0 else None, per_level=per_level)
     if args.profile_all and rank == 0:
         for k, (kms, kn, kb) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
             print(f"{k:20s} {kms:9.2f} ms {kn:7d} launches {100 * kms / ms:5.1f}%", file=sys.stderr)
@@ -227,11 +245,13 @@ def main():
     nld = len(g.cases) * int(case["n_levels"])
     h2d = ctypes.sizeof(lsb.Params) + 0  # the parameter struct the caller hands over each step
     d2h = 8 * (4 + 2 * g.D) * len(g.cases)
+    h2d *= len(g.cases)
     g.sync()
     u0 = g.cell_updates(total=True)
     t0 = time.perf_counter()
     for _ in range(E):
-        g.set_params(case)
+        for k, c in enumerate(cases):
+            g.set_params(c, k)
         g.step(1)
         g.observables()
     t1 = time.perf_counter()
@@ -244,15 +264,18 @@ def main():
 
     if rank != 0:
         return
-    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline()
-    line = dict(metric=METRIC, value=value, unit="MLUPS", n_gpus=world, steps=args.steps, warmup=args.warmup,
+    cpu = None if args.no_cpu_baseline or world > 1 or args.workload != "bubble3d" else cpu_baseline()
+    metric = METRIC if args.workload == "bubble3d" else f"MLUPS (leaf cell updates / s), {args.workload}"
+    lattice = "D2Q9" if args.workload == "ensemble" else "D3Q19"
+    wname = case["name"] if len(cases) == 1 else f"ensemble of {len(cases)} 2D rising bubbles (96x192..256x512, 1-3 levels)"
+    line = dict(metric=metric, value=value, unit="MLUPS", n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f32" if args.storage == "fp32" else "f16-store/f32-compute", data="synthetic",
-                config=dict(workload=case["name"], lattice="D3Q19", levels=int(case["n_levels"]),
+                config=dict(workload=wname, lattice=lattice, levels=int(case["n_levels"]),
                             storage=args.storage, parallelism=f"replicas{world}",
                             cell_updates_per_step=upd / args.steps, l2_flush="state 5.7 GB >> 129 MB L2",
-                            bubble=dict(centroid=[float(v) for v in obs["centroid"]],
-                                        velocity=[float(v) for v in obs["velocity"]])),
+                            bubble=dict(centroid=[float(v) if np.isfinite(v) else None for v in obs["centroid"]],
+                                        velocity=[float(v) if np.isfinite(v) else None for v in obs["velocity"]])),
                 roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clk)
     print(json.dumps(line), flush=True)
     if dist is not None:

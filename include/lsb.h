@@ -206,7 +206,8 @@ int lsb_lattice_table(int lattice, int *c, float *w, int *opp);
 lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, float *dJ_dphi0);
 
 /* Kernel timing for diagnostics and the bench roofline: mode 0 off, 1 times
- * every collide-and-stream launch, 2 times every launch.  Timed launches are
+ * every collide-and-stream launch (one class per level: k_collide_stream,
+ * k_collide_stream_l1, _l2, _l3), 2 times every launch.  Timed launches are
  * bracketed by CUDA events on the handle's stream (a few microseconds each).
  * Calling it discards earlier records.  Synchronises. */
 lsb_status lsb_profile(lsb_grid *g, int mode);

@@ -25,7 +25,8 @@ using namespace lsb;
 namespace {
 
 constexpr int MAXL = 4;
-const char *const KNAMES[] = {"k_collide_stream", "k_interface_bc", "k_restrict", "k_ghost", "k_prolong", "k_level_tags", "k_observables", "k_export", "k_classify_phase", "k_classify_links", "k_band", "k_geometry", "k_ext_init", "k_ext_iter", "k_adv_stage", "k_reinit_prep", "k_reinit_stage", "k_refill", "k_sensor", "k_init", "k_collect"};
+const char *const KNAMES[] = {"k_collide_stream", "k_interface_bc", "k_restrict", "k_ghost", "k_prolong", "k_level_tags", "k_observables", "k_export", "k_classify_phase", "k_classify_links", "k_band", "k_geometry", "k_ext_init", "k_ext_iter", "k_adv_stage", "k_reinit_prep", "k_reinit_stage", "k_refill", "k_sensor", "k_init", "k_collect",
+                               "k_collide_stream_l1", "k_collide_stream_l2", "k_collide_stream_l3"};
 constexpr int NKERN = sizeof(KNAMES) / sizeof(KNAMES[0]);
 
 struct ProfRec {
@@ -232,7 +233,10 @@ cudaEvent_t take_event(lsb_grid *g) {
   return e;
 }
 
-bool profiled(const lsb_grid *g, int kid) { return g->prof_mode == 2 || (g->prof_mode == 1 && kid == 0); }
+// Collide-and-stream launches carry one timing class per level (0, then 21..23).
+int collide_kid(int level) { return level == 0 ? 0 : 20 + level; }
+bool is_collide_kid(int kid) { return kid == 0 || (kid >= 21 && kid <= 23); }
+bool profiled(const lsb_grid *g, int kid) { return g->prof_mode == 2 || (g->prof_mode == 1 && is_collide_kid(kid)); }
 
 // Launch through a host launcher; with profiling on, bracket it with events.
 #define RUN(kid, bytes, grid, block, fn, ...)                         \
@@ -477,10 +481,10 @@ lsb_status advance(lsb_grid *g, int l) {
   const double cs_bytes = 2.0 * g->Q * (g->storage == LSB_FP32 ? 4 : 2) * g->leaf_cells[l];
   if (g->d_tmaps) {
     const int grid = std::min(g->cs[l].n, g->tma_grid);
-    RUN(0, cs_bytes, g->cs[l].n, nt, run_collide_stream_tma, Q, st, LN(g, grid, nt), C, S, (const int *)g->cs[l].d,
+    RUN(collide_kid(l), cs_bytes, g->cs[l].n, nt, run_collide_stream_tma, Q, st, LN(g, grid, nt), C, S, (const int *)g->cs[l].d,
         g->cs[l].n, (const CUtensorMap *)g->d_tmaps);
   } else {
-    RUN(0, cs_bytes, g->cs[l].n, nt, run_collide_stream, Q, st, LN(g, g->cs[l].n, nt), C, S, (const int *)g->cs[l].d,
+    RUN(collide_kid(l), cs_bytes, g->cs[l].n, nt, run_collide_stream, Q, st, LN(g, g->cs[l].n, nt), C, S, (const int *)g->cs[l].d,
         g->cs[l].n);
   }
   if (has_finest(g, l)) {
@@ -1046,7 +1050,8 @@ lsb_status lsb_observables(lsb_grid *g, double *out_host, size_t n_doubles) {
   CU(cudaMemsetAsync(g->d_obs, 0, sizeof(double) * stride * g->ncase, g->stream));
   Ctx C = make_ctx(g);
   BlockShape S = shape(g);
-  RUN(6, 0, g->leaf.n, g->nthreads, run_observables, g->Q, g->storage, LN(g, g->leaf.n, g->nthreads), C, S,
+  const int og = std::min(g->leaf.n, 152 * 4);
+  RUN(6, 0, g->leaf.n, g->nthreads, run_observables, g->Q, g->storage, LN(g, og, g->nthreads), C, S,
       (const int *)g->leaf.d, g->leaf.n, g->d_obs, stride);
   std::vector<double> h((size_t)stride * g->ncase);
   CU(cudaMemcpyAsync(h.data(), g->d_obs, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g->stream));

@@ -258,6 +258,15 @@ __device__ __forceinline__ float stage_ld<__half>(const __half *p, float inv) {
   return __half2float(*p) * inv;
 }
 
+// Per-block values the TMA-issuing thread publishes next to the stage it fills;
+// the stage's mbarrier (arrive = release, wait = acquire) makes them visible.
+struct BlockMeta {
+  long long cell_off, fine_off;
+  unsigned ncell, p0, p01;
+  int gb, ld, level, x0, y0, z0, n0, n1, n2, finest, band, per[3];
+  float omega[2], acc[2][3];
+};
+
 template <int Q, typename T>
 __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape S, const int *__restrict__ list,
                                                                int nlist, const CUtensorMap *__restrict__ tmaps) {
@@ -265,24 +274,46 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
   constexpr int D = LT::D;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[2];
+  __shared__ BlockMeta meta[2];
   const int nt = blockDim.x;
   const unsigned stage_bytes = (unsigned)(Q * nt * sizeof(T));
   const unsigned stage_stride = (stage_bytes + 127u) & ~127u;  // TMA destinations 128-byte aligned
-  T *stage[2] = {reinterpret_cast<T *>(smem_raw), reinterpret_cast<T *>(smem_raw + stage_stride)};
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  // thread 0: publish block w's metadata into meta[st] and start its TMA load into stage st
   auto issue = [&](int w, int st) {
     const int gb = __ldg(list + w);
     const int4 bi = __ldg(C.blk_info + gb);
     const LevelDev &L = C.lds[bi.x];
+    BlockMeta &m = meta[st];
+    m.gb = gb;
+    m.ld = bi.x;
+    m.level = L.level;
+    m.x0 = bi.y << S.lg[0];
+    m.y0 = bi.z << S.lg[1];
+    m.z0 = bi.w << S.lg[2];
+    m.n0 = L.n[0]; m.n1 = L.n[1]; m.n2 = L.n[2];
+    m.p0 = (unsigned)L.p[0];
+    m.p01 = (unsigned)(L.p[0] * L.p[1]);
+    m.ncell = (unsigned)L.ncell;
+    m.cell_off = L.cell_off;
+    m.fine_off = L.fine_off;
+    m.finest = L.finest;
+    m.band = L.finest ? (C.bflag[gb] & BF_BAND) : 0;
+    for (int a = 0; a < 3; ++a) m.per[a] = L.per[a];
+    for (int k = 0; k < 2; ++k) {
+      m.omega[k] = L.omega[k];
+      for (int a = 0; a < 3; ++a) m.acc[k][a] = L.acc[k][a];
+    }
     const CUtensorMap *tm = tmaps + 2 * bi.x + C.par[L.level];
+    T *dst = reinterpret_cast<T *>(smem_raw + st * stage_stride);
     mbar_expect_tx(&bar[st], stage_bytes);
-    if (D == 3) tma_load_4d(stage[st], tm, bi.y << S.lg[0], bi.z << S.lg[1], bi.w << S.lg[2], 0, &bar[st]);
-    else tma_load_3d(stage[st], tm, bi.y << S.lg[0], bi.z << S.lg[1], 0, &bar[st]);
+    if (D == 3) tma_load_4d(dst, tm, m.x0, m.y0, m.z0, 0, &bar[st]);
+    else tma_load_3d(dst, tm, m.x0, m.y0, 0, &bar[st]);
   };
   if (threadIdx.x == 0 && (int)blockIdx.x < nlist) issue(blockIdx.x, 0);
   int it = 0;
@@ -297,32 +328,29 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
       }
     }
     do {
-      const int gb = __ldg(list + w);
-      const int4 bi = __ldg(C.blk_info + gb);
-      const LevelDev &L = C.lds[bi.x];
+      const BlockMeta &m = meta[st];
       const int t = threadIdx.x;
-      const int x = (bi.y << S.lg[0]) + (t & (S.bs[0] - 1));
-      const int y = (bi.z << S.lg[1]) + ((t >> S.lg[0]) & (S.bs[1] - 1));
-      const int z = (bi.w << S.lg[2]) + (t >> (S.lg[0] + S.lg[1]));
-      const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
+      const int x = m.x0 + (t & (S.bs[0] - 1));
+      const int y = m.y0 + ((t >> S.lg[0]) & (S.bs[1] - 1));
+      const int z = m.z0 + (t >> (S.lg[0] + S.lg[1]));
+      const int n0 = m.n0, n1 = m.n1, n2 = m.n2;
       if (x >= n0 || y >= n1 || z >= n2) break;
-      const unsigned p0 = (unsigned)L.p[0], p01 = (unsigned)(L.p[0] * L.p[1]);
+      const unsigned p0 = m.p0, p01 = m.p01;
       const unsigned c = x + p0 * y + p01 * z;
-      const uint8_t tg = C.tag[L.cell_off + c];
+      const uint8_t tg = C.tag[m.cell_off + c];
       if (!(tg & (TAG_LEAF | TAG_RLAYER))) break;
-      const unsigned N = (unsigned)L.ncell;
-      T *__restrict__ B = fB<T, Q>(C, L);
-      const T *sp = stage[st];
+      const unsigned N = m.ncell;
+      T *__restrict__ B = reinterpret_cast<T *>(C.buf[1 - C.par[m.level]]) + m.cell_off * Q;
+      const T *sp = reinterpret_cast<const T *>(smem_raw + st * stage_stride);
       float f[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) f[i] = stage_ld<T>(sp + i * nt + t, C.fp16_inv);
       const int ph = tg & TAG_GAS;
-      const float acc[3] = {L.acc[ph][0], L.acc[ph][1], L.acc[ph][2]};
+      const float acc[3] = {m.acc[ph][0], m.acc[ph][1], m.acc[ph][2]};
       float drho, u[3], Sm[6];
-      const bool fine = L.finest != 0;
-      if (fine && (C.bflag[gb] & BF_BAND)) {
-        lb_collide<Q, true>(f, L.omega[ph], acc, drho, u, Sm);
-        const long long fc = L.fine_off + c;
+      if (m.band) {
+        lb_collide<Q, true>(f, m.omega[ph], acc, drho, u, Sm);
+        const long long fc = m.fine_off + c;
         const long long NF = C.nfine;
         float *M = C.macro;
         M[fc] = drho;
@@ -334,19 +362,20 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
           M[7 * NF + fc] = Sm[3]; M[8 * NF + fc] = Sm[4]; M[9 * NF + fc] = Sm[5];
         }
       } else {
-        lb_collide<Q, false>(f, L.omega[ph], acc, drho, u, Sm);
+        lb_collide<Q, false>(f, m.omega[ph], acc, drho, u, Sm);
       }
-      const bool wxm = x == 0 && !L.per[0], wxp = x == n0 - 1 && !L.per[0];
-      const bool wym = y == 0 && !L.per[1], wyp = y == n1 - 1 && !L.per[1];
-      const bool wzm = D == 3 && z == 0 && !L.per[2], wzp = D == 3 && z == n2 - 1 && !L.per[2];
+      const bool cut = m.finest && (tg & TAG_IFACE);
+      const bool wxm = x == 0 && !m.per[0], wxp = x == n0 - 1 && !m.per[0];
+      const bool wym = y == 0 && !m.per[1], wyp = y == n1 - 1 && !m.per[1];
+      const bool wzm = D == 3 && z == 0 && !m.per[2], wzp = D == 3 && z == n2 - 1 && !m.per[2];
       const int dxm = x > 0 ? -1 : n0 - 1, dxp = x < n0 - 1 ? 1 : 1 - n0;
       const int dym = y > 0 ? -(int)p0 : (n1 - 1) * (int)p0, dyp = y < n1 - 1 ? (int)p0 : (1 - n1) * (int)p0;
       const int dzm = z > 0 ? -(int)p01 : (n2 - 1) * (int)p01, dzp = z < n2 - 1 ? (int)p01 : (1 - n2) * (int)p01;
       uint32_t cm = 0;
       int cb = 0;
-      if (fine && (tg & TAG_IFACE)) {
-        cm = C.cmask[L.fine_off + c];
-        cb = C.cbase[L.fine_off + c];
+      if (cut) {
+        cm = C.cmask[m.fine_off + c];
+        cb = C.cbase[m.fine_off + c];
       }
       Store<T>::st(B + (LT::REST * N + c), f[LT::REST], C.fp16_scale);
 #pragma unroll
@@ -371,13 +400,13 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
           Store<T>::st(B + (i * N + (unsigned)((int)c + off)), f[i], C.fp16_scale);
         } else {
           const int face = wx ? (cxi < 0 ? 0 : 1) : (wy ? (cyi < 0 ? 2 : 3) : (czi < 0 ? 4 : 5));
-          const float *uw = L.wall_u[face];
+          const float *uw = C.lds[m.ld].wall_u[face];
           const float du = cxi * uw[0] + cyi * uw[1] + czi * uw[2];
           Store<T>::st(B + (k * N + c), f[i] - 6.0f * LT::w(i) * du, C.fp16_scale);
         }
       }
     } while (false);
-    __syncthreads();  // stage st is refilled at iteration it + 2's issue (one iteration from now)
+    __syncthreads();  // stage st and meta[st] are refilled one iteration from now
   }
 }
 
@@ -665,16 +694,43 @@ __global__ void k_level_tags(Ctx C, BlockShape S, const int *list, int nlist) {
 // ------------------------------------------------------------------ observables
 // Per case, float64: mass of each phase, gas volume, leaf count, centroid and
 // velocity of the gas (sharp Heaviside, Sec. 3.2), lengths in finest cells.
+// Persistent CTAs accumulate in registers while the case stays the same, then
+// reduce through warp shuffles and shared memory: one set of atomics per CTA
+// and case run instead of one per warp and block.
 template <int Q, typename T>
 __global__ void k_observables(Ctx C, BlockShape S, const int *list, int nlist, double *out, int stride) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
+  constexpr int NV = 4 + 2 * D;
+  __shared__ double red[32][NV];
+  double v[NV];
+  for (int k = 0; k < NV; ++k) v[k] = 0.0;
+  int cur_case = -1;
+  auto flush = [&](int case_id) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    for (int k = 0; k < NV; ++k) {
+      double s = v[k];
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+      if (lane == 0) red[warp][k] = s;
+      v[k] = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
+      if (s != 0.0) atomicAdd(out + (long long)case_id * stride + threadIdx.x, s);
+    }
+    __syncthreads();
+  };
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     const int gb = list[w];
+    const int case_id = C.lds[C.blk_info[gb].x].case_id;  // uniform over the CTA
+    if (case_id != cur_case) {
+      if (cur_case >= 0) flush(cur_case);
+      cur_case = case_id;
+    }
     int x, y, z;
     const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
-    double v[4 + 2 * 3];
-    for (int k = 0; k < 4 + 2 * D; ++k) v[k] = 0.0;
     if (x < L.n[0] && y < L.n[1] && z < L.n[2]) {
       const long long c = cidx(L, x, y, z);
       const uint8_t tg = C.tag[L.cell_off + c];
@@ -688,27 +744,22 @@ __global__ void k_observables(Ctx C, BlockShape S, const int *list, int nlist, d
         double vol = 1.0;
         for (int a = 0; a < D; ++a) vol *= (double)L.scale;
         const int gas = tg & TAG_GAS;
-        v[gas] = vol * (1.0 + (double)drho);
-        v[3] = 1.0;
-        bool finite = isfinite(drho) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
+        v[gas] += vol * (1.0 + (double)drho);
+        v[3] += 1.0;
+        const bool finite = isfinite(drho) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
         if (!finite) atomicOr(C.err, ERR_NONFINITE);
         if (gas) {
-          v[2] = vol;
+          v[2] += vol;
           const int crd[3] = {x, y, z};
           for (int a = 0; a < D; ++a) {
-            v[4 + a] = vol * ((double)crd[a] + 0.5) * (double)L.scale;
-            v[4 + D + a] = vol * (double)u[a];
+            v[4 + a] += vol * ((double)crd[a] + 0.5) * (double)L.scale;
+            v[4 + D + a] += vol * (double)u[a];
           }
         }
       }
     }
-    // block reduction in float64 (warp shuffles, then one atomic per warp)
-    for (int k = 0; k < 4 + 2 * D; ++k) {
-      double s = v[k];
-      for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-      if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(out + (long long)L.case_id * stride + k, s);
-    }
   }
+  if (cur_case >= 0) flush(cur_case);
 }
 
 // ------------------------------------------------------------------ field export

@@ -142,3 +142,15 @@ def ensemble(seed0=5000, n_cases=64, steps=2000, block=(32, 8), w_range=(96, 256
                         p_gas0=prm["sigma"] / R, refine_dist=dref, sensor="band", regrid_every=25, steps=steps,
                         Re_eff=prm["Re_eff"], **LS_DEFAULTS))
     return out
+
+
+def uniform_box(n=128, lattice="D3Q19", storage="fp32", nu=0.05, force=1e-6):
+    """Single-phase periodic box driven by a weak body force: the collide-and-stream
+    kernel alone, sized for profiling captures (n = 128: 2 x 160 MB of populations)."""
+    D = 3 if lattice == "D3Q19" else 2
+    base = (n,) * D
+    block = (32, 4, 4) if D == 3 else (32, 8)
+    bf = (force,) + (0.0,) * (D - 1)
+    return dict(name=f"uniform_box_{lattice}_{n}", lattice=lattice, base=base, n_levels=1, block=block,
+                periodic=(True,) * D, rho_phys=(1.0, 1.0), nu=(nu, nu), body_force=bf, phi0=-np.ones(n ** D),
+                ls_active=False, n_ext=0, reinit_every=0, storage=storage, fp16_scale=1024.0)
