@@ -1,0 +1,295 @@
+"""Discrete adjoint of the oracle's single-level step with a frozen interface.
+
+Test infrastructure (like the rest of ``oracle``): only the tests, the smoke
+check and the benchmark's CPU baseline use it.
+
+The paper has no adjoint; this module defines the one the library computes.
+With the level set held fixed over a window of steps (no advection, no
+reinitialisation, no refill; the phases, cut links, q, n and kappa are
+constants), one step is a smooth map f_n -> f_{n+1}(f_n; p) of the
+pre-collision populations (Sec. 2.1 and 2.3):
+
+  moments and strain rate of f_n -> BGK collision with forcing ->
+  push streaming with half-way bounce-back at walls and, on cut links,
+  the interpolated bounce-back of Eq. bb with the momentum term of Eq. bb_cc
+  and the stress jump of Eq. Sdecomp.
+
+The parameters are p = (sigma, rho_0, rho_1, nu_0, nu_1): surface tension,
+physical densities and kinematic viscosities of liquid (0) and gas (1).  The
+objective is a weighted sum a . obs of the observables of Sec. 3.2 after the
+last step, in the order the library reports them: liquid mass, gas mass, gas
+volume, leaf count, gas centroid (D), gas velocity (D).
+
+``FrozenStep.step_adjoint`` applies the transpose of the step's Jacobian to
+an adjoint population field (the chain rule written out by hand, link by
+link and cell by cell) and returns the parameter partials; ``gradients``
+runs the reverse sweep over a stored trajectory.  Pins in
+tests/test_oracle_adjoint.py: every parameter derivative against central
+finite differences of the forward map in float64, and the dot-product
+identity <J v, w> = <v, J^T w> of one step with J v from central
+differences, on cases that exercise every bounce-back branch.
+"""
+import numpy as np
+
+from .lattice import CS2
+from .lbm import equilibrium, moments, omega_from_nu, strain_rate
+from .levelset import fit_geometry
+
+NPARAM = 5  # sigma, rho_0, rho_1, nu_0, nu_1
+
+
+def params_of(sim):
+    """The parameter vector p of a Sim."""
+    return np.array([sim.sigma, sim.rho_phys[0], sim.rho_phys[1], sim.nu[0], sim.nu[1]], dtype=np.float64)
+
+
+class FrozenStep:
+    """The smooth single-level step of a Sim whose level set is held fixed."""
+
+    def __init__(self, sim):
+        assert sim.L == 1, "single-level grids only"
+        self.sim = sim
+        self.lat = lat = sim.lat
+        self.g = g = sim.geoms[0]
+        self.D, self.Q = lat.D, lat.Q
+        self.phase = sim.phase[0].copy()
+        self.leaf = sim.masks[0][0].copy()
+        self.phi = sim.phi.copy()
+        self.gravity = sim.gravity.copy()
+        self.body_force = sim.body_force.copy()
+        self.wall_u = sim.wall_u.copy()
+        # cut links (x, k): x - c_k lies in the other phase; i = opp(k) points from x to y = x + c_i
+        x, k = sim.cut_links(self.phase, self.leaf)
+        i = lat.opp[k]
+        y, _ = g.shift(x, lat.c[i].T)
+        self.x, self.k, self.i, self.y = x, k, i, y
+        self.q = self.phi[x] / (self.phi[x] - self.phi[y])  # radiation theorem, Sec. 2.3
+        self.A = self.phase[x]
+        self.B = 1 - self.A
+        back, _ = g.shift(x, -lat.c[i].T)
+        ok = back >= 0
+        ok[ok] = self.leaf[back[ok]] & (self.phase[back[ok]] == self.A[ok])
+        self.back, self.ok = back, ok
+        icells = np.unique(x)
+        nvec = np.zeros((self.D, g.N))
+        kap = np.zeros(g.N)
+        nv, kv, _, _ = fit_geometry(g, self.phi, icells)
+        nvec[:, icells] = nv
+        kap[icells] = kv
+        q = self.q
+        n = (1 - q) * nvec[:, x] + q * nvec[:, y]
+        nm = np.sqrt((n * n).sum(0))
+        n = np.where(nm > 0, n / np.where(nm > 0, nm, 1.0), 0.0)
+        sgn = np.where(self.A == 0, 1.0, -1.0)  # n points into the gas; n_A from A into B
+        self.nA = sgn * n
+        self.kA = sgn * ((1 - q) * kap[x] + q * kap[y])
+        self.ci = lat.cf[i].T
+        cells = np.arange(g.N)
+        self.src = [g.shift(cells, -lat.c[kk]) for kk in range(lat.Q)]
+        self.cut = np.zeros((lat.Q, g.N), dtype=bool)
+        self.cut[k, x] = True
+        self.gas = self.leaf & (self.phase == 1)
+        self.centers = g.centers(1.0)
+
+    # ---------------------------------------------------------------- parameters
+    def cell_params(self, p):
+        """omega and acceleration per cell for the parameter vector p."""
+        ph = self.phase
+        rp, nu = p[1:3], p[3:5]
+        om = omega_from_nu(nu[ph])
+        acc = self.gravity[:, None] + self.body_force[:, None] / rp[ph][None, :]
+        return om, acc
+
+    # ---------------------------------------------------------------- forward
+    def _link_pieces(self, rho, u, S, p):
+        q, A, B, x, y = self.q, self.A, self.B, self.x, self.y
+        rp, nu = p[1:3], p[3:5]
+        etaA, etaB = rp[A] * nu[A], rp[B] * nu[B]
+        eb = 0.5 * (etaA + etaB)
+        je = etaB - etaA
+        jp = CS2 * (rp[B] * (rho[y] - 1.0) - rp[A] * (rho[x] - 1.0))
+        Sbar = 0.5 * (S[:, :, x] + S[:, :, y])
+        nA, ci = self.nA, self.ci
+        v = np.einsum("abn,bn->an", Sbar, nA)
+        Snn = (nA * v).sum(0)
+        cn = (ci * nA).sum(0)
+        cvt = (ci * v).sum(0) - Snn * cn
+        r = je / eb
+        alpha = (jp + p[0] * self.kA) / (2.0 * eb) - r * Snn
+        ccS = alpha * cn * cn - 2.0 * r * cn * cvt  # c_i c_i : [S]
+        uI = (1 - q) * u[:, x] + q * u[:, y]
+        wi = self.lat.w[self.i]
+        df = -(2.0 * wi / CS2) * ((ci * uI).sum(0) - q * (1 - q) * ccS)  # Eq. bb_cc
+        return dict(eb=eb, je=je, jp=jp, Snn=Snn, cn=cn, cvt=cvt, r=r, alpha=alpha, df=df)
+
+    def step(self, f, p):
+        """f_{n+1} from the pre-collision populations f_n."""
+        lat = self.lat
+        om, acc = self.cell_params(p)
+        rho, u = moments(lat, f)
+        S = strain_rate(lat, f, om)
+        fc = f + om[None, :] * (equilibrium(lat, rho, u) - f) \
+            + lat.w[:, None] * rho[None, :] * (lat.cf @ acc) / CS2
+        fn = f.copy()
+        for k in range(lat.Q):
+            i = lat.opp[k]
+            src, face = self.src[k]
+            wall = (src < 0) & self.leaf
+            same = (src >= 0) & ~self.cut[k] & self.leaf
+            fn[k, same] = fc[k, src[same]]
+            if wall.any():
+                fn[k, wall] = fc[i, wall] - (2 * lat.w[i] / CS2) * (self.wall_u[face[wall]] @ lat.cf[i])
+        P = self._link_pieces(rho, u, S, p)
+        x, k, i, q = self.x, self.k, self.i, self.q
+        fi, fk = fc[i, x], fc[k, x]
+        fb = np.where(self.ok, fc[i, np.where(self.ok, self.back, 0)], 0.0)
+        df = P["df"]
+        fn[k, x] = np.where(q >= 0.5, fi / (2 * q) + (2 * q - 1) / (2 * q) * fk + df / (2 * q),
+                            np.where(self.ok, 2 * q * fi + (1 - 2 * q) * fb + df, fi + df))  # Eq. bb
+        return fn
+
+    def observables(self, f):
+        """liquid mass, gas mass, gas volume, leaf count, centroid (D), gas velocity (D)."""
+        rho, u = moments(self.lat, f)
+        leaf, gas = self.leaf, self.gas
+        vol = float(gas.sum())
+        return np.concatenate([[rho[leaf & (self.phase == 0)].sum(), rho[gas].sum(), vol, float(leaf.sum())],
+                               self.centers[:, gas].sum(1) / vol, u[:, gas].sum(1) / vol])
+
+    # ---------------------------------------------------------------- adjoint
+    def observables_adjoint(self, f, a):
+        """dJ/df for J = a . observables(f)."""
+        lat = self.lat
+        rho, u = moments(lat, f)
+        D = self.D
+        lam = np.zeros_like(f)
+        lam[:, self.leaf & (self.phase == 0)] += a[0]
+        lam[:, self.gas] += a[1]
+        vol = float(self.gas.sum())
+        au = np.asarray(a[4 + D:4 + 2 * D], dtype=np.float64)
+        g = self.gas
+        # d u_a / d f_j = (c_ja - u_a) / rho
+        lam[:, g] += ((lat.cf @ au)[:, None] - (au @ u[:, g])[None, :]) / rho[g][None, :] / vol
+        return lam
+
+    def step_adjoint(self, f, p, lam_next):
+        """(lam_n, dJ/dp): the transpose of the step's Jacobian applied to lam_next."""
+        lat, g = self.lat, self.g
+        D, Q, N = self.D, self.Q, g.N
+        om, acc = self.cell_params(p)
+        rho, u = moments(lat, f)
+        feq = equilibrium(lat, rho, u)
+        S = strain_rate(lat, f, om)
+        dp = np.zeros(NPARAM)
+        # ---- streaming: transpose of the push and of the wall bounce-back
+        lc = np.zeros_like(f)
+        for k in range(Q):
+            i = lat.opp[k]
+            src, _ = self.src[k]
+            same = (src >= 0) & ~self.cut[k] & self.leaf
+            np.add.at(lc[k], src[same], lam_next[k, same])
+            wall = (src < 0) & self.leaf
+            lc[i, wall] += lam_next[k, wall]
+        # ---- cut links: transpose of Eq. bb
+        x, k, i, q, y, A, B = self.x, self.k, self.i, self.q, self.y, self.A, self.B
+        lam = lam_next[k, x]
+        hi = q >= 0.5
+        ok = self.ok & ~hi
+        np.add.at(lc, (i, x), np.where(hi, 1 / (2 * q), np.where(ok, 2 * q, 1.0)) * lam)
+        np.add.at(lc, (k, x), np.where(hi, (2 * q - 1) / (2 * q), 0.0) * lam)
+        np.add.at(lc, (i[ok], self.back[ok]), (1 - 2 * q[ok]) * lam[ok])
+        l_df = np.where(hi, 1 / (2 * q), 1.0) * lam
+        # ---- Eq. bb_cc: df = -(2 w_i / cs2) (c_i . u_I - q (1 - q) c_i c_i : [S])
+        P = self._link_pieces(rho, u, S, p)
+        wi = lat.w[i]
+        ci, nA = self.ci, self.nA
+        l_uI = -(2 * wi / CS2) * l_df * ci
+        l_ccS = (2 * wi / CS2) * q * (1 - q) * l_df
+        lam_u = np.zeros((D, N))
+        for a in range(D):
+            np.add.at(lam_u[a], x, (1 - q) * l_uI[a])
+            np.add.at(lam_u[a], y, q * l_uI[a])
+        cn, cvt, Snn, r, eb, je = P["cn"], P["cvt"], P["Snn"], P["r"], P["eb"], P["je"]
+        l_alpha = l_ccS * cn * cn
+        l_cvt = -2 * r * cn * l_ccS
+        l_r = -2 * cn * cvt * l_ccS - Snn * l_alpha
+        l_jp = l_alpha / (2 * eb)
+        l_eb = -l_alpha * (P["jp"] + p[0] * self.kA) / (2 * eb * eb) - l_r * je / (eb * eb)
+        l_je = l_r / eb
+        l_etaA = 0.5 * l_eb - l_je
+        l_etaB = 0.5 * l_eb + l_je
+        dp[0] += (l_alpha * self.kA / (2 * eb)).sum()
+        rp, nu = p[1:3], p[3:5]
+        for ph in (0, 1):
+            mA, mB = A == ph, B == ph
+            l_eta = l_etaA[mA].sum() + l_etaB[mB].sum()
+            dp[1 + ph] += l_eta * nu[ph]
+            dp[3 + ph] += l_eta * rp[ph]
+            dp[1 + ph] += CS2 * ((l_jp * (rho[y] - 1.0))[mB].sum() - (l_jp * (rho[x] - 1.0))[mA].sum())
+        lam_rho = np.zeros(N)
+        np.add.at(lam_rho, y, CS2 * rp[B] * l_jp)
+        np.add.at(lam_rho, x, -CS2 * rp[A] * l_jp)
+        # Snn = n.Sbar.n and c.v_t = c.Sbar.n - Snn (c.n)
+        l_Snn = -r * l_alpha - cn * l_cvt
+        l_Sbar = np.einsum("an,bn->abn", ci, nA) * l_cvt + np.einsum("an,bn->abn", nA, nA) * l_Snn
+        lam_S = np.zeros((D, D, N))
+        for a in range(D):
+            for b in range(D):
+                np.add.at(lam_S[a, b], x, 0.5 * l_Sbar[a, b])
+                np.add.at(lam_S[a, b], y, 0.5 * l_Sbar[a, b])
+        # ---- collision: fc = f + omega (feq(rho, u) - f) + w rho (c . acc) / cs2
+        cu = lat.cf @ u
+        lam_n = (1 - om)[None, :] * lc
+        lam_n += ((om[None, :] * feq / rho[None, :] + lat.w[:, None] * (lat.cf @ acc) / CS2) * lc).sum(0)[None, :]
+        Bv = np.zeros((D, N))
+        for a in range(D):
+            dfeq = lat.w[:, None] * rho[None, :] * (lat.cf[:, a][:, None] / CS2 + cu * lat.cf[:, a][:, None] / CS2 ** 2
+                                                    - u[a][None, :] / CS2)
+            Bv[a] = om * (dfeq * lc).sum(0)
+        # moments: d rho / d f_j = 1, d u_a / d f_j = (c_ja - u_a) / rho
+        cmu = lat.cf[:, :, None] - u[None, :, :]
+        lam_n += np.einsum("an,jan->jn", Bv + lam_u, cmu) / rho[None, :]
+        lam_n += lam_rho[None, :]
+        # strain rate S_ab = kk Pi_ab, kk = -omega / (2 rho cs2), Pi_ab = sum_q c_qa c_qb (f_q - feq_q)
+        kk = -om / (2 * rho * CS2)
+        Pi = np.einsum("qa,qb,qn->abn", lat.cf, lat.cf, f - feq)
+        eye = np.eye(D)
+        for a in range(D):
+            for b in range(D):
+                dPi = ((lat.cf[:, a] * lat.cf[:, b])[:, None] - (CS2 * eye[a, b] - u[a] * u[b])[None, :]
+                       - lat.cf[:, a][:, None] * u[b][None, :] - u[a][None, :] * lat.cf[:, b][:, None])
+                lam_n += (lam_S[a, b] * kk)[None, :] * (dPi - Pi[a, b][None, :] / rho[None, :])
+        # parameter partials of the collision: omega(nu), acc(rho), and S through omega
+        l_om = (lc * (feq - f)).sum(0) + (lam_S * S).sum((0, 1)) / om
+        l_acc = np.einsum("qn,qa->an", lc * lat.w[:, None] * rho[None, :], lat.cf) / CS2
+        for ph in (0, 1):
+            m = self.leaf & (self.phase == ph)
+            om_p = omega_from_nu(nu[ph])
+            dp[3 + ph] += l_om[m].sum() * (-om_p * om_p / CS2)  # d omega / d nu
+            dp[1 + ph] += (l_acc[:, m].sum(1) * (-self.body_force / rp[ph] ** 2)).sum()
+        lam_n[:, ~self.leaf] = lam_next[:, ~self.leaf]
+        return lam_n, dp
+
+
+def trajectory(step, f0, p, nsteps):
+    fs = [f0]
+    for _ in range(nsteps):
+        fs.append(step.step(fs[-1], p))
+    return fs
+
+
+def objective(step, f0, p, nsteps, a):
+    return float(np.asarray(a) @ step.observables(trajectory(step, f0, p, nsteps)[-1]))
+
+
+def gradients(step, f0, p, nsteps, a):
+    """J = a . observables(f_N) and its adjoint gradients: (J, dJ/dp, dJ/df_0)."""
+    a = np.asarray(a, dtype=np.float64)
+    fs = trajectory(step, f0, p, nsteps)
+    J = float(a @ step.observables(fs[-1]))
+    lam = step.observables_adjoint(fs[-1], a)
+    dp = np.zeros(NPARAM)
+    for n in range(nsteps - 1, -1, -1):
+        lam, d = step.step_adjoint(fs[n], p, lam)
+        dp += d
+    return J, dp, lam
