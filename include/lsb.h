@@ -66,7 +66,9 @@ enum {
   LSB_FIELD_CUTMASK = 7,/* uint32 per cell: bit k set when the incoming direction
                           k's source lies in the other phase (finest level)       */
   LSB_FIELD_KAPPA = 8, /* curvature at interface cells (float, finest level)      */
-  LSB_FIELD_UEXT = 9   /* extension velocity u~ (D x cells, finest level)         */
+  LSB_FIELD_UEXT = 9,  /* extension velocity u~ (D x cells, finest level)         */
+  LSB_FIELD_ADJ_F = 10 /* after lsb_backward: dJ/df at the start of the recorded
+                          window (float, Q x cells, Fig. 1 order)                 */
 };
 
 /* Geometry and discretisation of one case, fixed for the handle's life. */
@@ -199,10 +201,42 @@ lsb_status lsb_cell_updates(const lsb_grid *g, double *per_coarse_step, double *
 int lsb_lattice_table(int lattice, int *c, float *w, int *opp);
 
 /*
- * Adjoint of the bubble observables with respect to the parameters
- * (Sec. 3.2 observables; no counterpart in the paper): not available in this
- * build.  Always returns LSB_ESTATE.
+ * Adjoint (the paper has no counterpart; the differentiated map is its
+ * step, Sec. 2.1 and 2.3).  With the level set frozen (ls_active = 0 in every
+ * case) the phases, cut links, q, n and kappa are constants and one step is
+ * a smooth map of the populations; lsb_backward computes, for
+ * J = sum over cases of dJ_dobs . observables (the lsb_observables vector
+ * after the last recorded step), the exact derivatives of that discrete map
+ * by a hand-written reverse sweep: transposes of the collision with forcing,
+ * the streaming with wall bounce-back, and the interface bounce-back of
+ * Eq. bb with Eq. bb_cc and Eq. Sdecomp.
+ *
+ * lsb_record(g, checkpoint_every): start a recording at the current state.
+ * The following lsb_step calls run eagerly (no CUDA graphs) and copy the
+ * state into a device checkpoint at the start of every checkpoint_every-th
+ * step (one buffer of Q x cells floats each, allocated as needed).  A new
+ * lsb_record, lsb_set_params or lsb_refine ends the recording and frees the
+ * checkpoints.  Errors: LSB_EINVAL (checkpoint_every < 1), LSB_ESTATE
+ * (more than one level, FP16 storage, or a case with ls_active != 0).
+ *
+ * lsb_backward(g, dJ_dobs, dJ_dparams, dJ_dphi0): reverse sweep over every
+ * step recorded so far.  Segment by segment, from the last, it restores the
+ * checkpoint, recomputes the segment's steps keeping their states (device
+ * memory for checkpoint_every states), and runs the adjoint steps backwards.
+ * dJ_dobs: host, n_cases x (4 + 2 D) doubles, weights of the observables
+ * in lsb_observables order (centroid, volume and leaf count are constants of
+ * the frozen map).  dJ_dparams: host, n_cases x LSB_NPARAM_ADJ doubles, or
+ * NULL; per case dJ/dsigma, dJ/drho[0], dJ/drho[1], dJ/dnu[0], dJ/dnu[1] at
+ * the recorded start state.  dJ_dphi0 must be NULL (derivatives with
+ * respect to the level set are not computed).  Afterwards the state is that
+ * of the last recorded step again, the recording stays open (lsb_backward
+ * may be called again, e.g. with other weights, and lsb_step extends the
+ * recording), and LSB_FIELD_ADJ_F returns dJ/df at the start of the
+ * window.  FP32 adjoint populations, FP64 parameter sums.  Synchronises.
+ * Errors: LSB_EINVAL, LSB_ESTATE (no recording), LSB_ENOMEM, LSB_ECUDA.
  */
+enum { LSB_NPARAM_ADJ = 5 };
+lsb_status lsb_record(lsb_grid *g, int checkpoint_every);
 lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, float *dJ_dphi0);
 
 /* Kernel timing for diagnostics and the bench roofline: mode 0 off, 1 times

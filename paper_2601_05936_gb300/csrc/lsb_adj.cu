@@ -1,0 +1,506 @@
+// Discrete adjoint of the frozen-interface step (the paper has no adjoint; the
+// forward step is Sec. 2.1 and 2.3).  With the level set held fixed, one
+// finest-level step maps the pre-collision populations f_n to f_{n+1} through
+// BGK collision with forcing (Eq. 1, feq, omega), push streaming with
+// half-way wall bounce-back, and the interpolated bounce-back of Eq. bb with
+// the momentum term of Eq. bb_cc and the stress jump of Eq. Sdecomp on cut
+// links.  The kernels here apply the transpose of that map's Jacobian to an
+// adjoint population field lambda_{n+1} (same layout as f) and accumulate the
+// partial derivatives with respect to the case parameters:
+//
+//   k_adj_seed      lambda_N = dJ/df_N for J = a . observables (Sec. 3.2)
+//   k_adj_links     per cut link: transpose of Eq. bb (coefficients of the
+//                   parked post-collision values go to the link buffer, the
+//                   back-neighbour coefficient is added in place), and of
+//                   Eq. bb_cc / Sdecomp down to the pre-collision moments and
+//                   strain rate of both link cells (macro adjoint, atomics)
+//                   and to sigma, the densities and the dynamic viscosities
+//   k_adj_collide   per cell: transpose of the push (a gather), plus the
+//                   link-buffer terms, then of the collision, the moments and
+//                   the strain rate; omega and acceleration partials
+//
+// Precision: lambda and the Jacobians in FP32 (the forward arithmetic), every
+// parameter partial summed in FP64.
+#include "lsb_kernels.h"
+
+namespace lsb {
+
+namespace {
+
+constexpr int kShCases = 64;  // cases whose link partials a CTA sums in shared memory
+
+// Index of the symmetric pair (a, b) in the strain-rate storage of the
+// forward kernels: 2D xx, xy, yy; 3D xx, xy, xz, yy, yz, zz.
+template <int D>
+__device__ __forceinline__ int sym(int a, int b) {
+  const int lo = a < b ? a : b, hi = a < b ? b : a;
+  if (D == 2) return lo + hi;
+  return lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
+}
+
+// Moments and strain rate S_ab = -(omega / (2 rho c_s^2)) sum_i c_ia c_ib (f_i - feq_i)
+// of one cell, S in the symmetric storage order above.
+template <int Q>
+__device__ __forceinline__ void moments_strain(const float *f, float om, float &drho, float u[3], float *S) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  lb_moments<Q>(f, drho, u);
+  const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float fn = f[i] - feq_dev<Q>(i, drho, u, usq);
+    const float c[3] = {(float)LT::cx(i), (float)LT::cy(i), (float)LT::cz(i)};
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = a; b < D; ++b) P[sym<D>(a, b)] += c[a] * c[b] * fn;
+  }
+  const float s = -1.5f * om / (1.0f + drho);
+#pragma unroll
+  for (int k = 0; k < D * (D + 1) / 2; ++k) S[k] = s * P[k];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ seed
+// lambda_N[j] at a leaf cell of volume v (finest cells): a_mass[phase] v, plus in
+// the gas v sum_a a_u[a] (c_ja - u_a) / (rho V_gas), the derivative of the gas
+// velocity observable sum(v u) / V_gas.  obs holds the raw sums of
+// k_observables (entry 2 of each case: V_gas).
+template <int Q>
+__global__ void k_adj_seed(Ctx C, BlockShape S, const int *list, int nlist, const float *F, float *lam,
+                           const double *wobs, const double *obs, int stride) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
+    int x, y, z;
+    const LevelDev &L = blk_cell(C, S, list[w], threadIdx.x, x, y, z);
+    if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
+    const long long c = cidx(L, x, y, z);
+    const uint8_t tg = C.tag[L.cell_off + c];
+    if (!(tg & TAG_LEAF)) continue;
+    const long long N = L.ncell;
+    const float *Fl = F + L.cell_off * Q;
+    float *lm = lam + L.cell_off * Q;
+    const double *a = wobs + (long long)L.case_id * stride;
+    const double V = obs[(long long)L.case_id * stride + 2];
+    float vol = 1.f;
+    for (int k = 0; k < D; ++k) vol *= (float)L.scale;
+    const int gas = tg & TAG_GAS;
+    float f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = Fl[i * N + c];
+    float drho, u[3];
+    lb_moments<Q>(f, drho, u);
+    const float base = vol * (float)a[gas];
+    float au[3] = {0.f, 0.f, 0.f}, auu = 0.f;
+    if (gas && V > 0.0) {
+      const float s = vol / ((1.0f + drho) * (float)V);
+      for (int k = 0; k < D; ++k) {
+        au[k] = s * (float)a[4 + D + k];
+        auu += au[k] * u[k];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+      lm[i * N + c] = base + au[0] * LT::cx(i) + au[1] * LT::cy(i) + au[2] * LT::cz(i) - auu;
+  }
+}
+
+// ------------------------------------------------------------------ cut links
+// One thread per interface cell x (phase A); for each cut link (x, k), i = opp(k)
+// points to y = x + c_i (phase B).  The forward value was
+//   q >= 1/2:          fi / 2q + (2q - 1)/2q fk + df / 2q
+//   q < 1/2, back ok:  2q fi + (1 - 2q) fb + df
+//   otherwise:         fi + df
+// with fi, fk the post-collision populations of x parked in the link buffer and
+// fb the value streamed into (x, i) from the back neighbour x - c_i.  The link
+// buffer receives the coefficients of fi and fk times lambda; the fb term is added
+// to lambda_{n+1}(x, i), which only the gather of the back neighbour reads
+// ((x, i) is not a cut link when the back neighbour is in phase A, and only this
+// thread writes it).  df's adjoint goes to the moments and strain rate of x and y.
+//
+// grad per case (NG_ADJ doubles): [0] sigma, [1, 2] rho_phys through [p],
+// [3, 4] eta, [5, 6] omega per phase, [7 .. 12] acceleration per phase.
+template <int Q>
+__global__ void k_adj_links(Ctx C, int glevel, const float *__restrict__ F, float *lamN, float *LA, float *MA,
+                            double *grad, int ncase) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  constexpr int NS = D * (D + 1) / 2;
+  __shared__ double sg[kShCases * 5];
+  const bool shared_sum = ncase <= kShCases;
+  for (int k = threadIdx.x; k < kShCases * 5; k += blockDim.x) sg[k] = 0.0;
+  __syncthreads();
+  const int n = min(C.counters[glevel * NCOUNT + 1], (int)C.list_cap);
+  const int2 *lst = C.iface_list + (long long)glevel * C.list_cap;
+  const long long NF = C.nfine;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 it = lst[e];
+    const LevelDev &L = C.lds[it.x];
+    const long long c = it.y;
+    const int x = (int)(c % L.p[0]);
+    const int y = (int)((c / L.p[0]) % L.p[1]);
+    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    const long long fo = L.fine_off;
+    const uint32_t cm = C.cmask[fo + c];
+    const int cb = C.cbase[fo + c];
+    const uint8_t tg = C.tag[L.cell_off + c];
+    const int A = tg & TAG_GAS;
+    const int Bp = 1 - A;
+    const long long N = L.ncell;
+    const float *Fl = F + L.cell_off * Q;
+    float *lam = lamN + L.cell_off * Q;
+    float f[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) f[j] = Fl[j * N + c];
+    float rA, uA[3], SA[6];
+    moments_strain<Q>(f, L.omega[A], rA, uA, SA);
+    const float phx = C.phi[fo + c];
+    float nx[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < D; ++a) nx[a] = C.nvec[a * NF + fo + c];
+    const float kx = C.kappa[fo + c];
+    const float etaA = L.eta[A], etaB = L.eta[Bp];
+    const float eb = 0.5f * (etaA + etaB);
+    const float je = etaB - etaA;
+    const float r = je / eb;
+    const float sgn = (A == 0) ? 1.0f : -1.0f;
+    // macro adjoint of x, summed over its links: rho, u[D], S[NS]
+    float mx[1 + 3 + 6];
+    for (int m = 0; m < 1 + D + NS; ++m) mx[m] = 0.f;
+    double gs = 0.0, grp[2] = {0.0, 0.0}, get[2] = {0.0, 0.0};
+    for (int k = 0; k < Q; ++k) {
+      if (!(cm & (1u << k))) continue;
+      const int i = LT::opp(k);
+      const long long li = cb + __popc(cm & ((1u << k) - 1u));
+      if (li >= C.link_cap) continue;
+      const float lml = lam[k * N + c];
+      int yx = x + LT::cx(i), yy = y + LT::cy(i), yz = z + LT::cz(i);
+      wrap(L, 0, yx); wrap(L, 1, yy); if (D == 3) wrap(L, 2, yz);
+      const long long cy_ = cidx(L, yx, yy, yz);
+      const float phy = C.phi[fo + cy_];
+      const float q = phx / (phx - phy);
+      // Bouzidi branch coefficients
+      bool hi = q >= 0.5f, ok = false;
+      if (!hi) {
+        int bx = x - LT::cx(i), by = y - LT::cy(i), bz = z - LT::cz(i);
+        ok = wrap(L, 0, bx) && wrap(L, 1, by) && (D == 2 || wrap(L, 2, bz));
+        if (ok) {
+          const uint8_t tb = C.tag[L.cell_off + cidx(L, bx, by, bz)];
+          ok = (tb & TAG_LEAF) && ((tb & TAG_GAS) == A);
+        }
+      }
+      const float c_fi = hi ? 0.5f / q : (ok ? 2.0f * q : 1.0f);
+      const float c_fk = hi ? (2.0f * q - 1.0f) / (2.0f * q) : 0.0f;
+      const float c_df = hi ? 0.5f / q : 1.0f;
+      LA[2 * li] = c_fi * lml;
+      LA[2 * li + 1] = c_fk * lml;
+      if (!hi && ok) lam[i * N + c] += (1.0f - 2.0f * q) * lml;
+      const float ldf = c_df * lml;
+      if (ldf == 0.0f) continue;
+      // forward pieces of Eq. bb_cc at this link
+      float fy[Q];
+#pragma unroll
+      for (int j = 0; j < Q; ++j) fy[j] = Fl[j * N + cy_];
+      float rB, uB[3], SB[6];
+      moments_strain<Q>(fy, L.omega[Bp], rB, uB, SB);
+      float nv[3] = {0.f, 0.f, 0.f}, nn = 0.f;
+      for (int a = 0; a < D; ++a) {
+        nv[a] = (1.0f - q) * nx[a] + q * C.nvec[a * NF + fo + cy_];
+        nn += nv[a] * nv[a];
+      }
+      nn = sqrtf(nn);
+      for (int a = 0; a < D; ++a) nv[a] = nn > 0.f ? sgn * nv[a] / nn : 0.f;
+      const float kap = sgn * ((1.0f - q) * kx + q * C.kappa[fo + cy_]);
+      float Sb[6];
+      for (int s = 0; s < NS; ++s) Sb[s] = 0.5f * (SA[s] + SB[s]);
+      const float jp = CS2 * (L.rho_phys[Bp] * rB - L.rho_phys[A] * rA);
+      const float ci[3] = {(float)LT::cx(i), (float)LT::cy(i), (float)LT::cz(i)};
+      float v[3] = {0.f, 0.f, 0.f}, Snn = 0.f, cn = 0.f, cv = 0.f;
+      for (int a = 0; a < D; ++a) {
+        for (int b = 0; b < D; ++b) v[a] += Sb[sym<D>(a, b)] * nv[b];
+        Snn += nv[a] * v[a];
+        cn += ci[a] * nv[a];
+        cv += ci[a] * v[a];
+      }
+      const float cvt = cv - Snn * cn;
+      // transpose of df = -6 w_i (c_i . u_I - q (1 - q) ccS), ccS = alpha cn^2 - 2 r cn cvt,
+      // alpha = (jp + sigma kappa) / (2 eb) - r Snn, r = je / eb
+      const float w6 = 6.0f * LT::w(i);
+      const float luI = -w6 * ldf;  // times c_i
+      const float lccS = w6 * q * (1.0f - q) * ldf;
+      const float la = lccS * cn * cn;
+      const float lcvt = -2.0f * r * cn * lccS;
+      const float lr = -2.0f * cn * cvt * lccS - Snn * la;
+      const float ljp = la / (2.0f * eb);
+      const float leb = -la * (jp + L.sigma * kap) / (2.0f * eb * eb) - lr * je / (eb * eb);
+      const float lje = lr / eb;
+      gs += (double)(la * kap / (2.0f * eb));
+      grp[Bp] += (double)(ljp * CS2 * rB);
+      grp[A] -= (double)(ljp * CS2 * rA);
+      get[A] += (double)(0.5f * leb - lje);
+      get[Bp] += (double)(0.5f * leb + lje);
+      const float lSnn = -r * la - cn * lcvt;
+      // macro adjoint: rho through [p], u through u_I, S through Sbar (half to each cell)
+      const long long my = fo + cy_;
+      mx[0] -= CS2 * L.rho_phys[A] * ljp;
+      atomicAdd(MA + my, CS2 * L.rho_phys[Bp] * ljp);
+      for (int a = 0; a < D; ++a) {
+        mx[1 + a] += (1.0f - q) * luI * ci[a];
+        atomicAdd(MA + (1 + a) * NF + my, q * luI * ci[a]);
+      }
+      for (int a = 0; a < D; ++a)
+        for (int b = a; b < D; ++b) {
+          // sum of the (a, b) and (b, a) entries of ci n^T lcvt + n n^T lSnn
+          const float t = a == b ? ci[a] * nv[a] * lcvt + nv[a] * nv[a] * lSnn
+                                 : (ci[a] * nv[b] + ci[b] * nv[a]) * lcvt + 2.0f * nv[a] * nv[b] * lSnn;
+          const int s = sym<D>(a, b);
+          mx[1 + D + s] += 0.5f * t;
+          atomicAdd(MA + (1 + D + s) * NF + my, 0.5f * t);
+        }
+    }
+    for (int m = 0; m < 1 + D + NS; ++m)
+      if (mx[m] != 0.f) atomicAdd(MA + m * NF + fo + c, mx[m]);
+    const double vals[5] = {gs, grp[0], grp[1], get[0], get[1]};
+    for (int k = 0; k < 5; ++k) {
+      if (vals[k] == 0.0) continue;
+      if (shared_sum) atomicAdd(sg + L.case_id * 5 + k, vals[k]);
+      else atomicAdd(grad + (long long)L.case_id * NG_ADJ + k, vals[k]);
+    }
+  }
+  __syncthreads();
+  if (shared_sum)
+    for (int k = threadIdx.x; k < ncase * 5; k += blockDim.x)
+      if (sg[k] != 0.0) atomicAdd(grad + (long long)(k / 5) * NG_ADJ + (k % 5), sg[k]);
+}
+
+// ------------------------------------------------------------------ streaming + collision
+// One thread per leaf cell.  lambda_c (adjoint of the post-collision values) is
+// the transpose of the forward push: population i of x went to x + c_i, to
+// (x, opp(i)) at a wall, or to the link buffer across the interface.  Then the
+// transpose of the collision f + omega (feq(rho, u) - f) + 3 w rho (c . acc),
+// of the moments (d rho / d f_j = 1, d u_a / d f_j = (c_ja - u_a) / rho) and of
+// the strain rate S = k Pi, k = -omega / (2 rho c_s^2),
+// Pi_ab = sum c_a c_b (f - feq), with dPi_ab / df_j = c_ja c_jb - c_s^2 d_ab
+// + u_a u_b - c_ja u_b - u_a c_jb.
+template <int Q>
+__global__ void __launch_bounds__(512, 1) k_adj_collide(Ctx C, BlockShape S, const int *__restrict__ list, int nlist,
+                                                      const float *__restrict__ F, const float *__restrict__ lamN,
+                                                      float *__restrict__ lamO, const float *__restrict__ LA,
+                                                      float *MA, double *grad) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  constexpr int NS = D * (D + 1) / 2;
+  constexpr int NV = 2 + 2 * 3;  // omega per phase, acceleration per phase
+  __shared__ double red[32][NV];
+  double acc_v[NV];
+  for (int k = 0; k < NV; ++k) acc_v[k] = 0.0;
+  int cur_case = -1;
+  auto flush = [&](int case_id) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    for (int k = 0; k < NV; ++k) {
+      double s = acc_v[k];
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+      if (lane == 0) red[warp][k] = s;
+      acc_v[k] = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
+      if (s != 0.0) atomicAdd(grad + (long long)case_id * NG_ADJ + 5 + threadIdx.x, s);
+    }
+    __syncthreads();
+  };
+  for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
+    const int gb = __ldg(list + w);
+    const int4 bi = __ldg(C.blk_info + gb);
+    const LevelDev &L = C.lds[bi.x];
+    if (L.case_id != cur_case) {
+      if (cur_case >= 0) flush(cur_case);
+      cur_case = L.case_id;
+    }
+    const int t = threadIdx.x;
+    const int x = (bi.y << S.lg[0]) + (t & (S.bs[0] - 1));
+    const int y = (bi.z << S.lg[1]) + ((t >> S.lg[0]) & (S.bs[1] - 1));
+    const int z = (bi.w << S.lg[2]) + (t >> (S.lg[0] + S.lg[1]));
+    const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
+    if (x >= n0 || y >= n1 || z >= n2) continue;
+    const unsigned p0 = (unsigned)L.p[0], p01 = (unsigned)(L.p[0] * L.p[1]);
+    const unsigned c = x + p0 * y + p01 * z;
+    const uint8_t tg = C.tag[L.cell_off + c];
+    if (!(tg & TAG_LEAF)) continue;
+    const unsigned N = (unsigned)L.ncell;
+    const float *Fl = F + L.cell_off * Q;
+    const float *lN = lamN + L.cell_off * Q;
+    float *lO = lamO + L.cell_off * Q;
+    // ---- transpose of the push
+    const bool wxm = x == 0 && !L.per[0], wxp = x == n0 - 1 && !L.per[0];
+    const bool wym = y == 0 && !L.per[1], wyp = y == n1 - 1 && !L.per[1];
+    const bool wzm = D == 3 && z == 0 && !L.per[2], wzp = D == 3 && z == n2 - 1 && !L.per[2];
+    const int dxm = x > 0 ? -1 : n0 - 1, dxp = x < n0 - 1 ? 1 : 1 - n0;
+    const int dym = y > 0 ? -(int)p0 : (n1 - 1) * (int)p0, dyp = y < n1 - 1 ? (int)p0 : (1 - n1) * (int)p0;
+    const int dzm = z > 0 ? -(int)p01 : (n2 - 1) * (int)p01, dzp = z < n2 - 1 ? (int)p01 : (1 - n2) * (int)p01;
+    const bool fine = L.finest != 0;
+    uint32_t cm = 0;
+    int cb = 0;
+    if (fine && (tg & TAG_IFACE)) {
+      cm = C.cmask[L.fine_off + c];
+      cb = C.cbase[L.fine_off + c];
+    }
+    float lc[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (i == LT::REST) {
+        lc[i] = lN[LT::REST * N + c];
+        continue;
+      }
+      const int cxi = LT::cx(i), cyi = LT::cy(i), czi = LT::cz(i);
+      const int k = LT::opp(i);
+      if (cm & (1u << k)) {
+        lc[i] = 0.f;
+        continue;
+      }
+      const bool wx = (cxi < 0 && wxm) || (cxi > 0 && wxp);
+      const bool wy = (cyi < 0 && wym) || (cyi > 0 && wyp);
+      const bool wz = (czi < 0 && wzm) || (czi > 0 && wzp);
+      if (!(wx || wy || wz)) {
+        const int off = (cxi < 0 ? dxm : (cxi > 0 ? dxp : 0)) + (cyi < 0 ? dym : (cyi > 0 ? dyp : 0)) +
+                        (czi < 0 ? dzm : (czi > 0 ? dzp : 0));
+        lc[i] = lN[i * N + (unsigned)((int)c + off)];
+      } else {
+        lc[i] = lN[k * N + c];
+      }
+    }
+    if (cm) {
+#pragma unroll
+      for (int k = 0; k < Q; ++k) {
+        if (!(cm & (1u << k))) continue;
+        const long long li = cb + __popc(cm & ((1u << k) - 1u));
+        if (li >= C.link_cap) continue;
+        lc[LT::opp(k)] += LA[2 * li];
+        lc[k] += LA[2 * li + 1];
+      }
+    }
+    // ---- macro adjoint from the interface (read and cleared for the next step)
+    float mrho = 0.f, mu[3] = {0.f, 0.f, 0.f}, mS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bool has_S = false;
+    if (fine && (tg & TAG_IFACE)) {
+      const long long NF = C.nfine, fc = L.fine_off + c;
+      mrho = MA[fc];
+      MA[fc] = 0.f;
+      for (int a = 0; a < D; ++a) {
+        mu[a] = MA[(1 + a) * NF + fc];
+        MA[(1 + a) * NF + fc] = 0.f;
+      }
+      for (int s = 0; s < NS; ++s) {
+        mS[s] = MA[(1 + D + s) * NF + fc];
+        MA[(1 + D + s) * NF + fc] = 0.f;
+        has_S |= mS[s] != 0.f;
+      }
+    }
+    // ---- transpose of the collision
+    float f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = Fl[i * N + c];
+    float drho, u[3];
+    lb_moments<Q>(f, drho, u);
+    const float rho = 1.0f + drho, irho = 1.0f / rho;
+    const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const int ph = tg & TAG_GAS;
+    const float om = L.omega[ph];
+    const float ac[3] = {L.acc[ph][0], L.acc[ph][1], L.acc[ph][2]};
+    float As = 0.f, Bv[3] = {0.f, 0.f, 0.f}, lom = 0.f, lac[3] = {0.f, 0.f, 0.f};
+    float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const float cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
+      const float cu = cx * u[0] + cy * u[1] + cz * u[2];
+      const float fe = feq_dev<Q>(i, drho, u, usq);
+      const float wl = LT::w(i) * lc[i];
+      // d feq_i / d rho = feq_i / rho (full feq = w + f~eq), d feq_i / d u_a = w rho (3 c_a + 9 cu c_a - 3 u_a)
+      As += lc[i] * (om * (fe + LT::w(i)) * irho + 3.0f * LT::w(i) * (cx * ac[0] + cy * ac[1] + cz * ac[2]));
+      const float g = om * wl * rho;
+      Bv[0] += g * (3.0f * cx + 9.0f * cu * cx - 3.0f * u[0]);
+      Bv[1] += g * (3.0f * cy + 9.0f * cu * cy - 3.0f * u[1]);
+      if (D == 3) Bv[2] += g * (3.0f * cz + 9.0f * cu * cz - 3.0f * u[2]);
+      lom += lc[i] * (fe - f[i]);
+      lac[0] += 3.0f * wl * rho * cx;
+      lac[1] += 3.0f * wl * rho * cy;
+      if (D == 3) lac[2] += 3.0f * wl * rho * cz;
+      if (has_S) {
+        const float fn = f[i] - fe;
+        const float c3[3] = {cx, cy, cz};
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int b = a; b < D; ++b) P[sym<D>(a, b)] += c3[a] * c3[b] * fn;
+      }
+    }
+    float g0[3];
+    for (int a = 0; a < 3; ++a) g0[a] = (Bv[a] + mu[a]) * irho;
+    const float gu = g0[0] * u[0] + g0[1] * u[1] + g0[2] * u[2];
+    const float base = As + mrho - gu;
+    // strain-rate terms: sum_{a<=b} mS_ab k (dPi_ab/df_j - Pi_ab / rho)
+    const float kk = -1.5f * om * irho;
+    float sP = 0.f, sD = 0.f, sUU = 0.f;
+    if (has_S) {
+      // dPi_ab/df_j = c_ja c_jb - cs2 d_ab + u_a u_b - c_ja u_b - u_a c_jb; collect the j-independent parts
+      for (int a = 0; a < D; ++a)
+        for (int b = a; b < D; ++b) {
+          const float m = mS[sym<D>(a, b)];
+          sP += m * P[sym<D>(a, b)];
+          sUU += m * u[a] * u[b];
+          if (a == b) sD += m;
+        }
+      lom += sP * kk / om;  // S / omega = k Pi / omega
+    }
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      const float cj[3] = {(float)LT::cx(j), (float)LT::cy(j), (float)LT::cz(j)};
+      float v = (1.0f - om) * lc[j] + base + g0[0] * cj[0] + g0[1] * cj[1] + g0[2] * cj[2];
+      if (has_S) {
+        float t = -CS2 * sD + sUU - sP * irho;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int b = a; b < D; ++b) {
+            const float m = mS[sym<D>(a, b)];
+            // (a, b) entry; for a < b the stored m already holds both orderings
+            t += m * (cj[a] * cj[b] - cj[a] * u[b] - u[a] * cj[b]);
+          }
+        v += kk * t;
+      }
+      lO[j * N + c] = v;
+    }
+    acc_v[ph] += (double)lom;
+    for (int a = 0; a < D; ++a) acc_v[2 + 3 * ph + a] += (double)lac[a];
+  }
+  if (cur_case >= 0) flush(cur_case);
+}
+
+// ------------------------------------------------------------------ launchers
+#define LSB_ADJ_Q(Q, fn, L, ...)                                                      \
+  do {                                                                                \
+    if ((Q) == 9) fn<9><<<(L).grid, (L).block, 0, (L).stream>>>(__VA_ARGS__);         \
+    else fn<19><<<(L).grid, (L).block, 0, (L).stream>>>(__VA_ARGS__);                 \
+    return cudaGetLastError();                                                        \
+  } while (0)
+
+cudaError_t run_adj_seed(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, const float *F, float *lam,
+                         const double *wobs, const double *obs, int stride) {
+  LSB_ADJ_Q(Q, k_adj_seed, L, C, S, list, n, F, lam, wobs, obs, stride);
+}
+
+cudaError_t run_adj_links(int Q, Launch L, Ctx C, int glevel, const float *F, float *lamN, float *LA, float *MA,
+                          double *grad, int ncase) {
+  LSB_ADJ_Q(Q, k_adj_links, L, C, glevel, F, lamN, LA, MA, grad, ncase);
+}
+
+cudaError_t run_adj_collide(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, const float *F,
+                            const float *lamN, float *lamO, const float *LA, float *MA, double *grad) {
+  LSB_ADJ_Q(Q, k_adj_collide, L, C, S, list, n, F, lamN, lamO, LA, MA, grad);
+}
+
+}  // namespace lsb

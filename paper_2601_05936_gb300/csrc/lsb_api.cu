@@ -26,7 +26,9 @@ namespace {
 
 constexpr int MAXL = 4;
 const char *const KNAMES[] = {"k_collide_stream", "k_interface_bc", "k_restrict", "k_ghost", "k_prolong", "k_level_tags", "k_observables", "k_export", "k_classify_phase", "k_classify_links", "k_band", "k_geometry", "k_ext_init", "k_ext_iter", "k_adv_stage", "k_reinit_prep", "k_reinit_stage", "k_refill", "k_sensor", "k_init", "k_collect",
-                               "k_collide_stream_l1", "k_collide_stream_l2", "k_collide_stream_l3"};
+                               "k_collide_stream_l1", "k_collide_stream_l2", "k_collide_stream_l3", "k_adj_seed",
+                               "k_adj_links", "k_adj_collide"};
+constexpr int KADJ_SEED = 24, KADJ_LINKS = 25, KADJ_COLLIDE = 26;
 constexpr int NKERN = sizeof(KNAMES) / sizeof(KNAMES[0]);
 
 struct ProfRec {
@@ -115,6 +117,16 @@ struct lsb_grid {
   int tma_grid = 0;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   uint64_t gnodes[2] = {0, 0};
+  // adjoint of the frozen-interface step: recording and reverse sweep
+  int rec_on = 0, rec_every = 0;
+  long long rec_steps = 0;
+  std::vector<float *> rec_ckpt;  // state at the start of steps 0, every, 2 every, ...
+  float *d_seg = nullptr;         // states of one recomputed segment
+  int seg_cap = 0;
+  float *d_adj[2] = {nullptr, nullptr};
+  int adj_cur = -1;               // d_adj[adj_cur] holds dJ/df_0 after lsb_backward
+  float *d_fsave = nullptr, *d_madj = nullptr, *d_linkadj = nullptr;
+  double *d_grad = nullptr, *d_wobs = nullptr;
 };
 
 namespace {
@@ -684,6 +696,68 @@ lsb_status replay_two_steps(lsb_grid *g) {
   return LSB_OK;
 }
 
+// Populations of every level (floats; the adjoint needs FP32 storage).
+size_t state_floats(const lsb_grid *g) { return (size_t)g->Q * (size_t)g->ncell_total; }
+
+void rec_clear(lsb_grid *g) {
+  for (float *p : g->rec_ckpt) cudaFree(p);
+  g->rec_ckpt.clear();
+  g->rec_on = 0;
+  g->rec_steps = 0;
+  g->adj_cur = -1;
+}
+
+// Copy the current state into a new checkpoint at the start of a recorded step.
+lsb_status rec_checkpoint(lsb_grid *g) {
+  const size_t bytes = sizeof(float) * state_floats(g);
+  float *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) return fail(g, LSB_ENOMEM, "checkpoint cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  g->rec_ckpt.push_back(p);
+  CU(cudaMemcpyAsync(p, g->d_buf[g->par[0]], bytes, cudaMemcpyDeviceToDevice, g->stream));
+  return LSB_OK;
+}
+
+// Working buffers of the reverse sweep, allocated on first use.
+lsb_status adj_buffers(lsb_grid *g, int seg_len) {
+  const size_t sb = sizeof(float) * state_floats(g);
+  const int MF = 1 + g->D + g->D * (g->D + 1) / 2;
+  if (!g->d_adj[0]) {
+    TRY(dalloc(g, &g->d_adj[0], sb));
+    TRY(dalloc(g, &g->d_adj[1], sb));
+    TRY(dalloc(g, &g->d_fsave, sb));
+    TRY(dalloc(g, &g->d_madj, sizeof(float) * (size_t)MF * g->nfine));
+    TRY(dalloc(g, &g->d_linkadj, sizeof(float) * 2 * (size_t)g->link_cap));
+    TRY(dalloc(g, &g->d_grad, sizeof(double) * NG_ADJ * g->ncase));
+    TRY(dalloc(g, &g->d_wobs, sizeof(double) * (4 + 2 * g->D) * g->ncase));
+    CU(cudaMemsetAsync(g->d_madj, 0, sizeof(float) * (size_t)MF * g->nfine, g->stream));
+  }
+  if (seg_len > g->seg_cap) {
+    if (g->d_seg) cudaFree(g->d_seg);
+    g->d_seg = nullptr;
+    g->seg_cap = 0;
+    cudaError_t e = cudaMalloc(&g->d_seg, sb * (size_t)seg_len);
+    if (e != cudaSuccess) return fail(g, LSB_ENOMEM, "segment store cudaMalloc(%zu): %s", sb * seg_len,
+                                      cudaGetErrorString(e));
+    g->seg_cap = seg_len;
+  }
+  return LSB_OK;
+}
+
+// One reverse step: lambda_n from lambda_{n+1} = d_adj[cur] at the state F = f_n.
+lsb_status adj_step(lsb_grid *g, const float *F, int cur) {
+  Ctx C = make_ctx(g);
+  BlockShape S = shape(g);
+  const int Q = g->Q;
+  RUN(KADJ_LINKS, 0, 1, 128, run_adj_links, Q, LN(g, DYN_GRID, 128), C, 0, F, g->d_adj[cur], g->d_linkadj,
+      g->d_madj, g->d_grad, g->ncase);
+  const int grid = std::min(g->cs[0].n, 152 * 2);
+  RUN(KADJ_COLLIDE, 3.0 * Q * sizeof(float) * g->leaf_cells[0], g->cs[0].n, g->nthreads, run_adj_collide, Q,
+      LN(g, grid, g->nthreads), C, S, (const int *)g->cs[0].d, g->cs[0].n, F, g->d_adj[cur], g->d_adj[1 - cur],
+      g->d_linkadj, g->d_madj, g->d_grad);
+  return LSB_OK;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -892,6 +966,7 @@ lsb_status lsb_set_params(lsb_grid *g, int case_idx, const lsb_params *params) {
   }
   if (params->n_ext != g->n_ext || params->reinit_every != g->reinit_every || params->n_reinit != g->n_reinit)
     if (g->ncase > 1 && case_idx != -1) return fail(g, LSB_EINVAL, "level-set iteration counts are shared by all cases");
+  if (g->rec_on) rec_clear(g);  // a recording covers one parameter set
   for (int c = 0; c < g->ncase; ++c) {
     if (case_idx != -1 && c != case_idx) continue;
     g->cases[c].p = *params;
@@ -908,6 +983,18 @@ lsb_status lsb_set_params(lsb_grid *g, int case_idx, const lsb_params *params) {
 
 lsb_status lsb_step(lsb_grid *g, int n) {
   if (!g || n < 0) return LSB_EINVAL;
+  if (g->rec_on) {  // recorded steps run eagerly, checkpointing every rec_every steps
+    for (int k = 0; k < n; ++k) {
+      if (g->rec_steps % g->rec_every == 0 && (size_t)(g->rec_steps / g->rec_every) == g->rec_ckpt.size())
+        TRY(rec_checkpoint(g));
+      TRY(advance(g, 0));
+      g->updates_done += updates_per_step(g);
+      g->coarse_steps++;
+      g->rec_steps++;
+      g->adj_cur = -1;
+    }
+    return LSB_OK;
+  }
   int k = 0;
   while (k < n) {
     const bool regrid_on = g->regrid_every > 0 && g->Lmax > 1;
@@ -937,6 +1024,7 @@ lsb_status lsb_use_graphs(lsb_grid *g, int enable) {
 
 lsb_status lsb_refine(lsb_grid *g) {
   if (!g) return LSB_EINVAL;
+  if (g->rec_on) rec_clear(g);
   return regrid(g, false);
 }
 
@@ -966,7 +1054,7 @@ size_t lsb_field_bytes(const lsb_grid *g, int case_idx, int field, int level) {
     case LSB_FIELD_RHO: case LSB_FIELD_PHI: case LSB_FIELD_KAPPA: return 4 * n;
     case LSB_FIELD_U: case LSB_FIELD_UEXT: return 4 * n * g->D;
     case LSB_FIELD_PHASE: case LSB_FIELD_TAG: return n;
-    case LSB_FIELD_F: return 4 * n * g->Q;
+    case LSB_FIELD_F: case LSB_FIELD_ADJ_F: return 4 * n * g->Q;
     case LSB_FIELD_BLOCKS: return (size_t)L.nblock;
     case LSB_FIELD_CUTMASK: return 4 * n;
     default: return 0;
@@ -1015,6 +1103,12 @@ lsb_status lsb_get_fields(lsb_grid *g, int case_idx, int field, int level, void 
     case LSB_FIELD_KAPPA: src = g->d_kappa + L.fine_off; break;
     case LSB_FIELD_CUTMASK: src = g->d_cmask + L.fine_off; break;
     case LSB_FIELD_UEXT: src = g->d_ut[0] + L.fine_off; planes = g->D; plane_stride = g->nfine; break;
+    case LSB_FIELD_ADJ_F:
+      if (g->adj_cur < 0) return fail(g, LSB_ESTATE, "no adjoint field: call lsb_backward first");
+      src = g->d_adj[g->adj_cur] + L.cell_off * g->Q;
+      planes = g->Q;
+      plane_stride = L.ncell;
+      break;
     case LSB_FIELD_PHASE: case LSB_FIELD_TAG: src = g->d_tag + L.cell_off; esz = 1; break;
     default: return fail(g, LSB_EINVAL, "field");
   }
@@ -1117,9 +1211,94 @@ const char *lsb_kernel_name(int k) { return (k >= 0 && k < NKERN) ? KNAMES[k] : 
 
 int lsb_kernel_count(void) { return NKERN; }
 
-lsb_status lsb_backward(lsb_grid *g, const double *, double *, float *) {
-  if (!g) return LSB_EINVAL;
-  return fail(g, LSB_ESTATE, "the adjoint is not available in this build");
+lsb_status lsb_record(lsb_grid *g, int checkpoint_every) {
+  if (!g || checkpoint_every < 1) return LSB_EINVAL;
+  if (g->Lmax != 1) return fail(g, LSB_ESTATE, "the adjoint covers single-level grids");
+  if (g->storage != LSB_FP32) return fail(g, LSB_ESTATE, "the adjoint needs FP32 population storage");
+  for (const CaseHost &c : g->cases)
+    if (c.p.ls_active) return fail(g, LSB_ESTATE, "the adjoint needs a frozen level set (ls_active = 0)");
+  CU(cudaStreamSynchronize(g->stream));
+  rec_clear(g);
+  g->rec_on = 1;
+  g->rec_every = checkpoint_every;
+  return LSB_OK;
+}
+
+lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, float *dJ_dphi0) {
+  if (!g || !dJ_dobs) return LSB_EINVAL;
+  if (dJ_dphi0) return fail(g, LSB_EINVAL, "dJ/dphi0 is not computed: pass NULL");
+  if (!g->rec_on) return fail(g, LSB_ESTATE, "no recording: call lsb_record before the steps to differentiate");
+  const int Q = g->Q, D = g->D, stride = 4 + 2 * D;
+  const long long T = g->rec_steps;
+  const int every = g->rec_every;
+  TRY(adj_buffers(g, (int)std::min<long long>(every, std::max<long long>(T, 1))));
+  const size_t sf = state_floats(g), sb = sizeof(float) * sf;
+  const int MF = 1 + D + D * (D + 1) / 2;
+  CU(cudaMemsetAsync(g->d_adj[0], 0, sb, g->stream));
+  CU(cudaMemsetAsync(g->d_adj[1], 0, sb, g->stream));
+  CU(cudaMemsetAsync(g->d_madj, 0, sizeof(float) * (size_t)MF * g->nfine, g->stream));
+  CU(cudaMemsetAsync(g->d_grad, 0, sizeof(double) * NG_ADJ * g->ncase, g->stream));
+  CU(cudaMemcpyAsync(g->d_wobs, dJ_dobs, sizeof(double) * stride * g->ncase, cudaMemcpyHostToDevice, g->stream));
+  // the final state; restored when the sweep is done
+  const int par0 = g->par[0];
+  const long long fs0 = g->fine_steps[0], cs0 = g->coarse_steps;
+  const double ud0 = g->updates_done;
+  CU(cudaMemcpyAsync(g->d_fsave, g->d_buf[par0], sb, cudaMemcpyDeviceToDevice, g->stream));
+  Ctx C = make_ctx(g);
+  BlockShape S = shape(g);
+  CU(cudaMemsetAsync(g->d_obs, 0, sizeof(double) * stride * g->ncase, g->stream));
+  const int og = std::min(g->leaf.n, 152 * 4);
+  RUN(6, 0, g->leaf.n, g->nthreads, run_observables, Q, g->storage, LN(g, og, g->nthreads), C, S,
+      (const int *)g->leaf.d, g->leaf.n, g->d_obs, stride);
+  RUN(KADJ_SEED, 0, g->leaf.n, g->nthreads, run_adj_seed, Q, LN(g, std::min(g->leaf.n, 152 * 8), g->nthreads), C,
+      S, (const int *)g->leaf.d, g->leaf.n, (const float *)g->d_fsave, g->d_adj[0], g->d_wobs, g->d_obs, stride);
+  int cur = 0;
+  lsb_status st = LSB_OK;
+  const long long nseg = (T + every - 1) / every;
+  for (long long sgi = nseg - 1; sgi >= 0 && st == LSB_OK; --sgi) {
+    const long long start = sgi * every;
+    const int len = (int)std::min<long long>(every, T - start);
+    // recompute the segment from its checkpoint, keeping every state
+    cudaError_t e = cudaMemcpyAsync(g->d_buf[g->par[0]], g->rec_ckpt[sgi], sb, cudaMemcpyDeviceToDevice, g->stream);
+    if (e != cudaSuccess) { st = fail(g, LSB_ECUDA, "checkpoint restore: %s", cudaGetErrorString(e)); break; }
+    for (int j = 0; j < len && st == LSB_OK; ++j) {
+      e = cudaMemcpyAsync(g->d_seg + sf * j, g->d_buf[g->par[0]], sb, cudaMemcpyDeviceToDevice, g->stream);
+      if (e != cudaSuccess) { st = fail(g, LSB_ECUDA, "segment store: %s", cudaGetErrorString(e)); break; }
+      st = advance(g, 0);
+    }
+    for (int j = len - 1; j >= 0 && st == LSB_OK; --j) {
+      st = adj_step(g, g->d_seg + sf * j, cur);
+      cur ^= 1;
+    }
+  }
+  g->par[0] = par0;
+  g->fine_steps[0] = fs0;
+  g->coarse_steps = cs0;
+  g->updates_done = ud0;
+  CU(cudaMemcpyAsync(g->d_buf[par0], g->d_fsave, sb, cudaMemcpyDeviceToDevice, g->stream));
+  if (st != LSB_OK) return st;
+  // classification of the final state (the recomputation left that of an earlier step)
+  TRY(classify(g, 0, 0));
+  std::vector<double> h((size_t)NG_ADJ * g->ncase);
+  CU(cudaMemcpyAsync(h.data(), g->d_grad, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g->stream));
+  TRY(lsb_sync(g));
+  g->adj_cur = cur;
+  if (dJ_dparams) {
+    for (int c = 0; c < g->ncase; ++c) {
+      const lsb_params &p = g->cases[c].p;
+      const double *gr = h.data() + (size_t)NG_ADJ * c;
+      double *o = dJ_dparams + (size_t)LSB_NPARAM_ADJ * c;
+      o[0] = gr[0];
+      for (int ph = 0; ph < 2; ++ph) {
+        const double om = 1.0 / (3.0 * p.nu[ph] + 0.5);
+        double dacc = 0.0;
+        for (int a = 0; a < D; ++a) dacc += gr[7 + 3 * ph + a] * (-p.body_force[a] / (p.rho[ph] * p.rho[ph]));
+        o[1 + ph] = gr[1 + ph] + gr[3 + ph] * p.nu[ph] + dacc;
+        o[3 + ph] = gr[3 + ph] * p.rho[ph] + gr[5 + ph] * (-3.0 * om * om);
+      }
+    }
+  }
+  return LSB_OK;
 }
 
 lsb_status lsb_get_fields_noalloc(lsb_grid *g, int case_idx, int field, int level, void *dst, size_t dst_bytes,

@@ -61,6 +61,34 @@ template <> struct Lat<19> {
   }
 };
 
+// ---------------------------------------------------------------- moments and equilibrium
+// Eq. macro on deviations f~ = f - w: drho = sum f~, u = sum c f~ / (1 + drho).
+template <int Q>
+__device__ __forceinline__ void lb_moments(const float *f, float &drho, float u[3]) {
+  using LT = Lat<Q>;
+  float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    d += f[i];
+    jx += LT::cx(i) * f[i];
+    jy += LT::cy(i) * f[i];
+    if (LT::D == 3) jz += LT::cz(i) * f[i];
+  }
+  float inv = 1.0f / (1.0f + d);
+  drho = d;
+  u[0] = jx * inv;
+  u[1] = jy * inv;
+  u[2] = jz * inv;
+}
+
+// Deviation of Eq. feq from the rest weights: f~eq_i = feq_i - w_i.
+template <int Q>
+__device__ __forceinline__ float feq_dev(int i, float drho, const float u[3], float usq) {
+  using LT = Lat<Q>;
+  float cu = LT::cx(i) * u[0] + LT::cy(i) * u[1] + LT::cz(i) * u[2];
+  return LT::w(i) * (drho + (1.0f + drho) * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
+}
+
 // ---------------------------------------------------------------- grid descriptors
 enum : int8_t { BLK_INACTIVE = 0, BLK_LEAF = 1, BLK_REFINED = 2 };
 

@@ -1,5 +1,5 @@
 // Host launchers of the lsb kernels.  Each is defined in the translation unit
-// that defines its kernel (lsb_lb.cu, lsb_ls.cu), so the launch and the kernel
+// that defines its kernel (lsb_lb.cu, lsb_ls.cu, lsb_adj.cu), so the launch and the kernel
 // registration live together; (Q, storage) pick the template instance.
 #pragma once
 #include <cuda.h>
@@ -51,5 +51,14 @@ cudaError_t run_reinit_prep(int Q, Launch L, Ctx C, BlockShape S, int glevel);
 cudaError_t run_reinit_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage);
 cudaError_t run_refill(int Q, int st, Launch L, Ctx C, int glevel);
 cudaError_t run_sensor(Launch L, Ctx C, BlockShape S, const int *list, int n, int mode, float *out);
+
+// lsb_adj.cu: adjoint of the frozen-interface step
+constexpr int NG_ADJ = 13;  // parameter partials per case accumulated on the device
+cudaError_t run_adj_seed(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, const float *F, float *lam,
+                         const double *wobs, const double *obs, int stride);
+cudaError_t run_adj_links(int Q, Launch L, Ctx C, int glevel, const float *F, float *lamN, float *LA, float *MA,
+                          double *grad, int ncase);
+cudaError_t run_adj_collide(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, const float *F,
+                            const float *lamN, float *lamO, const float *LA, float *MA, double *grad);
 
 }  // namespace lsb

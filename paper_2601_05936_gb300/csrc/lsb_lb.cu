@@ -18,32 +18,6 @@
 
 namespace lsb {
 
-// ------------------------------------------------------------------ helpers
-template <int Q>
-__device__ __forceinline__ void lb_moments(const float *f, float &drho, float u[3]) {
-  using LT = Lat<Q>;
-  float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    d += f[i];
-    jx += LT::cx(i) * f[i];
-    jy += LT::cy(i) * f[i];
-    if (LT::D == 3) jz += LT::cz(i) * f[i];
-  }
-  float inv = 1.0f / (1.0f + d);
-  drho = d;
-  u[0] = jx * inv;
-  u[1] = jy * inv;
-  u[2] = jz * inv;
-}
-
-template <int Q>
-__device__ __forceinline__ float feq_dev(int i, float drho, const float u[3], float usq) {
-  using LT = Lat<Q>;
-  float cu = LT::cx(i) * u[0] + LT::cy(i) * u[1] + LT::cz(i) * u[2];
-  return LT::w(i) * (drho + (1.0f + drho) * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
-}
-
 // BGK collision with forcing (Eq. 1), in place; optionally returns the strain rate.
 template <int Q, bool WANT_S>
 __device__ __forceinline__ void lb_collide(float *f, float om, const float acc[3], float &drho,

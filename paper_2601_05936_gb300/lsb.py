@@ -18,7 +18,8 @@ D2Q9, D3Q19 = 0, 1
 PERIODIC, WALL = 0, 1
 FP32, FP16S = 0, 1
 SENSOR_BAND, SENSOR_SIGNED = 0, 1
-FIELD = dict(rho=0, u=1, phi=2, phase=3, f=4, tag=5, blocks=6, cutmask=7, kappa=8, uext=9)
+FIELD = dict(rho=0, u=1, phi=2, phase=3, f=4, tag=5, blocks=6, cutmask=7, kappa=8, uext=9, adj_f=10)
+NPARAM_ADJ = 5  # sigma, rho[0], rho[1], nu[0], nu[1]
 STATUS = {0: "LSB_OK", 1: "LSB_EINVAL", 2: "LSB_ENOMEM", 3: "LSB_ECUDA", 4: "LSB_EUNSTABLE",
           5: "LSB_ETIMEOUT", 6: "LSB_ESTATE"}
 
@@ -70,6 +71,7 @@ def load():
     lib.lsb_observables.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]
     lib.lsb_cell_updates.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.lsb_backward.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
+    lib.lsb_record.argtypes = [vp, ctypes.c_int]
     lib.lsb_sync.argtypes = [vp]
     lib.lsb_kernel_launches.argtypes = [vp]
     lib.lsb_kernel_launches.restype = ctypes.c_uint64
@@ -87,7 +89,7 @@ def load():
     lib.lsb_kernel_count.argtypes = []
     lib.lsb_kernel_count.restype = ctypes.c_int
     for name in ("lsb_use_graphs", "lsb_get_fields_noalloc", "lsb_profile", "lsb_profile_read", "lsb_create_grid", "lsb_set_params", "lsb_step", "lsb_refine", "lsb_get_fields",
-                 "lsb_observables", "lsb_cell_updates", "lsb_backward", "lsb_sync"):
+                 "lsb_observables", "lsb_cell_updates", "lsb_backward", "lsb_record", "lsb_sync"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -278,11 +280,22 @@ class Grid:
     def kernel_launches(self):
         return int(self.lib.lsb_kernel_launches(self.h))
 
+    def record(self, checkpoint_every=100):
+        """Start recording the following steps for backward (frozen level set, one level, FP32)."""
+        self._check(self.lib.lsb_record(self.h, int(checkpoint_every)))
+
     def backward(self, dJ_dobs):
-        buf = (ctypes.c_double * len(dJ_dobs))(*dJ_dobs)
-        out = (ctypes.c_double * 3)()
-        self._check(self.lib.lsb_backward(self.h, buf, out, None))
-        return np.ctypeslib.as_array(out).copy()
+        """Reverse sweep over the recorded steps for J = sum of dJ_dobs . observables
+        (dJ_dobs: n_cases x (4 + 2 D), observables order).  Returns dJ/dp, shape
+        (n_cases, 5): sigma, rho[0], rho[1], nu[0], nu[1]."""
+        w = np.ascontiguousarray(np.asarray(dJ_dobs, dtype=np.float64).reshape(-1))
+        nc = len(self.cases)
+        if w.size != nc * (4 + 2 * self.D):
+            raise ValueError("dJ_dobs needs n_cases x (4 + 2 D) values")
+        out = np.zeros(nc * NPARAM_ADJ, dtype=np.float64)
+        self._check(self.lib.lsb_backward(self.h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None))
+        return out.reshape(nc, NPARAM_ADJ)
 
     def close(self):
         if getattr(self, "h", None):
