@@ -134,6 +134,87 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def adjoint_bench(args, world, rank, local, barrier, dist):
+    """Reverse sweep of the frozen-interface adjoint: single-level 128x128x256 D3Q19
+    box with the bubble of the benchmark workload (d = 32 cells, density ratio
+    1000), level set frozen.  A step of the metric is one adjoint step of the
+    sweep: recomputation of the forward step from the segment checkpoint, the
+    segment-store copy, the cut-link and the per-cell adjoint kernels."""
+    import torch
+    from paper_2601_05936_gb300 import autograd, lsb, workloads
+    case = workloads.rising_bubble_3d(levels=1)
+    case.update(ls_active=False, n_ext=0, reinit_every=0, regrid_every=0)
+    stream = torch.cuda.Stream()
+    g = lsb.Grid(case, stream=stream, device=local)
+    g.step(args.warmup)
+    g.record(args.checkpoint_every)
+    g.step(args.steps)
+    D = g.D
+    w = np.zeros((1, 4 + 2 * D))
+    w[0, 4 + 2 * D - 1] = 1.0  # vertical gas velocity
+    g.backward(w)  # warm-up sweep (allocates the segment store)
+    g.sync()
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    g.profile(2)
+    launches0 = g.kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    dp = g.backward(w)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = g.profile_read()
+    g.profile(0)
+    clk = clocks.stop()
+    launches = g.kernel_launches() - launches0
+    cells = g.cell_updates()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t[0])
+    value = world * cells * args.steps / (ms_max / 1e3) / 1e6
+    hbm, src = peaks()
+    kms, kn, kb = prof.get("k_adj_collide", (0.0, 0, 0.0))
+    achieved = kb / (kms / 1e3) / 1e9 if kms > 0 else None
+    roof = dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm if achieved else None,
+                traffic=None, peak_source=src + " (hbm_gbs, of " + src + ")", kernel="k_adj_collide", launches=kn,
+                bytes_per_launch=kb / max(kn, 1), avg_launch_ms=kms / max(kn, 1),
+                share_of_step=kms / ms if ms > 0 else None,
+                kernels={k: dict(ms=v[0], launches=v[1]) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])})
+    # end to end through the public API: autograd window (forward recorded steps + reverse sweep),
+    # parameters from a host tensor, gradient back on the host
+    E = max(1, min(args.steps, 50))
+    p = autograd.params_tensor([case])
+    g.sync()
+    t0 = time.perf_counter()
+    obs = autograd.window(g, p, E, checkpoint_every=args.checkpoint_every)
+    (grad,) = torch.autograd.grad(obs[0, 4 + 2 * D - 1], p)
+    t1 = time.perf_counter()
+    e2e = dict(value=world * cells * E / (t1 - t0) / 1e6, unit="MLUPS", h2d_bytes_per_step=8 * 5 / E,
+               d2h_bytes_per_step=(8 * (4 + 2 * D) + 8 * 5) / E, steps=E,
+               note="autograd.window(E steps) + torch.autograd.grad per window, host wall clock: "
+                    "forward recorded steps and the reverse sweep, MLUPS of one adjoint step each")
+    g.close()
+    if rank != 0:
+        return
+    line = dict(metric="MLUPS of the reverse sweep (adjoint cell steps / s), 3D D3Q19 frozen bubble 128x128x256",
+                value=value, unit="MLUPS", n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=ms_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32", data="synthetic",
+                config=dict(workload=case["name"] + "_frozen", lattice="D3Q19", levels=1, storage="fp32",
+                            parallelism=f"replicas{world}", checkpoint_every=args.checkpoint_every,
+                            cells=cells, l2_flush="state 318 MB x (segment store) >> 129 MB L2",
+                            dJ_dparams=[float(v) for v in dp[0]]),
+                roofline=roof, cpu_baseline=None, e2e=e2e, gpu_launches=launches, clocks=clk)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -144,9 +225,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-all", action="store_true", help="print a per-kernel time table to stderr")
-    ap.add_argument("--workload", default="bubble3d", choices=["bubble3d", "box3d", "ensemble"],
+    ap.add_argument("--workload", default="bubble3d", choices=["bubble3d", "box3d", "ensemble", "adjoint3d"],
                     help="bubble3d: the benchmark configuration; box3d: uniform periodic 128^3 box "
-                         "(collide-and-stream only, for profiling captures); ensemble: 64 uneven 2D bubbles")
+                         "(collide-and-stream only, for profiling captures); ensemble: 64 uneven 2D bubbles; "
+                         "adjoint3d: reverse sweep over --steps recorded steps of a frozen 3D bubble")
+    ap.add_argument("--checkpoint-every", type=int, default=100)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -171,6 +254,9 @@ def main():
     __graft_entry__.build()
     from paper_2601_05936_gb300 import lsb, workloads
 
+    if args.workload == "adjoint3d":
+        adjoint_bench(args, world, rank, local, barrier, dist)
+        return
     if args.workload == "bubble3d":
         case = workloads.rising_bubble_3d(storage=args.storage)
         cases = [case]

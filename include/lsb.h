@@ -77,7 +77,7 @@ typedef struct {
   int base[3];          /* base-level cells per axis (base[2] ignored in 2D)         */
   int n_levels;         /* total levels including the base (1 = uniform), <= 4       */
   int block[3];         /* block edge in cells, powers of two, same on every level;
-                           their product is a multiple of 32 and at most 1024       */
+                           their product is a multiple of 32 and at most 512        */
   int bc[3];            /* per axis: LSB_PERIODIC or LSB_WALL (walls on cell faces)  */
   double wall_u[6][3];  /* velocity of faces x-, x+, y-, y+, z-, z+                  */
   int storage;          /* LSB_FP32 or LSB_FP16S; all cases of a handle share it     */

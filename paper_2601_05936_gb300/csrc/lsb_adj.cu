@@ -16,8 +16,10 @@
 //                   strain rate of both link cells (macro adjoint, atomics)
 //                   and to sigma, the densities and the dynamic viscosities
 //   k_adj_collide   per cell: transpose of the push (a gather), plus the
-//                   link-buffer terms, then of the collision, the moments and
-//                   the strain rate; omega and acceleration partials
+//                   link-buffer terms, then of the collision and the moments;
+//                   omega and acceleration partials
+//   k_adj_macro     per interface cell: the moment and strain-rate adjoints
+//                   of the cut links carried to the populations
 //
 // Precision: lambda and the Jacobians in FP32 (the forward arithmetic), every
 // parameter partial summed in FP64.
@@ -288,27 +290,25 @@ template <int Q>
 __global__ void __launch_bounds__(512, 1) k_adj_collide(Ctx C, BlockShape S, const int *__restrict__ list, int nlist,
                                                       const float *__restrict__ F, const float *__restrict__ lamN,
                                                       float *__restrict__ lamO, const float *__restrict__ LA,
-                                                      float *MA, double *grad) {
+                                                      double *grad) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   constexpr int NS = D * (D + 1) / 2;
   constexpr int NV = 2 + 2 * 3;  // omega per phase, acceleration per phase
+  // per-warp FP64 partial sums in shared memory (no loop-carried registers)
   __shared__ double red[32][NV];
-  double acc_v[NV];
-  for (int k = 0; k < NV; ++k) acc_v[k] = 0.0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int k = threadIdx.x; k < 32 * NV; k += blockDim.x) red[k / NV][k % NV] = 0.0;
+  __syncthreads();
   int cur_case = -1;
   auto flush = [&](int case_id) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    for (int k = 0; k < NV; ++k) {
-      double s = acc_v[k];
-      for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-      if (lane == 0) red[warp][k] = s;
-      acc_v[k] = 0.0;
-    }
     __syncthreads();
     if (threadIdx.x < NV) {
       double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
+      for (int w = 0; w < nw; ++w) {
+        s += red[w][threadIdx.x];
+        red[w][threadIdx.x] = 0.0;
+      }
       if (s != 0.0) atomicAdd(grad + (long long)case_id * NG_ADJ + 5 + threadIdx.x, s);
     }
     __syncthreads();
@@ -321,16 +321,20 @@ __global__ void __launch_bounds__(512, 1) k_adj_collide(Ctx C, BlockShape S, con
       if (cur_case >= 0) flush(cur_case);
       cur_case = L.case_id;
     }
+    float part[NV];  // this cell's omega and acceleration partials, by phase
+#pragma unroll
+    for (int k = 0; k < NV; ++k) part[k] = 0.f;
+    do {
     const int t = threadIdx.x;
     const int x = (bi.y << S.lg[0]) + (t & (S.bs[0] - 1));
     const int y = (bi.z << S.lg[1]) + ((t >> S.lg[0]) & (S.bs[1] - 1));
     const int z = (bi.w << S.lg[2]) + (t >> (S.lg[0] + S.lg[1]));
     const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
-    if (x >= n0 || y >= n1 || z >= n2) continue;
+    if (x >= n0 || y >= n1 || z >= n2) break;
     const unsigned p0 = (unsigned)L.p[0], p01 = (unsigned)(L.p[0] * L.p[1]);
     const unsigned c = x + p0 * y + p01 * z;
     const uint8_t tg = C.tag[L.cell_off + c];
-    if (!(tg & TAG_LEAF)) continue;
+    if (!(tg & TAG_LEAF)) break;
     const unsigned N = (unsigned)L.ncell;
     const float *Fl = F + L.cell_off * Q;
     const float *lN = lamN + L.cell_off * Q;
@@ -349,17 +353,21 @@ __global__ void __launch_bounds__(512, 1) k_adj_collide(Ctx C, BlockShape S, con
       cm = C.cmask[L.fine_off + c];
       cb = C.cbase[L.fine_off + c];
     }
+    // lc: adjoint of the post-collision populations.  Held in registers with up to
+    // 128 of them per thread (one CTA of 512 per SM): more loads in flight per
+    // thread measured faster than two CTAs per SM with lc in shared memory.
     float lc[Q];
+#define LC(i) lc[(i)]
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if (i == LT::REST) {
-        lc[i] = lN[LT::REST * N + c];
+        LC(i) = lN[LT::REST * N + c];
         continue;
       }
       const int cxi = LT::cx(i), cyi = LT::cy(i), czi = LT::cz(i);
       const int k = LT::opp(i);
       if (cm & (1u << k)) {
-        lc[i] = 0.f;
+        LC(i) = 0.f;
         continue;
       }
       const bool wx = (cxi < 0 && wxm) || (cxi > 0 && wxp);
@@ -368,9 +376,9 @@ __global__ void __launch_bounds__(512, 1) k_adj_collide(Ctx C, BlockShape S, con
       if (!(wx || wy || wz)) {
         const int off = (cxi < 0 ? dxm : (cxi > 0 ? dxp : 0)) + (cyi < 0 ? dym : (cyi > 0 ? dyp : 0)) +
                         (czi < 0 ? dzm : (czi > 0 ? dzp : 0));
-        lc[i] = lN[i * N + (unsigned)((int)c + off)];
+        LC(i) = lN[i * N + (unsigned)((int)c + off)];
       } else {
-        lc[i] = lN[k * N + c];
+        LC(i) = lN[k * N + c];
       }
     }
     if (cm) {
@@ -379,105 +387,160 @@ __global__ void __launch_bounds__(512, 1) k_adj_collide(Ctx C, BlockShape S, con
         if (!(cm & (1u << k))) continue;
         const long long li = cb + __popc(cm & ((1u << k) - 1u));
         if (li >= C.link_cap) continue;
-        lc[LT::opp(k)] += LA[2 * li];
-        lc[k] += LA[2 * li + 1];
+        LC(LT::opp(k)) += LA[2 * li];
+        LC(k) += LA[2 * li + 1];
       }
     }
-    // ---- macro adjoint from the interface (read and cleared for the next step)
-    float mrho = 0.f, mu[3] = {0.f, 0.f, 0.f}, mS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    bool has_S = false;
-    if (fine && (tg & TAG_IFACE)) {
-      const long long NF = C.nfine, fc = L.fine_off + c;
-      mrho = MA[fc];
-      MA[fc] = 0.f;
-      for (int a = 0; a < D; ++a) {
-        mu[a] = MA[(1 + a) * NF + fc];
-        MA[(1 + a) * NF + fc] = 0.f;
-      }
-      for (int s = 0; s < NS; ++s) {
-        mS[s] = MA[(1 + D + s) * NF + fc];
-        MA[(1 + D + s) * NF + fc] = 0.f;
-        has_S |= mS[s] != 0.f;
-      }
-    }
-    // ---- transpose of the collision
-    float f[Q];
+    // ---- transpose of the collision.  f enters only through drho, j and
+    // sum lc_i f~_i (omega partial), so it is streamed once and not kept.  The
+    // interface cells' moment and strain-rate adjoints are added by k_adj_macro.
+    float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, slf = 0.f;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = Fl[i * N + c];
-    float drho, u[3];
-    lb_moments<Q>(f, drho, u);
-    const float rho = 1.0f + drho, irho = 1.0f / rho;
+    for (int i = 0; i < Q; ++i) {
+      const float fi = Fl[i * N + c];
+      d += fi;
+      jx += LT::cx(i) * fi;
+      jy += LT::cy(i) * fi;
+      if (D == 3) jz += LT::cz(i) * fi;
+      slf += LC(i) * fi;
+    }
+    const float drho = d, rho = 1.0f + d, irho = 1.0f / rho;
+    const float u[3] = {jx * irho, jy * irho, jz * irho};
     const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const int ph = tg & TAG_GAS;
     const float om = L.omega[ph];
     const float ac[3] = {L.acc[ph][0], L.acc[ph][1], L.acc[ph][2]};
-    float As = 0.f, Bv[3] = {0.f, 0.f, 0.f}, lom = 0.f, lac[3] = {0.f, 0.f, 0.f};
-    float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float As = 0.f, Bv[3] = {0.f, 0.f, 0.f}, slfe = 0.f, lac[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const float cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
       const float cu = cx * u[0] + cy * u[1] + cz * u[2];
       const float fe = feq_dev<Q>(i, drho, u, usq);
-      const float wl = LT::w(i) * lc[i];
+      const float l = LC(i);
+      const float wl = LT::w(i) * l;
       // d feq_i / d rho = feq_i / rho (full feq = w + f~eq), d feq_i / d u_a = w rho (3 c_a + 9 cu c_a - 3 u_a)
-      As += lc[i] * (om * (fe + LT::w(i)) * irho + 3.0f * LT::w(i) * (cx * ac[0] + cy * ac[1] + cz * ac[2]));
+      As += l * (om * (fe + LT::w(i)) * irho + 3.0f * LT::w(i) * (cx * ac[0] + cy * ac[1] + cz * ac[2]));
       const float g = om * wl * rho;
       Bv[0] += g * (3.0f * cx + 9.0f * cu * cx - 3.0f * u[0]);
       Bv[1] += g * (3.0f * cy + 9.0f * cu * cy - 3.0f * u[1]);
       if (D == 3) Bv[2] += g * (3.0f * cz + 9.0f * cu * cz - 3.0f * u[2]);
-      lom += lc[i] * (fe - f[i]);
+      slfe += l * fe;
       lac[0] += 3.0f * wl * rho * cx;
       lac[1] += 3.0f * wl * rho * cy;
       if (D == 3) lac[2] += 3.0f * wl * rho * cz;
-      if (has_S) {
-        const float fn = f[i] - fe;
-        const float c3[3] = {cx, cy, cz};
-#pragma unroll
-        for (int a = 0; a < D; ++a)
-#pragma unroll
-          for (int b = a; b < D; ++b) P[sym<D>(a, b)] += c3[a] * c3[b] * fn;
-      }
     }
+    const float lom = slfe - slf;  // sum lc_i (feq_i - f_i)
     float g0[3];
-    for (int a = 0; a < 3; ++a) g0[a] = (Bv[a] + mu[a]) * irho;
-    const float gu = g0[0] * u[0] + g0[1] * u[1] + g0[2] * u[2];
-    const float base = As + mrho - gu;
-    // strain-rate terms: sum_{a<=b} mS_ab k (dPi_ab/df_j - Pi_ab / rho)
-    const float kk = -1.5f * om * irho;
-    float sP = 0.f, sD = 0.f, sUU = 0.f;
-    if (has_S) {
-      // dPi_ab/df_j = c_ja c_jb - cs2 d_ab + u_a u_b - c_ja u_b - u_a c_jb; collect the j-independent parts
-      for (int a = 0; a < D; ++a)
-        for (int b = a; b < D; ++b) {
-          const float m = mS[sym<D>(a, b)];
-          sP += m * P[sym<D>(a, b)];
-          sUU += m * u[a] * u[b];
-          if (a == b) sD += m;
-        }
-      lom += sP * kk / om;  // S / omega = k Pi / omega
+    for (int a = 0; a < 3; ++a) g0[a] = Bv[a] * irho;
+    const float base = As - (g0[0] * u[0] + g0[1] * u[1] + g0[2] * u[2]);
+#pragma unroll
+    for (int j = 0; j < Q; ++j)
+      lO[j * N + c] = (1.0f - om) * LC(j) + base + g0[0] * LT::cx(j) + g0[1] * LT::cy(j) + g0[2] * LT::cz(j);
+    const float wl = ph ? 0.f : 1.f, wg = ph ? 1.f : 0.f;
+    part[0] = wl * lom;
+    part[1] = wg * lom;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      part[2 + a] = wl * lac[a];
+      part[5 + a] = wg * lac[a];
     }
+#undef LC
+    } while (false);
 #pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      const float cj[3] = {(float)LT::cx(j), (float)LT::cy(j), (float)LT::cz(j)};
-      float v = (1.0f - om) * lc[j] + base + g0[0] * cj[0] + g0[1] * cj[1] + g0[2] * cj[2];
-      if (has_S) {
-        float t = -CS2 * sD + sUU - sP * irho;
-#pragma unroll
-        for (int a = 0; a < D; ++a)
-#pragma unroll
-          for (int b = a; b < D; ++b) {
-            const float m = mS[sym<D>(a, b)];
-            // (a, b) entry; for a < b the stored m already holds both orderings
-            t += m * (cj[a] * cj[b] - cj[a] * u[b] - u[a] * cj[b]);
-          }
-        v += kk * t;
-      }
-      lO[j * N + c] = v;
+    for (int k = 0; k < NV; ++k) {
+      float v = part[k];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) red[warp][k] += (double)v;
     }
-    acc_v[ph] += (double)lom;
-    for (int a = 0; a < D; ++a) acc_v[2 + 3 * ph + a] += (double)lac[a];
   }
   if (cur_case >= 0) flush(cur_case);
+}
+
+// ------------------------------------------------------------------ interface-cell moment adjoints
+// One thread per interface cell, after k_adj_collide: the adjoints of the cell's
+// pre-collision drho, u and strain rate collected by k_adj_links (macro buffer,
+// read and cleared for the next step) are carried to the populations and added
+// to lambda_n:  lrho + lu . (c_j - u) / rho + k sum_{a<=b} lS_ab (dPi_ab/df_j - Pi_ab / rho),
+// with k = -omega / (2 rho c_s^2), Pi_ab = sum c_a c_b (f - feq), and
+// dPi_ab/df_j = c_ja c_jb - c_s^2 d_ab + u_a u_b - c_ja u_b - u_a c_jb; the strain
+// rate's omega dependence (S / omega) goes to the omega partial.
+template <int Q>
+__global__ void k_adj_macro(Ctx C, int glevel, const float *__restrict__ F, float *lamO, float *MA, double *grad,
+                            int ncase) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  constexpr int NS = D * (D + 1) / 2;
+  __shared__ double sg[kShCases * 2];
+  const bool shared_sum = ncase <= kShCases;
+  for (int k = threadIdx.x; k < kShCases * 2; k += blockDim.x) sg[k] = 0.0;
+  __syncthreads();
+  const int n = min(C.counters[glevel * NCOUNT + 1], (int)C.list_cap);
+  const int2 *lst = C.iface_list + (long long)glevel * C.list_cap;
+  const long long NF = C.nfine;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 it = lst[e];
+    const LevelDev &L = C.lds[it.x];
+    const long long c = it.y, fc = L.fine_off + c;
+    const long long N = L.ncell;
+    float m[1 + 3 + 6];
+    bool any = false;
+    for (int k = 0; k < 1 + D + NS; ++k) {
+      m[k] = MA[k * NF + fc];
+      MA[k * NF + fc] = 0.f;
+      any |= m[k] != 0.f;
+    }
+    if (!any) continue;
+    const float *Fl = F + L.cell_off * Q;
+    float *lO = lamO + L.cell_off * Q;
+    float d = 0.f, j[3] = {0.f, 0.f, 0.f}, m2[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int i = 0; i < Q; ++i) {
+      const float fi = Fl[i * N + c];
+      const float c3[3] = {(float)LT::cx(i), (float)LT::cy(i), (float)LT::cz(i)};
+      d += fi;
+      for (int a = 0; a < D; ++a) {
+        j[a] += c3[a] * fi;
+        for (int b = a; b < D; ++b) m2[sym<D>(a, b)] += c3[a] * c3[b] * fi;
+      }
+    }
+    const float rho = 1.0f + d, irho = 1.0f / rho;
+    const float u[3] = {j[0] * irho, j[1] * irho, j[2] * irho};
+    const int ph = C.tag[L.cell_off + c] & TAG_GAS;
+    const float om = L.omega[ph];
+    const float kk = -1.5f * om * irho;
+    const float *mu = m + 1, *mS = m + 1 + D;
+    // j-independent parts; Pi_ab = m2_ab - drho c_s^2 d_ab - rho u_a u_b (isotropy of the weights)
+    float sP = 0.f, sD = 0.f, sUU = 0.f, muu = 0.f;
+    for (int a = 0; a < D; ++a) {
+      muu += mu[a] * u[a];
+      for (int b = a; b < D; ++b) {
+        const float ms = mS[sym<D>(a, b)];
+        const float Pab = m2[sym<D>(a, b)] - (a == b ? CS2 * d : 0.f) - rho * u[a] * u[b];
+        sP += ms * Pab;
+        sUU += ms * u[a] * u[b];
+        if (a == b) sD += ms;
+      }
+    }
+    const float base = m[0] - muu * irho + kk * (-CS2 * sD + sUU - sP * irho);
+    for (int jj = 0; jj < Q; ++jj) {
+      const float cj[3] = {(float)LT::cx(jj), (float)LT::cy(jj), (float)LT::cz(jj)};
+      float v = base;
+      for (int a = 0; a < D; ++a) {
+        v += mu[a] * cj[a] * irho;
+        for (int b = a; b < D; ++b)  // for a < b the stored lS holds both orderings
+          v += kk * mS[sym<D>(a, b)] * (cj[a] * cj[b] - cj[a] * u[b] - u[a] * cj[b]);
+      }
+      lO[jj * N + c] += v;
+    }
+    const double lom = (double)(sP * kk / om);
+    if (lom != 0.0) {
+      if (shared_sum) atomicAdd(sg + L.case_id * 2 + ph, lom);
+      else atomicAdd(grad + (long long)L.case_id * NG_ADJ + 5 + ph, lom);
+    }
+  }
+  __syncthreads();
+  if (shared_sum)
+    for (int k = threadIdx.x; k < ncase * 2; k += blockDim.x)
+      if (sg[k] != 0.0) atomicAdd(grad + (long long)(k / 2) * NG_ADJ + 5 + (k % 2), sg[k]);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -499,8 +562,13 @@ cudaError_t run_adj_links(int Q, Launch L, Ctx C, int glevel, const float *F, fl
 }
 
 cudaError_t run_adj_collide(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, const float *F,
-                            const float *lamN, float *lamO, const float *LA, float *MA, double *grad) {
-  LSB_ADJ_Q(Q, k_adj_collide, L, C, S, list, n, F, lamN, lamO, LA, MA, grad);
+                            const float *lamN, float *lamO, const float *LA, double *grad) {
+  LSB_ADJ_Q(Q, k_adj_collide, L, C, S, list, n, F, lamN, lamO, LA, grad);
+}
+
+cudaError_t run_adj_macro(int Q, Launch L, Ctx C, int glevel, const float *F, float *lamO, float *MA, double *grad,
+                          int ncase) {
+  LSB_ADJ_Q(Q, k_adj_macro, L, C, glevel, F, lamO, MA, grad, ncase);
 }
 
 }  // namespace lsb

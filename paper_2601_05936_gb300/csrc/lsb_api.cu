@@ -27,8 +27,8 @@ namespace {
 constexpr int MAXL = 4;
 const char *const KNAMES[] = {"k_collide_stream", "k_interface_bc", "k_restrict", "k_ghost", "k_prolong", "k_level_tags", "k_observables", "k_export", "k_classify_phase", "k_classify_links", "k_band", "k_geometry", "k_ext_init", "k_ext_iter", "k_adv_stage", "k_reinit_prep", "k_reinit_stage", "k_refill", "k_sensor", "k_init", "k_collect",
                                "k_collide_stream_l1", "k_collide_stream_l2", "k_collide_stream_l3", "k_adj_seed",
-                               "k_adj_links", "k_adj_collide"};
-constexpr int KADJ_SEED = 24, KADJ_LINKS = 25, KADJ_COLLIDE = 26;
+                               "k_adj_links", "k_adj_collide", "k_adj_macro"};
+constexpr int KADJ_SEED = 24, KADJ_LINKS = 25, KADJ_COLLIDE = 26, KADJ_MACRO = 27;
 constexpr int NKERN = sizeof(KNAMES) / sizeof(KNAMES[0]);
 
 struct ProfRec {
@@ -119,6 +119,7 @@ struct lsb_grid {
   uint64_t gnodes[2] = {0, 0};
   // adjoint of the frozen-interface step: recording and reverse sweep
   int rec_on = 0, rec_every = 0;
+  int no_tma = 0;                 // recomputation writes into segment slots: plain collide kernel
   long long rec_steps = 0;
   std::vector<float *> rec_ckpt;  // state at the start of steps 0, every, 2 every, ...
   float *d_seg = nullptr;         // states of one recomputed segment
@@ -491,7 +492,7 @@ lsb_status advance(lsb_grid *g, int l) {
   const CellList &rc = g->rl_cells[l];
   RUN(2, 0, rc.n, 128, run_restrict_cells, Q, st, LN(g, (rc.n + 127) / 128, 128), C, (const int2 *)rc.d, rc.n);
   const double cs_bytes = 2.0 * g->Q * (g->storage == LSB_FP32 ? 4 : 2) * g->leaf_cells[l];
-  if (g->d_tmaps) {
+  if (g->d_tmaps && !g->no_tma) {
     const int grid = std::min(g->cs[l].n, g->tma_grid);
     RUN(collide_kid(l), cs_bytes, g->cs[l].n, nt, run_collide_stream_tma, Q, st, LN(g, grid, nt), C, S, (const int *)g->cs[l].d,
         g->cs[l].n, (const CUtensorMap *)g->d_tmaps);
@@ -501,10 +502,12 @@ lsb_status advance(lsb_grid *g, int l) {
   }
   if (has_finest(g, l)) {
     RUN(1, 0, 1, 128, run_interface_bc, Q, st, LN(g, DYN_GRID, 128), C, l);
-    if (ls_active_any(g, l)) TRY(levelset(g, l));
-    TRY(classify(g, l, 0));
-    C = make_ctx(g);
-    RUN(17, 0, 1, 128, run_refill, Q, st, LN(g, DYN_GRID, 128), C, l);
+    if (ls_active_any(g, l)) {
+      TRY(levelset(g, l));
+      TRY(classify(g, l, 0));
+      C = make_ctx(g);
+      RUN(17, 0, 1, 128, run_refill, Q, st, LN(g, DYN_GRID, 128), C, l);
+    }  // a frozen level set leaves phases, cut links and geometry as they are
     g->fine_steps[l]++;
   }
   if (l + 1 < g->Lmax) {
@@ -751,10 +754,12 @@ lsb_status adj_step(lsb_grid *g, const float *F, int cur) {
   const int Q = g->Q;
   RUN(KADJ_LINKS, 0, 1, 128, run_adj_links, Q, LN(g, DYN_GRID, 128), C, 0, F, g->d_adj[cur], g->d_linkadj,
       g->d_madj, g->d_grad, g->ncase);
-  const int grid = std::min(g->cs[0].n, 152 * 2);
+  const int grid = std::min(g->cs[0].n, 152);
   RUN(KADJ_COLLIDE, 3.0 * Q * sizeof(float) * g->leaf_cells[0], g->cs[0].n, g->nthreads, run_adj_collide, Q,
       LN(g, grid, g->nthreads), C, S, (const int *)g->cs[0].d, g->cs[0].n, F, g->d_adj[cur], g->d_adj[1 - cur],
-      g->d_linkadj, g->d_madj, g->d_grad);
+      g->d_linkadj, g->d_grad);
+  RUN(KADJ_MACRO, 0, 1, 128, run_adj_macro, Q, LN(g, DYN_GRID, 128), C, 0, F, g->d_adj[1 - cur], g->d_madj,
+      g->d_grad, g->ncase);
   return LSB_OK;
 }
 
@@ -777,7 +782,7 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
   for (int a = 0; a < D; ++a)
     if (bs[a] < 2 || (bs[a] & (bs[a] - 1))) return fail(nullptr, LSB_EINVAL, "block edges must be powers of two >= 2");
   const int nthreads = bs[0] * bs[1] * bs[2];
-  if (nthreads % 32 || nthreads > 1024) return fail(nullptr, LSB_EINVAL, "block must hold 32..1024 cells, a multiple of 32");
+  if (nthreads % 32 || nthreads > 512) return fail(nullptr, LSB_EINVAL, "block must hold 32..512 cells, a multiple of 32");
   for (int c = 0; c < n_cases; ++c) {
     const lsb_grid_desc &d = descs[c];
     if (d.lattice != d0.lattice || d.storage != d0.storage) return fail(nullptr, LSB_EINVAL, "cases must share lattice and storage");
@@ -1241,6 +1246,7 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
   CU(cudaMemcpyAsync(g->d_wobs, dJ_dobs, sizeof(double) * stride * g->ncase, cudaMemcpyHostToDevice, g->stream));
   // the final state; restored when the sweep is done
   const int par0 = g->par[0];
+  void *const bufs[2] = {g->d_buf[0], g->d_buf[1]};
   const long long fs0 = g->fine_steps[0], cs0 = g->coarse_steps;
   const double ud0 = g->updates_done;
   CU(cudaMemcpyAsync(g->d_fsave, g->d_buf[par0], sb, cudaMemcpyDeviceToDevice, g->stream));
@@ -1258,14 +1264,19 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
   for (long long sgi = nseg - 1; sgi >= 0 && st == LSB_OK; --sgi) {
     const long long start = sgi * every;
     const int len = (int)std::min<long long>(every, T - start);
-    // recompute the segment from its checkpoint, keeping every state
-    cudaError_t e = cudaMemcpyAsync(g->d_buf[g->par[0]], g->rec_ckpt[sgi], sb, cudaMemcpyDeviceToDevice, g->stream);
+    // recompute the segment from its checkpoint: step j reads slot j and pushes into
+    // slot j + 1 (the last step's result is not needed and goes to a grid buffer)
+    cudaError_t e = cudaMemcpyAsync(g->d_seg, g->rec_ckpt[sgi], sb, cudaMemcpyDeviceToDevice, g->stream);
     if (e != cudaSuccess) { st = fail(g, LSB_ECUDA, "checkpoint restore: %s", cudaGetErrorString(e)); break; }
+    g->no_tma = 1;  // the TMA tensor maps describe the grid buffers, not the slots
     for (int j = 0; j < len && st == LSB_OK; ++j) {
-      e = cudaMemcpyAsync(g->d_seg + sf * j, g->d_buf[g->par[0]], sb, cudaMemcpyDeviceToDevice, g->stream);
-      if (e != cudaSuccess) { st = fail(g, LSB_ECUDA, "segment store: %s", cudaGetErrorString(e)); break; }
+      g->d_buf[g->par[0]] = g->d_seg + sf * j;
+      g->d_buf[1 - g->par[0]] = j + 1 < len ? (void *)(g->d_seg + sf * (j + 1)) : bufs[0];
       st = advance(g, 0);
     }
+    g->no_tma = 0;
+    g->d_buf[0] = bufs[0];
+    g->d_buf[1] = bufs[1];
     for (int j = len - 1; j >= 0 && st == LSB_OK; --j) {
       st = adj_step(g, g->d_seg + sf * j, cur);
       cur ^= 1;
@@ -1277,8 +1288,6 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
   g->updates_done = ud0;
   CU(cudaMemcpyAsync(g->d_buf[par0], g->d_fsave, sb, cudaMemcpyDeviceToDevice, g->stream));
   if (st != LSB_OK) return st;
-  // classification of the final state (the recomputation left that of an earlier step)
-  TRY(classify(g, 0, 0));
   std::vector<double> h((size_t)NG_ADJ * g->ncase);
   CU(cudaMemcpyAsync(h.data(), g->d_grad, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g->stream));
   TRY(lsb_sync(g));

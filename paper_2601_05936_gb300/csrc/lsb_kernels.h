@@ -59,6 +59,8 @@ cudaError_t run_adj_seed(int Q, Launch L, Ctx C, BlockShape S, const int *list, 
 cudaError_t run_adj_links(int Q, Launch L, Ctx C, int glevel, const float *F, float *lamN, float *LA, float *MA,
                           double *grad, int ncase);
 cudaError_t run_adj_collide(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, const float *F,
-                            const float *lamN, float *lamO, const float *LA, float *MA, double *grad);
+                            const float *lamN, float *lamO, const float *LA, double *grad);
+cudaError_t run_adj_macro(int Q, Launch L, Ctx C, int glevel, const float *F, float *lamO, float *MA, double *grad,
+                          int ncase);
 
 }  // namespace lsb
