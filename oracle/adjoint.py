@@ -23,11 +23,16 @@ volume, leaf count, gas centroid (D), gas velocity (D).
 ``FrozenStep.step_adjoint`` applies the transpose of the step's Jacobian to
 an adjoint population field (the chain rule written out by hand, link by
 link and cell by cell) and returns the parameter partials; ``gradients``
-runs the reverse sweep over a stored trajectory.  Pins in
-tests/test_oracle_adjoint.py: every parameter derivative against central
-finite differences of the forward map in float64, and the dot-product
-identity <J v, w> = <v, J^T w> of one step with J v from central
-differences, on cases that exercise every bounce-back branch.
+runs the reverse sweep over a stored trajectory.  The level set
+itself is a further input: phi sets the link fractions q (radiation
+theorem) and, through the least-squares quadratic fit (Sec. 2.2), the
+interface cells' normal and curvature; ``gradients(..., want_phi=True)``
+also returns dJ/dphi, valid while no perturbation changes a sign of phi.
+Pins in tests/test_oracle_adjoint.py: every parameter derivative and
+directional derivatives in phi against central finite differences of the
+forward map in float64, and the dot-product identity
+<J v, w> = <v, J^T w> of one step with J v from central differences, on
+cases that exercise every bounce-back branch.
 """
 import numpy as np
 
@@ -46,7 +51,8 @@ def params_of(sim):
 class FrozenStep:
     """The smooth single-level step of a Sim whose level set is held fixed."""
 
-    def __init__(self, sim):
+    def __init__(self, sim, phi=None):
+        """``phi`` replaces the Sim's level set (same signs: the masks are the Sim's)."""
         assert sim.L == 1, "single-level grids only"
         self.sim = sim
         self.lat = lat = sim.lat
@@ -54,7 +60,8 @@ class FrozenStep:
         self.D, self.Q = lat.D, lat.Q
         self.phase = sim.phase[0].copy()
         self.leaf = sim.masks[0][0].copy()
-        self.phi = sim.phi.copy()
+        self.phi = (sim.phi if phi is None else np.asarray(phi, dtype=np.float64)).copy()
+        assert np.array_equal(self.phi >= 0, sim.phi >= 0), "phi must keep the Sim's signs"
         self.gravity = sim.gravity.copy()
         self.body_force = sim.body_force.copy()
         self.wall_u = sim.wall_u.copy()
@@ -76,11 +83,14 @@ class FrozenStep:
         nv, kv, _, _ = fit_geometry(g, self.phi, icells)
         nvec[:, icells] = nv
         kap[icells] = kv
+        self.icells, self.nvec, self.kap = icells, nvec, kap
         q = self.q
-        n = (1 - q) * nvec[:, x] + q * nvec[:, y]
-        nm = np.sqrt((n * n).sum(0))
-        n = np.where(nm > 0, n / np.where(nm > 0, nm, 1.0), 0.0)
+        m = (1 - q) * nvec[:, x] + q * nvec[:, y]
+        nm = np.sqrt((m * m).sum(0))
+        n = np.where(nm > 0, m / np.where(nm > 0, nm, 1.0), 0.0)
+        self.nhat, self.nm = n, nm
         sgn = np.where(self.A == 0, 1.0, -1.0)  # n points into the gas; n_A from A into B
+        self.sgn = sgn
         self.nA = sgn * n
         self.kA = sgn * ((1 - q) * kap[x] + q * kap[y])
         self.ci = lat.cf[i].T
@@ -120,7 +130,8 @@ class FrozenStep:
         uI = (1 - q) * u[:, x] + q * u[:, y]
         wi = self.lat.w[self.i]
         df = -(2.0 * wi / CS2) * ((ci * uI).sum(0) - q * (1 - q) * ccS)  # Eq. bb_cc
-        return dict(eb=eb, je=je, jp=jp, Snn=Snn, cn=cn, cvt=cvt, r=r, alpha=alpha, df=df)
+        return dict(eb=eb, je=je, jp=jp, Snn=Snn, cn=cn, cvt=cvt, r=r, alpha=alpha, df=df, ccS=ccS, v=v,
+                    Sbar=Sbar)
 
     def step(self, f, p):
         """f_{n+1} from the pre-collision populations f_n."""
@@ -172,8 +183,12 @@ class FrozenStep:
         lam[:, g] += ((lat.cf @ au)[:, None] - (au @ u[:, g])[None, :]) / rho[g][None, :] / vol
         return lam
 
-    def step_adjoint(self, f, p, lam_next):
-        """(lam_n, dJ/dp): the transpose of the step's Jacobian applied to lam_next."""
+    def step_adjoint(self, f, p, lam_next, geo=None):
+        """(lam_n, dJ/dp): the transpose of the step's Jacobian applied to lam_next.
+
+        With ``geo`` (dict of arrays phi (N,), n (D, N), kappa (N,)), also
+        accumulates the adjoints of the frozen geometry: of phi through the link
+        fractions q, and of the interface cells' normal and curvature."""
         lat, g = self.lat, self.g
         D, Q, N = self.D, self.Q, g.N
         om, acc = self.cell_params(p)
@@ -229,6 +244,8 @@ class FrozenStep:
         lam_rho = np.zeros(N)
         np.add.at(lam_rho, y, CS2 * rp[B] * l_jp)
         np.add.at(lam_rho, x, -CS2 * rp[A] * l_jp)
+        if geo is not None:
+            self._geometry_adjoint(f, p, om, rho, u, lam, hi, ok, l_df, l_ccS, P, geo)
         # Snn = n.Sbar.n and c.v_t = c.Sbar.n - Snn (c.n)
         l_Snn = -r * l_alpha - cn * l_cvt
         l_Sbar = np.einsum("an,bn->abn", ci, nA) * l_cvt + np.einsum("an,bn->abn", nA, nA) * l_Snn
@@ -271,6 +288,96 @@ class FrozenStep:
         return lam_n, dp
 
 
+    def _geometry_adjoint(self, f, p, om, rho, u, lam, hi, ok, l_df, l_ccS, P, geo):
+        """Per link: the adjoints of q (explicit in Eq. bb and through u_I, q(1-q), the
+        interpolated n and kappa) and of the link's n_A, kappa_A; n_A, kappa_A go on
+        to the interface cells' n and kappa, q to phi(x) and phi(y)."""
+        lat = self.lat
+        x, k, i, y, q = self.x, self.k, self.i, self.y, self.q
+        _, acc = self.cell_params(p)
+        from .lbm import equilibrium as feq_of
+        fc = f + om[None, :] * (feq_of(lat, rho, u) - f) + lat.w[:, None] * rho[None, :] * (lat.cf @ acc) / CS2
+        fi, fk = fc[i, x], fc[k, x]
+        fb = np.where(self.ok, fc[i, np.where(self.ok, self.back, 0)], 0.0)
+        df = P["df"]
+        w6 = 2 * lat.w[i] / CS2
+        ci = self.ci
+        # explicit q in the Bouzidi branches (df held fixed)
+        l_q = lam * np.where(hi, (-fi + fk - df) / (2 * q * q), np.where(ok, 2 * fi - 2 * fb, 0.0))
+        # df = -w6 (c.u_I - q (1 - q) ccS): u_I and the factor q (1 - q)
+        l_q += l_df * (-w6) * (ci * (u[:, y] - u[:, x])).sum(0)
+        l_q += l_df * w6 * (1 - 2 * q) * P["ccS"]
+        # ccS(n_A, kappa_A) = alpha cn^2 - 2 r cn cvt, alpha = (jp + sigma kappa_A) / (2 eb) - r Snn
+        cn, cvt, r, alpha, v, Snn, Sbar = P["cn"], P["cvt"], P["r"], P["alpha"], P["v"], P["Snn"], P["Sbar"]
+        Sc = np.einsum("abn,bn->an", Sbar, ci)
+        d_cvt = Sc - 2 * cn * v - Snn * ci  # d cvt / d n_A
+        l_nA = l_ccS * (cn * cn * (-2 * r * v) + (2 * alpha * cn - 2 * r * cvt) * ci - 2 * r * cn * d_cvt)
+        l_kA = l_ccS * cn * cn * p[0] / (2 * P["eb"])
+        # n_A = sgn m / |m|, m = (1 - q) n_x + q n_y;  kappa_A = sgn ((1 - q) kappa_x + q kappa_y)
+        nh, nm, sgn = self.nhat, self.nm, self.sgn
+        safe = np.where(nm > 0, nm, 1.0)
+        l_nh = sgn * l_nA
+        l_m = np.where(nm > 0, (l_nh - nh * (nh * l_nh).sum(0)) / safe, 0.0)
+        nx, ny = self.nvec[:, x], self.nvec[:, y]
+        l_q += (l_m * (ny - nx)).sum(0)
+        kx, ky = self.kap[x], self.kap[y]
+        l_q += sgn * (ky - kx) * l_kA
+        for a in range(self.D):
+            np.add.at(geo["n"][a], x, (1 - q) * l_m[a])
+            np.add.at(geo["n"][a], y, q * l_m[a])
+        np.add.at(geo["kappa"], x, sgn * (1 - q) * l_kA)
+        np.add.at(geo["kappa"], y, sgn * q * l_kA)
+        # q = phi_x / (phi_x - phi_y)
+        px, py = self.phi[x], self.phi[y]
+        den = (px - py) ** 2
+        np.add.at(geo["phi"], x, l_q * (-py) / den)
+        np.add.at(geo["phi"], y, l_q * px / den)
+
+    def geometry_to_phi(self, geo):
+        """dJ/dphi: geo["phi"] plus the transpose of the least-squares fit (Sec. 2.2)
+        applied to the interface cells' normal and curvature adjoints."""
+        from .levelset import _quad_design
+        g = self.g
+        D = self.D
+        offs, A, pairs = _quad_design(D)
+        Pinv = np.linalg.pinv(A)  # coef = Pinv vals
+        cells = self.icells
+        vals = np.stack([self.phi[g.clamp_shift(cells, o)] for o in offs])
+        coef = Pinv @ vals
+        gr = coef[1:1 + D]
+        H = np.zeros((D, D, len(cells)))
+        for a in range(D):
+            H[a, a] = 2.0 * coef[1 + D + a]
+        for kk, (a, b) in enumerate(pairs):
+            H[a, b] = H[b, a] = coef[1 + 2 * D + kk]
+        g2 = (gr * gr).sum(0)
+        mag = np.sqrt(g2)
+        okc = mag > 1e-12
+        safe = np.where(okc, mag, 1.0)
+        n = gr / safe
+        trH = np.trace(H)
+        Hg = np.einsum("abn,bn->an", H, gr)
+        kap = (g2 * trH - (gr * Hg).sum(0)) / safe ** 3
+        ln = geo["n"][:, cells]
+        lk = geo["kappa"][cells]
+        # n = g / |g|;  kappa = (|g|^2 tr H - g.H.g) / |g|^3
+        l_g = (ln - n * (n * ln).sum(0)) / safe
+        l_g += lk * ((2 * gr * trH - 2 * Hg) / safe ** 3 - 3 * kap * gr / safe ** 2)
+        l_H = lk * (g2[None, None, :] * np.eye(D)[:, :, None] - gr[:, None, :] * gr[None, :, :]) / safe ** 3
+        l_coef = np.zeros_like(coef)
+        l_coef[1:1 + D] = l_g
+        for a in range(D):
+            l_coef[1 + D + a] = 2.0 * l_H[a, a]
+        for kk, (a, b) in enumerate(pairs):
+            l_coef[1 + 2 * D + kk] = l_H[a, b] + l_H[b, a]
+        l_coef[:, ~okc] = 0.0
+        l_vals = Pinv.T @ l_coef
+        out = geo["phi"].copy()
+        for j, o in enumerate(offs):
+            np.add.at(out, g.clamp_shift(cells, o), l_vals[j])
+        return out
+
+
 def trajectory(step, f0, p, nsteps):
     fs = [f0]
     for _ in range(nsteps):
@@ -282,14 +389,19 @@ def objective(step, f0, p, nsteps, a):
     return float(np.asarray(a) @ step.observables(trajectory(step, f0, p, nsteps)[-1]))
 
 
-def gradients(step, f0, p, nsteps, a):
-    """J = a . observables(f_N) and its adjoint gradients: (J, dJ/dp, dJ/df_0)."""
+def gradients(step, f0, p, nsteps, a, want_phi=False):
+    """J = a . observables(f_N) and its adjoint gradients: (J, dJ/dp, dJ/df_0),
+    plus dJ/dphi (the frozen level set) with ``want_phi``."""
     a = np.asarray(a, dtype=np.float64)
     fs = trajectory(step, f0, p, nsteps)
     J = float(a @ step.observables(fs[-1]))
     lam = step.observables_adjoint(fs[-1], a)
     dp = np.zeros(NPARAM)
+    N = step.g.N
+    geo = dict(phi=np.zeros(N), n=np.zeros((step.D, N)), kappa=np.zeros(N)) if want_phi else None
     for n in range(nsteps - 1, -1, -1):
-        lam, d = step.step_adjoint(fs[n], p, lam)
+        lam, d = step.step_adjoint(fs[n], p, lam, geo)
         dp += d
+    if want_phi:
+        return J, dp, lam, step.geometry_to_phi(geo)
     return J, dp, lam

@@ -141,3 +141,38 @@ def test_pins_detect_a_planted_mistake(monkeypatch, piece):
         ref = ((st.step(f0, p + e) - st.step(f0, p - e)) / (2 * e[kp]) * w).sum()
         worst = max(worst, abs(ref - dp[kp]) / abs(ref))
     assert worst > 1e-4, worst
+
+
+@pytest.mark.parametrize("lattice,n", CASES)
+def test_level_set_gradient_matches_central_differences(lattice, n):
+    """dJ/dphi through q, n and kappa: directional derivatives along random
+    perturbations of the level set near the interface (no sign changes)."""
+    sim, st, f0, rng = _setup(lattice, n, seed=5)
+    p = params_of(sim)
+    D = st.D
+    a = rng.standard_normal(4 + 2 * D)
+    a[4 + D:] *= 100.0
+    nsteps = 4
+    J, dp, lam0, dphi = gradients(st, f0, p, nsteps, a, want_phi=True)
+    # cells within the fit stencils of interface cells
+    near = np.zeros(st.g.N, dtype=bool)
+    for o in np.array(np.meshgrid(*[[-1, 0, 1]] * D, indexing="ij")).reshape(D, -1).T:
+        near[st.g.clamp_shift(st.icells, o)] = True
+    assert np.abs(dphi[~near]).max() == 0.0
+    phi = st.phi
+    for trial in range(3):
+        v = rng.standard_normal(st.g.N) * near
+        eps = 1e-3 * np.abs(phi[near]).min() / np.abs(v).max()
+        Jp = objective(FrozenStep(sim, phi + eps * v), f0, p, nsteps, a)
+        Jm = objective(FrozenStep(sim, phi - eps * v), f0, p, nsteps, a)
+        fd = (Jp - Jm) / (2 * eps)
+        assert abs(fd - (dphi * v).sum()) <= 1e-5 * abs(fd), (fd, (dphi * v).sum())
+    # single cells: an interface cell and a neighbour that enters only through the fit
+    c0 = st.icells[len(st.icells) // 2]
+    for c in (c0, st.g.clamp_shift(np.array([c0]), np.eye(D, dtype=int)[0] * -1)[0]):
+        e = np.zeros(st.g.N)
+        e[c] = 1.0
+        eps = 1e-4 * abs(phi[c])
+        fd = (objective(FrozenStep(sim, phi + eps * e), f0, p, nsteps, a)
+              - objective(FrozenStep(sim, phi - eps * e), f0, p, nsteps, a)) / (2 * eps)
+        assert abs(fd - dphi[c]) <= 1e-5 * abs(fd) + 1e-12, (c, fd, dphi[c])
