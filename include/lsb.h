@@ -227,8 +227,12 @@ int lsb_lattice_table(int lattice, int *c, float *w, int *opp);
  * in lsb_observables order (centroid, volume and leaf count are constants of
  * the frozen map).  dJ_dparams: host, n_cases x LSB_NPARAM_ADJ doubles, or
  * NULL; per case dJ/dsigma, dJ/drho[0], dJ/drho[1], dJ/dnu[0], dJ/dnu[1] at
- * the recorded start state.  dJ_dphi0 must be NULL (derivatives with
- * respect to the level set are not computed).  Afterwards the state is that
+ * the recorded start state.  dJ_dphi0: device, or NULL; receives for each
+ * case in order the dense finest-level array (x fastest) of dJ/dphi of the
+ * frozen level set: through the link fractions q (radiation theorem, Sec.
+ * 2.3) and the interface cells' normal and curvature from the least-squares
+ * quadratic fit (Sec. 2.2).  Valid for perturbations of phi that change no
+ * sign (the masks are constants of the map).  Afterwards the state is that
  * of the last recorded step again, the recording stays open (lsb_backward
  * may be called again, e.g. with other weights, and lsb_step extends the
  * recording), and LSB_FIELD_ADJ_F returns dJ/df at the start of the

@@ -20,6 +20,10 @@
 //                   omega and acceleration partials
 //   k_adj_macro     per interface cell: the moment and strain-rate adjoints
 //                   of the cut links carried to the populations
+//   k_adj_geometry  once per sweep, when dJ/dphi is asked for: the interface
+//                   cells' normal and curvature adjoints through the
+//                   least-squares fit to phi (the link fractions' part is
+//                   added by k_adj_links)
 //
 // Precision: lambda and the Jacobians in FP32 (the forward arithmetic), every
 // parameter partial summed in FP64.
@@ -127,7 +131,7 @@ __global__ void k_adj_seed(Ctx C, BlockShape S, const int *list, int nlist, cons
 // [3, 4] eta, [5, 6] omega per phase, [7 .. 12] acceleration per phase.
 template <int Q>
 __global__ void k_adj_links(Ctx C, int glevel, const float *__restrict__ F, float *lamN, float *LA, float *MA,
-                            double *grad, int ncase) {
+                            double *grad, int ncase, GeoAdj G) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   constexpr int NS = D * (D + 1) / 2;
@@ -244,6 +248,80 @@ __global__ void k_adj_links(Ctx C, int glevel, const float *__restrict__ F, floa
       get[A] += (double)(0.5f * leb - lje);
       get[Bp] += (double)(0.5f * leb + lje);
       const float lSnn = -r * la - cn * lcvt;
+      if (G.phi) {
+        // adjoint of the frozen geometry: q (explicit in Eq. bb, in u_I, in q (1 - q)
+        // and in the interpolated n, kappa), the link's n_A and kappa_A
+        const float om = L.omega[A];
+        const float acA = LT::cx(i) * L.acc[A][0] + LT::cy(i) * L.acc[A][1] + LT::cz(i) * L.acc[A][2];
+        const float usA = uA[0] * uA[0] + uA[1] * uA[1] + uA[2] * uA[2];
+        // post-collision f_i, f_k of x (Eq. 1) and the forward df
+        float f_i = 0.f, f_k = 0.f;  // select without dynamic register indexing
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+          f_i = j == i ? f[j] : f_i;
+          f_k = j == k ? f[j] : f_k;
+        }
+        const float fi = f_i + om * (feq_dev<Q>(i, rA, uA, usA) - f_i) + 3.0f * LT::w(i) * (1.0f + rA) * acA;
+        const float fk = f_k + om * (feq_dev<Q>(k, rA, uA, usA) - f_k) - 3.0f * LT::w(k) * (1.0f + rA) * acA;
+        const float ccS = cn * cn * ((jp + L.sigma * kap) / (2.0f * eb) - r * Snn) - 2.0f * r * cn * cvt;
+        float cuI = 0.f, cdu = 0.f;
+        for (int a = 0; a < D; ++a) {
+          cuI += ci[a] * ((1.0f - q) * uA[a] + q * uB[a]);
+          cdu += ci[a] * (uB[a] - uA[a]);
+        }
+        const float df = -w6 * (cuI - q * (1.0f - q) * ccS);
+        float lq = 0.f;
+        if (hi) {
+          lq = lml * (-fi + fk - df) / (2.0f * q * q);
+        } else if (ok) {
+          int bx = x - LT::cx(i), by = y - LT::cy(i), bz = z - LT::cz(i);
+          wrap(L, 0, bx); wrap(L, 1, by); if (D == 3) wrap(L, 2, bz);
+          const long long cbk = cidx(L, bx, by, bz);
+          float fbv[Q];
+#pragma unroll
+          for (int j = 0; j < Q; ++j) fbv[j] = Fl[j * N + cbk];
+          float rb, ub[3];
+          lb_moments<Q>(fbv, rb, ub);
+          const float usb = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
+          const float fb_i = Fl[(long long)i * N + cbk];
+          const float fb = fb_i + om * (feq_dev<Q>(i, rb, ub, usb) - fb_i) + 3.0f * LT::w(i) * (1.0f + rb) * acA;
+          lq = lml * (2.0f * fi - 2.0f * fb);
+        }
+        lq += ldf * (-w6) * cdu + ldf * w6 * (1.0f - 2.0f * q) * ccS;
+        // d ccS / d n_A = cn^2 (-2 r v) + (2 alpha cn - 2 r cvt) c - 2 r cn (Sbar c - 2 cn v - Snn c)
+        const float alpha = (jp + L.sigma * kap) / (2.0f * eb) - r * Snn;
+        float lnA[3] = {0.f, 0.f, 0.f};
+        for (int a = 0; a < D; ++a) {
+          float Sc = 0.f;
+          for (int b = 0; b < D; ++b) Sc += Sb[sym<D>(a, b)] * ci[b];
+          lnA[a] = lccS * (-2.0f * r * cn * cn * v[a] + (2.0f * alpha * cn - 2.0f * r * cvt) * ci[a] -
+                           2.0f * r * cn * (Sc - 2.0f * cn * v[a] - Snn * ci[a]));
+        }
+        const float lkA = lccS * cn * cn * L.sigma / (2.0f * eb);
+        // n_A = sgn m / |m|, m = (1 - q) n_x + q n_y; kappa_A = sgn ((1 - q) kappa_x + q kappa_y)
+        const long long my = fo + cy_;
+        if (nn > 0.f) {
+          float nh[3], dot = 0.f;
+          for (int a = 0; a < D; ++a) {
+            nh[a] = sgn * nv[a];  // m / |m|
+            dot += nh[a] * sgn * lnA[a];
+          }
+          for (int a = 0; a < D; ++a) {
+            const float lm = (sgn * lnA[a] - nh[a] * dot) / nn;
+            lq += lm * (C.nvec[a * NF + my] - nx[a]);
+            atomicAdd(G.n + a * NF + fo + c, (1.0f - q) * lm);
+            atomicAdd(G.n + a * NF + my, q * lm);
+          }
+        }
+        const float ky = C.kappa[my];
+        lq += sgn * (ky - kx) * lkA;
+        atomicAdd(G.kappa + fo + c, sgn * (1.0f - q) * lkA);
+        atomicAdd(G.kappa + my, sgn * q * lkA);
+        // q = phi_x / (phi_x - phi_y)
+        const float den = (phx - phy) * (phx - phy);
+        atomicAdd(G.phi + fo + c, -lq * phy / den);
+        atomicAdd(G.phi + my, lq * phx / den);
+      }
       // macro adjoint: rho through [p], u through u_I, S through Sbar (half to each cell)
       const long long my = fo + cy_;
       mx[0] -= CS2 * L.rho_phys[A] * ljp;
@@ -543,6 +621,131 @@ __global__ void k_adj_macro(Ctx C, int glevel, const float *__restrict__ F, floa
       if (sg[k] != 0.0) atomicAdd(grad + (long long)(k / 2) * NG_ADJ + 5 + (k % 2), sg[k]);
 }
 
+// ------------------------------------------------------------------ level-set adjoint
+// One thread per interface cell, once after the sweep: the adjoints of the cell's
+// normal n = g / |g| and curvature kappa = (|g|^2 tr H - g.H.g) / |g|^3 (summed over
+// the window by k_adj_links) go back through the closed-form least-squares
+// quadratic of k_geometry (Sec. 2.2): gradient g and Hessian H are linear in the
+// stencil sums P = sum v, sx_a = sum o_a v, sxx_a = sum o_a^2 v, sxy = sum o_a o_b v
+// over the 3^D points (walls clamp, periodic axes wrap), so each point's phi
+// receives l_P + o . l_sx + o^2 . l_sxx + (o_a o_b) . l_sxy.
+template <int D>
+__global__ void k_adj_geometry(Ctx C, int glevel, GeoAdj G) {
+  const int n = min(C.counters[glevel * NCOUNT + 1], (int)C.list_cap);
+  const int2 *lst = C.iface_list + (long long)glevel * C.list_cap;
+  const long long NF = C.nfine;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 it = lst[e];
+    const LevelDev &L = C.lds[it.x];
+    const long long c = it.y, fc = L.fine_off + c;
+    double ln[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) ln[a] = G.n[a * NF + fc];
+    const double lk = G.kappa[fc];
+    if (lk == 0.0 && ln[0] == 0.0 && ln[1] == 0.0 && ln[2] == 0.0) continue;
+    const int x = (int)(c % L.p[0]);
+    const int y = (int)((c / L.p[0]) % L.p[1]);
+    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    double P = 0, sx[3] = {0, 0, 0}, sxx[3] = {0, 0, 0}, sxy[3] = {0, 0, 0};
+    for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz)
+      for (int oy = -1; oy <= 1; ++oy)
+        for (int ox = -1; ox <= 1; ++ox) {
+          const int xx = clampwrap(L, 0, x + ox), yy = clampwrap(L, 1, y + oy);
+          const int zz = D == 3 ? clampwrap(L, 2, z + oz) : 0;
+          const double v = (double)C.phi[L.fine_off + cidx(L, xx, yy, zz)];
+          const int o[3] = {ox, oy, oz};
+          P += v;
+          for (int a = 0; a < D; ++a) {
+            sx[a] += o[a] * v;
+            sxx[a] += o[a] * o[a] * v;
+          }
+          sxy[0] += ox * oy * v;
+          if (D == 3) {
+            sxy[1] += ox * oz * v;
+            sxy[2] += oy * oz * v;
+          }
+        }
+    // forward fit (as in k_geometry)
+    double g[3] = {0, 0, 0}, H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double a0, s;
+    if (D == 2) {
+      const double R = sxx[0] + sxx[1];
+      s = (3.0 * R - 4.0 * P) / 6.0;
+      a0 = (5.0 * P - 3.0 * R) / 9.0;
+      for (int a = 0; a < 2; ++a) {
+        g[a] = sx[a] / 6.0;
+        H[a][a] = sxx[a] - 6.0 * a0 - 4.0 * s;
+      }
+      H[0][1] = H[1][0] = sxy[0] / 4.0;
+    } else {
+      const double R = sxx[0] + sxx[1] + sxx[2];
+      s = (R - 2.0 * P) / 6.0;
+      a0 = (7.0 * P - 3.0 * R) / 27.0;
+      for (int a = 0; a < 3; ++a) {
+        g[a] = sx[a] / 18.0;
+        H[a][a] = (sxx[a] - 18.0 * a0 - 12.0 * s) / 3.0;
+      }
+      H[0][1] = H[1][0] = sxy[0] / 12.0;
+      H[0][2] = H[2][0] = sxy[1] / 12.0;
+      H[1][2] = H[2][1] = sxy[2] / 12.0;
+    }
+    double g2 = 0, tr = 0, gHg = 0, Hg[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) {
+      g2 += g[a] * g[a];
+      tr += H[a][a];
+      for (int b = 0; b < D; ++b) Hg[a] += H[a][b] * g[b];
+      gHg += g[a] * Hg[a];
+    }
+    const double mag = sqrt(g2);
+    if (!(mag > 1e-12)) continue;  // n = 0, kappa = 0: no dependence
+    const double kap = (g2 * tr - gHg) / (mag * mag * mag);
+    // l_g, l_H from l_n, l_kappa
+    double nd = 0, lg[3] = {0, 0, 0}, lH[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int a = 0; a < D; ++a) nd += g[a] / mag * ln[a];
+    for (int a = 0; a < D; ++a) {
+      lg[a] = (ln[a] - g[a] / mag * nd) / mag;
+      lg[a] += lk * ((2.0 * g[a] * tr - 2.0 * Hg[a]) / (mag * mag * mag) - 3.0 * kap * g[a] / g2);
+      for (int b = 0; b < D; ++b) lH[a][b] = lk * ((a == b ? g2 : 0.0) - g[a] * g[b]) / (mag * mag * mag);
+    }
+    // transpose of the closed-form fit
+    double lP = 0, lsx[3] = {0, 0, 0}, lsxx[3] = {0, 0, 0}, lsxy[3] = {0, 0, 0}, la0 = 0, ls = 0, lR = 0;
+    if (D == 2) {
+      for (int a = 0; a < 2; ++a) {
+        lsx[a] = lg[a] / 6.0;
+        lsxx[a] += lH[a][a];
+        la0 += -6.0 * lH[a][a];
+        ls += -4.0 * lH[a][a];
+      }
+      lsxy[0] = (lH[0][1] + lH[1][0]) / 4.0;
+      lP += 5.0 / 9.0 * la0 - 4.0 / 6.0 * ls;
+      lR += -3.0 / 9.0 * la0 + 3.0 / 6.0 * ls;
+    } else {
+      for (int a = 0; a < 3; ++a) {
+        lsx[a] = lg[a] / 18.0;
+        lsxx[a] += lH[a][a] / 3.0;
+        la0 += -6.0 * lH[a][a];
+        ls += -4.0 * lH[a][a];
+      }
+      lsxy[0] = (lH[0][1] + lH[1][0]) / 12.0;
+      lsxy[1] = (lH[0][2] + lH[2][0]) / 12.0;
+      lsxy[2] = (lH[1][2] + lH[2][1]) / 12.0;
+      lP += 7.0 / 27.0 * la0 - 2.0 / 6.0 * ls;
+      lR += -3.0 / 27.0 * la0 + 1.0 / 6.0 * ls;
+    }
+    for (int a = 0; a < D; ++a) lsxx[a] += lR;
+    for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz)
+      for (int oy = -1; oy <= 1; ++oy)
+        for (int ox = -1; ox <= 1; ++ox) {
+          const int o[3] = {ox, oy, oz};
+          double lv = lP + ox * oy * lsxy[0];
+          if (D == 3) lv += ox * oz * lsxy[1] + oy * oz * lsxy[2];
+          for (int a = 0; a < D; ++a) lv += o[a] * lsx[a] + o[a] * o[a] * lsxx[a];
+          const int xx = clampwrap(L, 0, x + ox), yy = clampwrap(L, 1, y + oy);
+          const int zz = D == 3 ? clampwrap(L, 2, z + oz) : 0;
+          atomicAdd(G.phi + L.fine_off + cidx(L, xx, yy, zz), (float)lv);
+        }
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 #define LSB_ADJ_Q(Q, fn, L, ...)                                                      \
   do {                                                                                \
@@ -557,8 +760,14 @@ cudaError_t run_adj_seed(int Q, Launch L, Ctx C, BlockShape S, const int *list, 
 }
 
 cudaError_t run_adj_links(int Q, Launch L, Ctx C, int glevel, const float *F, float *lamN, float *LA, float *MA,
-                          double *grad, int ncase) {
-  LSB_ADJ_Q(Q, k_adj_links, L, C, glevel, F, lamN, LA, MA, grad, ncase);
+                          double *grad, int ncase, GeoAdj G) {
+  LSB_ADJ_Q(Q, k_adj_links, L, C, glevel, F, lamN, LA, MA, grad, ncase, G);
+}
+
+cudaError_t run_adj_geometry(int D, Launch L, Ctx C, int glevel, GeoAdj G) {
+  if (D == 2) k_adj_geometry<2><<<L.grid, L.block, 0, L.stream>>>(C, glevel, G);
+  else k_adj_geometry<3><<<L.grid, L.block, 0, L.stream>>>(C, glevel, G);
+  return cudaGetLastError();
 }
 
 cudaError_t run_adj_collide(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, const float *F,

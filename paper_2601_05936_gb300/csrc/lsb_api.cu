@@ -27,8 +27,8 @@ namespace {
 constexpr int MAXL = 4;
 const char *const KNAMES[] = {"k_collide_stream", "k_interface_bc", "k_restrict", "k_ghost", "k_prolong", "k_level_tags", "k_observables", "k_export", "k_classify_phase", "k_classify_links", "k_band", "k_geometry", "k_ext_init", "k_ext_iter", "k_adv_stage", "k_reinit_prep", "k_reinit_stage", "k_refill", "k_sensor", "k_init", "k_collect",
                                "k_collide_stream_l1", "k_collide_stream_l2", "k_collide_stream_l3", "k_adj_seed",
-                               "k_adj_links", "k_adj_collide", "k_adj_macro"};
-constexpr int KADJ_SEED = 24, KADJ_LINKS = 25, KADJ_COLLIDE = 26, KADJ_MACRO = 27;
+                               "k_adj_links", "k_adj_collide", "k_adj_macro", "k_adj_geometry"};
+constexpr int KADJ_SEED = 24, KADJ_LINKS = 25, KADJ_COLLIDE = 26, KADJ_MACRO = 27, KADJ_GEOM = 28;
 constexpr int NKERN = sizeof(KNAMES) / sizeof(KNAMES[0]);
 
 struct ProfRec {
@@ -127,6 +127,7 @@ struct lsb_grid {
   float *d_adj[2] = {nullptr, nullptr};
   int adj_cur = -1;               // d_adj[adj_cur] holds dJ/df_0 after lsb_backward
   float *d_fsave = nullptr, *d_madj = nullptr, *d_linkadj = nullptr;
+  float *d_gphi = nullptr, *d_gn = nullptr, *d_gk = nullptr;  // level-set adjoint (finest level)
   double *d_grad = nullptr, *d_wobs = nullptr;
 };
 
@@ -733,6 +734,9 @@ lsb_status adj_buffers(lsb_grid *g, int seg_len) {
     TRY(dalloc(g, &g->d_linkadj, sizeof(float) * 2 * (size_t)g->link_cap));
     TRY(dalloc(g, &g->d_grad, sizeof(double) * NG_ADJ * g->ncase));
     TRY(dalloc(g, &g->d_wobs, sizeof(double) * (4 + 2 * g->D) * g->ncase));
+    TRY(dalloc(g, &g->d_gphi, sizeof(float) * (size_t)g->nfine));
+    TRY(dalloc(g, &g->d_gn, sizeof(float) * (size_t)g->D * g->nfine));
+    TRY(dalloc(g, &g->d_gk, sizeof(float) * (size_t)g->nfine));
     CU(cudaMemsetAsync(g->d_madj, 0, sizeof(float) * (size_t)MF * g->nfine, g->stream));
   }
   if (seg_len > g->seg_cap) {
@@ -748,12 +752,12 @@ lsb_status adj_buffers(lsb_grid *g, int seg_len) {
 }
 
 // One reverse step: lambda_n from lambda_{n+1} = d_adj[cur] at the state F = f_n.
-lsb_status adj_step(lsb_grid *g, const float *F, int cur) {
+lsb_status adj_step(lsb_grid *g, const float *F, int cur, GeoAdj G) {
   Ctx C = make_ctx(g);
   BlockShape S = shape(g);
   const int Q = g->Q;
   RUN(KADJ_LINKS, 0, 1, 128, run_adj_links, Q, LN(g, DYN_GRID, 128), C, 0, F, g->d_adj[cur], g->d_linkadj,
-      g->d_madj, g->d_grad, g->ncase);
+      g->d_madj, g->d_grad, g->ncase, G);
   const int grid = std::min(g->cs[0].n, 152);
   RUN(KADJ_COLLIDE, 3.0 * Q * sizeof(float) * g->leaf_cells[0], g->cs[0].n, g->nthreads, run_adj_collide, Q,
       LN(g, grid, g->nthreads), C, S, (const int *)g->cs[0].d, g->cs[0].n, F, g->d_adj[cur], g->d_adj[1 - cur],
@@ -1231,7 +1235,6 @@ lsb_status lsb_record(lsb_grid *g, int checkpoint_every) {
 
 lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, float *dJ_dphi0) {
   if (!g || !dJ_dobs) return LSB_EINVAL;
-  if (dJ_dphi0) return fail(g, LSB_EINVAL, "dJ/dphi0 is not computed: pass NULL");
   if (!g->rec_on) return fail(g, LSB_ESTATE, "no recording: call lsb_record before the steps to differentiate");
   const int Q = g->Q, D = g->D, stride = 4 + 2 * D;
   const long long T = g->rec_steps;
@@ -1243,6 +1246,13 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
   CU(cudaMemsetAsync(g->d_adj[1], 0, sb, g->stream));
   CU(cudaMemsetAsync(g->d_madj, 0, sizeof(float) * (size_t)MF * g->nfine, g->stream));
   CU(cudaMemsetAsync(g->d_grad, 0, sizeof(double) * NG_ADJ * g->ncase, g->stream));
+  GeoAdj G{nullptr, nullptr, nullptr};
+  if (dJ_dphi0) {
+    G = GeoAdj{g->d_gphi, g->d_gn, g->d_gk};
+    CU(cudaMemsetAsync(g->d_gphi, 0, sizeof(float) * (size_t)g->nfine, g->stream));
+    CU(cudaMemsetAsync(g->d_gn, 0, sizeof(float) * (size_t)D * g->nfine, g->stream));
+    CU(cudaMemsetAsync(g->d_gk, 0, sizeof(float) * (size_t)g->nfine, g->stream));
+  }
   CU(cudaMemcpyAsync(g->d_wobs, dJ_dobs, sizeof(double) * stride * g->ncase, cudaMemcpyHostToDevice, g->stream));
   // the final state; restored when the sweep is done
   const int par0 = g->par[0];
@@ -1278,7 +1288,7 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
     g->d_buf[0] = bufs[0];
     g->d_buf[1] = bufs[1];
     for (int j = len - 1; j >= 0 && st == LSB_OK; --j) {
-      st = adj_step(g, g->d_seg + sf * j, cur);
+      st = adj_step(g, g->d_seg + sf * j, cur, G);
       cur ^= 1;
     }
   }
@@ -1288,6 +1298,23 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
   g->updates_done = ud0;
   CU(cudaMemcpyAsync(g->d_buf[par0], g->d_fsave, sb, cudaMemcpyDeviceToDevice, g->stream));
   if (st != LSB_OK) return st;
+  if (dJ_dphi0) {
+    // normal and curvature adjoints through the least-squares fit, then the dense boxes
+    Ctx C2 = make_ctx(g);
+    RUN(KADJ_GEOM, 0, 1, 128, run_adj_geometry, D, LN(g, DYN_GRID, 128), C2, 0, G);
+    size_t off = 0;
+    for (int c = 0; c < g->ncase; ++c) {
+      const LevelDev &L = g->lds[g->cases[c].ld0 + g->cases[c].L - 1];
+      cudaMemcpy3DParms pr;
+      memset(&pr, 0, sizeof pr);
+      pr.srcPtr = make_cudaPitchedPtr((void *)(g->d_gphi + L.fine_off), 4 * (size_t)L.p[0], L.p[0], L.p[1]);
+      pr.dstPtr = make_cudaPitchedPtr((void *)(dJ_dphi0 + off), 4 * (size_t)L.n[0], L.n[0], L.n[1]);
+      pr.extent = make_cudaExtent(4 * (size_t)L.n[0], L.n[1], L.n[2]);
+      pr.kind = cudaMemcpyDeviceToDevice;
+      CU(cudaMemcpy3DAsync(&pr, g->stream));
+      off += (size_t)L.n[0] * L.n[1] * L.n[2];
+    }
+  }
   std::vector<double> h((size_t)NG_ADJ * g->ncase);
   CU(cudaMemcpyAsync(h.data(), g->d_grad, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g->stream));
   TRY(lsb_sync(g));

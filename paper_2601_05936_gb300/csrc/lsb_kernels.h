@@ -54,10 +54,16 @@ cudaError_t run_sensor(Launch L, Ctx C, BlockShape S, const int *list, int n, in
 
 // lsb_adj.cu: adjoint of the frozen-interface step
 constexpr int NG_ADJ = 13;  // parameter partials per case accumulated on the device
+// Adjoints of the frozen geometry, finest-level arrays (nullptr: not computed):
+// phi (nfine), interface cells' normal (D planes of nfine) and curvature (nfine).
+struct GeoAdj {
+  float *phi, *n, *kappa;
+};
 cudaError_t run_adj_seed(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, const float *F, float *lam,
                          const double *wobs, const double *obs, int stride);
 cudaError_t run_adj_links(int Q, Launch L, Ctx C, int glevel, const float *F, float *lamN, float *LA, float *MA,
-                          double *grad, int ncase);
+                          double *grad, int ncase, GeoAdj G);
+cudaError_t run_adj_geometry(int D, Launch L, Ctx C, int glevel, GeoAdj G);
 cudaError_t run_adj_collide(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, const float *F,
                             const float *lamN, float *lamO, const float *LA, double *grad);
 cudaError_t run_adj_macro(int Q, Launch L, Ctx C, int glevel, const float *F, float *lamO, float *MA, double *grad,

@@ -284,18 +284,35 @@ class Grid:
         """Start recording the following steps for backward (frozen level set, one level, FP32)."""
         self._check(self.lib.lsb_record(self.h, int(checkpoint_every)))
 
-    def backward(self, dJ_dobs):
+    def backward(self, dJ_dobs, want_phi=False):
         """Reverse sweep over the recorded steps for J = sum of dJ_dobs . observables
         (dJ_dobs: n_cases x (4 + 2 D), observables order).  Returns dJ/dp, shape
-        (n_cases, 5): sigma, rho[0], rho[1], nu[0], nu[1]."""
+        (n_cases, 5): sigma, rho[0], rho[1], nu[0], nu[1]; with ``want_phi`` also
+        the list of dJ/dphi arrays (finest level of each case, shape (nz,) ny, nx)."""
+        import torch
         w = np.ascontiguousarray(np.asarray(dJ_dobs, dtype=np.float64).reshape(-1))
         nc = len(self.cases)
         if w.size != nc * (4 + 2 * self.D):
             raise ValueError("dJ_dobs needs n_cases x (4 + 2 D) values")
         out = np.zeros(nc * NPARAM_ADJ, dtype=np.float64)
+        dims = [self.level_dims(k)[::-1] for k in range(nc)]
+        dphi = None
+        if want_phi:
+            dphi = torch.zeros(sum(int(np.prod(d)) for d in dims), dtype=torch.float32,
+                               device=torch.cuda.current_device())
         self._check(self.lib.lsb_backward(self.h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None))
-        return out.reshape(nc, NPARAM_ADJ)
+                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          ctypes.c_void_p(dphi.data_ptr()) if want_phi else None))
+        dp = out.reshape(nc, NPARAM_ADJ)
+        if not want_phi:
+            return dp
+        h = dphi.cpu().numpy()
+        res, o = [], 0
+        for d in dims:
+            m = int(np.prod(d))
+            res.append(h[o:o + m].reshape(d))
+            o += m
+        return dp, res
 
     def close(self):
         if getattr(self, "h", None):

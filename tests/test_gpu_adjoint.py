@@ -31,19 +31,22 @@ def _oracle(case, warmup, steps, a):
     sim = Sim(case)
     sim.step(warmup)
     st = FrozenStep(sim)
-    J, dp, lam0 = gradients(st, sim.f[0], params_of(sim), steps, a)
-    return J, dp, lam0
+    J, dp, lam0, dphi = gradients(st, sim.f[0], params_of(sim), steps, a, want_phi=True)
+    return J, dp, lam0, dphi
 
 
-def _gpu(case, warmup, steps, a, every):
+def _gpu(case, warmup, steps, a, every, want_phi=False):
     from paper_2601_05936_gb300 import lsb
     g = lsb.Grid(case)
     g.step(warmup)
     g.record(every)
     g.step(steps)
-    dp = g.backward(a.reshape(1, -1))[0]
+    if want_phi:
+        dp, dphi = g.backward(a.reshape(1, -1), want_phi=True)
+    else:
+        dp, dphi = g.backward(a.reshape(1, -1)), None
     lam0 = g.get("adj_f").reshape(g.Q, -1).astype(np.float64)
-    return g, dp, lam0
+    return g, dp[0], lam0, dphi
 
 
 CASES = [("D2Q9", (48, 32), 10, 30), ("D3Q19", (32, 16, 20), 6, 16)]
@@ -55,11 +58,16 @@ def test_adjoint_matches_oracle(lattice, n, warmup, steps):
     case = as_fp32_phi(workloads.adjoint_window(lattice, n=n))
     D = len(n)
     a = _weights(D)[0]
-    _, dp_o, lam_o = _oracle(case, warmup, steps, a)
-    g, dp_g, lam_g = _gpu(case, warmup, steps, a, every=7)
+    _, dp_o, lam_o, dphi_o = _oracle(case, warmup, steps, a)
+    g, dp_g, lam_g, dphi_g = _gpu(case, warmup, steps, a, every=7, want_phi=True)
     for k in range(5):
         assert abs(dp_g[k] - dp_o[k]) <= 2e-3 * abs(dp_o[k]) + 1e-9, (k, dp_g, dp_o)
     assert rel_l2(lam_g, lam_o) < 1e-3
+    # dJ/dphi of the frozen level set (q, normal, curvature): FP32 link arithmetic with
+    # 1/q^2 and 1/(phi_x - phi_y)^2 factors; relative L2 over the whole field
+    d_g = dphi_g[0].reshape(-1).astype(np.float64)
+    assert rel_l2(d_g, dphi_o) < 5e-3, rel_l2(d_g, dphi_o)
+    assert np.abs(d_g[dphi_o == 0]).max() == 0.0
     g.close()
 
 
@@ -67,7 +75,7 @@ def test_checkpoint_spacing_does_not_change_the_result():
     from paper_2601_05936_gb300 import workloads
     case = workloads.adjoint_window("D2Q9", n=(48, 32))
     a = _weights(2)[0]
-    res = [_gpu(case, 5, 20, a, every)[1:] for every in (1, 6, 100)]
+    res = [_gpu(case, 5, 20, a, every)[1:3] for every in (1, 6, 100)]
     for dp, lam in res[1:]:
         assert np.allclose(dp, res[0][0], rtol=1e-5, atol=0)
         assert rel_l2(lam, res[0][1]) < 1e-6
@@ -110,13 +118,15 @@ def test_ensemble_cases_are_independent():
     g.step(3)
     g.record(4)
     g.step(10)
-    dp = g.backward(a)
+    dp, dphi = g.backward(a, want_phi=True)
     for k, c in enumerate((c0, c1)):
         s = lsb.Grid(c)
         s.step(3)
         s.record(4)
         s.step(10)
-        assert np.allclose(dp[k], s.backward(a[k:k + 1])[0], rtol=1e-5)
+        dps, dphis = s.backward(a[k:k + 1], want_phi=True)
+        assert np.allclose(dp[k], dps[0], rtol=1e-5)
+        assert rel_l2(dphi[k].astype(np.float64), dphis[0].astype(np.float64)) < 1e-5
         s.close()
     g.close()
 
