@@ -230,6 +230,8 @@ def main():
                          "(collide-and-stream only, for profiling captures); ensemble: 64 uneven 2D bubbles; "
                          "adjoint3d: reverse sweep over --steps recorded steps of a frozen 3D bubble")
     ap.add_argument("--checkpoint-every", type=int, default=100)
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="bubble3d only: linear scale of the box and bubble (profiling captures of a smaller copy)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -258,7 +260,7 @@ def main():
         adjoint_bench(args, world, rank, local, barrier, dist)
         return
     if args.workload == "bubble3d":
-        case = workloads.rising_bubble_3d(storage=args.storage)
+        case = workloads.rising_bubble_3d(storage=args.storage, scale=args.scale)
         cases = [case]
     elif args.workload == "box3d":
         case = workloads.uniform_box(storage=args.storage)

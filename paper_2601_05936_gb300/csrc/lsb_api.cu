@@ -440,7 +440,8 @@ lsb_status classify(lsb_grid *g, int l, int init) {
   const int *fl = F.d;
   const int Q = g->Q, D = g->D, nt = g->nthreads;
   RUN(8, 0, F.n, nt, run_classify_phase, Q, LN(g, F.n, nt), C, S, fl, F.n, l, init);
-  RUN(9, 0, F.n, nt, run_classify_links, Q, LN(g, F.n, nt), C, S, fl, F.n, l);
+  if (!init) RUN(9, 0, 1, 128, run_flip_mark, Q, LN(g, DYN_GRID / 4, 128), C, S, l);
+  RUN(9, 0, F.n, nt, run_classify_links, Q, LN(g, F.n, nt), C, S, fl, F.n, l, init);
   RUN(10, 0, F.n, 128, run_band, Q, LN(g, (F.n + 127) / 128, 128), C, S, fl, F.n, l);
   RUN(11, 0, 1, 128, run_geometry, D, LN(g, DYN_GRID, 128), C, l, 0);
   RUN(11, 0, 1, 128, run_geometry, D, LN(g, DYN_GRID, 128), C, l, 1);

@@ -9,6 +9,9 @@
 // cell and their 3^D neighbours (active blocks only).  phi, the RK stage
 // arrays and the extension velocity are dense finest-level arrays; stencil
 // points outside the band read the committed fields.
+#include <map>
+#include <mutex>
+
 #include "lsb_kernels.h"
 
 namespace lsb {
@@ -20,11 +23,12 @@ __device__ __forceinline__ bool in_band(const Ctx &C, const LevelDev &L, const B
 // ------------------------------------------------------------------ classification
 // Pass 1: phase of every leaf cell from phi (liquid iff phi < 0); flipped cells
 // are listed.  init = 1 (after creation or regrid): no flips, previous = current.
+// The block's band flag of the last classification is kept as BF_OLDBAND.
 template <int Q>
 __global__ void k_classify_phase(Ctx C, BlockShape S, const int *list, int nlist, int glevel, int init) {
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     const int gb = list[w];
-    if (threadIdx.x == 0) C.bflag[gb] = 0;
+    if (threadIdx.x == 0) C.bflag[gb] = (!init && (C.bflag[gb] & BF_BAND)) ? BF_OLDBAND : 0;
     int x, y, z;
     const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
@@ -45,14 +49,49 @@ __global__ void k_classify_phase(Ctx C, BlockShape S, const int *list, int nlist
   }
 }
 
-// Pass 2: cut mask of every leaf cell (bit k: source x - c_k is a leaf of the
-// other phase), link base, interface list, block interface flag.
+// Pass 1b: blocks next to a flipped cell (or holding one) that were not in the
+// previous band get BF_CHECK.
 template <int Q>
-__global__ void k_classify_links(Ctx C, BlockShape S, const int *list, int nlist, int glevel) {
+__global__ void k_flip_mark(Ctx C, BlockShape S, int glevel) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  const int n = min(C.counters[glevel * NCOUNT + 2], (int)C.list_cap);
+  const int2 *lst = C.flip_list + (long long)glevel * C.list_cap;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 it = lst[e];
+    const LevelDev &L = C.lds[it.x];
+    const long long c = it.y;
+    const int x = (int)(c % L.p[0]);
+    const int y = (int)((c / L.p[0]) % L.p[1]);
+    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    for (int k = 0; k < Q; ++k) {
+      int sx = x + LT::cx(k), sy = y + LT::cy(k), sz = z + LT::cz(k);
+      if (!(wrap(L, 0, sx) && wrap(L, 1, sy) && (D == 2 || wrap(L, 2, sz)))) continue;
+      const int nb = L.block_off + block_of(L, sx, sy, sz, S);
+      const uint8_t f = C.bflag[nb];
+      if (!(f & (BF_OLDBAND | BF_CHECK))) C.bflag[nb] = f | BF_CHECK;  // byte store: only adds the bit
+    }
+  }
+}
+
+// Pass 2: cut mask of every leaf cell (bit k: source x - c_k is a leaf of the
+// other phase), link base, interface list, block interface flag.  Unless full,
+// only blocks of the previous band and blocks next to a flipped cell are
+// examined: phi changes only on band cells, so a cut link elsewhere would need a
+// neighbour that flipped; every other block has no cut link now and, having left
+// the band with none, an all-zero mask already.
+template <int Q>
+__global__ void k_classify_links(Ctx C, BlockShape S, const int *list, int nlist, int glevel, int full) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     const int gb = list[w];
+    const bool work = full || (C.bflag[gb] & (BF_OLDBAND | BF_CHECK));
+    __syncthreads();  // every thread has read the flags before thread 0 rewrites them
+    if (!work) {
+      if (threadIdx.x == 0) C.bflag[gb] = 0;
+      continue;
+    }
     int x, y, z;
     const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
     bool has = false;
@@ -81,7 +120,8 @@ __global__ void k_classify_links(Ctx C, BlockShape S, const int *list, int nlist
         }
       }
     }
-    if (__syncthreads_or(has) && threadIdx.x == 0) C.bflag[gb] = BF_IFACE;
+    const bool any = __syncthreads_or(has);
+    if (threadIdx.x == 0) C.bflag[gb] = any ? BF_IFACE : 0;
   }
 }
 
@@ -590,27 +630,61 @@ __global__ void k_sensor(Ctx C, BlockShape S, const int *list, int nlist, int mo
     else kern<3><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);               \
     return cudaGetLastError();                                                 \
   } while (0)
+// Same for a band-list kernel, with the grid capped at the resident CTAs.
+#define LDP(kern, ...)                                                                             \
+  do {                                                                                             \
+    if (D == 2) kern<2><<<resident_grid(kern<2>, L.block, L.grid), L.block, 0, L.stream>>>(__VA_ARGS__); \
+    else kern<3><<<resident_grid(kern<3>, L.block, L.grid), L.block, 0, L.stream>>>(__VA_ARGS__);        \
+    return cudaGetLastError();                                                                     \
+  } while (0)
+#define LQP(kern, ...)                                                                             \
+  do {                                                                                             \
+    if (Q == 9) kern<9><<<resident_grid(kern<9>, L.block, L.grid), L.block, 0, L.stream>>>(__VA_ARGS__); \
+    else kern<19><<<resident_grid(kern<19>, L.block, L.grid), L.block, 0, L.stream>>>(__VA_ARGS__);      \
+    return cudaGetLastError();                                                                     \
+  } while (0)
+
+// Band-list kernels walk a device-sized list with a block-stride loop; their grid
+// is capped at the CTAs resident at once (152 SMs x CTAs per SM for this kernel and
+// block size), so no wave of CTAs starts only to find the list exhausted.
+template <typename K>
+int resident_grid(K kern, int block, int want) {
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, int> cache;  // (kernel, block) -> resident CTAs
+  const std::pair<const void *, int> key{reinterpret_cast<const void *>(kern), block};
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it == cache.end()) {
+    int n = 1, dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, block, 0) != cudaSuccess || n < 1) n = 1;
+    it = cache.emplace(key, n * sms).first;
+  }
+  return want < it->second ? want : it->second;
+}
 
 cudaError_t run_classify_phase(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, int glevel, int init) {
   LQ(k_classify_phase, C, S, list, n, glevel, init);
 }
-cudaError_t run_classify_links(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, int glevel) {
-  LQ(k_classify_links, C, S, list, n, glevel);
+cudaError_t run_classify_links(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, int glevel, int full) {
+  LQ(k_classify_links, C, S, list, n, glevel, full);
 }
+cudaError_t run_flip_mark(int Q, Launch L, Ctx C, BlockShape S, int glevel) { LQ(k_flip_mark, C, S, glevel); }
 cudaError_t run_band(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, int glevel) {
   LQ(k_band, C, S, list, n, glevel);
 }
 cudaError_t run_geometry(int D, Launch L, Ctx C, int glevel, int which) { LD(k_geometry, C, glevel, which); }
 cudaError_t run_ext_init(int Q, Launch L, Ctx C, int glevel) { LQ(k_ext_init, C, glevel); }
 cudaError_t run_ext_iter(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int commit) {
-  LD(k_ext_iter, C, S, glevel, uin, uout, commit);
+  LDP(k_ext_iter, C, S, glevel, uin, uout, commit);
 }
 cudaError_t run_adv_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage) {
-  LD(k_adv_stage, C, S, glevel, stage);
+  LDP(k_adv_stage, C, S, glevel, stage);
 }
-cudaError_t run_reinit_prep(int Q, Launch L, Ctx C, BlockShape S, int glevel) { LQ(k_reinit_prep, C, S, glevel); }
+cudaError_t run_reinit_prep(int Q, Launch L, Ctx C, BlockShape S, int glevel) { LQP(k_reinit_prep, C, S, glevel); }
 cudaError_t run_reinit_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage) {
-  LD(k_reinit_stage, C, S, glevel, stage);
+  LDP(k_reinit_stage, C, S, glevel, stage);
 }
 cudaError_t run_refill(int Q, int st, Launch L, Ctx C, int glevel) {
   if (Q == 9) {
