@@ -189,6 +189,27 @@ size_t lsb_field_bytes(const lsb_grid *g, int case_idx, int field, int level);
  */
 lsb_status lsb_observables(lsb_grid *g, double *out_host, size_t n_doubles);
 
+/*
+ * Block-shape autotuner (the paper has no counterpart; the block edge is a
+ * free parameter of the block-structured grid, Sec. 2.5).  For each candidate
+ * shape (candidates: host array of n_cand x 3 ints, block edges x, y, z; NULL
+ * = six built-in shapes for the lattice of descs[0], n_cand ignored) it
+ * creates the handle with that block shape for every case, runs 2 untimed
+ * coarse steps, times `steps` coarse steps with CUDA events on `stream`
+ * (a cudaStream_t, NULL = legacy default) and destroys the handle.
+ * best: host, 3 ints, receives the fastest shape; ms_per_step: host array of
+ * n_cand doubles (6 with NULL candidates) or NULL, receives each candidate's
+ * milliseconds per coarse step (NaN for a shape that was rejected or failed).
+ * Other arguments as for lsb_create_grid.  Block shape changes the refined
+ * region (the sensor marks whole blocks), so the candidates are compared by
+ * wall time per coarse step of the same problem.  Synchronises.  Errors:
+ * LSB_EINVAL (bad arguments, or no candidate ran; lsb_last_error(NULL) says
+ * why).
+ */
+lsb_status lsb_autotune(int n_cases, const lsb_grid_desc *descs, const lsb_params *params,
+                        const float *const *phi0, void *stream, const int *candidates, int n_cand, int steps,
+                        int *best, double *ms_per_step);
+
 /* Cell updates (the MLUPS numerator): per_coarse_step = sum over levels of
  * leaf cells x 2^level for the current grid (all cases); total_done = the same
  * summed over every coarse step taken so far (regrids change the per-step

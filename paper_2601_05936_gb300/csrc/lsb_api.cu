@@ -1175,6 +1175,55 @@ lsb_status lsb_observables(lsb_grid *g, double *out_host, size_t n_doubles) {
   return s;
 }
 
+lsb_status lsb_autotune(int n_cases, const lsb_grid_desc *descs, const lsb_params *params,
+                        const float *const *phi0, void *stream, const int *candidates, int n_cand, int steps,
+                        int *best, double *ms_per_step) {
+  if (n_cases < 1 || !descs || !params || !phi0 || !best || steps < 1)
+    return fail(nullptr, LSB_EINVAL, "autotune: need cases, phi0, best and steps >= 1");
+  if (candidates && n_cand < 1) return fail(nullptr, LSB_EINVAL, "autotune: n_cand must be >= 1");
+  const bool d2 = descs[0].lattice == LSB_D2Q9;
+  // default shapes: one warp per x row (or two), thin in the other axes
+  static const int def2[][3] = {{32, 8, 1}, {32, 16, 1}, {64, 8, 1}, {16, 16, 1}, {64, 4, 1}, {128, 4, 1}};
+  static const int def3[][3] = {{32, 4, 4}, {32, 8, 2}, {16, 8, 4}, {64, 4, 2}, {32, 2, 8}, {16, 4, 8}};
+  const int *cand = candidates ? candidates : (d2 ? &def2[0][0] : &def3[0][0]);
+  const int nc = candidates ? n_cand : 6;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(nullptr, LSB_ECUDA, "autotune: event creation failed");
+  double best_ms = INFINITY;
+  std::vector<lsb_grid_desc> dd(descs, descs + n_cases);
+  std::string last_err;
+  for (int k = 0; k < nc; ++k) {
+    for (int c = 0; c < n_cases; ++c)
+      for (int a = 0; a < 3; ++a) dd[c].block[a] = cand[3 * k + a];
+    double ms = NAN;
+    lsb_grid *g = nullptr;
+    if (lsb_create_grid(n_cases, dd.data(), params, phi0, stream, &g) == LSB_OK) {
+      // two untimed steps, then `steps` steps bracketed by events on the handle's stream
+      lsb_status s = lsb_step(g, 2);
+      if (s == LSB_OK && cudaEventRecord(e0, st) == cudaSuccess && (s = lsb_step(g, steps)) == LSB_OK &&
+          cudaEventRecord(e1, st) == cudaSuccess && (s = lsb_sync(g)) == LSB_OK) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms = t / steps;
+      }
+      if (s != LSB_OK) last_err = g->err;
+      lsb_destroy(g);
+    } else {
+      last_err = g_create_error;
+    }
+    if (ms_per_step) ms_per_step[k] = ms;
+    if (ms == ms && ms < best_ms) {
+      best_ms = ms;
+      for (int a = 0; a < 3; ++a) best[a] = cand[3 * k + a];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!(best_ms < INFINITY)) return fail(nullptr, LSB_EINVAL, "autotune: no candidate ran (%s)", last_err.c_str());
+  return LSB_OK;
+}
+
 lsb_status lsb_cell_updates(const lsb_grid *g, double *per_coarse_step, double *total_done) {
   if (!g) return LSB_EINVAL;
   if (per_coarse_step) *per_coarse_step = updates_per_step(g);

@@ -299,31 +299,57 @@ __global__ void k_ext_iter(Ctx C, BlockShape S, int glevel, const float *uin, fl
       continue;
     }
     const int crd[3] = {x, y, z};
+    // interior: all +-1 neighbours inside the box (direct offsets, face-neighbour band flags)
+    bool inner = true;
+    for (int a = 0; a < D; ++a) inner = inner && crd[a] >= 1 && crd[a] + 1 < L.n[a];
+    const float *phiL = C.phi + fo;
+    const int str[3] = {1, L.p[0], L.p[0] * L.p[1]};
     float nvec[3], gm = 0.f;
     for (int a = 0; a < D; ++a) {
-      int p[3] = {x, y, z}, m[3] = {x, y, z};
-      p[a] = clampwrap(L, a, crd[a] + 1);
-      m[a] = clampwrap(L, a, crd[a] - 1);
-      nvec[a] = 0.5f * (C.phi[fo + cidx(L, p[0], p[1], p[2])] - C.phi[fo + cidx(L, m[0], m[1], m[2])]);
+      if (inner) {
+        nvec[a] = 0.5f * (phiL[(unsigned)c + str[a]] - phiL[(unsigned)c - str[a]]);
+      } else {
+        int p[3] = {x, y, z}, m[3] = {x, y, z};
+        p[a] = clampwrap(L, a, crd[a] + 1);
+        m[a] = clampwrap(L, a, crd[a] - 1);
+        nvec[a] = 0.5f * (phiL[cidx(L, p[0], p[1], p[2])] - phiL[cidx(L, m[0], m[1], m[2])]);
+      }
       gm += nvec[a] * nvec[a];
     }
     gm = sqrtf(gm);
-    const float ph = C.phi[fo + c];
+    const float ph = phiL[c];
     const float sg = ph / sqrtf(ph * ph + 1.0f);
+    float u0[3];
+    for (int b = 0; b < D; ++b) u0[b] = uin[b * NF + fo + c];
     float acc[3] = {0.f, 0.f, 0.f};
     for (int a = 0; a < D; ++a) {
       const float va = gm > 0.f ? sg * nvec[a] / gm : 0.f;
-      int nb[3] = {x, y, z};
-      nb[a] = clampwrap(L, a, crd[a] + (va > 0.f ? -1 : 1));
-      const long long cn = cidx(L, nb[0], nb[1], nb[2]);
-      const float *src = in_band(C, L, S, nb[0], nb[1], nb[2]) ? uin : C.ut0;
+      const int dir = va > 0.f ? -1 : 1;
+      long long cn;
+      bool inb;
+      if (inner) {
+        cn = c + dir * str[a];
+        const int s0 = (crd[a] >> S.lg[a]) << S.lg[a];
+        const int q = crd[a] + dir;
+        if (q >= s0 && q < s0 + S.bs[a]) {
+          inb = true;  // own block (a band block)
+        } else {
+          const int bstr = a == 0 ? 1 : (a == 1 ? L.nb[0] : L.nb[0] * L.nb[1]);
+          inb = (C.bflag[gb + dir * bstr] & BF_BAND) != 0;
+        }
+      } else {
+        int nb[3] = {x, y, z};
+        nb[a] = clampwrap(L, a, crd[a] + dir);
+        cn = cidx(L, nb[0], nb[1], nb[2]);
+        inb = in_band(C, L, S, nb[0], nb[1], nb[2]);
+      }
+      const float *src = inb ? uin : C.ut0;
       for (int b = 0; b < D; ++b) {
-        const float u0 = uin[b * NF + fo + c];
         const float un = src[b * NF + fo + cn];
-        acc[b] += va * (va > 0.f ? (u0 - un) : (un - u0));
+        acc[b] += va * (va > 0.f ? (u0[b] - un) : (un - u0[b]));
       }
     }
-    for (int b = 0; b < D; ++b) uout[b * NF + fo + c] = uin[b * NF + fo + c] - L.dtau_ext * acc[b];
+    for (int b = 0; b < D; ++b) uout[b * NF + fo + c] = u0[b] - L.dtau_ext * acc[b];
   }
 }
 
@@ -341,6 +367,43 @@ __device__ __forceinline__ void gather7(const Ctx &C, const LevelDev &L, const B
     bool upd = pin != C.phi && in_band(C, L, S, p[0], p[1], p[2]);
     if (upd && use_frozen) upd = !C.frozen[cc];
     v[m] = upd ? pin[cc] : C.phi[cc];
+  }
+}
+
+// gather7 for a cell of band block gb (global id) at level offset c.  When the
+// seven points lie inside the box on axis a (no clamping or wrapping), they are
+// read at direct offsets, and a point's band membership is its own block's
+// (always in the band) or that of the face neighbour it falls into; otherwise the
+// general path above.  Same values as gather7.
+template <int D>
+__device__ __forceinline__ void gather7f(const Ctx &C, const LevelDev &L, const BlockShape &S, int gb,
+                                         const float *pin, bool use_frozen, int x, int y, int z, unsigned c, int a,
+                                         float v[7]) {
+  const int crd = a == 0 ? x : (a == 1 ? y : z);
+  if (crd < 3 || crd + 3 >= L.n[a] || S.bs[a] < 4) {  // the fast path assumes at most one block crossed
+    gather7<D>(C, L, S, pin, use_frozen, x, y, z, a, v);
+    return;
+  }
+  const float *phiL = C.phi + L.fine_off;
+  const float *pinL = pin + L.fine_off;
+  const uint8_t *frzL = C.frozen + L.fine_off;
+  const bool merged = pin != C.phi;
+  const int str = a == 0 ? 1 : (a == 1 ? L.p[0] : L.p[0] * L.p[1]);
+  const int s0 = (crd >> S.lg[a]) << S.lg[a], s1 = s0 + S.bs[a];
+  const int bstr = a == 0 ? 1 : (a == 1 ? L.nb[0] : L.nb[0] * L.nb[1]);
+  bool fm = false, fp = false;
+  if (merged) {
+    if (crd - 3 < s0) fm = (C.bflag[gb - bstr] & BF_BAND) != 0;
+    if (crd + 3 >= s1) fp = (C.bflag[gb + bstr] & BF_BAND) != 0;
+  }
+#pragma unroll
+  for (int m = 0; m < 7; ++m) {
+    const int q = crd + m - 3;
+    const unsigned off = c + (m - 3) * str;
+    bool upd = merged && (q < s0 ? fm : (q >= s1 ? fp : true));
+    if (upd && use_frozen) upd = !frzL[off];
+    const float *src = upd ? pinL : phiL;  // one load from the selected array
+    v[m] = src[off];
   }
 }
 
@@ -367,7 +430,7 @@ __global__ void k_adv_stage(Ctx C, BlockShape S, int glevel, int stage) {
     float rhs = 0.f;
     for (int a = 0; a < D; ++a) {
       float v[7];
-      gather7<D>(C, L, S, pin, false, x, y, z, a, v);
+      gather7<D>(C, L, S, pin, false, x, y, z, a, v);  // measured faster here than gather7f
       const float ua = C.ut0[a * C.nfine + fc];
       rhs -= ua * (ua >= 0.f ? d5m(v) : d5p(v));
     }
@@ -434,13 +497,14 @@ __global__ void k_reinit_stage(Ctx C, BlockShape S, int glevel, int stage) {
     int x, y, z;
     const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
-    const long long fc = L.fine_off + cidx(L, x, y, z);
+    const unsigned cl = (unsigned)cidx(L, x, y, z);
+    const long long fc = L.fine_off + cl;
     if (C.frozen[fc]) continue;
     const float s0 = C.s0[fc];
     float g2 = 0.f;
     for (int a = 0; a < D; ++a) {
       float v[7];
-      gather7<D>(C, L, S, pin, true, x, y, z, a, v);
+      gather7f<D>(C, L, S, gb, pin, true, x, y, z, cl, a, v);
       const float dm = weno5(v[1] - v[0], v[2] - v[1], v[3] - v[2], v[4] - v[3], v[5] - v[4]);
       const float dp = weno5(v[6] - v[5], v[5] - v[4], v[4] - v[3], v[3] - v[2], v[2] - v[1]);
       float ga;

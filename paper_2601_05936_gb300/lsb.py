@@ -72,6 +72,9 @@ def load():
     lib.lsb_cell_updates.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.lsb_backward.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
     lib.lsb_record.argtypes = [vp, ctypes.c_int]
+    lib.lsb_autotune.argtypes = [ctypes.c_int, ctypes.POINTER(GridDesc), ctypes.POINTER(Params),
+                                 ctypes.POINTER(ctypes.c_void_p), vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                 ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     lib.lsb_sync.argtypes = [vp]
     lib.lsb_kernel_launches.argtypes = [vp]
     lib.lsb_kernel_launches.restype = ctypes.c_uint64
@@ -89,7 +92,7 @@ def load():
     lib.lsb_kernel_count.argtypes = []
     lib.lsb_kernel_count.restype = ctypes.c_int
     for name in ("lsb_use_graphs", "lsb_get_fields_noalloc", "lsb_profile", "lsb_profile_read", "lsb_create_grid", "lsb_set_params", "lsb_step", "lsb_refine", "lsb_get_fields",
-                 "lsb_observables", "lsb_cell_updates", "lsb_backward", "lsb_record", "lsb_sync"):
+                 "lsb_observables", "lsb_cell_updates", "lsb_backward", "lsb_record", "lsb_autotune", "lsb_sync"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -155,6 +158,55 @@ def _params(case, D):
     return p
 
 
+def _marshal(cases, device):
+    """ctypes arrays of descriptors and parameters, and the device copies of phi0."""
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("lsb needs a CUDA device; there is no CPU fallback")
+    n = len(cases)
+    descs = (GridDesc * n)()
+    params = (Params * n)()
+    D = None
+    phis = []
+    for c, case in enumerate(cases):
+        d, D = _desc(case)
+        descs[c] = d
+        params[c] = _params(case, D)
+        phis.append(torch.as_tensor(np.ascontiguousarray(np.asarray(case["phi0"], np.float32).reshape(-1)),
+                                    device=f"cuda:{device}"))
+    ptrs = (ctypes.c_void_p * n)(*[t.data_ptr() for t in phis])
+    return descs, params, ptrs, phis, D
+
+
+def autotune(cases, candidates=None, steps=10, stream=None, device=0):
+    """Time each block shape on these cases (lsb_autotune).  candidates: list of
+    (bx, by, bz) or None for the built-in list.  Returns (best shape, {shape: ms per
+    coarse step or nan})."""
+    lib = load()
+    if isinstance(cases, dict):
+        cases = [cases]
+    descs, params, ptrs, phis, D = _marshal(cases, device)
+    if candidates is None:
+        cand = None
+        nc = 6
+        shapes = None
+    else:
+        shapes = [tuple(int(v) for v in (list(c) + [1, 1])[:3]) for c in candidates]
+        nc = len(shapes)
+        cand = (ctypes.c_int * (3 * nc))(*[v for sh in shapes for v in sh])
+    best = (ctypes.c_int * 3)()
+    ms = (ctypes.c_double * nc)()
+    sp = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    st = lib.lsb_autotune(len(cases), descs, params, ptrs, sp, cand, nc, int(steps), best, ms)
+    if st != 0:
+        raise LsbError(st, lib.lsb_last_error(None).decode())
+    if shapes is None:
+        shapes = [None] * nc
+    res = {(sh if sh is not None else k): ms[k] for k, sh in enumerate(shapes)}
+    return tuple(best), res
+
+
 class Grid:
     """One handle of the library: an ensemble of one or more cases.
 
@@ -165,28 +217,12 @@ class Grid:
     """
 
     def __init__(self, cases, stream=None, device=0):
-        import torch
-
-        if not torch.cuda.is_available():
-            raise RuntimeError("lsb needs a CUDA device; there is no CPU fallback")
         self.lib = load()
         if isinstance(cases, dict):
             cases = [cases]
         self.cases = cases
         n = len(cases)
-        descs = (GridDesc * n)()
-        params = (Params * n)()
-        self.D = None
-        self._phi = []
-        for c, case in enumerate(cases):
-            d, D = _desc(case)
-            descs[c] = d
-            params[c] = _params(case, D)
-            self.D = D
-            phi = torch.as_tensor(np.ascontiguousarray(np.asarray(case["phi0"], np.float32).reshape(-1)),
-                                  device=f"cuda:{device}")
-            self._phi.append(phi)
-        ptrs = (ctypes.c_void_p * n)(*[t.data_ptr() for t in self._phi])
+        descs, params, ptrs, self._phi, self.D = _marshal(cases, device)
         self.stream = stream
         sp = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
         h = ctypes.c_void_p()

@@ -52,3 +52,10 @@ def test_status_codes_match_header():
     hdr = open(os.path.join(ROOT, "include", "lsb.h")).read()
     for code, name in lsb.STATUS.items():
         assert re.search(rf"{name}\s*=\s*{code}\b", hdr), name
+
+
+def test_autotune_rejects_bad_input_without_gpu(lib):
+    best = (ctypes.c_int * 3)()
+    st = lib.lsb_autotune(1, None, None, None, None, None, 0, 10, best, None)
+    assert st == 1
+    assert b"autotune" in lib.lsb_last_error(None)
