@@ -230,6 +230,8 @@ def main():
                          "(collide-and-stream only, for profiling captures); ensemble: 64 uneven 2D bubbles; "
                          "adjoint3d: reverse sweep over --steps recorded steps of a frozen 3D bubble")
     ap.add_argument("--checkpoint-every", type=int, default=100)
+    ap.add_argument("--driver", type=int, default=0, choices=[0, 1],
+                    help="level-set passes: 0 one launch each, 1 one persistent cooperative launch per finest step")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="bubble3d only: linear scale of the box and bubble (profiling captures of a smaller copy)")
     args = ap.parse_args()
@@ -272,6 +274,7 @@ def main():
         case = cases[0]
     stream = torch.cuda.Stream()
     g = lsb.Grid(cases, stream=stream, device=local)
+    g.set_driver(args.driver)
     g.step(args.warmup)
     g.sync()
 
@@ -360,7 +363,7 @@ def main():
                 ms_per_step=ms_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f32" if args.storage == "fp32" else "f16-store/f32-compute", data="synthetic",
                 config=dict(workload=wname, lattice=lattice, levels=int(case["n_levels"]),
-                            storage=args.storage, parallelism=f"replicas{world}",
+                            storage=args.storage, parallelism=f"replicas{world}", driver=args.driver,
                             cell_updates_per_step=upd / args.steps, l2_flush="state 5.7 GB >> 129 MB L2",
                             bubble=dict(centroid=[float(v) if np.isfinite(v) else None for v in obs["centroid"]],
                                         velocity=[float(v) if np.isfinite(v) else None for v in obs["velocity"]])),

@@ -140,6 +140,18 @@ lsb_status lsb_step(lsb_grid *g, int n);
  * otherwise).  Results are identical to eager stepping. */
 lsb_status lsb_use_graphs(lsb_grid *g, int enable);
 
+/*
+ * Launch structure of the level-set update (Sec. 2.2 passes: extension sweeps,
+ * TVD-RK3 transport, reinitialisation).  mode 0 (default): one launch per pass
+ * (up to 16 per finest step).  mode 1: one persistent cooperative launch per
+ * finest step that runs every pass over the band work list of all cases, with
+ * a device-wide barrier between passes; the barrier's wait has an iteration
+ * limit, and on expiry the kernel ends and the next synchronising call returns
+ * LSB_ETIMEOUT.  Both modes give identical results.  Errors: LSB_EINVAL (bad
+ * mode, or no cooperative launch on this device).
+ */
+lsb_status lsb_set_driver(lsb_grid *g, int mode);
+
 /* Run the refinement sensor and regrid every case now (Sec. 2.6). */
 lsb_status lsb_refine(lsb_grid *g);
 

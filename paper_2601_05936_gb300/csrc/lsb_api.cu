@@ -27,8 +27,9 @@ namespace {
 constexpr int MAXL = 4;
 const char *const KNAMES[] = {"k_collide_stream", "k_interface_bc", "k_restrict", "k_ghost", "k_prolong", "k_level_tags", "k_observables", "k_export", "k_classify_phase", "k_classify_links", "k_band", "k_geometry", "k_ext_init", "k_ext_iter", "k_adv_stage", "k_reinit_prep", "k_reinit_stage", "k_refill", "k_sensor", "k_init", "k_collect",
                                "k_collide_stream_l1", "k_collide_stream_l2", "k_collide_stream_l3", "k_adj_seed",
-                               "k_adj_links", "k_adj_collide", "k_adj_macro", "k_adj_geometry"};
-constexpr int KADJ_SEED = 24, KADJ_LINKS = 25, KADJ_COLLIDE = 26, KADJ_MACRO = 27, KADJ_GEOM = 28;
+                               "k_adj_links", "k_adj_collide", "k_adj_macro", "k_adj_geometry",
+                               "k_levelset_persistent"};
+constexpr int KADJ_SEED = 24, KADJ_LINKS = 25, KADJ_COLLIDE = 26, KADJ_MACRO = 27, KADJ_GEOM = 28, KLS_PERSIST = 29;
 constexpr int NKERN = sizeof(KNAMES) / sizeof(KNAMES[0]);
 
 struct ProfRec {
@@ -84,6 +85,8 @@ struct lsb_grid {
   int *d_cbase = nullptr;
   float *d_macro = nullptr, *d_nvec = nullptr, *d_kappa = nullptr, *d_linkbuf = nullptr;
   int *d_counters = nullptr, *d_err = nullptr, *d_band = nullptr;
+  unsigned *d_bar = nullptr;  // grid barrier of the persistent level-set kernel
+  int driver = 0;             // 0: one launch per level-set pass, 1: one persistent launch
   int2 *d_iface = nullptr, *d_flip = nullptr;
   double *d_obs = nullptr;
   float *d_sens = nullptr;
@@ -455,6 +458,12 @@ lsb_status levelset(lsb_grid *g, int l) {
   const int nb = std::max(1, std::min(g->band_cap, 152 * 16));
   const int nt = g->nthreads;
   const int Q = g->Q, D = g->D;
+  if (g->driver == 1) {
+    const bool due = g->reinit_every > 0 && ((g->fine_steps[l] + 1) % g->reinit_every == 0) && g->n_reinit > 0;
+    RUN(KLS_PERSIST, 0, 1, nt, run_levelset_persistent, Q, LN(g, nb, nt), C, S, l, g->n_ext, due ? 1 : 0,
+        g->n_reinit, g->d_bar);
+    return LSB_OK;
+  }
   RUN(12, 0, 1, 128, run_ext_init, Q, LN(g, DYN_GRID, 128), C, l);
   const float *uin = g->d_ut[0];
   for (int it = 0; it < g->n_ext; ++it) {
@@ -908,6 +917,7 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
   ALLOC(g->d_linkbuf, 8 * g->link_cap);
   ALLOC(g->d_counters, sizeof(int) * MAXL * NCOUNT);
   ALLOC(g->d_err, sizeof(int));
+  ALLOC(g->d_bar, 2 * sizeof(unsigned));
   ALLOC(g->d_iface, sizeof(int2) * MAXL * g->list_cap);
   ALLOC(g->d_flip, sizeof(int2) * MAXL * g->list_cap);
   ALLOC(g->d_band, sizeof(int) * MAXL * (size_t)std::max(1, g->band_cap));
@@ -935,6 +945,7 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
       cuerr(cudaMemset(g->d_tag, 0, g->ncell_total), "tag") ||
       cuerr(cudaMemset(g->d_bflag, 0, g->nblock_total), "bflag") ||
       cuerr(cudaMemset(g->d_err, 0, sizeof(int)), "err") ||
+      cuerr(cudaMemset(g->d_bar, 0, 2 * sizeof(unsigned)), "barrier") ||
       cuerr(cudaMemset(g->d_counters, 0, sizeof(int) * MAXL * NCOUNT), "counters") ||
       cuerr(cudaMemset(g->d_cmask, 0, 4 * nf), "cmask") ||
       cuerr(cudaMemset(g->d_nvec, 0, 4 * D * nf), "nvec") ||
@@ -1029,6 +1040,19 @@ lsb_status lsb_use_graphs(lsb_grid *g, int enable) {
   if (enable && !g->stream) return fail(g, LSB_EINVAL, "CUDA graphs need a non-default stream");
   g->use_graphs = enable;
   if (!enable) drop_graphs(g);
+  return LSB_OK;
+}
+
+lsb_status lsb_set_driver(lsb_grid *g, int mode) {
+  if (!g || (mode != 0 && mode != 1)) return LSB_EINVAL;
+  if (mode == 1) {
+    int dev = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop) return fail(g, LSB_EINVAL, "the device does not support cooperative launches");
+  }
+  if (mode != g->driver) drop_graphs(g);  // captured launch sequences change
+  g->driver = mode;
   return LSB_OK;
 }
 

@@ -51,6 +51,8 @@ cudaError_t run_adv_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int 
 cudaError_t run_reinit_prep(int Q, Launch L, Ctx C, BlockShape S, int glevel);
 cudaError_t run_reinit_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage);
 cudaError_t run_refill(int Q, int st, Launch L, Ctx C, int glevel);
+cudaError_t run_levelset_persistent(int Q, Launch L, Ctx C, BlockShape S, int glevel, int n_ext, int reinit,
+                                    int n_reinit, unsigned *bar);
 cudaError_t run_sensor(Launch L, Ctx C, BlockShape S, const int *list, int n, int mode, float *out);
 
 // lsb_adj.cu: adjoint of the frozen-interface step

@@ -243,7 +243,7 @@ __global__ void k_geometry(Ctx C, int glevel, int which) {
 // ------------------------------------------------------------------ velocity extension
 // Interface cells: mean of u_I = (1-q) u(x) + q u(x + c_i) over their cut links.
 template <int Q>
-__global__ void k_ext_init(Ctx C, int glevel) {
+__device__ __forceinline__ void d_ext_init(const Ctx &C, int glevel) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   const int n = min(C.counters[glevel * NCOUNT + 1], (int)C.list_cap);
@@ -274,12 +274,14 @@ __global__ void k_ext_init(Ctx C, int glevel) {
     for (int a = 0; a < D; ++a) C.ut0[a * NF + fo + c] = acc[a] / (float)cnt;
   }
 }
+template <int Q>
+__global__ void k_ext_init(Ctx C, int glevel) { d_ext_init<Q>(C, glevel); }
 
 // One Jacobi sweep of first-order upwind extension on the band (interface cells
 // copy their value).  Neighbours outside the band read the committed field ut0.
 // commit = 1: copy uin into ut0 on the band instead.
 template <int D>
-__global__ void k_ext_iter(Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int commit) {
+__device__ __forceinline__ void d_ext_iter(const Ctx &C, BlockShape S, int glevel, const float *uin, float *uout, int commit) {
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
   const int *lst = C.band_list + (long long)glevel * C.band_cap;
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
@@ -352,6 +354,8 @@ __global__ void k_ext_iter(Ctx C, BlockShape S, int glevel, const float *uin, fl
     for (int b = 0; b < D; ++b) uout[b * NF + fo + c] = u0[b] - L.dtau_ext * acc[b];
   }
 }
+template <int D>
+__global__ void k_ext_iter(Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int commit) { d_ext_iter<D>(C, S, glevel, uin, uout, commit); }
 
 // ------------------------------------------------------------------ transport
 // Gather phi along axis a at offsets -3..+3; points in the band (and, for the
@@ -417,7 +421,7 @@ __device__ __forceinline__ float d5p(const float v[7]) {  // mirror image
 // TVD-RK3 stage of d phi/dt = -u~ . grad phi on the band (dt = 1):
 // stage 1: p1 = phi + L(phi); 2: p2 = 3/4 phi + 1/4 (p1 + L(p1)); 3: phi = 1/3 phi + 2/3 (p2 + L(p2)).
 template <int D>
-__global__ void k_adv_stage(Ctx C, BlockShape S, int glevel, int stage) {
+__device__ __forceinline__ void d_adv_stage(const Ctx &C, BlockShape S, int glevel, int stage) {
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
   const int *lst = C.band_list + (long long)glevel * C.band_cap;
   const float *pin = stage == 1 ? C.phi : (stage == 2 ? C.p1 : C.p2);
@@ -440,11 +444,13 @@ __global__ void k_adv_stage(Ctx C, BlockShape S, int glevel, int stage) {
     else C.phi[fc] = p0 / 3.0f + (2.0f / 3.0f) * (C.p2[fc] + rhs);
   }
 }
+template <int D>
+__global__ void k_adv_stage(Ctx C, BlockShape S, int glevel, int stage) { d_adv_stage<D>(C, S, glevel, stage); }
 
 // ------------------------------------------------------------------ reinitialisation
 // Frozen cells (sign change to any lattice neighbour in the box) and S(phi0).
 template <int Q>
-__global__ void k_reinit_prep(Ctx C, BlockShape S, int glevel) {
+__device__ __forceinline__ void d_reinit_prep(const Ctx &C, BlockShape S, int glevel) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
@@ -468,6 +474,8 @@ __global__ void k_reinit_prep(Ctx C, BlockShape S, int glevel) {
     C.s0[fc] = p / sqrtf(p * p + 1.0f);
   }
 }
+template <int Q>
+__global__ void k_reinit_prep(Ctx C, BlockShape S, int glevel) { d_reinit_prep<Q>(C, S, glevel); }
 
 // HJ-WENO5 one-sided derivative (Jiang & Peng 2000) from the five differences.
 __device__ __forceinline__ float weno5(float v1, float v2, float v3, float v4, float v5) {
@@ -488,7 +496,7 @@ __device__ __forceinline__ float weno5(float v1, float v2, float v3, float v4, f
 
 // TVD-RK3 stage of phi_tau = -S(phi0)(|grad phi|_G - 1) on band cells that are not frozen.
 template <int D>
-__global__ void k_reinit_stage(Ctx C, BlockShape S, int glevel, int stage) {
+__device__ __forceinline__ void d_reinit_stage(const Ctx &C, BlockShape S, int glevel, int stage) {
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
   const int *lst = C.band_list + (long long)glevel * C.band_cap;
   const float *pin = stage == 1 ? C.phi : (stage == 2 ? C.p1 : C.p2);
@@ -517,6 +525,80 @@ __global__ void k_reinit_stage(Ctx C, BlockShape S, int glevel, int stage) {
     if (stage == 1) C.p1[fc] = p0 + rhs;
     else if (stage == 2) C.p2[fc] = 0.75f * p0 + 0.25f * (C.p1[fc] + rhs);
     else C.phi[fc] = p0 / 3.0f + (2.0f / 3.0f) * (C.p2[fc] + rhs);
+  }
+}
+template <int D>
+__global__ void k_reinit_stage(Ctx C, BlockShape S, int glevel, int stage) { d_reinit_stage<D>(C, S, glevel, stage); }
+
+// ------------------------------------------------------------------ persistent level-set phase
+// The whole level-set update of a finest level (extension, transport,
+// reinitialisation: up to 16 dependent passes over the band list) as one
+// cooperative launch, with a grid barrier between passes.  The barrier spins
+// with an iteration limit: on expiry the block sets ERR_TIMEOUT and returns, so
+// a barrier that cannot complete ends the kernel instead of hanging it (the
+// cooperative launch makes every CTA resident, so this does not happen in
+// normal operation).  bar: two words, arrival count and generation, zero at rest.
+constexpr long kBarrierLimit = 1L << 22;  // x ~64 ns sleeps: ~0.3 s
+
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
+  __shared__ int abort_flag;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    volatile unsigned *vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long it = 0;
+      while (*vgen == gen) {
+        if (++it > kBarrierLimit) {
+          atomicOr(err, ERR_TIMEOUT);
+          abort_flag = 1;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return abort_flag == 0;
+}
+
+template <int Q>
+__global__ void k_levelset_persistent(Ctx C, BlockShape S, int glevel, int n_ext, int reinit, int n_reinit,
+                                      unsigned *bar) {
+  constexpr int D = Lat<Q>::D;
+  d_ext_init<Q>(C, glevel);
+  if (!grid_barrier(bar, C.err)) return;
+  const float *uin = C.ut0;
+  for (int it = 0; it < n_ext; ++it) {
+    float *uout = (it & 1) ? C.ut2 : C.ut1;
+    d_ext_iter<D>(C, S, glevel, uin, uout, 0);
+    if (!grid_barrier(bar, C.err)) return;
+    uin = uout;
+  }
+  if (n_ext > 0) {
+    d_ext_iter<D>(C, S, glevel, uin, nullptr, 1);
+    if (!grid_barrier(bar, C.err)) return;
+  }
+  for (int st = 1; st <= 3; ++st) {
+    d_adv_stage<D>(C, S, glevel, st);
+    if (!grid_barrier(bar, C.err)) return;
+  }
+  if (reinit) {
+    d_reinit_prep<Q>(C, S, glevel);
+    if (!grid_barrier(bar, C.err)) return;
+    for (int r = 0; r < n_reinit; ++r)
+      for (int st = 1; st <= 3; ++st) {
+        d_reinit_stage<D>(C, S, glevel, st);
+        if (!grid_barrier(bar, C.err)) return;
+      }
   }
 }
 
@@ -763,6 +845,19 @@ cudaError_t run_refill(int Q, int st, Launch L, Ctx C, int glevel) {
 cudaError_t run_sensor(Launch L, Ctx C, BlockShape S, const int *list, int n, int mode, float *out) {
   k_sensor<<<L.grid, L.block, 0, L.stream>>>(C, S, list, n, mode, out);
   return cudaGetLastError();
+}
+
+// One cooperative launch of the level-set phase; grid = resident CTAs (required
+// for a cooperative launch, which fails rather than oversubscribe).
+cudaError_t run_levelset_persistent(int Q, Launch L, Ctx C, BlockShape S, int glevel, int n_ext, int reinit,
+                                    int n_reinit, unsigned *bar) {
+  void *args[] = {&C, &S, &glevel, &n_ext, &reinit, &n_reinit, &bar};
+  if (Q == 9) {
+    const int grid = resident_grid(k_levelset_persistent<9>, L.block, L.grid);
+    return cudaLaunchCooperativeKernel((const void *)k_levelset_persistent<9>, grid, L.block, args, 0, L.stream);
+  }
+  const int grid = resident_grid(k_levelset_persistent<19>, L.block, L.grid);
+  return cudaLaunchCooperativeKernel((const void *)k_levelset_persistent<19>, grid, L.block, args, 0, L.stream);
 }
 
 }  // namespace lsb

@@ -72,6 +72,7 @@ def load():
     lib.lsb_cell_updates.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.lsb_backward.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
     lib.lsb_record.argtypes = [vp, ctypes.c_int]
+    lib.lsb_set_driver.argtypes = [vp, ctypes.c_int]
     lib.lsb_autotune.argtypes = [ctypes.c_int, ctypes.POINTER(GridDesc), ctypes.POINTER(Params),
                                  ctypes.POINTER(ctypes.c_void_p), vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                  ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
@@ -92,7 +93,7 @@ def load():
     lib.lsb_kernel_count.argtypes = []
     lib.lsb_kernel_count.restype = ctypes.c_int
     for name in ("lsb_use_graphs", "lsb_get_fields_noalloc", "lsb_profile", "lsb_profile_read", "lsb_create_grid", "lsb_set_params", "lsb_step", "lsb_refine", "lsb_get_fields",
-                 "lsb_observables", "lsb_cell_updates", "lsb_backward", "lsb_record", "lsb_autotune", "lsb_sync"):
+                 "lsb_observables", "lsb_cell_updates", "lsb_backward", "lsb_record", "lsb_autotune", "lsb_set_driver", "lsb_sync"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -242,6 +243,10 @@ class Grid:
     def use_graphs(self, enable=True):
         """Replay two coarse steps at a time from CUDA graphs (needs a non-default stream)."""
         self._check(self.lib.lsb_use_graphs(self.h, 1 if enable else 0))
+
+    def set_driver(self, mode):
+        """0: one launch per level-set pass; 1: one persistent cooperative launch per finest step."""
+        self._check(self.lib.lsb_set_driver(self.h, int(mode)))
 
     def refine(self):
         self._check(self.lib.lsb_refine(self.h))

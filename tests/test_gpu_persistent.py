@@ -1,0 +1,63 @@
+"""Persistent level-set driver (lsb_set_driver(g, 1)): the extension, transport
+and reinitialisation passes of a finest step run as one cooperative launch with
+bounded device-wide barriers between passes.  The passes are the same code as
+the per-pass launches, so the state must match them exactly, with and without
+CUDA-graph replay, for single cases and ensembles."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(cases, steps, driver, graphs=False):
+    import torch
+
+    from paper_2601_05936_gb300 import lsb
+    st = torch.cuda.Stream()
+    g = lsb.Grid(cases, stream=st)
+    g.set_driver(driver)
+    if graphs:
+        g.use_graphs(True)
+    g.step(steps)
+    g.sync()
+    out = []
+    for k, c in enumerate(g.cases):
+        L = int(c.get("n_levels", 1))
+        out += [g.get(f, k, l) for l in range(L) for f in ("rho", "u")] + [g.get("phi", k), g.get("tag", k)]
+    g.close()
+    return out
+
+
+def _same(a, b):
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_persistent_matches_per_pass_2d_bubble_with_regrid():
+    from tests.test_gpu_parity import _bubble2d
+    case = _bubble2d(N=64, R=6.0, levels=2, rr=100.0, nu=(0.06, 0.6), g=2e-5, sigma=2e-3)
+    case["refine_dist"] = [8.0]
+    case["regrid_every"] = 6
+    _same(_run(case, 15, 0), _run(case, 15, 1))
+
+
+def test_persistent_with_graphs_matches_eager():
+    from tests.test_gpu_parity import _bubble2d
+    case = _bubble2d(N=64, R=6.0, levels=2, rr=100.0, nu=(0.06, 0.6), g=2e-5, sigma=2e-3)
+    _same(_run(case, 12, 0), _run(case, 12, 1, graphs=True))
+
+
+def test_persistent_matches_per_pass_3d_and_ensemble():
+    from paper_2601_05936_gb300 import workloads
+    c3 = workloads.rising_bubble_3d(scale=0.25)
+    _same(_run(c3, 6, 0), _run(c3, 6, 1))
+    ens = workloads.ensemble(n_cases=3, w_range=(96, 128))
+    _same(_run(ens, 6, 0), _run(ens, 6, 1))
+
+
+def test_set_driver_rejects_bad_mode():
+    from paper_2601_05936_gb300 import lsb, workloads
+    g = lsb.Grid(workloads.stratified_channel(steps=1))
+    with pytest.raises(lsb.LsbError):
+        g.set_driver(2)
+    g.close()
