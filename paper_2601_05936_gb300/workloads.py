@@ -173,7 +173,11 @@ def adjoint_window(lattice="D2Q9", seed=6000, n=(32, 24), steps=20, warmup=10):
     R = 0.18 * min(n) + rng.random()
     bubble = R - np.sqrt(sum((cen[a] - c[a]) ** 2 for a in range(D)))
     h0 = 0.75 + 0.1 * rng.random()
-    film = h0 + 0.05 * np.sin(2 * np.pi * cen[0] / n[0]) - cen[D - 1]
+    # phase-shifted modulations: no cell centre sits on an extremum, so no normal
+    # component is exactly zero (the upwind choice of the extension has a kink there)
+    film = h0 + 0.05 * np.sin(2 * np.pi * cen[0] / n[0] + 0.37) - cen[D - 1]
+    if D == 3:
+        film = film + 0.03 * np.sin(2 * np.pi * cen[1] / n[1] + 1.13)
     phi = np.maximum(bubble, film)
     wall_u = np.zeros((2 * D, D))
     wall_u[2 * D - 1, 0] = 0.02  # top wall moves along x
