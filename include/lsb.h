@@ -67,8 +67,10 @@ enum {
                           k's source lies in the other phase (finest level)       */
   LSB_FIELD_KAPPA = 8, /* curvature at interface cells (float, finest level)      */
   LSB_FIELD_UEXT = 9,  /* extension velocity u~ (D x cells, finest level)         */
-  LSB_FIELD_ADJ_F = 10 /* after lsb_backward: dJ/df at the start of the recorded
+  LSB_FIELD_ADJ_F = 10,/* after lsb_backward: dJ/df at the start of the recorded
                           window (float, Q x cells, Fig. 1 order)                 */
+  LSB_FIELD_ADJ_UEXT = 11 /* after lsb_backward over a moving level set: dJ/du~ at
+                          the start of the window (D x cells, finest level)      */
 };
 
 /* Geometry and discretisation of one case, fixed for the handle's life. */
@@ -235,42 +237,57 @@ int lsb_lattice_table(int lattice, int *c, float *w, int *opp);
 
 /*
  * Adjoint (the paper has no counterpart; the differentiated map is its
- * step, Sec. 2.1 and 2.3).  With the level set frozen (ls_active = 0 in every
- * case) the phases, cut links, q, n and kappa are constants and one step is
- * a smooth map of the populations; lsb_backward computes, for
- * J = sum over cases of dJ_dobs . observables (the lsb_observables vector
- * after the last recorded step), the exact derivatives of that discrete map
- * by a hand-written reverse sweep: transposes of the collision with forcing,
- * the streaming with wall bounce-back, and the interface bounce-back of
- * Eq. bb with Eq. bb_cc and Eq. Sdecomp.
+ * step, Sec. 2).  lsb_backward computes, for J = sum over cases of
+ * dJ_dobs . observables (the lsb_observables vector after the last recorded
+ * step), the exact derivatives of the discrete step map by a hand-written
+ * reverse sweep, on windows where the discrete decisions of the method stay
+ * fixed:
+ *  - frozen level set (ls_active = 0 in every case): the phases, cut links,
+ *    q, n and kappa are constants; transposes of the collision with forcing,
+ *    the streaming with wall bounce-back and the interface bounce-back of
+ *    Eq. bb with Eq. bb_cc and Eq. Sdecomp;
+ *  - moving level set (ls_active = 1 in every case, reinit_every <= 1,
+ *    n_reinit <= 1): the state is (f, phi, u~) and the sweep also transposes
+ *    the interface velocity, the extension sweeps (Eq.
+ *    hyperbolicExtension), the TVD-RK3 upwind-5 transport and the HJ-WENO5
+ *    reinitialisation (Sec. 2.2), with phases, cut links, band, frozen cells,
+ *    upwind sides and Godunov branches as in the forward steps.  No cell may
+ *    change phase inside the window (refill is not differentiated):
+ *    lsb_backward returns LSB_ESTATE if one did.
  *
  * lsb_record(g, checkpoint_every): start a recording at the current state.
  * The following lsb_step calls run eagerly (no CUDA graphs) and copy the
- * state into a device checkpoint at the start of every checkpoint_every-th
- * step (one buffer of Q x cells floats each, allocated as needed).  A new
- * lsb_record, lsb_set_params or lsb_refine ends the recording and frees the
- * checkpoints.  Errors: LSB_EINVAL (checkpoint_every < 1), LSB_ESTATE
- * (more than one level, FP16 storage, or a case with ls_active != 0).
+ * state (populations; with a moving level set also phi and u~) into a device
+ * checkpoint at the start of every checkpoint_every-th step (allocated as
+ * needed).  A new lsb_record, lsb_set_params or lsb_refine ends the
+ * recording and frees the checkpoints.  Errors: LSB_EINVAL
+ * (checkpoint_every < 1), LSB_ESTATE (more than one level, FP16 storage,
+ * cases mixing live and frozen level sets, or a moving level set with
+ * reinit_every > 1 or n_reinit > 1).
  *
  * lsb_backward(g, dJ_dobs, dJ_dparams, dJ_dphi0): reverse sweep over every
  * step recorded so far.  Segment by segment, from the last, it restores the
  * checkpoint, recomputes the segment's steps keeping their states (device
- * memory for checkpoint_every states), and runs the adjoint steps backwards.
+ * memory for checkpoint_every states), and runs the adjoint steps backwards
+ * (with a moving level set each adjoint step first replays that step's
+ * level-set passes).
  * dJ_dobs: host, n_cases x (4 + 2 D) doubles, weights of the observables
  * in lsb_observables order (centroid, volume and leaf count are constants of
- * the frozen map).  dJ_dparams: host, n_cases x LSB_NPARAM_ADJ doubles, or
- * NULL; per case dJ/dsigma, dJ/drho[0], dJ/drho[1], dJ/dnu[0], dJ/dnu[1] at
- * the recorded start state.  dJ_dphi0: device, or NULL; receives for each
- * case in order the dense finest-level array (x fastest) of dJ/dphi of the
- * frozen level set: through the link fractions q (radiation theorem, Sec.
- * 2.3) and the interface cells' normal and curvature from the least-squares
- * quadratic fit (Sec. 2.2).  Valid for perturbations of phi that change no
- * sign (the masks are constants of the map).  Afterwards the state is that
- * of the last recorded step again, the recording stays open (lsb_backward
- * may be called again, e.g. with other weights, and lsb_step extends the
- * recording), and LSB_FIELD_ADJ_F returns dJ/df at the start of the
- * window.  FP32 adjoint populations, FP64 parameter sums.  Synchronises.
- * Errors: LSB_EINVAL, LSB_ESTATE (no recording), LSB_ENOMEM, LSB_ECUDA.
+ * the map).  dJ_dparams: host, n_cases x LSB_NPARAM_ADJ doubles, or NULL;
+ * per case dJ/dsigma, dJ/drho[0], dJ/drho[1], dJ/dnu[0], dJ/dnu[1] at the
+ * recorded start state.  dJ_dphi0: device, or NULL; receives for each case
+ * in order the dense finest-level array (x fastest) of dJ/dphi at the start
+ * of the window: frozen level set: through the link fractions q (radiation
+ * theorem, Sec. 2.3) and the interface cells' normal and curvature from the
+ * least-squares fit (Sec. 2.2); moving level set: through every pass of
+ * every step.  Valid for perturbations of phi that change no sign.
+ * Afterwards the state is that of the last recorded step again, the
+ * recording stays open (lsb_backward may be called again, e.g. with other
+ * weights, and lsb_step extends the recording), LSB_FIELD_ADJ_F returns dJ/df
+ * and, with a moving level set, LSB_FIELD_ADJ_UEXT dJ/du~ at the start of the
+ * window.  FP32 adjoint fields, FP64 parameter sums.  Synchronises.  Errors:
+ * LSB_EINVAL, LSB_ESTATE (no recording, or a phase change in the window),
+ * LSB_ENOMEM, LSB_ECUDA.
  */
 enum { LSB_NPARAM_ADJ = 5 };
 lsb_status lsb_record(lsb_grid *g, int checkpoint_every);

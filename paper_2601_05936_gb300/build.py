@@ -1,6 +1,6 @@
 """Build the lsb CUDA library (liblsb.so) in-tree for sm_103a with nvcc.
 
-Four translation units are compiled in parallel and linked into
+Five translation units are compiled in parallel and linked into
 paper_2601_05936_gb300/_lib/liblsb.so.  Nothing here runs on the GPU.
 """
 import concurrent.futures as cf
@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblsb.so")
-SOURCES = ["lsb_lb.cu", "lsb_ls.cu", "lsb_adj.cu", "lsb_api.cu"]
+SOURCES = ["lsb_lb.cu", "lsb_ls.cu", "lsb_adj.cu", "lsb_adj_ls.cu", "lsb_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

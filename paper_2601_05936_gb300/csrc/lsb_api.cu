@@ -28,8 +28,9 @@ constexpr int MAXL = 4;
 const char *const KNAMES[] = {"k_collide_stream", "k_interface_bc", "k_restrict", "k_ghost", "k_prolong", "k_level_tags", "k_observables", "k_export", "k_classify_phase", "k_classify_links", "k_band", "k_geometry", "k_ext_init", "k_ext_iter", "k_adv_stage", "k_reinit_prep", "k_reinit_stage", "k_refill", "k_sensor", "k_init", "k_collect",
                                "k_collide_stream_l1", "k_collide_stream_l2", "k_collide_stream_l3", "k_adj_seed",
                                "k_adj_links", "k_adj_collide", "k_adj_macro", "k_adj_geometry",
-                               "k_levelset_persistent"};
-constexpr int KADJ_SEED = 24, KADJ_LINKS = 25, KADJ_COLLIDE = 26, KADJ_MACRO = 27, KADJ_GEOM = 28, KLS_PERSIST = 29;
+                               "k_levelset_persistent", "k_lsa"};
+constexpr int KADJ_SEED = 24, KADJ_LINKS = 25, KADJ_COLLIDE = 26, KADJ_MACRO = 27, KADJ_GEOM = 28, KLS_PERSIST = 29,
+              KLSA = 30;
 constexpr int NKERN = sizeof(KNAMES) / sizeof(KNAMES[0]);
 
 struct ProfRec {
@@ -127,10 +128,17 @@ struct lsb_grid {
   std::vector<float *> rec_ckpt;  // state at the start of steps 0, every, 2 every, ...
   float *d_seg = nullptr;         // states of one recomputed segment
   int seg_cap = 0;
+  size_t seg_slot = 0;            // bytes per stored state
   float *d_adj[2] = {nullptr, nullptr};
   int adj_cur = -1;               // d_adj[adj_cur] holds dJ/df_0 after lsb_backward
   float *d_fsave = nullptr, *d_madj = nullptr, *d_linkadj = nullptr;
   float *d_gphi = nullptr, *d_gn = nullptr, *d_gk = nullptr;  // level-set adjoint (finest level)
+  // moving level set: the state is (f, phi, u~); scratch of the level-set replay and transposes
+  int rec_moving = 0;
+  int *d_recflip = nullptr;  // set when a recorded step flipped a cell
+  float *d_lsa = nullptr;    // one allocation, carved by lsa_ptrs()
+  size_t lsa_floats = 0;
+  float *d_phisave = nullptr, *d_utsave = nullptr;
   double *d_grad = nullptr, *d_wobs = nullptr;
 };
 
@@ -721,15 +729,67 @@ void rec_clear(lsb_grid *g) {
   g->adj_cur = -1;
 }
 
+// One stored state: the populations, plus phi and u~ (finest level) when the level set moves.
+size_t slot_floats(const lsb_grid *g) {
+  return state_floats(g) + (g->rec_moving ? (size_t)(1 + g->D) * g->nfine : 0);
+}
+
 // Copy the current state into a new checkpoint at the start of a recorded step.
 lsb_status rec_checkpoint(lsb_grid *g) {
-  const size_t bytes = sizeof(float) * state_floats(g);
+  const size_t bytes = sizeof(float) * slot_floats(g);
   float *p = nullptr;
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) return fail(g, LSB_ENOMEM, "checkpoint cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
   g->rec_ckpt.push_back(p);
-  CU(cudaMemcpyAsync(p, g->d_buf[g->par[0]], bytes, cudaMemcpyDeviceToDevice, g->stream));
+  const size_t sf = state_floats(g);
+  CU(cudaMemcpyAsync(p, g->d_buf[g->par[0]], sizeof(float) * sf, cudaMemcpyDeviceToDevice, g->stream));
+  if (g->rec_moving) {
+    CU(cudaMemcpyAsync(p + sf, g->d_phi, sizeof(float) * g->nfine, cudaMemcpyDeviceToDevice, g->stream));
+    CU(cudaMemcpyAsync(p + sf + g->nfine, g->d_ut[0], sizeof(float) * g->D * g->nfine, cudaMemcpyDeviceToDevice,
+                       g->stream));
+  }
   return LSB_OK;
+}
+
+// Scratch of the moving level-set adjoint, carved from one allocation (finest-level
+// arrays of nfine floats; "vector" arrays hold D planes).
+struct LsaPtrs {
+  float *S;                       // S_0 .. S_n_ext: u~ after the interface pass and each sweep
+  float *U1;                      // committed u~ of the step
+  float *PHI0, *PS, *A1, *A2, *R1, *R2, *SS, *KP;
+  float *NV;                      // normals of phi_n (D planes)
+  float *L0r, *L1, *L2, *LS0;     // RK3 adjoints and d/dS0
+  float *LA, *LK[2], *LOFF, *LV;  // adjoints of the extension (D planes each)
+  float *LP[2];                   // adjoint of phi (ping-pong)
+  float *LU[2];                   // adjoint of u~ (ping-pong, D planes)
+  uint8_t *FR;                    // frozen cells of the reinitialisation
+};
+
+size_t lsa_floats_needed(const lsb_grid *g) {
+  const size_t NF = g->nfine, D = g->D;
+  return NF * (D * (g->n_ext + 1) + D + 8 + D + 4 + 5 * D + 2 + 2 * D) + NF / 4 + 64;
+}
+
+LsaPtrs lsa_ptrs(const lsb_grid *g) {
+  const size_t NF = g->nfine, D = g->D;
+  float *p = g->d_lsa;
+  auto take = [&](size_t planes) {
+    float *r = p;
+    p += planes * NF;
+    return r;
+  };
+  LsaPtrs P;
+  P.S = take(D * (g->n_ext + 1));
+  P.U1 = take(D);
+  P.PHI0 = take(1); P.PS = take(1); P.A1 = take(1); P.A2 = take(1);
+  P.R1 = take(1); P.R2 = take(1); P.SS = take(1); P.KP = take(1);
+  P.NV = take(D);
+  P.L0r = take(1); P.L1 = take(1); P.L2 = take(1); P.LS0 = take(1);
+  P.LA = take(D); P.LK[0] = take(D); P.LK[1] = take(D); P.LOFF = take(D); P.LV = take(D);
+  P.LP[0] = take(1); P.LP[1] = take(1);
+  P.LU[0] = take(D); P.LU[1] = take(D);
+  P.FR = reinterpret_cast<uint8_t *>(p);
+  return P;
 }
 
 // Working buffers of the reverse sweep, allocated on first use.
@@ -749,21 +809,43 @@ lsb_status adj_buffers(lsb_grid *g, int seg_len) {
     TRY(dalloc(g, &g->d_gk, sizeof(float) * (size_t)g->nfine));
     CU(cudaMemsetAsync(g->d_madj, 0, sizeof(float) * (size_t)MF * g->nfine, g->stream));
   }
-  if (seg_len > g->seg_cap) {
+  const size_t slb = sizeof(float) * slot_floats(g);
+  if (seg_len > g->seg_cap || g->seg_slot != slb) {
     if (g->d_seg) cudaFree(g->d_seg);
     g->d_seg = nullptr;
     g->seg_cap = 0;
-    cudaError_t e = cudaMalloc(&g->d_seg, sb * (size_t)seg_len);
-    if (e != cudaSuccess) return fail(g, LSB_ENOMEM, "segment store cudaMalloc(%zu): %s", sb * seg_len,
+    cudaError_t e = cudaMalloc(&g->d_seg, slb * (size_t)seg_len);
+    if (e != cudaSuccess) return fail(g, LSB_ENOMEM, "segment store cudaMalloc(%zu): %s", slb * seg_len,
                                       cudaGetErrorString(e));
     g->seg_cap = seg_len;
+    g->seg_slot = slb;
+  }
+  if (g->rec_moving) {
+    const size_t need = lsa_floats_needed(g);
+    if (g->lsa_floats < need) {
+      if (g->d_lsa) cudaFree(g->d_lsa);
+      g->d_lsa = nullptr;
+      g->lsa_floats = 0;
+      cudaError_t e = cudaMalloc(&g->d_lsa, sizeof(float) * need);
+      if (e != cudaSuccess) return fail(g, LSB_ENOMEM, "level-set adjoint scratch cudaMalloc: %s", cudaGetErrorString(e));
+      g->lsa_floats = need;
+    }
+    CU(cudaMemsetAsync(g->d_lsa, 0, sizeof(float) * g->lsa_floats, g->stream));
+    if (!g->d_phisave) {
+      TRY(dalloc(g, &g->d_phisave, sizeof(float) * g->nfine));
+      TRY(dalloc(g, &g->d_utsave, sizeof(float) * g->D * g->nfine));
+    }
   }
   return LSB_OK;
 }
 
 // One reverse step: lambda_n from lambda_{n+1} = d_adj[cur] at the state F = f_n.
-lsb_status adj_step(lsb_grid *g, const float *F, int cur, GeoAdj G) {
+lsb_status adj_step(lsb_grid *g, const float *F, int cur, GeoAdj G, float *phi = nullptr, float *nvec = nullptr,
+                    float *kappa = nullptr) {
   Ctx C = make_ctx(g);
+  if (phi) C.phi = phi;  // geometry of phi_n when the level set moves
+  if (nvec) C.nvec = nvec;
+  if (kappa) C.kappa = kappa;
   BlockShape S = shape(g);
   const int Q = g->Q;
   RUN(KADJ_LINKS, 0, 1, 128, run_adj_links, Q, LN(g, DYN_GRID, 128), C, 0, F, g->d_adj[cur], g->d_linkadj,
@@ -774,6 +856,113 @@ lsb_status adj_step(lsb_grid *g, const float *F, int cur, GeoAdj G) {
       g->d_linkadj, g->d_grad);
   RUN(KADJ_MACRO, 0, 1, 128, run_adj_macro, Q, LN(g, DYN_GRID, 128), C, 0, F, g->d_adj[1 - cur], g->d_madj,
       g->d_grad, g->ncase);
+  return LSB_OK;
+}
+
+// One reverse step with a moving level set: replay the level-set passes of step n
+// from (f_n, phi_n, u~_n), then the transposes in reverse order (reinitialisation,
+// transport, extension, interface velocity), then the lattice Boltzmann part with
+// the geometry of phi_n.  Adjoints in: d_adj[cur], LP[cur], LU[cur]; out: the others.
+lsb_status adj_step_moving(lsb_grid *g, const float *F, float *phi_n, const float *ut_n, int cur) {
+  const LsaPtrs P = lsa_ptrs(g);
+  const int Q = g->Q, D = g->D, nt = g->nthreads;
+  const long long NF = g->nfine;
+  const size_t b1 = sizeof(float) * NF, bD = sizeof(float) * D * NF;
+  const Ctx base = make_ctx(g);
+  const BlockShape S = shape(g);
+  const int nb = std::max(1, std::min(g->band_cap, 152 * 16));
+  auto Sk = [&](int k) { return P.S + (size_t)k * D * NF; };
+  // ---- replay of the level-set passes of step n
+  CU(cudaMemcpyAsync(Sk(0), ut_n, bD, cudaMemcpyDeviceToDevice, g->stream));
+  Ctx R = base;
+  R.phi = phi_n;
+  RUN(KLSA, 0, 1, 128, run_lsa_init, Q, LN(g, DYN_GRID, 128), R, 0, F, Sk(0));
+  Ctx E = base;
+  E.phi = phi_n;
+  E.ut0 = Sk(0);
+  for (int k = 0; k < g->n_ext; ++k) RUN(KLSA, 0, nb, nt, run_ext_iter, D, LN(g, nb, nt), E, S, 0, Sk(k), Sk(k + 1), 0);
+  CU(cudaMemcpyAsync(P.U1, Sk(0), bD, cudaMemcpyDeviceToDevice, g->stream));
+  if (g->n_ext > 0) {
+    Ctx Cm = base;
+    Cm.ut0 = P.U1;
+    RUN(KLSA, 0, nb, nt, run_ext_iter, D, LN(g, nb, nt), Cm, S, 0, Sk(g->n_ext), (float *)nullptr, 1);
+  }
+  CU(cudaMemcpyAsync(P.PHI0, phi_n, b1, cudaMemcpyDeviceToDevice, g->stream));
+  Ctx A = base;
+  A.phi = P.PHI0;
+  A.p1 = P.A1;
+  A.p2 = P.A2;
+  A.ut0 = P.U1;
+  for (int st = 1; st <= 3; ++st) RUN(KLSA, 0, nb, nt, run_adv_stage, D, LN(g, nb, nt), A, S, 0, st);
+  const bool rein = g->reinit_every == 1 && g->n_reinit > 0;
+  Ctx Rt = base;
+  Rt.phi = P.PS;
+  Rt.p1 = P.R1;
+  Rt.p2 = P.R2;
+  Rt.frozen = P.FR;
+  Rt.s0 = P.SS;
+  if (rein) {
+    CU(cudaMemcpyAsync(P.PS, P.PHI0, b1, cudaMemcpyDeviceToDevice, g->stream));
+    RUN(KLSA, 0, nb, nt, run_reinit_prep, Q, LN(g, nb, nt), Rt, S, 0);
+    Ctx Rs = Rt;
+    Rs.phi = P.PHI0;
+    for (int st = 1; st <= 3; ++st) RUN(KLSA, 0, nb, nt, run_reinit_stage, D, LN(g, nb, nt), Rs, S, 0, st);
+  }
+  Ctx Gm = base;
+  Gm.phi = phi_n;
+  Gm.nvec = P.NV;
+  Gm.kappa = P.KP;
+  RUN(11, 0, 1, 128, run_geometry, D, LN(g, DYN_GRID, 128), Gm, 0, 0);
+  // ---- transposes
+  float *LPin = P.LP[cur], *LPout = P.LP[1 - cur], *LUin = P.LU[cur], *LUout = P.LU[1 - cur];
+  const float *lps = LPin;
+  if (rein) {
+    CU(cudaMemcpyAsync(P.L0r, LPin, b1, cudaMemcpyDeviceToDevice, g->stream));
+    CU(cudaMemsetAsync(P.LS0, 0, b1, g->stream));
+    RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), Rt, S, 0, 0, 1, LPin, P.L0r, P.L1, P.L2, P.LS0);
+    RUN(KLSA, 0, nb, nt, run_lsa_reinit_rt, D, LN(g, nb, nt), Rt, S, 0, P.R2, LPin, 2.0f / 3.0f, P.L2, P.L0r, P.LS0);
+    RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), Rt, S, 0, 1, 1, LPin, P.L0r, P.L1, P.L2, P.LS0);
+    RUN(KLSA, 0, nb, nt, run_lsa_reinit_rt, D, LN(g, nb, nt), Rt, S, 0, P.R1, P.L2, 0.25f, P.L1, P.L0r, P.LS0);
+    RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), Rt, S, 0, 2, 1, LPin, P.L0r, P.L1, P.L2, P.LS0);
+    RUN(KLSA, 0, nb, nt, run_lsa_reinit_rt, D, LN(g, nb, nt), Rt, S, 0, P.PS, P.L1, 1.0f, P.L0r, P.L0r, P.LS0);
+    RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), Rt, S, 0, 3, 1, LPin, P.L0r, P.L1, P.L2, P.LS0);
+    lps = P.L0r;
+  }
+  Ctx At = base;
+  At.phi = phi_n;
+  At.p1 = P.A1;
+  At.p2 = P.A2;
+  At.ut0 = P.U1;
+  CU(cudaMemcpyAsync(LPout, lps, b1, cudaMemcpyDeviceToDevice, g->stream));
+  CU(cudaMemcpyAsync(P.LA, LUin, bD, cudaMemcpyDeviceToDevice, g->stream));
+  RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), At, S, 0, 0, 0, lps, LPout, P.L1, P.L2, P.LS0);
+  RUN(KLSA, 0, nb, nt, run_lsa_adv_rt, D, LN(g, nb, nt), At, S, 0, P.A2, lps, 2.0f / 3.0f, P.L2, LPout, P.LA);
+  RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), At, S, 0, 1, 0, lps, LPout, P.L1, P.L2, P.LS0);
+  RUN(KLSA, 0, nb, nt, run_lsa_adv_rt, D, LN(g, nb, nt), At, S, 0, P.A1, P.L2, 0.25f, P.L1, LPout, P.LA);
+  RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), At, S, 0, 2, 0, lps, LPout, P.L1, P.L2, P.LS0);
+  RUN(KLSA, 0, nb, nt, run_lsa_adv_rt, D, LN(g, nb, nt), At, S, 0, (const float *)phi_n, P.L1, 1.0f, LPout, LPout,
+      P.LA);
+  float *Lc = P.LA;
+  if (g->n_ext > 0) {
+    CU(cudaMemsetAsync(P.LOFF, 0, bD, g->stream));
+    for (int k = g->n_ext - 1; k >= 0; --k) {
+      float *out = Lc == P.LK[0] ? P.LK[1] : P.LK[0];
+      CU(cudaMemcpyAsync(out, Lc, bD, cudaMemcpyDeviceToDevice, g->stream));
+      RUN(KLSA, 0, nb, nt, run_lsa_ext_T, D, LN(g, nb, nt), E, S, 0, (const float *)Sk(k), (const float *)Sk(0),
+          (const float *)Lc, out, P.LOFF, P.LV);
+      Lc = out;
+    }
+    RUN(KLSA, 0, nb, nt, run_lsa_ext_v, D, LN(g, nb, nt), E, S, 0, P.LV, LPout);
+    RUN(KLSA, 0, 1, 256, run_lsa_axpy, LN(g, 152 * 8, 256), (long long)D * NF, (const float *)P.LOFF, Lc);
+  }
+  RUN(KLSA, 0, 1, 128, run_lsa_init_T, Q, LN(g, DYN_GRID, 128), R, 0, F, Lc, g->d_madj, LPout);
+  CU(cudaMemcpyAsync(LUout, Lc, bD, cudaMemcpyDeviceToDevice, g->stream));
+  // lattice Boltzmann part with the geometry of phi_n; its phi adjoint goes to LPout
+  const GeoAdj G{LPout, g->d_gn, g->d_gk};
+  TRY(adj_step(g, F, cur, G, phi_n, P.NV, P.KP));
+  RUN(KADJ_GEOM, 0, 1, 128, run_adj_geometry, D, LN(g, DYN_GRID, 128), R, 0, G);
+  CU(cudaMemsetAsync(g->d_gn, 0, bD, g->stream));
+  CU(cudaMemsetAsync(g->d_gk, 0, b1, g->stream));
   return LSB_OK;
 }
 
@@ -1009,6 +1198,7 @@ lsb_status lsb_step(lsb_grid *g, int n) {
       if (g->rec_steps % g->rec_every == 0 && (size_t)(g->rec_steps / g->rec_every) == g->rec_ckpt.size())
         TRY(rec_checkpoint(g));
       TRY(advance(g, 0));
+      if (g->rec_moving) TRY(launched(g, run_lsa_flipflag(LN(g, 1, 32), g->d_counters, 0, g->d_recflip)));
       g->updates_done += updates_per_step(g);
       g->coarse_steps++;
       g->rec_steps++;
@@ -1089,6 +1279,7 @@ size_t lsb_field_bytes(const lsb_grid *g, int case_idx, int field, int level) {
     case LSB_FIELD_U: case LSB_FIELD_UEXT: return 4 * n * g->D;
     case LSB_FIELD_PHASE: case LSB_FIELD_TAG: return n;
     case LSB_FIELD_F: case LSB_FIELD_ADJ_F: return 4 * n * g->Q;
+    case LSB_FIELD_ADJ_UEXT: return L.finest ? 4 * n * g->D : 0;
     case LSB_FIELD_BLOCKS: return (size_t)L.nblock;
     case LSB_FIELD_CUTMASK: return 4 * n;
     default: return 0;
@@ -1137,6 +1328,13 @@ lsb_status lsb_get_fields(lsb_grid *g, int case_idx, int field, int level, void 
     case LSB_FIELD_KAPPA: src = g->d_kappa + L.fine_off; break;
     case LSB_FIELD_CUTMASK: src = g->d_cmask + L.fine_off; break;
     case LSB_FIELD_UEXT: src = g->d_ut[0] + L.fine_off; planes = g->D; plane_stride = g->nfine; break;
+    case LSB_FIELD_ADJ_UEXT:
+      if (g->adj_cur < 0 || !g->rec_moving)
+        return fail(g, LSB_ESTATE, "no u~ adjoint: lsb_backward over a moving level set first");
+      src = lsa_ptrs(g).LU[g->adj_cur] + L.fine_off;
+      planes = g->D;
+      plane_stride = g->nfine;
+      break;
     case LSB_FIELD_ADJ_F:
       if (g->adj_cur < 0) return fail(g, LSB_ESTATE, "no adjoint field: call lsb_backward first");
       src = g->d_adj[g->adj_cur] + L.cell_off * g->Q;
@@ -1298,11 +1496,18 @@ lsb_status lsb_record(lsb_grid *g, int checkpoint_every) {
   if (!g || checkpoint_every < 1) return LSB_EINVAL;
   if (g->Lmax != 1) return fail(g, LSB_ESTATE, "the adjoint covers single-level grids");
   if (g->storage != LSB_FP32) return fail(g, LSB_ESTATE, "the adjoint needs FP32 population storage");
-  for (const CaseHost &c : g->cases)
-    if (c.p.ls_active) return fail(g, LSB_ESTATE, "the adjoint needs a frozen level set (ls_active = 0)");
+  int live = 0;
+  for (const CaseHost &c : g->cases) live += c.p.ls_active ? 1 : 0;
+  if (live != 0 && live != g->ncase)
+    return fail(g, LSB_ESTATE, "the adjoint needs the level set live in every case or frozen in every case");
+  if (live && (g->reinit_every > 1 || g->n_reinit > 1))
+    return fail(g, LSB_ESTATE, "the moving-interface adjoint needs reinit_every <= 1 and n_reinit <= 1");
   CU(cudaStreamSynchronize(g->stream));
   rec_clear(g);
+  if (!g->d_recflip) TRY(dalloc(g, &g->d_recflip, sizeof(int)));
+  CU(cudaMemset(g->d_recflip, 0, sizeof(int)));
   g->rec_on = 1;
+  g->rec_moving = live ? 1 : 0;
   g->rec_every = checkpoint_every;
   return LSB_OK;
 }
@@ -1313,8 +1518,16 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
   const int Q = g->Q, D = g->D, stride = 4 + 2 * D;
   const long long T = g->rec_steps;
   const int every = g->rec_every;
+  const bool mv = g->rec_moving != 0;
+  if (mv) {
+    int flip = 0;
+    CU(cudaStreamSynchronize(g->stream));
+    CU(cudaMemcpy(&flip, g->d_recflip, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flip) return fail(g, LSB_ESTATE, "a cell changed phase during the recorded window");
+  }
   TRY(adj_buffers(g, (int)std::min<long long>(every, std::max<long long>(T, 1))));
-  const size_t sf = state_floats(g), sb = sizeof(float) * sf;
+  const size_t sf = state_floats(g), sb = sizeof(float) * sf, sl = slot_floats(g);
+  const size_t NF = g->nfine;
   const int MF = 1 + D + D * (D + 1) / 2;
   CU(cudaMemsetAsync(g->d_adj[0], 0, sb, g->stream));
   CU(cudaMemsetAsync(g->d_adj[1], 0, sb, g->stream));
@@ -1334,6 +1547,12 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
   const long long fs0 = g->fine_steps[0], cs0 = g->coarse_steps;
   const double ud0 = g->updates_done;
   CU(cudaMemcpyAsync(g->d_fsave, g->d_buf[par0], sb, cudaMemcpyDeviceToDevice, g->stream));
+  if (mv) {
+    CU(cudaMemsetAsync(g->d_gn, 0, sizeof(float) * D * NF, g->stream));
+    CU(cudaMemsetAsync(g->d_gk, 0, sizeof(float) * NF, g->stream));
+    CU(cudaMemcpyAsync(g->d_phisave, g->d_phi, sizeof(float) * NF, cudaMemcpyDeviceToDevice, g->stream));
+    CU(cudaMemcpyAsync(g->d_utsave, g->d_ut[0], sizeof(float) * D * NF, cudaMemcpyDeviceToDevice, g->stream));
+  }
   Ctx C = make_ctx(g);
   BlockShape S = shape(g);
   CU(cudaMemsetAsync(g->d_obs, 0, sizeof(double) * stride * g->ncase, g->stream));
@@ -1350,19 +1569,35 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
     const int len = (int)std::min<long long>(every, T - start);
     // recompute the segment from its checkpoint: step j reads slot j and pushes into
     // slot j + 1 (the last step's result is not needed and goes to a grid buffer)
-    cudaError_t e = cudaMemcpyAsync(g->d_seg, g->rec_ckpt[sgi], sb, cudaMemcpyDeviceToDevice, g->stream);
+    float *ck = g->rec_ckpt[sgi];
+    cudaError_t e = cudaMemcpyAsync(g->d_seg, ck, sb, cudaMemcpyDeviceToDevice, g->stream);
+    if (e == cudaSuccess && mv) {
+      e = cudaMemcpyAsync(g->d_phi, ck + sf, sizeof(float) * NF, cudaMemcpyDeviceToDevice, g->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->d_ut[0], ck + sf + NF, sizeof(float) * D * NF, cudaMemcpyDeviceToDevice, g->stream);
+    }
     if (e != cudaSuccess) { st = fail(g, LSB_ECUDA, "checkpoint restore: %s", cudaGetErrorString(e)); break; }
+    // the interface geometry (n, kappa) the first step uses is that of the restored phi
+    if (mv && (st = classify(g, 0, 0)) != LSB_OK) break;
     g->no_tma = 1;  // the TMA tensor maps describe the grid buffers, not the slots
     for (int j = 0; j < len && st == LSB_OK; ++j) {
-      g->d_buf[g->par[0]] = g->d_seg + sf * j;
-      g->d_buf[1 - g->par[0]] = j + 1 < len ? (void *)(g->d_seg + sf * (j + 1)) : bufs[0];
+      float *slot = g->d_seg + sl * j;
+      if (mv) {
+        e = cudaMemcpyAsync(slot + sf, g->d_phi, sizeof(float) * NF, cudaMemcpyDeviceToDevice, g->stream);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(slot + sf + NF, g->d_ut[0], sizeof(float) * D * NF, cudaMemcpyDeviceToDevice, g->stream);
+        if (e != cudaSuccess) { st = fail(g, LSB_ECUDA, "segment store: %s", cudaGetErrorString(e)); break; }
+      }
+      g->d_buf[g->par[0]] = slot;
+      g->d_buf[1 - g->par[0]] = j + 1 < len ? (void *)(g->d_seg + sl * (j + 1)) : bufs[0];
       st = advance(g, 0);
     }
     g->no_tma = 0;
     g->d_buf[0] = bufs[0];
     g->d_buf[1] = bufs[1];
     for (int j = len - 1; j >= 0 && st == LSB_OK; --j) {
-      st = adj_step(g, g->d_seg + sf * j, cur, G);
+      float *slot = g->d_seg + sl * j;
+      st = mv ? adj_step_moving(g, slot, slot + sf, slot + sf + NF, cur) : adj_step(g, slot, cur, G);
       cur ^= 1;
     }
   }
@@ -1371,17 +1606,27 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
   g->coarse_steps = cs0;
   g->updates_done = ud0;
   CU(cudaMemcpyAsync(g->d_buf[par0], g->d_fsave, sb, cudaMemcpyDeviceToDevice, g->stream));
+  if (mv) {
+    CU(cudaMemcpyAsync(g->d_phi, g->d_phisave, sizeof(float) * NF, cudaMemcpyDeviceToDevice, g->stream));
+    CU(cudaMemcpyAsync(g->d_ut[0], g->d_utsave, sizeof(float) * D * NF, cudaMemcpyDeviceToDevice, g->stream));
+    if (st == LSB_OK) st = classify(g, 0, 0);  // geometry and lists of the restored phi
+  }
   if (st != LSB_OK) return st;
   if (dJ_dphi0) {
-    // normal and curvature adjoints through the least-squares fit, then the dense boxes
-    Ctx C2 = make_ctx(g);
-    RUN(KADJ_GEOM, 0, 1, 128, run_adj_geometry, D, LN(g, DYN_GRID, 128), C2, 0, G);
+    const float *src = g->d_gphi;
+    if (mv) {
+      src = lsa_ptrs(g).LP[cur];  // the adjoint of phi_0 through every pass
+    } else {
+      // normal and curvature adjoints through the least-squares fit, then the dense boxes
+      Ctx C2 = make_ctx(g);
+      RUN(KADJ_GEOM, 0, 1, 128, run_adj_geometry, D, LN(g, DYN_GRID, 128), C2, 0, G);
+    }
     size_t off = 0;
     for (int c = 0; c < g->ncase; ++c) {
       const LevelDev &L = g->lds[g->cases[c].ld0 + g->cases[c].L - 1];
       cudaMemcpy3DParms pr;
       memset(&pr, 0, sizeof pr);
-      pr.srcPtr = make_cudaPitchedPtr((void *)(g->d_gphi + L.fine_off), 4 * (size_t)L.p[0], L.p[0], L.p[1]);
+      pr.srcPtr = make_cudaPitchedPtr((void *)(src + L.fine_off), 4 * (size_t)L.p[0], L.p[0], L.p[1]);
       pr.dstPtr = make_cudaPitchedPtr((void *)(dJ_dphi0 + off), 4 * (size_t)L.n[0], L.n[0], L.n[1]);
       pr.extent = make_cudaExtent(4 * (size_t)L.n[0], L.n[1], L.n[2]);
       pr.kind = cudaMemcpyDeviceToDevice;
@@ -1442,6 +1687,9 @@ void lsb_destroy(lsb_grid *g) {
   else cudaDeviceSynchronize();
   drop_graphs(g);
   for (void *p : g->allocs) cudaFree(p);
+  if (g->d_lsa) cudaFree(g->d_lsa);
+  if (g->d_seg) cudaFree(g->d_seg);
+  for (float *p : g->rec_ckpt) cudaFree(p);
   for (ProfRec &r : g->prof) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);

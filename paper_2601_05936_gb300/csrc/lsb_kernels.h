@@ -72,4 +72,19 @@ cudaError_t run_adj_collide(int Q, Launch L, Ctx C, BlockShape S, const int *lis
 cudaError_t run_adj_macro(int Q, Launch L, Ctx C, int glevel, const float *F, float *lamO, float *MA, double *grad,
                           int ncase);
 
+// lsb_adj_ls.cu: adjoint of the level-set passes of a step with a moving interface
+cudaError_t run_lsa_init(int Q, Launch L, Ctx C, int glevel, const float *F, float *U0);
+cudaError_t run_lsa_init_T(int Q, Launch L, Ctx C, int glevel, const float *F, float *LS0, float *MA, float *LPHI);
+cudaError_t run_lsa_mix(int D, Launch L, Ctx C, BlockShape S, int glevel, int mode, int use_frozen, const float *L3,
+                        float *L0, float *L1, float *L2, const float *Ls0);
+cudaError_t run_lsa_reinit_rt(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *pin, const float *MU,
+                              float scale, float *Lt, float *L0, float *Ls0);
+cudaError_t run_lsa_adv_rt(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *pin, const float *MU,
+                           float scale, float *Lt, float *L0, float *LU);
+cudaError_t run_lsa_ext_T(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *Sk, const float *S0,
+                          const float *Lin, float *Lout, float *LOFF, float *LV);
+cudaError_t run_lsa_ext_v(int D, Launch L, Ctx C, BlockShape S, int glevel, float *LV, float *LPHI);
+cudaError_t run_lsa_axpy(Launch L, long long n, const float *x, float *y);
+cudaError_t run_lsa_flipflag(Launch L, const int *counters, int glevel, int *flag);
+
 }  // namespace lsb

@@ -251,6 +251,7 @@ __device__ __forceinline__ void d_ext_init(const Ctx &C, int glevel) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     const int2 it = lst[e];
     const LevelDev &L = C.lds[it.x];
+    if (!L.ls_active) continue;  // frozen level set in this case
     const long long c = it.y;
     const int x = (int)(c % L.p[0]);
     const int y = (int)((c / L.p[0]) % L.p[1]);
@@ -288,6 +289,7 @@ __device__ __forceinline__ void d_ext_iter(const Ctx &C, BlockShape S, int gleve
     const int gb = lst[w];
     int x, y, z;
     const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
+    if (!L.ls_active) continue;  // frozen level set in this case
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long fo = L.fine_off, NF = C.nfine;
     const long long c = cidx(L, x, y, z);
@@ -429,6 +431,7 @@ __device__ __forceinline__ void d_adv_stage(const Ctx &C, BlockShape S, int glev
     const int gb = lst[w];
     int x, y, z;
     const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
+    if (!L.ls_active) continue;  // frozen level set in this case
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long fc = L.fine_off + cidx(L, x, y, z);
     float rhs = 0.f;
@@ -459,6 +462,7 @@ __device__ __forceinline__ void d_reinit_prep(const Ctx &C, BlockShape S, int gl
     const int gb = lst[w];
     int x, y, z;
     const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
+    if (!L.ls_active) continue;  // frozen level set in this case
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long fc = L.fine_off + cidx(L, x, y, z);
     const float p = C.phi[fc];
@@ -504,6 +508,7 @@ __device__ __forceinline__ void d_reinit_stage(const Ctx &C, BlockShape S, int g
     const int gb = lst[w];
     int x, y, z;
     const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
+    if (!L.ls_active) continue;  // frozen level set in this case
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const unsigned cl = (unsigned)cidx(L, x, y, z);
     const long long fc = L.fine_off + cl;

@@ -18,7 +18,7 @@ D2Q9, D3Q19 = 0, 1
 PERIODIC, WALL = 0, 1
 FP32, FP16S = 0, 1
 SENSOR_BAND, SENSOR_SIGNED = 0, 1
-FIELD = dict(rho=0, u=1, phi=2, phase=3, f=4, tag=5, blocks=6, cutmask=7, kappa=8, uext=9, adj_f=10)
+FIELD = dict(rho=0, u=1, phi=2, phase=3, f=4, tag=5, blocks=6, cutmask=7, kappa=8, uext=9, adj_f=10, adj_uext=11)
 NPARAM_ADJ = 5  # sigma, rho[0], rho[1], nu[0], nu[1]
 STATUS = {0: "LSB_OK", 1: "LSB_EINVAL", 2: "LSB_ENOMEM", 3: "LSB_ECUDA", 4: "LSB_EUNSTABLE",
           5: "LSB_ETIMEOUT", 6: "LSB_ESTATE"}

@@ -148,7 +148,7 @@ def test_adjoint_state_errors():
         g.backward(a)
     g.close()
     live = dict(case, ls_active=True)
-    h = lsb.Grid(live)
+    h = lsb.Grid([case, live])  # live and frozen level sets in one recording
     with pytest.raises(lsb.LsbError) as e:
         h.record(3)
     assert e.value.status == 6
