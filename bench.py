@@ -134,7 +134,7 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def adjoint_bench(args, world, rank, local, barrier, dist):
+def adjoint_bench(args, world, rank, local, barrier, dist, moving=False):
     """Reverse sweep of the frozen-interface adjoint: single-level 128x128x256 D3Q19
     box with the bubble of the benchmark workload (d = 32 cells, density ratio
     1000), level set frozen.  A step of the metric is one adjoint step of the
@@ -143,7 +143,10 @@ def adjoint_bench(args, world, rank, local, barrier, dist):
     import torch
     from paper_2601_05936_gb300 import autograd, lsb, workloads
     case = workloads.rising_bubble_3d(levels=1)
-    case.update(ls_active=False, n_ext=0, reinit_every=0, regrid_every=0)
+    if moving:  # level set live: the sweep also replays and transposes the level-set passes
+        case.update(regrid_every=0)
+    else:
+        case.update(ls_active=False, n_ext=0, reinit_every=0, regrid_every=0)
     stream = torch.cuda.Stream()
     g = lsb.Grid(case, stream=stream, device=local)
     g.step(args.warmup)
@@ -203,11 +206,13 @@ def adjoint_bench(args, world, rank, local, barrier, dist):
     g.close()
     if rank != 0:
         return
-    line = dict(metric="MLUPS of the reverse sweep (adjoint cell steps / s), 3D D3Q19 frozen bubble 128x128x256",
+    line = dict(metric="MLUPS of the reverse sweep (adjoint cell steps / s), 3D D3Q19 "
+                       + ("moving" if moving else "frozen") + " bubble 128x128x256",
                 value=value, unit="MLUPS", n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f32", data="synthetic",
-                config=dict(workload=case["name"] + "_frozen", lattice="D3Q19", levels=1, storage="fp32",
+                config=dict(workload=case["name"] + ("_moving" if moving else "_frozen"), lattice="D3Q19", levels=1,
+                            storage="fp32",
                             parallelism=f"replicas{world}", checkpoint_every=args.checkpoint_every,
                             cells=cells, l2_flush="state 318 MB x (segment store) >> 129 MB L2",
                             dJ_dparams=[float(v) for v in dp[0]]),
@@ -225,10 +230,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-all", action="store_true", help="print a per-kernel time table to stderr")
-    ap.add_argument("--workload", default="bubble3d", choices=["bubble3d", "box3d", "ensemble", "adjoint3d"],
+    ap.add_argument("--workload", default="bubble3d", choices=["bubble3d", "box3d", "ensemble", "adjoint3d", "adjoint3d_ls"],
                     help="bubble3d: the benchmark configuration; box3d: uniform periodic 128^3 box "
                          "(collide-and-stream only, for profiling captures); ensemble: 64 uneven 2D bubbles; "
-                         "adjoint3d: reverse sweep over --steps recorded steps of a frozen 3D bubble")
+                         "adjoint3d: reverse sweep over --steps recorded steps of a frozen 3D bubble; "
+                         "adjoint3d_ls: the same with the level set moving (short windows: no phase change)")
     ap.add_argument("--checkpoint-every", type=int, default=100)
     ap.add_argument("--driver", type=int, default=0, choices=[0, 1],
                     help="level-set passes: 0 one launch each, 1 one persistent cooperative launch per finest step")
@@ -258,8 +264,8 @@ def main():
     __graft_entry__.build()
     from paper_2601_05936_gb300 import lsb, workloads
 
-    if args.workload == "adjoint3d":
-        adjoint_bench(args, world, rank, local, barrier, dist)
+    if args.workload in ("adjoint3d", "adjoint3d_ls"):
+        adjoint_bench(args, world, rank, local, barrier, dist, moving=args.workload == "adjoint3d_ls")
         return
     if args.workload == "bubble3d":
         case = workloads.rising_bubble_3d(storage=args.storage, scale=args.scale)
