@@ -85,6 +85,9 @@ struct lsb_grid {
   uint32_t *d_cmask = nullptr;
   int *d_cbase = nullptr;
   float *d_macro = nullptr, *d_nvec = nullptr, *d_kappa = nullptr, *d_linkbuf = nullptr;
+  int2 *d_linkcell = nullptr;
+  uint8_t *d_linkdir = nullptr;
+  long long link_list_off[MAXL] = {0, 0, 0, 0};
   int *d_counters = nullptr, *d_err = nullptr, *d_band = nullptr;
   unsigned *d_bar = nullptr;  // grid barrier of the persistent level-set kernel
   int driver = 0;             // 0: one launch per level-set pass, 1: one persistent launch
@@ -215,6 +218,9 @@ Ctx make_ctx(lsb_grid *g) {
   C.linkbuf = g->d_linkbuf;
   C.nfine = g->nfine;
   C.link_cap = g->link_cap;
+  C.link_cell = g->d_linkcell;
+  C.link_dir = g->d_linkdir;
+  for (int l = 0; l < MAXL; ++l) C.link_list_off[l] = g->link_list_off[l];
   C.counters = g->d_counters;
   C.iface_list = g->d_iface;
   C.flip_list = g->d_flip;
@@ -1104,6 +1110,19 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
   ALLOC(g->d_nvec, 4 * D * nf);
   ALLOC(g->d_kappa, 4 * nf);
   ALLOC(g->d_linkbuf, 8 * g->link_cap);
+  {
+    // the link list lives from one classification to the next step's bounce-back, so
+    // every finest global level keeps its own region (the link buffer is shared)
+    long long nl = 0;
+    for (int l = 0; l < MAXL; ++l) {
+      g->link_list_off[l] = nl * g->link_cap;
+      bool fin = false;
+      for (int c = 0; c < n_cases; ++c) fin = fin || (g->cases[c].L - 1 == l);
+      if (fin) ++nl;
+    }
+    ALLOC(g->d_linkcell, 8 * g->link_cap * nl);
+    ALLOC(g->d_linkdir, g->link_cap * nl);
+  }
   ALLOC(g->d_counters, sizeof(int) * MAXL * NCOUNT);
   ALLOC(g->d_err, sizeof(int));
   ALLOC(g->d_bar, 2 * sizeof(unsigned));

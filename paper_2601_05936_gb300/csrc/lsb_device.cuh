@@ -151,6 +151,9 @@ struct Ctx {
   float *macro;            // MF planes of nfine: drho, u[D], S (sym, D(D+1)/2)
   float *nvec, *kappa;     // geometry at interface cells (D planes + 1)
   float *linkbuf;          // 2 floats per cut link
+  int2 *link_cell;         // per cut link: (level descriptor, cell) of x
+  uint8_t *link_dir;       // per cut link: incoming direction k
+  long long link_list_off[4];  // start of each finest global level's region of the link list
   long long nfine;         // finest-level cells over all cases
   long long link_cap;
   int *counters;           // per global level: [0] links, [1] iface cells, [2] flipped, [3] band blocks

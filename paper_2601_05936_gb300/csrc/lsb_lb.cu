@@ -385,16 +385,17 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
 }
 
 // ------------------------------------------------------------------ interface post-pass
-// For every cut link (x, k) of an interface cell: Eq. bb with the momentum term of
-// Eq. bb_cc; i = opp(k) points from x (phase A) to x + c_i (phase B).
+// For every cut link (x, k): Eq. bb with the momentum term of Eq. bb_cc;
+// i = opp(k) points from x (phase A) to x + c_i (phase B).  One thread per link
+// (the link list of the classification, in link-buffer order).
 template <int Q, typename T>
 __global__ void k_interface_bc(Ctx C, int glevel) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
-  const int n = min(C.counters[glevel * NCOUNT + 1], (int)C.list_cap);
-  const int2 *lst = C.iface_list + (long long)glevel * C.list_cap;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    const int2 it = lst[e];
+  const long long n = min((long long)C.counters[glevel * NCOUNT + 0], C.link_cap);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int2 it = C.link_cell[C.link_list_off[glevel] + e];
+    const int k = C.link_dir[C.link_list_off[glevel] + e];
     const LevelDev &L = C.lds[it.x];
     const long long c = it.y;
     const int x = (int)(c % L.p[0]);
@@ -402,8 +403,6 @@ __global__ void k_interface_bc(Ctx C, int glevel) {
     const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
     const long long fo = L.fine_off;
     const long long NF = C.nfine;
-    const uint32_t cm = C.cmask[fo + c];
-    const int cb = C.cbase[fo + c];
     const uint8_t tg = C.tag[L.cell_off + c];
     const int A = tg & TAG_GAS;
     const int Bp = 1 - A;
@@ -424,11 +423,9 @@ __global__ void k_interface_bc(Ctx C, int glevel) {
     const float eta_bar = 0.5f * (etaA + etaB);
     const float jeta = etaB - etaA;
     const float sgn = (A == 0) ? 1.0f : -1.0f;
-    for (int k = 0; k < Q; ++k) {
-      if (!(cm & (1u << k))) continue;
+    {
       const int i = LT::opp(k);
-      const long long li = cb + __popc(cm & ((1u << k) - 1u));
-      if (li >= C.link_cap) continue;
+      const long long li = e;
       const float fi = C.linkbuf[2 * li], fk = C.linkbuf[2 * li + 1];
       int yx = x + LT::cx(i), yy = y + LT::cy(i), yz = z + LT::cz(i);
       wrap(L, 0, yx); wrap(L, 1, yy); if (D == 3) wrap(L, 2, yz);

@@ -113,6 +113,17 @@ __global__ void k_classify_links(Ctx C, BlockShape S, const int *list, int nlist
           int base = atomicAdd(&C.counters[glevel * NCOUNT + 0], __popc(m));
           if ((long long)base + __popc(m) > C.link_cap) atomicOr(C.err, ERR_LINK_OVF);
           C.cbase[L.fine_off + c] = base;
+          // the link list: one entry per cut link, in link-buffer order
+          const int2 cell = make_int2(C.blk_ld[gb], (int)c);
+          uint32_t mm = m;
+          for (int r = 0; mm; ++r) {
+            const int k = __ffs(mm) - 1;
+            mm &= mm - 1u;
+            if ((long long)base + r < C.link_cap) {
+              C.link_cell[C.link_list_off[glevel] + base + r] = cell;
+              C.link_dir[C.link_list_off[glevel] + base + r] = (uint8_t)k;
+            }
+          }
           C.tag[L.cell_off + c] = tg | TAG_IFACE;
           int e = atomicAdd(&C.counters[glevel * NCOUNT + 1], 1);
           if (e < C.list_cap) C.iface_list[(long long)glevel * C.list_cap + e] = make_int2(C.blk_ld[gb], (int)c);
@@ -179,25 +190,38 @@ __global__ void k_geometry(Ctx C, int glevel, int which) {
     const int x = (int)(c % L.p[0]);
     const int y = (int)((c / L.p[0]) % L.p[1]);
     const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
-    double P = 0, sx[3] = {0, 0, 0}, sxx[3] = {0, 0, 0}, sxy[3] = {0, 0, 0};
+    // Stencil sums exactly: phi (float) in fixed point with 30 fraction bits (exact
+    // for |phi| >= 2^-6, within 2^-31 below), summed in 64-bit integers, then
+    // converted to float64 (exact below 2^53).  This keeps the float64 work of the
+    // fit to the closed-form solve; GB300 runs float64 at a small fraction of its
+    // integer rate.
+    long long iP = 0, isx[3] = {0, 0, 0}, isxx[3] = {0, 0, 0}, isxy[3] = {0, 0, 0};
     for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz)
       for (int oy = -1; oy <= 1; ++oy)
         for (int ox = -1; ox <= 1; ++ox) {
           const int xx = clampwrap(L, 0, x + ox), yy = clampwrap(L, 1, y + oy);
           const int zz = D == 3 ? clampwrap(L, 2, z + oz) : 0;
-          const double v = (double)C.phi[L.fine_off + cidx(L, xx, yy, zz)];
+          const long long v = __float2ll_rn(C.phi[L.fine_off + cidx(L, xx, yy, zz)] * 1073741824.0f);
           const int o[3] = {ox, oy, oz};
-          P += v;
+          iP += v;
           for (int a = 0; a < D; ++a) {
-            sx[a] += o[a] * v;
-            sxx[a] += o[a] * o[a] * v;
+            isx[a] += o[a] > 0 ? v : (o[a] < 0 ? -v : 0);
+            isxx[a] += o[a] != 0 ? v : 0;
           }
-          sxy[0] += ox * oy * v;
+          isxy[0] += ox * oy > 0 ? v : (ox * oy < 0 ? -v : 0);
           if (D == 3) {
-            sxy[1] += ox * oz * v;
-            sxy[2] += oy * oz * v;
+            isxy[1] += ox * oz > 0 ? v : (ox * oz < 0 ? -v : 0);
+            isxy[2] += oy * oz > 0 ? v : (oy * oz < 0 ? -v : 0);
           }
         }
+    const double sc = 1.0 / 1073741824.0;
+    const double P = (double)iP * sc;
+    double sx[3], sxx[3], sxy[3];
+    for (int a = 0; a < 3; ++a) {
+      sx[a] = (double)isx[a] * sc;
+      sxx[a] = (double)isxx[a] * sc;
+      sxy[a] = (double)isxy[a] * sc;
+    }
     double g[3] = {0, 0, 0}, H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     if (D == 2) {
       // sums over 9 points: sum o^2 = 6, sum o_x^2 o_y^2 = 4, sum o^4 = 6
