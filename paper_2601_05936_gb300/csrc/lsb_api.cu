@@ -82,6 +82,8 @@ struct lsb_grid {
   void *d_buf[2] = {nullptr, nullptr};
   float *d_phi = nullptr, *d_p1 = nullptr, *d_p2 = nullptr, *d_s0 = nullptr;
   float *d_ut[3] = {nullptr, nullptr, nullptr};
+  float *d_plan_v = nullptr;
+  uint8_t *d_plan_f = nullptr;
   uint32_t *d_cmask = nullptr;
   int *d_cbase = nullptr;
   float *d_macro = nullptr, *d_nvec = nullptr, *d_kappa = nullptr, *d_linkbuf = nullptr;
@@ -210,6 +212,8 @@ Ctx make_ctx(lsb_grid *g) {
   C.ut0 = g->d_ut[0];
   C.ut1 = g->d_ut[1];
   C.ut2 = g->d_ut[2];
+  C.plan_v = g->d_plan_v;
+  C.plan_f = g->d_plan_f;
   C.cmask = g->d_cmask;
   C.cbase = g->d_cbase;
   C.macro = g->d_macro;
@@ -482,7 +486,7 @@ lsb_status levelset(lsb_grid *g, int l) {
   const float *uin = g->d_ut[0];
   for (int it = 0; it < g->n_ext; ++it) {
     float *uout = g->d_ut[1 + (it & 1)];
-    RUN(13, 0, nb, nt, run_ext_iter, D, LN(g, nb, nt), C, S, l, uin, uout, 0);
+    RUN(13, 0, nb, nt, run_ext_iter, D, LN(g, nb, nt), C, S, l, uin, uout, it == 0 ? 2 : 3);  // plan, then reuse
     uin = uout;
   }
   if (g->n_ext > 0) {
@@ -886,7 +890,8 @@ lsb_status adj_step_moving(lsb_grid *g, const float *F, float *phi_n, const floa
   Ctx E = base;
   E.phi = phi_n;
   E.ut0 = Sk(0);
-  for (int k = 0; k < g->n_ext; ++k) RUN(KLSA, 0, nb, nt, run_ext_iter, D, LN(g, nb, nt), E, S, 0, Sk(k), Sk(k + 1), 0);
+  for (int k = 0; k < g->n_ext; ++k)
+    RUN(KLSA, 0, nb, nt, run_ext_iter, D, LN(g, nb, nt), E, S, 0, Sk(k), Sk(k + 1), k == 0 ? 2 : 3);
   CU(cudaMemcpyAsync(P.U1, Sk(0), bD, cudaMemcpyDeviceToDevice, g->stream));
   if (g->n_ext > 0) {
     Ctx Cm = base;
@@ -1104,6 +1109,8 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
   ALLOC(g->d_s0, 4 * nf);
   ALLOC(g->d_frozen, nf);
   for (int k = 0; k < 3; ++k) ALLOC(g->d_ut[k], 4 * D * nf);
+  ALLOC(g->d_plan_v, 4 * D * nf);
+  ALLOC(g->d_plan_f, nf);
   ALLOC(g->d_cmask, 4 * nf);
   ALLOC(g->d_cbase, 4 * nf);
   ALLOC(g->d_macro, 4 * (size_t)MF * nf);

@@ -146,6 +146,8 @@ struct Ctx {
   float *phi, *p1, *p2, *s0;
   uint8_t *frozen;
   float *ut0, *ut1, *ut2;  // extension velocity (D planes of nfine each)
+  float *plan_v;           // extension plan: upwind velocity (D planes of nfine)
+  uint8_t *plan_f;         // extension plan: side / band / interface / boundary bits
   uint32_t *cmask;
   int *cbase;
   float *macro;            // MF planes of nfine: drho, u[D], S (sym, D(D+1)/2)

@@ -46,7 +46,7 @@ cudaError_t run_flip_mark(int Q, Launch L, Ctx C, BlockShape S, int glevel);
 cudaError_t run_band(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, int glevel);
 cudaError_t run_geometry(int D, Launch L, Ctx C, int glevel, int which);
 cudaError_t run_ext_init(int Q, Launch L, Ctx C, int glevel);
-cudaError_t run_ext_iter(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int commit);
+cudaError_t run_ext_iter(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int mode);
 cudaError_t run_adv_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage);
 cudaError_t run_reinit_prep(int Q, Launch L, Ctx C, BlockShape S, int glevel);
 cudaError_t run_reinit_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage);

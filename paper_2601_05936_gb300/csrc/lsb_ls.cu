@@ -304,9 +304,12 @@ __global__ void k_ext_init(Ctx C, int glevel) { d_ext_init<Q>(C, glevel); }
 
 // One Jacobi sweep of first-order upwind extension on the band (interface cells
 // copy their value).  Neighbours outside the band read the committed field ut0.
-// commit = 1: copy uin into ut0 on the band instead.
+// mode 0: sweep; 2: sweep and store the plan (velocity S(phi) n, upwind side and
+// band membership of each upwind neighbour, interface / boundary bits), which phi
+// fixes for all sweeps of a step; 3: sweep from the plan; 1: copy uin into ut0 on
+// the band (commit).
 template <int D>
-__device__ __forceinline__ void d_ext_iter(const Ctx &C, BlockShape S, int glevel, const float *uin, float *uout, int commit) {
+__device__ __forceinline__ void d_ext_iter(const Ctx &C, BlockShape S, int glevel, const float *uin, float *uout, int mode) {
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
   const int *lst = C.band_list + (long long)glevel * C.band_cap;
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
@@ -317,22 +320,54 @@ __device__ __forceinline__ void d_ext_iter(const Ctx &C, BlockShape S, int gleve
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long fo = L.fine_off, NF = C.nfine;
     const long long c = cidx(L, x, y, z);
-    if (commit) {
+    if (mode == 1) {
       for (int a = 0; a < D; ++a) C.ut0[a * NF + fo + c] = uin[a * NF + fo + c];
+      continue;
+    }
+    const int crd[3] = {x, y, z};
+    const int str[3] = {1, L.p[0], L.p[0] * L.p[1]};
+    if (mode == 3) {
+      // sweep from the plan of the first sweep: same values, no normal, no band lookups
+      const uint8_t pf = C.plan_f[fo + c];
+      if (pf & 64) {
+        for (int a = 0; a < D; ++a) uout[a * NF + fo + c] = uin[a * NF + fo + c];
+        continue;
+      }
+      float u0[3];
+      for (int b = 0; b < D; ++b) u0[b] = uin[b * NF + fo + c];
+      float acc[3] = {0.f, 0.f, 0.f};
+      for (int a = 0; a < D; ++a) {
+        const float va = C.plan_v[a * NF + fo + c];
+        const int dir = (pf >> a) & 1 ? -1 : 1;
+        long long cn;
+        if (pf & 128) {
+          int nb[3] = {x, y, z};
+          nb[a] = clampwrap(L, a, crd[a] + dir);
+          cn = cidx(L, nb[0], nb[1], nb[2]);
+        } else {
+          cn = c + dir * str[a];
+        }
+        const float *src = (pf >> (3 + a)) & 1 ? uin : C.ut0;
+        for (int b = 0; b < D; ++b) {
+          const float un = src[b * NF + fo + cn];
+          acc[b] += va * (va > 0.f ? (u0[b] - un) : (un - u0[b]));
+        }
+      }
+      for (int b = 0; b < D; ++b) uout[b * NF + fo + c] = u0[b] - L.dtau_ext * acc[b];
       continue;
     }
     const uint8_t tg = C.tag[L.cell_off + c];
     if (tg & TAG_IFACE) {
       for (int a = 0; a < D; ++a) uout[a * NF + fo + c] = uin[a * NF + fo + c];
+      if (mode == 2) C.plan_f[fo + c] = 64;
       continue;
     }
-    const int crd[3] = {x, y, z};
     // interior: all +-1 neighbours inside the box (direct offsets, face-neighbour band flags)
     bool inner = true;
     for (int a = 0; a < D; ++a) inner = inner && crd[a] >= 1 && crd[a] + 1 < L.n[a];
     const float *phiL = C.phi + fo;
-    const int str[3] = {1, L.p[0], L.p[0] * L.p[1]};
     float nvec[3], gm = 0.f;
+    uint8_t pf = inner ? 0 : 128;
     for (int a = 0; a < D; ++a) {
       if (inner) {
         nvec[a] = 0.5f * (phiL[(unsigned)c + str[a]] - phiL[(unsigned)c - str[a]]);
@@ -376,12 +411,18 @@ __device__ __forceinline__ void d_ext_iter(const Ctx &C, BlockShape S, int gleve
         const float un = src[b * NF + fo + cn];
         acc[b] += va * (va > 0.f ? (u0[b] - un) : (un - u0[b]));
       }
+      if (mode == 2) {
+        C.plan_v[a * NF + fo + c] = va;
+        pf |= (dir < 0 ? 1 : 0) << a;
+        pf |= (inb ? 1 : 0) << (3 + a);
+      }
     }
     for (int b = 0; b < D; ++b) uout[b * NF + fo + c] = u0[b] - L.dtau_ext * acc[b];
+    if (mode == 2) C.plan_f[fo + c] = pf;
   }
 }
 template <int D>
-__global__ void k_ext_iter(Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int commit) { d_ext_iter<D>(C, S, glevel, uin, uout, commit); }
+__global__ void k_ext_iter(Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int mode) { d_ext_iter<D>(C, S, glevel, uin, uout, mode); }
 
 // ------------------------------------------------------------------ transport
 // Gather phi along axis a at offsets -3..+3; points in the band (and, for the
@@ -608,7 +649,7 @@ __global__ void k_levelset_persistent(Ctx C, BlockShape S, int glevel, int n_ext
   const float *uin = C.ut0;
   for (int it = 0; it < n_ext; ++it) {
     float *uout = (it & 1) ? C.ut2 : C.ut1;
-    d_ext_iter<D>(C, S, glevel, uin, uout, 0);
+    d_ext_iter<D>(C, S, glevel, uin, uout, it == 0 ? 2 : 3);
     if (!grid_barrier(bar, C.err)) return;
     uin = uout;
   }
@@ -851,8 +892,8 @@ cudaError_t run_band(int Q, Launch L, Ctx C, BlockShape S, const int *list, int 
 }
 cudaError_t run_geometry(int D, Launch L, Ctx C, int glevel, int which) { LD(k_geometry, C, glevel, which); }
 cudaError_t run_ext_init(int Q, Launch L, Ctx C, int glevel) { LQ(k_ext_init, C, glevel); }
-cudaError_t run_ext_iter(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int commit) {
-  LDP(k_ext_iter, C, S, glevel, uin, uout, commit);
+cudaError_t run_ext_iter(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int mode) {
+  LDP(k_ext_iter, C, S, glevel, uin, uout, mode);
 }
 cudaError_t run_adv_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage) {
   LDP(k_adv_stage, C, S, glevel, stage);
