@@ -1775,6 +1775,14 @@ lsb_status collect_cells(lsb_grid *g) {
       CU(cudaMemcpyAsync(&n, g->d_count, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
       CU(cudaStreamSynchronize(g->stream));
       cl.n = std::min(n, cl.cap);
+      // the atomics append in arbitrary order: sort by (level, cell) so that neighbouring
+      // threads work on neighbouring cells (shared coarse parents and pushes in L1/L2)
+      if (cl.n > 1) {
+        std::vector<int2> h(cl.n);
+        CU(cudaMemcpy(h.data(), cl.d, sizeof(int2) * cl.n, cudaMemcpyDeviceToHost));
+        std::sort(h.begin(), h.end(), [](const int2 &a, const int2 &b) { return a.x != b.x ? a.x < b.x : a.y < b.y; });
+        CU(cudaMemcpy(cl.d, h.data(), sizeof(int2) * cl.n, cudaMemcpyHostToDevice));
+      }
     }
   }
   return LSB_OK;

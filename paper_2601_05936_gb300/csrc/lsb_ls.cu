@@ -100,12 +100,24 @@ __global__ void k_classify_links(Ctx C, BlockShape S, const int *list, int nlist
       const uint8_t tg = C.tag[L.cell_off + c];
       if (tg & TAG_LEAF) {
         uint32_t m = 0;
-        for (int k = 0; k < Q; ++k) {
-          if (k == LT::REST) continue;
-          int sx = x - LT::cx(k), sy = y - LT::cy(k), sz = z - LT::cz(k);
-          if (!(wrap(L, 0, sx) && wrap(L, 1, sy) && (D == 2 || wrap(L, 2, sz)))) continue;
-          const uint8_t ts = C.tag[L.cell_off + cidx(L, sx, sy, sz)];
-          if ((ts & TAG_LEAF) && ((ts & TAG_GAS) != (tg & TAG_GAS))) m |= 1u << k;
+        const bool inner = x >= 1 && x + 1 < L.n[0] && y >= 1 && y + 1 < L.n[1] && (D == 2 || (z >= 1 && z + 1 < L.n[2]));
+        if (inner) {  // every source inside the box: direct offsets
+          const long long p0 = L.p[0], p01 = (long long)L.p[0] * L.p[1];
+          const uint8_t *tc = C.tag + L.cell_off + c;
+#pragma unroll
+          for (int k = 0; k < Q; ++k) {
+            if (k == LT::REST) continue;
+            const uint8_t ts = tc[-(LT::cx(k) + LT::cy(k) * p0 + LT::cz(k) * p01)];
+            if ((ts & TAG_LEAF) && ((ts & TAG_GAS) != (tg & TAG_GAS))) m |= 1u << k;
+          }
+        } else {
+          for (int k = 0; k < Q; ++k) {
+            if (k == LT::REST) continue;
+            int sx = x - LT::cx(k), sy = y - LT::cy(k), sz = z - LT::cz(k);
+            if (!(wrap(L, 0, sx) && wrap(L, 1, sy) && (D == 2 || wrap(L, 2, sz)))) continue;
+            const uint8_t ts = C.tag[L.cell_off + cidx(L, sx, sy, sz)];
+            if ((ts & TAG_LEAF) && ((ts & TAG_GAS) != (tg & TAG_GAS))) m |= 1u << k;
+          }
         }
         C.cmask[L.fine_off + c] = m;
         if (m) {
@@ -533,11 +545,21 @@ __device__ __forceinline__ void d_reinit_prep(const Ctx &C, BlockShape S, int gl
     const float p = C.phi[fc];
     const bool g = p >= 0.f;
     bool fr = false;
-    for (int i = 0; i < Q; ++i) {
-      if (i == LT::REST) continue;
-      int tx = x + LT::cx(i), ty = y + LT::cy(i), tz = z + LT::cz(i);
-      if (!(wrap(L, 0, tx) && wrap(L, 1, ty) && (D == 2 || wrap(L, 2, tz)))) continue;
-      if ((C.phi[L.fine_off + cidx(L, tx, ty, tz)] >= 0.f) != g) fr = true;
+    const bool inner = x >= 1 && x + 1 < L.n[0] && y >= 1 && y + 1 < L.n[1] && (D == 2 || (z >= 1 && z + 1 < L.n[2]));
+    if (inner) {  // every lattice neighbour inside the box: direct offsets
+      const int p0 = L.p[0], p01 = L.p[0] * L.p[1];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if (i == LT::REST) continue;
+        if ((C.phi[fc + LT::cx(i) + LT::cy(i) * p0 + LT::cz(i) * p01] >= 0.f) != g) fr = true;
+      }
+    } else {
+      for (int i = 0; i < Q; ++i) {
+        if (i == LT::REST) continue;
+        int tx = x + LT::cx(i), ty = y + LT::cy(i), tz = z + LT::cz(i);
+        if (!(wrap(L, 0, tx) && wrap(L, 1, ty) && (D == 2 || wrap(L, 2, tz)))) continue;
+        if ((C.phi[L.fine_off + cidx(L, tx, ty, tz)] >= 0.f) != g) fr = true;
+      }
     }
     C.frozen[fc] = fr ? 1 : 0;
     C.s0[fc] = p / sqrtf(p * p + 1.0f);
@@ -547,19 +569,23 @@ template <int Q>
 __global__ void k_reinit_prep(Ctx C, BlockShape S, int glevel) { d_reinit_prep<Q>(C, S, glevel); }
 
 // HJ-WENO5 one-sided derivative (Jiang & Peng 2000) from the five differences.
+// Constant divisions are multiplications by the reciprocals, and the three weights
+// gamma_k / (s_k + eps)^2 are formed as gamma_k prod_{j != k} (s_j + eps)^2 (the
+// same normalised weights, one division instead of four).
 __device__ __forceinline__ float weno5(float v1, float v2, float v3, float v4, float v5) {
   const float eps = 1e-6f;
-  const float d1 = v1 / 3.f - 7.f * v2 / 6.f + 11.f * v3 / 6.f;
-  const float d2 = -v2 / 6.f + 5.f * v3 / 6.f + v4 / 3.f;
-  const float d3 = v3 / 3.f + 5.f * v4 / 6.f - v5 / 6.f;
-  const float s1 = 13.f / 12.f * (v1 - 2.f * v2 + v3) * (v1 - 2.f * v2 + v3) +
-                   0.25f * (v1 - 4.f * v2 + 3.f * v3) * (v1 - 4.f * v2 + 3.f * v3);
-  const float s2 = 13.f / 12.f * (v2 - 2.f * v3 + v4) * (v2 - 2.f * v3 + v4) + 0.25f * (v2 - v4) * (v2 - v4);
-  const float s3 = 13.f / 12.f * (v3 - 2.f * v4 + v5) * (v3 - 2.f * v4 + v5) +
-                   0.25f * (3.f * v3 - 4.f * v4 + v5) * (3.f * v3 - 4.f * v4 + v5);
-  const float a1 = 0.1f / ((s1 + eps) * (s1 + eps));
-  const float a2 = 0.6f / ((s2 + eps) * (s2 + eps));
-  const float a3 = 0.3f / ((s3 + eps) * (s3 + eps));
+  const float r3 = 1.f / 3.f, r6 = 1.f / 6.f;
+  const float d1 = v1 * r3 - 7.f * r6 * v2 + 11.f * r6 * v3;
+  const float d2 = -v2 * r6 + 5.f * r6 * v3 + v4 * r3;
+  const float d3 = v3 * r3 + 5.f * r6 * v4 - v5 * r6;
+  const float b1 = v1 - 2.f * v2 + v3, c1 = v1 - 4.f * v2 + 3.f * v3;
+  const float b2 = v2 - 2.f * v3 + v4, c2 = v2 - v4;
+  const float b3 = v3 - 2.f * v4 + v5, c3 = 3.f * v3 - 4.f * v4 + v5;
+  const float t1 = 13.f / 12.f * b1 * b1 + 0.25f * c1 * c1 + eps;
+  const float t2 = 13.f / 12.f * b2 * b2 + 0.25f * c2 * c2 + eps;
+  const float t3 = 13.f / 12.f * b3 * b3 + 0.25f * c3 * c3 + eps;
+  const float q1 = t1 * t1, q2 = t2 * t2, q3 = t3 * t3;
+  const float a1 = 0.1f * q2 * q3, a2 = 0.6f * q1 * q3, a3 = 0.3f * q1 * q2;
   return (a1 * d1 + a2 * d2 + a3 * d3) / (a1 + a2 + a3);
 }
 
