@@ -22,13 +22,19 @@ __device__ __forceinline__ bool in_band(const Ctx &C, const LevelDev &L, const B
 
 // ------------------------------------------------------------------ classification
 // Pass 1: phase of every leaf cell from phi (liquid iff phi < 0); flipped cells
-// are listed.  init = 1 (after creation or regrid): no flips, previous = current.
-// The block's band flag of the last classification is kept as BF_OLDBAND.
+// are listed.  init = 1 (after creation or regrid): all blocks, no flips,
+// previous = current.  Otherwise only blocks of the previous band, whose band
+// flag is kept as BF_OLDBAND (other blocks keep flag 0).
 template <int Q>
 __global__ void k_classify_phase(Ctx C, BlockShape S, const int *list, int nlist, int glevel, int init) {
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     const int gb = list[w];
-    if (threadIdx.x == 0) C.bflag[gb] = (!init && (C.bflag[gb] & BF_BAND)) ? BF_OLDBAND : 0;
+    // phi changes only on band cells, so outside the previous band no phase (and no
+    // stale flip bit: flips happen next to the interface, inside the band) can change
+    const bool band = (C.bflag[gb] & BF_BAND) != 0;
+    __syncthreads();  // every thread has read the flag before thread 0 rewrites it
+    if (!init && !band) continue;
+    if (threadIdx.x == 0) C.bflag[gb] = init ? 0 : BF_OLDBAND;
     int x, y, z;
     const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
