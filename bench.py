@@ -119,6 +119,19 @@ def cpu_baseline(budget_s=20.0):
                        f"{upd:.0f} cell updates in {dt:.1f} s (numpy float64, single thread)")
 
 
+def reduce_ranks(ms, upd, dist, device):
+    """Replicas: the job's time is the slowest rank's, its work the sum over ranks."""
+    if dist is None:
+        return ms, upd
+    import torch
+    t = torch.tensor([ms, upd], dtype=torch.float64, device=device)
+    tm = t.clone()
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    ts = t.clone()
+    dist.all_reduce(ts, op=dist.ReduceOp.SUM)
+    return float(tm[0]), float(ts[1])
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -307,15 +320,7 @@ def main():
     upd = g.cell_updates(total=True) - upd0
     g.sync()
 
-    t = torch.tensor([ms, upd], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        tm = t.clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        ts = t.clone()
-        dist.all_reduce(ts, op=dist.ReduceOp.SUM)
-        ms_max, upd_sum = float(tm[0]), float(ts[1])
-    else:
-        ms_max, upd_sum = ms, upd
+    ms_max, upd_sum = reduce_ranks(ms, upd, dist, "cuda")
     value = upd_sum / (ms_max / 1e3) / 1e6
 
     # roofline of the dominant kernel (collide-and-stream), from events on the library stream
