@@ -163,6 +163,15 @@ def adjoint_bench(args, world, rank, local, barrier, dist, moving=False):
     stream = torch.cuda.Stream()
     g = lsb.Grid(case, stream=stream, device=local)
     g.step(args.warmup)
+    # forward step time of the same workload (eager, as the recorded steps run)
+    g.sync()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    g.step(args.steps)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = f0.elapsed_time(f1) / args.steps
     g.record(args.checkpoint_every)
     g.step(args.steps)
     D = g.D
@@ -228,7 +237,8 @@ def adjoint_bench(args, world, rank, local, barrier, dist, moving=False):
                             storage="fp32",
                             parallelism=f"replicas{world}", checkpoint_every=args.checkpoint_every,
                             cells=cells, l2_flush="state 318 MB x (segment store) >> 129 MB L2",
-                            dJ_dparams=[float(v) for v in dp[0]]),
+                            dJ_dparams=[float(v) for v in dp[0]], forward_ms_per_step=fwd_ms,
+                            adjoint_over_forward=(ms_max / args.steps) / fwd_ms),
                 roofline=roof, cpu_baseline=None, e2e=e2e, gpu_launches=launches, clocks=clk)
     print(json.dumps(line), flush=True)
 
