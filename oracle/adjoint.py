@@ -49,17 +49,23 @@ def params_of(sim):
 
 
 class FrozenStep:
-    """The smooth single-level step of a Sim whose level set is held fixed."""
+    """The smooth step of the finest level of a Sim whose level set is held fixed.
+
+    On a single-level grid this is the whole step.  On a multi-level grid it is
+    one finest-level sub-step: leaves that stream from the ghost ring take the
+    ring's post-collision values ``gh`` (an input here, built from the coarser
+    level by oracle/adjoint_amr.py), and ``step_adjoint`` returns their adjoint.
+    """
 
     def __init__(self, sim, phi=None):
         """``phi`` replaces the Sim's level set (same signs: the masks are the Sim's)."""
-        assert sim.L == 1, "single-level grids only"
         self.sim = sim
         self.lat = lat = sim.lat
-        self.g = g = sim.geoms[0]
+        self.g = g = sim.geoms[-1]
         self.D, self.Q = lat.D, lat.Q
-        self.phase = sim.phase[0].copy()
-        self.leaf = sim.masks[0][0].copy()
+        self.phase = sim.phase[-1].copy()
+        self.leaf = sim.masks[-1][0].copy()
+        self.ghostm = sim.masks[-1][3].copy()
         self.phi = (sim.phi if phi is None else np.asarray(phi, dtype=np.float64)).copy()
         assert np.array_equal(self.phi >= 0, sim.phi >= 0), "phi must keep the Sim's signs"
         self.gravity = sim.gravity.copy()
@@ -98,6 +104,13 @@ class FrozenStep:
         self.src = [g.shift(cells, -lat.c[kk]) for kk in range(lat.Q)]
         self.cut = np.zeros((lat.Q, g.N), dtype=bool)
         self.cut[k, x] = True
+        # leaves whose source x - c_k is a ghost-ring cell (none on a single level)
+        self.from_ghost = np.zeros((lat.Q, g.N), dtype=bool)
+        for kk in range(lat.Q):
+            src = self.src[kk][0]
+            ok = (src >= 0) & self.leaf
+            ok[ok] = self.ghostm[src[ok]]
+            self.from_ghost[kk] = ok
         self.gas = self.leaf & (self.phase == 1)
         self.centers = g.centers(1.0)
 
@@ -133,8 +146,8 @@ class FrozenStep:
         return dict(eb=eb, je=je, jp=jp, Snn=Snn, cn=cn, cvt=cvt, r=r, alpha=alpha, df=df, ccS=ccS, v=v,
                     Sbar=Sbar)
 
-    def step(self, f, p):
-        """f_{n+1} from the pre-collision populations f_n."""
+    def step(self, f, p, gh=None):
+        """f_{n+1} from the pre-collision populations f_n (and the ghost ring's values gh)."""
         lat = self.lat
         om, acc = self.cell_params(p)
         rho, u = moments(lat, f)
@@ -146,8 +159,11 @@ class FrozenStep:
             i = lat.opp[k]
             src, face = self.src[k]
             wall = (src < 0) & self.leaf
-            same = (src >= 0) & ~self.cut[k] & self.leaf
+            fg = self.from_ghost[k]
+            same = (src >= 0) & ~self.cut[k] & self.leaf & ~fg
             fn[k, same] = fc[k, src[same]]
+            if fg.any():
+                fn[k, fg] = gh[k, src[fg]]
             if wall.any():
                 fn[k, wall] = fc[i, wall] - (2 * lat.w[i] / CS2) * (self.wall_u[face[wall]] @ lat.cf[i])
         P = self._link_pieces(rho, u, S, p)
@@ -183,12 +199,13 @@ class FrozenStep:
         lam[:, g] += ((lat.cf @ au)[:, None] - (au @ u[:, g])[None, :]) / rho[g][None, :] / vol
         return lam
 
-    def step_adjoint(self, f, p, lam_next, geo=None):
+    def step_adjoint(self, f, p, lam_next, geo=None, lam_gh=None):
         """(lam_n, dJ/dp): the transpose of the step's Jacobian applied to lam_next.
 
         With ``geo`` (dict of arrays phi (N,), n (D, N), kappa (N,)), also
         accumulates the adjoints of the frozen geometry: of phi through the link
-        fractions q, and of the interface cells' normal and curvature."""
+        fractions q, and of the interface cells' normal and curvature.  With
+        ``lam_gh`` ((Q, N)), accumulates the adjoint of the ghost-ring values."""
         lat, g = self.lat, self.g
         D, Q, N = self.D, self.Q, g.N
         om, acc = self.cell_params(p)
@@ -201,8 +218,11 @@ class FrozenStep:
         for k in range(Q):
             i = lat.opp[k]
             src, _ = self.src[k]
-            same = (src >= 0) & ~self.cut[k] & self.leaf
+            fg = self.from_ghost[k]
+            same = (src >= 0) & ~self.cut[k] & self.leaf & ~fg
             np.add.at(lc[k], src[same], lam_next[k, same])
+            if fg.any():
+                np.add.at(lam_gh[k], src[fg], lam_next[k, fg])
             wall = (src < 0) & self.leaf
             lc[i, wall] += lam_next[k, wall]
         # ---- cut links: transpose of Eq. bb

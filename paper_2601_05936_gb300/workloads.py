@@ -156,35 +156,44 @@ def uniform_box(n=128, lattice="D3Q19", storage="fp32", nu=0.05, force=1e-6):
                 ls_active=False, n_ext=0, reinit_every=0, storage=storage, fp16_scale=1024.0)
 
 
-def adjoint_window(lattice="D2Q9", seed=6000, n=(32, 24), steps=20, warmup=10):
+def adjoint_window(lattice="D2Q9", seed=6000, n=(32, 24), steps=20, warmup=10, levels=1, block=None,
+                   refine_dist=4.0):
     """Frozen-interface window for the adjoint (level set held fixed, ls_active off):
     a gas bubble plus a one-cell gas film on the bottom wall (so that every
     bounce-back branch occurs: links whose back neighbour is the wall take the
     half-way fallback), a moving top wall, gravity, a body force along x,
     density ratio 10 and unequal viscosities.  ``warmup`` forward steps develop
-    the flow before the recorded ``steps``."""
+    the flow before the recorded ``steps``.  With ``levels`` > 1, ``n`` is the
+    coarse grid, the shapes are drawn on the finest grid (n * 2^(levels-1)) and
+    blocks within ``refine_dist`` finest cells of the interface are refined,
+    with no regrid (the block layout stays fixed over the window)."""
     rng = np.random.default_rng(seed)
     D = 2 if lattice == "D2Q9" else 3
     n = tuple(int(v) for v in n)
     assert len(n) == D
-    cen = _grid_centers(n)
-    c = [(0.3 + 0.1 * rng.random()) * n[0], (0.45 + 0.1 * rng.random()) * n[1]] + \
-        ([(0.45 + 0.1 * rng.random()) * n[2]] if D == 3 else [])
-    R = 0.18 * min(n) + rng.random()
+    nf = tuple(v * 2 ** (levels - 1) for v in n)
+    cen = _grid_centers(nf)
+    c = [(0.3 + 0.1 * rng.random()) * nf[0], (0.45 + 0.1 * rng.random()) * nf[1]] + \
+        ([(0.45 + 0.1 * rng.random()) * nf[2]] if D == 3 else [])
+    R = 0.18 * min(nf) + rng.random()
     bubble = R - np.sqrt(sum((cen[a] - c[a]) ** 2 for a in range(D)))
     h0 = 0.75 + 0.1 * rng.random()
     # phase-shifted modulations: no cell centre sits on an extremum, so no normal
     # component is exactly zero (the upwind choice of the extension has a kink there)
-    film = h0 + 0.05 * np.sin(2 * np.pi * cen[0] / n[0] + 0.37) - cen[D - 1]
+    film = h0 + 0.05 * np.sin(2 * np.pi * cen[0] / nf[0] + 0.37) - cen[D - 1]
     if D == 3:
-        film = film + 0.03 * np.sin(2 * np.pi * cen[1] / n[1] + 1.13)
+        film = film + 0.03 * np.sin(2 * np.pi * cen[1] / nf[1] + 1.13)
     phi = np.maximum(bubble, film)
     wall_u = np.zeros((2 * D, D))
     wall_u[2 * D - 1, 0] = 0.02  # top wall moves along x
     grav = (0.0,) * (D - 1) + (-2e-5,)
     bf = (1e-5,) + (0.0,) * (D - 1)
-    return dict(name=f"adjoint_window_{lattice}_{'x'.join(map(str, n))}", lattice=lattice, base=n, n_levels=1,
-                block=(32, 8) if D == 2 else (32, 4, 4), periodic=(True,) * (D - 1) + (False,),
+    if block is None:
+        block = (32, 8) if D == 2 else (32, 4, 4)
+    tag = f"_L{levels}" if levels > 1 else ""
+    return dict(name=f"adjoint_window_{lattice}_{'x'.join(map(str, n))}{tag}", lattice=lattice, base=n,
+                n_levels=levels, block=tuple(block), periodic=(True,) * (D - 1) + (False,),
                 rho_phys=(1.0, 0.1), nu=(0.08, 0.3), sigma=float(0.01 * (1 + rng.random())), gravity=grav,
                 body_force=bf, wall_u=wall_u.reshape(-1), phi0=phi.reshape(-1), ls_active=False, n_ext=0,
-                reinit_every=0, steps=steps, warmup=warmup)
+                reinit_every=0, steps=steps, warmup=warmup, refine_dist=[float(refine_dist)] * (levels - 1),
+                sensor="band", regrid_every=0)
