@@ -245,8 +245,14 @@ int lsb_lattice_table(int lattice, int *c, float *w, int *opp);
  *  - frozen level set (ls_active = 0 in every case): the phases, cut links,
  *    q, n and kappa are constants; transposes of the collision with forcing,
  *    the streaming with wall bounce-back and the interface bounce-back of
- *    Eq. bb with Eq. bb_cc and Eq. Sdecomp;
- *  - moving level set (ls_active = 1 in every case, reinit_every <= 1,
+ *    Eq. bb with Eq. bb_cc and Eq. Sdecomp; on block-refined grids (Sec. 2.1,
+ *    last paragraph; Sec. 2.6) also of the level recursion: the restriction
+ *    to the covered cells leaves stream from (children mean, f^neq scaled by
+ *    2 tau_c / tau_f), the fine ghost ring's values at t and t + 1/2 (coarse
+ *    interpolation, f^neq scaled by tau_f / (2 tau_c), fine collision) and
+ *    every level's sub-steps, with the block layout fixed (recorded steps do
+ *    not regrid) and every case on the same number of levels;
+ *  - moving level set (single-level grids) (ls_active = 1 in every case, reinit_every <= 1,
  *    n_reinit <= 1): the state is (f, phi, u~) and the sweep also transposes
  *    the interface velocity, the extension sweeps (Eq.
  *    hyperbolicExtension), the TVD-RK3 upwind-5 transport and the HJ-WENO5
@@ -260,17 +266,21 @@ int lsb_lattice_table(int lattice, int *c, float *w, int *opp);
  * state (populations; with a moving level set also phi and u~) into a device
  * checkpoint at the start of every checkpoint_every-th step (allocated as
  * needed).  A new lsb_record, lsb_set_params or lsb_refine ends the
- * recording and frees the checkpoints.  Errors: LSB_EINVAL
- * (checkpoint_every < 1), LSB_ESTATE (more than one level, FP16 storage,
- * cases mixing live and frozen level sets, or a moving level set with
- * reinit_every > 1 or n_reinit > 1).
+ * recording and frees the checkpoints.  Recorded steps never regrid.
+ * Errors: LSB_EINVAL (checkpoint_every < 1), LSB_ESTATE (FP16 storage, cases
+ * mixing live and frozen level sets, a moving level set with more than one
+ * level, reinit_every > 1 or n_reinit > 1, or cases with different numbers
+ * of levels on a multi-level grid).
  *
  * lsb_backward(g, dJ_dobs, dJ_dparams, dJ_dphi0): reverse sweep over every
  * step recorded so far.  Segment by segment, from the last, it restores the
  * checkpoint, recomputes the segment's steps keeping their states (device
  * memory for checkpoint_every states), and runs the adjoint steps backwards
  * (with a moving level set each adjoint step first replays that step's
- * level-set passes).
+ * level-set passes; on a multi-level grid each adjoint step first replays
+ * its coarse step, keeping every level's populations per call of the level
+ * recursion: 2^L - 1 further states plus 2^(L-1) - 1 for the coarse
+ * sub-steps' results, allocated on the first multi-level lsb_backward).
  * dJ_dobs: host, n_cases x (4 + 2 D) doubles, weights of the observables
  * in lsb_observables order (centroid, volume and leaf count are constants of
  * the map).  dJ_dparams: host, n_cases x LSB_NPARAM_ADJ doubles, or NULL;
@@ -284,7 +294,7 @@ int lsb_lattice_table(int lattice, int *c, float *w, int *opp);
  * Afterwards the state is that of the last recorded step again, the
  * recording stays open (lsb_backward may be called again, e.g. with other
  * weights, and lsb_step extends the recording), LSB_FIELD_ADJ_F returns dJ/df
- * and, with a moving level set, LSB_FIELD_ADJ_UEXT dJ/du~ at the start of the
+ * (per level; zero outside the leaves) and, with a moving level set, LSB_FIELD_ADJ_UEXT dJ/du~ at the start of the
  * window.  FP32 adjoint fields, FP64 parameter sums.  Synchronises.  Errors:
  * LSB_EINVAL, LSB_ESTATE (no recording, or a phase change in the window),
  * LSB_ENOMEM, LSB_ECUDA.

@@ -128,7 +128,10 @@ __global__ void k_adj_seed(Ctx C, BlockShape S, const int *list, int nlist, cons
 // thread writes it).  df's adjoint goes to the moments and strain rate of x and y.
 //
 // grad per case (NG_ADJ doubles): [0] sigma, [1, 2] rho_phys through [p],
-// [3, 4] eta, [5, 6] omega per phase, [7 .. 12] acceleration per phase.
+// [3, 4] eta, [5, 6] the kinematic viscosity per phase through the relaxation
+// rates and times of every level (d omega_l / d nu = -3 omega_l^2 / r_l with
+// r_l = 2^(L-1-l)), [7 .. 12] the finest level's lattice acceleration per phase
+// (level l uses r_l times it).
 template <int Q>
 __global__ void k_adj_links(Ctx C, int glevel, const float *__restrict__ F, float *lamN, float *LA, float *MA,
                             double *grad, int ncase, GeoAdj G) {
@@ -412,7 +415,9 @@ __global__ void __launch_bounds__(512, 1) k_adj_collide(Ctx C, BlockShape S, con
     const unsigned p0 = (unsigned)L.p[0], p01 = (unsigned)(L.p[0] * L.p[1]);
     const unsigned c = x + p0 * y + p01 * z;
     const uint8_t tg = C.tag[L.cell_off + c];
-    if (!(tg & TAG_LEAF)) break;
+    // leaves and the covered cells that leaves stream from collide and push; a
+    // push into any other cell is not used, and lambda is zero there
+    if (!(tg & (TAG_LEAF | TAG_RLAYER))) break;
     const unsigned N = (unsigned)L.ncell;
     const float *Fl = F + L.cell_off * Q;
     const float *lN = lamN + L.cell_off * Q;
@@ -515,12 +520,14 @@ __global__ void __launch_bounds__(512, 1) k_adj_collide(Ctx C, BlockShape S, con
     for (int j = 0; j < Q; ++j)
       lO[j * N + c] = (1.0f - om) * LC(j) + base + g0[0] * LT::cx(j) + g0[1] * LT::cy(j) + g0[2] * LT::cz(j);
     const float wl = ph ? 0.f : 1.f, wg = ph ? 1.f : 0.f;
-    part[0] = wl * lom;
-    part[1] = wg * lom;
+    const float r = (float)L.scale;
+    const float dnu = -3.0f * om * om / r;  // d omega_l / d nu
+    part[0] = wl * lom * dnu;
+    part[1] = wg * lom * dnu;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      part[2 + a] = wl * lac[a];
-      part[5 + a] = wg * lac[a];
+      part[2 + a] = wl * lac[a] * r;
+      part[5 + a] = wg * lac[a] * r;
     }
 #undef LC
     } while (false);
@@ -609,7 +616,7 @@ __global__ void k_adj_macro(Ctx C, int glevel, const float *__restrict__ F, floa
       }
       lO[jj * N + c] += v;
     }
-    const double lom = (double)(sP * kk / om);
+    const double lom = (double)(sP * kk / om) * (double)(-3.0f * om * om / (float)L.scale);  // per nu
     if (lom != 0.0) {
       if (shared_sum) atomicAdd(sg + L.case_id * 2 + ph, lom);
       else atomicAdd(grad + (long long)L.case_id * NG_ADJ + 5 + ph, lom);
@@ -746,6 +753,346 @@ __global__ void k_adj_geometry(Ctx C, int glevel, GeoAdj G) {
   }
 }
 
+// ------------------------------------------------------------------ level transfers (multi-level grids)
+// Transposes of the Dupuis-Chopard transfers of the forward step (Sec. 2.1, last
+// paragraph): the fine ghost ring's values (coarse interpolation at time weight
+// theta, f^neq scaled by tau_f / (2 tau_c), fine collision) and the restriction
+// (children mean, f^neq scaled by 2 tau_c / tau_f).  The forward values are
+// recomputed from the recorded states of the step.
+
+namespace {
+
+// out_j += d/df_j sum_i lam_i f~eq_i(rho(f), u(f)) on deviations f~ = f - w:
+// d feq_i / d rho = feq_i / rho, d feq_i / d u_a = w_i rho (3 c_ia + 9 (c_i.u) c_ia - 3 u_a),
+// d rho / d f_j = 1, d u_a / d f_j = (c_ja - u_a) / rho.
+template <int Q>
+__device__ __forceinline__ void feq_T(const float *f, const float *lam, float *out) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  float drho, u[3];
+  lb_moments<Q>(f, drho, u);
+  const float rho = 1.0f + drho, irho = 1.0f / rho;
+  const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  float As = 0.f, B[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
+    const float cu = cx * u[0] + cy * u[1] + cz * u[2];
+    As += lam[i] * (feq_dev<Q>(i, drho, u, usq) + LT::w(i)) * irho;
+    const float g = lam[i] * LT::w(i) * rho;
+    B[0] += g * (3.0f * cx + 9.0f * cu * cx - 3.0f * u[0]);
+    B[1] += g * (3.0f * cy + 9.0f * cu * cy - 3.0f * u[1]);
+    if (D == 3) B[2] += g * (3.0f * cz + 9.0f * cu * cz - 3.0f * u[2]);
+  }
+  const float base = As - (B[0] * u[0] + B[1] * u[1] + B[2] * u[2]) * irho;
+#pragma unroll
+  for (int j = 0; j < Q; ++j)
+    out[j] += base + (B[0] * LT::cx(j) + B[1] * LT::cy(j) + B[2] * LT::cz(j)) * irho;
+}
+
+// f~ -> f~eq(rho, u) + fac (f~ - f~eq), in place
+template <int Q>
+__device__ __forceinline__ void rescale_q(float *f, float fac) {
+  float drho, u[3];
+  lb_moments<Q>(f, drho, u);
+  const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float fe = feq_dev<Q>(i, drho, u, usq);
+    f[i] = fe + fac * (f[i] - fe);
+  }
+}
+
+// The coarse cells a fine cell interpolates from: the parent and, per axis, the
+// upper and lower neighbours where they are leaves (central difference with
+// both, one-sided with one), with the weights of the forward interpolation.
+// Returns the number of (cell, weight) pairs written (at most 1 + 2 D).
+template <int D>
+__device__ __forceinline__ int interp_stencil(const Ctx &C, const LevelDev &Lc, int x, int y, int z,
+                                              long long *cell, float *wt) {
+  const int P[3] = {x >> 1, y >> 1, D == 3 ? (z >> 1) : 0};
+  const long long cp = cidx(Lc, P[0], P[1], P[2]);
+  int n = 1;
+  cell[0] = cp;
+  wt[0] = 1.f;
+  const int fcrd[3] = {x, y, z};
+  for (int a = 0; a < D; ++a) {
+    const float delta = ((fcrd[a] & 1) - 0.5f) * 0.5f;
+    int up[3] = {P[0], P[1], P[2]}, dn[3] = {P[0], P[1], P[2]};
+    up[a] += 1;
+    dn[a] -= 1;
+    bool upok = wrap(Lc, a, up[a]);
+    bool dnok = wrap(Lc, a, dn[a]);
+    long long cu = 0, cd = 0;
+    if (upok) {
+      cu = cidx(Lc, up[0], up[1], up[2]);
+      upok = (C.tag[Lc.cell_off + cu] & TAG_LEAF) != 0;
+    }
+    if (dnok) {
+      cd = cidx(Lc, dn[0], dn[1], dn[2]);
+      dnok = (C.tag[Lc.cell_off + cd] & TAG_LEAF) != 0;
+    }
+    if (upok && dnok) {
+      cell[n] = cu; wt[n++] = 0.5f * delta;
+      cell[n] = cd; wt[n++] = -0.5f * delta;
+    } else if (upok) {
+      cell[n] = cu; wt[n++] = delta;
+      wt[0] -= delta;
+    } else if (dnok) {
+      cell[n] = cd; wt[n++] = -delta;
+      wt[0] += delta;
+    }
+  }
+  return n;
+}
+
+// Per-CTA FP64 sums of the transfer partials (nu per phase, acceleration per
+// phase), flushed to grad; cases beyond kShCases go straight to global atomics.
+struct TransferSums {
+  double *sg;
+  bool shared_sum;
+  __device__ void add(double *grad, int case_id, int k, float v) {
+    if (v == 0.f) return;
+    if (shared_sum) atomicAdd(sg + case_id * 8 + k, (double)v);
+    else atomicAdd(grad + (long long)case_id * NG_ADJ + 5 + k, (double)v);
+  }
+};
+
+}  // namespace
+
+// One thread per ghost cell g of a fine level: the adjoint of its post-collision
+// values is what the fine leaves that pulled them hold in lambda (lamNf, the
+// fine level's adjoint after the sub-step): lg_i = lambda(g + c_i, i) where that
+// cell is a leaf.  Back through the fine collision, the f^neq rescale and the
+// interpolation to the coarse cells, split (1 - theta) to the coarse state at t
+// (accumulated in lamX) and theta to the state at t + 1 (lamNc, before the
+// coarse sub-step's transpose reads it).
+template <int Q>
+__global__ void k_adj_ghost(Ctx C, const int2 *cells, int n, float theta, const float *__restrict__ Fold,
+                            const float *__restrict__ Fnew, const float *__restrict__ lamNf, float *lamX, float *lamNc,
+                            double *grad, int ncase) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  __shared__ double sg[kShCases * 8];
+  TransferSums T{sg, ncase <= kShCases};
+  for (int k = threadIdx.x; k < kShCases * 8; k += blockDim.x) sg[k] = 0.0;
+  __syncthreads();
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 it = cells[e];
+    const LevelDev &F = C.lds[it.x];
+    const LevelDev &Lc = C.lds[F.parent_ld];
+    const long long c = it.y;
+    const int x = (int)(c % F.p[0]);
+    const int y = (int)((c / F.p[0]) % F.p[1]);
+    const int z = (int)(c / ((long long)F.p[0] * F.p[1]));
+    float lg[Q];
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      lg[i] = 0.f;
+      if (i == LT::REST) continue;
+      int tx = x + LT::cx(i), ty = y + LT::cy(i), tz = z + LT::cz(i);
+      if (!(wrap(F, 0, tx) && wrap(F, 1, ty) && (D == 2 || wrap(F, 2, tz)))) continue;
+      const long long ct = cidx(F, tx, ty, tz);
+      if (!(C.tag[F.cell_off + ct] & TAG_LEAF)) continue;
+      lg[i] = lamNf[F.cell_off * Q + (long long)i * F.ncell + ct];
+      any |= lg[i] != 0.f;
+    }
+    if (!any) continue;
+    // forward: interpolation at theta, rescale, fine collision
+    long long sc[1 + 2 * 3];
+    float sw[1 + 2 * 3];
+    const int ns = interp_stencil<D>(C, Lc, x, y, z, sc, sw);
+    const long long Nc = Lc.ncell;
+    const float *Ao = Fold + Lc.cell_off * Q;
+    const float *An = Fnew + Lc.cell_off * Q;
+    float fi[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fi[i] = 0.f;
+    for (int s = 0; s < ns; ++s) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        float a = Ao[i * Nc + sc[s]];
+        if (theta != 0.f) a = (1.0f - theta) * a + theta * An[i * Nc + sc[s]];
+        fi[i] += sw[s] * a;
+      }
+    }
+    const long long cpar = sc[0];
+    const int ph = C.tag[Lc.cell_off + cpar] & TAG_GAS;
+    const float tf = F.tau[ph], tc = Lc.tau[ph];
+    const float fac = tf / (2.0f * tc);
+    float fr[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fr[i] = fi[i];
+    rescale_q<Q>(fr, fac);
+    // transpose of the collision fc = f + om (feq - f) + 3 w rho (c.acc)
+    const float om = F.omega[ph];
+    const float acc[3] = {F.acc[ph][0], F.acc[ph][1], F.acc[ph][2]};
+    float drho, u[3];
+    lb_moments<Q>(fr, drho, u);
+    const float rho = 1.0f + drho, usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    float lr[Q], lom_in[Q];
+    float lom = 0.f, lac[3] = {0.f, 0.f, 0.f}, frc = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const float cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
+      lom += lg[i] * (feq_dev<Q>(i, drho, u, usq) - fr[i]);
+      const float wl = 3.0f * LT::w(i) * lg[i];
+      frc += wl * (cx * acc[0] + cy * acc[1] + cz * acc[2]);
+      lac[0] += wl * rho * cx;
+      lac[1] += wl * rho * cy;
+      lac[2] += wl * rho * cz;
+      lr[i] = (1.0f - om) * lg[i];
+      lom_in[i] = om * lg[i];
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) lr[i] += frc;  // the forcing's rho
+    feq_T<Q>(fr, lom_in, lr);
+    // transpose of the rescale f -> feq + fac (f - feq) at fi
+    float li[Q], l1[Q];
+    float dfe = 0.f;
+    {
+      float dr2, u2[3];
+      lb_moments<Q>(fi, dr2, u2);
+      const float us2 = u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        dfe += lr[i] * (fi[i] - feq_dev<Q>(i, dr2, u2, us2));
+        li[i] = fac * lr[i];
+        l1[i] = (1.0f - fac) * lr[i];
+      }
+    }
+    feq_T<Q>(fi, l1, li);
+    // transpose of the interpolation, split between the coarse states at t and t + 1
+    for (int s = 0; s < ns; ++s) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const float v = sw[s] * li[i];
+        const long long o = Lc.cell_off * Q + (long long)i * Nc + sc[s];
+        atomicAdd(lamX + o, (1.0f - theta) * v);
+        if (theta != 0.f) atomicAdd(lamNc + o, theta * v);
+      }
+    }
+    // partials: omega_f(nu), the rescale factor tau_f / (2 tau_c)(nu), acc_f = r_f acc
+    const float rf = (float)F.scale, rc = (float)Lc.scale;
+    const float dfac = (3.0f / rf * tc - tf * 3.0f / rc) / (2.0f * tc * tc);
+    T.add(grad, F.case_id, ph, lom * (-3.0f * om * om / rf) + dfe * dfac);
+    for (int a = 0; a < D; ++a) T.add(grad, F.case_id, 2 + 3 * ph + a, lac[a] * rf);
+  }
+  __syncthreads();
+  if (T.shared_sum)
+    for (int k = threadIdx.x; k < ncase * 8; k += blockDim.x)
+      if (sg[k] != 0.0) atomicAdd(grad + (long long)(k / 8) * NG_ADJ + 5 + (k % 8), sg[k]);
+}
+
+// After the coarse sub-step's transpose: lamX (the ghost rings' share of the
+// coarse state at t) joins lamOc and is cleared.  One thread per ghost cell walks
+// its interpolation stencil; atomicExch hands each value to one thread.
+template <int Q>
+__global__ void k_adj_ghost_apply(Ctx C, const int2 *cells, int n, float *lamX, float *lamOc) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 it = cells[e];
+    const LevelDev &F = C.lds[it.x];
+    const LevelDev &Lc = C.lds[F.parent_ld];
+    const long long c = it.y;
+    const int x = (int)(c % F.p[0]);
+    const int y = (int)((c / F.p[0]) % F.p[1]);
+    const int z = (int)(c / ((long long)F.p[0] * F.p[1]));
+    long long sc[1 + 2 * 3];
+    float sw[1 + 2 * 3];
+    const int ns = interp_stencil<D>(C, Lc, x, y, z, sc, sw);
+    for (int s = 0; s < ns; ++s)
+      for (int i = 0; i < Q; ++i) {
+        const long long o = Lc.cell_off * Q + (long long)i * Lc.ncell + sc[s];
+        const float v = atomicExch(lamX + o, 0.f);
+        if (v != 0.f) lamOc[o] += v;
+      }
+  }
+}
+
+// One thread per restriction-layer cell of a coarse level: its adjoint (written
+// by the coarse sub-step's transpose) goes back through the rescale by
+// 2 tau_c / tau_f and the mean to the 2^D children's adjoints (lamF, the fine
+// level's adjoint at the start of the coarse sub-step), and is cleared.  Ff: the
+// fine level's populations the restriction read.
+template <int Q>
+__global__ void k_adj_restrict(Ctx C, const int2 *cells, int n, const float *__restrict__ Ff, float *lamOc,
+                               float *lamF, double *grad, int ncase) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  __shared__ double sg[kShCases * 8];
+  TransferSums T{sg, ncase <= kShCases};
+  for (int k = threadIdx.x; k < kShCases * 8; k += blockDim.x) sg[k] = 0.0;
+  __syncthreads();
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 it = cells[e];
+    const LevelDev &L = C.lds[it.x];
+    const LevelDev &F = C.lds[L.child_ld];
+    const long long c = it.y;
+    const int x = (int)(c % L.p[0]);
+    const int y = (int)((c / L.p[0]) % L.p[1]);
+    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    float lr[Q];
+    bool any = false;
+    float *lo = lamOc + L.cell_off * Q;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      lr[i] = lo[i * L.ncell + c];
+      lo[i * L.ncell + c] = 0.f;
+      any |= lr[i] != 0.f;
+    }
+    if (!any) continue;
+    const int nz = (D == 3) ? 2 : 1;
+    const float inv = 1.0f / (float)(4 * nz);
+    const float *Af = Ff + F.cell_off * Q;
+    float m[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) m[i] = 0.f;
+    for (int sz = 0; sz < nz; ++sz)
+      for (int sy = 0; sy < 2; ++sy)
+        for (int sx = 0; sx < 2; ++sx) {
+          const long long cf = cidx(F, 2 * x + sx, 2 * y + sy, D == 3 ? 2 * z + sz : 0);
+#pragma unroll
+          for (int i = 0; i < Q; ++i) m[i] += Af[i * F.ncell + cf];
+        }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) m[i] *= inv;
+    const int ph = C.tag[L.cell_off + c] & TAG_GAS;
+    const float tc = L.tau[ph], tf = F.tau[ph];
+    const float fac = 2.0f * tc / tf;
+    float lm[Q], l1[Q], dfe = 0.f;
+    {
+      float dr, u[3];
+      lb_moments<Q>(m, dr, u);
+      const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        dfe += lr[i] * (m[i] - feq_dev<Q>(i, dr, u, usq));
+        lm[i] = fac * lr[i];
+        l1[i] = (1.0f - fac) * lr[i];
+      }
+    }
+    feq_T<Q>(m, l1, lm);
+    float *lf = lamF + F.cell_off * Q;
+    for (int sz = 0; sz < nz; ++sz)
+      for (int sy = 0; sy < 2; ++sy)
+        for (int sx = 0; sx < 2; ++sx) {
+          const long long cf = cidx(F, 2 * x + sx, 2 * y + sy, D == 3 ? 2 * z + sz : 0);
+#pragma unroll
+          for (int i = 0; i < Q; ++i) lf[i * F.ncell + cf] += lm[i] * inv;
+        }
+    const float rf = (float)F.scale, rc = (float)L.scale;
+    const float dfac = 2.0f * (3.0f / rc * tf - tc * 3.0f / rf) / (tf * tf);
+    T.add(grad, L.case_id, ph, dfe * dfac);
+  }
+  __syncthreads();
+  if (T.shared_sum)
+    for (int k = threadIdx.x; k < ncase * 8; k += blockDim.x)
+      if (sg[k] != 0.0) atomicAdd(grad + (long long)(k / 8) * NG_ADJ + 5 + (k % 8), sg[k]);
+}
+
 // ------------------------------------------------------------------ launchers
 #define LSB_ADJ_Q(Q, fn, L, ...)                                                      \
   do {                                                                                \
@@ -778,6 +1125,20 @@ cudaError_t run_adj_collide(int Q, Launch L, Ctx C, BlockShape S, const int *lis
 cudaError_t run_adj_macro(int Q, Launch L, Ctx C, int glevel, const float *F, float *lamO, float *MA, double *grad,
                           int ncase) {
   LSB_ADJ_Q(Q, k_adj_macro, L, C, glevel, F, lamO, MA, grad, ncase);
+}
+
+cudaError_t run_adj_ghost(int Q, Launch L, Ctx C, const int2 *cells, int n, float theta, const float *Fold,
+                          const float *Fnew, const float *lamNf, float *lamX, float *lamNc, double *grad, int ncase) {
+  LSB_ADJ_Q(Q, k_adj_ghost, L, C, cells, n, theta, Fold, Fnew, lamNf, lamX, lamNc, grad, ncase);
+}
+
+cudaError_t run_adj_ghost_apply(int Q, Launch L, Ctx C, const int2 *cells, int n, float *lamX, float *lamOc) {
+  LSB_ADJ_Q(Q, k_adj_ghost_apply, L, C, cells, n, lamX, lamOc);
+}
+
+cudaError_t run_adj_restrict(int Q, Launch L, Ctx C, const int2 *cells, int n, const float *Ff, float *lamOc,
+                             float *lamF, double *grad, int ncase) {
+  LSB_ADJ_Q(Q, k_adj_restrict, L, C, cells, n, Ff, lamOc, lamF, grad, ncase);
 }
 
 }  // namespace lsb

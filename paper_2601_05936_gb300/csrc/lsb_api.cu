@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -28,9 +29,10 @@ constexpr int MAXL = 4;
 const char *const KNAMES[] = {"k_collide_stream", "k_interface_bc", "k_restrict", "k_ghost", "k_prolong", "k_level_tags", "k_observables", "k_export", "k_classify_phase", "k_classify_links", "k_band", "k_geometry", "k_ext_init", "k_ext_iter", "k_adv_stage", "k_reinit_prep", "k_reinit_stage", "k_refill", "k_sensor", "k_init", "k_collect",
                                "k_collide_stream_l1", "k_collide_stream_l2", "k_collide_stream_l3", "k_adj_seed",
                                "k_adj_links", "k_adj_collide", "k_adj_macro", "k_adj_geometry",
-                               "k_levelset_persistent", "k_lsa"};
+                               "k_levelset_persistent", "k_lsa", "k_adj_ghost", "k_adj_ghost_apply",
+                               "k_adj_restrict", "k_tape"};
 constexpr int KADJ_SEED = 24, KADJ_LINKS = 25, KADJ_COLLIDE = 26, KADJ_MACRO = 27, KADJ_GEOM = 28, KLS_PERSIST = 29,
-              KLSA = 30;
+              KLSA = 30, KADJ_GHOST = 31, KADJ_GAPPLY = 32, KADJ_RESTRICT = 33;
 constexpr int NKERN = sizeof(KNAMES) / sizeof(KNAMES[0]);
 
 struct ProfRec {
@@ -135,7 +137,13 @@ struct lsb_grid {
   int seg_cap = 0;
   size_t seg_slot = 0;            // bytes per stored state
   float *d_adj[2] = {nullptr, nullptr};
-  int adj_cur = -1;               // d_adj[adj_cur] holds dJ/df_0 after lsb_backward
+  int adj_cur = -1;               // >= 0 once lsb_backward has run: dJ/df_0 is held in d_adj
+  int apar[MAXL] = {0, 0, 0, 0};  // level l's adjoint is d_adj[apar[l]] (its region of the buffer)
+  // multi-level grids: the step is replayed with every level's populations recorded per
+  // call of the level recursion (preorder), input of the transposed transfers
+  int tape_on = 0, tape_call = 0;
+  std::vector<float *> tape_old, tape_new;  // state at the call's start (after restriction), after its sub-step
+  float *d_adjx = nullptr;                  // coarse adjoint shares of the ghost rings (kept zero)
   float *d_fsave = nullptr, *d_madj = nullptr, *d_linkadj = nullptr;
   float *d_gphi = nullptr, *d_gn = nullptr, *d_gk = nullptr;  // level-set adjoint (finest level)
   // moving level set: the state is (f, phi, u~); scratch of the level-set replay and transposes
@@ -512,6 +520,28 @@ bool ls_active_any(const lsb_grid *g, int l) {
   return false;
 }
 
+// Copy every case's level-l populations from src to dst (same offsets: each level's
+// region of a Q x ncell_total array).
+lsb_status copy_level(lsb_grid *g, float *dst, const float *src, int l) {
+  for (const LevelDev &L : g->lds) {
+    if (L.level != l) continue;
+    const size_t off = (size_t)L.cell_off * g->Q, n = (size_t)L.ncell * g->Q;
+    CU(cudaMemcpyAsync(dst + off, src + off, sizeof(float) * n, cudaMemcpyDeviceToDevice, g->stream));
+  }
+  return LSB_OK;
+}
+
+// The populations of every level (each level's current buffer) into one
+// Q x ncell_total array, and back.
+lsb_status snapshot(lsb_grid *g, float *dst) {
+  for (int l = 0; l < g->Lmax; ++l) TRY(copy_level(g, dst, (const float *)g->d_buf[g->par[l]], l));
+  return LSB_OK;
+}
+lsb_status restore(lsb_grid *g, const float *src) {
+  for (int l = 0; l < g->Lmax; ++l) TRY(copy_level(g, (float *)g->d_buf[g->par[l]], src, l));
+  return LSB_OK;
+}
+
 // One advance of global level l (recursive over finer levels).
 lsb_status advance(lsb_grid *g, int l) {
   BlockShape S = shape(g);
@@ -520,6 +550,8 @@ lsb_status advance(lsb_grid *g, int l) {
   const int Q = g->Q, st = g->storage;
   const CellList &rc = g->rl_cells[l];
   RUN(2, 0, rc.n, 128, run_restrict_cells, Q, st, LN(g, (rc.n + 127) / 128, 128), C, (const int2 *)rc.d, rc.n);
+  const int call = g->tape_on ? g->tape_call++ : -1;
+  if (call >= 0) TRY(copy_level(g, g->tape_old[call], (const float *)g->d_buf[g->par[l]], l));
   const double cs_bytes = 2.0 * g->Q * (g->storage == LSB_FP32 ? 4 : 2) * g->leaf_cells[l];
   if (g->d_tmaps && !g->no_tma) {
     const int grid = std::min(g->cs[l].n, g->tma_grid);
@@ -539,6 +571,7 @@ lsb_status advance(lsb_grid *g, int l) {
     }  // a frozen level set leaves phases, cut links and geometry as they are
     g->fine_steps[l]++;
   }
+  if (call >= 0 && l + 1 < g->Lmax) TRY(copy_level(g, g->tape_new[call], (const float *)g->d_buf[1 - g->par[l]], l));
   if (l + 1 < g->Lmax) {
     for (int sub = 0; sub < 2; ++sub) {
       C = make_ctx(g);
@@ -752,7 +785,8 @@ lsb_status rec_checkpoint(lsb_grid *g) {
   if (e != cudaSuccess) return fail(g, LSB_ENOMEM, "checkpoint cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
   g->rec_ckpt.push_back(p);
   const size_t sf = state_floats(g);
-  CU(cudaMemcpyAsync(p, g->d_buf[g->par[0]], sizeof(float) * sf, cudaMemcpyDeviceToDevice, g->stream));
+  if (g->Lmax > 1) TRY(snapshot(g, p));
+  else CU(cudaMemcpyAsync(p, g->d_buf[g->par[0]], sizeof(float) * sf, cudaMemcpyDeviceToDevice, g->stream));
   if (g->rec_moving) {
     CU(cudaMemcpyAsync(p + sf, g->d_phi, sizeof(float) * g->nfine, cudaMemcpyDeviceToDevice, g->stream));
     CU(cudaMemcpyAsync(p + sf + g->nfine, g->d_ut[0], sizeof(float) * g->D * g->nfine, cudaMemcpyDeviceToDevice,
@@ -974,6 +1008,122 @@ lsb_status adj_step_moving(lsb_grid *g, const float *F, float *phi_n, const floa
   RUN(KADJ_GEOM, 0, 1, 128, run_adj_geometry, D, LN(g, DYN_GRID, 128), R, 0, G);
   CU(cudaMemsetAsync(g->d_gn, 0, bD, g->stream));
   CU(cudaMemsetAsync(g->d_gk, 0, b1, g->stream));
+  return LSB_OK;
+}
+
+// Multi-level grids: tape buffers for one replayed coarse step (a full-size state
+// per call of the level recursion, two for calls of non-finest levels) and the
+// zeroed scratch of the ghost rings' coarse shares.
+lsb_status amr_buffers(lsb_grid *g) {
+  const size_t sb = sizeof(float) * state_floats(g);
+  const int ncall = (1 << g->Lmax) - 1;
+  if ((int)g->tape_old.size() == ncall) return LSB_OK;
+  for (float *p : g->tape_old) cudaFree(p);
+  for (float *p : g->tape_new) cudaFree(p);
+  g->tape_old.assign(ncall, nullptr);
+  g->tape_new.assign(ncall, nullptr);
+  // preorder: call c sits at level lev[c]
+  std::vector<int> lev;
+  std::function<void(int)> walk = [&](int l) {
+    lev.push_back(l);
+    if (l + 1 < g->Lmax) {
+      walk(l + 1);
+      walk(l + 1);
+    }
+  };
+  walk(0);
+  for (int c = 0; c < ncall; ++c) {
+    cudaError_t e = cudaMalloc(&g->tape_old[c], sb);
+    if (e == cudaSuccess && lev[c] + 1 < g->Lmax) e = cudaMalloc(&g->tape_new[c], sb);
+    if (e != cudaSuccess) return fail(g, LSB_ENOMEM, "adjoint tape cudaMalloc(%zu): %s", sb, cudaGetErrorString(e));
+  }
+  if (!g->d_adjx) TRY(dalloc(g, &g->d_adjx, sb));
+  CU(cudaMemsetAsync(g->d_adjx, 0, sb, g->stream));
+  return LSB_OK;
+}
+
+// Reverse of advance(g, l) for the call with preorder index `call` of the replayed
+// step: the second fine sub-step, the ghost transfer at t + 1/2, the first fine
+// sub-step, the ghost transfer at t, the level's own sub-step (links, collision and
+// streaming, moment adjoints on the finest level), the ghost rings' share of the
+// level's state at t, and the restriction, whose adjoint goes to the finer level.
+lsb_status adj_amr(lsb_grid *g, int l, int call, GeoAdj G) {
+  const int Q = g->Q, Lm = g->Lmax;
+  const bool last = l == Lm - 1;
+  const Ctx C = make_ctx(g);
+  const BlockShape S = shape(g);
+  const float *Fold = g->tape_old[call];
+  float *lamN = g->d_adj[g->apar[l]], *lamO = g->d_adj[1 - g->apar[l]];
+  const int tb = 128;
+  if (!last) {
+    const int sub = (1 << (Lm - l - 1)) - 1;  // calls in a child's subtree
+    const int c1 = call + 1, c2 = call + 1 + sub;
+    const CellList &gc = g->ghost_cells[l + 1];
+    const int gg = std::max(1, std::min((gc.n + tb - 1) / tb, DYN_GRID));
+    TRY(adj_amr(g, l + 1, c2, G));
+    // the finer level's adjoint after the sub-step is the input its transpose just read
+    RUN(KADJ_GHOST, 0, gc.n, tb, run_adj_ghost, Q, LN(g, gg, tb), C, (const int2 *)gc.d, gc.n, 0.5f, Fold,
+        (const float *)g->tape_new[call], (const float *)g->d_adj[1 - g->apar[l + 1]], g->d_adjx, lamN, g->d_grad,
+        g->ncase);
+    TRY(adj_amr(g, l + 1, c1, G));
+    RUN(KADJ_GHOST, 0, gc.n, tb, run_adj_ghost, Q, LN(g, gg, tb), C, (const int2 *)gc.d, gc.n, 0.0f, Fold,
+        (const float *)nullptr, (const float *)g->d_adj[1 - g->apar[l + 1]], g->d_adjx, lamN, g->d_grad, g->ncase);
+  }
+  if (last)
+    RUN(KADJ_LINKS, 0, 1, 128, run_adj_links, Q, LN(g, DYN_GRID, 128), C, l, Fold, lamN, g->d_linkadj, g->d_madj,
+        g->d_grad, g->ncase, G);
+  const int grid = std::min(g->cs[l].n, 152);
+  RUN(KADJ_COLLIDE, 3.0 * Q * sizeof(float) * g->leaf_cells[l], g->cs[l].n, g->nthreads, run_adj_collide, Q,
+      LN(g, grid, g->nthreads), C, S, (const int *)g->cs[l].d, g->cs[l].n, Fold, (const float *)lamN, lamO,
+      (const float *)g->d_linkadj, g->d_grad);
+  if (last)
+    RUN(KADJ_MACRO, 0, 1, 128, run_adj_macro, Q, LN(g, DYN_GRID, 128), C, l, Fold, lamO, g->d_madj, g->d_grad,
+        g->ncase);
+  if (!last) {
+    const CellList &gc = g->ghost_cells[l + 1];
+    const int gg = std::max(1, std::min((gc.n + tb - 1) / tb, DYN_GRID));
+    RUN(KADJ_GAPPLY, 0, gc.n, tb, run_adj_ghost_apply, Q, LN(g, gg, tb), C, (const int2 *)gc.d, gc.n, g->d_adjx,
+        lamO);
+  }
+  g->apar[l] ^= 1;
+  if (!last) {
+    const CellList &rc = g->rl_cells[l];
+    const int rg = std::max(1, std::min((rc.n + tb - 1) / tb, DYN_GRID));
+    RUN(KADJ_RESTRICT, 0, rc.n, tb, run_adj_restrict, Q, LN(g, rg, tb), C, (const int2 *)rc.d, rc.n,
+        (const float *)g->tape_old[call + 1], lamO, g->d_adj[g->apar[l + 1]], g->d_grad, g->ncase);
+  }
+  return LSB_OK;
+}
+
+// Reverse sweep over a multi-level recording (frozen level set): segments are
+// recomputed from their checkpoints with every coarse step's start state stored;
+// each step is then replayed once more with the tape on and transposed.  The
+// adjoint of the final observables is already in d_adj[0] (every level).
+lsb_status backward_amr(lsb_grid *g, GeoAdj G) {
+  const long long T = g->rec_steps;
+  const int every = g->rec_every;
+  const size_t sl = slot_floats(g);
+  TRY(amr_buffers(g));
+  for (int l = 0; l < MAXL; ++l) g->apar[l] = 0;
+  const long long nseg = (T + every - 1) / every;
+  for (long long sgi = nseg - 1; sgi >= 0; --sgi) {
+    const long long start = sgi * every;
+    const int len = (int)std::min<long long>(every, T - start);
+    TRY(restore(g, g->rec_ckpt[sgi]));
+    for (int j = 0; j < len; ++j) {
+      TRY(snapshot(g, g->d_seg + sl * j));
+      TRY(advance(g, 0));
+    }
+    for (int j = len - 1; j >= 0; --j) {
+      TRY(restore(g, g->d_seg + sl * j));
+      g->tape_on = 1;
+      g->tape_call = 0;
+      const lsb_status st = advance(g, 0);
+      g->tape_on = 0;
+      TRY(st);
+      TRY(adj_amr(g, 0, 0, G));
+    }
+  }
   return LSB_OK;
 }
 
@@ -1363,7 +1513,7 @@ lsb_status lsb_get_fields(lsb_grid *g, int case_idx, int field, int level, void 
       break;
     case LSB_FIELD_ADJ_F:
       if (g->adj_cur < 0) return fail(g, LSB_ESTATE, "no adjoint field: call lsb_backward first");
-      src = g->d_adj[g->adj_cur] + L.cell_off * g->Q;
+      src = g->d_adj[g->apar[L.level]] + L.cell_off * g->Q;
       planes = g->Q;
       plane_stride = L.ncell;
       break;
@@ -1520,12 +1670,16 @@ int lsb_kernel_count(void) { return NKERN; }
 
 lsb_status lsb_record(lsb_grid *g, int checkpoint_every) {
   if (!g || checkpoint_every < 1) return LSB_EINVAL;
-  if (g->Lmax != 1) return fail(g, LSB_ESTATE, "the adjoint covers single-level grids");
   if (g->storage != LSB_FP32) return fail(g, LSB_ESTATE, "the adjoint needs FP32 population storage");
   int live = 0;
   for (const CaseHost &c : g->cases) live += c.p.ls_active ? 1 : 0;
   if (live != 0 && live != g->ncase)
     return fail(g, LSB_ESTATE, "the adjoint needs the level set live in every case or frozen in every case");
+  if (g->Lmax > 1) {
+    if (live) return fail(g, LSB_ESTATE, "the moving-interface adjoint covers single-level grids");
+    for (const CaseHost &c : g->cases)
+      if (c.L != g->Lmax) return fail(g, LSB_ESTATE, "a multi-level recording needs the same levels in every case");
+  }
   if (live && (g->reinit_every > 1 || g->n_reinit > 1))
     return fail(g, LSB_ESTATE, "the moving-interface adjoint needs reinit_every <= 1 and n_reinit <= 1");
   CU(cudaStreamSynchronize(g->stream));
@@ -1569,10 +1723,18 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
   CU(cudaMemcpyAsync(g->d_wobs, dJ_dobs, sizeof(double) * stride * g->ncase, cudaMemcpyHostToDevice, g->stream));
   // the final state; restored when the sweep is done
   const int par0 = g->par[0];
+  const bool amr = g->Lmax > 1;
+  int par_all[MAXL];
+  long long fs_all[MAXL];
+  for (int l = 0; l < MAXL; ++l) {
+    par_all[l] = g->par[l];
+    fs_all[l] = g->fine_steps[l];
+  }
   void *const bufs[2] = {g->d_buf[0], g->d_buf[1]};
   const long long fs0 = g->fine_steps[0], cs0 = g->coarse_steps;
   const double ud0 = g->updates_done;
-  CU(cudaMemcpyAsync(g->d_fsave, g->d_buf[par0], sb, cudaMemcpyDeviceToDevice, g->stream));
+  if (amr) TRY(snapshot(g, g->d_fsave));
+  else CU(cudaMemcpyAsync(g->d_fsave, g->d_buf[par0], sb, cudaMemcpyDeviceToDevice, g->stream));
   if (mv) {
     CU(cudaMemsetAsync(g->d_gn, 0, sizeof(float) * D * NF, g->stream));
     CU(cudaMemsetAsync(g->d_gk, 0, sizeof(float) * NF, g->stream));
@@ -1589,7 +1751,8 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
       S, (const int *)g->leaf.d, g->leaf.n, (const float *)g->d_fsave, g->d_adj[0], g->d_wobs, g->d_obs, stride);
   int cur = 0;
   lsb_status st = LSB_OK;
-  const long long nseg = (T + every - 1) / every;
+  const long long nseg = amr ? 0 : (T + every - 1) / every;
+  if (amr) st = backward_amr(g, G);
   for (long long sgi = nseg - 1; sgi >= 0 && st == LSB_OK; --sgi) {
     const long long start = sgi * every;
     const int len = (int)std::min<long long>(every, T - start);
@@ -1631,7 +1794,15 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
   g->fine_steps[0] = fs0;
   g->coarse_steps = cs0;
   g->updates_done = ud0;
-  CU(cudaMemcpyAsync(g->d_buf[par0], g->d_fsave, sb, cudaMemcpyDeviceToDevice, g->stream));
+  if (amr) {
+    for (int l = 0; l < MAXL; ++l) {
+      g->par[l] = par_all[l];
+      g->fine_steps[l] = fs_all[l];
+    }
+    TRY(restore(g, g->d_fsave));
+  } else {
+    CU(cudaMemcpyAsync(g->d_buf[par0], g->d_fsave, sb, cudaMemcpyDeviceToDevice, g->stream));
+  }
   if (mv) {
     CU(cudaMemcpyAsync(g->d_phi, g->d_phisave, sizeof(float) * NF, cudaMemcpyDeviceToDevice, g->stream));
     CU(cudaMemcpyAsync(g->d_ut[0], g->d_utsave, sizeof(float) * D * NF, cudaMemcpyDeviceToDevice, g->stream));
@@ -1645,7 +1816,7 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
     } else {
       // normal and curvature adjoints through the least-squares fit, then the dense boxes
       Ctx C2 = make_ctx(g);
-      RUN(KADJ_GEOM, 0, 1, 128, run_adj_geometry, D, LN(g, DYN_GRID, 128), C2, 0, G);
+      RUN(KADJ_GEOM, 0, 1, 128, run_adj_geometry, D, LN(g, DYN_GRID, 128), C2, g->Lmax - 1, G);
     }
     size_t off = 0;
     for (int c = 0; c < g->ncase; ++c) {
@@ -1664,6 +1835,7 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
   CU(cudaMemcpyAsync(h.data(), g->d_grad, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g->stream));
   TRY(lsb_sync(g));
   g->adj_cur = cur;
+  if (!amr) g->apar[0] = cur;
   if (dJ_dparams) {
     for (int c = 0; c < g->ncase; ++c) {
       const lsb_params &p = g->cases[c].p;
@@ -1671,11 +1843,10 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
       double *o = dJ_dparams + (size_t)LSB_NPARAM_ADJ * c;
       o[0] = gr[0];
       for (int ph = 0; ph < 2; ++ph) {
-        const double om = 1.0 / (3.0 * p.nu[ph] + 0.5);
         double dacc = 0.0;
         for (int a = 0; a < D; ++a) dacc += gr[7 + 3 * ph + a] * (-p.body_force[a] / (p.rho[ph] * p.rho[ph]));
         o[1 + ph] = gr[1 + ph] + gr[3 + ph] * p.nu[ph] + dacc;
-        o[3 + ph] = gr[3 + ph] * p.rho[ph] + gr[5 + ph] * (-3.0 * om * om);
+        o[3 + ph] = gr[3 + ph] * p.rho[ph] + gr[5 + ph];
       }
     }
   }
@@ -1716,6 +1887,8 @@ void lsb_destroy(lsb_grid *g) {
   if (g->d_lsa) cudaFree(g->d_lsa);
   if (g->d_seg) cudaFree(g->d_seg);
   for (float *p : g->rec_ckpt) cudaFree(p);
+  for (float *p : g->tape_old) cudaFree(p);
+  for (float *p : g->tape_new) cudaFree(p);
   for (ProfRec &r : g->prof) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);

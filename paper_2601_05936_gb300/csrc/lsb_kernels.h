@@ -71,6 +71,15 @@ cudaError_t run_adj_collide(int Q, Launch L, Ctx C, BlockShape S, const int *lis
                             const float *lamN, float *lamO, const float *LA, double *grad);
 cudaError_t run_adj_macro(int Q, Launch L, Ctx C, int glevel, const float *F, float *lamO, float *MA, double *grad,
                           int ncase);
+// Multi-level grids: transposes of the ghost-ring transfer (per ghost cell of a
+// fine level, coarse states at t and t + 1 blended by theta), of its coarse
+// share's hand-over after the coarse sub-step, and of the restriction (per
+// restriction-layer cell of a coarse level).
+cudaError_t run_adj_ghost(int Q, Launch L, Ctx C, const int2 *cells, int n, float theta, const float *Fold,
+                          const float *Fnew, const float *lamNf, float *lamX, float *lamNc, double *grad, int ncase);
+cudaError_t run_adj_ghost_apply(int Q, Launch L, Ctx C, const int2 *cells, int n, float *lamX, float *lamOc);
+cudaError_t run_adj_restrict(int Q, Launch L, Ctx C, const int2 *cells, int n, const float *Ff, float *lamOc,
+                             float *lamF, double *grad, int ncase);
 
 // lsb_adj_ls.cu: adjoint of the level-set passes of a step with a moving interface
 cudaError_t run_lsa_init(int Q, Launch L, Ctx C, int glevel, const float *F, float *U0);

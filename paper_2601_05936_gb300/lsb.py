@@ -322,7 +322,8 @@ class Grid:
         return int(self.lib.lsb_kernel_launches(self.h))
 
     def record(self, checkpoint_every=100):
-        """Start recording the following steps for backward (frozen level set, one level, FP32)."""
+        """Start recording the following steps for backward (FP32; frozen level set on any number of
+        levels, or a moving level set on one level)."""
         self._check(self.lib.lsb_record(self.h, int(checkpoint_every)))
 
     def backward(self, dJ_dobs, want_phi=False):
