@@ -147,15 +147,17 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def adjoint_bench(args, world, rank, local, barrier, dist, moving=False):
-    """Reverse sweep of the frozen-interface adjoint: single-level 128x128x256 D3Q19
-    box with the bubble of the benchmark workload (d = 32 cells, density ratio
-    1000), level set frozen.  A step of the metric is one adjoint step of the
-    sweep: recomputation of the forward step from the segment checkpoint, the
-    segment-store copy, the cut-link and the per-cell adjoint kernels."""
+def adjoint_bench(args, world, rank, local, barrier, dist, moving=False, levels=1):
+    """Reverse sweep of the adjoint: 128x128x256 D3Q19 box with the bubble of the
+    benchmark workload (d = 32 finest cells, density ratio 1000), single-level
+    (level set frozen or moving) or the benchmark's two-level grid (frozen).  A
+    step of the metric is one adjoint step of the sweep: recomputation of the
+    forward step from the segment checkpoint, the segment-store copy (on two
+    levels also the replay of the step with its per-call record), the cut-link,
+    per-cell and level-transfer adjoint kernels."""
     import torch
     from paper_2601_05936_gb300 import autograd, lsb, workloads
-    case = workloads.rising_bubble_3d(levels=1)
+    case = workloads.rising_bubble_3d(levels=levels)
     if moving:  # level set live: the sweep also replays and transposes the level-set passes
         case.update(regrid_every=0)
     else:
@@ -226,17 +228,19 @@ def adjoint_bench(args, world, rank, local, barrier, dist, moving=False):
                note="autograd.window(E steps) + torch.autograd.grad per window, host wall clock: "
                     "forward recorded steps and the reverse sweep, MLUPS of one adjoint step each")
     g.close()
+    state_mb = sum(float(np.prod([b * 2 ** l for b in case["base"]])) for l in range(levels)) * 19 * 4 / 1e6
     if rank != 0:
         return
     line = dict(metric="MLUPS of the reverse sweep (adjoint cell steps / s), 3D D3Q19 "
-                       + ("moving" if moving else "frozen") + " bubble 128x128x256",
+                       + ("moving" if moving else "frozen") + " bubble 128x128x256"
+                       + (f", {levels} levels" if levels > 1 else ""),
                 value=value, unit="MLUPS", n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f32", data="synthetic",
-                config=dict(workload=case["name"] + ("_moving" if moving else "_frozen"), lattice="D3Q19", levels=1,
+                config=dict(workload=case["name"] + ("_moving" if moving else "_frozen"), lattice="D3Q19", levels=levels,
                             storage="fp32",
                             parallelism=f"replicas{world}", checkpoint_every=args.checkpoint_every,
-                            cells=cells, l2_flush="state 318 MB x (segment store) >> 129 MB L2",
+                            cells=cells, l2_flush=f"state {state_mb:.0f} MB x (segment store) >> 129 MB L2",
                             dJ_dparams=[float(v) for v in dp[0]], forward_ms_per_step=fwd_ms,
                             adjoint_over_forward=(ms_max / args.steps) / fwd_ms),
                 roofline=roof, cpu_baseline=None, e2e=e2e, gpu_launches=launches, clocks=clk)
@@ -253,11 +257,13 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-all", action="store_true", help="print a per-kernel time table to stderr")
-    ap.add_argument("--workload", default="bubble3d", choices=["bubble3d", "box3d", "ensemble", "adjoint3d", "adjoint3d_ls"],
+    ap.add_argument("--workload", default="bubble3d",
+                    choices=["bubble3d", "box3d", "ensemble", "adjoint3d", "adjoint3d_ls", "adjoint3d_amr"],
                     help="bubble3d: the benchmark configuration; box3d: uniform periodic 128^3 box "
                          "(collide-and-stream only, for profiling captures); ensemble: 64 uneven 2D bubbles; "
                          "adjoint3d: reverse sweep over --steps recorded steps of a frozen 3D bubble; "
-                         "adjoint3d_ls: the same with the level set moving (short windows: no phase change)")
+                         "adjoint3d_ls: the same with the level set moving (short windows: no phase change); "
+                         "adjoint3d_amr: the frozen adjoint on the two-level grid of bubble3d")
     ap.add_argument("--checkpoint-every", type=int, default=100)
     ap.add_argument("--driver", type=int, default=0, choices=[0, 1],
                     help="level-set passes: 0 one launch each, 1 one persistent cooperative launch per finest step")
@@ -287,8 +293,9 @@ def main():
     __graft_entry__.build()
     from paper_2601_05936_gb300 import lsb, workloads
 
-    if args.workload in ("adjoint3d", "adjoint3d_ls"):
-        adjoint_bench(args, world, rank, local, barrier, dist, moving=args.workload == "adjoint3d_ls")
+    if args.workload in ("adjoint3d", "adjoint3d_ls", "adjoint3d_amr"):
+        adjoint_bench(args, world, rank, local, barrier, dist, moving=args.workload == "adjoint3d_ls",
+                      levels=2 if args.workload == "adjoint3d_amr" else 1)
         return
     if args.workload == "bubble3d":
         case = workloads.rising_bubble_3d(storage=args.storage, scale=args.scale)

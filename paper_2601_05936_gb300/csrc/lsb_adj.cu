@@ -1093,6 +1093,24 @@ __global__ void k_adj_restrict(Ctx C, const int2 *cells, int n, const float *__r
       if (sg[k] != 0.0) atomicAdd(grad + (long long)(k / 8) * NG_ADJ + 5 + (k % 8), sg[k]);
 }
 
+// ------------------------------------------------------------------ state copies of listed blocks
+// All Q populations of the cells of the listed blocks, from one full-size state
+// array to another (same offsets).  The adjoint's checkpoints, segment store and
+// per-call records hold the cells the step reads (leaves and the covered cells
+// leaves stream from); the rest of the dense level boxes is never read.
+template <int Q>
+__global__ void k_copy_blocks(Ctx C, BlockShape S, const int *list, int n, const float *__restrict__ src,
+                              float *__restrict__ dst) {
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    int x, y, z;
+    const LevelDev &L = blk_cell(C, S, list[w], threadIdx.x, x, y, z);
+    if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
+    const long long c = cidx(L, x, y, z), base = L.cell_off * Q;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dst[base + (long long)i * L.ncell + c] = src[base + (long long)i * L.ncell + c];
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 #define LSB_ADJ_Q(Q, fn, L, ...)                                                      \
   do {                                                                                \
@@ -1125,6 +1143,11 @@ cudaError_t run_adj_collide(int Q, Launch L, Ctx C, BlockShape S, const int *lis
 cudaError_t run_adj_macro(int Q, Launch L, Ctx C, int glevel, const float *F, float *lamO, float *MA, double *grad,
                           int ncase) {
   LSB_ADJ_Q(Q, k_adj_macro, L, C, glevel, F, lamO, MA, grad, ncase);
+}
+
+cudaError_t run_copy_blocks(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, const float *src,
+                            float *dst) {
+  LSB_ADJ_Q(Q, k_copy_blocks, L, C, S, list, n, src, dst);
 }
 
 cudaError_t run_adj_ghost(int Q, Launch L, Ctx C, const int2 *cells, int n, float theta, const float *Fold,

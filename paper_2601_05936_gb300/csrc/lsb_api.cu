@@ -32,7 +32,7 @@ const char *const KNAMES[] = {"k_collide_stream", "k_interface_bc", "k_restrict"
                                "k_levelset_persistent", "k_lsa", "k_adj_ghost", "k_adj_ghost_apply",
                                "k_adj_restrict", "k_tape"};
 constexpr int KADJ_SEED = 24, KADJ_LINKS = 25, KADJ_COLLIDE = 26, KADJ_MACRO = 27, KADJ_GEOM = 28, KLS_PERSIST = 29,
-              KLSA = 30, KADJ_GHOST = 31, KADJ_GAPPLY = 32, KADJ_RESTRICT = 33;
+              KLSA = 30, KADJ_GHOST = 31, KADJ_GAPPLY = 32, KADJ_RESTRICT = 33, KTAPE = 34;
 constexpr int NKERN = sizeof(KNAMES) / sizeof(KNAMES[0]);
 
 struct ProfRec {
@@ -521,13 +521,12 @@ bool ls_active_any(const lsb_grid *g, int l) {
 }
 
 // Copy every case's level-l populations from src to dst (same offsets: each level's
-// region of a Q x ncell_total array).
+// region of a Q x ncell_total array): the cells of the level's leaf blocks and of the
+// covered blocks leaves stream from, the only ones a step reads.
 lsb_status copy_level(lsb_grid *g, float *dst, const float *src, int l) {
-  for (const LevelDev &L : g->lds) {
-    if (L.level != l) continue;
-    const size_t off = (size_t)L.cell_off * g->Q, n = (size_t)L.ncell * g->Q;
-    CU(cudaMemcpyAsync(dst + off, src + off, sizeof(float) * n, cudaMemcpyDeviceToDevice, g->stream));
-  }
+  const WorkList &w = g->cs[l];
+  RUN(KTAPE, 2.0 * sizeof(float) * g->Q * g->nthreads * (double)w.n, w.n, g->nthreads, run_copy_blocks, g->Q,
+      LN(g, std::min(w.n, DYN_GRID), g->nthreads), make_ctx(g), shape(g), (const int *)w.d, w.n, src, dst);
   return LSB_OK;
 }
 
@@ -1096,7 +1095,8 @@ lsb_status adj_amr(lsb_grid *g, int l, int call, GeoAdj G) {
 }
 
 // Reverse sweep over a multi-level recording (frozen level set): segments are
-// recomputed from their checkpoints with every coarse step's start state stored;
+// recomputed from their checkpoints with every coarse step's start state stored
+// (but the last's, whose start is the working state when the recomputation ends);
 // each step is then replayed once more with the tape on and transposed.  The
 // adjoint of the final observables is already in d_adj[0] (every level).
 lsb_status backward_amr(lsb_grid *g, GeoAdj G) {
@@ -1110,12 +1110,13 @@ lsb_status backward_amr(lsb_grid *g, GeoAdj G) {
     const long long start = sgi * every;
     const int len = (int)std::min<long long>(every, T - start);
     TRY(restore(g, g->rec_ckpt[sgi]));
-    for (int j = 0; j < len; ++j) {
+    for (int j = 0; j + 1 < len; ++j) {
       TRY(snapshot(g, g->d_seg + sl * j));
       TRY(advance(g, 0));
     }
+    // the working state is the start of the segment's last step: replayed first, as it is
     for (int j = len - 1; j >= 0; --j) {
-      TRY(restore(g, g->d_seg + sl * j));
+      if (j + 1 < len) TRY(restore(g, g->d_seg + sl * j));
       g->tape_on = 1;
       g->tape_call = 0;
       const lsb_status st = advance(g, 0);

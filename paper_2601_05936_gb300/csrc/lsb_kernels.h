@@ -75,6 +75,8 @@ cudaError_t run_adj_macro(int Q, Launch L, Ctx C, int glevel, const float *F, fl
 // fine level, coarse states at t and t + 1 blended by theta), of its coarse
 // share's hand-over after the coarse sub-step, and of the restriction (per
 // restriction-layer cell of a coarse level).
+cudaError_t run_copy_blocks(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, const float *src,
+                            float *dst);
 cudaError_t run_adj_ghost(int Q, Launch L, Ctx C, const int2 *cells, int n, float theta, const float *Fold,
                           const float *Fnew, const float *lamNf, float *lamX, float *lamNc, double *grad, int ncase);
 cudaError_t run_adj_ghost_apply(int Q, Launch L, Ctx C, const int2 *cells, int n, float *lamX, float *lamOc);
