@@ -20,6 +20,9 @@ from oracle.sim import Sim
 from paper_2601_05936_gb300 import workloads
 
 CASES = [("D2Q9", (48, 24), (8, 8), 4.0), ("D3Q19", (12, 8, 12), (4, 4, 4), 2.0)]
+# refinement distances below a cell: parts of the interface stay on coarse leaves, where a
+# link into the other phase takes plain bounce-back
+CUT_CASES = [("D2Q9", (48, 24), (8, 8), 0.2), ("D3Q19", (12, 8, 12), (4, 4, 4), 0.2)]
 
 
 def _case(lattice, n, block, rd):
@@ -48,7 +51,7 @@ def _dot(A, B):
     return sum(float((a * b).sum()) for a, b in zip(A, B))
 
 
-@pytest.mark.parametrize("lattice,n,block,rd", CASES)
+@pytest.mark.parametrize("lattice,n,block,rd", CASES + CUT_CASES)
 def test_amr_step_is_the_oracle_step(lattice, n, block, rd):
     sim = Sim(_case(lattice, n, block, rd))
     leaf0, _, rl0, _ = sim.masks[0]
@@ -59,6 +62,7 @@ def test_amr_step_is_the_oracle_step(lattice, n, block, rd):
     for _ in range(3):
         F = st.step(F, p)
     sim.step(3)
+    assert (sim.stats["coarse_cut"] > 0) == (rd < 1.0)
     for a, b in zip(F, sim.f):
         assert np.abs(a - b).max() < 1e-14
     obs = sim.observables()
@@ -66,11 +70,12 @@ def test_amr_step_is_the_oracle_step(lattice, n, block, rd):
     D = sim.D
     assert np.allclose(mine[:2], obs["mass"], rtol=1e-14) and mine[2] == obs["volume"]
     assert np.allclose(mine[4:4 + D], obs["centroid"], rtol=1e-14)
-    assert np.allclose(mine[4 + D:], obs["velocity"], rtol=1e-12, atol=1e-18)
+    vel = obs["velocity"]
+    assert np.allclose(mine[4 + D:], vel, rtol=1e-12, atol=1e-12 * np.abs(vel).max())
 
 
 @pytest.mark.parametrize("part", ["all", "coarse", "fine"])
-@pytest.mark.parametrize("lattice,n,block,rd", CASES)
+@pytest.mark.parametrize("lattice,n,block,rd", CASES + CUT_CASES)
 def test_dot_product_identity_one_coarse_step(lattice, n, block, rd, part):
     sim, st, F0, rng = _setup(lattice, n, block, rd)
     p = params_of(sim)
