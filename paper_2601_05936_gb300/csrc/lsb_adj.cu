@@ -436,6 +436,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_collide(Ctx C, BlockShape S, con
       cm = C.cmask[L.fine_off + c];
       cb = C.cbase[L.fine_off + c];
     }
+    const bool ccut = !fine && (tg & TAG_CCUT);
     // lc: adjoint of the post-collision populations.  Held in registers with up to
     // 128 of them per thread (one CTA of 512 per SM): more loads in flight per
     // thread measured faster than two CTAs per SM with lc in shared memory.
@@ -459,7 +460,12 @@ __global__ void __launch_bounds__(512, 1) k_adj_collide(Ctx C, BlockShape S, con
       if (!(wx || wy || wz)) {
         const int off = (cxi < 0 ? dxm : (cxi > 0 ? dxp : 0)) + (cyi < 0 ? dym : (cyi > 0 ? dyp : 0)) +
                         (czi < 0 ? dzm : (czi > 0 ? dzp : 0));
-        LC(i) = lN[i * N + (unsigned)((int)c + off)];
+        const unsigned ct = (unsigned)((int)c + off);
+        LC(i) = lN[i * N + ct];
+        if (ccut) {  // coarser level, neighbour of the other phase: the push bounced back
+          const uint8_t tt = C.tag[L.cell_off + ct];
+          if (!(tt & TAG_GHOST) && ((tt ^ tg) & TAG_GAS)) LC(i) = lN[k * N + c];
+        }
       } else {
         LC(i) = lN[k * N + c];
       }

@@ -100,7 +100,9 @@ enum : uint8_t {
   TAG_PREVGAS = 8,  // phase before the last classification
   TAG_RLAYER = 16,  // covered cell a leaf streams from (fine-to-coarse target)
   TAG_GHOST = 32,   // inactive cell a leaf streams from (coarse-to-fine target)
-  TAG_LEAF = 64     // cell of a leaf block inside the box
+  TAG_LEAF = 64,    // cell of a leaf block inside the box
+  TAG_CCUT = 128    // coarser level: a lattice neighbour (not a ghost cell) has the other phase;
+                    // pushes towards it bounce back into the cell's own opposite population
 };
 
 // per-block flag bits (finest level)

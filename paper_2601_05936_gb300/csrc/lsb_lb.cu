@@ -13,6 +13,7 @@
 #include <cuda.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "lsb_kernels.h"
 
@@ -145,6 +146,7 @@ __global__ void __launch_bounds__(512, LSB_CS_MINB) k_collide_stream(Ctx C, Bloc
       cm = C.cmask[L.fine_off + c];
       cb = C.cbase[L.fine_off + c];
     }
+    const bool ccut = !fine && (tg & TAG_CCUT);
     Store<T>::st(B + (LT::REST * N + c), f[LT::REST], C.fp16_scale);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -165,7 +167,15 @@ __global__ void __launch_bounds__(512, LSB_CS_MINB) k_collide_stream(Ctx C, Bloc
       if (!(wx || wy || wz)) {
         const int off = (cxi < 0 ? dxm : (cxi > 0 ? dxp : 0)) + (cyi < 0 ? dym : (cyi > 0 ? dyp : 0)) +
                         (czi < 0 ? dzm : (czi > 0 ? dzp : 0));
-        Store<T>::st(B + (i * N + (unsigned)((int)c + off)), f[i], C.fp16_scale);
+        const unsigned ct = (unsigned)((int)c + off);
+        if (ccut) {  // coarser level, neighbour of the other phase: plain bounce-back
+          const uint8_t tt = C.tag[L.cell_off + ct];
+          if (!(tt & TAG_GHOST) && ((tt ^ tg) & TAG_GAS)) {
+            Store<T>::st(B + (k * N + c), f[i], C.fp16_scale);
+            continue;
+          }
+        }
+        Store<T>::st(B + (i * N + ct), f[i], C.fp16_scale);
       } else {
         // half-way bounce-back with the moving-wall term, i pointing at the wall
         const int face = wx ? (cxi < 0 ? 0 : 1) : (wy ? (cyi < 0 ? 2 : 3) : (czi < 0 ? 4 : 5));
@@ -352,33 +362,47 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
         cb = C.cbase[m.fine_off + c];
       }
       Store<T>::st(B + (LT::REST * N + c), f[LT::REST], C.fp16_scale);
+      // cells next to the other phase on a coarser level take a checking copy of the loop
+      auto push = [&](auto check) {
+        constexpr bool CHECK = decltype(check)::value;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        if (i == LT::REST) continue;
-        const int cxi = LT::cx(i), cyi = LT::cy(i), czi = LT::cz(i);
-        const int k = LT::opp(i);
-        if (cm & (1u << k)) {
-          const long long li = cb + __popc(cm & ((1u << k) - 1u));
-          if (li < C.link_cap) {
-            C.linkbuf[2 * li] = f[i];
-            C.linkbuf[2 * li + 1] = f[k];
+        for (int i = 0; i < Q; ++i) {
+          if (i == LT::REST) continue;
+          const int cxi = LT::cx(i), cyi = LT::cy(i), czi = LT::cz(i);
+          const int k = LT::opp(i);
+          if (cm & (1u << k)) {
+            const long long li = cb + __popc(cm & ((1u << k) - 1u));
+            if (li < C.link_cap) {
+              C.linkbuf[2 * li] = f[i];
+              C.linkbuf[2 * li + 1] = f[k];
+            }
+            continue;
           }
-          continue;
+          const bool wx = (cxi < 0 && wxm) || (cxi > 0 && wxp);
+          const bool wy = (cyi < 0 && wym) || (cyi > 0 && wyp);
+          const bool wz = (czi < 0 && wzm) || (czi > 0 && wzp);
+          if (!(wx || wy || wz)) {
+            const int off = (cxi < 0 ? dxm : (cxi > 0 ? dxp : 0)) + (cyi < 0 ? dym : (cyi > 0 ? dyp : 0)) +
+                            (czi < 0 ? dzm : (czi > 0 ? dzp : 0));
+            const unsigned ct = (unsigned)((int)c + off);
+            if constexpr (CHECK) {  // coarser level, neighbour of the other phase: plain bounce-back
+              const uint8_t tt = C.tag[m.cell_off + ct];
+              if (!(tt & TAG_GHOST) && ((tt ^ tg) & TAG_GAS)) {
+                Store<T>::st(B + (k * N + c), f[i], C.fp16_scale);
+                continue;
+              }
+            }
+            Store<T>::st(B + (i * N + ct), f[i], C.fp16_scale);
+          } else {
+            const int face = wx ? (cxi < 0 ? 0 : 1) : (wy ? (cyi < 0 ? 2 : 3) : (czi < 0 ? 4 : 5));
+            const float *uw = C.lds[m.ld].wall_u[face];
+            const float du = cxi * uw[0] + cyi * uw[1] + czi * uw[2];
+            Store<T>::st(B + (k * N + c), f[i] - 6.0f * LT::w(i) * du, C.fp16_scale);
+          }
         }
-        const bool wx = (cxi < 0 && wxm) || (cxi > 0 && wxp);
-        const bool wy = (cyi < 0 && wym) || (cyi > 0 && wyp);
-        const bool wz = (czi < 0 && wzm) || (czi > 0 && wzp);
-        if (!(wx || wy || wz)) {
-          const int off = (cxi < 0 ? dxm : (cxi > 0 ? dxp : 0)) + (cyi < 0 ? dym : (cyi > 0 ? dyp : 0)) +
-                          (czi < 0 ? dzm : (czi > 0 ? dzp : 0));
-          Store<T>::st(B + (i * N + (unsigned)((int)c + off)), f[i], C.fp16_scale);
-        } else {
-          const int face = wx ? (cxi < 0 ? 0 : 1) : (wy ? (cyi < 0 ? 2 : 3) : (czi < 0 ? 4 : 5));
-          const float *uw = C.lds[m.ld].wall_u[face];
-          const float du = cxi * uw[0] + cyi * uw[1] + czi * uw[2];
-          Store<T>::st(B + (k * N + c), f[i] - 6.0f * LT::w(i) * du, C.fp16_scale);
-        }
-      }
+      };
+      if (!m.finest && (tg & TAG_CCUT)) push(std::true_type{});
+      else push(std::false_type{});
     } while (false);
     __syncthreads();  // stage st and meta[st] are refilled one iteration from now
   }
@@ -646,16 +670,24 @@ __global__ void k_level_tags(Ctx C, BlockShape S, const int *list, int nlist) {
     const long long cf = cidx(Fn, x * L.scale, y * L.scale, z * L.scale);
     uint8_t tg = (C.phi[Fn.fine_off + cf] >= 0.0f) ? TAG_GAS : 0;
     const int8_t st = C.bstat[gb];
-    bool near_leaf = false;
+    bool near_leaf = false, ccut = false;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if (i == LT::REST) continue;
       int tx = x + LT::cx(i), ty = y + LT::cy(i), tz = z + LT::cz(i);
       if (!(wrap(L, 0, tx) && wrap(L, 1, ty) && (D == 2 || wrap(L, 2, tz)))) continue;
-      if (C.bstat[L.block_off + block_of(L, tx, ty, tz, S)] == BLK_LEAF) near_leaf = true;
+      const int8_t sb = C.bstat[L.block_off + block_of(L, tx, ty, tz, S)];
+      if (sb == BLK_LEAF) near_leaf = true;
+      // coarser levels: a neighbour of the other phase that is not a ghost cell (the
+      // inactive neighbours of leaves are their ghost ring; a covered cell's are active)
+      if (!L.finest && sb != BLK_INACTIVE) {
+        const long long ct = cidx(Fn, tx * L.scale, ty * L.scale, tz * L.scale);
+        if ((C.phi[Fn.fine_off + ct] >= 0.0f) != ((tg & TAG_GAS) != 0)) ccut = true;
+      }
     }
     if (st == BLK_LEAF) tg |= TAG_LEAF;
     if (st == BLK_REFINED && near_leaf) tg |= TAG_RLAYER;
+    if (ccut && (tg & (TAG_LEAF | TAG_RLAYER))) tg |= TAG_CCUT;
     if (st == BLK_INACTIVE && near_leaf) tg |= TAG_GHOST;
     if (tg & TAG_GAS) tg |= TAG_PREVGAS;
     C.tag[L.cell_off + c] = tg;

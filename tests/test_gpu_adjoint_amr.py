@@ -17,7 +17,9 @@ from gpu_util import as_fp32_phi, rel_l2
 
 pytestmark = pytest.mark.gpu
 
-CASES = [("D2Q9", (48, 24), (8, 8), 4.0, 6, 10), ("D3Q19", (12, 8, 12), (4, 4, 4), 2.0, 4, 6)]
+CASES = [("D2Q9", (48, 24), (8, 8), 4.0, 6, 10), ("D3Q19", (12, 8, 12), (4, 4, 4), 2.0, 4, 6),
+         # refinement distance below a cell: coarse leaves meet the other phase (plain bounce-back)
+         ("D2Q9", (48, 24), (8, 8), 0.2, 6, 10), ("D3Q19", (12, 8, 12), (4, 4, 4), 0.2, 4, 6)]
 
 
 def _case(lattice, n, block, rd):

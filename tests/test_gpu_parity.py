@@ -102,6 +102,21 @@ def test_two_level_bubble_parity():
         assert np.array_equal(g.get("blocks", 0, l), s.status[l]), l
 
 
+@pytest.mark.parametrize("lattice,n,block", [("D2Q9", (48, 24), (8, 8)), ("D3Q19", (12, 8, 12), (4, 4, 4))])
+def test_two_level_coarse_cut_links_parity(lattice, n, block):
+    """Interface partly on coarse leaves (refinement distance below a cell): a link into
+    the other phase on a coarser level takes plain bounce-back, as in the oracle."""
+    from paper_2601_05936_gb300 import workloads
+    case = workloads.adjoint_window(lattice, n=n, levels=2, block=block, refine_dist=0.2)
+    g, s = run_both(case, 12)
+    assert s.stats["coarse_cut"] > 0
+    for r in compare_levels(g, s):
+        assert r["leaf_equal"], r
+        assert r["u"] < 1e-4 and r["drho_abs"] < 1e-5, r
+    tag0 = g.get("tag", 0, 0).reshape(-1)
+    assert ((tag0 & 128) != 0).any()
+
+
 def test_cut_masks_bit_exact_on_random_level_sets():
     from oracle.sim import Sim
     from paper_2601_05936_gb300 import lsb
