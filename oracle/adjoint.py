@@ -101,16 +101,25 @@ class FrozenStep:
         self.kA = sgn * ((1 - q) * kap[x] + q * kap[y])
         self.ci = lat.cf[i].T
         cells = np.arange(g.N)
-        self.src = [g.shift(cells, -lat.c[kk]) for kk in range(lat.Q)]
+        # pull sources: (src, face, direction at the source), reflected at slip walls
+        self.src = []
+        for kk in range(lat.Q):
+            src, face, flip = g.pull(cells, lat.c[kk])
+            self.src.append((src, face, lat.mirror[kk, flip]))
         self.cut = np.zeros((lat.Q, g.N), dtype=bool)
         self.cut[k, x] = True
         # leaves whose source x - c_k is a ghost-ring cell (none on a single level)
         self.from_ghost = np.zeros((lat.Q, g.N), dtype=bool)
+        # links reflected at a slip wall whose source lies in the other phase: plain bounce-back
+        self.rcut = np.zeros((lat.Q, g.N), dtype=bool)
         for kk in range(lat.Q):
-            src = self.src[kk][0]
+            src, _, ks = self.src[kk]
             ok = (src >= 0) & self.leaf
             ok[ok] = self.ghostm[src[ok]]
             self.from_ghost[kk] = ok
+            r = (src >= 0) & self.leaf & (ks != kk) & ~ok
+            r[r] = self.phase[src[r]] != self.phase[r]
+            self.rcut[kk] = r
         self.gas = self.leaf & (self.phase == 1)
         self.centers = g.centers(1.0)
 
@@ -157,13 +166,15 @@ class FrozenStep:
         fn = f.copy()
         for k in range(lat.Q):
             i = lat.opp[k]
-            src, face = self.src[k]
+            src, face, ks = self.src[k]
             wall = (src < 0) & self.leaf
-            fg = self.from_ghost[k]
-            same = (src >= 0) & ~self.cut[k] & self.leaf & ~fg
-            fn[k, same] = fc[k, src[same]]
+            fg, rc = self.from_ghost[k], self.rcut[k]
+            same = (src >= 0) & ~self.cut[k] & self.leaf & ~fg & ~rc
+            fn[k, same] = fc[ks[same], src[same]]
             if fg.any():
-                fn[k, fg] = gh[k, src[fg]]
+                fn[k, fg] = gh[ks[fg], src[fg]]
+            if rc.any():
+                fn[k, rc] = fc[i, rc]
             if wall.any():
                 fn[k, wall] = fc[i, wall] - (2 * lat.w[i] / CS2) * (self.wall_u[face[wall]] @ lat.cf[i])
         P = self._link_pieces(rho, u, S, p)
@@ -217,12 +228,13 @@ class FrozenStep:
         lc = np.zeros_like(f)
         for k in range(Q):
             i = lat.opp[k]
-            src, _ = self.src[k]
-            fg = self.from_ghost[k]
-            same = (src >= 0) & ~self.cut[k] & self.leaf & ~fg
-            np.add.at(lc[k], src[same], lam_next[k, same])
+            src, _, ks = self.src[k]
+            fg, rc = self.from_ghost[k], self.rcut[k]
+            same = (src >= 0) & ~self.cut[k] & self.leaf & ~fg & ~rc
+            np.add.at(lc, (ks[same], src[same]), lam_next[k, same])
             if fg.any():
-                np.add.at(lam_gh[k], src[fg], lam_next[k, fg])
+                np.add.at(lam_gh, (ks[fg], src[fg]), lam_next[k, fg])
+            lc[i, rc] += lam_next[k, rc]
             wall = (src < 0) & self.leaf
             lc[i, wall] += lam_next[k, wall]
         # ---- cut links: transpose of Eq. bb

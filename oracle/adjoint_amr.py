@@ -132,12 +132,12 @@ class CoarseLevel:
         cells = np.arange(g.N)
         self.src, self.same, self.fg, self.cut, self.wall = [], [], [], [], []
         for k in range(lat.Q):
-            src, face = g.shift(cells, -lat.c[k])
+            src, face, flip = g.pull(cells, lat.c[k])  # reflected at slip walls
             ok = (src >= 0) & self.leaf
             s = np.where(ok, src, 0)
             fg = ok & self.ghostm[s]
             cut = ok & ~fg & (self.phase[s] != self.phase) & (k != lat.rest)
-            self.src.append((src, face))
+            self.src.append((src, face, lat.mirror[k, flip]))
             self.fg.append(fg)
             self.cut.append(cut)
             self.same.append(ok & ~fg & ~cut)
@@ -158,11 +158,11 @@ class CoarseLevel:
         fn = f.copy()
         for k in range(lat.Q):
             i = lat.opp[k]
-            src, face = self.src[k]
+            src, face, ks = self.src[k]
             same, fg, cut, wall = self.same[k], self.fg[k], self.cut[k], self.wall[k]
-            fn[k, same] = fc[k, src[same]]
+            fn[k, same] = fc[ks[same], src[same]]
             if fg.any():
-                fn[k, fg] = gh[k, src[fg]]
+                fn[k, fg] = gh[ks[fg], src[fg]]
             if cut.any():
                 fn[k, cut] = fc[i, cut]
             if wall.any():
@@ -176,10 +176,10 @@ class CoarseLevel:
         lc = np.zeros_like(f)
         for k in range(lat.Q):
             i = lat.opp[k]
-            src, _ = self.src[k]
+            src, _, ks = self.src[k]
             same, fg, cut, wall = self.same[k], self.fg[k], self.cut[k], self.wall[k]
-            np.add.at(lc[k], src[same], lam_next[k, same])
-            np.add.at(lam_gh[k], src[fg], lam_next[k, fg])
+            np.add.at(lc, (ks[same], src[same]), lam_next[k, same])
+            np.add.at(lam_gh, (ks[fg], src[fg]), lam_next[k, fg])
             lc[i, cut] += lam_next[k, cut]
             lc[i, wall] += lam_next[k, wall]
         c = self.coll

@@ -25,6 +25,13 @@ class Lattice:
         )
         self.rest = int(np.flatnonzero((self.c == 0).all(1))[0])
         self.norm = np.sqrt((self.cf ** 2).sum(1))
+        # mirror[i, m]: the velocity c_i with the components of the axes in bit mask m negated
+        # (specular reflection at slip walls normal to those axes)
+        self.mirror = np.zeros((self.Q, 2 ** self.D), dtype=np.int64)
+        for i in range(self.Q):
+            for m in range(2 ** self.D):
+                sgn = np.array([-1 if (m >> a) & 1 else 1 for a in range(self.D)])
+                self.mirror[i, m] = int(np.flatnonzero((self.c == sgn * self.c[i]).all(1))[0])
 
 
 _D2 = [(-1, 0), (1, 0), (0, -1), (0, 1), (-1, -1), (-1, 1), (1, 1), (1, -1), (0, 0)]

@@ -31,7 +31,7 @@ from .lbm import collide, equilibrium, moments, omega_from_nu, strain_rate
 DEFAULTS = dict(
     n_levels=1, sigma=0.0, body_force=None, gravity=None, x_ref=None, wall_u=None, p_gas0=0.0,
     n_ext=8, dtau_ext=0.5, reinit_every=1, n_reinit=1, dtau_reinit=0.3,
-    refine_dist=None, sensor="band", regrid_every=0, ls_active=True,
+    refine_dist=None, sensor="band", regrid_every=0, ls_active=True, slip=None,
 )
 
 
@@ -49,7 +49,8 @@ class Sim:
         self.L = int(c["n_levels"])
         base = tuple(int(b) for b in c["base"])
         self.periodic = tuple(bool(p) for p in c["periodic"])
-        self.geoms = [LevelGeom(tuple(b * 2 ** l for b in base), self.periodic, c["block"])
+        self.slip = tuple(bool(s) for s in (c["slip"] or (False,) * D))
+        self.geoms = [LevelGeom(tuple(b * 2 ** l for b in base), self.periodic, c["block"], self.slip)
                       for l in range(self.L)]
         gF = self.geoms[-1]
         self.rho_phys = np.asarray(c["rho_phys"], dtype=np.float64)
@@ -178,7 +179,7 @@ class Sim:
         gh = self.ghost[l]
         for k in range(lat.Q):
             i = lat.opp[k]
-            src, face = g.shift(cells, -lat.c[k])
+            src, face, flip = g.pull(cells, lat.c[k])
             wall = src < 0
             val = np.empty(len(cells))
             if wall.any():
@@ -187,12 +188,18 @@ class Sim:
                 val[wall] = fc[i, cells[wall]] - (2.0 * lat.w[i] / CS2) * du
             inn = ~wall
             s = src[inn]
+            ks = lat.mirror[k, flip[inn]]  # the population's direction at its source
             from_ghost = ghost[s]
-            v = fc[k, s]
+            v = fc[ks, s]
             if gh is not None:
-                v = np.where(from_ghost, gh[k, s], v)
+                v = np.where(from_ghost, gh[ks, s], v)
             if k != lat.rest:
                 cut = (~from_ghost) & (ph[s] != ph[cells[inn]])
+                refl = cut & (flip[inn] != 0)  # reflected at a slip wall into the other phase
+                if refl.any():
+                    v = v.copy()
+                    v[refl] = fc[i, cells[inn][refl]]
+                    cut &= ~refl
                 if cut.any():
                     if finest:
                         v = v.copy()
