@@ -48,7 +48,13 @@ typedef enum {
 } lsb_status;
 
 enum { LSB_D2Q9 = 0, LSB_D3Q19 = 1 };           /* velocity sets, Sec. 2.1 / Fig. 1 */
-enum { LSB_PERIODIC = 0, LSB_WALL = 1 };        /* per-axis boundary kind */
+/* per-axis boundary kind: periodic, no-slip wall (half-way bounce-back, Eq. bb
+ * with q = 1/2, plus the moving-wall term) or slip wall (specular reflection: a
+ * population leaving through the wall returns with its normal component negated,
+ * moved on tangentially; the lateral walls of the paper's 3D benchmark, Sec. 3.2).
+ * Where a link crosses a slip and a no-slip wall the no-slip bounce-back applies;
+ * a reflected link into the other phase takes plain bounce-back. */
+enum { LSB_PERIODIC = 0, LSB_WALL = 1, LSB_SLIP = 2 };
 enum { LSB_FP32 = 0, LSB_FP16S = 1 };           /* population storage */
 enum { LSB_SENSOR_BAND = 0, LSB_SENSOR_SIGNED = 1 }; /* refinement sensor, Sec. 2.6, 3.2.2 */
 
@@ -80,7 +86,7 @@ typedef struct {
   int n_levels;         /* total levels including the base (1 = uniform), <= 4       */
   int block[3];         /* block edge in cells, powers of two, same on every level;
                            their product is a multiple of 32 and at most 512        */
-  int bc[3];            /* per axis: LSB_PERIODIC or LSB_WALL (walls on cell faces)  */
+  int bc[3];            /* per axis: LSB_PERIODIC, LSB_WALL or LSB_SLIP (walls on cell faces) */
   double wall_u[6][3];  /* velocity of faces x-, x+, y-, y+, z-, z+                  */
   int storage;          /* LSB_FP32 or LSB_FP16S; all cases of a handle share it     */
   double fp16_scale;    /* LSB_FP16S: populations stored as (f - w) * scale, a power

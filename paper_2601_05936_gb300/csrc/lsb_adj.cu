@@ -466,8 +466,16 @@ __global__ void __launch_bounds__(512, 1) k_adj_collide(Ctx C, BlockShape S, con
           const uint8_t tt = C.tag[L.cell_off + ct];
           if (!(tt & TAG_GHOST) && ((tt ^ tg) & TAG_GAS)) LC(i) = lN[k * N + c];
         }
-      } else {
-        LC(i) = lN[k * N + c];
+      } else if ((wx && !L.slip[0]) || (wy && !L.slip[1]) || (wz && !L.slip[2])) {
+        LC(i) = lN[k * N + c];  // no-slip bounce-back
+      } else {  // slip walls: the reflected push (into the other phase: bounce-back)
+        const int off = (wx ? 0 : (cxi < 0 ? dxm : (cxi > 0 ? dxp : 0))) +
+                        (wy ? 0 : (cyi < 0 ? dym : (cyi > 0 ? dyp : 0))) +
+                        (wz ? 0 : (czi < 0 ? dzm : (czi > 0 ? dzp : 0)));
+        const unsigned ct = (unsigned)((int)c + off);
+        const uint8_t tt = C.tag[L.cell_off + ct];
+        if (!(tt & TAG_GHOST) && ((tt ^ tg) & TAG_GAS)) LC(i) = lN[k * N + c];
+        else LC(i) = lN[mirror_dir<Q>(i, (wx ? 1 : 0) | (wy ? 2 : 0) | (wz ? 4 : 0)) * N + ct];
       }
     }
     if (cm) {
@@ -897,11 +905,23 @@ __global__ void k_adj_ghost(Ctx C, const int2 *cells, int n, float theta, const 
     for (int i = 0; i < Q; ++i) {
       lg[i] = 0.f;
       if (i == LT::REST) continue;
-      int tx = x + LT::cx(i), ty = y + LT::cy(i), tz = z + LT::cz(i);
-      if (!(wrap(F, 0, tx) && wrap(F, 1, ty) && (D == 2 || wrap(F, 2, tz)))) continue;
-      const long long ct = cidx(F, tx, ty, tz);
+      int t[3] = {x + LT::cx(i), y + LT::cy(i), z + LT::cz(i)};  // as the forward push: mirrored
+      const int o[3] = {x, y, z};                                 // through slip walls
+      int mm = 0;
+      bool ok = true;
+      for (int a = 0; a < D; ++a)
+        if (!wrap(F, a, t[a])) {
+          if (F.slip[a]) {
+            t[a] = o[a];
+            mm |= 1 << a;
+          } else {
+            ok = false;
+          }
+        }
+      if (!ok) continue;
+      const long long ct = cidx(F, t[0], t[1], t[2]);
       if (!(C.tag[F.cell_off + ct] & TAG_LEAF)) continue;
-      lg[i] = lamNf[F.cell_off * Q + (long long)i * F.ncell + ct];
+      lg[i] = lamNf[F.cell_off * Q + (long long)mirror_dir<Q>(i, mm) * F.ncell + ct];
       any |= lg[i] != 0.f;
     }
     if (!any) continue;

@@ -1156,7 +1156,8 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
     if (d.n_levels < 1 || d.n_levels > MAXL) return fail(nullptr, LSB_EINVAL, "n_levels must be 1..%d", MAXL);
     for (int a = 0; a < D; ++a) {
       if (d.base[a] < 1) return fail(nullptr, LSB_EINVAL, "base must be positive");
-      if (d.bc[a] != LSB_PERIODIC && d.bc[a] != LSB_WALL) return fail(nullptr, LSB_EINVAL, "bad bc");
+      if (d.bc[a] != LSB_PERIODIC && d.bc[a] != LSB_WALL && d.bc[a] != LSB_SLIP)
+        return fail(nullptr, LSB_EINVAL, "bad bc");
     }
     std::string why;
     if (check_params(params[c], d, why)) return fail(nullptr, LSB_EINVAL, "case %d: %s", c, why.c_str());
@@ -1205,6 +1206,7 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
         L.p[a] = ((L.n[a] + bs[a] - 1) / bs[a]) * bs[a];
         L.nb[a] = L.p[a] / bs[a];
         L.per[a] = a < D ? (descs[c].bc[a] == LSB_PERIODIC) : 1;
+        L.slip[a] = a < D && descs[c].bc[a] == LSB_SLIP;
         L.ncell *= L.p[a];
       }
       L.nblock = L.nb[0] * L.nb[1] * L.nb[2];

@@ -61,6 +61,21 @@ template <> struct Lat<19> {
   }
 };
 
+// The direction c_i with the components of the axes in bit mask m negated: the
+// direction a population leaves a slip wall with (specular reflection).
+template <int Q>
+__host__ __device__ __forceinline__ int mirror_dir(int i, int m) {
+  using LT = Lat<Q>;
+  const int x = (m & 1) ? -LT::cx(i) : LT::cx(i);
+  const int y = (m & 2) ? -LT::cy(i) : LT::cy(i);
+  const int z = (m & 4) ? -LT::cz(i) : LT::cz(i);
+  int r = i;
+#pragma unroll
+  for (int j = 0; j < Q; ++j)
+    if (LT::cx(j) == x && LT::cy(j) == y && LT::cz(j) == z) r = j;
+  return r;
+}
+
 // ---------------------------------------------------------------- moments and equilibrium
 // Eq. macro on deviations f~ = f - w: drho = sum f~, u = sum c f~ / (1 + drho).
 template <int Q>
@@ -116,6 +131,7 @@ struct LevelDev {
   int p[3];        // padded to whole blocks
   int nb[3];       // blocks per axis
   int per[3];      // periodic axis flags
+  int slip[3];     // walled axes with slip walls (specular reflection)
   long long ncell; // p0*p1*p2
   long long cell_off;  // offset in per-cell arrays of all levels (f uses *Q)
   long long fine_off;  // offset in finest-level arrays, -1 if not finest

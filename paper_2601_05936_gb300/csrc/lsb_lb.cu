@@ -177,11 +177,27 @@ __global__ void __launch_bounds__(512, LSB_CS_MINB) k_collide_stream(Ctx C, Bloc
         }
         Store<T>::st(B + (i * N + ct), f[i], C.fp16_scale);
       } else {
-        // half-way bounce-back with the moving-wall term, i pointing at the wall
-        const int face = wx ? (cxi < 0 ? 0 : 1) : (wy ? (cyi < 0 ? 2 : 3) : (czi < 0 ? 4 : 5));
-        const float *uw = L.wall_u[face];
-        const float du = cxi * uw[0] + cyi * uw[1] + czi * uw[2];
-        Store<T>::st(B + (k * N + c), f[i] - 6.0f * LT::w(i) * du, C.fp16_scale);
+        const bool nx = wx && !L.slip[0], ny = wy && !L.slip[1], nz = wz && !L.slip[2];
+        if (__builtin_expect(nx || ny || nz, 1)) {
+          // half-way bounce-back with the moving-wall term, i pointing at the (no-slip) wall
+          const int face = nx ? (cxi < 0 ? 0 : 1) : (ny ? (cyi < 0 ? 2 : 3) : (czi < 0 ? 4 : 5));
+          const float *uw = L.wall_u[face];
+          const float du = cxi * uw[0] + cyi * uw[1] + czi * uw[2];
+          Store<T>::st(B + (k * N + c), f[i] - 6.0f * LT::w(i) * du, C.fp16_scale);
+        } else {
+          // slip walls only: specular reflection, moved on along the other axes; into the
+          // other phase (not a ghost cell) plain bounce-back
+          const int off = (wx ? 0 : (cxi < 0 ? dxm : (cxi > 0 ? dxp : 0))) +
+                          (wy ? 0 : (cyi < 0 ? dym : (cyi > 0 ? dyp : 0))) +
+                          (wz ? 0 : (czi < 0 ? dzm : (czi > 0 ? dzp : 0)));
+          const unsigned ct = (unsigned)((int)c + off);
+          const uint8_t tt = C.tag[L.cell_off + ct];
+          if (!(tt & TAG_GHOST) && ((tt ^ tg) & TAG_GAS))
+            Store<T>::st(B + (k * N + c), f[i], C.fp16_scale);
+          else
+            Store<T>::st(B + (mirror_dir<Q>(i, (wx ? 1 : 0) | (wy ? 2 : 0) | (wz ? 4 : 0)) * N + ct), f[i],
+                         C.fp16_scale);
+        }
       }
     }
   }
@@ -394,10 +410,25 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
             }
             Store<T>::st(B + (i * N + ct), f[i], C.fp16_scale);
           } else {
-            const int face = wx ? (cxi < 0 ? 0 : 1) : (wy ? (cyi < 0 ? 2 : 3) : (czi < 0 ? 4 : 5));
-            const float *uw = C.lds[m.ld].wall_u[face];
-            const float du = cxi * uw[0] + cyi * uw[1] + czi * uw[2];
-            Store<T>::st(B + (k * N + c), f[i] - 6.0f * LT::w(i) * du, C.fp16_scale);
+            const LevelDev &Ld = C.lds[m.ld];
+            const bool nx = wx && !Ld.slip[0], ny = wy && !Ld.slip[1], nz = wz && !Ld.slip[2];
+            if (nx || ny || nz) {  // no-slip: half-way bounce-back with the moving-wall term
+              const int face = nx ? (cxi < 0 ? 0 : 1) : (ny ? (cyi < 0 ? 2 : 3) : (czi < 0 ? 4 : 5));
+              const float *uw = Ld.wall_u[face];
+              const float du = cxi * uw[0] + cyi * uw[1] + czi * uw[2];
+              Store<T>::st(B + (k * N + c), f[i] - 6.0f * LT::w(i) * du, C.fp16_scale);
+            } else {  // slip: specular reflection (into the other phase: plain bounce-back)
+              const int off = (wx ? 0 : (cxi < 0 ? dxm : (cxi > 0 ? dxp : 0))) +
+                              (wy ? 0 : (cyi < 0 ? dym : (cyi > 0 ? dyp : 0))) +
+                              (wz ? 0 : (czi < 0 ? dzm : (czi > 0 ? dzp : 0)));
+              const unsigned ct = (unsigned)((int)c + off);
+              const uint8_t tt = C.tag[m.cell_off + ct];
+              if (!(tt & TAG_GHOST) && ((tt ^ tg) & TAG_GAS))
+                Store<T>::st(B + (k * N + c), f[i], C.fp16_scale);
+              else
+                Store<T>::st(B + (mirror_dir<Q>(i, (wx ? 1 : 0) | (wy ? 2 : 0) | (wz ? 4 : 0)) * N + ct), f[i],
+                             C.fp16_scale);
+            }
           }
         }
       };
@@ -876,10 +907,24 @@ __global__ void k_ghost_cells(Ctx C, const int2 *cells, int n, float theta) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if (i == LT::REST) continue;
-      int tx = x + LT::cx(i), ty = y + LT::cy(i), tz = z + LT::cz(i);
-      if (!(wrap(F, 0, tx) && wrap(F, 1, ty) && (D == 2 || wrap(F, 2, tz)))) continue;
-      const long long ct = cidx(F, tx, ty, tz);
-      if (C.tag[F.cell_off + ct] & TAG_LEAF) Store<T>::st(Bf + i * F.ncell + ct, f[i], C.fp16_scale);
+      // through a slip wall the population comes back mirrored, moved on tangentially
+      int t[3] = {x + LT::cx(i), y + LT::cy(i), z + LT::cz(i)};
+      const int o[3] = {x, y, z};
+      int mm = 0;
+      bool ok = true;
+      for (int a = 0; a < D; ++a)
+        if (!wrap(F, a, t[a])) {
+          if (F.slip[a]) {
+            t[a] = o[a];
+            mm |= 1 << a;
+          } else {
+            ok = false;
+          }
+        }
+      if (!ok) continue;
+      const long long ct = cidx(F, t[0], t[1], t[2]);
+      if (C.tag[F.cell_off + ct] & TAG_LEAF)
+        Store<T>::st(Bf + mirror_dir<Q>(i, mm) * F.ncell + ct, f[i], C.fp16_scale);
     }
   }
 }

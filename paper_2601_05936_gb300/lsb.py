@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("LSB_LIBRARY") or os.path.join(HERE, "_lib", "liblsb.so")
 
 D2Q9, D3Q19 = 0, 1
-PERIODIC, WALL = 0, 1
+PERIODIC, WALL, SLIP = 0, 1, 2
 FP32, FP16S = 0, 1
 SENSOR_BAND, SENSOR_SIGNED = 0, 1
 FIELD = dict(rho=0, u=1, phi=2, phase=3, f=4, tag=5, blocks=6, cutmask=7, kappa=8, uext=9, adj_f=10, adj_uext=11)
@@ -117,7 +117,8 @@ def _desc(case):
     for a in range(3):
         d.base[a] = int(case["base"][a]) if a < D else 1
         d.block[a] = int(case["block"][a]) if a < D else 1
-        d.bc[a] = (PERIODIC if case["periodic"][a] else WALL) if a < D else PERIODIC
+        slip = bool((case.get("slip") or (False,) * D)[a]) if a < D else False
+        d.bc[a] = (PERIODIC if case["periodic"][a] else (SLIP if slip else WALL)) if a < D else PERIODIC
     d.n_levels = int(case.get("n_levels", 1))
     wu = np.zeros((6, 3))
     if case.get("wall_u") is not None:
