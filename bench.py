@@ -258,12 +258,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-all", action="store_true", help="print a per-kernel time table to stderr")
     ap.add_argument("--workload", default="bubble3d",
-                    choices=["bubble3d", "box3d", "ensemble", "adjoint3d", "adjoint3d_ls", "adjoint3d_amr"],
+                    choices=["bubble3d", "box3d", "ensemble", "adjoint3d", "adjoint3d_ls", "adjoint3d_amr",
+                             "paper3d", "couette2d"],
                     help="bubble3d: the benchmark configuration; box3d: uniform periodic 128^3 box "
                          "(collide-and-stream only, for profiling captures); ensemble: 64 uneven 2D bubbles; "
                          "adjoint3d: reverse sweep over --steps recorded steps of a frozen 3D bubble; "
                          "adjoint3d_ls: the same with the level set moving (short windows: no phase change); "
-                         "adjoint3d_amr: the frozen adjoint on the two-level grid of bubble3d")
+                         "adjoint3d_amr: the frozen adjoint on the two-level grid of bubble3d; "
+                         "paper3d: the paper's own 3D box (2d x 2d x 4d, d = 64, uniform, slip lateral walls, "
+                         "case --paper-case); couette2d: two-layer Couette with a moving wall, 2048^2")
+    ap.add_argument("--paper-case", default="I", choices=["I", "II"], help="paper3d: parameter set of Sec. 3.2")
+    ap.add_argument("--nu-floor", type=float, default=None,
+                    help="paper3d: lower bound of the lattice viscosities (default 0.05 for case I, 0.1 for "
+                         "case II, the smallest measured stable; BGK in both phases is unstable at the "
+                         "paper's Re = 35, tau = 0.563, where the paper's gas solver is a cumulant model)")
     ap.add_argument("--checkpoint-every", type=int, default=100)
     ap.add_argument("--driver", type=int, default=0, choices=[0, 1],
                     help="level-set passes: 0 one launch each, 1 one persistent cooperative launch per finest step")
@@ -302,6 +310,14 @@ def main():
         cases = [case]
     elif args.workload == "box3d":
         case = workloads.uniform_box(storage=args.storage)
+        cases = [case]
+    elif args.workload == "paper3d":
+        floor = args.nu_floor if args.nu_floor is not None else {"I": 0.05, "II": 0.1}[args.paper_case]
+        case = workloads.paper_box_3d(args.paper_case, storage=args.storage, nu_floor=floor)
+        cases = [case]
+    elif args.workload == "couette2d":
+        case = workloads.two_layer_couette()
+        case["storage"] = args.storage
         cases = [case]
     else:
         cases = workloads.ensemble()
@@ -385,14 +401,17 @@ def main():
         return
     cpu = None if args.no_cpu_baseline or world > 1 or args.workload != "bubble3d" else cpu_baseline()
     metric = METRIC if args.workload == "bubble3d" else f"MLUPS (leaf cell updates / s), {args.workload}"
-    lattice = "D2Q9" if args.workload == "ensemble" else "D3Q19"
+    lattice = case["lattice"]
+    state_gb = sum(float(np.prod([b * 2 ** l for b in c["base"]])) for c in cases
+                   for l in range(int(c["n_levels"]))) * 2 * (9 if lattice == "D2Q9" else 19) * 4 / 1e9
     wname = case["name"] if len(cases) == 1 else f"ensemble of {len(cases)} 2D rising bubbles (96x192..256x512, 1-3 levels)"
     line = dict(metric=metric, value=value, unit="MLUPS", n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f32" if args.storage == "fp32" else "f16-store/f32-compute", data="synthetic",
                 config=dict(workload=wname, lattice=lattice, levels=int(case["n_levels"]),
                             storage=args.storage, parallelism=f"replicas{world}", driver=args.driver,
-                            cell_updates_per_step=upd / args.steps, l2_flush="state 5.7 GB >> 129 MB L2",
+                            cell_updates_per_step=upd / args.steps,
+                            l2_flush=f"state {state_gb:.1f} GB (both buffers) >> 129 MB L2",
                             bubble=dict(centroid=[float(v) if np.isfinite(v) else None for v in obs["centroid"]],
                                         velocity=[float(v) if np.isfinite(v) else None for v in obs["velocity"]])),
                 roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clk)

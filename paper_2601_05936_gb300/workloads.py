@@ -117,6 +117,56 @@ def rising_bubble_3d(seed=4000, nx=128, ny=128, nz=256, levels=2, radius_base=16
                 Re_eff=prm["Re_eff"], p_gas0=2.0 * prm["sigma"] / (d / 2), **LS_DEFAULTS)
 
 
+PAPER_CASES = {"I": dict(Re=35.0, Eo=10.0, rho_ratio=10.0, eta_ratio=10.0),
+               "II": dict(Re=35.0, Eo=125.0, rho_ratio=1000.0, eta_ratio=100.0)}
+
+
+def paper_box_3d(case="I", d=64, levels=1, seed=4100, block=(32, 4, 4), storage="fp32", steps=2000,
+                 Ma=0.02, nu_floor=0.0):
+    """The 3D rising-bubble benchmark in the paper's own box (Sec. 3.2): width 2 d, depth 2 d,
+    height 4 d (z up, gravity along -z), slip lateral walls, no-slip top and bottom, bubble
+    diameter d (finest cells; the paper uses d = 64 on a uniform grid), parameter set I or II
+    of the paper's table, Ma = 0.02.  The bubble starts centred laterally one diameter above
+    the floor (a sub-cell random offset from ``seed``); the paper's text does not state the
+    start height.  With levels > 1 the coarse grid is the box / 2^(levels-1) and the band of
+    the interface is refined."""
+    rng = np.random.default_rng(seed)
+    prm = bubble_params(float(d), Ma=Ma, nu_floor=nu_floor, **PAPER_CASES[case])
+    r = 2 ** (levels - 1)
+    nf = (2 * d, 2 * d, 4 * d)
+    base = tuple(n // r for n in nf)
+    assert all(b * r == n for b, n in zip(base, nf)), "box not divisible by the level ratio"
+    x, y, z = _grid_centers(nf)
+    off = rng.random(3) * 0.5
+    c = (d + off[0], d + off[1], d + off[2])
+    phi = 0.5 * d - np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2)
+    return dict(name=f"paper_box_3d_case{case}_d{d}_L{levels}", lattice="D3Q19", base=base, n_levels=levels,
+                block=block, periodic=(False, False, False), slip=(True, True, False), rho_phys=prm["rho_phys"],
+                nu=prm["nu"], gravity=(0.0, 0.0, -prm["g"]), sigma=prm["sigma"], x_ref=c,
+                phi0=phi.reshape(-1).astype(np.float32), refine_dist=[8.0] * (levels - 1), sensor="band",
+                regrid_every=25 if levels > 1 else 0, steps=steps, storage=storage, fp16_scale=1024.0,
+                Ma=prm["Ma"], Re_eff=prm["Re_eff"], p_gas0=2.0 * prm["sigma"] / (d / 2), **LS_DEFAULTS)
+
+
+def two_layer_couette(nx=2048, ny=2048, h_frac=0.5 + 1.0 / 512, U=0.01, rho=(1.0, 0.1), eta_ratio=5.0, nu_heavy=0.1,
+                      block=(32, 8), steps=1000):
+    """Two-layer Couette flow (Sec. 3.1): the domain [0, 2] x [-1, 1] of the paper on an
+    nx x ny grid, periodic in x, a resting bottom wall and a top wall moving at U along x,
+    a flat interface at height h (heavy fluid below) that stays put (u . n = 0), level set
+    live.  Steady state: the piecewise-linear profile with the shear-stress jump set by the
+    viscosity ratio."""
+    h = h_frac * ny
+    _, yy = _grid_centers((nx, ny))
+    phi = yy - h
+    etaA = rho[0] * nu_heavy
+    nu = (nu_heavy, etaA / eta_ratio / rho[1])
+    wall = np.zeros((4, 2))
+    wall[3, 0] = U
+    return dict(name=f"two_layer_couette_{nx}x{ny}", lattice="D2Q9", base=(nx, ny), n_levels=1, block=block,
+                periodic=(True, False), rho_phys=rho, nu=nu, wall_u=wall.reshape(-1), phi0=phi.reshape(-1),
+                steps=steps, regrid_every=0, **LS_DEFAULTS)
+
+
 def ensemble(seed0=5000, n_cases=64, steps=2000, block=(32, 8), w_range=(96, 256), max_levels=3):
     """Uneven 2D rising bubbles: width ~ U{96..256} (even), height 2*width, levels U{1..3},
     density ratio log-uniform [10, 1000], Eo U[1, 40], Re U[10, 100], radius width/8."""

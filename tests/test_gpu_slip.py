@@ -90,3 +90,27 @@ def test_slip_window_adjoint(lattice, n, levels, kw, warmup, steps):
         lam_g = g.get("adj_f", 0, l).reshape(g.Q, -1).astype(np.float64)
         assert rel_l2(lam_g, lam_o[l]) < 1e-3, (l, rel_l2(lam_g, lam_o[l]))
     g.close()
+
+
+@pytest.mark.parametrize("pcase", ["I", "II"])
+def test_paper_box_parity(pcase):
+    """The paper's box (slip lateral walls) at d = 8 cells, level set live; viscosity floored
+    at 0.1 as for the downsampled benchmark bubble (tau 0.508 at the paper's Re is unstable)."""
+    from paper_2601_05936_gb300 import workloads
+    case = workloads.paper_box_3d(pcase, d=8, block=(16, 4, 4), nu_floor=0.1)
+    g, s = run_both(case, 16)
+    r = compare_levels(g, s)[0]
+    assert r["leaf_equal"], r
+    assert r["u"] < 1e-3 and r["drho_abs"] < 1e-5, r
+    phi_g = g.get("phi").reshape(-1).astype(np.float64)
+    assert np.abs(phi_g - s.phi).max() < 1e-4
+    g.close()
+
+
+def test_two_layer_couette_parity():
+    from paper_2601_05936_gb300 import workloads
+    case = workloads.two_layer_couette(nx=32, ny=32)
+    g, s = run_both(case, 150)
+    r = compare_levels(g, s)[0]
+    assert r["u"] < 1e-4 and r["drho_abs"] < 1e-5, r
+    g.close()
