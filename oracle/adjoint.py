@@ -59,6 +59,7 @@ class FrozenStep:
 
     def __init__(self, sim, phi=None):
         """``phi`` replaces the Sim's level set (same signs: the masks are the Sim's)."""
+        assert sim.collision == ("bgk", "bgk"), "the adjoint transposes the BGK collision"
         self.sim = sim
         self.lat = lat = sim.lat
         self.g = g = sim.geoms[-1]

@@ -26,12 +26,13 @@ import numpy as np
 from . import amr, coupling, levelset
 from .grid import LevelGeom
 from .lattice import CS2, get as get_lattice
-from .lbm import collide, equilibrium, moments, omega_from_nu, strain_rate
+from .lbm import collide, equilibrium, forcing, moments, omega_from_nu, strain_rate
 
 DEFAULTS = dict(
     n_levels=1, sigma=0.0, body_force=None, gravity=None, x_ref=None, wall_u=None, p_gas0=0.0,
     n_ext=8, dtau_ext=0.5, reinit_every=1, n_reinit=1, dtau_reinit=0.3,
     refine_dist=None, sensor="band", regrid_every=0, ls_active=True, slip=None,
+    collision=("bgk", "bgk"),
 )
 
 
@@ -50,6 +51,10 @@ class Sim:
         base = tuple(int(b) for b in c["base"])
         self.periodic = tuple(bool(p) for p in c["periodic"])
         self.slip = tuple(bool(s) for s in (c["slip"] or (False,) * D))
+        # collision operator per phase (liquid, gas): BGK, or the cumulant model on D3Q27
+        self.collision = tuple(str(k) for k in c["collision"])
+        assert all(k in ("bgk", "cumulant") for k in self.collision)
+        assert "cumulant" not in self.collision or c["lattice"] == "D3Q27", "cumulant collision needs D3Q27"
         self.geoms = [LevelGeom(tuple(b * 2 ** l for b in base), self.periodic, c["block"], self.slip)
                       for l in range(self.L)]
         gF = self.geoms[-1]
@@ -108,6 +113,16 @@ class Sim:
         acc = (self.gravity[:, None] + self.body_force[:, None] / self.rho_phys[phase][None, :]) * r
         return om, acc
 
+    def collide(self, f, om, acc, phase):
+        """Post-collision populations with each cell's phase operator and forcing (Eq. 1)."""
+        out = collide(self.lat, f, om, acc)
+        for p in (0, 1):
+            m = phase == p
+            if self.collision[p] == "cumulant" and m.any():
+                from .cumulant import cumulant_collide
+                out[:, m] = cumulant_collide(self.lat, f[:, m], om[m]) + forcing(self.lat, f[:, m].sum(0), acc[:, m])
+        return out
+
     def tau(self, l, phase):
         return 1.0 / self.level_params(l, phase)[0]
 
@@ -160,7 +175,7 @@ class Sim:
         om, acc = self.level_params(l, ph)
         coll = np.flatnonzero(leaf | rlayer)
         fc = np.zeros_like(self.f[l])
-        fc[:, coll] = collide(lat, self.f[l][:, coll], om[coll], acc[:, coll])
+        fc[:, coll] = self.collide(self.f[l][:, coll], om[coll], acc[:, coll], ph[coll])
         if finest:
             fluid = leaf
             rho, u = moments(lat, self.f[l])
@@ -284,7 +299,7 @@ class Sim:
         fac = self.tau(l + 1, ph) / (2.0 * self.tau(l, ph))
         fi = amr.rescale_neq(lat, fi, fac)
         om, acc = self.level_params(l + 1, ph)
-        out[:, gcells] = collide(lat, fi, om, acc)
+        out[:, gcells] = self.collide(fi, om, acc, ph)
         return out
 
     def regrid(self):
