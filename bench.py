@@ -268,6 +268,9 @@ def main():
                          "paper3d: the paper's own 3D box (2d x 2d x 4d, d = 64, uniform, slip lateral walls, "
                          "case --paper-case); couette2d: two-layer Couette with a moving wall, 2048^2")
     ap.add_argument("--paper-case", default="I", choices=["I", "II"], help="paper3d: parameter set of Sec. 3.2")
+    ap.add_argument("--lattice", default="D3Q19", choices=["D3Q19", "D3Q27"],
+                    help="paper3d: D3Q19 with BGK in both phases, or the paper's own 3D setup: D3Q27 with BGK "
+                         "in the liquid and the cumulant model in the gas")
     ap.add_argument("--nu-floor", type=float, default=None,
                     help="paper3d: lower bound of the lattice viscosities (default 0.05 for case I, 0.1 for "
                          "case II, the smallest measured stable; BGK in both phases is unstable at the "
@@ -313,7 +316,9 @@ def main():
         cases = [case]
     elif args.workload == "paper3d":
         floor = args.nu_floor if args.nu_floor is not None else {"I": 0.05, "II": 0.1}[args.paper_case]
-        case = workloads.paper_box_3d(args.paper_case, storage=args.storage, nu_floor=floor)
+        coll = ("bgk", "cumulant") if args.lattice == "D3Q27" else ("bgk", "bgk")
+        case = workloads.paper_box_3d(args.paper_case, storage=args.storage, nu_floor=floor, lattice=args.lattice,
+                                      collision=coll)
         cases = [case]
     elif args.workload == "couette2d":
         case = workloads.two_layer_couette()
@@ -403,7 +408,7 @@ def main():
     metric = METRIC if args.workload == "bubble3d" else f"MLUPS (leaf cell updates / s), {args.workload}"
     lattice = case["lattice"]
     state_gb = sum(float(np.prod([b * 2 ** l for b in c["base"]])) for c in cases
-                   for l in range(int(c["n_levels"]))) * 2 * (9 if lattice == "D2Q9" else 19) * 4 / 1e9
+                   for l in range(int(c["n_levels"]))) * 2 * {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}[lattice] * 4 / 1e9
     wname = case["name"] if len(cases) == 1 else f"ensemble of {len(cases)} 2D rising bubbles (96x192..256x512, 1-3 levels)"
     line = dict(metric=metric, value=value, unit="MLUPS", n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,

@@ -47,7 +47,12 @@ typedef enum {
   LSB_ESTATE = 6     /* call not valid in the handle's current state */
 } lsb_status;
 
-enum { LSB_D2Q9 = 0, LSB_D3Q19 = 1 };           /* velocity sets, Sec. 2.1 / Fig. 1 */
+enum { LSB_D2Q9 = 0, LSB_D3Q19 = 1, LSB_D3Q27 = 2 }; /* velocity sets, Sec. 2.1 / Fig. 1 */
+/* collision operator of a phase: BGK with forcing (Eq. 1), or the cumulant model
+ * (D3Q27 only; the paper's gas operator in 3D, Sec. 3.2): second cumulants relaxed
+ * with the phase's shear rate (deviatoric part) and rate 1 (trace), every higher
+ * cumulant relaxed to zero with rate 1 */
+enum { LSB_BGK = 0, LSB_CUMULANT = 1 };
 /* per-axis boundary kind: periodic, no-slip wall (half-way bounce-back, Eq. bb
  * with q = 1/2, plus the moving-wall term) or slip wall (specular reflection: a
  * population leaving through the wall returns with its normal component negated,
@@ -81,7 +86,8 @@ enum {
 
 /* Geometry and discretisation of one case, fixed for the handle's life. */
 typedef struct {
-  int lattice;          /* LSB_D2Q9 or LSB_D3Q19; all cases of a handle share it     */
+  int lattice;          /* LSB_D2Q9, LSB_D3Q19 or LSB_D3Q27 (FP32 storage only);
+                           all cases share it                                       */
   int base[3];          /* base-level cells per axis (base[2] ignored in 2D)         */
   int n_levels;         /* total levels including the base (1 = uniform), <= 4       */
   int block[3];         /* block edge in cells, powers of two, same on every level;
@@ -91,6 +97,8 @@ typedef struct {
   int storage;          /* LSB_FP32 or LSB_FP16S; all cases of a handle share it     */
   double fp16_scale;    /* LSB_FP16S: populations stored as (f - w) * scale, a power
                            of two that keeps them out of the half subnormal range   */
+  int collision[2];     /* operator of [0] liquid, [1] gas: LSB_BGK or LSB_CUMULANT
+                           (D3Q27 only); zero-initialised = BGK in both            */
 } lsb_grid_desc;
 
 /* Physics and method parameters of one case (lattice units of the finest level). */

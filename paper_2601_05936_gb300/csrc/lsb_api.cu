@@ -634,6 +634,7 @@ void fill_physics(lsb_grid *g, LevelDev &L, const CaseHost &ch) {
   }
   L.ls_active = p.ls_active;
   L.p_gas0 = (float)p.p_gas0;
+  for (int k = 0; k < 2; ++k) L.cumulant[k] = ch.d.collision[k] == LSB_CUMULANT;
   (void)g;
 }
 
@@ -1140,8 +1141,10 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
   *out = nullptr;
   if (n_cases < 1 || !descs || !params || !phi0) return fail(nullptr, LSB_EINVAL, "need n_cases >= 1 and arrays");
   const lsb_grid_desc &d0 = descs[0];
-  if (d0.lattice != LSB_D2Q9 && d0.lattice != LSB_D3Q19) return fail(nullptr, LSB_EINVAL, "unknown lattice");
+  if (d0.lattice != LSB_D2Q9 && d0.lattice != LSB_D3Q19 && d0.lattice != LSB_D3Q27)
+    return fail(nullptr, LSB_EINVAL, "unknown lattice");
   if (d0.storage != LSB_FP32 && d0.storage != LSB_FP16S) return fail(nullptr, LSB_EINVAL, "unknown storage");
+  if (d0.lattice == LSB_D3Q27 && d0.storage != LSB_FP32) return fail(nullptr, LSB_EINVAL, "D3Q27 needs FP32 storage");
   const int D = d0.lattice == LSB_D2Q9 ? 2 : 3;
   int bs[3] = {d0.block[0], d0.block[1], D == 3 ? d0.block[2] : 1};
   for (int a = 0; a < D; ++a)
@@ -1154,6 +1157,12 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
     for (int a = 0; a < 3; ++a)
       if (d.block[a] != d0.block[a] && (a < D)) return fail(nullptr, LSB_EINVAL, "cases must share the block shape");
     if (d.n_levels < 1 || d.n_levels > MAXL) return fail(nullptr, LSB_EINVAL, "n_levels must be 1..%d", MAXL);
+    for (int k = 0; k < 2; ++k) {
+      if (d.collision[k] != LSB_BGK && d.collision[k] != LSB_CUMULANT)
+        return fail(nullptr, LSB_EINVAL, "collision must be LSB_BGK or LSB_CUMULANT");
+      if (d.collision[k] == LSB_CUMULANT && d.lattice != LSB_D3Q27)
+        return fail(nullptr, LSB_EINVAL, "the cumulant collision needs D3Q27");
+    }
     for (int a = 0; a < D; ++a) {
       if (d.base[a] < 1) return fail(nullptr, LSB_EINVAL, "base must be positive");
       if (d.bc[a] != LSB_PERIODIC && d.bc[a] != LSB_WALL && d.bc[a] != LSB_SLIP)
@@ -1171,7 +1180,7 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
 
   g = new lsb_grid();
   g->ncase = n_cases;
-  g->Q = D == 2 ? 9 : 19;
+  g->Q = D == 2 ? 9 : (d0.lattice == LSB_D3Q27 ? 27 : 19);
   g->D = D;
   g->storage = d0.storage;
   g->fp16_scale = d0.storage == LSB_FP16S ? (float)d0.fp16_scale : 1.0f;
@@ -1674,6 +1683,7 @@ int lsb_kernel_count(void) { return NKERN; }
 lsb_status lsb_record(lsb_grid *g, int checkpoint_every) {
   if (!g || checkpoint_every < 1) return LSB_EINVAL;
   if (g->storage != LSB_FP32) return fail(g, LSB_ESTATE, "the adjoint needs FP32 population storage");
+  if (g->Q == 27) return fail(g, LSB_ESTATE, "the adjoint covers D2Q9 and D3Q19 with BGK collision");
   int live = 0;
   for (const CaseHost &c : g->cases) live += c.p.ls_active ? 1 : 0;
   if (live != 0 && live != g->ncase)
@@ -1918,6 +1928,14 @@ int lsb_lattice_table(int lattice, int *c, float *w, int *opp) {
       if (opp) opp[i] = Lat<19>::opp(i);
     }
     return 19;
+  }
+  if (lattice == LSB_D3Q27) {
+    for (int i = 0; i < 27; ++i) {
+      if (c) { c[3 * i] = Lat<27>::cx(i); c[3 * i + 1] = Lat<27>::cy(i); c[3 * i + 2] = Lat<27>::cz(i); }
+      if (w) w[i] = Lat<27>::w(i);
+      if (opp) opp[i] = Lat<27>::opp(i);
+    }
+    return 27;
   }
   return 0;
 }

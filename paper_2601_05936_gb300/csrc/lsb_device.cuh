@@ -61,6 +61,25 @@ template <> struct Lat<19> {
   }
 };
 
+template <> struct Lat<27> {
+  static constexpr int D = 3;
+  static constexpr int REST = 26;
+  // axis and edge velocities as D3Q19 (0..17); corners 18..25: 18 + 4 [cx > 0] + 2 [cy > 0] + [cz > 0]
+  __host__ __device__ static constexpr int cx(int i) {
+    return i < 18 ? Lat<19>::cx(i) : (i < 26 ? (((i - 18) & 4) ? 1 : -1) : 0);
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    return i < 18 ? Lat<19>::cy(i) : (i < 26 ? (((i - 18) & 2) ? 1 : -1) : 0);
+  }
+  __host__ __device__ static constexpr int cz(int i) {
+    return i < 18 ? Lat<19>::cz(i) : (i < 26 ? (((i - 18) & 1) ? 1 : -1) : 0);
+  }
+  __host__ __device__ static constexpr float w(int i) {
+    return i < 6 ? 2.0f / 27.0f : (i < 18 ? 1.0f / 54.0f : (i < 26 ? 1.0f / 216.0f : 8.0f / 27.0f));
+  }
+  __host__ __device__ static constexpr int opp(int i) { return i < 18 ? Lat<19>::opp(i) : (i < 26 ? 43 - i : 26); }
+};
+
 // The direction c_i with the components of the axes in bit mask m negated: the
 // direction a population leaves a slip wall with (specular reflection).
 template <int Q>
@@ -132,6 +151,7 @@ struct LevelDev {
   int nb[3];       // blocks per axis
   int per[3];      // periodic axis flags
   int slip[3];     // walled axes with slip walls (specular reflection)
+  int cumulant[2]; // per phase: cumulant collision (D3Q27) instead of BGK
   long long ncell; // p0*p1*p2
   long long cell_off;  // offset in per-cell arrays of all levels (f uses *Q)
   long long fine_off;  // offset in finest-level arrays, -1 if not finest

@@ -53,6 +53,91 @@ __device__ __forceinline__ void lb_collide(float *f, float om, const float acc[3
   }
 }
 
+// Cumulant collision on D3Q27 (the paper's gas operator in 3D, Sec. 3.2), in place on
+// deviations f~ = f - w, with forcing as for BGK.  The central moments follow from three
+// passes of 3-point transforms (z, y, x: populations at -1, 0, +1 -> orders 0, 1, 2 about
+// u_a).  The second cumulants (= central moments / rho) relax: off-diagonal ones and the
+// differences of the diagonal ones with om, the trace with rate 1 to 3 c_s^2 = 1.  Every
+// higher cumulant relaxes with rate 1 to zero, so the post-collision central moments of
+// orders 3 to 6 are those of a Gaussian with the relaxed second moments (odd ones vanish;
+// even ones by Isserlis' theorem); the inverse passes give the populations.
+template <bool WANT_S>
+__device__ __forceinline__ void cumulant_collide27(float *f, float om, const float acc[3], float &drho, float u[3],
+                                                   float Sout[6]) {
+  using LT = Lat<27>;
+  lb_moments<27>(f, drho, u);
+  const float rho = 1.0f + drho, ir = 1.0f / rho;
+  float m[27];  // slot (cx + 1) 9 + (cy + 1) 3 + (cz + 1); after the passes (px 9 + py 3 + pz): central moments
+#pragma unroll
+  for (int i = 0; i < 27; ++i) m[(LT::cx(i) + 1) * 9 + (LT::cy(i) + 1) * 3 + (LT::cz(i) + 1)] = f[i] + LT::w(i);
+  auto fwd = [](float &a, float &b, float &c, float v) {
+    const float M0 = a + b + c, M1 = c - a, M2 = a + c;
+    a = M0;
+    b = M1 - v * M0;
+    c = M2 - 2.0f * v * M1 + v * v * M0;
+  };
+#pragma unroll
+  for (int p = 0; p < 9; ++p) fwd(m[p * 3], m[p * 3 + 1], m[p * 3 + 2], u[2]);
+#pragma unroll
+  for (int p = 0; p < 9; ++p) fwd(m[(p / 3) * 9 + (p % 3)], m[(p / 3) * 9 + 3 + (p % 3)], m[(p / 3) * 9 + 6 + (p % 3)], u[1]);
+#pragma unroll
+  for (int p = 0; p < 9; ++p) fwd(m[p], m[9 + p], m[18 + p], u[0]);
+  const float kxx = m[18] * ir, kyy = m[6] * ir, kzz = m[2] * ir;
+  const float kxy = m[12] * ir, kxz = m[10] * ir, kyz = m[4] * ir;
+  if (WANT_S) {  // S = -(om / (2 rho c_s^2)) (central second moments - rho c_s^2 I), as for BGK
+    const float s = -1.5f * om;
+    Sout[0] = s * (kxx - CS2); Sout[1] = s * kxy; Sout[2] = s * kxz;
+    Sout[3] = s * (kyy - CS2); Sout[4] = s * kyz; Sout[5] = s * (kzz - CS2);
+  }
+  const float r1 = 1.0f - om;
+  const float dxy = r1 * (kxx - kyy), dxz = r1 * (kxx - kzz);
+  const float sxx = (1.0f + dxy + dxz) * (1.0f / 3.0f), syy = sxx - dxy, szz = sxx - dxz;
+  const float sxy = r1 * kxy, sxz = r1 * kxz, syz = r1 * kyz;
+#pragma unroll
+  for (int p = 0; p < 27; ++p) m[p] = 0.f;
+  m[0] = rho;
+  m[18] = rho * sxx; m[6] = rho * syy; m[2] = rho * szz;
+  m[12] = rho * sxy; m[10] = rho * sxz; m[4] = rho * syz;
+  m[24] = rho * (sxx * syy + 2.0f * sxy * sxy);  // (2, 2, 0)
+  m[20] = rho * (sxx * szz + 2.0f * sxz * sxz);  // (2, 0, 2)
+  m[8] = rho * (syy * szz + 2.0f * syz * syz);   // (0, 2, 2)
+  m[22] = rho * (sxx * syz + 2.0f * sxy * sxz);  // (2, 1, 1)
+  m[16] = rho * (syy * sxz + 2.0f * sxy * syz);  // (1, 2, 1)
+  m[14] = rho * (szz * sxy + 2.0f * sxz * syz);  // (1, 1, 2)
+  m[26] = rho * (sxx * syy * szz + 2.0f * (sxx * syz * syz + syy * sxz * sxz + szz * sxy * sxy) +
+                 8.0f * sxy * sxz * syz);       // (2, 2, 2)
+  auto bwd = [](float &a, float &b, float &c, float v) {
+    const float M0 = a, M1 = b + v * M0, M2 = c + 2.0f * v * M1 - v * v * M0;
+    a = 0.5f * (M2 - M1);
+    b = M0 - M2;
+    c = 0.5f * (M2 + M1);
+  };
+#pragma unroll
+  for (int p = 0; p < 9; ++p) bwd(m[p], m[9 + p], m[18 + p], u[0]);
+#pragma unroll
+  for (int p = 0; p < 9; ++p) bwd(m[(p / 3) * 9 + (p % 3)], m[(p / 3) * 9 + 3 + (p % 3)], m[(p / 3) * 9 + 6 + (p % 3)], u[1]);
+#pragma unroll
+  for (int p = 0; p < 9; ++p) bwd(m[p * 3], m[p * 3 + 1], m[p * 3 + 2], u[2]);
+#pragma unroll
+  for (int i = 0; i < 27; ++i) {
+    const float F = 3.0f * LT::w(i) * rho * (LT::cx(i) * acc[0] + LT::cy(i) * acc[1] + LT::cz(i) * acc[2]);
+    f[i] = m[(LT::cx(i) + 1) * 9 + (LT::cy(i) + 1) * 3 + (LT::cz(i) + 1)] - LT::w(i) + F;
+  }
+}
+
+// The cell's phase operator: BGK, or on D3Q27 the cumulant model where the level asks for it.
+template <int Q, bool WANT_S>
+__device__ __forceinline__ void collide_phase(float *f, float om, const float acc[3], float &drho, float u[3],
+                                              float Sout[6], bool cumulant) {
+  if constexpr (Q == 27) {
+    if (cumulant) {
+      cumulant_collide27<WANT_S>(f, om, acc, drho, u, Sout);
+      return;
+    }
+  }
+  lb_collide<Q, WANT_S>(f, om, acc, drho, u, Sout);
+}
+
 // ------------------------------------------------------------------ init
 // Rest equilibrium with the hydrostatic density rho_hat = 1 - g.(x - x_ref)/c_s^2.
 template <int Q, typename T>
@@ -89,7 +174,7 @@ __global__ void k_init(Ctx C, BlockShape S, const int *list, int nlist) {
 // axes, or a wall) are formed once per cell, so every population's
 // destination is one add and boundary cells take no divergent slow path.
 template <int Q, typename T>
-__global__ void __launch_bounds__(512, LSB_CS_MINB) k_collide_stream(Ctx C, BlockShape S,
+__global__ void __launch_bounds__(512, (Q == 27 ? 1 : LSB_CS_MINB)) k_collide_stream(Ctx C, BlockShape S,
                                                                      const int *__restrict__ list, int nlist) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
@@ -118,7 +203,7 @@ __global__ void __launch_bounds__(512, LSB_CS_MINB) k_collide_stream(Ctx C, Bloc
     float drho, u[3], Sm[6];
     const bool fine = L.finest != 0;
     if (fine && (C.bflag[gb] & BF_BAND)) {
-      lb_collide<Q, true>(f, L.omega[ph], acc, drho, u, Sm);
+      collide_phase<Q, true>(f, L.omega[ph], acc, drho, u, Sm, L.cumulant[ph]);
       const long long fc = L.fine_off + c;
       const long long NF = C.nfine;
       float *M = C.macro;
@@ -131,7 +216,7 @@ __global__ void __launch_bounds__(512, LSB_CS_MINB) k_collide_stream(Ctx C, Bloc
         M[7 * NF + fc] = Sm[3]; M[8 * NF + fc] = Sm[4]; M[9 * NF + fc] = Sm[5];
       }
     } else {
-      lb_collide<Q, false>(f, L.omega[ph], acc, drho, u, Sm);
+      collide_phase<Q, false>(f, L.omega[ph], acc, drho, u, Sm, L.cumulant[ph]);
     }
     // per-axis neighbour offsets and wall flags
     const bool wxm = x == 0 && !L.per[0], wxp = x == n0 - 1 && !L.per[0];
@@ -263,12 +348,12 @@ __device__ __forceinline__ float stage_ld<__half>(const __half *p, float inv) {
 struct BlockMeta {
   long long cell_off, fine_off;
   unsigned ncell, p0, p01;
-  int gb, ld, level, x0, y0, z0, n0, n1, n2, finest, band, per[3];
+  int gb, ld, level, x0, y0, z0, n0, n1, n2, finest, band, per[3], cum[2];
   float omega[2], acc[2][3];
 };
 
 template <int Q, typename T>
-__global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape S, const int *__restrict__ list,
+__global__ void __launch_bounds__(512, (Q == 27 ? 1 : 2)) k_collide_stream_tma(Ctx C, BlockShape S, const int *__restrict__ list,
                                                                int nlist, const CUtensorMap *__restrict__ tmaps) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
@@ -306,6 +391,7 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
     m.band = L.finest ? (C.bflag[gb] & BF_BAND) : 0;
     for (int a = 0; a < 3; ++a) m.per[a] = L.per[a];
     for (int k = 0; k < 2; ++k) {
+      m.cum[k] = L.cumulant[k];
       m.omega[k] = L.omega[k];
       for (int a = 0; a < 3; ++a) m.acc[k][a] = L.acc[k][a];
     }
@@ -349,7 +435,7 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
       const float acc[3] = {m.acc[ph][0], m.acc[ph][1], m.acc[ph][2]};
       float drho, u[3], Sm[6];
       if (m.band) {
-        lb_collide<Q, true>(f, m.omega[ph], acc, drho, u, Sm);
+        collide_phase<Q, true>(f, m.omega[ph], acc, drho, u, Sm, m.cum[ph]);
         const long long fc = m.fine_off + c;
         const long long NF = C.nfine;
         float *M = C.macro;
@@ -362,7 +448,7 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
           M[7 * NF + fc] = Sm[3]; M[8 * NF + fc] = Sm[4]; M[9 * NF + fc] = Sm[5];
         }
       } else {
-        lb_collide<Q, false>(f, m.omega[ph], acc, drho, u, Sm);
+        collide_phase<Q, false>(f, m.omega[ph], acc, drho, u, Sm, m.cum[ph]);
       }
       const bool cut = m.finest && (tg & TAG_IFACE);
       const bool wxm = x == 0 && !m.per[0], wxp = x == n0 - 1 && !m.per[0];
@@ -902,7 +988,7 @@ __global__ void k_ghost_cells(Ctx C, const int2 *cells, int n, float theta) {
     rescale_neq<Q>(f, F.tau[ph] / (2.0f * Lc.tau[ph]));
     float drho, u[3], Sm[6];
     const float acc[3] = {F.acc[ph][0], F.acc[ph][1], F.acc[ph][2]};
-    lb_collide<Q, false>(f, F.omega[ph], acc, drho, u, Sm);
+    collide_phase<Q, false>(f, F.omega[ph], acc, drho, u, Sm, F.cumulant[ph]);
     T *Bf = fB<T, Q>(C, F);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -961,9 +1047,13 @@ cudaError_t noalloc_scratch(float **ptr) {
     if (Q == 9) {                                                \
       if (st == 0) { constexpr int Q_ = 9; using T_ = float; CALL; } \
       else { constexpr int Q_ = 9; using T_ = __half; CALL; }    \
-    } else {                                                     \
+    } else if (Q == 19) {                                        \
       if (st == 0) { constexpr int Q_ = 19; using T_ = float; CALL; } \
       else { constexpr int Q_ = 19; using T_ = __half; CALL; }   \
+    } else if (st == 0) { /* D3Q27: FP32 storage only */        \
+      constexpr int Q_ = 27; using T_ = float; CALL;             \
+    } else {                                                     \
+      return cudaErrorInvalidValue;                              \
     }                                                            \
     return cudaGetLastError();                                   \
   } while (0)
@@ -987,19 +1077,14 @@ cudaError_t prepare_collide_stream_tma(int Q, int st, int nthreads, int *ctas_pe
   const size_t smem = tma_smem_bytes(Q, st, nthreads);
   cudaError_t e = cudaSuccess;
   int nb = 0;
-  if (Q == 9 && st == 0) {
-    e = cudaFuncSetAttribute(k_collide_stream_tma<9, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_collide_stream_tma<9, float>, nthreads, smem);
-  } else if (Q == 9) {
-    e = cudaFuncSetAttribute(k_collide_stream_tma<9, __half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_collide_stream_tma<9, __half>, nthreads, smem);
-  } else if (st == 0) {
-    e = cudaFuncSetAttribute(k_collide_stream_tma<19, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_collide_stream_tma<19, float>, nthreads, smem);
-  } else {
-    e = cudaFuncSetAttribute(k_collide_stream_tma<19, __half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_collide_stream_tma<19, __half>, nthreads, smem);
-  }
+  auto prep = [&](auto kern) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, nthreads, smem);
+  };
+  if (Q == 9) st == 0 ? prep(k_collide_stream_tma<9, float>) : prep(k_collide_stream_tma<9, __half>);
+  else if (Q == 19) st == 0 ? prep(k_collide_stream_tma<19, float>) : prep(k_collide_stream_tma<19, __half>);
+  else if (st == 0) prep(k_collide_stream_tma<27, float>);
+  else e = cudaErrorInvalidValue;  // D3Q27: FP32 storage only
   *ctas_per_sm = nb;
   return e;
 }
@@ -1044,7 +1129,8 @@ cudaError_t run_ghost_cells(int Q, int st, Launch L, Ctx C, const int2 *cells, i
 }
 cudaError_t run_level_tags(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n) {
   if (Q == 9) k_level_tags<9><<<L.grid, L.block, 0, L.stream>>>(C, S, list, n);
-  else k_level_tags<19><<<L.grid, L.block, 0, L.stream>>>(C, S, list, n);
+  else if (Q == 19) k_level_tags<19><<<L.grid, L.block, 0, L.stream>>>(C, S, list, n);
+  else k_level_tags<27><<<L.grid, L.block, 0, L.stream>>>(C, S, list, n);
   return cudaGetLastError();
 }
 

@@ -869,7 +869,8 @@ __global__ void k_sensor(Ctx C, BlockShape S, const int *list, int nlist, int mo
 #define LQ(kern, ...)                                                          \
   do {                                                                         \
     if (Q == 9) kern<9><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);        \
-    else kern<19><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);              \
+    else if (Q == 19) kern<19><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__); \
+    else kern<27><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);              \
     return cudaGetLastError();                                                 \
   } while (0)
 #define LD(kern, ...)                                                          \
@@ -888,7 +889,8 @@ __global__ void k_sensor(Ctx C, BlockShape S, const int *list, int nlist, int mo
 #define LQP(kern, ...)                                                                             \
   do {                                                                                             \
     if (Q == 9) kern<9><<<resident_grid(kern<9>, L.block, L.grid), L.block, 0, L.stream>>>(__VA_ARGS__); \
-    else kern<19><<<resident_grid(kern<19>, L.block, L.grid), L.block, 0, L.stream>>>(__VA_ARGS__);      \
+    else if (Q == 19) kern<19><<<resident_grid(kern<19>, L.block, L.grid), L.block, 0, L.stream>>>(__VA_ARGS__); \
+    else kern<27><<<resident_grid(kern<27>, L.block, L.grid), L.block, 0, L.stream>>>(__VA_ARGS__);      \
     return cudaGetLastError();                                                                     \
   } while (0)
 
@@ -938,9 +940,12 @@ cudaError_t run_refill(int Q, int st, Launch L, Ctx C, int glevel) {
   if (Q == 9) {
     if (st == 0) k_refill<9, float><<<L.grid, L.block, 0, L.stream>>>(C, glevel);
     else k_refill<9, __half><<<L.grid, L.block, 0, L.stream>>>(C, glevel);
-  } else {
+  } else if (Q == 19) {
     if (st == 0) k_refill<19, float><<<L.grid, L.block, 0, L.stream>>>(C, glevel);
     else k_refill<19, __half><<<L.grid, L.block, 0, L.stream>>>(C, glevel);
+  } else {
+    if (st != 0) return cudaErrorInvalidValue;  // D3Q27: FP32 storage only
+    k_refill<27, float><<<L.grid, L.block, 0, L.stream>>>(C, glevel);
   }
   return cudaGetLastError();
 }
@@ -958,8 +963,12 @@ cudaError_t run_levelset_persistent(int Q, Launch L, Ctx C, BlockShape S, int gl
     const int grid = resident_grid(k_levelset_persistent<9>, L.block, L.grid);
     return cudaLaunchCooperativeKernel((const void *)k_levelset_persistent<9>, grid, L.block, args, 0, L.stream);
   }
-  const int grid = resident_grid(k_levelset_persistent<19>, L.block, L.grid);
-  return cudaLaunchCooperativeKernel((const void *)k_levelset_persistent<19>, grid, L.block, args, 0, L.stream);
+  if (Q == 19) {
+    const int grid = resident_grid(k_levelset_persistent<19>, L.block, L.grid);
+    return cudaLaunchCooperativeKernel((const void *)k_levelset_persistent<19>, grid, L.block, args, 0, L.stream);
+  }
+  const int grid = resident_grid(k_levelset_persistent<27>, L.block, L.grid);
+  return cudaLaunchCooperativeKernel((const void *)k_levelset_persistent<27>, grid, L.block, args, 0, L.stream);
 }
 
 }  // namespace lsb

@@ -14,7 +14,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("LSB_LIBRARY") or os.path.join(HERE, "_lib", "liblsb.so")
 
-D2Q9, D3Q19 = 0, 1
+D2Q9, D3Q19, D3Q27 = 0, 1, 2
+BGK, CUMULANT = 0, 1
 PERIODIC, WALL, SLIP = 0, 1, 2
 FP32, FP16S = 0, 1
 SENSOR_BAND, SENSOR_SIGNED = 0, 1
@@ -27,7 +28,7 @@ STATUS = {0: "LSB_OK", 1: "LSB_EINVAL", 2: "LSB_ENOMEM", 3: "LSB_ECUDA", 4: "LSB
 class GridDesc(ctypes.Structure):
     _fields_ = [("lattice", ctypes.c_int), ("base", ctypes.c_int * 3), ("n_levels", ctypes.c_int),
                 ("block", ctypes.c_int * 3), ("bc", ctypes.c_int * 3), ("wall_u", (ctypes.c_double * 3) * 6),
-                ("storage", ctypes.c_int), ("fp16_scale", ctypes.c_double)]
+                ("storage", ctypes.c_int), ("fp16_scale", ctypes.c_double), ("collision", ctypes.c_int * 2)]
 
 
 class Params(ctypes.Structure):
@@ -113,7 +114,9 @@ def lattice_table(lattice):
 def _desc(case):
     D = 2 if case["lattice"] == "D2Q9" else 3
     d = GridDesc()
-    d.lattice = D2Q9 if D == 2 else D3Q19
+    d.lattice = {"D2Q9": D2Q9, "D3Q19": D3Q19, "D3Q27": D3Q27}[case["lattice"]]
+    for k, op in enumerate(case.get("collision", ("bgk", "bgk"))):
+        d.collision[k] = {"bgk": BGK, "cumulant": CUMULANT}[op]
     for a in range(3):
         d.base[a] = int(case["base"][a]) if a < D else 1
         d.block[a] = int(case["block"][a]) if a < D else 1

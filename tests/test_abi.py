@@ -8,7 +8,7 @@ import re
 import numpy as np
 import pytest
 
-from oracle.lattice import D2Q9, D3Q19
+from oracle.lattice import D2Q9, D3Q19, D3Q27
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -29,7 +29,7 @@ def test_header_symbols_exported(lib):
         assert hasattr(lib, n), n
 
 
-@pytest.mark.parametrize("code,lat", [(0, D2Q9), (1, D3Q19)], ids=["D2Q9", "D3Q19"])
+@pytest.mark.parametrize("code,lat", [(0, D2Q9), (1, D3Q19), (2, D3Q27)], ids=["D2Q9", "D3Q19", "D3Q27"])
 def test_lattice_tables_match_oracle(lib, code, lat):
     from paper_2601_05936_gb300 import lsb
     c, w, opp = lsb.lattice_table(code)
