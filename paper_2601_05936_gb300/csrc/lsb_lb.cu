@@ -353,7 +353,7 @@ struct BlockMeta {
 };
 
 template <int Q, typename T>
-__global__ void __launch_bounds__(512, (Q == 27 ? 1 : 2)) k_collide_stream_tma(Ctx C, BlockShape S, const int *__restrict__ list,
+__global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape S, const int *__restrict__ list,
                                                                int nlist, const CUtensorMap *__restrict__ tmaps) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
