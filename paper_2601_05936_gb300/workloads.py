@@ -122,14 +122,17 @@ PAPER_CASES = {"I": dict(Re=35.0, Eo=10.0, rho_ratio=10.0, eta_ratio=10.0),
 
 
 def paper_box_3d(case="I", d=64, levels=1, seed=4100, block=(32, 4, 4), storage="fp32", steps=2000,
-                 Ma=0.02, nu_floor=0.0, lattice="D3Q19", collision=("bgk", "bgk")):
+                 Ma=0.02, nu_floor=0.0, lattice="D3Q19", collision=("bgk", "bgk"), sensor="band", refine_dist=8.0,
+                 regrid_every=25):
     """The 3D rising-bubble benchmark in the paper's own box (Sec. 3.2): width 2 d, depth 2 d,
     height 4 d (z up, gravity along -z), slip lateral walls, no-slip top and bottom, bubble
     diameter d (finest cells; the paper uses d = 64 on a uniform grid), parameter set I or II
     of the paper's table, Ma = 0.02.  The bubble starts centred laterally one diameter above
     the floor (a sub-cell random offset from ``seed``); the paper's text does not state the
     start height.  With levels > 1 the coarse grid is the box / 2^(levels-1) and the band of
-    the interface is refined.  The paper's own runs use D3Q27 with BGK in the liquid and
+    the interface is refined (``sensor`` "band": |phi| <= refine_dist; "signed": the gas plus
+    the liquid within refine_dist of the interface, the paper's AMR study; refine_dist in
+    finest cells).  The paper's own runs use D3Q27 with BGK in the liquid and
     the cumulant model in the gas: lattice="D3Q27", collision=("bgk", "cumulant")."""
     rng = np.random.default_rng(seed)
     prm = bubble_params(float(d), Ma=Ma, nu_floor=nu_floor, **PAPER_CASES[case])
@@ -146,8 +149,9 @@ def paper_box_3d(case="I", d=64, levels=1, seed=4100, block=(32, 4, 4), storage=
                 base=base, n_levels=levels,
                 block=block, periodic=(False, False, False), slip=(True, True, False), rho_phys=prm["rho_phys"],
                 nu=prm["nu"], gravity=(0.0, 0.0, -prm["g"]), sigma=prm["sigma"], x_ref=c,
-                phi0=phi.reshape(-1).astype(np.float32), refine_dist=[8.0] * (levels - 1), sensor="band",
-                regrid_every=25 if levels > 1 else 0, steps=steps, storage=storage, fp16_scale=1024.0,
+                phi0=phi.reshape(-1).astype(np.float32), refine_dist=[float(refine_dist)] * (levels - 1),
+                sensor=sensor, regrid_every=regrid_every if levels > 1 else 0, steps=steps, storage=storage,
+                fp16_scale=1024.0,
                 Ma=prm["Ma"], Re_eff=prm["Re_eff"], p_gas0=2.0 * prm["sigma"] / (d / 2), **LS_DEFAULTS)
 
 
