@@ -366,12 +366,20 @@ def main():
     cs_ms = sum(v[0] for v in cs)
     cs_n = sum(v[1] for v in cs)
     cs_bytes = sum(v[2] for v in cs)
-    per_level = {k: dict(ms=v[0], launches=v[1], gbs=(v[2] / (v[0] / 1e3) / 1e9 if v[0] > 0 else None))
+    per_level = {k: dict(ms=v[0], launches=v[1], bytes_per_launch=v[2] / max(v[1], 1),
+                         gbs=(v[2] / (v[0] / 1e3) / 1e9 if v[0] > 0 else None))
                  for k, v in prof.items() if k.startswith("k_collide_stream")}
     hbm, src = peaks()
     achieved = cs_bytes / (cs_ms / 1e3) / 1e9 if cs_ms > 0 else None
+    # DRAM bytes per launch of the current collide-and-stream kernel on this workload (ncu
+    # dram__bytes_read.sum + dram__bytes_write.sum, one coarse step of the full-size FP32 run):
+    # launch-weighted over the levels; other workloads have no capture
+    traffic = None
+    if args.workload == "bubble3d" and args.scale == 1.0 and args.storage == "fp32" and cs_n > 0:
+        per = {"k_collide_stream": 585.5e6, "k_collide_stream_l1": 277.95e6}
+        traffic = sum(per.get(k, 0.0) * v[1] for k, v in prof.items() if k.startswith("k_collide_stream")) / cs_n
     roof = dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s",
-                frac=(achieved / hbm) if achieved else None, traffic=None, peak_source=src + " (hbm_gbs, of "
+                frac=(achieved / hbm) if achieved else None, traffic=traffic, peak_source=src + " (hbm_gbs, of "
                 + src + ")", kernel="k_collide_stream", launches=cs_n,
                 bytes_per_launch=cs_bytes / max(cs_n, 1), avg_launch_ms=cs_ms / max(cs_n, 1),
                 share_of_step=cs_ms / ms if ms > 0 else None, per_level=per_level)
