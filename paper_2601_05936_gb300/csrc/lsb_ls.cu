@@ -442,6 +442,56 @@ __device__ __forceinline__ void d_ext_iter(const Ctx &C, BlockShape S, int gleve
 template <int D>
 __global__ void k_ext_iter(Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int mode) { d_ext_iter<D>(C, S, glevel, uin, uout, mode); }
 
+// The sweeps after the first (mode 3 of d_ext_iter: the same arithmetic in the same order)
+// as a lean kernel of its own: without the first sweep's path it fits in 32 registers, so
+// four CTAs of 512 stay resident per SM; its chain of dependent loads (band list, plan,
+// values, upwind neighbours) is latency-bound, which the occupancy hides.
+template <int D>
+__global__ void __launch_bounds__(512, 3) k_ext_plan(Ctx C, BlockShape S, int glevel, const float *uin, float *uout) {
+  const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
+  const int *lst = C.band_list + (long long)glevel * C.band_cap;
+  const long long NF = C.nfine;
+  for (int w = blockIdx.x; w < nl; w += gridDim.x) {
+    int x, y, z;
+    const LevelDev &L = blk_cell(C, S, lst[w], threadIdx.x, x, y, z);
+    if (!L.ls_active || x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
+    const long long fo = L.fine_off, c = cidx(L, x, y, z);
+    const float *ui = uin + fo;
+    float *uo = uout + fo;
+    const uint8_t pf = C.plan_f[fo + c];
+    if (pf & 64) {
+#pragma unroll
+      for (int b = 0; b < D; ++b) uo[b * NF + c] = ui[b * NF + c];
+      continue;
+    }
+    float u0[3], acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < D; ++b) u0[b] = ui[b * NF + c];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const float va = C.plan_v[a * NF + fo + c];
+      const int dir = (pf >> a) & 1 ? -1 : 1;
+      long long cn;
+      if (pf & 128) {  // box-boundary cell: the neighbour clamped or wrapped
+        const int nx = a == 0 ? clampwrap(L, 0, x + dir) : x;
+        const int ny = a == 1 ? clampwrap(L, 1, y + dir) : y;
+        const int nz = a == 2 ? clampwrap(L, 2, z + dir) : z;
+        cn = cidx(L, nx, ny, nz);
+      } else {
+        cn = c + dir * (a == 0 ? 1LL : (a == 1 ? (long long)L.p[0] : (long long)L.p[0] * L.p[1]));
+      }
+      const float *src = ((pf >> (3 + a)) & 1) ? ui : C.ut0 + fo;
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        const float un = src[b * NF + cn];
+        acc[b] += va * (va > 0.f ? (u0[b] - un) : (un - u0[b]));
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < D; ++b) uo[b * NF + c] = u0[b] - L.dtau_ext * acc[b];
+  }
+}
+
 // ------------------------------------------------------------------ transport
 // Gather phi along axis a at offsets -3..+3; points in the band (and, for the
 // reinitialisation, not frozen) read the stage array, others the committed phi.
@@ -927,6 +977,7 @@ cudaError_t run_band(int Q, Launch L, Ctx C, BlockShape S, const int *list, int 
 cudaError_t run_geometry(int D, Launch L, Ctx C, int glevel, int which) { LD(k_geometry, C, glevel, which); }
 cudaError_t run_ext_init(int Q, Launch L, Ctx C, int glevel) { LQ(k_ext_init, C, glevel); }
 cudaError_t run_ext_iter(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int mode) {
+  if (mode == 3) LDP(k_ext_plan, C, S, glevel, uin, uout);
   LDP(k_ext_iter, C, S, glevel, uin, uout, mode);
 }
 cudaError_t run_adv_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage) {
