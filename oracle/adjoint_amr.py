@@ -313,7 +313,7 @@ class AMRFrozenStep:
                 F[l][:, rl] = self._restrict(l, F[l + 1], p)
         f_old = F[l].copy()
         rec["f_old"], rec["gh"] = f_old, gh
-        F[l] = self.levels[l].step(f_old, p, gh)
+        F[l] = self._level_step(l, f_old, p, gh, rec)
         if not last:
             rec["f_new"] = F[l].copy()
             rec["kids"] = []
@@ -321,6 +321,14 @@ class AMRFrozenStep:
                 kid = {}
                 self._advance(l + 1, F, p, self._ghost(l, src, p), kid)
                 rec["kids"].append(kid)
+
+    def _level_step(self, l, f_old, p, gh, rec):
+        return self.levels[l].step(f_old, p, gh)
+
+    def _level_step_T(self, l, f_old, p, lam_new, lam_gh, geo, rec):
+        if l == self.L - 1:
+            return self.fine.step_adjoint(f_old, p, lam_new, geo, lam_gh)
+        return self.levels[l].step_adjoint(f_old, p, lam_new, lam_gh)
 
     def step(self, F, p, rec=None):
         """The per-level populations after one coarse step."""
@@ -346,10 +354,7 @@ class AMRFrozenStep:
             lg = self._advance_T(l + 1, lamF, p, rec["kids"][0], dp, geo)
             lam_old_extra += self._ghost_T(l, f_old, p, lg, dp)
         lam_gh = np.zeros((Q, self.geoms[l].N))
-        if last:
-            lam_old, d = self.fine.step_adjoint(f_old, p, lam_new, geo, lam_gh)
-        else:
-            lam_old, d = self.levels[l].step_adjoint(f_old, p, lam_new, lam_gh)
+        lam_old, d = self._level_step_T(l, f_old, p, lam_new, lam_gh, geo, rec)
         dp += d
         lam_old += lam_old_extra
         if not last:
@@ -417,8 +422,73 @@ class AMRFrozenStep:
         return self.fine.geometry_to_phi(geo)
 
 
+# --------------------------------------------------------------------------- moving level set
+class AMRMovingStep(AMRFrozenStep):
+    """One coarse step of a multi-level Sim with the finest level's level set transported.
+
+    The state is (per-level populations, phi, u~); phi and u~ live on the finest level and
+    advance in each of its 2^(L-1) sub-steps (oracle/adjoint_ls.py's MovingStep, with the
+    ghost-ring values an input).  As there, the window must keep every discrete decision:
+    no cell changes phase (so refill is the identity and the coarse levels' phases, fixed at
+    the last regrid, stay valid), the band, frozen cells, upwind sides and Godunov branches
+    stay those of the forward steps; blocks do not regrid.  The reverse recursion is the
+    frozen one with the finest sub-step's transpose replaced by MovingStep's, which carries
+    the adjoints of phi and u~ from sub-step to sub-step."""
+
+    def __init__(self, sim):
+        super().__init__(sim)
+        from .adjoint_ls import MovingStep
+        self.moving = MovingStep(sim)
+
+    def _level_step(self, l, f_old, p, gh, rec):
+        if l < self.L - 1:
+            return self.levels[l].step(f_old, p, gh)
+        rec["ls"] = (self._ls[0], self._ls[1])
+        f1, phi1, ut1 = self.moving.step((f_old, self._ls[0], self._ls[1]), p, gh)
+        self._ls = [phi1, ut1]
+        return f1
+
+    def _level_step_T(self, l, f_old, p, lam_new, lam_gh, geo, rec):
+        if l < self.L - 1:
+            return self.levels[l].step_adjoint(f_old, p, lam_new, lam_gh)
+        phi, ut = rec["ls"]
+        (lf, lphi, lut), d = self.moving.step_adjoint((f_old, phi, ut), p, (lam_new, self._lls[0], self._lls[1]),
+                                                      lam_gh)
+        self._lls = [lphi, lut]
+        return lf, d
+
+    def step(self, S, p, rec=None):
+        """(per-level populations, phi, u~) after one coarse step."""
+        F = [f.copy() for f in S[0]]
+        self._ls = [S[1].copy(), S[2].copy()]
+        self._advance(0, F, p, None, {} if rec is None else rec)
+        return (F, self._ls[0], self._ls[1])
+
+    def step_adjoint(self, S, p, LAM, geo=None):
+        """Adjoints of (populations, phi, u~) at the step's start, and dJ/dp."""
+        rec = {}
+        self.step(S, p, rec)
+        lam = [x.copy() for x in LAM[0]]
+        self._lls = [LAM[1].copy(), LAM[2].copy()]
+        dp = np.zeros(NPARAM)
+        self._advance_T(0, lam, p, rec, dp, None)
+        return (lam, self._lls[0], self._lls[1]), dp
+
+    def observables(self, S):
+        return AMRFrozenStep.observables(self, S[0])
+
+    def observables_adjoint(self, S, a):
+        N = self.geoms[-1].N
+        return (AMRFrozenStep.observables_adjoint(self, S[0], a), np.zeros(N), np.zeros((self.D, N)))
+
+
 # --------------------------------------------------------------------------- windows
 def trajectory(step, F0, p, nsteps):
+    if isinstance(F0, tuple):  # (populations, phi, u~): steps return new arrays
+        out = [F0]
+        for _ in range(nsteps):
+            out.append(step.step(out[-1], p))
+        return out
     out = [[f.copy() for f in F0]]
     for _ in range(nsteps):
         out.append(step.step(out[-1], p))

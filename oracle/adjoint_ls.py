@@ -113,19 +113,20 @@ def _rk3_stages(p0, cells, rhs, dt):
 
 # --------------------------------------------------------------------------- the moving step
 class MovingStep:
-    """Step and transposed step of a single-level Sim with the level set transported."""
+    """Step and transposed step of the finest level of a Sim with the level set transported
+    (the whole step on a single-level grid; on a multi-level grid one finest sub-step, whose
+    ghost-ring values are an input, see oracle/adjoint_amr.py)."""
 
     def __init__(self, sim):
         c = sim.case
-        assert sim.L == 1, "single-level grids only"
         assert c["ls_active"], "the level set must be live"
         assert int(c["reinit_every"]) in (0, 1), "reinitialisation every step or never"
         self.sim = sim
-        self.g = g = sim.geoms[0]
+        self.g = g = sim.geoms[-1]
         self.lat = lat = sim.lat
         self.D = lat.D
-        self.phase = sim.phase[0].copy()
-        self.leaf = sim.masks[0][0].copy()
+        self.phase = sim.phase[-1].copy()
+        self.leaf = sim.masks[-1][0].copy()
         self.lx, self.lk = sim.cut_links(self.phase, self.leaf)
         iface = np.zeros(g.N, dtype=bool)
         iface[self.lx] = True
@@ -177,9 +178,9 @@ class MovingStep:
                 rein.append(st)
         return dict(rho=rho, u=u, ut0=ut0, sweeps=sweeps, ut1=ut1, adv=adv_st, ps=ps, rein=rein, phi1=phi1)
 
-    def step(self, state, p):
+    def step(self, state, p, gh=None):
         f, phi, ut = state
-        f1 = self.frozen_step(phi).step(f, p)
+        f1 = self.frozen_step(phi).step(f, p, gh)
         F = self._forward_ls(f, phi, ut)
         if not np.array_equal(F["phi1"][self.leaf] >= 0, phi[self.leaf] >= 0):
             raise ValueError("a cell changed phase: the window must be free of flips")
@@ -333,8 +334,9 @@ class MovingStep:
         return lut, lf, lphi
 
     # ------------------------------------------------------------------ the transposed step
-    def step_adjoint(self, state, p, lam):
-        """Adjoints of (f_n, phi_n, u~_n) and dJ/dp from those of (f_{n+1}, phi_{n+1}, u~_{n+1})."""
+    def step_adjoint(self, state, p, lam, lam_gh=None):
+        """Adjoints of (f_n, phi_n, u~_n) and dJ/dp from those of (f_{n+1}, phi_{n+1}, u~_{n+1});
+        with ``lam_gh`` also accumulates the adjoint of the ghost-ring values."""
         f, phi, ut = state
         lf1, lphi1, lut1 = lam
         F = self._forward_ls(f, phi, ut)
@@ -345,7 +347,7 @@ class MovingStep:
         st = self.frozen_step(phi)
         N = self.g.N
         geo = dict(phi=np.zeros(N), n=np.zeros((self.D, N)), kappa=np.zeros(N))
-        lf, dp = st.step_adjoint(f, p, lf1, geo)
+        lf, dp = st.step_adjoint(f, p, lf1, geo, lam_gh)
         lphi = lphi + lphi_ext + lphi_init + st.geometry_to_phi(geo)
         return (lf + lf_init, lphi, lut), dp
 
