@@ -266,14 +266,16 @@ int lsb_lattice_table(int lattice, int *c, float *w, int *opp);
  *    interpolation, f^neq scaled by tau_f / (2 tau_c), fine collision) and
  *    every level's sub-steps, with the block layout fixed (recorded steps do
  *    not regrid) and every case on the same number of levels;
- *  - moving level set (single-level grids) (ls_active = 1 in every case, reinit_every <= 1,
+ *  - moving level set (ls_active = 1 in every case, reinit_every <= 1,
  *    n_reinit <= 1): the state is (f, phi, u~) and the sweep also transposes
  *    the interface velocity, the extension sweeps (Eq.
  *    hyperbolicExtension), the TVD-RK3 upwind-5 transport and the HJ-WENO5
  *    reinitialisation (Sec. 2.2), with phases, cut links, band, frozen cells,
  *    upwind sides and Godunov branches as in the forward steps.  No cell may
  *    change phase inside the window (refill is not differentiated):
- *    lsb_backward returns LSB_ESTATE if one did.
+ *    lsb_backward returns LSB_ESTATE if one did.  On block-refined grids the
+ *    level set lives on the finest level and advances in each of its
+ *    sub-steps; the coarser levels keep the phases of the last regrid.
  *
  * lsb_record(g, checkpoint_every): start a recording at the current state.
  * The following lsb_step calls run eagerly (no CUDA graphs) and copy the
@@ -281,10 +283,10 @@ int lsb_lattice_table(int lattice, int *c, float *w, int *opp);
  * checkpoint at the start of every checkpoint_every-th step (allocated as
  * needed).  A new lsb_record, lsb_set_params or lsb_refine ends the
  * recording and frees the checkpoints.  Recorded steps never regrid.
- * Errors: LSB_EINVAL (checkpoint_every < 1), LSB_ESTATE (FP16 storage, cases
- * mixing live and frozen level sets, a moving level set with more than one
- * level, reinit_every > 1 or n_reinit > 1, or cases with different numbers
- * of levels on a multi-level grid).
+ * Errors: LSB_EINVAL (checkpoint_every < 1), LSB_ESTATE (FP16 storage, D3Q27,
+ * cases mixing live and frozen level sets, a moving level set with
+ * reinit_every > 1 or n_reinit > 1, or cases with different numbers of levels
+ * on a multi-level grid).
  *
  * lsb_backward(g, dJ_dobs, dJ_dparams, dJ_dphi0): reverse sweep over every
  * step recorded so far.  Segment by segment, from the last, it restores the
@@ -294,7 +296,8 @@ int lsb_lattice_table(int lattice, int *c, float *w, int *opp);
  * level-set passes; on a multi-level grid each adjoint step first replays
  * its coarse step, keeping every level's populations per call of the level
  * recursion: 2^L - 1 further states plus 2^(L-1) - 1 for the coarse
- * sub-steps' results, allocated on the first multi-level lsb_backward).
+ * sub-steps' results, and with a moving level set phi and u~ at the start of
+ * each finest sub-step; allocated on the first multi-level lsb_backward).
  * dJ_dobs: host, n_cases x (4 + 2 D) doubles, weights of the observables
  * in lsb_observables order (centroid, volume and leaf count are constants of
  * the map).  dJ_dparams: host, n_cases x LSB_NPARAM_ADJ doubles, or NULL;
@@ -308,8 +311,8 @@ int lsb_lattice_table(int lattice, int *c, float *w, int *opp);
  * Afterwards the state is that of the last recorded step again, the
  * recording stays open (lsb_backward may be called again, e.g. with other
  * weights, and lsb_step extends the recording), LSB_FIELD_ADJ_F returns dJ/df
- * (per level; zero outside the leaves) and, with a moving level set, LSB_FIELD_ADJ_UEXT dJ/du~ at the start of the
- * window.  FP32 adjoint fields, FP64 parameter sums.  Synchronises.  Errors:
+ * (per level; zero outside the leaves) and, with a moving level set,
+ * LSB_FIELD_ADJ_UEXT dJ/du~ at the start of the window.  FP32 adjoint fields, FP64 parameter sums.  Synchronises.  Errors:
  * LSB_EINVAL, LSB_ESTATE (no recording, or a phase change in the window),
  * LSB_ENOMEM, LSB_ECUDA.
  */

@@ -143,6 +143,8 @@ struct lsb_grid {
   // call of the level recursion (preorder), input of the transposed transfers
   int tape_on = 0, tape_call = 0;
   std::vector<float *> tape_old, tape_new;  // state at the call's start (after restriction), after its sub-step
+  std::vector<float *> tape_ls;             // moving level set: phi and u~ at each finest call's start
+  int lspar = 0;                            // moving level set: its adjoints are in LP[lspar], LU[lspar]
   float *d_adjx = nullptr;                  // coarse adjoint shares of the ghost rings (kept zero)
   float *d_fsave = nullptr, *d_madj = nullptr, *d_linkadj = nullptr;
   float *d_gphi = nullptr, *d_gn = nullptr, *d_gk = nullptr;  // level-set adjoint (finest level)
@@ -551,6 +553,12 @@ lsb_status advance(lsb_grid *g, int l) {
   RUN(2, 0, rc.n, 128, run_restrict_cells, Q, st, LN(g, (rc.n + 127) / 128, 128), C, (const int2 *)rc.d, rc.n);
   const int call = g->tape_on ? g->tape_call++ : -1;
   if (call >= 0) TRY(copy_level(g, g->tape_old[call], (const float *)g->d_buf[g->par[l]], l));
+  if (call >= 0 && g->rec_moving && l == g->Lmax - 1) {  // the level set at the finest sub-step's start
+    float *t = g->tape_ls[call];
+    CU(cudaMemcpyAsync(t, g->d_phi, sizeof(float) * g->nfine, cudaMemcpyDeviceToDevice, g->stream));
+    CU(cudaMemcpyAsync(t + g->nfine, g->d_ut[0], sizeof(float) * g->D * g->nfine, cudaMemcpyDeviceToDevice,
+                       g->stream));
+  }
   const double cs_bytes = 2.0 * g->Q * (g->storage == LSB_FP32 ? 4 : 2) * g->leaf_cells[l];
   if (g->d_tmaps && !g->no_tma) {
     const int grid = std::min(g->cs[l].n, g->tma_grid);
@@ -883,31 +891,43 @@ lsb_status adj_buffers(lsb_grid *g, int seg_len) {
   return LSB_OK;
 }
 
-// One reverse step: lambda_n from lambda_{n+1} = d_adj[cur] at the state F = f_n.
-lsb_status adj_step(lsb_grid *g, const float *F, int cur, GeoAdj G, float *phi = nullptr, float *nvec = nullptr,
-                    float *kappa = nullptr) {
+// The lattice Boltzmann part of one reverse (sub-)step of level l (whose cut links
+// and moment adjoints exist on the finest level only): lambda at the state F of the
+// step's start into lamO from lamN, the adjoint after it.
+lsb_status adj_lb(lsb_grid *g, int l, const float *F, float *lamN, float *lamO, GeoAdj G, float *phi = nullptr,
+                  float *nvec = nullptr, float *kappa = nullptr) {
   Ctx C = make_ctx(g);
   if (phi) C.phi = phi;  // geometry of phi_n when the level set moves
   if (nvec) C.nvec = nvec;
   if (kappa) C.kappa = kappa;
   BlockShape S = shape(g);
   const int Q = g->Q;
-  RUN(KADJ_LINKS, 0, 1, 128, run_adj_links, Q, LN(g, DYN_GRID, 128), C, 0, F, g->d_adj[cur], g->d_linkadj,
-      g->d_madj, g->d_grad, g->ncase, G);
-  const int grid = std::min(g->cs[0].n, 152);
-  RUN(KADJ_COLLIDE, 3.0 * Q * sizeof(float) * g->leaf_cells[0], g->cs[0].n, g->nthreads, run_adj_collide, Q,
-      LN(g, grid, g->nthreads), C, S, (const int *)g->cs[0].d, g->cs[0].n, F, g->d_adj[cur], g->d_adj[1 - cur],
-      g->d_linkadj, g->d_grad);
-  RUN(KADJ_MACRO, 0, 1, 128, run_adj_macro, Q, LN(g, DYN_GRID, 128), C, 0, F, g->d_adj[1 - cur], g->d_madj,
-      g->d_grad, g->ncase);
+  const bool fine = l == g->Lmax - 1;
+  if (fine)
+    RUN(KADJ_LINKS, 0, 1, 128, run_adj_links, Q, LN(g, DYN_GRID, 128), C, l, F, lamN, g->d_linkadj, g->d_madj,
+        g->d_grad, g->ncase, G);
+  const int grid = std::min(g->cs[l].n, 152);
+  RUN(KADJ_COLLIDE, 3.0 * Q * sizeof(float) * g->leaf_cells[l], g->cs[l].n, g->nthreads, run_adj_collide, Q,
+      LN(g, grid, g->nthreads), C, S, (const int *)g->cs[l].d, g->cs[l].n, F, (const float *)lamN, lamO,
+      (const float *)g->d_linkadj, g->d_grad);
+  if (fine)
+    RUN(KADJ_MACRO, 0, 1, 128, run_adj_macro, Q, LN(g, DYN_GRID, 128), C, l, F, lamO, g->d_madj, g->d_grad,
+        g->ncase);
   return LSB_OK;
+}
+
+// One reverse step of a single-level grid: lambda_n from lambda_{n+1} = d_adj[cur] at F = f_n.
+lsb_status adj_step(lsb_grid *g, const float *F, int cur, GeoAdj G) {
+  return adj_lb(g, 0, F, g->d_adj[cur], g->d_adj[1 - cur], G);
 }
 
 // One reverse step with a moving level set: replay the level-set passes of step n
 // from (f_n, phi_n, u~_n), then the transposes in reverse order (reinitialisation,
 // transport, extension, interface velocity), then the lattice Boltzmann part with
-// the geometry of phi_n.  Adjoints in: d_adj[cur], LP[cur], LU[cur]; out: the others.
-lsb_status adj_step_moving(lsb_grid *g, const float *F, float *phi_n, const float *ut_n, int cur) {
+// the geometry of phi_n.  l is the finest level; population adjoints lamN -> lamO, the
+// level set's LP[cur], LU[cur] -> LP[1 - cur], LU[1 - cur].
+lsb_status adj_moving(lsb_grid *g, int l, const float *F, float *phi_n, const float *ut_n, float *lamN, float *lamO,
+                      int cur) {
   const LsaPtrs P = lsa_ptrs(g);
   const int Q = g->Q, D = g->D, nt = g->nthreads;
   const long long NF = g->nfine;
@@ -920,17 +940,17 @@ lsb_status adj_step_moving(lsb_grid *g, const float *F, float *phi_n, const floa
   CU(cudaMemcpyAsync(Sk(0), ut_n, bD, cudaMemcpyDeviceToDevice, g->stream));
   Ctx R = base;
   R.phi = phi_n;
-  RUN(KLSA, 0, 1, 128, run_lsa_init, Q, LN(g, DYN_GRID, 128), R, 0, F, Sk(0));
+  RUN(KLSA, 0, 1, 128, run_lsa_init, Q, LN(g, DYN_GRID, 128), R, l, F, Sk(0));
   Ctx E = base;
   E.phi = phi_n;
   E.ut0 = Sk(0);
   for (int k = 0; k < g->n_ext; ++k)
-    RUN(KLSA, 0, nb, nt, run_ext_iter, D, LN(g, nb, nt), E, S, 0, Sk(k), Sk(k + 1), k == 0 ? 2 : 3);
+    RUN(KLSA, 0, nb, nt, run_ext_iter, D, LN(g, nb, nt), E, S, l, Sk(k), Sk(k + 1), k == 0 ? 2 : 3);
   CU(cudaMemcpyAsync(P.U1, Sk(0), bD, cudaMemcpyDeviceToDevice, g->stream));
   if (g->n_ext > 0) {
     Ctx Cm = base;
     Cm.ut0 = P.U1;
-    RUN(KLSA, 0, nb, nt, run_ext_iter, D, LN(g, nb, nt), Cm, S, 0, Sk(g->n_ext), (float *)nullptr, 1);
+    RUN(KLSA, 0, nb, nt, run_ext_iter, D, LN(g, nb, nt), Cm, S, l, Sk(g->n_ext), (float *)nullptr, 1);
   }
   CU(cudaMemcpyAsync(P.PHI0, phi_n, b1, cudaMemcpyDeviceToDevice, g->stream));
   Ctx A = base;
@@ -938,7 +958,7 @@ lsb_status adj_step_moving(lsb_grid *g, const float *F, float *phi_n, const floa
   A.p1 = P.A1;
   A.p2 = P.A2;
   A.ut0 = P.U1;
-  for (int st = 1; st <= 3; ++st) RUN(KLSA, 0, nb, nt, run_adv_stage, D, LN(g, nb, nt), A, S, 0, st);
+  for (int st = 1; st <= 3; ++st) RUN(KLSA, 0, nb, nt, run_adv_stage, D, LN(g, nb, nt), A, S, l, st);
   const bool rein = g->reinit_every == 1 && g->n_reinit > 0;
   Ctx Rt = base;
   Rt.phi = P.PS;
@@ -948,29 +968,29 @@ lsb_status adj_step_moving(lsb_grid *g, const float *F, float *phi_n, const floa
   Rt.s0 = P.SS;
   if (rein) {
     CU(cudaMemcpyAsync(P.PS, P.PHI0, b1, cudaMemcpyDeviceToDevice, g->stream));
-    RUN(KLSA, 0, nb, nt, run_reinit_prep, Q, LN(g, nb, nt), Rt, S, 0);
+    RUN(KLSA, 0, nb, nt, run_reinit_prep, Q, LN(g, nb, nt), Rt, S, l);
     Ctx Rs = Rt;
     Rs.phi = P.PHI0;
-    for (int st = 1; st <= 3; ++st) RUN(KLSA, 0, nb, nt, run_reinit_stage, D, LN(g, nb, nt), Rs, S, 0, st);
+    for (int st = 1; st <= 3; ++st) RUN(KLSA, 0, nb, nt, run_reinit_stage, D, LN(g, nb, nt), Rs, S, l, st);
   }
   Ctx Gm = base;
   Gm.phi = phi_n;
   Gm.nvec = P.NV;
   Gm.kappa = P.KP;
-  RUN(11, 0, 1, 128, run_geometry, D, LN(g, DYN_GRID, 128), Gm, 0, 0);
+  RUN(11, 0, 1, 128, run_geometry, D, LN(g, DYN_GRID, 128), Gm, l, 0);
   // ---- transposes
   float *LPin = P.LP[cur], *LPout = P.LP[1 - cur], *LUin = P.LU[cur], *LUout = P.LU[1 - cur];
   const float *lps = LPin;
   if (rein) {
     CU(cudaMemcpyAsync(P.L0r, LPin, b1, cudaMemcpyDeviceToDevice, g->stream));
     CU(cudaMemsetAsync(P.LS0, 0, b1, g->stream));
-    RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), Rt, S, 0, 0, 1, LPin, P.L0r, P.L1, P.L2, P.LS0);
-    RUN(KLSA, 0, nb, nt, run_lsa_reinit_rt, D, LN(g, nb, nt), Rt, S, 0, P.R2, LPin, 2.0f / 3.0f, P.L2, P.L0r, P.LS0);
-    RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), Rt, S, 0, 1, 1, LPin, P.L0r, P.L1, P.L2, P.LS0);
-    RUN(KLSA, 0, nb, nt, run_lsa_reinit_rt, D, LN(g, nb, nt), Rt, S, 0, P.R1, P.L2, 0.25f, P.L1, P.L0r, P.LS0);
-    RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), Rt, S, 0, 2, 1, LPin, P.L0r, P.L1, P.L2, P.LS0);
-    RUN(KLSA, 0, nb, nt, run_lsa_reinit_rt, D, LN(g, nb, nt), Rt, S, 0, P.PS, P.L1, 1.0f, P.L0r, P.L0r, P.LS0);
-    RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), Rt, S, 0, 3, 1, LPin, P.L0r, P.L1, P.L2, P.LS0);
+    RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), Rt, S, l, 0, 1, LPin, P.L0r, P.L1, P.L2, P.LS0);
+    RUN(KLSA, 0, nb, nt, run_lsa_reinit_rt, D, LN(g, nb, nt), Rt, S, l, P.R2, LPin, 2.0f / 3.0f, P.L2, P.L0r, P.LS0);
+    RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), Rt, S, l, 1, 1, LPin, P.L0r, P.L1, P.L2, P.LS0);
+    RUN(KLSA, 0, nb, nt, run_lsa_reinit_rt, D, LN(g, nb, nt), Rt, S, l, P.R1, P.L2, 0.25f, P.L1, P.L0r, P.LS0);
+    RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), Rt, S, l, 2, 1, LPin, P.L0r, P.L1, P.L2, P.LS0);
+    RUN(KLSA, 0, nb, nt, run_lsa_reinit_rt, D, LN(g, nb, nt), Rt, S, l, P.PS, P.L1, 1.0f, P.L0r, P.L0r, P.LS0);
+    RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), Rt, S, l, 3, 1, LPin, P.L0r, P.L1, P.L2, P.LS0);
     lps = P.L0r;
   }
   Ctx At = base;
@@ -980,12 +1000,12 @@ lsb_status adj_step_moving(lsb_grid *g, const float *F, float *phi_n, const floa
   At.ut0 = P.U1;
   CU(cudaMemcpyAsync(LPout, lps, b1, cudaMemcpyDeviceToDevice, g->stream));
   CU(cudaMemcpyAsync(P.LA, LUin, bD, cudaMemcpyDeviceToDevice, g->stream));
-  RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), At, S, 0, 0, 0, lps, LPout, P.L1, P.L2, P.LS0);
-  RUN(KLSA, 0, nb, nt, run_lsa_adv_rt, D, LN(g, nb, nt), At, S, 0, P.A2, lps, 2.0f / 3.0f, P.L2, LPout, P.LA);
-  RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), At, S, 0, 1, 0, lps, LPout, P.L1, P.L2, P.LS0);
-  RUN(KLSA, 0, nb, nt, run_lsa_adv_rt, D, LN(g, nb, nt), At, S, 0, P.A1, P.L2, 0.25f, P.L1, LPout, P.LA);
-  RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), At, S, 0, 2, 0, lps, LPout, P.L1, P.L2, P.LS0);
-  RUN(KLSA, 0, nb, nt, run_lsa_adv_rt, D, LN(g, nb, nt), At, S, 0, (const float *)phi_n, P.L1, 1.0f, LPout, LPout,
+  RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), At, S, l, 0, 0, lps, LPout, P.L1, P.L2, P.LS0);
+  RUN(KLSA, 0, nb, nt, run_lsa_adv_rt, D, LN(g, nb, nt), At, S, l, P.A2, lps, 2.0f / 3.0f, P.L2, LPout, P.LA);
+  RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), At, S, l, 1, 0, lps, LPout, P.L1, P.L2, P.LS0);
+  RUN(KLSA, 0, nb, nt, run_lsa_adv_rt, D, LN(g, nb, nt), At, S, l, P.A1, P.L2, 0.25f, P.L1, LPout, P.LA);
+  RUN(KLSA, 0, nb, nt, run_lsa_mix, D, LN(g, nb, nt), At, S, l, 2, 0, lps, LPout, P.L1, P.L2, P.LS0);
+  RUN(KLSA, 0, nb, nt, run_lsa_adv_rt, D, LN(g, nb, nt), At, S, l, (const float *)phi_n, P.L1, 1.0f, LPout, LPout,
       P.LA);
   float *Lc = P.LA;
   if (g->n_ext > 0) {
@@ -993,19 +1013,19 @@ lsb_status adj_step_moving(lsb_grid *g, const float *F, float *phi_n, const floa
     for (int k = g->n_ext - 1; k >= 0; --k) {
       float *out = Lc == P.LK[0] ? P.LK[1] : P.LK[0];
       CU(cudaMemcpyAsync(out, Lc, bD, cudaMemcpyDeviceToDevice, g->stream));
-      RUN(KLSA, 0, nb, nt, run_lsa_ext_T, D, LN(g, nb, nt), E, S, 0, (const float *)Sk(k), (const float *)Sk(0),
+      RUN(KLSA, 0, nb, nt, run_lsa_ext_T, D, LN(g, nb, nt), E, S, l, (const float *)Sk(k), (const float *)Sk(0),
           (const float *)Lc, out, P.LOFF, P.LV);
       Lc = out;
     }
-    RUN(KLSA, 0, nb, nt, run_lsa_ext_v, D, LN(g, nb, nt), E, S, 0, P.LV, LPout);
+    RUN(KLSA, 0, nb, nt, run_lsa_ext_v, D, LN(g, nb, nt), E, S, l, P.LV, LPout);
     RUN(KLSA, 0, 1, 256, run_lsa_axpy, LN(g, 152 * 8, 256), (long long)D * NF, (const float *)P.LOFF, Lc);
   }
-  RUN(KLSA, 0, 1, 128, run_lsa_init_T, Q, LN(g, DYN_GRID, 128), R, 0, F, Lc, g->d_madj, LPout);
+  RUN(KLSA, 0, 1, 128, run_lsa_init_T, Q, LN(g, DYN_GRID, 128), R, l, F, Lc, g->d_madj, LPout);
   CU(cudaMemcpyAsync(LUout, Lc, bD, cudaMemcpyDeviceToDevice, g->stream));
   // lattice Boltzmann part with the geometry of phi_n; its phi adjoint goes to LPout
   const GeoAdj G{LPout, g->d_gn, g->d_gk};
-  TRY(adj_step(g, F, cur, G, phi_n, P.NV, P.KP));
-  RUN(KADJ_GEOM, 0, 1, 128, run_adj_geometry, D, LN(g, DYN_GRID, 128), R, 0, G);
+  TRY(adj_lb(g, l, F, lamN, lamO, G, phi_n, P.NV, P.KP));
+  RUN(KADJ_GEOM, 0, 1, 128, run_adj_geometry, D, LN(g, DYN_GRID, 128), R, l, G);
   CU(cudaMemsetAsync(g->d_gn, 0, bD, g->stream));
   CU(cudaMemsetAsync(g->d_gk, 0, b1, g->stream));
   return LSB_OK;
@@ -1017,6 +1037,22 @@ lsb_status adj_step_moving(lsb_grid *g, const float *F, float *phi_n, const floa
 lsb_status amr_buffers(lsb_grid *g) {
   const size_t sb = sizeof(float) * state_floats(g);
   const int ncall = (1 << g->Lmax) - 1;
+  if (g->rec_moving && g->tape_ls.size() != (size_t)ncall) {  // finest calls only; others stay null
+    for (float *p : g->tape_ls) cudaFree(p);
+    g->tape_ls.assign(ncall, nullptr);
+    bool ok = true;
+    std::function<void(int, int)> walk = [&](int l, int c) {  // c: preorder index of a call of level l
+      if (l == g->Lmax - 1) {
+        ok = ok && cudaMalloc(&g->tape_ls[c], sizeof(float) * (1 + g->D) * g->nfine) == cudaSuccess;
+        return;
+      }
+      const int sub = (1 << (g->Lmax - l - 1)) - 1;  // calls in a child's subtree
+      walk(l + 1, c + 1);
+      walk(l + 1, c + 1 + sub);
+    };
+    walk(0, 0);
+    if (!ok) return fail(g, LSB_ENOMEM, "adjoint level-set tape cudaMalloc");
+  }
   if ((int)g->tape_old.size() == ncall) return LSB_OK;
   for (float *p : g->tape_old) cudaFree(p);
   for (float *p : g->tape_new) cudaFree(p);
@@ -1069,16 +1105,13 @@ lsb_status adj_amr(lsb_grid *g, int l, int call, GeoAdj G) {
     RUN(KADJ_GHOST, 0, gc.n, tb, run_adj_ghost, Q, LN(g, gg, tb), C, (const int2 *)gc.d, gc.n, 0.0f, Fold,
         (const float *)nullptr, (const float *)g->d_adj[1 - g->apar[l + 1]], g->d_adjx, lamN, g->d_grad, g->ncase);
   }
-  if (last)
-    RUN(KADJ_LINKS, 0, 1, 128, run_adj_links, Q, LN(g, DYN_GRID, 128), C, l, Fold, lamN, g->d_linkadj, g->d_madj,
-        g->d_grad, g->ncase, G);
-  const int grid = std::min(g->cs[l].n, 152);
-  RUN(KADJ_COLLIDE, 3.0 * Q * sizeof(float) * g->leaf_cells[l], g->cs[l].n, g->nthreads, run_adj_collide, Q,
-      LN(g, grid, g->nthreads), C, S, (const int *)g->cs[l].d, g->cs[l].n, Fold, (const float *)lamN, lamO,
-      (const float *)g->d_linkadj, g->d_grad);
-  if (last)
-    RUN(KADJ_MACRO, 0, 1, 128, run_adj_macro, Q, LN(g, DYN_GRID, 128), C, l, Fold, lamO, g->d_madj, g->d_grad,
-        g->ncase);
+  if (last && g->rec_moving) {  // finest sub-step with the level set transported
+    float *t = g->tape_ls[call];
+    TRY(adj_moving(g, l, Fold, t, t + g->nfine, lamN, lamO, g->lspar));
+    g->lspar ^= 1;
+  } else {
+    TRY(adj_lb(g, l, Fold, lamN, lamO, G));
+  }
   if (!last) {
     const CellList &gc = g->ghost_cells[l + 1];
     const int gg = std::max(1, std::min((gc.n + tb - 1) / tb, DYN_GRID));
@@ -1103,21 +1136,41 @@ lsb_status adj_amr(lsb_grid *g, int l, int call, GeoAdj G) {
 lsb_status backward_amr(lsb_grid *g, GeoAdj G) {
   const long long T = g->rec_steps;
   const int every = g->rec_every;
-  const size_t sl = slot_floats(g);
+  const size_t sl = slot_floats(g), sf = state_floats(g), NF = g->nfine;
   TRY(amr_buffers(g));
   for (int l = 0; l < MAXL; ++l) g->apar[l] = 0;
+  g->lspar = 0;
+  // a stored state: every level's populations, and with a moving level set phi and u~ after
+  // them; a loaded one is reclassified (interface geometry and lists of its phi)
+  auto save = [&](float *dst) -> lsb_status {
+    TRY(snapshot(g, dst));
+    if (g->rec_moving) {
+      CU(cudaMemcpyAsync(dst + sf, g->d_phi, sizeof(float) * NF, cudaMemcpyDeviceToDevice, g->stream));
+      CU(cudaMemcpyAsync(dst + sf + NF, g->d_ut[0], sizeof(float) * g->D * NF, cudaMemcpyDeviceToDevice, g->stream));
+    }
+    return LSB_OK;
+  };
+  auto load = [&](const float *src) -> lsb_status {
+    TRY(restore(g, src));
+    if (g->rec_moving) {
+      CU(cudaMemcpyAsync(g->d_phi, src + sf, sizeof(float) * NF, cudaMemcpyDeviceToDevice, g->stream));
+      CU(cudaMemcpyAsync(g->d_ut[0], src + sf + NF, sizeof(float) * g->D * NF, cudaMemcpyDeviceToDevice, g->stream));
+      TRY(classify(g, g->Lmax - 1, 0));
+    }
+    return LSB_OK;
+  };
   const long long nseg = (T + every - 1) / every;
   for (long long sgi = nseg - 1; sgi >= 0; --sgi) {
     const long long start = sgi * every;
     const int len = (int)std::min<long long>(every, T - start);
-    TRY(restore(g, g->rec_ckpt[sgi]));
+    TRY(load(g->rec_ckpt[sgi]));
     for (int j = 0; j + 1 < len; ++j) {
-      TRY(snapshot(g, g->d_seg + sl * j));
+      TRY(save(g->d_seg + sl * j));
       TRY(advance(g, 0));
     }
     // the working state is the start of the segment's last step: replayed first, as it is
     for (int j = len - 1; j >= 0; --j) {
-      if (j + 1 < len) TRY(restore(g, g->d_seg + sl * j));
+      if (j + 1 < len) TRY(load(g->d_seg + sl * j));
       g->tape_on = 1;
       g->tape_call = 0;
       const lsb_status st = advance(g, 0);
@@ -1386,7 +1439,8 @@ lsb_status lsb_step(lsb_grid *g, int n) {
       if (g->rec_steps % g->rec_every == 0 && (size_t)(g->rec_steps / g->rec_every) == g->rec_ckpt.size())
         TRY(rec_checkpoint(g));
       TRY(advance(g, 0));
-      if (g->rec_moving) TRY(launched(g, run_lsa_flipflag(LN(g, 1, 32), g->d_counters, 0, g->d_recflip)));
+      if (g->rec_moving)
+        TRY(launched(g, run_lsa_flipflag(LN(g, 1, 32), g->d_counters, g->Lmax - 1, g->d_recflip)));
       g->updates_done += updates_per_step(g);
       g->coarse_steps++;
       g->rec_steps++;
@@ -1689,7 +1743,6 @@ lsb_status lsb_record(lsb_grid *g, int checkpoint_every) {
   if (live != 0 && live != g->ncase)
     return fail(g, LSB_ESTATE, "the adjoint needs the level set live in every case or frozen in every case");
   if (g->Lmax > 1) {
-    if (live) return fail(g, LSB_ESTATE, "the moving-interface adjoint covers single-level grids");
     for (const CaseHost &c : g->cases)
       if (c.L != g->Lmax) return fail(g, LSB_ESTATE, "a multi-level recording needs the same levels in every case");
   }
@@ -1799,7 +1852,8 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
     g->d_buf[1] = bufs[1];
     for (int j = len - 1; j >= 0 && st == LSB_OK; --j) {
       float *slot = g->d_seg + sl * j;
-      st = mv ? adj_step_moving(g, slot, slot + sf, slot + sf + NF, cur) : adj_step(g, slot, cur, G);
+      st = mv ? adj_moving(g, 0, slot, slot + sf, slot + sf + NF, g->d_adj[cur], g->d_adj[1 - cur], cur)
+              : adj_step(g, slot, cur, G);
       cur ^= 1;
     }
   }
@@ -1819,13 +1873,13 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
   if (mv) {
     CU(cudaMemcpyAsync(g->d_phi, g->d_phisave, sizeof(float) * NF, cudaMemcpyDeviceToDevice, g->stream));
     CU(cudaMemcpyAsync(g->d_ut[0], g->d_utsave, sizeof(float) * D * NF, cudaMemcpyDeviceToDevice, g->stream));
-    if (st == LSB_OK) st = classify(g, 0, 0);  // geometry and lists of the restored phi
+    if (st == LSB_OK) st = classify(g, g->Lmax - 1, 0);  // geometry and lists of the restored phi
   }
   if (st != LSB_OK) return st;
   if (dJ_dphi0) {
     const float *src = g->d_gphi;
     if (mv) {
-      src = lsa_ptrs(g).LP[cur];  // the adjoint of phi_0 through every pass
+      src = lsa_ptrs(g).LP[amr ? g->lspar : cur];  // the adjoint of phi_0 through every pass
     } else {
       // normal and curvature adjoints through the least-squares fit, then the dense boxes
       Ctx C2 = make_ctx(g);
@@ -1847,7 +1901,7 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
   std::vector<double> h((size_t)NG_ADJ * g->ncase);
   CU(cudaMemcpyAsync(h.data(), g->d_grad, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g->stream));
   TRY(lsb_sync(g));
-  g->adj_cur = cur;
+  g->adj_cur = amr ? g->lspar : cur;  // with a moving level set on several levels: LU[lspar]
   if (!amr) g->apar[0] = cur;
   if (dJ_dparams) {
     for (int c = 0; c < g->ncase; ++c) {
@@ -1902,6 +1956,7 @@ void lsb_destroy(lsb_grid *g) {
   for (float *p : g->rec_ckpt) cudaFree(p);
   for (float *p : g->tape_old) cudaFree(p);
   for (float *p : g->tape_new) cudaFree(p);
+  for (float *p : g->tape_ls) cudaFree(p);
   for (ProfRec &r : g->prof) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
