@@ -150,7 +150,7 @@ def reference_arm(args):
 def adjoint_bench(args, world, rank, local, barrier, dist, moving=False, levels=1):
     """Reverse sweep of the adjoint: 128x128x256 D3Q19 box with the bubble of the
     benchmark workload (d = 32 finest cells, density ratio 1000), single-level
-    (level set frozen or moving) or the benchmark's two-level grid (frozen).  A
+    or on the benchmark's two-level grid, level set frozen or moving.  A
     step of the metric is one adjoint step of the sweep: recomputation of the
     forward step from the segment checkpoint, the segment-store copy (on two
     levels also the replay of the step with its per-call record), the cut-link,
@@ -259,12 +259,14 @@ def main():
     ap.add_argument("--profile-all", action="store_true", help="print a per-kernel time table to stderr")
     ap.add_argument("--workload", default="bubble3d",
                     choices=["bubble3d", "box3d", "ensemble", "adjoint3d", "adjoint3d_ls", "adjoint3d_amr",
+                             "adjoint3d_amr_ls",
                              "paper3d", "couette2d"],
                     help="bubble3d: the benchmark configuration; box3d: uniform periodic 128^3 box "
                          "(collide-and-stream only, for profiling captures); ensemble: 64 uneven 2D bubbles; "
                          "adjoint3d: reverse sweep over --steps recorded steps of a frozen 3D bubble; "
                          "adjoint3d_ls: the same with the level set moving (short windows: no phase change); "
                          "adjoint3d_amr: the frozen adjoint on the two-level grid of bubble3d; "
+                         "adjoint3d_amr_ls: the same with the finest level's level set moving; "
                          "paper3d: the paper's own 3D box (2d x 2d x 4d, d = 64, uniform, slip lateral walls, "
                          "case --paper-case); couette2d: two-layer Couette with a moving wall, 2048^2")
     ap.add_argument("--paper-case", default="I", choices=["I", "II"], help="paper3d: parameter set of Sec. 3.2")
@@ -304,9 +306,9 @@ def main():
     __graft_entry__.build()
     from paper_2601_05936_gb300 import lsb, workloads
 
-    if args.workload in ("adjoint3d", "adjoint3d_ls", "adjoint3d_amr"):
-        adjoint_bench(args, world, rank, local, barrier, dist, moving=args.workload == "adjoint3d_ls",
-                      levels=2 if args.workload == "adjoint3d_amr" else 1)
+    if args.workload in ("adjoint3d", "adjoint3d_ls", "adjoint3d_amr", "adjoint3d_amr_ls"):
+        adjoint_bench(args, world, rank, local, barrier, dist, moving=args.workload.endswith("_ls"),
+                      levels=2 if "_amr" in args.workload else 1)
         return
     if args.workload == "bubble3d":
         case = workloads.rising_bubble_3d(storage=args.storage, scale=args.scale)
