@@ -281,7 +281,8 @@ def main():
     ap.add_argument("--driver", type=int, default=0, choices=[0, 1],
                     help="level-set passes: 0 one launch each, 1 one persistent cooperative launch per finest step")
     ap.add_argument("--scale", type=float, default=1.0,
-                    help="bubble3d only: linear scale of the box and bubble (profiling captures of a smaller copy)")
+                    help="bubble3d and box3d: linear scale of the box (and bubble) (profiling captures of a "
+                         "smaller copy; box3d at 2.0 is the 256^3 box)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -314,7 +315,7 @@ def main():
         case = workloads.rising_bubble_3d(storage=args.storage, scale=args.scale)
         cases = [case]
     elif args.workload == "box3d":
-        case = workloads.uniform_box(storage=args.storage)
+        case = workloads.uniform_box(n=int(round(128 * args.scale)), storage=args.storage)
         cases = [case]
     elif args.workload == "paper3d":
         floor = args.nu_floor if args.nu_floor is not None else {"I": 0.05, "II": 0.1}[args.paper_case]
@@ -378,7 +379,7 @@ def main():
     # launch-weighted over the levels; other workloads have no capture
     traffic = None
     if args.workload == "bubble3d" and args.scale == 1.0 and args.storage == "fp32" and cs_n > 0:
-        per = {"k_collide_stream": 585.5e6, "k_collide_stream_l1": 277.95e6}
+        per = {"k_collide_stream": 586.7e6, "k_collide_stream_l1": 262.9e6}
         traffic = sum(per.get(k, 0.0) * v[1] for k, v in prof.items() if k.startswith("k_collide_stream")) / cs_n
     roof = dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s",
                 frac=(achieved / hbm) if achieved else None, traffic=traffic, peak_source=src + " (hbm_gbs, of "

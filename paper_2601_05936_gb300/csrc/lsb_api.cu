@@ -126,6 +126,7 @@ struct lsb_grid {
   // TMA tensor maps of every level's population buffers (2 per level descriptor)
   CUtensorMap *d_tmaps = nullptr;
   int tma_grid = 0;
+  int tma_tags = 0;               // d_tmaps also holds one cell-tag map per level descriptor
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   uint64_t gnodes[2] = {0, 0};
   // adjoint of the frozen-interface step: recording and reverse sweep
@@ -562,8 +563,9 @@ lsb_status advance(lsb_grid *g, int l) {
   const double cs_bytes = 2.0 * g->Q * (g->storage == LSB_FP32 ? 4 : 2) * g->leaf_cells[l];
   if (g->d_tmaps && !g->no_tma) {
     const int grid = std::min(g->cs[l].n, g->tma_grid);
+    const CUtensorMap *tm = (const CUtensorMap *)g->d_tmaps;
     RUN(collide_kid(l), cs_bytes, g->cs[l].n, nt, run_collide_stream_tma, Q, st, LN(g, grid, nt), C, S, (const int *)g->cs[l].d,
-        g->cs[l].n, (const CUtensorMap *)g->d_tmaps);
+        g->cs[l].n, tm, g->tma_tags ? tm + 2 * g->lds.size() : nullptr);
   } else {
     RUN(collide_kid(l), cs_bytes, g->cs[l].n, nt, run_collide_stream, Q, st, LN(g, g->cs[l].n, nt), C, S, (const int *)g->cs[l].d,
         g->cs[l].n);
@@ -648,8 +650,10 @@ void fill_physics(lsb_grid *g, LevelDev &L, const CaseHost &ch) {
 
 // Tensor maps for the TMA-staged collide kernel: per level descriptor and
 // buffer, a (x, y, [z,] q) view of that level's populations with a box of one
-// block x all Q populations.  Returns false (and leaves d_tmaps NULL) when the
-// driver entry point is unavailable; the plain kernel is used then.
+// block x all Q populations; then, when a block row of tags is whole 16-byte
+// units, per level descriptor an (x, y, [z]) view of its cell tags with a box
+// of one block.  Leaves d_tmaps NULL when the driver entry point is
+// unavailable; the plain kernel is used then.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -668,7 +672,8 @@ lsb_status build_tensor_maps(lsb_grid *g) {
   if ((g->bs[0] * es) % 16 != 0 || g->bs[0] > 256 || g->bs[1] > 256 || g->bs[2] > 256) return LSB_OK;
   const CUtensorMapDataType dt =
       g->storage == LSB_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-  std::vector<CUtensorMap> maps(2 * g->lds.size());
+  const bool tags = g->bs[0] % 16 == 0;  // tag rows of whole 16-byte units (cell_off, p[0] follow)
+  std::vector<CUtensorMap> maps((tags ? 3 : 2) * g->lds.size());
   for (size_t ld = 0; ld < g->lds.size(); ++ld) {
     const LevelDev &L = g->lds[ld];
     for (int b = 0; b < 2; ++b) {
@@ -695,6 +700,16 @@ lsb_status build_tensor_maps(lsb_grid *g) {
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS) return LSB_OK;  // keep the plain kernel
     }
+    if (tags) {
+      cuuint64_t dims[3] = {(cuuint64_t)L.p[0], (cuuint64_t)L.p[1], (cuuint64_t)L.p[2]};
+      cuuint64_t strides[2] = {(cuuint64_t)L.p[0], (cuuint64_t)L.p[0] * L.p[1]};
+      cuuint32_t box[3] = {(cuuint32_t)g->bs[0], (cuuint32_t)g->bs[1], (cuuint32_t)g->bs[2]}, estr[3] = {1, 1, 1};
+      CUresult r = encode(&maps[2 * g->lds.size() + ld], CU_TENSOR_MAP_DATA_TYPE_UINT8, g->D == 3 ? 3 : 2,
+                          g->d_tag + L.cell_off, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return LSB_OK;
+    }
   }
   int per_sm = 0, nsm = 0, dev = 0;
   CU(cudaGetDevice(&dev));
@@ -706,6 +721,7 @@ lsb_status build_tensor_maps(lsb_grid *g) {
   TRY(dalloc(g, &g->d_tmaps, sizeof(CUtensorMap) * maps.size()));
   CU(cudaMemcpy(g->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
   g->tma_grid = per_sm * nsm;
+  g->tma_tags = tags;
   return LSB_OK;
 }
 

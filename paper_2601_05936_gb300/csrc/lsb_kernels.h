@@ -22,7 +22,7 @@ struct Launch {
 cudaError_t run_init(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n);
 cudaError_t run_collide_stream(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n);
 cudaError_t run_collide_stream_tma(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n,
-                                   const CUtensorMap *tmaps);
+                                   const CUtensorMap *tmaps, const CUtensorMap *tmaps_tag);
 size_t tma_smem_bytes(int Q, int st, int nthreads);
 cudaError_t prepare_collide_stream_tma(int Q, int st, int nthreads, int *ctas_per_sm);
 cudaError_t run_interface_bc(int Q, int st, Launch L, Ctx C, int glevel);

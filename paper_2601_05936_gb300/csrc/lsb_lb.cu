@@ -19,37 +19,32 @@
 
 namespace lsb {
 
-// BGK collision with forcing (Eq. 1), in place; optionally returns the strain rate.
-template <int Q, bool WANT_S>
-__device__ __forceinline__ void lb_collide(float *f, float om, const float acc[3], float &drho,
-                                           float u[3], float Sout[6]) {
+// BGK collision with forcing (Eq. 1), in place on deviations f~ = f - w, written per pair
+// (i, opp(i)):
+//   f_i' = (1 - om) f_i + w_i [om drho + rho (H cu^2 - K) + 3 rho c_i.v],
+//   H = 9 om / 2, K = 3 om usq / 2, v = om u + acc, cu = c_i.u,
+// where the first two terms are even and the last odd under c_i -> -c_i, so one evaluation
+// serves both populations of a pair.  drho and u are the pre-collision moments.
+template <int Q>
+__device__ __forceinline__ void lb_collide(float *f, float om, const float acc[3], float &drho, float u[3]) {
   using LT = Lat<Q>;
   lb_moments<Q>(f, drho, u);
-  float rho = 1.0f + drho;
-  float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-  float pxx = 0, pxy = 0, pxz = 0, pyy = 0, pyz = 0, pzz = 0;
+  const float rho = 1.0f + drho;
+  const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const float keep = 1.0f - om, A = om * drho, K = 1.5f * om * usq, H = 4.5f * om, r3 = 3.0f * rho;
+  const float v0 = om * u[0] + acc[0], v1 = om * u[1] + acc[1], v2 = om * u[2] + acc[2];
+  f[LT::REST] = keep * f[LT::REST] + LT::w(LT::REST) * (A - rho * K);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
+    if (i == LT::REST || LT::opp(i) < i) continue;
+    const int k = LT::opp(i);
     const float cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i);
-    float fe = feq_dev<Q>(i, drho, u, usq);
-    if (WANT_S) {
-      float fn = f[i] - fe;
-      pxx += cx * cx * fn;
-      pxy += cx * cy * fn;
-      pyy += cy * cy * fn;
-      if (LT::D == 3) {
-        pxz += cx * cz * fn;
-        pyz += cy * cz * fn;
-        pzz += cz * cz * fn;
-      }
-    }
-    float F = 3.0f * LT::w(i) * rho * (cx * acc[0] + cy * acc[1] + cz * acc[2]);
-    f[i] = f[i] + om * (fe - f[i]) + F;
-  }
-  if (WANT_S) {
-    float s = -1.5f * om / rho;  // -omega / (2 rho c_s^2)
-    Sout[0] = s * pxx; Sout[1] = s * pxy; Sout[2] = s * pxz;
-    Sout[3] = s * pyy; Sout[4] = s * pyz; Sout[5] = s * pzz;
+    const float cu = cx * u[0] + cy * u[1] + cz * u[2];
+    const float cv = cx * v0 + cy * v1 + cz * v2;
+    const float P = LT::w(i) * (A + rho * (H * cu * cu - K));
+    const float R = LT::w(i) * r3 * cv;
+    f[i] = keep * f[i] + (P + R);
+    f[k] = keep * f[k] + (P - R);
   }
 }
 
@@ -61,9 +56,7 @@ __device__ __forceinline__ void lb_collide(float *f, float om, const float acc[3
 // higher cumulant relaxes with rate 1 to zero, so the post-collision central moments of
 // orders 3 to 6 are those of a Gaussian with the relaxed second moments (odd ones vanish;
 // even ones by Isserlis' theorem); the inverse passes give the populations.
-template <bool WANT_S>
-__device__ __forceinline__ void cumulant_collide27(float *f, float om, const float acc[3], float &drho, float u[3],
-                                                   float Sout[6]) {
+__device__ __forceinline__ void cumulant_collide27(float *f, float om, const float acc[3], float &drho, float u[3]) {
   using LT = Lat<27>;
   lb_moments<27>(f, drho, u);
   const float rho = 1.0f + drho, ir = 1.0f / rho;
@@ -84,11 +77,6 @@ __device__ __forceinline__ void cumulant_collide27(float *f, float om, const flo
   for (int p = 0; p < 9; ++p) fwd(m[p], m[9 + p], m[18 + p], u[0]);
   const float kxx = m[18] * ir, kyy = m[6] * ir, kzz = m[2] * ir;
   const float kxy = m[12] * ir, kxz = m[10] * ir, kyz = m[4] * ir;
-  if (WANT_S) {  // S = -(om / (2 rho c_s^2)) (central second moments - rho c_s^2 I), as for BGK
-    const float s = -1.5f * om;
-    Sout[0] = s * (kxx - CS2); Sout[1] = s * kxy; Sout[2] = s * kxz;
-    Sout[3] = s * (kyy - CS2); Sout[4] = s * kyz; Sout[5] = s * (kzz - CS2);
-  }
   const float r1 = 1.0f - om;
   const float dxy = r1 * (kxx - kyy), dxz = r1 * (kxx - kzz);
   const float sxx = (1.0f + dxy + dxz) * (1.0f / 3.0f), syy = sxx - dxy, szz = sxx - dxz;
@@ -125,17 +113,62 @@ __device__ __forceinline__ void cumulant_collide27(float *f, float om, const flo
   }
 }
 
+// drho, u and the strain rate of an interface cell's pre-collision populations, kept for the
+// interface condition (Eq. bb_cc, Sdecomp) in the finest-level macro planes (drho, u[D], S):
+// S = -(om / (2 rho c_s^2)) sum_i c_i c_i (f_i - feq_i).  In deviation form the equilibrium's
+// second moments are sum_i c_a c_b f~eq_i = drho c_s^2 delta_ab + rho u_a u_b, for the BGK
+// equilibrium and for the cumulant model's Gaussian alike, so no per-population feq is needed.
+// fi(i) returns pre-collision population i (from the stage or buffer A).
+template <int Q, typename Ld>
+__device__ __forceinline__ void store_iface_macro(const Ctx &C, long long fc, Ld fi, float om) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  float d = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pxy = 0, pxz = 0, pyy = 0, pyz = 0, pzz = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float cx = LT::cx(i), cy = LT::cy(i), cz = LT::cz(i), v = fi(i);
+    d += v;
+    jx += cx * v;
+    jy += cy * v;
+    pxx += cx * cx * v;
+    pxy += cx * cy * v;
+    pyy += cy * cy * v;
+    if (D == 3) {
+      jz += cz * v;
+      pxz += cx * cz * v;
+      pyz += cy * cz * v;
+      pzz += cz * cz * v;
+    }
+  }
+  const float drho = d, inv = 1.0f / (1.0f + d);
+  const float u[3] = {jx * inv, jy * inv, jz * inv};
+  const float rho = 1.0f + drho, s = -1.5f * om / rho, iso = CS2 * drho;
+  const long long NF = C.nfine;
+  float *M = C.macro;
+  M[fc] = drho;
+  for (int a = 0; a < D; ++a) M[(1 + a) * NF + fc] = u[a];
+  const float sxx = s * (pxx - iso - rho * u[0] * u[0]), sxy = s * (pxy - rho * u[0] * u[1]);
+  const float syy = s * (pyy - iso - rho * u[1] * u[1]);
+  if (D == 2) {
+    M[3 * NF + fc] = sxx; M[4 * NF + fc] = sxy; M[5 * NF + fc] = syy;
+  } else {
+    M[4 * NF + fc] = sxx; M[5 * NF + fc] = sxy; M[6 * NF + fc] = s * (pxz - rho * u[0] * u[2]);
+    M[7 * NF + fc] = syy; M[8 * NF + fc] = s * (pyz - rho * u[1] * u[2]);
+    M[9 * NF + fc] = s * (pzz - iso - rho * u[2] * u[2]);
+  }
+}
+
 // The cell's phase operator: BGK, or on D3Q27 the cumulant model where the level asks for it.
-template <int Q, bool WANT_S>
+template <int Q>
 __device__ __forceinline__ void collide_phase(float *f, float om, const float acc[3], float &drho, float u[3],
-                                              float Sout[6], bool cumulant) {
+                                              bool cumulant) {
   if constexpr (Q == 27) {
     if (cumulant) {
-      cumulant_collide27<WANT_S>(f, om, acc, drho, u, Sout);
+      cumulant_collide27(f, om, acc, drho, u);
       return;
     }
   }
-  lb_collide<Q, WANT_S>(f, om, acc, drho, u, Sout);
+  lb_collide<Q>(f, om, acc, drho, u);
 }
 
 // ------------------------------------------------------------------ init
@@ -195,29 +228,20 @@ __global__ void __launch_bounds__(512, (Q == 27 ? 1 : LSB_CS_MINB)) k_collide_st
     const unsigned N = (unsigned)L.ncell;
     const T *__restrict__ A = fA<T, Q>(C, L);
     T *__restrict__ B = fB<T, Q>(C, L);
+    const int ph = tg & TAG_GAS;
+    const bool fine = L.finest != 0;
+    if (fine && (tg & TAG_IFACE)) {  // before the populations are held in registers
+      const T *A2;  // an opaque copy: these loads are not reused for f below
+      asm("mov.b64 %0, %1;" : "=l"(A2) : "l"(A));
+      store_iface_macro<Q>(C, L.fine_off + c, [&](int i) { return Store<T>::ld(A2 + (i * N + c), C.fp16_inv); },
+                           L.omega[ph]);
+    }
     float f[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) f[i] = Store<T>::ld(A + (i * N + c), C.fp16_inv);
-    const int ph = tg & TAG_GAS;
     const float acc[3] = {L.acc[ph][0], L.acc[ph][1], L.acc[ph][2]};
-    float drho, u[3], Sm[6];
-    const bool fine = L.finest != 0;
-    if (fine && (C.bflag[gb] & BF_BAND)) {
-      collide_phase<Q, true>(f, L.omega[ph], acc, drho, u, Sm, L.cumulant[ph]);
-      const long long fc = L.fine_off + c;
-      const long long NF = C.nfine;
-      float *M = C.macro;
-      M[fc] = drho;
-      for (int a = 0; a < D; ++a) M[(1 + a) * NF + fc] = u[a];
-      if (D == 2) {
-        M[3 * NF + fc] = Sm[0]; M[4 * NF + fc] = Sm[1]; M[5 * NF + fc] = Sm[3];
-      } else {
-        M[4 * NF + fc] = Sm[0]; M[5 * NF + fc] = Sm[1]; M[6 * NF + fc] = Sm[2];
-        M[7 * NF + fc] = Sm[3]; M[8 * NF + fc] = Sm[4]; M[9 * NF + fc] = Sm[5];
-      }
-    } else {
-      collide_phase<Q, false>(f, L.omega[ph], acc, drho, u, Sm, L.cumulant[ph]);
-    }
+    float drho, u[3];
+    collide_phase<Q>(f, L.omega[ph], acc, drho, u, L.cumulant[ph]);
     // per-axis neighbour offsets and wall flags
     const bool wxm = x == 0 && !L.per[0], wxp = x == n0 - 1 && !L.per[0];
     const bool wym = y == 0 && !L.per[1], wyp = y == n1 - 1 && !L.per[1];
@@ -291,11 +315,16 @@ __global__ void __launch_bounds__(512, (Q == 27 ? 1 : LSB_CS_MINB)) k_collide_st
 // ------------------------------------------------------------------ collide + stream, TMA-staged
 // Same update as k_collide_stream, with the A populations of each block
 // brought into shared memory by one TMA tensor load (a box of
-// bs0 x bs1 x bs2 cells x Q populations), double buffered: while a CTA
-// collides block w, the load of its next block is in flight.  Persistent CTAs
-// walk the work list; one thread issues the loads, every thread waits on the
-// stage's mbarrier with an iteration limit (on expiry the error word gets
-// ERR_TIMEOUT and the CTA stops).
+// bs0 x bs1 x bs2 cells x Q populations) into one of two stages.  When the
+// level's cell tags have a tensor map too (block rows of whole 16-byte units),
+// the block's tags come with the same stage, so no thread waits on a global
+// load before its collision.  Persistent CTAs walk the work list; one thread
+// issues the loads.  A stage is released as soon as every thread has copied its
+// populations into registers, and is refilled at once with the block after
+// next, so two loads per CTA are in flight while it collides and pushes.  Every
+// thread waits on the stage's mbarrier with an iteration limit; on expiry the
+// error word gets ERR_TIMEOUT and the whole CTA stops after a bounded wait for
+// its other load in flight.
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -320,6 +349,13 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const void *tmap, int c0,
       "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
       "[%6];" ::"r"(smem_u32(dst)),
       "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int c0, int c1, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(smem_u32(bar))
       : "memory");
 }
 __device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int c0, int c1, int c2, uint64_t *bar) {
@@ -348,33 +384,36 @@ __device__ __forceinline__ float stage_ld<__half>(const __half *p, float inv) {
 struct BlockMeta {
   long long cell_off, fine_off;
   unsigned ncell, p0, p01;
-  int gb, ld, level, x0, y0, z0, n0, n1, n2, finest, band, per[3], cum[2];
+  int gb, ld, level, x0, y0, z0, n0, n1, n2, finest, per[3], cum[2];
   float omega[2], acc[2][3];
 };
 
 template <int Q, typename T>
 __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape S, const int *__restrict__ list,
-                                                               int nlist, const CUtensorMap *__restrict__ tmaps) {
+                                                               int nlist, const CUtensorMap *__restrict__ tmaps,
+                                                               const CUtensorMap *__restrict__ tmaps_tag) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[2];
-  __shared__ BlockMeta meta[2];
+  __shared__ BlockMeta meta[4];  // iteration it uses meta[it & 3]; two blocks are staged ahead
   const int nt = blockDim.x;
+  const bool stag = tmaps_tag != nullptr;
   const unsigned stage_bytes = (unsigned)(Q * nt * sizeof(T));
-  const unsigned stage_stride = (stage_bytes + 127u) & ~127u;  // TMA destinations 128-byte aligned
+  const unsigned tag_off = (stage_bytes + 127u) & ~127u;  // TMA destinations 128-byte aligned
+  const unsigned stage_stride = (tag_off + nt + 127u) & ~127u;
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  // thread 0: publish block w's metadata into meta[st] and start its TMA load into stage st
-  auto issue = [&](int w, int st) {
+  // thread 0: publish block w's metadata into meta[ms] and start its TMA load into stage st
+  auto issue = [&](int w, int st, int ms) {
     const int gb = __ldg(list + w);
     const int4 bi = __ldg(C.blk_info + gb);
     const LevelDev &L = C.lds[bi.x];
-    BlockMeta &m = meta[st];
+    BlockMeta &m = meta[ms];
     m.gb = gb;
     m.ld = bi.x;
     m.level = L.level;
@@ -388,7 +427,6 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
     m.cell_off = L.cell_off;
     m.fine_off = L.fine_off;
     m.finest = L.finest;
-    m.band = L.finest ? (C.bflag[gb] & BF_BAND) : 0;
     for (int a = 0; a < 3; ++a) m.per[a] = L.per[a];
     for (int k = 0; k < 2; ++k) {
       m.cum[k] = L.cumulant[k];
@@ -397,60 +435,72 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
     }
     const CUtensorMap *tm = tmaps + 2 * bi.x + C.par[L.level];
     T *dst = reinterpret_cast<T *>(smem_raw + st * stage_stride);
-    mbar_expect_tx(&bar[st], stage_bytes);
+    mbar_expect_tx(&bar[st], stage_bytes + (stag ? (unsigned)nt : 0u));
     if (D == 3) tma_load_4d(dst, tm, m.x0, m.y0, m.z0, 0, &bar[st]);
     else tma_load_3d(dst, tm, m.x0, m.y0, 0, &bar[st]);
-  };
-  if (threadIdx.x == 0 && (int)blockIdx.x < nlist) issue(blockIdx.x, 0);
-  int it = 0;
-  for (int w = blockIdx.x; w < nlist; w += gridDim.x, ++it) {
-    const int st = it & 1;
-    if (threadIdx.x == 0 && w + (int)gridDim.x < nlist) issue(w + gridDim.x, st ^ 1);
-    unsigned spins = 0;
-    while (!mbar_try_wait(&bar[st], (it >> 1) & 1)) {
-      if (++spins > kWaitLimit) {
-        atomicOr(C.err, ERR_TIMEOUT);
-        return;
-      }
+    if (stag) {
+      unsigned char *tdst = smem_raw + st * stage_stride + tag_off;
+      if (D == 3) tma_load_3d(tdst, tmaps_tag + bi.x, m.x0, m.y0, m.z0, &bar[st]);
+      else tma_load_2d(tdst, tmaps_tag + bi.x, m.x0, m.y0, &bar[st]);
     }
-    do {
-      const BlockMeta &m = meta[st];
-      const int t = threadIdx.x;
-      const int x = m.x0 + (t & (S.bs[0] - 1));
-      const int y = m.y0 + ((t >> S.lg[0]) & (S.bs[1] - 1));
-      const int z = m.z0 + (t >> (S.lg[0] + S.lg[1]));
-      const int n0 = m.n0, n1 = m.n1, n2 = m.n2;
-      if (x >= n0 || y >= n1 || z >= n2) break;
-      const unsigned p0 = m.p0, p01 = m.p01;
-      const unsigned c = x + p0 * y + p01 * z;
-      const uint8_t tg = C.tag[m.cell_off + c];
-      if (!(tg & (TAG_LEAF | TAG_RLAYER))) break;
-      const unsigned N = m.ncell;
-      T *__restrict__ B = reinterpret_cast<T *>(C.buf[1 - C.par[m.level]]) + m.cell_off * Q;
+  };
+  const int G = gridDim.x;
+  if (threadIdx.x == 0) {
+    if ((int)blockIdx.x < nlist) issue(blockIdx.x, 0, 0);
+    if ((int)blockIdx.x + G < nlist) issue(blockIdx.x + G, 1, 1);
+  }
+  // bounded wait for the load of iteration j (stage j & 1, its (j >> 1)-th use)
+  auto wait_stage = [&](int j) {
+    for (unsigned spins = 0; !mbar_try_wait(&bar[j & 1], (j >> 1) & 1);)
+      if (++spins > kWaitLimit) return false;
+    return true;
+  };
+  int it = 0;
+  for (int w = blockIdx.x; w < nlist; w += G, ++it) {
+    const int st = it & 1;
+    const bool ok = wait_stage(it);
+    const BlockMeta &m = meta[it & 3];
+    const int t = threadIdx.x;
+    const int x = m.x0 + (t & (S.bs[0] - 1));
+    const int y = m.y0 + ((t >> S.lg[0]) & (S.bs[1] - 1));
+    const int z = m.z0 + (t >> (S.lg[0] + S.lg[1]));
+    const int n0 = m.n0, n1 = m.n1, n2 = m.n2;
+    const unsigned p0 = m.p0, p01 = m.p01;
+    const unsigned c = x + p0 * y + p01 * z;
+    bool act = ok && x < n0 && y < n1 && z < n2;
+    uint8_t tg = 0;
+    if (act) {
+      tg = stag ? smem_raw[st * stage_stride + tag_off + t] : C.tag[m.cell_off + c];
+      act = (tg & (TAG_LEAF | TAG_RLAYER)) != 0;
+    }
+    const int ph = tg & TAG_GAS;
+    const bool cut = act && m.finest && (tg & TAG_IFACE);
+    float f[Q];
+    if (act) {
       const T *sp = reinterpret_cast<const T *>(smem_raw + st * stage_stride);
-      float f[Q];
+      if (cut)  // before the populations are held in registers
+        store_iface_macro<Q>(C, m.fine_off + c, [&](int i) { return stage_ld<T>(sp + i * nt + t, C.fp16_inv); },
+                             m.omega[ph]);
 #pragma unroll
       for (int i = 0; i < Q; ++i) f[i] = stage_ld<T>(sp + i * nt + t, C.fp16_inv);
-      const int ph = tg & TAG_GAS;
-      const float acc[3] = {m.acc[ph][0], m.acc[ph][1], m.acc[ph][2]};
-      float drho, u[3], Sm[6];
-      if (m.band) {
-        collide_phase<Q, true>(f, m.omega[ph], acc, drho, u, Sm, m.cum[ph]);
-        const long long fc = m.fine_off + c;
-        const long long NF = C.nfine;
-        float *M = C.macro;
-        M[fc] = drho;
-        for (int a = 0; a < D; ++a) M[(1 + a) * NF + fc] = u[a];
-        if (D == 2) {
-          M[3 * NF + fc] = Sm[0]; M[4 * NF + fc] = Sm[1]; M[5 * NF + fc] = Sm[3];
-        } else {
-          M[4 * NF + fc] = Sm[0]; M[5 * NF + fc] = Sm[1]; M[6 * NF + fc] = Sm[2];
-          M[7 * NF + fc] = Sm[3]; M[8 * NF + fc] = Sm[4]; M[9 * NF + fc] = Sm[5];
-        }
-      } else {
-        collide_phase<Q, false>(f, m.omega[ph], acc, drho, u, Sm, m.cum[ph]);
+    }
+    // every thread holds its populations: stage st takes the block after next
+    if (__syncthreads_or(!ok)) {  // a load never arrived: drain the other one in flight, stop
+      if (t == 0) {
+        atomicOr(C.err, ERR_TIMEOUT);
+        if (w + G < nlist) wait_stage(it + 1);
       }
-      const bool cut = m.finest && (tg & TAG_IFACE);
+      return;
+    }
+    if (t == 0 && w + 2 * G < nlist) issue(w + 2 * G, st, (it + 2) & 3);
+    do {
+      if (!act) break;
+
+      const unsigned N = m.ncell;
+      T *__restrict__ B = reinterpret_cast<T *>(C.buf[1 - C.par[m.level]]) + m.cell_off * Q;
+      const float acc[3] = {m.acc[ph][0], m.acc[ph][1], m.acc[ph][2]};
+      float drho, u[3];
+      collide_phase<Q>(f, m.omega[ph], acc, drho, u, m.cum[ph]);
       const bool wxm = x == 0 && !m.per[0], wxp = x == n0 - 1 && !m.per[0];
       const bool wym = y == 0 && !m.per[1], wyp = y == n1 - 1 && !m.per[1];
       const bool wzm = D == 3 && z == 0 && !m.per[2], wzp = D == 3 && z == n2 - 1 && !m.per[2];
@@ -521,7 +571,6 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
       if (!m.finest && (tg & TAG_CCUT)) push(std::true_type{});
       else push(std::false_type{});
     } while (false);
-    __syncthreads();  // stage st and meta[st] are refilled one iteration from now
   }
 }
 
@@ -986,9 +1035,9 @@ __global__ void k_ghost_cells(Ctx C, const int2 *cells, int n, float theta) {
     const long long cpar = cidx(Lc, x >> 1, y >> 1, D == 3 ? (z >> 1) : 0);
     const int ph = C.tag[Lc.cell_off + cpar] & TAG_GAS;
     rescale_neq<Q>(f, F.tau[ph] / (2.0f * Lc.tau[ph]));
-    float drho, u[3], Sm[6];
+    float drho, u[3];
     const float acc[3] = {F.acc[ph][0], F.acc[ph][1], F.acc[ph][2]};
-    collide_phase<Q, false>(f, F.omega[ph], acc, drho, u, Sm, F.cumulant[ph]);
+    collide_phase<Q>(f, F.omega[ph], acc, drho, u, F.cumulant[ph]);
     T *Bf = fB<T, Q>(C, F);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -1068,8 +1117,8 @@ cudaError_t run_collide_stream(int Q, int st, Launch L, Ctx C, BlockShape S, con
 }
 // Dynamic shared memory of the TMA-staged kernel: two stages of Q x block cells.
 size_t tma_smem_bytes(int Q, int st, int nthreads) {
-  const size_t stage = (size_t)Q * nthreads * (st == 0 ? 4 : 2);
-  return 2 * ((stage + 127) & ~size_t(127));
+  const size_t stage = ((size_t)Q * nthreads * (st == 0 ? 4 : 2) + 127) & ~size_t(127);
+  return 2 * ((stage + nthreads + 127) & ~size_t(127));  // populations, then the block's tags
 }
 // Raise the kernel's dynamic shared-memory limit (once, outside any capture) and
 // report how many CTAs of nthreads fit on one SM.
@@ -1089,9 +1138,10 @@ cudaError_t prepare_collide_stream_tma(int Q, int st, int nthreads, int *ctas_pe
   return e;
 }
 cudaError_t run_collide_stream_tma(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n,
-                                   const CUtensorMap *tmaps) {
+                                   const CUtensorMap *tmaps, const CUtensorMap *tmaps_tag) {
   const size_t smem = tma_smem_bytes(Q, st, L.block);
-  LSB_QT(Q, st, (k_collide_stream_tma<Q_, T_><<<L.grid, L.block, smem, L.stream>>>(C, S, list, n, tmaps)));
+  LSB_QT(Q, st,
+         (k_collide_stream_tma<Q_, T_><<<L.grid, L.block, smem, L.stream>>>(C, S, list, n, tmaps, tmaps_tag)));
 }
 cudaError_t run_interface_bc(int Q, int st, Launch L, Ctx C, int glevel) {
   LSB_QT(Q, st, (LK(k_interface_bc)(C, glevel)));
