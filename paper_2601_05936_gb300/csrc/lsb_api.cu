@@ -2040,12 +2040,26 @@ lsb_status collect_cells(lsb_grid *g) {
       CU(cudaMemcpyAsync(&n, g->d_count, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
       CU(cudaStreamSynchronize(g->stream));
       cl.n = std::min(n, cl.cap);
-      // the atomics append in arbitrary order: sort by (level, cell) so that neighbouring
-      // threads work on neighbouring cells (shared coarse parents and pushes in L1/L2)
+      // the atomics append in arbitrary order: sort so that neighbouring threads work on
+      // neighbouring cells.  Restriction cells: by (level, cell).  Ghost cells: by (level,
+      // coarse parent, position in the parent), so that the up to 2^D fine cells
+      // interpolated from the same coarse cells sit in adjacent lanes.
       if (cl.n > 1) {
         std::vector<int2> h(cl.n);
         CU(cudaMemcpy(h.data(), cl.d, sizeof(int2) * cl.n, cudaMemcpyDeviceToHost));
-        std::sort(h.begin(), h.end(), [](const int2 &a, const int2 &b) { return a.x != b.x ? a.x < b.x : a.y < b.y; });
+        if (kind == 0) {
+          auto key = [g](const int2 &a) {
+            const LevelDev &L = g->lds[a.x];
+            const unsigned long long c = (unsigned)a.y, p0 = L.p[0], p1 = L.p[1];
+            const unsigned long long x = c % p0, y = (c / p0) % p1, z = c / (p0 * p1);
+            const unsigned long long par = (x >> 1) + (p0 >> 1) * ((y >> 1) + (p1 >> 1) * (z >> 1));
+            return ((unsigned long long)a.x << 56) | (par << 3) | ((z & 1) << 2) | ((y & 1) << 1) | (x & 1);
+          };
+          std::sort(h.begin(), h.end(), [&](const int2 &a, const int2 &b) { return key(a) < key(b); });
+        } else {
+          std::sort(h.begin(), h.end(),
+                    [](const int2 &a, const int2 &b) { return a.x != b.x ? a.x < b.x : a.y < b.y; });
+        }
         CU(cudaMemcpy(cl.d, h.data(), sizeof(int2) * cl.n, cudaMemcpyHostToDevice));
       }
     }
