@@ -278,6 +278,8 @@ def main():
                          "case II, the smallest measured stable; BGK in both phases is unstable at the "
                          "paper's Re = 35, tau = 0.563, where the paper's gas solver is a cumulant model)")
     ap.add_argument("--checkpoint-every", type=int, default=100)
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch every kernel from the host instead of replaying captured CUDA graphs")
     ap.add_argument("--driver", type=int, default=0, choices=[0, 1],
                     help="level-set passes: 0 one launch each, 1 one persistent cooperative launch per finest step")
     ap.add_argument("--scale", type=float, default=1.0,
@@ -335,13 +337,14 @@ def main():
     stream = torch.cuda.Stream()
     g = lsb.Grid(cases, stream=stream, device=local)
     g.set_driver(args.driver)
+    graphs = not args.no_graphs and args.driver == 0
+    g.use_graphs(graphs)  # two coarse steps per graph replay; the warm-up captures them
     g.step(args.warmup)
     g.sync()
 
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
-    g.profile(2 if args.profile_all else 1)
     launches0 = g.kernel_launches()
     upd0 = g.cell_updates(total=True)
     barrier()
@@ -354,11 +357,21 @@ def main():
     torch.cuda.synchronize()
     barrier()
     ms = ev0.elapsed_time(ev1)
+    launches = g.kernel_launches() - launches0
+    upd = g.cell_updates(total=True) - upd0
+    # per-kernel times for the roofline: a second, shorter pass with an event pair around
+    # every launch (eager launches: per-launch events and graph replay exclude each other)
+    P = max(2, min(args.steps, 50))
+    g.profile(2 if args.profile_all else 1)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    g.step(P)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_p = ev0.elapsed_time(ev1)
     prof = g.profile_read()
     g.profile(0)
     clk = clocks.stop()
-    launches = g.kernel_launches() - launches0
-    upd = g.cell_updates(total=True) - upd0
     g.sync()
 
     ms_max, upd_sum = reduce_ranks(ms, upd, dist, "cuda")
@@ -385,10 +398,11 @@ def main():
                 frac=(achieved / hbm) if achieved else None, traffic=traffic, peak_source=src + " (hbm_gbs, of "
                 + src + ")", kernel="k_collide_stream", launches=cs_n,
                 bytes_per_launch=cs_bytes / max(cs_n, 1), avg_launch_ms=cs_ms / max(cs_n, 1),
-                share_of_step=cs_ms / ms if ms > 0 else None, per_level=per_level)
+                share_of_step=cs_ms / ms_p if ms_p > 0 else None, per_level=per_level,
+                timed_in=f"separate pass of {P} steps with per-launch events (eager launches)")
     if args.profile_all and rank == 0:
         for k, (kms, kn, kb) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
-            print(f"{k:20s} {kms:9.2f} ms {kn:7d} launches {100 * kms / ms:5.1f}%", file=sys.stderr)
+            print(f"{k:20s} {kms:9.2f} ms {kn:7d} launches {100 * kms / ms_p:5.1f}%", file=sys.stderr)
 
     # end to end through the public API with host buffers: parameters H2D, step, observables D2H
     import ctypes
@@ -426,6 +440,7 @@ def main():
                 dtype="f32" if args.storage == "fp32" else "f16-store/f32-compute", data="synthetic",
                 config=dict(workload=wname, lattice=lattice, levels=int(case["n_levels"]),
                             storage=args.storage, parallelism=f"replicas{world}", driver=args.driver,
+                            cuda_graphs=graphs,
                             cell_updates_per_step=upd / args.steps,
                             l2_flush=f"state {state_gb:.1f} GB (both buffers) >> 129 MB L2",
                             bubble=dict(centroid=[float(v) if np.isfinite(v) else None for v in obs["centroid"]],
