@@ -443,52 +443,94 @@ template <int D>
 __global__ void k_ext_iter(Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int mode) { d_ext_iter<D>(C, S, glevel, uin, uout, mode); }
 
 // The sweeps after the first (mode 3 of d_ext_iter: the same arithmetic in the same order)
-// as a lean kernel of its own: without the first sweep's path it fits in 32 registers, so
-// four CTAs of 512 stay resident per SM; its chain of dependent loads (band list, plan,
-// values, upwind neighbours) is latency-bound, which the occupancy hides.
+// as a lean kernel of its own.  Its chain of dependent loads (band list, block coordinates,
+// plan, values, upwind neighbours) is latency-bound and the band holds only a few blocks
+// per resident CTA, so each thread carries two blocks at once with their loads interleaved.
 template <int D>
-__global__ void __launch_bounds__(512, 3) k_ext_plan(Ctx C, BlockShape S, int glevel, const float *uin, float *uout) {
+__global__ void __launch_bounds__(512, 2) k_ext_plan(Ctx C, BlockShape S, int glevel, const float *__restrict__ uin,
+                                                     float *__restrict__ uout) {
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
   const int *lst = C.band_list + (long long)glevel * C.band_cap;
   const long long NF = C.nfine;
-  for (int w = blockIdx.x; w < nl; w += gridDim.x) {
-    int x, y, z;
-    const LevelDev &L = blk_cell(C, S, lst[w], threadIdx.x, x, y, z);
-    if (!L.ls_active || x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
-    const long long fo = L.fine_off, c = cidx(L, x, y, z);
-    const float *ui = uin + fo;
-    float *uo = uout + fo;
-    const uint8_t pf = C.plan_f[fo + c];
-    if (pf & 64) {
+  const int G = gridDim.x;
+  // each thread takes its cell in two band blocks per pass, with both blocks' dependent
+  // loads (list entry, block coordinates, plan, neighbours) issued side by side
+  constexpr int U = 2;
+  for (int w0 = blockIdx.x; w0 < nl; w0 += U * G) {
+    int gb[U];
 #pragma unroll
-      for (int b = 0; b < D; ++b) uo[b * NF + c] = ui[b * NF + c];
-      continue;
+    for (int k = 0; k < U; ++k) gb[k] = w0 + k * G < nl ? __ldg(lst + w0 + k * G) : -1;
+    int4 bi[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) bi[k] = gb[k] >= 0 ? __ldg(C.blk_info + gb[k]) : make_int4(-1, 0, 0, 0);
+    bool act[U];
+    long long fo[U], c[U];
+    int x[U], y[U], z[U];
+    uint8_t pf[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      act[k] = bi[k].x >= 0;
+      fo[k] = 0;
+      c[k] = 0;
+      x[k] = y[k] = z[k] = 0;
+      pf[k] = 64;
+      if (!act[k]) continue;
+      const LevelDev &L = C.lds[bi[k].x];
+      x[k] = (bi[k].y << S.lg[0]) + (threadIdx.x & (S.bs[0] - 1));
+      y[k] = (bi[k].z << S.lg[1]) + ((threadIdx.x >> S.lg[0]) & (S.bs[1] - 1));
+      z[k] = (bi[k].w << S.lg[2]) + (threadIdx.x >> (S.lg[0] + S.lg[1]));
+      act[k] = L.ls_active && x[k] < L.n[0] && y[k] < L.n[1] && z[k] < L.n[2];
+      if (!act[k]) continue;
+      fo[k] = L.fine_off;
+      c[k] = cidx(L, x[k], y[k], z[k]);
+      pf[k] = __ldg(C.plan_f + fo[k] + c[k]);
     }
-    float u0[3], acc[3] = {0.f, 0.f, 0.f};
+    float u0[U][3], un[U][D][3], va[U][3];
 #pragma unroll
-    for (int b = 0; b < D; ++b) u0[b] = ui[b * NF + c];
+    for (int k = 0; k < U; ++k) {
+      if (!act[k]) continue;
+      const float *ui = uin + fo[k];
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const float va = C.plan_v[a * NF + fo + c];
-      const int dir = (pf >> a) & 1 ? -1 : 1;
-      long long cn;
-      if (pf & 128) {  // box-boundary cell: the neighbour clamped or wrapped
-        const int nx = a == 0 ? clampwrap(L, 0, x + dir) : x;
-        const int ny = a == 1 ? clampwrap(L, 1, y + dir) : y;
-        const int nz = a == 2 ? clampwrap(L, 2, z + dir) : z;
-        cn = cidx(L, nx, ny, nz);
-      } else {
-        cn = c + dir * (a == 0 ? 1LL : (a == 1 ? (long long)L.p[0] : (long long)L.p[0] * L.p[1]));
-      }
-      const float *src = ((pf >> (3 + a)) & 1) ? ui : C.ut0 + fo;
+      for (int b = 0; b < D; ++b) u0[k][b] = __ldg(ui + b * NF + c[k]);
+      if (pf[k] & 64) continue;
+      const LevelDev &L = C.lds[bi[k].x];
 #pragma unroll
-      for (int b = 0; b < D; ++b) {
-        const float un = src[b * NF + cn];
-        acc[b] += va * (va > 0.f ? (u0[b] - un) : (un - u0[b]));
+      for (int a = 0; a < D; ++a) {
+        va[k][a] = __ldg(C.plan_v + a * NF + fo[k] + c[k]);
+        const int dir = (pf[k] >> a) & 1 ? -1 : 1;
+        long long cn;
+        if (pf[k] & 128) {  // box-boundary cell: the neighbour clamped or wrapped
+          const int nx = a == 0 ? clampwrap(L, 0, x[k] + dir) : x[k];
+          const int ny = a == 1 ? clampwrap(L, 1, y[k] + dir) : y[k];
+          const int nz = a == 2 ? clampwrap(L, 2, z[k] + dir) : z[k];
+          cn = cidx(L, nx, ny, nz);
+        } else {
+          cn = c[k] + dir * (a == 0 ? 1LL : (a == 1 ? (long long)L.p[0] : (long long)L.p[0] * L.p[1]));
+        }
+        const float *src = ((pf[k] >> (3 + a)) & 1) ? ui : C.ut0 + fo[k];
+#pragma unroll
+        for (int b = 0; b < D; ++b) un[k][a][b] = __ldg(src + b * NF + cn);
       }
     }
 #pragma unroll
-    for (int b = 0; b < D; ++b) uo[b * NF + c] = u0[b] - L.dtau_ext * acc[b];
+    for (int k = 0; k < U; ++k) {
+      if (!act[k]) continue;
+      float *uo = uout + fo[k];
+      if (pf[k] & 64) {  // outside the band: carried over
+#pragma unroll
+        for (int b = 0; b < D; ++b) uo[b * NF + c[k]] = u0[k][b];
+        continue;
+      }
+      float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b)
+          acc[b] += va[k][a] * (va[k][a] > 0.f ? (u0[k][b] - un[k][a][b]) : (un[k][a][b] - u0[k][b]));
+      const float dt = C.lds[bi[k].x].dtau_ext;
+#pragma unroll
+      for (int b = 0; b < D; ++b) uo[b * NF + c[k]] = u0[k][b] - dt * acc[b];
+    }
   }
 }
 
