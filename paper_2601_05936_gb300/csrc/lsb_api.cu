@@ -136,6 +136,9 @@ struct lsb_grid {
   std::vector<float *> rec_ckpt;  // state at the start of steps 0, every, 2 every, ...
   float *d_seg = nullptr;         // states of one recomputed segment
   int seg_cap = 0;
+  CUtensorMap *d_seg_tmaps = nullptr;  // per slot and level descriptor: that slot's populations
+  const CUtensorMap *tma_a = nullptr;  // population maps the next collide launches read (default d_tmaps)
+  void *encode_fn = nullptr;           // cuTensorMapEncodeTiled
   size_t seg_slot = 0;            // bytes per stored state
   float *d_adj[2] = {nullptr, nullptr};
   int adj_cur = -1;               // >= 0 once lsb_backward has run: dJ/df_0 is held in d_adj
@@ -565,7 +568,7 @@ lsb_status advance(lsb_grid *g, int l) {
     const int grid = std::min(g->cs[l].n, g->tma_grid);
     const CUtensorMap *tm = (const CUtensorMap *)g->d_tmaps;
     RUN(collide_kid(l), cs_bytes, g->cs[l].n, nt, run_collide_stream_tma, Q, st, LN(g, grid, nt), C, S, (const int *)g->cs[l].d,
-        g->cs[l].n, tm, g->tma_tags ? tm + 2 * g->lds.size() : nullptr);
+        g->cs[l].n, g->tma_a ? g->tma_a : tm, g->tma_tags ? tm + 2 * g->lds.size() : nullptr);
   } else {
     RUN(collide_kid(l), cs_bytes, g->cs[l].n, nt, run_collide_stream, Q, st, LN(g, g->cs[l].n, nt), C, S, (const int *)g->cs[l].d,
         g->cs[l].n);
@@ -658,6 +661,35 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// The (x, y, [z,] q) view of level L's populations in the state array at buf, with a box of
+// one block x all Q populations.
+bool encode_pop_map(const lsb_grid *g, EncodeTiledFn encode, void *buf, const LevelDev &L, CUtensorMap *out) {
+  const size_t es = g->storage == LSB_FP32 ? 4 : 2;
+  const CUtensorMapDataType dt =
+      g->storage == LSB_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  char *base = static_cast<char *>(buf) + (size_t)L.cell_off * g->Q * es;
+  cuuint64_t dims[4], strides[3];
+  cuuint32_t box[4], estr[4] = {1, 1, 1, 1};
+  cuuint32_t rank;
+  if (g->D == 3) {
+    rank = 4;
+    dims[0] = L.p[0]; dims[1] = L.p[1]; dims[2] = L.p[2]; dims[3] = g->Q;
+    strides[0] = (cuuint64_t)L.p[0] * es;
+    strides[1] = (cuuint64_t)L.p[0] * L.p[1] * es;
+    strides[2] = (cuuint64_t)L.ncell * es;
+    box[0] = g->bs[0]; box[1] = g->bs[1]; box[2] = g->bs[2]; box[3] = g->Q;
+  } else {
+    rank = 3;
+    dims[0] = L.p[0]; dims[1] = L.p[1]; dims[2] = g->Q;
+    strides[0] = (cuuint64_t)L.p[0] * es;
+    strides[1] = (cuuint64_t)L.ncell * es;
+    box[0] = g->bs[0]; box[1] = g->bs[1]; box[2] = g->Q;
+  }
+  return encode(out, dt, rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 lsb_status build_tensor_maps(lsb_grid *g) {
   void *fn = nullptr;
   cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
@@ -670,36 +702,12 @@ lsb_status build_tensor_maps(lsb_grid *g) {
   const size_t es = g->storage == LSB_FP32 ? 4 : 2;
   // A box row must be whole 16-byte units: then every block's x origin is 16-byte aligned too.
   if ((g->bs[0] * es) % 16 != 0 || g->bs[0] > 256 || g->bs[1] > 256 || g->bs[2] > 256) return LSB_OK;
-  const CUtensorMapDataType dt =
-      g->storage == LSB_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   const bool tags = g->bs[0] % 16 == 0;  // tag rows of whole 16-byte units (cell_off, p[0] follow)
   std::vector<CUtensorMap> maps((tags ? 3 : 2) * g->lds.size());
   for (size_t ld = 0; ld < g->lds.size(); ++ld) {
     const LevelDev &L = g->lds[ld];
-    for (int b = 0; b < 2; ++b) {
-      char *base = static_cast<char *>(g->d_buf[b]) + (size_t)L.cell_off * g->Q * es;
-      cuuint64_t dims[4], strides[3];
-      cuuint32_t box[4], estr[4] = {1, 1, 1, 1};
-      cuuint32_t rank;
-      if (g->D == 3) {
-        rank = 4;
-        dims[0] = L.p[0]; dims[1] = L.p[1]; dims[2] = L.p[2]; dims[3] = g->Q;
-        strides[0] = (cuuint64_t)L.p[0] * es;
-        strides[1] = (cuuint64_t)L.p[0] * L.p[1] * es;
-        strides[2] = (cuuint64_t)L.ncell * es;
-        box[0] = g->bs[0]; box[1] = g->bs[1]; box[2] = g->bs[2]; box[3] = g->Q;
-      } else {
-        rank = 3;
-        dims[0] = L.p[0]; dims[1] = L.p[1]; dims[2] = g->Q;
-        strides[0] = (cuuint64_t)L.p[0] * es;
-        strides[1] = (cuuint64_t)L.ncell * es;
-        box[0] = g->bs[0]; box[1] = g->bs[1]; box[2] = g->Q;
-      }
-      CUresult r = encode(&maps[2 * ld + b], dt, rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) return LSB_OK;  // keep the plain kernel
-    }
+    for (int b = 0; b < 2; ++b)
+      if (!encode_pop_map(g, encode, g->d_buf[b], L, &maps[2 * ld + b])) return LSB_OK;  // keep the plain kernel
     if (tags) {
       cuuint64_t dims[3] = {(cuuint64_t)L.p[0], (cuuint64_t)L.p[1], (cuuint64_t)L.p[2]};
       cuuint64_t strides[2] = {(cuuint64_t)L.p[0], (cuuint64_t)L.p[0] * L.p[1]};
@@ -722,6 +730,7 @@ lsb_status build_tensor_maps(lsb_grid *g) {
   CU(cudaMemcpy(g->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
   g->tma_grid = per_sm * nsm;
   g->tma_tags = tags;
+  g->encode_fn = fn;
   return LSB_OK;
 }
 
@@ -880,6 +889,7 @@ lsb_status adj_buffers(lsb_grid *g, int seg_len) {
   const size_t slb = sizeof(float) * slot_floats(g);
   if (seg_len > g->seg_cap || g->seg_slot != slb) {
     if (g->d_seg) cudaFree(g->d_seg);
+  if (g->d_seg_tmaps) cudaFree(g->d_seg_tmaps);
     g->d_seg = nullptr;
     g->seg_cap = 0;
     cudaError_t e = cudaMalloc(&g->d_seg, slb * (size_t)seg_len);
@@ -887,6 +897,26 @@ lsb_status adj_buffers(lsb_grid *g, int seg_len) {
                                       cudaGetErrorString(e));
     g->seg_cap = seg_len;
     g->seg_slot = slb;
+    // tensor maps of every slot (both parity entries name the slot), so that the
+    // recomputation reads its slots through the TMA-staged collide kernel
+    if (g->d_seg_tmaps) cudaFree(g->d_seg_tmaps);
+    g->d_seg_tmaps = nullptr;
+    if (g->d_tmaps && g->encode_fn) {
+      const size_t nld = g->lds.size();
+      std::vector<CUtensorMap> maps(2 * nld * (size_t)seg_len);
+      bool ok = true;
+      for (int j = 0; j < seg_len && ok; ++j)
+        for (size_t ld = 0; ld < nld && ok; ++ld) {
+          CUtensorMap *m = &maps[(j * nld + ld) * 2];
+          ok = encode_pop_map(g, reinterpret_cast<EncodeTiledFn>(g->encode_fn), g->d_seg + slot_floats(g) * j,
+                              g->lds[ld], m);
+          m[1] = m[0];
+        }
+      if (ok && cudaMalloc(&g->d_seg_tmaps, sizeof(CUtensorMap) * maps.size()) == cudaSuccess)
+        CU(cudaMemcpy(g->d_seg_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
+      else
+        cudaGetLastError();
+    }
   }
   if (g->rec_moving) {
     const size_t need = lsa_floats_needed(g);
@@ -1850,9 +1880,12 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
     if (e != cudaSuccess) { st = fail(g, LSB_ECUDA, "checkpoint restore: %s", cudaGetErrorString(e)); break; }
     // the interface geometry (n, kappa) the first step uses is that of the restored phi
     if (mv && (st = classify(g, 0, 0)) != LSB_OK) break;
-    g->no_tma = 1;  // the TMA tensor maps describe the grid buffers, not the slots
+    // the grid's tensor maps describe its own buffers: the slots have maps of their own,
+    // else the plain collide kernel runs
+    if (!g->d_seg_tmaps) g->no_tma = 1;
     for (int j = 0; j < len && st == LSB_OK; ++j) {
       float *slot = g->d_seg + sl * j;
+      if (g->d_seg_tmaps) g->tma_a = g->d_seg_tmaps + (size_t)j * 2 * g->lds.size();
       if (mv) {
         e = cudaMemcpyAsync(slot + sf, g->d_phi, sizeof(float) * NF, cudaMemcpyDeviceToDevice, g->stream);
         if (e == cudaSuccess)
@@ -1864,6 +1897,7 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
       st = advance(g, 0);
     }
     g->no_tma = 0;
+    g->tma_a = nullptr;
     g->d_buf[0] = bufs[0];
     g->d_buf[1] = bufs[1];
     for (int j = len - 1; j >= 0 && st == LSB_OK; --j) {
