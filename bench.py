@@ -260,7 +260,7 @@ def main():
     ap.add_argument("--workload", default="bubble3d",
                     choices=["bubble3d", "box3d", "ensemble", "adjoint3d", "adjoint3d_ls", "adjoint3d_amr",
                              "adjoint3d_amr_ls",
-                             "paper3d", "couette2d"],
+                             "paper3d", "couette2d", "cluster3d"],
                     help="bubble3d: the benchmark configuration; box3d: uniform periodic 128^3 box "
                          "(collide-and-stream only, for profiling captures); ensemble: 64 uneven 2D bubbles; "
                          "adjoint3d: reverse sweep over --steps recorded steps of a frozen 3D bubble; "
@@ -268,7 +268,8 @@ def main():
                          "adjoint3d_amr: the frozen adjoint on the two-level grid of bubble3d; "
                          "adjoint3d_amr_ls: the same with the finest level's level set moving; "
                          "paper3d: the paper's own 3D box (2d x 2d x 4d, d = 64, uniform, slip lateral walls, "
-                         "case --paper-case); couette2d: two-layer Couette with a moving wall, 2048^2")
+                         "case --paper-case); couette2d: two-layer Couette with a moving wall, 2048^2; cluster3d: nine "
+                         "rising bubbles (case I) in a 10 d x 10 d x 20 d box, d = 32 finest cells, 2 levels")
     ap.add_argument("--paper-case", default="I", choices=["I", "II"], help="paper3d: parameter set of Sec. 3.2")
     ap.add_argument("--lattice", default="D3Q19", choices=["D3Q19", "D3Q27"],
                     help="paper3d: D3Q19 with BGK in both phases, or the paper's own 3D setup: D3Q27 with BGK "
@@ -324,6 +325,9 @@ def main():
         coll = ("bgk", "cumulant") if args.lattice == "D3Q27" else ("bgk", "bgk")
         case = workloads.paper_box_3d(args.paper_case, storage=args.storage, nu_floor=floor, lattice=args.lattice,
                                       collision=coll)
+        cases = [case]
+    elif args.workload == "cluster3d":
+        case = workloads.bubble_cluster_3d(d=32, levels=2, storage=args.storage)
         cases = [case]
     elif args.workload == "couette2d":
         case = workloads.two_layer_couette()

@@ -155,6 +155,41 @@ def paper_box_3d(case="I", d=64, levels=1, seed=4100, block=(32, 4, 4), storage=
                 Ma=prm["Ma"], Re_eff=prm["Re_eff"], p_gas0=2.0 * prm["sigma"] / (d / 2), **LS_DEFAULTS)
 
 
+def bubble_cluster_3d(case="I", d=16, levels=1, seed=4200, block=(32, 4, 4), storage="fp32", steps=2000,
+                      Ma=0.02, nu_floor=0.05, spacing=1.5, sensor="band", refine_dist=8.0, regrid_every=25):
+    """Cluster of nine rising bubbles (Sec. 3.2, last example): a box of 10 d x 10 d x 20 d
+    (z up, gravity along -z), bubble diameter d (finest cells), parameter set I, two layers
+    of five and four bubbles.  The paper gives neither the positions nor the walls; this
+    reading: lower layer at height 2 d with one bubble on the vertical axis and four on the
+    diagonals at (+-s, +-s), upper layer at height 2 d + s with four bubbles on the axes at
+    (+-s, 0) and (0, +-s), s = spacing x d (1.5 d: neighbouring bubbles 2.1 d apart), the
+    whole cluster shifted by a sub-cell offset from ``seed``; walls as in the single-bubble
+    box (slip lateral walls, no-slip top and bottom).  Levels and sensor as paper_box_3d."""
+    rng = np.random.default_rng(seed)
+    prm = bubble_params(float(d), Ma=Ma, nu_floor=nu_floor, **PAPER_CASES[case])
+    r = 2 ** (levels - 1)
+    nf = (10 * d, 10 * d, 20 * d)
+    base = tuple(n // r for n in nf)
+    assert all(b * r == n for b, n in zip(base, nf)), "box not divisible by the level ratio"
+    off = rng.random(3) * 0.5
+    cx, cy, s = 5.0 * d + off[0], 5.0 * d + off[1], spacing * d
+    z0 = 2.0 * d + off[2]
+    centres = [(cx, cy, z0)] + [(cx + a * s, cy + b * s, z0) for a in (-1, 1) for b in (-1, 1)]
+    centres += [(cx + a, cy + b, z0 + s) for a, b in ((-s, 0.0), (s, 0.0), (0.0, -s), (0.0, s))]
+    x, y, z = _grid_centers(nf)
+    phi = np.full(x.shape, -np.inf)
+    for c in centres:  # gas inside any bubble: the largest signed distance
+        phi = np.maximum(phi, 0.5 * d - np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2))
+    xr = tuple(float(v) for v in np.mean(np.asarray(centres), axis=0))
+    return dict(name=f"bubble_cluster_3d_case{case}_d{d}_L{levels}", lattice="D3Q19", base=base, n_levels=levels,
+                block=block, periodic=(False, False, False), slip=(True, True, False), rho_phys=prm["rho_phys"],
+                nu=prm["nu"], gravity=(0.0, 0.0, -prm["g"]), sigma=prm["sigma"], x_ref=xr,
+                phi0=phi.reshape(-1).astype(np.float32), refine_dist=[float(refine_dist)] * (levels - 1),
+                sensor=sensor, regrid_every=regrid_every if levels > 1 else 0, steps=steps, storage=storage,
+                fp16_scale=1024.0, Ma=prm["Ma"], Re_eff=prm["Re_eff"], p_gas0=2.0 * prm["sigma"] / (d / 2),
+                centres=centres, **LS_DEFAULTS)
+
+
 def two_layer_couette(nx=2048, ny=2048, h_frac=0.5 + 1.0 / 512, U=0.01, rho=(1.0, 0.1), eta_ratio=5.0, nu_heavy=0.1,
                       block=(32, 8), steps=1000):
     """Two-layer Couette flow (Sec. 3.1): the domain [0, 2] x [-1, 1] of the paper on an
