@@ -127,8 +127,8 @@ struct lsb_grid {
   CUtensorMap *d_tmaps = nullptr;
   int tma_grid = 0;
   int tma_tags = 0;               // d_tmaps also holds one cell-tag map per level descriptor
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  uint64_t gnodes[2] = {0, 0};
+  cudaGraphExec_t gexec[2][2] = {};  // [coarse steps per replay - 1][level-0 parity at the start]
+  uint64_t gnodes[2][2] = {};
   // adjoint of the frozen-interface step: recording and reverse sweep
   int rec_on = 0, rec_every = 0;
   int no_tma = 0;                 // recomputation writes into segment slots: plain collide kernel
@@ -735,11 +735,12 @@ lsb_status build_tensor_maps(lsb_grid *g) {
 }
 
 void drop_graphs(lsb_grid *g) {
-  for (int p = 0; p < 2; ++p)
-    if (g->gexec[p]) {
-      cudaGraphExecDestroy(g->gexec[p]);
-      g->gexec[p] = nullptr;
-    }
+  for (int k = 0; k < 2; ++k)
+    for (int p = 0; p < 2; ++p)
+      if (g->gexec[k][p]) {
+        cudaGraphExecDestroy(g->gexec[k][p]);
+        g->gexec[k][p] = nullptr;
+      }
 }
 
 // Graph replay needs a non-default stream, no kernel timing, and a fixed
@@ -748,46 +749,48 @@ bool graphs_usable(const lsb_grid *g) {
   return g->use_graphs && g->stream && g->prof_mode == 0 && g->reinit_every <= 1;
 }
 
-// Two coarse steps as one CUDA graph: every level's buffer parity returns to
-// its starting value, so the captured kernel arguments stay valid until the
-// next regrid rebuilds the work lists.
-lsb_status replay_two_steps(lsb_grid *g) {
-  const int p0 = g->par[0];
-  if (!g->gexec[p0]) {
+// One or two coarse steps as one CUDA graph, one graph per starting parity of
+// level 0.  A coarse step advances level l 2^l times, so every finer level's
+// parity is the same at the start of every coarse step and level 0's alone
+// alternates: the graph for (steps, level-0 parity) always meets the buffers it
+// was captured with, until the next regrid rebuilds the work lists.
+lsb_status replay_steps(lsb_grid *g, int nsteps) {
+  const int p0 = g->par[0], ks = nsteps - 1;
+  if (!g->gexec[ks][p0]) {
     int par[MAXL];
     long long fs[MAXL];
     std::copy(g->par, g->par + MAXL, par);
     std::copy(g->fine_steps, g->fine_steps + MAXL, fs);
     const uint64_t l0 = g->launches;
     CU(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
-    lsb_status s = advance(g, 0);
-    if (s == LSB_OK) s = advance(g, 0);
+    lsb_status s = LSB_OK;
+    for (int k = 0; k < nsteps && s == LSB_OK; ++k) s = advance(g, 0);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
     std::copy(par, par + MAXL, g->par);
     std::copy(fs, fs + MAXL, g->fine_steps);
-    g->gnodes[p0] = g->launches - l0;
+    g->gnodes[ks][p0] = g->launches - l0;
     g->launches = l0;
     if (s != LSB_OK) {
       if (graph) cudaGraphDestroy(graph);
       return s;
     }
     if (e != cudaSuccess) return fail(g, LSB_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&g->gexec[p0], graph, 0);
+    e = cudaGraphInstantiate(&g->gexec[ks][p0], graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(g, LSB_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
   }
-  CU(cudaGraphLaunch(g->gexec[p0], g->stream));
-  g->launches += g->gnodes[p0];
+  CU(cudaGraphLaunch(g->gexec[ks][p0], g->stream));
+  g->launches += g->gnodes[ks][p0];
   for (int l = 0; l < MAXL; ++l) {
-    // level l advances 2^(l+1) times in two coarse steps; its parity flips that often
-    const long long adv = 2LL << l;
+    // level l advances 2^l times per coarse step; its parity flips that often
+    const long long adv = (long long)nsteps << l;
     if (l < g->Lmax) {
       if (adv & 1) g->par[l] ^= 1;
       if (has_finest(g, l)) g->fine_steps[l] += adv;
     }
   }
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < nsteps; ++k) {
     g->updates_done += updates_per_step(g);
     g->coarse_steps++;
   }
@@ -1464,8 +1467,12 @@ lsb_status lsb_set_params(lsb_grid *g, int case_idx, const lsb_params *params) {
   if (params->n_ext != g->n_ext || params->reinit_every != g->reinit_every || params->n_reinit != g->n_reinit)
     if (g->ncase > 1 && case_idx != -1) return fail(g, LSB_EINVAL, "level-set iteration counts are shared by all cases");
   if (g->rec_on) rec_clear(g);  // a recording covers one parameter set
+  // captured graphs hold the launch sequence, which these decide on the host
+  bool relaunch = params->n_ext != g->n_ext || params->reinit_every != g->reinit_every ||
+                  params->n_reinit != g->n_reinit || params->regrid_every != g->regrid_every;
   for (int c = 0; c < g->ncase; ++c) {
     if (case_idx != -1 && c != case_idx) continue;
+    relaunch = relaunch || params->ls_active != g->cases[c].p.ls_active;
     g->cases[c].p = *params;
     for (int l = 0; l < g->cases[c].L; ++l) fill_physics(g, g->lds[g->cases[c].ld0 + l], g->cases[c]);
   }
@@ -1473,6 +1480,7 @@ lsb_status lsb_set_params(lsb_grid *g, int case_idx, const lsb_params *params) {
   g->reinit_every = params->reinit_every;
   g->n_reinit = params->n_reinit;
   g->regrid_every = params->regrid_every;
+  if (relaunch) drop_graphs(g);
   CU(cudaMemcpyAsync(g->d_lds, g->lds.data(), sizeof(LevelDev) * g->lds.size(), cudaMemcpyHostToDevice, g->stream));
   CU(cudaStreamSynchronize(g->stream));
   return LSB_OK;
@@ -1500,13 +1508,17 @@ lsb_status lsb_step(lsb_grid *g, int n) {
     const bool regrid_soon =
         regrid_on && ((g->coarse_steps + 1) % g->regrid_every == 0 || (g->coarse_steps + 2) % g->regrid_every == 0);
     if (n - k >= 2 && !regrid_soon && graphs_usable(g)) {
-      TRY(replay_two_steps(g));
+      TRY(replay_steps(g, 2));
       k += 2;
       continue;
     }
-    TRY(advance(g, 0));
-    g->updates_done += updates_per_step(g);
-    g->coarse_steps++;
+    if (graphs_usable(g)) {  // one step (a regrid, if due, follows it as after an eager step)
+      TRY(replay_steps(g, 1));
+    } else {
+      TRY(advance(g, 0));
+      g->updates_done += updates_per_step(g);
+      g->coarse_steps++;
+    }
     ++k;
     if (regrid_on && g->coarse_steps % g->regrid_every == 0) TRY(regrid(g, false));
   }

@@ -61,3 +61,43 @@ def test_set_driver_rejects_bad_mode():
     with pytest.raises(lsb.LsbError):
         g.set_driver(2)
     g.close()
+
+
+def test_single_step_graph_replay_matches_eager():
+    """lsb_step(1) calls replay one-step graphs (one per starting parity of level 0),
+    across a regrid and an odd total; a change of the level-set iteration counts through
+    lsb_set_params drops the graphs."""
+    import torch
+
+    from paper_2601_05936_gb300 import lsb
+    from tests.test_gpu_parity import _bubble2d
+    case = _bubble2d(N=64, R=6.0, levels=2, rr=100.0, nu=(0.06, 0.6), g=2e-5, sigma=2e-3)
+    case["refine_dist"] = [8.0]
+    case["regrid_every"] = 6
+
+    def run(graphs, one_at_a_time, change_at=None):
+        st = torch.cuda.Stream()
+        g = lsb.Grid(case, stream=st)
+        g.use_graphs(graphs)
+        for k in range(13):
+            if k == change_at:
+                c2 = dict(case, n_ext=6)
+                g.set_params(c2)
+            if one_at_a_time:
+                g.step(1)
+            elif k % 2 == 0:
+                g.step(2 if k < 12 else 1)
+        g.sync()
+        out = [g.get(f, 0, l) for l in range(2) for f in ("rho", "u")] + [g.get("phi"), g.get("tag")]
+        launches = g.kernel_launches()
+        g.close()
+        return out, launches
+
+    ref, n_ref = run(False, True)
+    for mode in (True, False):
+        got, n = run(True, mode)
+        _same(ref, got)
+        assert n == n_ref
+    ref2, _ = run(False, True, change_at=9)
+    got2, _ = run(True, True, change_at=9)
+    _same(ref2, got2)
