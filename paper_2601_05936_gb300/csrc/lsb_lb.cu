@@ -832,17 +832,22 @@ __global__ void k_observables(Ctx C, BlockShape S, const int *list, int nlist, d
   constexpr int D = LT::D;
   constexpr int NV = 4 + 2 * D;
   __shared__ double red[32][NV];
-  double v[NV];
-  for (int k = 0; k < NV; ++k) v[k] = 0.0;
+  // per-thread partials in FP32 over the thread's few cells, FP64 from the warp sum on:
+  // cell volumes, counts and centroid terms are integer-valued (exact in FP32 while a
+  // thread's sums stay below 2^24); mass is kept as volume + vol * drho with the small
+  // second part summed apart
+  float vol_ph[2] = {0.f, 0.f}, dm_ph[2] = {0.f, 0.f}, v[NV];
+  for (int k = 0; k < NV; ++k) v[k] = 0.f;
   int cur_case = -1;
   auto flush = [&](int case_id) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     for (int k = 0; k < NV; ++k) {
-      double s = v[k];
+      double s = k < 2 ? (double)vol_ph[k] + (double)dm_ph[k] : (double)v[k];
       for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
       if (lane == 0) red[warp][k] = s;
-      v[k] = 0.0;
+      v[k] = 0.f;
     }
+    vol_ph[0] = vol_ph[1] = dm_ph[0] = dm_ph[1] = 0.f;
     __syncthreads();
     if (threadIdx.x < NV) {
       double s = 0.0;
@@ -870,19 +875,20 @@ __global__ void k_observables(Ctx C, BlockShape S, const int *list, int nlist, d
         for (int i = 0; i < Q; ++i) f[i] = Store<T>::ld(A + i * L.ncell + c, C.fp16_inv);
         float drho, u[3];
         lb_moments<Q>(f, drho, u);
-        double vol = 1.0;
-        for (int a = 0; a < D; ++a) vol *= (double)L.scale;
+        float vol = 1.f;
+        for (int a = 0; a < D; ++a) vol *= (float)L.scale;
         const int gas = tg & TAG_GAS;
-        v[gas] += vol * (1.0 + (double)drho);
-        v[3] += 1.0;
+        vol_ph[gas] += vol;
+        dm_ph[gas] += vol * drho;
+        v[3] += 1.f;
         const bool finite = isfinite(drho) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
         if (!finite) atomicOr(C.err, ERR_NONFINITE);
         if (gas) {
           v[2] += vol;
           const int crd[3] = {x, y, z};
           for (int a = 0; a < D; ++a) {
-            v[4 + a] += vol * ((double)crd[a] + 0.5) * (double)L.scale;
-            v[4 + D + a] += vol * (double)u[a];
+            v[4 + a] += vol * ((float)crd[a] + 0.5f) * (float)L.scale;
+            v[4 + D + a] += vol * u[a];
           }
         }
       }

@@ -105,3 +105,19 @@ def test_graph_replay_matches_eager_bit_identical():
         g.close()
     for a, b in zip(*out):
         assert np.array_equal(a, b)
+
+
+def test_observables_match_oracle():
+    """The FP64 reductions (Sec. 3.2 observables) on the 3D two-level bubble's 32x32x64 copy:
+    gas volume and centroid exactly (integer-valued sums over identical phase masks), mass
+    per phase to the FP32 state's rounding, rise velocity to 1e-3 of its magnitude."""
+    from paper_2601_05936_gb300 import workloads
+    case = workloads.rising_bubble_3d(scale=0.25)
+    g, s = run_both(case, 10)
+    og, oo = g.observables()[0], s.observables()
+    assert og["volume"] == oo["volume"]
+    assert np.array_equal(og["centroid"], oo["centroid"]), (og["centroid"], oo["centroid"])
+    assert np.abs(og["mass"] / oo["mass"] - 1.0).max() < 1e-7, (og["mass"], oo["mass"])
+    vmag = np.abs(oo["velocity"]).max()
+    assert vmag > 0 and np.abs(og["velocity"] - oo["velocity"]).max() < 1e-3 * vmag, (og["velocity"], oo["velocity"])
+    g.close()
