@@ -149,11 +149,14 @@ lsb_status lsb_set_params(lsb_grid *g, int case_idx, const lsb_params *params);
 lsb_status lsb_step(lsb_grid *g, int n);
 
 /* Replay steps from CUDA graphs (enable = 1) instead of launching each kernel.
- * Two coarse steps are captured at a time (one graph per starting buffer
- * parity), re-captured after every regrid; steps next to a regrid, steps while
- * kernel timing is on, and handles whose reinitialisation period is above 1
- * run eagerly.  Needs the handle to use a non-default stream (LSB_EINVAL
- * otherwise).  Results are identical to eager stepping. */
+ * Graphs hold two coarse steps, or one for an odd remainder (so lsb_step(g, 1)
+ * replays too), one graph per level-0 buffer parity at the start; they are
+ * re-captured after every regrid and after an lsb_set_params call that
+ * changes the launch sequence (level-set iteration counts, regrid interval,
+ * level set on or off).  Two-step replays are not used across a regrid; steps
+ * while kernel timing is on and handles whose reinitialisation period is
+ * above 1 run eagerly.  Needs the handle to use a non-default stream
+ * (LSB_EINVAL otherwise).  Results are identical to eager stepping. */
 lsb_status lsb_use_graphs(lsb_grid *g, int enable);
 
 /*
