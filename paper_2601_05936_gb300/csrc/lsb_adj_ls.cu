@@ -191,10 +191,9 @@ template <int D>
 __global__ void k_lsa_mix(Ctx C, BlockShape S, int glevel, int mode, int use_frozen, const float *L3, float *L0,
                           float *L1, float *L2, const float *Ls0) {
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
-  const int *lst = C.band_list + (long long)glevel * C.band_cap;
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
     int x, y, z;
-    const LevelDev &L = blk_cell(C, S, lst[w], threadIdx.x, x, y, z);
+    const LevelDev &L = band_cell(C, S, glevel, w, threadIdx.x, x, y, z);
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long fc = L.fine_off + cidx(L, x, y, z);
     if (use_frozen && C.frozen[fc]) continue;
@@ -225,10 +224,9 @@ template <int D>
 __global__ void k_lsa_reinit_rt(Ctx C, BlockShape S, int glevel, const float *pin, const float *MU, float scale,
                                 float *Lt, float *L0, float *Ls0) {
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
-  const int *lst = C.band_list + (long long)glevel * C.band_cap;
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
     int x, y, z;
-    const LevelDev &L = blk_cell(C, S, lst[w], threadIdx.x, x, y, z);
+    const LevelDev &L = band_cell(C, S, glevel, w, threadIdx.x, x, y, z);
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long fo = L.fine_off;
     const long long fc = fo + cidx(L, x, y, z);
@@ -300,11 +298,10 @@ __global__ void k_lsa_adv_rt(Ctx C, BlockShape S, int glevel, const float *pin, 
                              float *Lt, float *L0, float *LU) {
   const float wm[7] = {-2.f / 60.f, 15.f / 60.f, -60.f / 60.f, 20.f / 60.f, 30.f / 60.f, -3.f / 60.f, 0.f};
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
-  const int *lst = C.band_list + (long long)glevel * C.band_cap;
   const long long NF = C.nfine;
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
     int x, y, z;
-    const LevelDev &L = blk_cell(C, S, lst[w], threadIdx.x, x, y, z);
+    const LevelDev &L = band_cell(C, S, glevel, w, threadIdx.x, x, y, z);
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long fo = L.fine_off;
     const long long fc = fo + cidx(L, x, y, z);
@@ -341,11 +338,10 @@ template <int D>
 __global__ void k_lsa_ext_T(Ctx C, BlockShape S, int glevel, const float *Sk, const float *S0, const float *Lin,
                             float *Lout, float *LOFF, float *LV) {
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
-  const int *lst = C.band_list + (long long)glevel * C.band_cap;
   const long long NF = C.nfine;
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
     int x, y, z;
-    const LevelDev &L = blk_cell(C, S, lst[w], threadIdx.x, x, y, z);
+    const LevelDev &L = band_cell(C, S, glevel, w, threadIdx.x, x, y, z);
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long fo = L.fine_off;
     const long long c = cidx(L, x, y, z);
@@ -390,11 +386,10 @@ __global__ void k_lsa_ext_T(Ctx C, BlockShape S, int glevel, const float *Sk, co
 template <int D>
 __global__ void k_lsa_ext_v(Ctx C, BlockShape S, int glevel, float *LV, float *LPHI) {
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
-  const int *lst = C.band_list + (long long)glevel * C.band_cap;
   const long long NF = C.nfine;
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
     int x, y, z;
-    const LevelDev &L = blk_cell(C, S, lst[w], threadIdx.x, x, y, z);
+    const LevelDev &L = band_cell(C, S, glevel, w, threadIdx.x, x, y, z);
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long fo = L.fine_off;
     const long long c = cidx(L, x, y, z);

@@ -93,6 +93,7 @@ struct lsb_grid {
   uint8_t *d_linkdir = nullptr;
   long long link_list_off[MAXL] = {0, 0, 0, 0};
   int *d_counters = nullptr, *d_err = nullptr, *d_band = nullptr;
+  int4 *d_band_info = nullptr;
   unsigned *d_bar = nullptr;  // grid barrier of the persistent level-set kernel
   int driver = 0;             // 0: one launch per level-set pass, 1: one persistent launch
   int2 *d_iface = nullptr, *d_flip = nullptr;
@@ -243,6 +244,7 @@ Ctx make_ctx(lsb_grid *g) {
   C.iface_list = g->d_iface;
   C.flip_list = g->d_flip;
   C.band_list = g->d_band;
+  C.band_info = g->d_band_info;
   C.list_cap = g->list_cap;
   C.band_cap = g->band_cap;
   C.err = g->d_err;
@@ -1400,6 +1402,7 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
   ALLOC(g->d_iface, sizeof(int2) * MAXL * g->list_cap);
   ALLOC(g->d_flip, sizeof(int2) * MAXL * g->list_cap);
   ALLOC(g->d_band, sizeof(int) * MAXL * (size_t)std::max(1, g->band_cap));
+  ALLOC(g->d_band_info, sizeof(int4) * MAXL * (size_t)std::max(1, g->band_cap));
   ALLOC(g->d_obs, sizeof(double) * n_cases * 16);
   ALLOC(g->d_sens, sizeof(float) * g->nblock_total);
 #undef ALLOC

@@ -199,6 +199,7 @@ struct Ctx {
   int *counters;           // per global level: [0] links, [1] iface cells, [2] flipped, [3] band blocks
   int2 *iface_list, *flip_list;   // (ld, cell)
   int *band_list;          // global block ids
+  int4 *band_info;         // beside each band-list entry: its block coordinates (as blk_info)
   long long list_cap;      // capacity of iface/flip lists per global level
   int band_cap;
   int *err;                // latched error bits
@@ -277,6 +278,18 @@ __device__ __forceinline__ int block_of(const LevelDev &L, int x, int y, int z, 
 __device__ __forceinline__ const LevelDev &blk_cell(const Ctx &C, const BlockShape &S, int gb, int t, int &x, int &y,
                                                     int &z) {
   const int4 bi = __ldg(C.blk_info + gb);
+  x = (bi.y << S.lg[0]) + (t & (S.bs[0] - 1));
+  y = (bi.z << S.lg[1]) + ((t >> S.lg[0]) & (S.bs[1] - 1));
+  z = (bi.w << S.lg[2]) + (t >> (S.lg[0] + S.lg[1]));
+  return C.lds[bi.x];
+}
+
+// Cell (x, y, z) of thread t in band-list entry w of global level glevel: the block
+// coordinates come from the copy k_band stores beside the list, so they do not wait
+// on the list entry.
+__device__ __forceinline__ const LevelDev &band_cell(const Ctx &C, const BlockShape &S, int glevel, int w, int t,
+                                                     int &x, int &y, int &z) {
+  const int4 bi = __ldg(C.band_info + (long long)glevel * C.band_cap + w);
   x = (bi.y << S.lg[0]) + (t & (S.bs[0] - 1));
   y = (bi.z << S.lg[1]) + ((t >> S.lg[0]) & (S.bs[1] - 1));
   z = (bi.w << S.lg[2]) + (t >> (S.lg[0] + S.lg[1]));

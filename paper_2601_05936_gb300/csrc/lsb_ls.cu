@@ -185,7 +185,10 @@ __global__ void k_band(Ctx C, BlockShape S, const int *list, int nlist, int glev
     if (band && C.bstat[gb] == BLK_LEAF) {
       C.bflag[gb] = C.bflag[gb] | BF_BAND;
       int e = atomicAdd(&C.counters[glevel * NCOUNT + 3], 1);
-      if (e < C.band_cap) C.band_list[(long long)glevel * C.band_cap + e] = gb;
+      if (e < C.band_cap) {
+        C.band_list[(long long)glevel * C.band_cap + e] = gb;
+        C.band_info[(long long)glevel * C.band_cap + e] = C.blk_info[gb];
+      }
       else atomicOr(C.err, ERR_BAND_OVF);
     }
   }
@@ -333,7 +336,7 @@ __device__ __forceinline__ void d_ext_iter(const Ctx &C, BlockShape S, int gleve
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
     const int gb = lst[w];
     int x, y, z;
-    const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
+    const LevelDev &L = band_cell(C, S, glevel, w, threadIdx.x, x, y, z);
     if (!L.ls_active) continue;  // frozen level set in this case
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long fo = L.fine_off, NF = C.nfine;
@@ -462,7 +465,8 @@ __global__ void __launch_bounds__(512, 2) k_ext_plan(Ctx C, BlockShape S, int gl
     for (int k = 0; k < U; ++k) gb[k] = w0 + k * G < nl ? __ldg(lst + w0 + k * G) : -1;
     int4 bi[U];
 #pragma unroll
-    for (int k = 0; k < U; ++k) bi[k] = gb[k] >= 0 ? __ldg(C.blk_info + gb[k]) : make_int4(-1, 0, 0, 0);
+    for (int k = 0; k < U; ++k)
+      bi[k] = gb[k] >= 0 ? __ldg(C.band_info + (long long)glevel * C.band_cap + w0 + k * G) : make_int4(-1, 0, 0, 0);
     bool act[U];
     long long fo[U], c[U];
     int x[U], y[U], z[U];
@@ -600,12 +604,10 @@ __device__ __forceinline__ float d5p(const float v[7]) {  // mirror image
 template <int D>
 __device__ __forceinline__ void d_adv_stage(const Ctx &C, BlockShape S, int glevel, int stage) {
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
-  const int *lst = C.band_list + (long long)glevel * C.band_cap;
   const float *pin = stage == 1 ? C.phi : (stage == 2 ? C.p1 : C.p2);
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
-    const int gb = lst[w];
     int x, y, z;
-    const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
+    const LevelDev &L = band_cell(C, S, glevel, w, threadIdx.x, x, y, z);
     if (!L.ls_active) continue;  // frozen level set in this case
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long fc = L.fine_off + cidx(L, x, y, z);
@@ -632,11 +634,9 @@ __device__ __forceinline__ void d_reinit_prep(const Ctx &C, BlockShape S, int gl
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
-  const int *lst = C.band_list + (long long)glevel * C.band_cap;
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
-    const int gb = lst[w];
     int x, y, z;
-    const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
+    const LevelDev &L = band_cell(C, S, glevel, w, threadIdx.x, x, y, z);
     if (!L.ls_active) continue;  // frozen level set in this case
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long fc = L.fine_off + cidx(L, x, y, z);
@@ -696,7 +696,7 @@ __device__ __forceinline__ void d_reinit_stage(const Ctx &C, BlockShape S, int g
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
     const int gb = lst[w];
     int x, y, z;
-    const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
+    const LevelDev &L = band_cell(C, S, glevel, w, threadIdx.x, x, y, z);
     if (!L.ls_active) continue;  // frozen level set in this case
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const unsigned cl = (unsigned)cidx(L, x, y, z);
