@@ -149,9 +149,8 @@ __global__ void k_adj_links(Ctx C, int glevel, const float *__restrict__ F, floa
     const int2 it = lst[e];
     const LevelDev &L = C.lds[it.x];
     const long long c = it.y;
-    const int x = (int)(c % L.p[0]);
-    const int y = (int)((c / L.p[0]) % L.p[1]);
-    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    int x, y, z;
+    cell_xyz(L, c, x, y, z);
     const long long fo = L.fine_off;
     const uint32_t cm = C.cmask[fo + c];
     const int cb = C.cbase[fo + c];
@@ -374,7 +373,6 @@ __global__ void __launch_bounds__(512, 1) k_adj_collide(Ctx C, BlockShape S, con
                                                       double *grad) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
-  constexpr int NS = D * (D + 1) / 2;
   constexpr int NV = 2 + 2 * 3;  // omega per phase, acceleration per phase
   // per-warp FP64 partial sums in shared memory (no loop-carried registers)
   __shared__ double red[32][NV];
@@ -663,9 +661,8 @@ __global__ void k_adj_geometry(Ctx C, int glevel, GeoAdj G) {
     for (int a = 0; a < D; ++a) ln[a] = G.n[a * NF + fc];
     const double lk = G.kappa[fc];
     if (lk == 0.0 && ln[0] == 0.0 && ln[1] == 0.0 && ln[2] == 0.0) continue;
-    const int x = (int)(c % L.p[0]);
-    const int y = (int)((c / L.p[0]) % L.p[1]);
-    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    int x, y, z;
+    cell_xyz(L, c, x, y, z);
     double P = 0, sx[3] = {0, 0, 0}, sxx[3] = {0, 0, 0}, sxy[3] = {0, 0, 0};
     for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz)
       for (int oy = -1; oy <= 1; ++oy)
@@ -896,9 +893,8 @@ __global__ void k_adj_ghost(Ctx C, const int2 *cells, int n, float theta, const 
     const LevelDev &F = C.lds[it.x];
     const LevelDev &Lc = C.lds[F.parent_ld];
     const long long c = it.y;
-    const int x = (int)(c % F.p[0]);
-    const int y = (int)((c / F.p[0]) % F.p[1]);
-    const int z = (int)(c / ((long long)F.p[0] * F.p[1]));
+    int x, y, z;
+    cell_xyz(F, c, x, y, z);
     float lg[Q];
     bool any = false;
 #pragma unroll
@@ -1023,9 +1019,8 @@ __global__ void k_adj_ghost_apply(Ctx C, const int2 *cells, int n, float *lamX, 
     const LevelDev &F = C.lds[it.x];
     const LevelDev &Lc = C.lds[F.parent_ld];
     const long long c = it.y;
-    const int x = (int)(c % F.p[0]);
-    const int y = (int)((c / F.p[0]) % F.p[1]);
-    const int z = (int)(c / ((long long)F.p[0] * F.p[1]));
+    int x, y, z;
+    cell_xyz(F, c, x, y, z);
     long long sc[1 + 2 * 3];
     float sw[1 + 2 * 3];
     const int ns = interp_stencil<D>(C, Lc, x, y, z, sc, sw);
@@ -1057,9 +1052,8 @@ __global__ void k_adj_restrict(Ctx C, const int2 *cells, int n, const float *__r
     const LevelDev &L = C.lds[it.x];
     const LevelDev &F = C.lds[L.child_ld];
     const long long c = it.y;
-    const int x = (int)(c % L.p[0]);
-    const int y = (int)((c / L.p[0]) % L.p[1]);
-    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    int x, y, z;
+    cell_xyz(L, c, x, y, z);
     float lr[Q];
     bool any = false;
     float *lo = lamOc + L.cell_off * Q;

@@ -86,9 +86,8 @@ __global__ void k_lsa_init(Ctx C, int glevel, const float *__restrict__ F, float
     const int2 it = lst[e];
     const LevelDev &L = C.lds[it.x];
     const long long c = it.y;
-    const int x = (int)(c % L.p[0]);
-    const int y = (int)((c / L.p[0]) % L.p[1]);
-    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    int x, y, z;
+    cell_xyz(L, c, x, y, z);
     const long long fo = L.fine_off, NF = C.nfine, N = L.ncell;
     const float *Fl = F + L.cell_off * Q;
     const uint32_t m = C.cmask[fo + c];
@@ -133,9 +132,8 @@ __global__ void k_lsa_init_T(Ctx C, int glevel, const float *__restrict__ F, flo
     const int2 it = lst[e];
     const LevelDev &L = C.lds[it.x];
     const long long c = it.y;
-    const int x = (int)(c % L.p[0]);
-    const int y = (int)((c / L.p[0]) % L.p[1]);
-    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    int x, y, z;
+    cell_xyz(L, c, x, y, z);
     const long long fo = L.fine_off, N = L.ncell;
     const float *Fl = F + L.cell_off * Q;
     const uint32_t m = C.cmask[fo + c];

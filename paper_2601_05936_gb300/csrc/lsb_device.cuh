@@ -296,6 +296,16 @@ __device__ __forceinline__ const LevelDev &band_cell(const Ctx &C, const BlockSh
   return C.lds[bi.x];
 }
 
+// (x, y, z) of level-local cell index c, in 32-bit arithmetic: every level holds fewer
+// than 2^32 / (Q + 1) cells (checked when the grid is created).
+__device__ __forceinline__ void cell_xyz(const LevelDev &L, long long c, int &x, int &y, int &z) {
+  const unsigned u = (unsigned)c, p0 = (unsigned)L.p[0], p1 = (unsigned)L.p[1];
+  const unsigned q = u / p0;
+  x = (int)(u - q * p0);
+  y = (int)(q % p1);
+  z = (int)(q / p1);
+}
+
 // Wrap a coordinate on a periodic axis; returns false if it leaves through a wall.
 __device__ __forceinline__ bool wrap(const LevelDev &L, int a, int &v) {
   int n = L.n[a];

@@ -548,9 +548,8 @@ __global__ void k_interface_bc(Ctx C, int glevel) {
     const int k = C.link_dir[C.link_list_off[glevel] + e];
     const LevelDev &L = C.lds[it.x];
     const long long c = it.y;
-    const int x = (int)(c % L.p[0]);
-    const int y = (int)((c / L.p[0]) % L.p[1]);
-    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    int x, y, z;
+    cell_xyz(L, c, x, y, z);
     const long long fo = L.fine_off;
     const long long NF = C.nfine;
     const uint8_t tg = C.tag[L.cell_off + c];
@@ -954,9 +953,8 @@ __global__ void k_restrict_cells(Ctx C, const int2 *cells, int n) {
     const int2 it = cells[e];
     const LevelDev &L = C.lds[it.x];
     const long long c = it.y;
-    const int x = (int)(c % L.p[0]);
-    const int y = (int)((c / L.p[0]) % L.p[1]);
-    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    int x, y, z;
+    cell_xyz(L, c, x, y, z);
     const LevelDev &F = C.lds[L.child_ld];
     const T *Af = fA<T, Q>(C, F);
     float f[Q];
@@ -992,9 +990,8 @@ __global__ void k_ghost_cells(Ctx C, const int2 *cells, int n, float theta) {
     const int2 it = cells[e];
     const LevelDev &F = C.lds[it.x];
     const long long c = it.y;
-    const int x = (int)(c % F.p[0]);
-    const int y = (int)((c / F.p[0]) % F.p[1]);
-    const int z = (int)(c / ((long long)F.p[0] * F.p[1]));
+    int x, y, z;
+    cell_xyz(F, c, x, y, z);
     const LevelDev &Lc = C.lds[F.parent_ld];
     float f[Q];
     interp_coarse<Q, T>(C, Lc, x, y, z, theta, f);

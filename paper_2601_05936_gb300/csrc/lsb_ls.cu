@@ -67,9 +67,8 @@ __global__ void k_flip_mark(Ctx C, BlockShape S, int glevel) {
     const int2 it = lst[e];
     const LevelDev &L = C.lds[it.x];
     const long long c = it.y;
-    const int x = (int)(c % L.p[0]);
-    const int y = (int)((c / L.p[0]) % L.p[1]);
-    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    int x, y, z;
+    cell_xyz(L, c, x, y, z);
     for (int k = 0; k < Q; ++k) {
       int sx = x + LT::cx(k), sy = y + LT::cy(k), sz = z + LT::cz(k);
       if (!(wrap(L, 0, sx) && wrap(L, 1, sy) && (D == 2 || wrap(L, 2, sz)))) continue;
@@ -208,9 +207,8 @@ __global__ void k_geometry(Ctx C, int glevel, int which) {
     const int2 it = lst[e];
     const LevelDev &L = C.lds[it.x];
     const long long c = it.y;
-    const int x = (int)(c % L.p[0]);
-    const int y = (int)((c / L.p[0]) % L.p[1]);
-    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    int x, y, z;
+    cell_xyz(L, c, x, y, z);
     // Stencil sums exactly: phi (float) in fixed point with 30 fraction bits (exact
     // for |phi| >= 2^-6, within 2^-31 below), summed in 64-bit integers, then
     // converted to float64 (exact below 2^53).  This keeps the float64 work of the
@@ -298,9 +296,8 @@ __device__ __forceinline__ void d_ext_init(const Ctx &C, int glevel) {
     const LevelDev &L = C.lds[it.x];
     if (!L.ls_active) continue;  // frozen level set in this case
     const long long c = it.y;
-    const int x = (int)(c % L.p[0]);
-    const int y = (int)((c / L.p[0]) % L.p[1]);
-    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    int x, y, z;
+    cell_xyz(L, c, x, y, z);
     const long long fo = L.fine_off, NF = C.nfine;
     const uint32_t m = C.cmask[fo + c];
     const float phx = C.phi[fo + c];
@@ -830,9 +827,8 @@ __global__ void k_refill(Ctx C, int glevel) {
     const int2 it = lst[e];
     const LevelDev &L = C.lds[it.x];
     const long long c = it.y;
-    const int x = (int)(c % L.p[0]);
-    const int y = (int)((c / L.p[0]) % L.p[1]);
-    const int z = (int)(c / ((long long)L.p[0] * L.p[1]));
+    int x, y, z;
+    cell_xyz(L, c, x, y, z);
     const long long fo = L.fine_off, NF = C.nfine, N = L.ncell;
     T *Bf = fB<T, Q>(C, L);
     const uint8_t tg = C.tag[L.cell_off + c];
