@@ -96,14 +96,42 @@ class Clocks:
                     reasons=sorted(reasons), samples=len(sm))
 
 
-def cpu_baseline(budget_s=20.0, warmup=0):
+def oracle_error(case, s, steps, storage):
+    """The CUDA path on the oracle's case for the same number of coarse steps, against the
+    oracle's state: per level rel-L2 of u and max |drho| on leaf cells, max |phi| error,
+    leaf masks and phases compared bit for bit."""
+    from paper_2601_05936_gb300 import lsb
+    c = dict(case, storage=storage)
+    g = lsb.Grid(c)
+    g.step(steps)
+    out = dict(storage=storage, steps=steps, leaf_masks_equal=True, u_rel_l2=0.0, drho_max_abs=0.0)
+    for l, geom in enumerate(s.geoms):
+        leaf = s.masks[l][0]
+        tag = g.get("tag", 0, l).reshape(-1)
+        out["leaf_masks_equal"] &= bool(np.array_equal((tag & 64) != 0, leaf))
+        rho_o, u_o = s.macros(l)
+        rho_g = g.get("rho", 0, l).reshape(-1).astype(np.float64)
+        u_g = g.get("u", 0, l).reshape(geom.D, -1).astype(np.float64)
+        den = float(np.sqrt((u_o[:, leaf] ** 2).sum())) or 1.0
+        out["u_rel_l2"] = max(out["u_rel_l2"], float(np.sqrt(((u_g[:, leaf] - u_o[:, leaf]) ** 2).sum())) / den)
+        out["drho_max_abs"] = max(out["drho_max_abs"], float(np.abs(rho_g[leaf] - rho_o[leaf]).max()))
+    out["phi_max_abs"] = float(np.abs(g.get("phi").reshape(-1).astype(np.float64) - s.phi).max())
+    out["phases_equal"] = bool(np.array_equal(g.get("phase").reshape(-1), s.phase[-1].astype(np.uint8)))
+    g.close()
+    return out
+
+
+def cpu_baseline(budget_s=20.0, warmup=0, compare_storage=None):
     """The FP64 oracle as it stands on the host cores: bounded sample = the
     downsampled 32x32x64 copy of the workload (same physics, d scaled by 1/4),
     `warmup` untimed coarse steps, then as many timed coarse steps as fit in
-    ~budget_s (at least one)."""
+    ~budget_s (at least one).  With compare_storage, the CUDA path then runs the
+    same case for the same steps and its field errors against the oracle's state
+    are reported."""
     from oracle.sim import Sim
     from paper_2601_05936_gb300 import workloads
     case = workloads.rising_bubble_3d(scale=0.25)
+    case["phi0"] = np.asarray(case["phi0"], np.float32).astype(np.float64)  # one initial level set for both
     s = Sim(case)
     s.step(warmup)
     t0 = time.perf_counter()
@@ -118,8 +146,9 @@ def cpu_baseline(budget_s=20.0, warmup=0):
             break
     dt = time.perf_counter() - t0
     cores = (time.process_time() - c0) / dt  # threads busy on average over the timed steps
+    err = oracle_error(case, s, warmup + n, compare_storage) if compare_storage else None
     return dict(value=upd / dt / 1e6, unit="MLUPS", cores=round(max(cores, 1.0), 1), kind="oracle",
-                ms_per_step=dt / n * 1e3,
+                ms_per_step=dt / n * 1e3, error_vs_oracle=err,
                 sample=f"downsampled 32x32x64 base / 2-level copy of the workload, {warmup} untimed and {n} "
                        f"timed coarse steps, {upd:.0f} cell updates in {dt:.1f} s (numpy float64; cores = CPU "
                        f"time / wall time of the timed steps, {os.cpu_count()} host cores)")
@@ -442,7 +471,8 @@ def main():
 
     if rank != 0:
         return
-    cpu = None if args.no_cpu_baseline or world > 1 or args.workload != "bubble3d" else cpu_baseline()
+    cpu = None if args.no_cpu_baseline or world > 1 or args.workload != "bubble3d" else \
+        cpu_baseline(compare_storage=args.storage)
     metric = METRIC if args.workload == "bubble3d" else f"MLUPS (leaf cell updates / s), {args.workload}"
     lattice = case["lattice"]
     state_gb = sum(float(np.prod([b * 2 ** l for b in c["base"]])) for c in cases
