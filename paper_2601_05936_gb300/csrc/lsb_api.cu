@@ -129,6 +129,8 @@ struct lsb_grid {
   int tma_grid = 0;
   int tma_tags = 0;               // d_tmaps also holds one cell-tag map per level descriptor
   cudaGraphExec_t gexec[2][2] = {};  // [coarse steps per replay - 1][level-0 parity at the start]
+  cudaStream_t side[MAXL] = {};        // per level: its collide-and-stream beside the first fine sub-step
+  cudaEvent_t ev_fork[MAXL] = {}, ev_join[MAXL] = {};
   uint64_t gnodes[2][2] = {};
   // adjoint of the frozen-interface step: recording and reverse sweep
   int rec_on = 0, rec_every = 0;
@@ -566,7 +568,26 @@ lsb_status advance(lsb_grid *g, int l) {
                        g->stream));
   }
   const double cs_bytes = 2.0 * g->Q * (g->storage == LSB_FP32 ? 4 : 2) * g->leaf_cells[l];
-  if (g->d_tmaps && !g->no_tma) {
+  // A coarser level's collide-and-stream writes only its own B buffer, and the first fine
+  // sub-step reads only its A buffer (ghost ring at theta = 0): with no case finishing at
+  // this level, the collide runs on a side stream beside that sub-step (half the resident
+  // CTAs, so the sub-step's kernels find room) and is joined before the second sub-step.
+  const bool fork = g->stream && g->prof_mode == 0 && !g->tape_on && l + 1 < g->Lmax && !has_finest(g, l) &&
+                    g->d_tmaps && !g->no_tma && !g->tma_a;
+  if (fork) {
+    if (!g->side[l]) {
+      CU(cudaStreamCreateWithFlags(&g->side[l], cudaStreamNonBlocking));
+      CU(cudaEventCreateWithFlags(&g->ev_fork[l], cudaEventDisableTiming));
+      CU(cudaEventCreateWithFlags(&g->ev_join[l], cudaEventDisableTiming));
+    }
+    CU(cudaEventRecord(g->ev_fork[l], g->stream));
+    CU(cudaStreamWaitEvent(g->side[l], g->ev_fork[l], 0));
+    const int grid = std::min(g->cs[l].n, std::max(1, g->tma_grid / 2));
+    const CUtensorMap *tm = (const CUtensorMap *)g->d_tmaps;
+    RUN(collide_kid(l), cs_bytes, g->cs[l].n, nt, run_collide_stream_tma, Q, st, Launch{grid, nt, g->side[l]}, C, S,
+        (const int *)g->cs[l].d, g->cs[l].n, tm, g->tma_tags ? tm + 2 * g->lds.size() : nullptr);
+    CU(cudaEventRecord(g->ev_join[l], g->side[l]));
+  } else if (g->d_tmaps && !g->no_tma) {
     const int grid = std::min(g->cs[l].n, g->tma_grid);
     const CUtensorMap *tm = (const CUtensorMap *)g->d_tmaps;
     RUN(collide_kid(l), cs_bytes, g->cs[l].n, nt, run_collide_stream_tma, Q, st, LN(g, grid, nt), C, S, (const int *)g->cs[l].d,
@@ -588,6 +609,7 @@ lsb_status advance(lsb_grid *g, int l) {
   if (call >= 0 && l + 1 < g->Lmax) TRY(copy_level(g, g->tape_new[call], (const float *)g->d_buf[1 - g->par[l]], l));
   if (l + 1 < g->Lmax) {
     for (int sub = 0; sub < 2; ++sub) {
+      if (sub == 1 && fork) CU(cudaStreamWaitEvent(g->stream, g->ev_join[l], 0));  // theta = 1/2 reads B
       C = make_ctx(g);
       const float theta = sub == 0 ? 0.0f : 0.5f;
       const CellList &gc = g->ghost_cells[l + 1];
@@ -2015,6 +2037,13 @@ void lsb_destroy(lsb_grid *g) {
   if (g->stream) cudaStreamSynchronize(g->stream);
   else cudaDeviceSynchronize();
   drop_graphs(g);
+  for (int l = 0; l < MAXL; ++l)
+    if (g->side[l]) {
+      cudaStreamSynchronize(g->side[l]);
+      cudaStreamDestroy(g->side[l]);
+      cudaEventDestroy(g->ev_fork[l]);
+      cudaEventDestroy(g->ev_join[l]);
+    }
   for (void *p : g->allocs) cudaFree(p);
   if (g->d_lsa) cudaFree(g->d_lsa);
   if (g->d_seg) cudaFree(g->d_seg);
