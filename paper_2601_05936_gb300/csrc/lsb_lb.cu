@@ -339,8 +339,9 @@ __device__ __forceinline__ float stage_ld<__half>(const __half *p, float inv) {
   return __half2float(*p) * inv;
 }
 
-// Per-block values the TMA-issuing thread publishes next to the stage it fills;
-// the stage's mbarrier (arrive = release, wait = acquire) makes them visible.
+// Per-block values the TMA-issuing thread publishes with each stage it fills, in the
+// ring slot of the iteration that consumes the stage; the stage's mbarrier
+// (arrive = release, wait = acquire) makes them visible.
 struct BlockMeta {
   long long cell_off, fine_off;
   unsigned ncell, p0, p01;
