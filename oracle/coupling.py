@@ -6,7 +6,7 @@ direction from x towards the interface, so x + c_i is the other-phase node of
 Eq. bb.  Phase A is x's phase, B the other one; [X] = X_B - X_A; n_A is the
 unit normal pointing from A into B and kappa_A = div n_A.
 
-Readings (the passages are garbled or silent; each is listed in the design doc):
+Readings (where the passages are garbled or silent):
 
 * Eq. bb, q >= 1/2 branch: the second population is the opposite one at the
   same node, f_k^c(x) (linear Bouzidi); the printed x - c_i would not be a
