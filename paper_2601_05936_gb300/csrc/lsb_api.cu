@@ -1506,8 +1506,9 @@ lsb_status lsb_set_params(lsb_grid *g, int case_idx, const lsb_params *params) {
   g->n_reinit = params->n_reinit;
   g->regrid_every = params->regrid_every;
   if (relaunch) drop_graphs(g);
+  // stream-ordered before the next step; a copy from pageable memory returns once the
+  // source is staged, so the host descriptors may change again right away
   CU(cudaMemcpyAsync(g->d_lds, g->lds.data(), sizeof(LevelDev) * g->lds.size(), cudaMemcpyHostToDevice, g->stream));
-  CU(cudaStreamSynchronize(g->stream));
   return LSB_OK;
 }
 
