@@ -836,18 +836,18 @@ __global__ void k_observables(Ctx C, BlockShape S, const int *list, int nlist, d
   // cell volumes, counts and centroid terms are integer-valued (exact in FP32 while a
   // thread's sums stay below 2^24); mass is kept as volume + vol * drho with the small
   // second part summed apart
-  float vol_ph[2] = {0.f, 0.f}, dm_ph[2] = {0.f, 0.f}, v[NV];
+  float vol_l = 0.f, vol_g = 0.f, dm_l = 0.f, dm_g = 0.f, v[NV];  // per phase as scalars (registers)
   for (int k = 0; k < NV; ++k) v[k] = 0.f;
   int cur_case = -1;
   auto flush = [&](int case_id) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     for (int k = 0; k < NV; ++k) {
-      double s = k < 2 ? (double)vol_ph[k] + (double)dm_ph[k] : (double)v[k];
+      double s = k == 0 ? (double)vol_l + (double)dm_l : (k == 1 ? (double)vol_g + (double)dm_g : (double)v[k]);
       for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
       if (lane == 0) red[warp][k] = s;
       v[k] = 0.f;
     }
-    vol_ph[0] = vol_ph[1] = dm_ph[0] = dm_ph[1] = 0.f;
+    vol_l = vol_g = dm_l = dm_g = 0.f;
     __syncthreads();
     if (threadIdx.x < NV) {
       double s = 0.0;
@@ -878,8 +878,13 @@ __global__ void k_observables(Ctx C, BlockShape S, const int *list, int nlist, d
         float vol = 1.f;
         for (int a = 0; a < D; ++a) vol *= (float)L.scale;
         const int gas = tg & TAG_GAS;
-        vol_ph[gas] += vol;
-        dm_ph[gas] += vol * drho;
+        if (gas) {
+          vol_g += vol;
+          dm_g += vol * drho;
+        } else {
+          vol_l += vol;
+          dm_l += vol * drho;
+        }
         v[3] += 1.f;
         const bool finite = isfinite(drho) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
         if (!finite) atomicOr(C.err, ERR_NONFINITE);
