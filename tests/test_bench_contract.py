@@ -24,3 +24,28 @@ def test_reference_arm_line_keys():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1.0 and cb["value"] == line["value"]
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+import pytest  # noqa: E402
+
+
+@pytest.mark.gpu
+def test_cuda_arm_line_keys():
+    r = subprocess.run([sys.executable, "bench.py", "--steps", "4", "--warmup", "3", "--no-cpu-baseline",
+                        "--e2e-steps", "2"], cwd=ROOT, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "gpu_launches", "clocks"):
+        assert k in line, k
+    assert line["value"] > 0 and line["gpu_launches"] > 0 and line["n_gpus"] == 1
+    roof = line["roofline"]
+    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert k in roof, k
+    assert roof["bound"] == "hbm" and 0.0 < roof["frac"] < 1.5 and roof["achieved"] > 0
+    for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"):
+        assert k in line["e2e"], k
+    assert line["e2e"]["h2d_bytes_per_step"] > 0 and line["e2e"]["d2h_bytes_per_step"] > 0
+    for k in ("sm_mhz", "sm_max_mhz", "reasons"):
+        assert k in line["clocks"], k
+    assert "workload" in line["config"] and "l2_flush" in line["config"]
