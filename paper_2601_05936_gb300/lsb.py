@@ -245,7 +245,8 @@ class Grid:
         self._check(self.lib.lsb_step(self.h, int(n)))
 
     def use_graphs(self, enable=True):
-        """Replay two coarse steps at a time from CUDA graphs (needs a non-default stream)."""
+        """Replay coarse steps from CUDA graphs, two per replay and one for an odd remainder
+        (needs a non-default stream); results are identical to eager stepping."""
         self._check(self.lib.lsb_use_graphs(self.h, 1 if enable else 0))
 
     def set_driver(self, mode):
