@@ -42,9 +42,14 @@ Readings (where the passages are garbled or silent):
   p_new = p_old + sigma kappa_new.  f^neq is copied from x_r + e_min.
 
 Pins: tests/test_oracle_coupling.py (weights exact on quadratics and summing to
-one, q exact for linear phi, e_min brute force) and the two-layer Poiseuille /
-Couette closed forms and the static-drop Laplace jump in
-tests/test_oracle_flows.py.
+one, q exact for linear phi, e_min brute force); tests/test_oracle_refill.py
+(the composed refill: new-phase density and velocity polynomials along e_min
+that meet the interface conditions at Gamma are reproduced exactly for any q
+on both branches, a static drop's flipped cells land on their new phase's
+pressure either way, a planted moment-free f^neq at x_r + e_min is copied
+exactly, no usable neighbour gives the rest state, and planted mistakes fail);
+the two-layer Poiseuille / Couette closed forms and the static-drop Laplace
+jump in tests/test_oracle_flows.py.
 """
 import numpy as np
 

@@ -18,8 +18,11 @@ finest level, Sec. 2.5) inside the Dupuis-Chopard recursion described in
 ``amr``.  A coarse step advances the finest level 2^(L-1) times.
 
 Parity is pinned by the closed-form flows in tests/test_oracle_flows.py and
-tests/test_oracle_amr.py; the step order itself is a reading (parity unpinned
-beyond those closed forms).
+tests/test_oracle_amr.py, the cut-link enumeration by brute force
+(tests/test_oracle_cut_links.py) and the refill by exact reproduction of
+fields built to satisfy the interface conditions
+(tests/test_oracle_refill.py); the step order itself is a reading (parity
+unpinned beyond those checks).
 """
 import numpy as np
 
@@ -128,7 +131,10 @@ class Sim:
 
     # ------------------------------------------------------------ interface
     def cut_links(self, phase, fluid):
-        """All (x, k) with x fluid on the finest level and x - c_k of the other phase."""
+        """All (x, k) with x fluid on the finest level and x - c_k of the other phase.
+
+        Pinned by brute force over every sign pattern of a 3x3 patch (D2Q9) and
+        random 3x3x3 patterns (D3Q19), tests/test_oracle_cut_links.py."""
         lat = self.lat
         gF = self.geoms[-1]
         xs, ks = [], []
