@@ -171,6 +171,18 @@ lsb_status lsb_use_graphs(lsb_grid *g, int enable);
  */
 lsb_status lsb_set_driver(lsb_grid *g, int mode);
 
+/*
+ * Iteration limit of the library's bounded device-side waits (the grid barrier
+ * of lsb_set_driver mode 1; the paper has no counterpart).  A waiting CTA
+ * sleeps ~64 ns per iteration and, after `spins` iterations, records the
+ * timeout, leaves the kernel, and the next synchronising call returns
+ * LSB_ETIMEOUT (a latched error: the handle stays in error; the CUDA context
+ * stays usable).  Default 2^22 (~0.3 s).  0 makes every wait that would have to
+ * wait give up at once, which exercises the timeout path without a stalled
+ * GPU.  Errors: LSB_EINVAL (negative spins).
+ */
+lsb_status lsb_set_wait_limit(lsb_grid *g, long long spins);
+
 /* Run the refinement sensor and regrid every case now (Sec. 2.6). */
 lsb_status lsb_refine(lsb_grid *g);
 

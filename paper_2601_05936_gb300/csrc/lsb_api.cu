@@ -95,6 +95,7 @@ struct lsb_grid {
   int *d_counters = nullptr, *d_err = nullptr, *d_band = nullptr;
   int4 *d_band_info = nullptr;
   unsigned *d_bar = nullptr;  // grid barrier of the persistent level-set kernel
+  long long wait_limit = 1LL << 22;  // sleeps of ~64 ns before a device-side wait gives up
   int driver = 0;             // 0: one launch per level-set pass, 1: one persistent launch
   int2 *d_iface = nullptr, *d_flip = nullptr;
   double *d_obs = nullptr;
@@ -496,8 +497,10 @@ lsb_status levelset(lsb_grid *g, int l) {
   const int Q = g->Q, D = g->D;
   if (g->driver == 1) {
     const bool due = g->reinit_every > 0 && ((g->fine_steps[l] + 1) % g->reinit_every == 0) && g->n_reinit > 0;
+    // a barrier that gave up leaves its count behind: start every launch from zero
+    CU(cudaMemsetAsync(g->d_bar, 0, 2 * sizeof(unsigned), g->stream));
     RUN(KLS_PERSIST, 0, 1, nt, run_levelset_persistent, Q, LN(g, nb, nt), C, S, l, g->n_ext, due ? 1 : 0,
-        g->n_reinit, g->d_bar);
+        g->n_reinit, g->d_bar, g->wait_limit);
     return LSB_OK;
   }
   RUN(12, 0, 1, 128, run_ext_init, Q, LN(g, DYN_GRID, 128), C, l);
@@ -1556,6 +1559,13 @@ lsb_status lsb_use_graphs(lsb_grid *g, int enable) {
   if (enable && !g->stream) return fail(g, LSB_EINVAL, "CUDA graphs need a non-default stream");
   g->use_graphs = enable;
   if (!enable) drop_graphs(g);
+  return LSB_OK;
+}
+
+lsb_status lsb_set_wait_limit(lsb_grid *g, long long spins) {
+  if (!g || spins < 0) return LSB_EINVAL;
+  if (spins != g->wait_limit) drop_graphs(g);  // the limit is a captured kernel argument
+  g->wait_limit = spins;
   return LSB_OK;
 }
 

@@ -52,7 +52,7 @@ cudaError_t run_reinit_prep(int Q, Launch L, Ctx C, BlockShape S, int glevel);
 cudaError_t run_reinit_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage);
 cudaError_t run_refill(int Q, int st, Launch L, Ctx C, int glevel);
 cudaError_t run_levelset_persistent(int Q, Launch L, Ctx C, BlockShape S, int glevel, int n_ext, int reinit,
-                                    int n_reinit, unsigned *bar);
+                                    int n_reinit, unsigned *bar, long long limit);
 cudaError_t run_sensor(Launch L, Ctx C, BlockShape S, const int *list, int n, int mode, float *out);
 
 // lsb_adj.cu: adjoint of the frozen-interface step

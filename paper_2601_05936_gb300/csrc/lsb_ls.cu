@@ -728,10 +728,10 @@ __global__ void k_reinit_stage(Ctx C, BlockShape S, int glevel, int stage) { d_r
 // with an iteration limit: on expiry the block sets ERR_TIMEOUT and returns, so
 // a barrier that cannot complete ends the kernel instead of hanging it (the
 // cooperative launch makes every CTA resident, so this does not happen in
-// normal operation).  bar: two words, arrival count and generation, zero at rest.
-constexpr long kBarrierLimit = 1L << 22;  // x ~64 ns sleeps: ~0.3 s
-
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
+// normal operation).  bar: two words, arrival count and generation, zero at rest
+// (cleared before every launch).  limit: sleeps of ~64 ns before giving up (the
+// handle's wait limit, 2^22 ~ 0.3 s by default; 0 gives up at the first wait).
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, long long limit) {
   __shared__ int abort_flag;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -745,9 +745,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
-      long it = 0;
+      long long it = 0;
       while (*vgen == gen) {
-        if (++it > kBarrierLimit) {
+        if (++it > limit) {
           atomicOr(err, ERR_TIMEOUT);
           abort_flag = 1;
           break;
@@ -763,32 +763,32 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
 
 template <int Q>
 __global__ void k_levelset_persistent(Ctx C, BlockShape S, int glevel, int n_ext, int reinit, int n_reinit,
-                                      unsigned *bar) {
+                                      unsigned *bar, long long limit) {
   constexpr int D = Lat<Q>::D;
   d_ext_init<Q>(C, glevel);
-  if (!grid_barrier(bar, C.err)) return;
+  if (!grid_barrier(bar, C.err, limit)) return;
   const float *uin = C.ut0;
   for (int it = 0; it < n_ext; ++it) {
     float *uout = (it & 1) ? C.ut2 : C.ut1;
     d_ext_iter<D>(C, S, glevel, uin, uout, it == 0 ? 2 : 3);
-    if (!grid_barrier(bar, C.err)) return;
+    if (!grid_barrier(bar, C.err, limit)) return;
     uin = uout;
   }
   if (n_ext > 0) {
     d_ext_iter<D>(C, S, glevel, uin, nullptr, 1);
-    if (!grid_barrier(bar, C.err)) return;
+    if (!grid_barrier(bar, C.err, limit)) return;
   }
   for (int st = 1; st <= 3; ++st) {
     d_adv_stage<D>(C, S, glevel, st);
-    if (!grid_barrier(bar, C.err)) return;
+    if (!grid_barrier(bar, C.err, limit)) return;
   }
   if (reinit) {
     d_reinit_prep<Q>(C, S, glevel);
-    if (!grid_barrier(bar, C.err)) return;
+    if (!grid_barrier(bar, C.err, limit)) return;
     for (int r = 0; r < n_reinit; ++r)
       for (int st = 1; st <= 3; ++st) {
         d_reinit_stage<D>(C, S, glevel, st);
-        if (!grid_barrier(bar, C.err)) return;
+        if (!grid_barrier(bar, C.err, limit)) return;
       }
   }
 }
@@ -1046,8 +1046,8 @@ cudaError_t run_sensor(Launch L, Ctx C, BlockShape S, const int *list, int n, in
 // One cooperative launch of the level-set phase; grid = resident CTAs (required
 // for a cooperative launch, which fails rather than oversubscribe).
 cudaError_t run_levelset_persistent(int Q, Launch L, Ctx C, BlockShape S, int glevel, int n_ext, int reinit,
-                                    int n_reinit, unsigned *bar) {
-  void *args[] = {&C, &S, &glevel, &n_ext, &reinit, &n_reinit, &bar};
+                                    int n_reinit, unsigned *bar, long long limit) {
+  void *args[] = {&C, &S, &glevel, &n_ext, &reinit, &n_reinit, &bar, &limit};
   if (Q == 9) {
     const int grid = resident_grid(k_levelset_persistent<9>, L.block, L.grid);
     return cudaLaunchCooperativeKernel((const void *)k_levelset_persistent<9>, grid, L.block, args, 0, L.stream);

@@ -11,11 +11,14 @@ Re / Eo definitions): with bubble diameter d in finest cells, U = Ma c_s,
 g = U^2 / d, nu_l = U d / Re, nu_g = nu_l (eta_g/eta_l)(rho_l/rho_g),
 sigma = rho_l g d^2 / Eo (rho_l = 1).
 
-Two limits of the method as implemented shape the choice of Ma and nu_l
-(measured, see the design notes): the explicit normal-stress coupling needs
-nu_l >~ 0.1 at density ratio 1000, and the gas, whose lattice pressure is
-rho_g c_s^2 rho_hat, compresses by ~400 Ma^2 under the Laplace pressure at
-density ratio 1000.  So nu_l is floored at ``nu_floor`` (the effective
+Two limits of the method as implemented shape the choice of Ma and nu_l.
+Both were measured on the oracle and the library alike: the explicit
+normal-stress coupling of Eq. Sdecomp relaxes a pressure mismatch with a gain
+of ~ q(1-q) rho c_s / (2 eta_bar), and static drops at density ratio 1000
+diverge below nu_l ~ 0.05 (stable from ~0.1); and the gas, whose lattice
+pressure is rho_g c_s^2 rho_hat, compresses by ~400 Ma^2 under the Laplace
+pressure at density ratio 1000, so the 3D bubble at the paper's Re = 35
+(nu_l = 0.021 at Ma 0.02, d = 64) diverges within 100 steps.  So nu_l is floored at ``nu_floor`` (the effective
 Reynolds number U d / nu_l is stored with the case) and the gas starts at its
 Laplace pressure (p_gas0 = sigma (D-1) / R).
 """

@@ -6,9 +6,9 @@ parameter gradients and its adjoint populations dJ/df_0 on the same
 frozen-interface window, after the same forward warm-up.  The library's
 forward state is FP32 (relative error ~1e-6 against the oracle) and the
 reverse sweep runs in FP32 with FP64 parameter sums, so gradients agree to
-~1e-4 relative; the tolerances below (2e-3 on each parameter gradient, 1e-3
-relative L2 on dJ/df_0) leave an order of magnitude for the accumulation
-over the window.
+~1e-4 relative; the tolerances below (1e-3 on each parameter gradient, the
+agreement with finite differences that the adjoint is held to, and 1e-3
+relative L2 on dJ/df_0) leave room for the accumulation over the window.
 """
 import numpy as np
 import pytest
@@ -61,7 +61,7 @@ def test_adjoint_matches_oracle(lattice, n, warmup, steps):
     _, dp_o, lam_o, dphi_o = _oracle(case, warmup, steps, a)
     g, dp_g, lam_g, dphi_g = _gpu(case, warmup, steps, a, every=7, want_phi=True)
     for k in range(5):
-        assert abs(dp_g[k] - dp_o[k]) <= 2e-3 * abs(dp_o[k]) + 1e-9, (k, dp_g, dp_o)
+        assert abs(dp_g[k] - dp_o[k]) <= 1e-3 * abs(dp_o[k]) + 1e-9, (k, dp_g, dp_o)
     assert rel_l2(lam_g, lam_o) < 1e-3
     # dJ/dphi of the frozen level set (q, normal, curvature): FP32 link arithmetic with
     # 1/q^2 and 1/(phi_x - phi_y)^2 factors; relative L2 over the whole field

@@ -5,7 +5,7 @@ float64 forward map; here the CUDA reverse sweep over a two-level recording
 must reproduce its parameter gradients, the per-level adjoint populations
 dJ/df_0 and dJ/dphi on the same frozen-interface window after the same
 forward warm-up.  FP32 state and adjoint against float64: the tolerances are
-those of the single-level adjoint test (2e-3 per parameter gradient, 1e-3
+those of the single-level adjoint test (1e-3 per parameter gradient, 1e-3
 relative L2 on dJ/df_0 per level, 5e-3 on dJ/dphi).  The layouts hold coarse
 leaves, a restriction layer and a fine ghost ring, so every transposed
 transfer is on the compared path.
@@ -61,7 +61,7 @@ def test_amr_adjoint_matches_oracle(lattice, n, block, rd, warmup, steps):
     for l in range(2):
         assert np.array_equal(g.get("blocks", 0, l), sim.status[l]), l
     for k in range(5):
-        assert abs(dp_g[k] - dp_o[k]) <= 2e-3 * abs(dp_o[k]) + 1e-9, (k, dp_g, dp_o)
+        assert abs(dp_g[k] - dp_o[k]) <= 1e-3 * abs(dp_o[k]) + 1e-9, (k, dp_g, dp_o)
     for l in range(2):
         assert rel_l2(lam_g[l], lam_o[l]) < 1e-3, (l, rel_l2(lam_g[l], lam_o[l]))
         assert np.abs(lam_g[l][:, ~sim.masks[l][0]]).max() == 0.0  # zero off the leaves

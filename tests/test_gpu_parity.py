@@ -9,7 +9,7 @@ sides classify the same float32 level set).
 import numpy as np
 import pytest
 
-from tests.gpu_util import as_fp32_phi, compare_levels, rel_l2, run_both
+from tests.gpu_util import as_fp32_phi, compare_levels, interface_errors, rel_l2, run_both, run_both_schedule
 
 pytestmark = pytest.mark.gpu
 
@@ -74,6 +74,8 @@ def test_static_bubble_levelset_parity():
     g, s = run_both(case, 40)
     r = compare_levels(g, s)[0]
     assert r["u"] < 1e-4 and r["drho"] < 1e-4, r
+    ie = interface_errors(g, s)
+    assert ie["iface_equal"] and ie["u_rel_max"] < 1e-3 and ie["drho_max"] < 1e-5, ie
     phi_g = g.get("phi").reshape(-1).astype(np.float64)
     assert np.abs(phi_g - s.phi).max() < 1e-4
     assert np.array_equal(g.get("phase").reshape(-1), s.phase[-1].astype(np.uint8))
@@ -81,12 +83,15 @@ def test_static_bubble_levelset_parity():
 
 def test_rising_bubble_with_refill_parity():
     case = _bubble2d(N=40, R=7.0, rr=100.0, nu=(0.06, 0.6), g=2e-5, sigma=2e-3)
-    g, s = run_both(case, 60)
+    g, s, refilled = run_both_schedule(case, 60)
     r = compare_levels(g, s)[0]
-    assert s.stats["flipped"] > 0
-    assert r["u"] < 1e-3, r
+    assert s.stats["flipped"] > 0 and refilled.any()
+    assert r["u"] < 1e-4 and r["drho_abs"] < 1e-5, r
+    # cell by cell on the interface cells and on every cell refilled during the run
+    ie = interface_errors(g, s, refilled)
+    assert ie["iface_equal"] and ie["u_rel_max"] < 1e-3 and ie["drho_max"] < 1e-5, ie
     phi_g = g.get("phi").reshape(-1).astype(np.float64)
-    assert np.abs(phi_g - s.phi).max() < 1e-3
+    assert np.abs(phi_g - s.phi).max() < 1e-4
 
 
 def test_two_level_bubble_parity():
@@ -100,6 +105,8 @@ def test_two_level_bubble_parity():
         assert r["u"] < 1e-4 and r["drho_abs"] < 1e-5, r
     for l in range(2):
         assert np.array_equal(g.get("blocks", 0, l), s.status[l]), l
+    ie = interface_errors(g, s)
+    assert ie["iface_equal"] and ie["u_rel_max"] < 1e-3 and ie["drho_max"] < 1e-5, ie
 
 
 @pytest.mark.parametrize("lattice,n,block", [("D2Q9", (48, 24), (8, 8)), ("D3Q19", (12, 8, 12), (4, 4, 4))])

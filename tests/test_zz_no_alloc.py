@@ -70,3 +70,32 @@ def test_noalloc_rejects_fields_larger_than_its_array():
     assert st == 1
     assert b"staging array" in g.lib.lsb_last_error(g.h)
     g.close()
+
+
+def test_noalloc_allocates_nothing_and_exports_to_device_memory():
+    """After the first call (which resolves the fixed array's address and loads the export
+    kernel), repeated calls leave the device's free memory unchanged; a device destination
+    (a torch CUDA tensor, dst_on_host = 0) receives the same values as lsb_get_fields."""
+    import torch
+    from paper_2601_05936_gb300 import lsb
+    g = _grid("D3Q19", 32, 4)
+    code = lsb.FIELD["f"]
+    nbytes = g.lib.lsb_field_bytes(g.h, 0, code, 0)
+    dst = torch.zeros(nbytes // 4, dtype=torch.float32, device="cuda")
+    host = np.empty(nbytes // 4, dtype=np.float32)
+    assert g.lib.lsb_get_fields_noalloc(g.h, 0, code, 0, ctypes.c_void_p(dst.data_ptr()), nbytes, 0) == 0
+    assert g.lib.lsb_get_fields_noalloc(g.h, 0, code, 0, host.ctypes.data, nbytes, 1) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        dst.zero_()
+        st = g.lib.lsb_get_fields_noalloc(g.h, 0, code, 0, ctypes.c_void_p(dst.data_ptr()), nbytes, 0)
+        assert st == 0, g.lib.lsb_last_error(g.h)
+        assert g.lib.lsb_get_fields_noalloc(g.h, 0, code, 0, host.ctypes.data, nbytes, 1) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    want = g.get("f").reshape(-1)
+    assert np.allclose(dst.cpu().numpy(), want, rtol=1e-6, atol=1e-7)
+    assert np.array_equal(dst.cpu().numpy(), host)
+    g.close()
