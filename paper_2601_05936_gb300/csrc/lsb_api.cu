@@ -96,6 +96,7 @@ struct lsb_grid {
   int4 *d_band_info = nullptr;
   unsigned *d_bar = nullptr;  // grid barrier of the persistent level-set kernel
   long long wait_limit = 1LL << 22;  // sleeps of ~64 ns before a device-side wait gives up
+  bool ls_dirty = false;  // stage arrays no longer mirror phi / u~ outside the band (driver 1 ran)
   int driver = 0;             // 0: one launch per level-set pass, 1: one persistent launch
   int2 *d_iface = nullptr, *d_flip = nullptr;
   double *d_obs = nullptr;
@@ -488,6 +489,19 @@ lsb_status classify(lsb_grid *g, int l, int init) {
   return LSB_OK;
 }
 
+// The precondition of the mirrored level-set passes, set in full: p1 = p2 = phi and
+// ut1 = ut2 = ut0 at every finest cell (after creation and after phi or u~ were
+// restored from a stored state).
+lsb_status ls_mirror(lsb_grid *g) {
+  const size_t b1 = sizeof(float) * (size_t)g->nfine, bD = b1 * g->D;
+  CU(cudaMemcpyAsync(g->d_p1, g->d_phi, b1, cudaMemcpyDeviceToDevice, g->stream));
+  CU(cudaMemcpyAsync(g->d_p2, g->d_phi, b1, cudaMemcpyDeviceToDevice, g->stream));
+  CU(cudaMemcpyAsync(g->d_ut[1], g->d_ut[0], bD, cudaMemcpyDeviceToDevice, g->stream));
+  CU(cudaMemcpyAsync(g->d_ut[2], g->d_ut[0], bD, cudaMemcpyDeviceToDevice, g->stream));
+  g->ls_dirty = false;
+  return LSB_OK;
+}
+
 // Level-set update of the finest level l (extension, transport, reinitialisation).
 lsb_status levelset(lsb_grid *g, int l) {
   Ctx C = make_ctx(g);
@@ -496,6 +510,7 @@ lsb_status levelset(lsb_grid *g, int l) {
   const int nt = g->nthreads;
   const int Q = g->Q, D = g->D;
   if (g->driver == 1) {
+    g->ls_dirty = true;  // its passes keep no mirror of u~ in the sweep buffers
     const bool due = g->reinit_every > 0 && ((g->fine_steps[l] + 1) % g->reinit_every == 0) && g->n_reinit > 0;
     // a barrier that gave up leaves its count behind: start every launch from zero
     CU(cudaMemsetAsync(g->d_bar, 0, 2 * sizeof(unsigned), g->stream));
@@ -503,25 +518,25 @@ lsb_status levelset(lsb_grid *g, int l) {
         g->n_reinit, g->d_bar, g->wait_limit);
     return LSB_OK;
   }
+  // passes on mirrored stage arrays: the first sweep stores the plan, the others reuse
+  // it; the first transport stage commits u~; the first reinitialisation stage finds
+  // the frozen cells
   RUN(12, 0, 1, 128, run_ext_init, Q, LN(g, DYN_GRID, 128), C, l);
   const float *uin = g->d_ut[0];
   for (int it = 0; it < g->n_ext; ++it) {
     float *uout = g->d_ut[1 + (it & 1)];
-    RUN(13, 0, nb, nt, run_ext_iter, D, LN(g, nb, nt), C, S, l, uin, uout, it == 0 ? 2 : 3);  // plan, then reuse
+    if (it == 0) RUN(13, 0, nb, nt, run_ext_first, D, LN(g, nb, nt), C, S, l, uin, uout);
+    else RUN(13, 0, nb, nt, run_ext_sweep_mirror, D, LN(g, nb, nt), C, S, l, uin, uout);
     uin = uout;
   }
-  if (g->n_ext > 0) {
-    RUN(13, 0, nb, nt, run_ext_iter, D, LN(g, nb, nt), C, S, l, uin, (float *)nullptr, 1);
-  }
   for (int st = 1; st <= 3; ++st) {
-    RUN(14, 0, nb, nt, run_adv_stage, D, LN(g, nb, nt), C, S, l, st);
+    RUN(14, 0, nb, nt, run_adv_mirror, D, LN(g, nb, nt), C, S, l, st, uin);
   }
   const bool due = g->reinit_every > 0 && ((g->fine_steps[l] + 1) % g->reinit_every == 0);
   if (due && g->n_reinit > 0) {
-    RUN(15, 0, nb, nt, run_reinit_prep, Q, LN(g, nb, nt), C, S, l);
     for (int r = 0; r < g->n_reinit; ++r)
       for (int st = 1; st <= 3; ++st) {
-        RUN(16, 0, nb, nt, run_reinit_stage, D, LN(g, nb, nt), C, S, l, st);
+        RUN(16, 0, nb, nt, run_reinit_mirror, Q, LN(g, nb, nt), C, S, l, st, r == 0 && st == 1 ? 1 : 0);
       }
   }
   return LSB_OK;
@@ -1231,6 +1246,7 @@ lsb_status backward_amr(lsb_grid *g, GeoAdj G) {
     if (g->rec_moving) {
       CU(cudaMemcpyAsync(g->d_phi, src + sf, sizeof(float) * NF, cudaMemcpyDeviceToDevice, g->stream));
       CU(cudaMemcpyAsync(g->d_ut[0], src + sf + NF, sizeof(float) * g->D * NF, cudaMemcpyDeviceToDevice, g->stream));
+      TRY(ls_mirror(g));
       TRY(classify(g, g->Lmax - 1, 0));
     }
     return LSB_OK;
@@ -1478,6 +1494,7 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
     if (cuerr(cudaMemcpy3D(&pr), "phi0 copy")) { lsb_destroy(g); return LSB_ECUDA; }
   }
   s = build_tensor_maps(g);
+  if (s == LSB_OK) s = ls_mirror(g);
   if (s == LSB_OK) s = regrid(g, true);
   if (s) { g_create_error = g->err; lsb_destroy(g); return s; }
   *out = g;
@@ -1517,6 +1534,7 @@ lsb_status lsb_set_params(lsb_grid *g, int case_idx, const lsb_params *params) {
 
 lsb_status lsb_step(lsb_grid *g, int n) {
   if (!g || n < 0) return LSB_EINVAL;
+  if (g->ls_dirty && g->driver == 0) TRY(ls_mirror(g));
   if (g->rec_on) {  // recorded steps run eagerly, checkpointing every rec_every steps
     for (int k = 0; k < n; ++k) {
       if (g->rec_steps % g->rec_every == 0 && (size_t)(g->rec_steps / g->rec_every) == g->rec_ckpt.size())
@@ -1926,6 +1944,7 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
         e = cudaMemcpyAsync(g->d_ut[0], ck + sf + NF, sizeof(float) * D * NF, cudaMemcpyDeviceToDevice, g->stream);
     }
     if (e != cudaSuccess) { st = fail(g, LSB_ECUDA, "checkpoint restore: %s", cudaGetErrorString(e)); break; }
+    if (mv && (st = ls_mirror(g)) != LSB_OK) break;
     // the interface geometry (n, kappa) the first step uses is that of the restored phi
     if (mv && (st = classify(g, 0, 0)) != LSB_OK) break;
     // the grid's tensor maps describe its own buffers: the slots have maps of their own,
@@ -1971,6 +1990,7 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
   if (mv) {
     CU(cudaMemcpyAsync(g->d_phi, g->d_phisave, sizeof(float) * NF, cudaMemcpyDeviceToDevice, g->stream));
     CU(cudaMemcpyAsync(g->d_ut[0], g->d_utsave, sizeof(float) * D * NF, cudaMemcpyDeviceToDevice, g->stream));
+    TRY(ls_mirror(g));
     if (st == LSB_OK) st = classify(g, g->Lmax - 1, 0);  // geometry and lists of the restored phi
   }
   if (st != LSB_OK) return st;

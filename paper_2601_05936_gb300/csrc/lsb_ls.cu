@@ -41,7 +41,12 @@ __global__ void k_classify_phase(Ctx C, BlockShape S, const int *list, int nlist
     const long long c = cidx(L, x, y, z);
     const uint8_t tg = C.tag[L.cell_off + c];
     if (!(tg & TAG_LEAF)) continue;
-    const int gas = C.phi[L.fine_off + c] >= 0.0f ? 1 : 0;
+    const float ph = C.phi[L.fine_off + c];
+    // the transport and reinitialisation stages of this update wrote p1, p2 on band
+    // cells: back to phi, as the mirrored passes expect outside the next band
+    C.p1[L.fine_off + c] = ph;
+    C.p2[L.fine_off + c] = ph;
+    const int gas = ph >= 0.0f ? 1 : 0;
     const int prev = init ? gas : (tg & TAG_GAS);
     const bool flip = !init && (gas != prev);
     uint8_t nt = (tg & (TAG_LEAF | TAG_RLAYER | TAG_GHOST)) | (gas ? TAG_GAS : 0) | (prev ? TAG_PREVGAS : 0) |
@@ -446,7 +451,9 @@ __global__ void k_ext_iter(Ctx C, BlockShape S, int glevel, const float *uin, fl
 // as a lean kernel of its own.  Its chain of dependent loads (band list, block coordinates,
 // plan, values, upwind neighbours) is latency-bound and the band holds only a few blocks
 // per resident CTA, so each thread carries two blocks at once with their loads interleaved.
-template <int D>
+// MIRROR: the forward step's stage arrays equal ut0 outside the band, so every
+// upwind neighbour reads uin (no band bit of the plan consulted).
+template <int D, bool MIRROR = false>
 __global__ void __launch_bounds__(512, 2) k_ext_plan(Ctx C, BlockShape S, int glevel, const float *__restrict__ uin,
                                                      float *__restrict__ uout) {
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
@@ -508,7 +515,7 @@ __global__ void __launch_bounds__(512, 2) k_ext_plan(Ctx C, BlockShape S, int gl
         } else {
           cn = c[k] + dir * (a == 0 ? 1LL : (a == 1 ? (long long)L.p[0] : (long long)L.p[0] * L.p[1]));
         }
-        const float *src = ((pf[k] >> (3 + a)) & 1) ? ui : C.ut0 + fo[k];
+        const float *src = (MIRROR || ((pf[k] >> (3 + a)) & 1)) ? ui : C.ut0 + fo[k];
 #pragma unroll
         for (int b = 0; b < D; ++b) un[k][a][b] = __ldg(src + b * NF + cn);
       }
@@ -720,6 +727,212 @@ __device__ __forceinline__ void d_reinit_stage(const Ctx &C, BlockShape S, int g
 }
 template <int D>
 __global__ void k_reinit_stage(Ctx C, BlockShape S, int glevel, int stage) { d_reinit_stage<D>(C, S, glevel, stage); }
+
+// ------------------------------------------------------------------ forward passes on mirrored stage arrays
+// The forward step keeps the stage arrays equal to the committed fields at every
+// finest cell outside the band when a level-set update starts: p1 = p2 = phi and
+// ut1 = ut2 = ut0.  Band cells restore this at the end of each update (u~ in the
+// first transport stage, which also commits the extension; phi in the phase pass
+// of the classification), and the host copies the arrays in full after creation
+// and after every restore of phi or u~.  A stencil point then reads the stage
+// array wherever it lies, so the passes below need no band or frozen-cell lookups;
+// frozen cells of the reinitialisation write phi into the stage arrays their
+// neighbours read.  The arithmetic and its order are those of the passes above,
+// so the results are the same bit for bit.
+
+// seven values of the stage array along axis a at offsets -3..+3 (clamped or
+// wrapped at the box faces like gather7)
+__device__ __forceinline__ void gather7m(const LevelDev &L, const float *__restrict__ pinL, int x, int y, int z,
+                                         unsigned c, int a, float v[7]) {
+  const int crd = a == 0 ? x : (a == 1 ? y : z);
+  if (crd >= 3 && crd + 3 < L.n[a]) {
+    const int str = a == 0 ? 1 : (a == 1 ? L.p[0] : L.p[0] * L.p[1]);
+#pragma unroll
+    for (int m = 0; m < 7; ++m) v[m] = pinL[c + (m - 3) * str];
+  } else {
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+      int p[3] = {x, y, z};
+      p[a] = clampwrap(L, a, crd + m - 3);
+      v[m] = pinL[cidx(L, p[0], p[1], p[2])];
+    }
+  }
+}
+
+// First extension sweep of a step (mode 2 of d_ext_iter): sweep from uin = ut0 and
+// store the plan (S(phi) n, upwind sides, interface and box-boundary bits).
+template <int D>
+__global__ void k_ext_first(Ctx C, BlockShape S, int glevel, const float *__restrict__ uin,
+                            float *__restrict__ uout) {
+  const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
+  const long long NF = C.nfine;
+  for (int w = blockIdx.x; w < nl; w += gridDim.x) {
+    int x, y, z;
+    const LevelDev &L = band_cell(C, S, glevel, w, threadIdx.x, x, y, z);
+    if (!L.ls_active) continue;
+    if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
+    const long long fo = L.fine_off;
+    const long long c = cidx(L, x, y, z);
+    if (C.tag[L.cell_off + c] & TAG_IFACE) {
+      for (int a = 0; a < D; ++a) uout[a * NF + fo + c] = uin[a * NF + fo + c];
+      C.plan_f[fo + c] = 64;
+      continue;
+    }
+    const int crd[3] = {x, y, z};
+    const int str[3] = {1, L.p[0], L.p[0] * L.p[1]};
+    bool inner = true;
+    for (int a = 0; a < D; ++a) inner = inner && crd[a] >= 1 && crd[a] + 1 < L.n[a];
+    const float *phiL = C.phi + fo;
+    float nvec[3], gm = 0.f;
+    uint8_t pf = inner ? 0 : 128;
+    for (int a = 0; a < D; ++a) {
+      if (inner) {
+        nvec[a] = 0.5f * (phiL[(unsigned)c + str[a]] - phiL[(unsigned)c - str[a]]);
+      } else {
+        int p[3] = {x, y, z}, m[3] = {x, y, z};
+        p[a] = clampwrap(L, a, crd[a] + 1);
+        m[a] = clampwrap(L, a, crd[a] - 1);
+        nvec[a] = 0.5f * (phiL[cidx(L, p[0], p[1], p[2])] - phiL[cidx(L, m[0], m[1], m[2])]);
+      }
+      gm += nvec[a] * nvec[a];
+    }
+    gm = sqrtf(gm);
+    const float ph = phiL[c];
+    const float sg = ph / sqrtf(ph * ph + 1.0f);
+    float u0[3];
+    for (int b = 0; b < D; ++b) u0[b] = uin[b * NF + fo + c];
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < D; ++a) {
+      const float va = gm > 0.f ? sg * nvec[a] / gm : 0.f;
+      const int dir = va > 0.f ? -1 : 1;
+      long long cn;
+      if (inner) {
+        cn = c + dir * str[a];
+      } else {
+        int nb[3] = {x, y, z};
+        nb[a] = clampwrap(L, a, crd[a] + dir);
+        cn = cidx(L, nb[0], nb[1], nb[2]);
+      }
+      for (int b = 0; b < D; ++b) {
+        const float un = uin[b * NF + fo + cn];
+        acc[b] += va * (va > 0.f ? (u0[b] - un) : (un - u0[b]));
+      }
+      C.plan_v[a * NF + fo + c] = va;
+      pf |= (dir < 0 ? 1 : 0) << a;
+    }
+    for (int b = 0; b < D; ++b) uout[b * NF + fo + c] = u0[b] - L.dtau_ext * acc[b];
+    C.plan_f[fo + c] = pf;
+  }
+}
+
+// TVD-RK3 transport stage (as d_adv_stage).  Stage 1 takes u~ from the last
+// extension sweep (ufin) and commits it to ut0, ut1 and ut2 at the cell.
+template <int D>
+__global__ void k_adv_mirror(Ctx C, BlockShape S, int glevel, int stage, const float *__restrict__ ufin) {
+  const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
+  const float *pin = stage == 1 ? C.phi : (stage == 2 ? C.p1 : C.p2);
+  const long long NF = C.nfine;
+  for (int w = blockIdx.x; w < nl; w += gridDim.x) {
+    int x, y, z;
+    const LevelDev &L = band_cell(C, S, glevel, w, threadIdx.x, x, y, z);
+    if (!L.ls_active) continue;
+    if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
+    const unsigned c = (unsigned)cidx(L, x, y, z);
+    const long long fc = L.fine_off + c;
+    float ua[3];
+    if (stage == 1) {
+      for (int a = 0; a < D; ++a) {
+        const float u = ufin[a * NF + fc];
+        ua[a] = u;
+        C.ut0[a * NF + fc] = u;
+        C.ut1[a * NF + fc] = u;
+        C.ut2[a * NF + fc] = u;
+      }
+    } else {
+      for (int a = 0; a < D; ++a) ua[a] = C.ut0[a * NF + fc];
+    }
+    const float *pinL = pin + L.fine_off;
+    float rhs = 0.f;
+    for (int a = 0; a < D; ++a) {
+      float v[7];
+      gather7m(L, pinL, x, y, z, c, a, v);
+      rhs -= ua[a] * (ua[a] >= 0.f ? d5m(v) : d5p(v));
+    }
+    const float p0 = C.phi[fc];
+    if (stage == 1) C.p1[fc] = p0 + rhs;
+    else if (stage == 2) C.p2[fc] = 0.75f * p0 + 0.25f * (C.p1[fc] + rhs);
+    else C.phi[fc] = p0 / 3.0f + (2.0f / 3.0f) * (C.p2[fc] + rhs);
+  }
+}
+
+// Reinitialisation stage (as d_reinit_stage); with prep set (first stage of the first
+// pseudo step) it also finds the frozen cells and S(phi0) as d_reinit_prep does.
+// Frozen cells leave phi as it is and write it into the stage array of stages 1, 2.
+template <int Q>
+__global__ void k_reinit_mirror(Ctx C, BlockShape S, int glevel, int stage, int prep) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
+  const float *pin = stage == 1 ? C.phi : (stage == 2 ? C.p1 : C.p2);
+  for (int w = blockIdx.x; w < nl; w += gridDim.x) {
+    int x, y, z;
+    const LevelDev &L = band_cell(C, S, glevel, w, threadIdx.x, x, y, z);
+    if (!L.ls_active) continue;
+    if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
+    const unsigned cl = (unsigned)cidx(L, x, y, z);
+    const long long fc = L.fine_off + cl;
+    const float p0 = C.phi[fc];
+    bool fr;
+    float s0;
+    if (prep) {
+      const bool g = p0 >= 0.f;
+      fr = false;
+      const bool inner = x >= 1 && x + 1 < L.n[0] && y >= 1 && y + 1 < L.n[1] && (D == 2 || (z >= 1 && z + 1 < L.n[2]));
+      if (inner) {
+        const int q0 = L.p[0], q01 = L.p[0] * L.p[1];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          if (i == LT::REST) continue;
+          if ((C.phi[fc + LT::cx(i) + LT::cy(i) * q0 + LT::cz(i) * q01] >= 0.f) != g) fr = true;
+        }
+      } else {
+        for (int i = 0; i < Q; ++i) {
+          if (i == LT::REST) continue;
+          int tx = x + LT::cx(i), ty = y + LT::cy(i), tz = z + LT::cz(i);
+          if (!(wrap(L, 0, tx) && wrap(L, 1, ty) && (D == 2 || wrap(L, 2, tz)))) continue;
+          if ((C.phi[L.fine_off + cidx(L, tx, ty, tz)] >= 0.f) != g) fr = true;
+        }
+      }
+      s0 = p0 / sqrtf(p0 * p0 + 1.0f);
+      C.frozen[fc] = fr ? 1 : 0;
+      C.s0[fc] = s0;
+    } else {
+      fr = C.frozen[fc] != 0;
+      s0 = C.s0[fc];
+    }
+    if (fr) {
+      if (stage == 1) C.p1[fc] = p0;
+      else if (stage == 2) C.p2[fc] = p0;
+      continue;
+    }
+    const float *pinL = pin + L.fine_off;
+    float g2 = 0.f;
+    for (int a = 0; a < D; ++a) {
+      float v[7];
+      gather7m(L, pinL, x, y, z, cl, a, v);
+      const float dm = weno5(v[1] - v[0], v[2] - v[1], v[3] - v[2], v[4] - v[3], v[5] - v[4]);
+      const float dp = weno5(v[6] - v[5], v[5] - v[4], v[4] - v[3], v[3] - v[2], v[2] - v[1]);
+      float ga;
+      if (s0 > 0.f) ga = fmaxf(fmaxf(dm, 0.f) * fmaxf(dm, 0.f), fminf(dp, 0.f) * fminf(dp, 0.f));
+      else ga = fmaxf(fminf(dm, 0.f) * fminf(dm, 0.f), fmaxf(dp, 0.f) * fmaxf(dp, 0.f));
+      g2 += ga;
+    }
+    const float rhs = L.dtau_reinit * (-s0 * (sqrtf(g2) - 1.0f));
+    if (stage == 1) C.p1[fc] = p0 + rhs;
+    else if (stage == 2) C.p2[fc] = 0.75f * p0 + 0.25f * (C.p1[fc] + rhs);
+    else C.phi[fc] = p0 / 3.0f + (2.0f / 3.0f) * (C.p2[fc] + rhs);
+  }
+}
 
 // ------------------------------------------------------------------ persistent level-set phase
 // The whole level-set update of a finest level (extension, transport,
@@ -1020,6 +1233,24 @@ cudaError_t run_ext_iter(int D, Launch L, Ctx C, BlockShape S, int glevel, const
 }
 cudaError_t run_adv_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage) {
   LDP(k_adv_stage, C, S, glevel, stage);
+}
+cudaError_t run_ext_first(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout) {
+  LDP(k_ext_first, C, S, glevel, uin, uout);
+}
+cudaError_t run_ext_sweep_mirror(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout) {
+  if (D == 2)
+    k_ext_plan<2, true><<<resident_grid(k_ext_plan<2, true>, L.block, L.grid), L.block, 0, L.stream>>>(C, S, glevel, uin,
+                                                                                                      uout);
+  else
+    k_ext_plan<3, true><<<resident_grid(k_ext_plan<3, true>, L.block, L.grid), L.block, 0, L.stream>>>(C, S, glevel, uin,
+                                                                                                      uout);
+  return cudaGetLastError();
+}
+cudaError_t run_adv_mirror(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage, const float *ufin) {
+  LDP(k_adv_mirror, C, S, glevel, stage, ufin);
+}
+cudaError_t run_reinit_mirror(int Q, Launch L, Ctx C, BlockShape S, int glevel, int stage, int prep) {
+  LQP(k_reinit_mirror, C, S, glevel, stage, prep);
 }
 cudaError_t run_reinit_prep(int Q, Launch L, Ctx C, BlockShape S, int glevel) { LQP(k_reinit_prep, C, S, glevel); }
 cudaError_t run_reinit_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage) {

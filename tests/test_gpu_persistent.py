@@ -129,3 +129,26 @@ def test_side_stream_coarse_collide_matches_serial():
     ref = run(True, False)
     _same(ref, run(False, False))
     _same(ref, run(False, True))
+
+
+def test_switching_driver_mid_run_matches_per_pass():
+    """The per-pass launches read stage arrays that mirror phi and u~ outside the band;
+    the persistent launch keeps no such mirror, so after steps with it the handle
+    restores the mirror before the next per-pass step.  Switching 0 -> 1 -> 0 mid-run
+    gives the state of per-pass launches throughout, bit for bit."""
+    from paper_2601_05936_gb300 import lsb
+    from tests.test_gpu_parity import _bubble2d
+    case = _bubble2d(N=64, R=6.0, levels=2, rr=100.0, nu=(0.06, 0.6), g=2e-5, sigma=2e-3)
+    case["refine_dist"] = [8.0]
+    case["regrid_every"] = 5
+    ref = _run(case, 12, 0)
+    g = lsb.Grid(case)
+    g.step(3)
+    g.set_driver(1)
+    g.step(4)
+    g.set_driver(0)
+    g.step(5)
+    g.sync()
+    got = [g.get(f, 0, l) for l in range(2) for f in ("rho", "u")] + [g.get("phi"), g.get("tag")]
+    g.close()
+    _same(ref, got)
