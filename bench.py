@@ -146,12 +146,143 @@ def cpu_baseline(budget_s=20.0, warmup=0, compare_storage=None):
             break
     dt = time.perf_counter() - t0
     cores = (time.process_time() - c0) / dt  # threads busy on average over the timed steps
-    err = oracle_error(case, s, warmup + n, compare_storage) if compare_storage else None
+    if isinstance(compare_storage, (list, tuple)):
+        err = {st: oracle_error(case, s, warmup + n, st) for st in compare_storage}
+    else:
+        err = oracle_error(case, s, warmup + n, compare_storage) if compare_storage else None
     return dict(value=upd / dt / 1e6, unit="MLUPS", cores=round(max(cores, 1.0), 1), kind="oracle",
                 ms_per_step=dt / n * 1e3, error_vs_oracle=err,
                 sample=f"downsampled 32x32x64 base / 2-level copy of the workload, {warmup} untimed and {n} "
                        f"timed coarse steps, {upd:.0f} cell updates in {dt:.1f} s (numpy float64; cores = CPU "
                        f"time / wall time of the timed steps, {os.cpu_count()} host cores)")
+
+
+# DRAM bytes per launch of the collide-and-stream kernel (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum per level's launch class) on a workload, with the sha1 of the kernel
+# sources the capture was taken on: a change to them voids the figure (traffic null).
+TRAFFIC = dict(sources_sha1=None, per_launch={})
+
+
+def kernel_sources_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("lsb_lb.cu", "lsb_device.cuh", "lsb_tma.cuh"):
+        with open(os.path.join(ROOT, "paper_2601_05936_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def step_bytes(g, cases):
+    """Algorithmic bytes of one coarse step, pass by pass: every pass reads each of its
+    inputs once and writes each of its outputs once (s = bytes per stored population,
+    4 or 2; fields float32).  Counts are the work lists after the last step
+    (lsb_work_counts); levels are global, level l takes 2^l sub-steps per coarse step.
+      collide-and-stream: 2 Q s per leaf cell update;
+      ghost ring: 2 Q s per ghost cell and fill (coarse sources read, pushes written);
+      restriction: (2^D + 1) Q s per covered cell and sub-step of the coarse level;
+    finest level, per sub-step (B band cells, I interface cells, K cut links):
+      interface bounce-back: per link the two parked populations, the populations written
+        and the other node's moments, strain rate, normal and curvature;
+      interface velocity: per interface cell its mask, phi, u and u~; per link phi and u;
+      extension sweeps: the first reads phi, u~ and writes u~ and the plan, each later
+        one reads the plan and u~ and writes u~;
+      transport (3 TVD-RK3 stages): stage 1 reads u~ and phi and writes u~ x3 and p1, the
+        others read u~, phi and their stage array and write the next;
+      reinitialisation (3 stages per pseudo step): phi, S(phi0), frozen flag and stage arrays;
+      classification: phase (phi, tag, p1/p2 written back) and cut masks over the band,
+        link list entries per link; curvature fit per interface cell (phi, n, kappa)."""
+    c0 = cases[0]
+    D = 2 if c0["lattice"] == "D2Q9" else 3
+    Q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}[c0["lattice"]]
+    s = 2 if c0.get("storage", "fp32") == "fp16s" else 4
+    L = max(int(c.get("n_levels", 1)) for c in cases)
+    n_ext = int(c0.get("n_ext", 8))
+    re_every = int(c0.get("reinit_every", 1))
+    n_re = int(c0.get("n_reinit", 1)) if re_every == 1 else 0  # bench workloads reinitialise every step
+    live = bool(c0.get("ls_active", True))
+    MF = 1 + D + D * (D + 1) // 2
+    by = dict(collide=0.0, ghost=0.0, restrict=0.0, interface=0.0, ext=0.0, transport=0.0, reinit=0.0,
+              classify=0.0)
+    for l in range(L):
+        w = g.work_counts(l)
+        sub = 2 ** l
+        by["collide"] += sub * w["leaf"] * 2 * Q * s
+        by["ghost"] += sub * w["ghost"] * 2 * Q * s
+        by["restrict"] += sub * w["restrict"] * (2 ** D + 1) * Q * s
+        B, I, K = w["band"], w["iface"], w["links"]
+        if B == 0 and K == 0:
+            continue
+        by["interface"] += sub * K * (8 + s + (MF + D + 1) * 4)
+        if not live:
+            continue
+        by["ext"] += sub * (I * (8 + 2 * D * 4) + K * (1 + D) * 4)
+        if n_ext > 0:
+            by["ext"] += sub * B * (((3 * D + 1) * 4 + 2) + (n_ext - 1) * (3 * D * 4 + 1))
+        by["transport"] += sub * B * ((4 * D + 2) * 4 + 2 * (D + 3) * 4)
+        if n_re > 0:
+            by["reinit"] += sub * B * (13 + 17 * (3 * n_re - 1))
+        by["classify"] += sub * (B * (14 + 5) + K * 9 + I * (4 + (D + 1) * 4))
+    return sum(by.values()), by
+
+
+def oracle_compare(case, steps):
+    """The oracle on the workload's own case (full size, `steps` coarse steps, host cores),
+    then the CUDA path for the same steps: the oracle's throughput and the field errors."""
+    from oracle.sim import Sim
+    case = dict(case)
+    case["phi0"] = np.asarray(case["phi0"], np.float32).astype(np.float64)  # one initial level set for both
+    s = Sim(case)
+    t0 = time.perf_counter()
+    c0 = time.process_time()
+    upd = 0.0
+    for _ in range(steps):
+        s.step(1)
+        upd += sum(float(m[0].sum()) * 2 ** l for l, m in enumerate(s.masks))
+    dt = time.perf_counter() - t0
+    cores = (time.process_time() - c0) / dt
+    err = oracle_error(case, s, steps, case.get("storage", "fp32"))
+    return dict(value=upd / dt / 1e6, unit="MLUPS", cores=round(max(cores, 1.0), 1), kind="oracle",
+                ms_per_step=dt / steps * 1e3, error_vs_oracle=err,
+                sample=f"the workload's own case, {steps} coarse steps, {upd:.0f} cell updates in {dt:.1f} s "
+                       f"(numpy float64; {os.cpu_count()} host cores)")
+
+
+def timed_record(cases, steps, warmup, local, label):
+    """A secondary throughput record: the cases in one handle with graph replay, `warmup`
+    untimed and `steps` timed coarse steps (CUDA events on the library stream), clocks
+    sampled during the timed steps."""
+    import torch
+    from paper_2601_05936_gb300 import lsb
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    g = lsb.Grid(cases, stream=stream, device=local)
+    g.use_graphs(True)
+    g.step(warmup)
+    g.sync()
+    setup_s = time.perf_counter() - t0
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    l0, u0 = g.kernel_launches(), g.cell_updates(total=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches, upd = g.kernel_launches() - l0, g.cell_updates(total=True) - u0
+    sb, by_pass = step_bytes(g, cases)
+    hbm, src = peaks()
+    ach = sb / (ms / steps / 1e3) / 1e9
+    g.close()
+    return dict(label=label, value=upd / (ms / 1e3) / 1e6, unit="MLUPS", steps=steps, warmup=warmup,
+                ms_per_step=ms / steps, gpu_launches=launches, launches_per_step=launches / steps,
+                cell_updates_per_step=upd / steps, setup_s=setup_s,
+                step_roofline=dict(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                                   bytes_per_step=sb, peak_source=src), clocks=clk)
 
 
 def reduce_ranks(ms, upd, dist, device):
@@ -298,7 +429,7 @@ def main():
     ap.add_argument("--workload", default="bubble3d",
                     choices=["bubble3d", "box3d", "ensemble", "adjoint3d", "adjoint3d_ls", "adjoint3d_amr",
                              "adjoint3d_amr_ls",
-                             "paper3d", "couette2d", "cluster3d"],
+                             "paper3d", "couette2d", "cluster3d", "stratified", "drop2d", "bubble2d"],
                     help="bubble3d: the benchmark configuration; box3d: uniform periodic 128^3 box "
                          "(collide-and-stream only, for profiling captures); ensemble: 64 uneven 2D bubbles; "
                          "adjoint3d: reverse sweep over --steps recorded steps of a frozen 3D bubble; "
@@ -307,7 +438,15 @@ def main():
                          "adjoint3d_amr_ls: the same with the finest level's level set moving; "
                          "paper3d: the paper's own 3D box (2d x 2d x 4d, d = 64, uniform, slip lateral walls, "
                          "case --paper-case); couette2d: two-layer Couette with a moving wall, 2048^2; cluster3d: nine "
-                         "rising bubbles (case I) in a 10 d x 10 d x 20 d box, d = 32 finest cells, 2 levels")
+                         "rising bubbles (case I) in a 10 d x 10 d x 20 d box, d = 32 finest cells, 2 levels; "
+                         "stratified: the two-layer channel, 64x32, D2Q9; drop2d: the Laplace static drop, "
+                         "128^2 base, 2 levels; bubble2d: the 2D rising bubble, 160x320 base, 3 levels "
+                         "(the last three also run the oracle on the same case for --oracle-steps)")
+    ap.add_argument("--oracle-steps", type=int, default=None,
+                    help="stratified / drop2d / bubble2d: coarse steps of the oracle comparison "
+                         "(default 1000 / 20 / 2)")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="bubble3d: skip the secondary records (64-case ensemble, FP16 storage)")
     ap.add_argument("--paper-case", default="I", choices=["I", "II"], help="paper3d: parameter set of Sec. 3.2")
     ap.add_argument("--lattice", default="D3Q19", choices=["D3Q19", "D3Q27"],
                     help="paper3d: D3Q19 with BGK in both phases, or the paper's own 3D setup: D3Q27 with BGK "
@@ -369,6 +508,11 @@ def main():
         cases = [case]
     elif args.workload == "couette2d":
         case = workloads.two_layer_couette()
+        case["storage"] = args.storage
+        cases = [case]
+    elif args.workload in ("stratified", "drop2d", "bubble2d"):
+        case = {"stratified": workloads.stratified_channel, "drop2d": workloads.static_drop,
+                "bubble2d": workloads.rising_bubble_2d}[args.workload]()
         case["storage"] = args.storage
         cases = [case]
     else:
@@ -433,8 +577,9 @@ def main():
     # dram__bytes_read.sum + dram__bytes_write.sum, one coarse step of the full-size FP32 run):
     # launch-weighted over the levels; other workloads have no capture
     traffic = None
-    if args.workload == "bubble3d" and args.scale == 1.0 and args.storage == "fp32" and cs_n > 0:
-        per = {"k_collide_stream": 586.7e6, "k_collide_stream_l1": 262.9e6}
+    key = (args.workload, args.scale, args.storage)
+    if TRAFFIC.get("sources_sha1") == kernel_sources_sha1() and key in TRAFFIC.get("per_launch", {}) and cs_n > 0:
+        per = TRAFFIC["per_launch"][key]
         traffic = sum(per.get(k, 0.0) * v[1] for k, v in prof.items() if k.startswith("k_collide_stream")) / cs_n
     roof = dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s",
                 frac=(achieved / hbm) if achieved else None, traffic=traffic, peak_source=src + " (hbm_gbs, of "
@@ -442,6 +587,15 @@ def main():
                 bytes_per_launch=cs_bytes / max(cs_n, 1), avg_launch_ms=cs_ms / max(cs_n, 1),
                 share_of_step=cs_ms / ms_p if ms_p > 0 else None, per_level=per_level,
                 timed_in=f"separate pass of {P} steps with per-launch events (eager launches)")
+    # whole-step roofline: the algorithmic bytes of every pass of a coarse step over the
+    # timed ms per step
+    sb, by_pass = step_bytes(g, cases)
+    step_ach = sb / (ms_max / args.steps / 1e3) / 1e9
+    step_roof = dict(bound="hbm", achieved=step_ach, peak=hbm, unit="GB/s", frac=step_ach / hbm,
+                     bytes_per_step=sb, by_pass_bytes=by_pass, peak_source=src + " (hbm_gbs, of " + src + ")",
+                     note="algorithmic bytes of every pass of one coarse step (each pass reads its inputs once "
+                          "and writes its outputs once; work lists after the last step) / ms_per_step; the "
+                          "finest level's band fields (a few MB) stay in L2 between passes")
     if args.profile_all and rank == 0:
         for k, (kms, kn, kb) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
             print(f"{k:20s} {kms:9.2f} ms {kn:7d} launches {100 * kms / ms_p:5.1f}%", file=sys.stderr)
@@ -471,8 +625,20 @@ def main():
 
     if rank != 0:
         return
-    cpu = None if args.no_cpu_baseline or world > 1 or args.workload != "bubble3d" else \
-        cpu_baseline(compare_storage=args.storage)
+    cpu = None
+    secondary = None
+    if not args.no_cpu_baseline and world == 1 and args.workload == "bubble3d":
+        cpu = cpu_baseline(compare_storage=[args.storage] + (["fp16s"] if args.storage == "fp32" else []))
+    elif not args.no_cpu_baseline and world == 1 and args.workload in ("stratified", "drop2d", "bubble2d"):
+        osteps = args.oracle_steps or {"stratified": 1000, "drop2d": 20, "bubble2d": 2}[args.workload]
+        cpu = oracle_compare(case, osteps)
+    if world == 1 and args.workload == "bubble3d" and args.scale == 1.0 and not args.no_secondary:
+        ens = workloads.ensemble()
+        secondary = dict(
+            ensemble=timed_record(ens, args.steps, args.warmup, local,
+                                  "ensemble of 64 2D rising bubbles (96x192..256x512, 1-3 levels), one handle"),
+            fp16s=timed_record([workloads.rising_bubble_3d(storage="fp16s")], args.steps, args.warmup, local,
+                               "the same 3D bubble with FP16 storage / FP32 arithmetic"))
     metric = METRIC if args.workload == "bubble3d" else f"MLUPS (leaf cell updates / s), {args.workload}"
     lattice = case["lattice"]
     state_gb = sum(float(np.prod([b * 2 ** l for b in c["base"]])) for c in cases
@@ -488,7 +654,8 @@ def main():
                             l2_flush=f"state {state_gb:.1f} GB (both buffers) >> 129 MB L2",
                             bubble=dict(centroid=[float(v) if np.isfinite(v) else None for v in obs["centroid"]],
                                         velocity=[float(v) if np.isfinite(v) else None for v in obs["velocity"]])),
-                roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches, clocks=clk)
+                roofline=roof, step_roofline=step_roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches,
+                launches_per_step=launches / args.steps, clocks=clk, secondary=secondary)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

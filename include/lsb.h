@@ -259,6 +259,19 @@ lsb_status lsb_autotune(int n_cases, const lsb_grid_desc *descs, const lsb_param
  * count).  Either pointer may be NULL.  Needs no synchronisation. */
 lsb_status lsb_cell_updates(const lsb_grid *g, double *per_coarse_step, double *total_done);
 
+/*
+ * Sizes of the work lists of global level `level` (summed over the cases whose
+ * level it is) as they stand after the last step, for diagnostics and the
+ * throughput accounting (the paper has no counterpart): out[0] leaf cells,
+ * out[1] band cells (band blocks x block cells), out[2] interface cells,
+ * out[3] cut links, out[4] cells flipped at the last finest step (1..4: the
+ * finest level of a case only, else 0), out[5] ghost-ring cells filled from
+ * the coarser level, out[6] covered cells restricted from the finer level.
+ * Host array of n <= LSB_NWORK values.  Synchronises.  Errors: LSB_EINVAL.
+ */
+enum { LSB_NWORK = 7 };
+lsb_status lsb_work_counts(lsb_grid *g, int level, long long *out, int n);
+
 /* Velocity-set tables compiled into the library (Sec. 2.1, Fig. 1): c receives
  * Q x 3 ints, w Q floats, opp Q ints (opposite directions); any may be NULL.
  * Returns Q, or 0 for an unknown lattice.  Needs no GPU. */

@@ -275,7 +275,15 @@ lsb_status launched(lsb_grid *g, cudaError_t e) {
   return LSB_OK;
 }
 
-Launch LN(const lsb_grid *g, int grid, int block) { return Launch{grid, block, g->stream}; }
+// Kernels of a handle with a stream of its own launch as programmatic dependents of the
+// kernel before them (off while kernel timing is on, so that each launch's events
+// bracket that launch alone).
+#ifndef LSB_PDL
+#define LSB_PDL 1
+#endif
+Launch LN(const lsb_grid *g, int grid, int block) {
+  return Launch{grid, block, g->stream, LSB_PDL && g->stream != nullptr && g->prof_mode == 0 ? 1 : 0};
+}
 
 cudaEvent_t take_event(lsb_grid *g) {
   if (!g->ev_pool.empty()) {
@@ -1804,6 +1812,25 @@ lsb_status lsb_cell_updates(const lsb_grid *g, double *per_coarse_step, double *
   if (!g) return LSB_EINVAL;
   if (per_coarse_step) *per_coarse_step = updates_per_step(g);
   if (total_done) *total_done = g->updates_done;
+  return LSB_OK;
+}
+
+lsb_status lsb_work_counts(lsb_grid *g, int level, long long *out, int n) {
+  if (!g || !out || n < 0 || level < 0 || level >= MAXL) return LSB_EINVAL;
+  long long v[LSB_NWORK] = {0};
+  v[0] = (long long)g->leaf_cells[level];
+  v[5] = g->ghost_cells[level].n;
+  v[6] = g->rl_cells[level].n;
+  if (has_finest(g, level)) {
+    int h[NCOUNT] = {0};
+    CU(cudaMemcpyAsync(h, g->d_counters + level * NCOUNT, sizeof(int) * NCOUNT, cudaMemcpyDeviceToHost, g->stream));
+    CU(cudaStreamSynchronize(g->stream));
+    v[1] = (long long)std::min(h[3], g->band_cap) * g->nthreads;
+    v[2] = std::min<long long>(h[1], g->list_cap);
+    v[3] = std::min<long long>(h[0], g->link_cap);
+    v[4] = std::min<long long>(h[2], g->list_cap);
+  }
+  for (int k = 0; k < n && k < LSB_NWORK; ++k) out[k] = v[k];
   return LSB_OK;
 }
 

@@ -12,6 +12,11 @@ constexpr float CS2 = 1.0f / 3.0f;
 // ---------------------------------------------------------------- lattices
 // D2Q9 ordering of Fig. 1a: -x, +x, -y, +y, (-1,-1), (-1,1), (1,1), (1,-1), rest.
 // D3Q19: the axis and edge velocities of Fig. 1b in that order, rest last.
+// First statement of every kernel of the step: wait for the grid the kernel depends
+// on (and its memory) when it was launched as a programmatic dependent, then let the
+// next kernel on the stream be scheduled.  Both are no-ops for an ordinary launch.
+#define LSB_GRID_WAIT() asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory")
+
 template <int Q> struct Lat;
 
 template <> struct Lat<9> {

@@ -16,7 +16,45 @@ constexpr int kMaxDevices = 64;
 struct Launch {
   int grid, block;
   cudaStream_t stream;
+  int pdl = 0;  // programmatic dependent launch: may overlap the previous kernel's tail
 };
+
+// Launch kern on L's grid and stream.  With L.pdl the launch carries the
+// programmatic-stream-serialization attribute: the kernel may be scheduled while
+// the kernel before it on the stream finishes, and waits for it (and for its
+// memory) in LSB_GRID_WAIT at its start.
+template <typename... P, typename... A>
+inline void lsb_launch(void (*kern)(P...), const Launch &L, size_t smem, A... args) {
+  if (!L.pdl) {
+    kern<<<L.grid, L.block, smem, L.stream>>>(args...);
+    return;
+  }
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)L.grid);
+  cfg.blockDim = dim3((unsigned)L.block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = L.stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+template <typename K>
+struct Launcher {
+  K kern;
+  Launch L;
+  size_t smem;
+  template <typename... A>
+  void operator()(A... args) const { lsb_launch(kern, L, smem, args...); }
+};
+template <typename K>
+inline Launcher<K> launcher(K kern, const Launch &L, size_t smem = 0) { return Launcher<K>{kern, L, smem}; }
+inline Launch with_grid(Launch L, int grid) {
+  L.grid = grid;
+  return L;
+}
 
 // lsb_lb.cu: lattice Boltzmann, interface bounce-back, level transfers
 cudaError_t run_init(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n);

@@ -177,6 +177,7 @@ __device__ __forceinline__ void collide_phase(float *f, float om, const float ac
 // Rest equilibrium with the hydrostatic density rho_hat = 1 - g.(x - x_ref)/c_s^2.
 template <int Q, typename T>
 __global__ void k_init(Ctx C, BlockShape S, const int *list, int nlist) {
+  LSB_GRID_WAIT();
   using LT = Lat<Q>;
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     int gb = list[w];
@@ -211,6 +212,7 @@ __global__ void k_init(Ctx C, BlockShape S, const int *list, int nlist) {
 template <int Q, typename T>
 __global__ void __launch_bounds__(512, (Q == 27 ? 1 : LSB_CS_MINB)) k_collide_stream(Ctx C, BlockShape S,
                                                                      const int *__restrict__ list, int nlist) {
+  LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
@@ -353,6 +355,7 @@ template <int Q, typename T>
 __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape S, const int *__restrict__ list,
                                                                int nlist, const CUtensorMap *__restrict__ tmaps,
                                                                const CUtensorMap *__restrict__ tmaps_tag) {
+  LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -541,6 +544,7 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
 // (the link list of the classification, in link-buffer order).
 template <int Q, typename T>
 __global__ void k_interface_bc(Ctx C, int glevel) {
+  LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   const long long n = min((long long)C.counters[glevel * NCOUNT + 0], C.link_cap);
@@ -664,6 +668,7 @@ __device__ __forceinline__ void rescale_neq(float *f, float fac) {
 // every cell of the listed blocks.
 template <int Q, typename T>
 __global__ void k_restrict(Ctx C, BlockShape S, const int *list, int nlist, int all_cells) {
+  LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
@@ -757,6 +762,7 @@ __device__ __forceinline__ void interp_coarse(const Ctx &C, const LevelDev &Lc, 
 // TAG_LEAF must mark the cells that hold valid data (old or new leaves).
 template <int Q, typename T>
 __global__ void k_prolong(Ctx C, BlockShape S, const int *list, int nlist) {
+  LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
@@ -784,6 +790,7 @@ __global__ void k_prolong(Ctx C, BlockShape S, const int *list, int nlist) {
 // classification that follows every regrid.
 template <int Q>
 __global__ void k_level_tags(Ctx C, BlockShape S, const int *list, int nlist) {
+  LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
@@ -828,6 +835,7 @@ __global__ void k_level_tags(Ctx C, BlockShape S, const int *list, int nlist) {
 // and case run instead of one per warp and block.
 template <int Q, typename T>
 __global__ void k_observables(Ctx C, BlockShape S, const int *list, int nlist, double *out, int stride) {
+  LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   constexpr int NV = 4 + 2 * D;
@@ -906,6 +914,7 @@ __global__ void k_observables(Ctx C, BlockShape S, const int *list, int nlist, d
 // Dense copy of one level: populations (full f = f~ + w), rho_hat, u.
 template <int Q, typename T>
 __global__ void k_export(Ctx C, int ld, int field, float *dst) {
+  LSB_GRID_WAIT();
   using LT = Lat<Q>;
   const LevelDev &L = C.lds[ld];
   const long long ntrue = (long long)L.n[0] * L.n[1] * L.n[2];
@@ -938,6 +947,7 @@ __global__ void k_export(Ctx C, int ld, int field, float *dst) {
 // one thread per cell instead of one CTA per mostly idle block.
 __global__ void k_collect(Ctx C, BlockShape S, const int *list, int nlist, int bits, int2 *out, int *count,
                           int cap) {
+  LSB_GRID_WAIT();
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     const int gb = list[w];
     int x, y, z;
@@ -954,6 +964,7 @@ __global__ void k_collect(Ctx C, BlockShape S, const int *list, int nlist, int b
 // Restriction layer from a cell list (one thread per covered cell).
 template <int Q, typename T>
 __global__ void k_restrict_cells(Ctx C, const int2 *cells, int n) {
+  LSB_GRID_WAIT();
   constexpr int D = Lat<Q>::D;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     const int2 it = cells[e];
@@ -990,6 +1001,7 @@ __global__ void k_restrict_cells(Ctx C, const int2 *cells, int n) {
 // fine-level collision, pushed into the fine leaves that stream from it.
 template <int Q, typename T>
 __global__ void k_ghost_cells(Ctx C, const int2 *cells, int n, float theta) {
+  LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
@@ -1072,6 +1084,7 @@ __device__ __forceinline__ float feq_lane(float wi, int cxi, int cyi, int czi, f
 
 template <int Q, typename T>
 __global__ void k_restrict_cells_w(Ctx C, const int2 *cells, int n) {
+  LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D, LPC = GroupLanes<Q>::LPC, GPW = GroupLanes<Q>::GPW;
   const int lane = threadIdx.x & 31, sub = lane & (LPC - 1);
@@ -1148,7 +1161,7 @@ cudaError_t noalloc_scratch(float **ptr) {
     return cudaGetLastError();                                   \
   } while (0)
 
-#define LK(kern) kern<Q_, T_><<<L.grid, L.block, 0, L.stream>>>
+#define LK(kern) launcher(kern<Q_, T_>, L, 0)
 
 cudaError_t run_init(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n) {
   LSB_QT(Q, st, (LK(k_init)(C, S, list, n)));
@@ -1182,7 +1195,7 @@ cudaError_t run_collide_stream_tma(int Q, int st, Launch L, Ctx C, BlockShape S,
                                    const CUtensorMap *tmaps, const CUtensorMap *tmaps_tag) {
   const size_t smem = tma_smem_bytes(Q, st, L.block);
   LSB_QT(Q, st,
-         (k_collide_stream_tma<Q_, T_><<<L.grid, L.block, smem, L.stream>>>(C, S, list, n, tmaps, tmaps_tag)));
+         (launcher(k_collide_stream_tma<Q_, T_>, L, smem)(C, S, list, n, tmaps, tmaps_tag)));
 }
 cudaError_t run_interface_bc(int Q, int st, Launch L, Ctx C, int glevel) {
   LSB_QT(Q, st, (LK(k_interface_bc)(C, glevel)));
@@ -1209,7 +1222,7 @@ cudaError_t run_export_noalloc(int Q, int st, Launch L, Ctx C, int ld, int field
 }
 cudaError_t run_collect(Launch L, Ctx C, BlockShape S, const int *list, int n, int bits, int2 *out, int *count,
                         int cap) {
-  k_collect<<<L.grid, L.block, 0, L.stream>>>(C, S, list, n, bits, out, count, cap);
+  launcher(k_collect, L, 0)(C, S, list, n, bits, out, count, cap);
   return cudaGetLastError();
 }
 // One warp per GPW cells for the lattices with a group kernel (D2Q9, D3Q19); D3Q27 keeps
@@ -1225,11 +1238,11 @@ Launch group_launch(Launch L, int Q, int n) {
   do {                                                                                             \
     L = group_launch(L, Q, n);                                                                     \
     if (Q == 9) {                                                                                  \
-      if (st == 0) KERN<9, float><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);                \
-      else KERN<9, __half><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);                       \
+      if (st == 0) launcher(KERN<9, float>, L, 0)(__VA_ARGS__);                \
+      else launcher(KERN<9, __half>, L, 0)(__VA_ARGS__);                       \
     } else {                                                                                       \
-      if (st == 0) KERN<19, float><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);               \
-      else KERN<19, __half><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);                      \
+      if (st == 0) launcher(KERN<19, float>, L, 0)(__VA_ARGS__);               \
+      else launcher(KERN<19, __half>, L, 0)(__VA_ARGS__);                      \
     }                                                                                              \
     return cudaGetLastError();                                                                     \
   } while (0)
@@ -1241,9 +1254,9 @@ cudaError_t run_ghost_cells(int Q, int st, Launch L, Ctx C, const int2 *cells, i
   LSB_QT(Q, st, (LK(k_ghost_cells)(C, cells, n, theta)));
 }
 cudaError_t run_level_tags(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n) {
-  if (Q == 9) k_level_tags<9><<<L.grid, L.block, 0, L.stream>>>(C, S, list, n);
-  else if (Q == 19) k_level_tags<19><<<L.grid, L.block, 0, L.stream>>>(C, S, list, n);
-  else k_level_tags<27><<<L.grid, L.block, 0, L.stream>>>(C, S, list, n);
+  if (Q == 9) launcher(k_level_tags<9>, L, 0)(C, S, list, n);
+  else if (Q == 19) launcher(k_level_tags<19>, L, 0)(C, S, list, n);
+  else launcher(k_level_tags<27>, L, 0)(C, S, list, n);
   return cudaGetLastError();
 }
 

@@ -9,6 +9,8 @@
 // cell and their 3^D neighbours (active blocks only).  phi, the RK stage
 // arrays and the extension velocity are dense finest-level arrays; stencil
 // points outside the band read the committed fields.
+#include <cooperative_groups.h>
+
 #include <map>
 #include <mutex>
 
@@ -27,6 +29,7 @@ __device__ __forceinline__ bool in_band(const Ctx &C, const LevelDev &L, const B
 // flag is kept as BF_OLDBAND (other blocks keep flag 0).
 template <int Q>
 __global__ void k_classify_phase(Ctx C, BlockShape S, const int *list, int nlist, int glevel, int init) {
+  LSB_GRID_WAIT();
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     const int gb = list[w];
     // phi changes only on band cells, so outside the previous band no phase (and no
@@ -64,6 +67,7 @@ __global__ void k_classify_phase(Ctx C, BlockShape S, const int *list, int nlist
 // previous band get BF_CHECK.
 template <int Q>
 __global__ void k_flip_mark(Ctx C, BlockShape S, int glevel) {
+  LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   const int n = min(C.counters[glevel * NCOUNT + 2], (int)C.list_cap);
@@ -92,6 +96,7 @@ __global__ void k_flip_mark(Ctx C, BlockShape S, int glevel) {
 // the band with none, an all-zero mask already.
 template <int Q>
 __global__ void k_classify_links(Ctx C, BlockShape S, const int *list, int nlist, int glevel, int full) {
+  LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
@@ -104,12 +109,13 @@ __global__ void k_classify_links(Ctx C, BlockShape S, const int *list, int nlist
     }
     int x, y, z;
     const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
-    bool has = false;
+    uint32_t m = 0;
+    long long c = 0;
+    uint8_t tg = 0;
     if (x < L.n[0] && y < L.n[1] && z < L.n[2]) {
-      const long long c = cidx(L, x, y, z);
-      const uint8_t tg = C.tag[L.cell_off + c];
+      c = cidx(L, x, y, z);
+      tg = C.tag[L.cell_off + c];
       if (tg & TAG_LEAF) {
-        uint32_t m = 0;
         const bool inner = x >= 1 && x + 1 < L.n[0] && y >= 1 && y + 1 < L.n[1] && (D == 2 || (z >= 1 && z + 1 < L.n[2]));
         if (inner) {  // every source inside the box: direct offsets
           const long long p0 = L.p[0], p01 = (long long)L.p[0] * L.p[1];
@@ -130,30 +136,48 @@ __global__ void k_classify_links(Ctx C, BlockShape S, const int *list, int nlist
           }
         }
         C.cmask[L.fine_off + c] = m;
-        if (m) {
-          has = true;
-          int base = atomicAdd(&C.counters[glevel * NCOUNT + 0], __popc(m));
-          if ((long long)base + __popc(m) > C.link_cap) atomicOr(C.err, ERR_LINK_OVF);
-          C.cbase[L.fine_off + c] = base;
-          // the link list: one entry per cut link, in link-buffer order
-          const int2 cell = make_int2(C.blk_ld[gb], (int)c);
-          uint32_t mm = m;
-          for (int r = 0; mm; ++r) {
-            const int k = __ffs(mm) - 1;
-            mm &= mm - 1u;
-            if ((long long)base + r < C.link_cap) {
-              C.link_cell[C.link_list_off[glevel] + base + r] = cell;
-              C.link_dir[C.link_list_off[glevel] + base + r] = (uint8_t)k;
-            }
-          }
-          C.tag[L.cell_off + c] = tg | TAG_IFACE;
-          int e = atomicAdd(&C.counters[glevel * NCOUNT + 1], 1);
-          if (e < C.list_cap) C.iface_list[(long long)glevel * C.list_cap + e] = make_int2(C.blk_ld[gb], (int)c);
-          else atomicOr(C.err, ERR_LIST_OVF);
-        }
       }
     }
-    const bool any = __syncthreads_or(has);
+    // slots in the link list and the interface list, one atomic per warp (every lane
+    // of the CTA is here: the block-level branch above is uniform)
+    const int lane = threadIdx.x & 31;
+    const int np = __popc(m);
+    int incl = np;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int wlinks = __shfl_sync(0xffffffffu, incl, 31);
+    const unsigned wcells = __ballot_sync(0xffffffffu, m != 0);
+    int lbase = 0, cbase0 = 0;
+    if (lane == 0 && wcells) {
+      lbase = atomicAdd(&C.counters[glevel * NCOUNT + 0], wlinks);
+      cbase0 = atomicAdd(&C.counters[glevel * NCOUNT + 1], __popc(wcells));
+    }
+    lbase = __shfl_sync(0xffffffffu, lbase, 0);
+    cbase0 = __shfl_sync(0xffffffffu, cbase0, 0);
+    if (m) {
+      const int base = lbase + incl - np;
+      if ((long long)base + np > C.link_cap) atomicOr(C.err, ERR_LINK_OVF);
+      C.cbase[L.fine_off + c] = base;
+      // the link list: one entry per cut link, in link-buffer order
+      const int2 cell = make_int2(C.blk_ld[gb], (int)c);
+      uint32_t mm = m;
+      for (int r = 0; mm; ++r) {
+        const int k = __ffs(mm) - 1;
+        mm &= mm - 1u;
+        if ((long long)base + r < C.link_cap) {
+          C.link_cell[C.link_list_off[glevel] + base + r] = cell;
+          C.link_dir[C.link_list_off[glevel] + base + r] = (uint8_t)k;
+        }
+      }
+      C.tag[L.cell_off + c] = tg | TAG_IFACE;
+      const int e = cbase0 + __popc(wcells & ((1u << lane) - 1u));
+      if (e < C.list_cap) C.iface_list[(long long)glevel * C.list_cap + e] = make_int2(C.blk_ld[gb], (int)c);
+      else atomicOr(C.err, ERR_LIST_OVF);
+    }
+    const bool any = __syncthreads_or(m != 0);
     if (threadIdx.x == 0) C.bflag[gb] = any ? BF_IFACE : 0;
   }
 }
@@ -162,6 +186,7 @@ __global__ void k_classify_links(Ctx C, BlockShape S, const int *list, int nlist
 // holds an interface cell); band blocks are listed.
 template <int Q>
 __global__ void k_band(Ctx C, BlockShape S, const int *list, int nlist, int glevel) {
+  LSB_GRID_WAIT();
   constexpr int D = Lat<Q>::D;
   for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nlist; w += gridDim.x * blockDim.x) {
     const int gb = list[w];
@@ -188,7 +213,11 @@ __global__ void k_band(Ctx C, BlockShape S, const int *list, int nlist, int glev
         }
     if (band && C.bstat[gb] == BLK_LEAF) {
       C.bflag[gb] = C.bflag[gb] | BF_BAND;
-      int e = atomicAdd(&C.counters[glevel * NCOUNT + 3], 1);
+      // one atomic per group of lanes that list a block together
+      cooperative_groups::coalesced_group grp = cooperative_groups::coalesced_threads();
+      int e0 = 0;
+      if (grp.thread_rank() == 0) e0 = atomicAdd(&C.counters[glevel * NCOUNT + 3], (int)grp.size());
+      const int e = grp.shfl(e0, 0) + (int)grp.thread_rank();
       if (e < C.band_cap) {
         C.band_list[(long long)glevel * C.band_cap + e] = gb;
         C.band_info[(long long)glevel * C.band_cap + e] = C.blk_info[gb];
@@ -206,6 +235,7 @@ __global__ void k_band(Ctx C, BlockShape S, const int *list, int nlist, int glev
 // n = g/|g|, kappa = (|g|^2 tr H - g.H.g)/|g|^3.
 template <int D>
 __global__ void k_geometry(Ctx C, int glevel, int which) {
+  LSB_GRID_WAIT();
   const int n = min(C.counters[glevel * NCOUNT + (which ? 2 : 1)], (int)C.list_cap);
   const int2 *lst = (which ? C.flip_list : C.iface_list) + (long long)glevel * C.list_cap;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
@@ -323,7 +353,10 @@ __device__ __forceinline__ void d_ext_init(const Ctx &C, int glevel) {
   }
 }
 template <int Q>
-__global__ void k_ext_init(Ctx C, int glevel) { d_ext_init<Q>(C, glevel); }
+__global__ void k_ext_init(Ctx C, int glevel) {
+  LSB_GRID_WAIT();
+  d_ext_init<Q>(C, glevel);
+}
 
 // One Jacobi sweep of first-order upwind extension on the band (interface cells
 // copy their value).  Neighbours outside the band read the committed field ut0.
@@ -445,7 +478,10 @@ __device__ __forceinline__ void d_ext_iter(const Ctx &C, BlockShape S, int gleve
   }
 }
 template <int D>
-__global__ void k_ext_iter(Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int mode) { d_ext_iter<D>(C, S, glevel, uin, uout, mode); }
+__global__ void k_ext_iter(Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int mode) {
+  LSB_GRID_WAIT();
+  d_ext_iter<D>(C, S, glevel, uin, uout, mode);
+}
 
 // The sweeps after the first (mode 3 of d_ext_iter: the same arithmetic in the same order)
 // as a lean kernel of its own.  Its chain of dependent loads (band list, block coordinates,
@@ -456,6 +492,7 @@ __global__ void k_ext_iter(Ctx C, BlockShape S, int glevel, const float *uin, fl
 template <int D, bool MIRROR = false>
 __global__ void __launch_bounds__(512, 2) k_ext_plan(Ctx C, BlockShape S, int glevel, const float *__restrict__ uin,
                                                      float *__restrict__ uout) {
+  LSB_GRID_WAIT();
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
   const int *lst = C.band_list + (long long)glevel * C.band_cap;
   const long long NF = C.nfine;
@@ -629,7 +666,10 @@ __device__ __forceinline__ void d_adv_stage(const Ctx &C, BlockShape S, int glev
   }
 }
 template <int D>
-__global__ void k_adv_stage(Ctx C, BlockShape S, int glevel, int stage) { d_adv_stage<D>(C, S, glevel, stage); }
+__global__ void k_adv_stage(Ctx C, BlockShape S, int glevel, int stage) {
+  LSB_GRID_WAIT();
+  d_adv_stage<D>(C, S, glevel, stage);
+}
 
 // ------------------------------------------------------------------ reinitialisation
 // Frozen cells (sign change to any lattice neighbour in the box) and S(phi0).
@@ -668,7 +708,10 @@ __device__ __forceinline__ void d_reinit_prep(const Ctx &C, BlockShape S, int gl
   }
 }
 template <int Q>
-__global__ void k_reinit_prep(Ctx C, BlockShape S, int glevel) { d_reinit_prep<Q>(C, S, glevel); }
+__global__ void k_reinit_prep(Ctx C, BlockShape S, int glevel) {
+  LSB_GRID_WAIT();
+  d_reinit_prep<Q>(C, S, glevel);
+}
 
 // HJ-WENO5 one-sided derivative (Jiang & Peng 2000) from the five differences.
 // Constant divisions are multiplications by the reciprocals, and the three weights
@@ -726,7 +769,10 @@ __device__ __forceinline__ void d_reinit_stage(const Ctx &C, BlockShape S, int g
   }
 }
 template <int D>
-__global__ void k_reinit_stage(Ctx C, BlockShape S, int glevel, int stage) { d_reinit_stage<D>(C, S, glevel, stage); }
+__global__ void k_reinit_stage(Ctx C, BlockShape S, int glevel, int stage) {
+  LSB_GRID_WAIT();
+  d_reinit_stage<D>(C, S, glevel, stage);
+}
 
 // ------------------------------------------------------------------ forward passes on mirrored stage arrays
 // The forward step keeps the stage arrays equal to the committed fields at every
@@ -764,6 +810,7 @@ __device__ __forceinline__ void gather7m(const LevelDev &L, const float *__restr
 template <int D>
 __global__ void k_ext_first(Ctx C, BlockShape S, int glevel, const float *__restrict__ uin,
                             float *__restrict__ uout) {
+  LSB_GRID_WAIT();
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
   const long long NF = C.nfine;
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
@@ -829,6 +876,7 @@ __global__ void k_ext_first(Ctx C, BlockShape S, int glevel, const float *__rest
 // extension sweep (ufin) and commits it to ut0, ut1 and ut2 at the cell.
 template <int D>
 __global__ void k_adv_mirror(Ctx C, BlockShape S, int glevel, int stage, const float *__restrict__ ufin) {
+  LSB_GRID_WAIT();
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
   const float *pin = stage == 1 ? C.phi : (stage == 2 ? C.p1 : C.p2);
   const long long NF = C.nfine;
@@ -870,6 +918,7 @@ __global__ void k_adv_mirror(Ctx C, BlockShape S, int glevel, int stage, const f
 // Frozen cells leave phi as it is and write it into the stage array of stages 1, 2.
 template <int Q>
 __global__ void k_reinit_mirror(Ctx C, BlockShape S, int glevel, int stage, int prep) {
+  LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
@@ -977,6 +1026,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, long long 
 template <int Q>
 __global__ void k_levelset_persistent(Ctx C, BlockShape S, int glevel, int n_ext, int reinit, int n_reinit,
                                       unsigned *bar, long long limit) {
+  LSB_GRID_WAIT();
   constexpr int D = Lat<Q>::D;
   d_ext_init<Q>(C, glevel);
   if (!grid_barrier(bar, C.err, limit)) return;
@@ -1032,6 +1082,7 @@ __device__ __forceinline__ float feq_q(int i, float drho, const float u[3]) {
 
 template <int Q, typename T>
 __global__ void k_refill(Ctx C, int glevel) {
+  LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   const int n = min(C.counters[glevel * NCOUNT + 2], (int)C.list_cap);
@@ -1128,6 +1179,7 @@ __global__ void k_refill(Ctx C, int glevel) {
 // Per listed coarse block: min |phi| (mode 0) or max phi (mode 1) over the
 // finest cells under it.
 __global__ void k_sensor(Ctx C, BlockShape S, const int *list, int nlist, int mode, float *out) {
+  LSB_GRID_WAIT();
   __shared__ float red[32];
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     const int gb = list[w];
@@ -1169,29 +1221,29 @@ __global__ void k_sensor(Ctx C, BlockShape S, const int *list, int nlist, int mo
 // ------------------------------------------------------------------ host launchers
 #define LQ(kern, ...)                                                          \
   do {                                                                         \
-    if (Q == 9) kern<9><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);        \
-    else if (Q == 19) kern<19><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__); \
-    else kern<27><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);              \
+    if (Q == 9) launcher(kern<9>, L, 0)(__VA_ARGS__);        \
+    else if (Q == 19) launcher(kern<19>, L, 0)(__VA_ARGS__); \
+    else launcher(kern<27>, L, 0)(__VA_ARGS__);              \
     return cudaGetLastError();                                                 \
   } while (0)
 #define LD(kern, ...)                                                          \
   do {                                                                         \
-    if (D == 2) kern<2><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);        \
-    else kern<3><<<L.grid, L.block, 0, L.stream>>>(__VA_ARGS__);               \
+    if (D == 2) launcher(kern<2>, L, 0)(__VA_ARGS__);        \
+    else launcher(kern<3>, L, 0)(__VA_ARGS__);               \
     return cudaGetLastError();                                                 \
   } while (0)
 // Same for a band-list kernel, with the grid capped at the resident CTAs.
 #define LDP(kern, ...)                                                                             \
   do {                                                                                             \
-    if (D == 2) kern<2><<<resident_grid(kern<2>, L.block, L.grid), L.block, 0, L.stream>>>(__VA_ARGS__); \
-    else kern<3><<<resident_grid(kern<3>, L.block, L.grid), L.block, 0, L.stream>>>(__VA_ARGS__);        \
+    if (D == 2) launcher(kern<2>, with_grid(L, resident_grid(kern<2>, L.block, L.grid)))(__VA_ARGS__); \
+    else launcher(kern<3>, with_grid(L, resident_grid(kern<3>, L.block, L.grid)))(__VA_ARGS__);        \
     return cudaGetLastError();                                                                     \
   } while (0)
 #define LQP(kern, ...)                                                                             \
   do {                                                                                             \
-    if (Q == 9) kern<9><<<resident_grid(kern<9>, L.block, L.grid), L.block, 0, L.stream>>>(__VA_ARGS__); \
-    else if (Q == 19) kern<19><<<resident_grid(kern<19>, L.block, L.grid), L.block, 0, L.stream>>>(__VA_ARGS__); \
-    else kern<27><<<resident_grid(kern<27>, L.block, L.grid), L.block, 0, L.stream>>>(__VA_ARGS__);      \
+    if (Q == 9) launcher(kern<9>, with_grid(L, resident_grid(kern<9>, L.block, L.grid)))(__VA_ARGS__); \
+    else if (Q == 19) launcher(kern<19>, with_grid(L, resident_grid(kern<19>, L.block, L.grid)))(__VA_ARGS__); \
+    else launcher(kern<27>, with_grid(L, resident_grid(kern<27>, L.block, L.grid)))(__VA_ARGS__);      \
     return cudaGetLastError();                                                                     \
   } while (0)
 
@@ -1239,10 +1291,10 @@ cudaError_t run_ext_first(int D, Launch L, Ctx C, BlockShape S, int glevel, cons
 }
 cudaError_t run_ext_sweep_mirror(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout) {
   if (D == 2)
-    k_ext_plan<2, true><<<resident_grid(k_ext_plan<2, true>, L.block, L.grid), L.block, 0, L.stream>>>(C, S, glevel, uin,
+    launcher(k_ext_plan<2, true>, with_grid(L, resident_grid(k_ext_plan<2, true>, L.block, L.grid)))(C, S, glevel, uin,
                                                                                                       uout);
   else
-    k_ext_plan<3, true><<<resident_grid(k_ext_plan<3, true>, L.block, L.grid), L.block, 0, L.stream>>>(C, S, glevel, uin,
+    launcher(k_ext_plan<3, true>, with_grid(L, resident_grid(k_ext_plan<3, true>, L.block, L.grid)))(C, S, glevel, uin,
                                                                                                       uout);
   return cudaGetLastError();
 }
@@ -1258,19 +1310,19 @@ cudaError_t run_reinit_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, i
 }
 cudaError_t run_refill(int Q, int st, Launch L, Ctx C, int glevel) {
   if (Q == 9) {
-    if (st == 0) k_refill<9, float><<<L.grid, L.block, 0, L.stream>>>(C, glevel);
-    else k_refill<9, __half><<<L.grid, L.block, 0, L.stream>>>(C, glevel);
+    if (st == 0) launcher(k_refill<9, float>, L, 0)(C, glevel);
+    else launcher(k_refill<9, __half>, L, 0)(C, glevel);
   } else if (Q == 19) {
-    if (st == 0) k_refill<19, float><<<L.grid, L.block, 0, L.stream>>>(C, glevel);
-    else k_refill<19, __half><<<L.grid, L.block, 0, L.stream>>>(C, glevel);
+    if (st == 0) launcher(k_refill<19, float>, L, 0)(C, glevel);
+    else launcher(k_refill<19, __half>, L, 0)(C, glevel);
   } else {
     if (st != 0) return cudaErrorInvalidValue;  // D3Q27: FP32 storage only
-    k_refill<27, float><<<L.grid, L.block, 0, L.stream>>>(C, glevel);
+    launcher(k_refill<27, float>, L, 0)(C, glevel);
   }
   return cudaGetLastError();
 }
 cudaError_t run_sensor(Launch L, Ctx C, BlockShape S, const int *list, int n, int mode, float *out) {
-  k_sensor<<<L.grid, L.block, 0, L.stream>>>(C, S, list, n, mode, out);
+  launcher(k_sensor, L, 0)(C, S, list, n, mode, out);
   return cudaGetLastError();
 }
 

@@ -75,6 +75,7 @@ def load():
     lib.lsb_record.argtypes = [vp, ctypes.c_int]
     lib.lsb_set_driver.argtypes = [vp, ctypes.c_int]
     lib.lsb_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+    lib.lsb_work_counts.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     lib.lsb_autotune.argtypes = [ctypes.c_int, ctypes.POINTER(GridDesc), ctypes.POINTER(Params),
                                  ctypes.POINTER(ctypes.c_void_p), vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                  ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
@@ -96,7 +97,7 @@ def load():
     lib.lsb_kernel_count.restype = ctypes.c_int
     for name in ("lsb_use_graphs", "lsb_get_fields_noalloc", "lsb_profile", "lsb_profile_read", "lsb_create_grid", "lsb_set_params", "lsb_step", "lsb_refine", "lsb_get_fields",
                  "lsb_observables", "lsb_cell_updates", "lsb_backward", "lsb_record", "lsb_autotune", "lsb_set_driver", "lsb_sync",
-                 "lsb_set_wait_limit"):
+                 "lsb_set_wait_limit", "lsb_work_counts"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -328,6 +329,13 @@ class Grid:
         la = (ctypes.c_uint64 * n)()
         self._check(self.lib.lsb_profile_read(self.h, ms, by, la, n))
         return {self.lib.lsb_kernel_name(k).decode(): (ms[k], int(la[k]), by[k]) for k in range(n) if la[k]}
+
+    def work_counts(self, level):
+        """Work-list sizes of global level ``level`` after the last step (lsb_work_counts)."""
+        names = ("leaf", "band", "iface", "links", "flipped", "ghost", "restrict")
+        out = (ctypes.c_longlong * len(names))()
+        self._check(self.lib.lsb_work_counts(self.h, int(level), out, len(names)))
+        return dict(zip(names, (int(v) for v in out)))
 
     def kernel_launches(self):
         return int(self.lib.lsb_kernel_launches(self.h))
