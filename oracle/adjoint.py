@@ -38,6 +38,7 @@ import numpy as np
 
 from .lattice import CS2
 from .lbm import equilibrium, moments, omega_from_nu, strain_rate
+from . import objective as indicator
 from .levelset import fit_geometry
 
 NPARAM = 5  # sigma, rho_0, rho_1, nu_0, nu_1
@@ -57,9 +58,12 @@ class FrozenStep:
     level by oracle/adjoint_amr.py), and ``step_adjoint`` returns their adjoint.
     """
 
-    def __init__(self, sim, phi=None):
-        """``phi`` replaces the Sim's level set (same signs: the masks are the Sim's)."""
+    def __init__(self, sim, phi=None, eps=None):
+        """``phi`` replaces the Sim's level set (same signs: the masks are the Sim's).
+        ``eps``: None for the sharp gas indicator in the observables, else the width of
+        the smoothed indicator H_eps (oracle/objective.py)."""
         assert sim.collision == ("bgk", "bgk"), "the adjoint transposes the BGK collision"
+        self.eps = eps
         self.sim = sim
         self.lat = lat = sim.lat
         self.g = g = sim.geoms[-1]
@@ -189,6 +193,8 @@ class FrozenStep:
 
     def observables(self, f):
         """liquid mass, gas mass, gas volume, leaf count, centroid (D), gas velocity (D)."""
+        if self.eps is not None:
+            return indicator.observables(self.lat, indicator.levels_of(self.sim), [f], self.phi, self.eps)
         rho, u = moments(self.lat, f)
         leaf, gas = self.leaf, self.gas
         vol = float(gas.sum())
@@ -196,8 +202,18 @@ class FrozenStep:
                                self.centers[:, gas].sum(1) / vol, u[:, gas].sum(1) / vol])
 
     # ---------------------------------------------------------------- adjoint
+    def observables_phi_adjoint(self, f, a):
+        """dJ/dphi of J = a . observables(f) at fixed f: zero with the sharp indicator, the
+        H_eps' terms with the smoothed one."""
+        if self.eps is None:
+            return np.zeros(self.g.N)
+        return indicator.observables_adjoint(self.lat, indicator.levels_of(self.sim), [f], self.phi, self.eps, a)[1]
+
     def observables_adjoint(self, f, a):
         """dJ/df for J = a . observables(f)."""
+        if self.eps is not None:
+            return indicator.observables_adjoint(self.lat, indicator.levels_of(self.sim), [f], self.phi,
+                                                 self.eps, a)[0][0]
         lat = self.lat
         rho, u = moments(lat, f)
         D = self.D
@@ -436,5 +452,5 @@ def gradients(step, f0, p, nsteps, a, want_phi=False):
         lam, d = step.step_adjoint(fs[n], p, lam, geo)
         dp += d
     if want_phi:
-        return J, dp, lam, step.geometry_to_phi(geo)
+        return J, dp, lam, step.geometry_to_phi(geo) + step.observables_phi_adjoint(fs[-1], a)
     return J, dp, lam

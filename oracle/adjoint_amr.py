@@ -38,6 +38,7 @@ against central differences of the objective in float64.
 import numpy as np
 
 from . import amr
+from . import objective as indicator
 from .adjoint import NPARAM, FrozenStep, params_of  # noqa: F401  (params_of re-exported)
 from .lattice import CS2
 from .lbm import collide, equilibrium, moments, omega_from_nu
@@ -206,7 +207,10 @@ def _tau(nu, r):
 class AMRFrozenStep:
     """One coarse step of a multi-level Sim with the level set and blocks held fixed."""
 
-    def __init__(self, sim, phi=None):
+    def __init__(self, sim, phi=None, eps=None):
+        """``eps``: None for the sharp gas indicator in the observables, else the width of
+        the smoothed indicator H_eps (oracle/objective.py)."""
+        self.eps = eps
         self.sim = sim
         self.lat = sim.lat
         self.L = L = sim.L
@@ -378,9 +382,12 @@ class AMRFrozenStep:
         return lam, dp
 
     # ---------------------------------------------------------------- observables
-    def observables(self, F):
+    def observables(self, F, phi=None):
         """liquid mass, gas mass, gas volume, leaf updates per coarse step, centroid (D),
         gas velocity (D); sums over the leaves of all levels in finest-cell units."""
+        if self.eps is not None:
+            phi = self.fine.phi if phi is None else phi
+            return indicator.observables(self.lat, indicator.levels_of(self.sim), F, phi, self.eps)
         D = self.D
         mass = np.zeros(2)
         vol, nupd = 0.0, 0.0
@@ -399,7 +406,17 @@ class AMRFrozenStep:
             us += v * u[:, gas].sum(1)
         return np.concatenate([mass, [vol, nupd], xs / vol, us / vol])
 
-    def observables_adjoint(self, F, a):
+    def observables_phi_adjoint(self, F, a, phi=None):
+        """dJ/dphi (finest level) of J = a . observables at fixed populations."""
+        if self.eps is None:
+            return np.zeros(self.geoms[-1].N)
+        phi = self.fine.phi if phi is None else phi
+        return indicator.observables_adjoint(self.lat, indicator.levels_of(self.sim), F, phi, self.eps, a)[1]
+
+    def observables_adjoint(self, F, a, phi=None):
+        if self.eps is not None:
+            phi = self.fine.phi if phi is None else phi
+            return indicator.observables_adjoint(self.lat, indicator.levels_of(self.sim), F, phi, self.eps, a)[0]
         D = self.D
         a = np.asarray(a, dtype=np.float64)
         vol = sum((self.r[l] ** D) * (self.leaf[l] & (self.phase[l] == 1)).sum() for l in range(self.L))
@@ -435,8 +452,8 @@ class AMRMovingStep(AMRFrozenStep):
     frozen one with the finest sub-step's transpose replaced by MovingStep's, which carries
     the adjoints of phi and u~ from sub-step to sub-step."""
 
-    def __init__(self, sim):
-        super().__init__(sim)
+    def __init__(self, sim, eps=None):
+        super().__init__(sim, eps=eps)
         from .adjoint_ls import MovingStep
         self.moving = MovingStep(sim)
 
@@ -475,11 +492,12 @@ class AMRMovingStep(AMRFrozenStep):
         return (lam, self._lls[0], self._lls[1]), dp
 
     def observables(self, S):
-        return AMRFrozenStep.observables(self, S[0])
+        return AMRFrozenStep.observables(self, S[0], S[1])
 
     def observables_adjoint(self, S, a):
         N = self.geoms[-1].N
-        return (AMRFrozenStep.observables_adjoint(self, S[0], a), np.zeros(N), np.zeros((self.D, N)))
+        return (AMRFrozenStep.observables_adjoint(self, S[0], a, S[1]),
+                AMRFrozenStep.observables_phi_adjoint(self, S[0], a, S[1]), np.zeros((self.D, N)))
 
 
 # --------------------------------------------------------------------------- windows
@@ -513,5 +531,5 @@ def gradients(step, F0, p, nsteps, a, want_phi=False):
         lam, d = step.step_adjoint(tr[n], p, lam, geo)
         dp += d
     if want_phi:
-        return J, dp, lam, step.geometry_to_phi(geo)
+        return J, dp, lam, step.geometry_to_phi(geo) + step.observables_phi_adjoint(tr[-1], a)
     return J, dp, lam

@@ -117,9 +117,13 @@ class MovingStep:
     (the whole step on a single-level grid; on a multi-level grid one finest sub-step, whose
     ghost-ring values are an input, see oracle/adjoint_amr.py)."""
 
-    def __init__(self, sim):
+    def __init__(self, sim, eps=None):
+        """``eps``: None for the sharp gas indicator in the observables, else the width of
+        the smoothed indicator H_eps (oracle/objective.py), which makes volume, centroid and
+        velocity depend on phi."""
         c = sim.case
         assert c["ls_active"], "the level set must be live"
+        self.eps = eps
         assert int(c["reinit_every"]) in (0, 1), "reinitialisation every step or never"
         self.sim = sim
         self.g = g = sim.geoms[-1]
@@ -187,7 +191,7 @@ class MovingStep:
         return (f1, F["phi1"], F["ut1"])
 
     def observables(self, state):
-        return FrozenStep.observables(self.frozen_step(state[1]), state[0])
+        return FrozenStep(self.sim, state[1], self.eps).observables(state[0])
 
     # ------------------------------------------------------------------ transposes of the passes
     def _reinit_T(self, lam, F):
@@ -353,7 +357,8 @@ class MovingStep:
 
     def observables_adjoint(self, state, a):
         f, phi, ut = state
-        return (self.frozen_step(phi).observables_adjoint(f, a), np.zeros(self.g.N), np.zeros((self.D, self.g.N)))
+        st = FrozenStep(self.sim, phi, self.eps)
+        return (st.observables_adjoint(f, a), st.observables_phi_adjoint(f, a), np.zeros((self.D, self.g.N)))
 
 
 def trajectory(step, s0, p, nsteps):
