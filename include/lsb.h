@@ -219,6 +219,21 @@ lsb_status lsb_get_fields(lsb_grid *g, int case_idx, int field, int level, void 
 lsb_status lsb_get_fields_noalloc(lsb_grid *g, int case_idx, int field, int level, void *dst,
                                   size_t dst_bytes, int dst_on_host);
 
+/*
+ * Gas indicator of the volume, centroid and velocity observables (Sec. 3.2 gives them
+ * as integrals over the gas region).  eps = 0 (default): the sharp indicator [phi >= 0]
+ * (the leaf's phase).  eps > 0: the smoothed indicator H_eps(phi) = 1/2 (1 + t +
+ * sin(pi t)/pi), t = phi/eps on |phi| <= eps (0 below, 1 above), of phi at the leaf's
+ * first finest child, eps in finest cells (1.5 is the usual width).  The masses stay
+ * phase sums.  With the sharp indicator these observables are piecewise constant in
+ * phi, so their adjoint gradients with respect to sigma, the densities, viscosities or
+ * the initial interface vanish between cell flips; the smoothed one makes them
+ * differentiable: lsb_observables and lsb_backward use it, and dJ/dphi0 then also
+ * carries the indicator's own dependence on phi.  Ends a recording (lsb_record).
+ * Errors: LSB_EINVAL (negative or non-finite eps).
+ */
+lsb_status lsb_set_objective(lsb_grid *g, double eps);
+
 /* Bytes lsb_get_fields writes for (case, field, level); 0 for invalid input. */
 size_t lsb_field_bytes(const lsb_grid *g, int case_idx, int field, int level);
 

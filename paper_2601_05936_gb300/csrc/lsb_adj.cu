@@ -75,8 +75,12 @@ __device__ __forceinline__ void moments_strain(const float *f, float om, float &
 // velocity observable sum(v u) / V_gas.  obs holds the raw sums of
 // k_observables (entry 2 of each case: V_gas).
 template <int Q>
+// eps > 0: the smoothed-indicator objective (k_observables with eps): the velocity
+// weights carry H_eps of phi at the leaf's first finest child, and lphi (finest-level
+// adjoint of phi, or NULL) receives the direct term vol H_eps' (a_V + a_X.(x - X)/V +
+// a_U.(u - U)/V).  obs holds the raw sums (volume, sum x h vol, sum u h vol).
 __global__ void k_adj_seed(Ctx C, BlockShape S, const int *list, int nlist, const float *F, float *lam,
-                           const double *wobs, const double *obs, int stride) {
+                           const double *wobs, const double *obs, int stride, float eps, float *lphi) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
@@ -101,11 +105,30 @@ __global__ void k_adj_seed(Ctx C, BlockShape S, const int *list, int nlist, cons
     lb_moments<Q>(f, drho, u);
     const float base = vol * (float)a[gas];
     float au[3] = {0.f, 0.f, 0.f}, auu = 0.f;
-    if (gas && V > 0.0) {
-      const float s = vol / ((1.0f + drho) * (float)V);
+    float h = gas ? 1.f : 0.f;
+    long long pc = -1;
+    if (eps > 0.f) {
+      pc = corner_phi_index(C, L, x, y, z);
+      h = smooth_h(C.phi[pc], eps);
+    }
+    if (h != 0.f && V > 0.0) {
+      const float s = vol * h / ((1.0f + drho) * (float)V);
       for (int k = 0; k < D; ++k) {
         au[k] = s * (float)a[4 + D + k];
         auu += au[k] * u[k];
+      }
+    }
+    if (eps > 0.f && lphi && V > 0.0) {
+      const float dh = smooth_dh(C.phi[pc], eps);
+      if (dh != 0.f) {
+        const double *o = obs + (long long)L.case_id * stride;
+        const int crd[3] = {x, y, z};
+        double t = a[2];
+        for (int k = 0; k < D; ++k) {
+          const double xk = ((double)crd[k] + 0.5) * L.scale;
+          t += a[4 + k] * (xk - o[4 + k] / V) / V + a[4 + D + k] * ((double)u[k] - o[4 + D + k] / V) / V;
+        }
+        lphi[pc] += (float)((double)(vol * dh) * t);  // one leaf per finest cell: no other writer
       }
     }
 #pragma unroll
@@ -1140,8 +1163,8 @@ __global__ void k_copy_blocks(Ctx C, BlockShape S, const int *list, int n, const
   } while (0)
 
 cudaError_t run_adj_seed(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, const float *F, float *lam,
-                         const double *wobs, const double *obs, int stride) {
-  LSB_ADJ_Q(Q, k_adj_seed, L, C, S, list, n, F, lam, wobs, obs, stride);
+                         const double *wobs, const double *obs, int stride, float eps, float *lphi) {
+  LSB_ADJ_Q(Q, k_adj_seed, L, C, S, list, n, F, lam, wobs, obs, stride, eps, lphi);
 }
 
 cudaError_t run_adj_links(int Q, Launch L, Ctx C, int glevel, const float *F, float *lamN, float *LA, float *MA,

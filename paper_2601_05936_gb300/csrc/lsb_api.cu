@@ -97,6 +97,7 @@ struct lsb_grid {
   unsigned *d_bar = nullptr;  // grid barrier of the persistent level-set kernel
   long long wait_limit = 1LL << 22;  // sleeps of ~64 ns before a device-side wait gives up
   bool ls_dirty = false;  // stage arrays no longer mirror phi / u~ outside the band (driver 1 ran)
+  float obj_eps = 0.f;    // > 0: observables and objective with the smoothed gas indicator H_eps
   int driver = 0;             // 0: one launch per level-set pass, 1: one persistent launch
   int2 *d_iface = nullptr, *d_flip = nullptr;
   double *d_obs = nullptr;
@@ -108,6 +109,7 @@ struct lsb_grid {
   WorkList cs[MAXL], rst[MAXL], ghost[MAXL], finest[MAXL], leaf, tags, sens, all_active;
   std::vector<int> tags_prev;
   CellList ghost_cells[MAXL], rl_cells[MAXL];
+  CellList ghost_par[MAXL];  // ghost cells grouped by coarse parent: {first cell, cells}
   int *d_count = nullptr;
   int par[MAXL] = {0, 0, 0, 0};
   long long fine_steps[MAXL] = {0, 0, 0, 0};
@@ -639,7 +641,9 @@ lsb_status advance(lsb_grid *g, int l) {
       C = make_ctx(g);
       const float theta = sub == 0 ? 0.0f : 0.5f;
       const CellList &gc = g->ghost_cells[l + 1];
-      RUN(3, 0, gc.n, 128, run_ghost_cells, Q, st, LN(g, (gc.n + 127) / 128, 128), C, (const int2 *)gc.d, gc.n, theta);
+      const CellList &gp = g->ghost_par[l + 1];
+      RUN(3, 0, gp.n, 128, run_ghost_parents, Q, st, LN(g, (gp.n + 127) / 128, 128), C, (const int2 *)gc.d,
+          (const int2 *)gp.d, gp.n, theta);
       TRY(advance(g, l + 1));
     }
   }
@@ -1588,6 +1592,13 @@ lsb_status lsb_use_graphs(lsb_grid *g, int enable) {
   return LSB_OK;
 }
 
+lsb_status lsb_set_objective(lsb_grid *g, double eps) {
+  if (!g || !(eps >= 0.0) || !std::isfinite(eps)) return LSB_EINVAL;
+  if (g->rec_on) rec_clear(g);  // a recording covers one objective
+  g->obj_eps = (float)eps;
+  return LSB_OK;
+}
+
 lsb_status lsb_set_wait_limit(lsb_grid *g, long long spins) {
   if (!g || spins < 0) return LSB_EINVAL;
   if (spins != g->wait_limit) drop_graphs(g);  // the limit is a captured kernel argument
@@ -1740,7 +1751,7 @@ lsb_status lsb_observables(lsb_grid *g, double *out_host, size_t n_doubles) {
   BlockShape S = shape(g);
   const int og = std::min(g->leaf.n, 152 * 4);
   RUN(6, 0, g->leaf.n, g->nthreads, run_observables, g->Q, g->storage, LN(g, og, g->nthreads), C, S,
-      (const int *)g->leaf.d, g->leaf.n, g->d_obs, stride);
+      (const int *)g->leaf.d, g->leaf.n, g->d_obs, stride, g->obj_eps);
   std::vector<double> h((size_t)stride * g->ncase);
   CU(cudaMemcpyAsync(h.data(), g->d_obs, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g->stream));
   lsb_status s = lsb_sync(g);
@@ -1951,9 +1962,13 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
   CU(cudaMemsetAsync(g->d_obs, 0, sizeof(double) * stride * g->ncase, g->stream));
   const int og = std::min(g->leaf.n, 152 * 4);
   RUN(6, 0, g->leaf.n, g->nthreads, run_observables, Q, g->storage, LN(g, og, g->nthreads), C, S,
-      (const int *)g->leaf.d, g->leaf.n, g->d_obs, stride);
+      (const int *)g->leaf.d, g->leaf.n, g->d_obs, stride, g->obj_eps);
+  // the objective's direct dependence on phi (smoothed indicator): into the level set's
+  // adjoint at the end of the window (moving), or into dJ/dphi (frozen)
+  float *lphi = g->obj_eps > 0.f ? (mv ? lsa_ptrs(g).LP[0] : (dJ_dphi0 ? g->d_gphi : nullptr)) : nullptr;
   RUN(KADJ_SEED, 0, g->leaf.n, g->nthreads, run_adj_seed, Q, LN(g, std::min(g->leaf.n, 152 * 8), g->nthreads), C,
-      S, (const int *)g->leaf.d, g->leaf.n, (const float *)g->d_fsave, g->d_adj[0], g->d_wobs, g->d_obs, stride);
+      S, (const int *)g->leaf.d, g->leaf.n, (const float *)g->d_fsave, g->d_adj[0], g->d_wobs, g->d_obs, stride,
+      g->obj_eps, lphi);
   int cur = 0;
   lsb_status st = LSB_OK;
   const long long nseg = amr ? 0 : (T + every - 1) / every;
@@ -2162,6 +2177,7 @@ lsb_status collect_cells(lsb_grid *g) {
       CellList &cl = kind == 0 ? g->ghost_cells[l] : g->rl_cells[l];
       const int bits = kind == 0 ? TAG_GHOST : TAG_RLAYER;
       cl.n = 0;
+      if (kind == 0) g->ghost_par[l].n = 0;
       if (bl.n == 0) continue;
       const int need = bl.n * g->nthreads;
       if (need > cl.cap) {
@@ -2176,6 +2192,16 @@ lsb_status collect_cells(lsb_grid *g) {
       CU(cudaMemcpyAsync(&n, g->d_count, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
       CU(cudaStreamSynchronize(g->stream));
       cl.n = std::min(n, cl.cap);
+      if (kind == 0 && cl.n == 1) {
+        const int2 one = make_int2(0, 1);
+        CellList &pl = g->ghost_par[l];
+        if (pl.cap < 1) {
+          TRY(dalloc(g, &pl.d, sizeof(int2)));
+          pl.cap = 1;
+        }
+        pl.n = 1;
+        CU(cudaMemcpy(pl.d, &one, sizeof(int2), cudaMemcpyHostToDevice));
+      }
       // the atomics append in arbitrary order: sort so that neighbouring threads work on
       // neighbouring cells.  Restriction cells: by (level, cell).  Ghost cells: by (level,
       // coarse parent, position in the parent), so that the up to 2^D fine cells
@@ -2192,6 +2218,18 @@ lsb_status collect_cells(lsb_grid *g) {
             return ((unsigned long long)a.x << 56) | (par << 3) | ((z & 1) << 2) | ((y & 1) << 1) | (x & 1);
           };
           std::sort(h.begin(), h.end(), [&](const int2 &a, const int2 &b) { return key(a) < key(b); });
+          // runs of cells with the same (level, parent): one entry per coarse parent
+          std::vector<int2> par;
+          for (int e = 0; e < cl.n; ++e)
+            if (e == 0 || (key(h[e]) >> 3) != (key(h[e - 1]) >> 3)) par.push_back(make_int2(e, 1));
+            else par.back().y++;
+          CellList &pl = g->ghost_par[l];
+          if ((int)par.size() > pl.cap) {
+            TRY(dalloc(g, &pl.d, sizeof(int2) * par.size()));
+            pl.cap = (int)par.size();
+          }
+          pl.n = (int)par.size();
+          CU(cudaMemcpy(pl.d, par.data(), sizeof(int2) * par.size(), cudaMemcpyHostToDevice));
         } else {
           std::sort(h.begin(), h.end(),
                     [](const int2 &a, const int2 &b) { return a.x != b.x ? a.x < b.x : a.y < b.y; });

@@ -301,6 +301,35 @@ __device__ __forceinline__ const LevelDev &band_cell(const Ctx &C, const BlockSh
   return C.lds[bi.x];
 }
 
+// The same from a band-list entry already loaded (prefetched one iteration ahead).
+__device__ __forceinline__ const LevelDev &band_cell_at(const Ctx &C, const BlockShape &S, int4 bi, int t, int &x,
+                                                        int &y, int &z) {
+  x = (bi.y << S.lg[0]) + (t & (S.bs[0] - 1));
+  y = (bi.z << S.lg[1]) + ((t >> S.lg[0]) & (S.bs[1] - 1));
+  z = (bi.w << S.lg[2]) + (t >> (S.lg[0] + S.lg[1]));
+  return C.lds[bi.x];
+}
+
+// Smoothed gas indicator of the adjoint objective (Sec. 3.2's integrals weighted so
+// that they depend smoothly on phi): H(phi) = 1/2 (1 + t + sin(pi t)/pi), t = phi/eps on
+// |phi| <= eps, 0 below, 1 above; and its derivative.
+__device__ __forceinline__ float smooth_h(float phi, float eps) {
+  if (phi >= eps) return 1.0f;
+  if (phi <= -eps) return 0.0f;
+  const float t = phi / eps;
+  return 0.5f * (1.0f + t + sinpif(t) * 0.318309886183790672f);
+}
+__device__ __forceinline__ float smooth_dh(float phi, float eps) {
+  if (phi >= eps || phi <= -eps) return 0.0f;
+  return 0.5f / eps * (1.0f + cospif(phi / eps));
+}
+// phi of the finest cell a leaf of level L reads its indicator at (its first finest child).
+__device__ __forceinline__ long long corner_phi_index(const Ctx &C, const LevelDev &L, int x, int y, int z) {
+  const LevelDev &F = C.lds[L.fine_ld];
+  const int s = L.scale;
+  return F.fine_off + cidx(F, x * s, y * s, z * s);
+}
+
 // (x, y, z) of level-local cell index c, in 32-bit arithmetic: every level holds fewer
 // than 2^32 / (Q + 1) cells (checked when the grid is created).
 __device__ __forceinline__ void cell_xyz(const LevelDev &L, long long c, int &x, int &y, int &z) {

@@ -71,8 +71,11 @@ cudaError_t run_collect(Launch L, Ctx C, BlockShape S, const int *list, int n, i
                         int cap);
 cudaError_t run_restrict_cells(int Q, int st, Launch L, Ctx C, const int2 *cells, int n);
 cudaError_t run_ghost_cells(int Q, int st, Launch L, Ctx C, const int2 *cells, int n, float theta);
+// the ghost ring with one thread per coarse parent (parents: {first child in cells, children})
+cudaError_t run_ghost_parents(int Q, int st, Launch L, Ctx C, const int2 *cells, const int2 *parents, int n,
+                              float theta);
 cudaError_t run_observables(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, double *out,
-                            int stride);
+                            int stride, float eps);
 cudaError_t run_export(int Q, int st, Launch L, Ctx C, int ld, int field, float *dst);
 // Export into the file-scope staging array; *staged receives its device address.
 cudaError_t run_export_noalloc(int Q, int st, Launch L, Ctx C, int ld, int field, float **staged);
@@ -106,7 +109,7 @@ struct GeoAdj {
   float *phi, *n, *kappa;
 };
 cudaError_t run_adj_seed(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, const float *F, float *lam,
-                         const double *wobs, const double *obs, int stride);
+                         const double *wobs, const double *obs, int stride, float eps, float *lphi);
 cudaError_t run_adj_links(int Q, Launch L, Ctx C, int glevel, const float *F, float *lamN, float *LA, float *MA,
                           double *grad, int ncase, GeoAdj G);
 cudaError_t run_adj_geometry(int D, Launch L, Ctx C, int glevel, GeoAdj G);

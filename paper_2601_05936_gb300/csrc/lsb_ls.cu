@@ -336,18 +336,43 @@ __device__ __forceinline__ void d_ext_init(const Ctx &C, int glevel) {
     const long long fo = L.fine_off, NF = C.nfine;
     const uint32_t m = C.cmask[fo + c];
     const float phx = C.phi[fo + c];
+    float ux[3];
+    for (int a = 0; a < D; ++a) ux[a] = C.macro[(1 + a) * NF + fo + c];
+    // the cut links' partners, loaded in groups of four with every load of a group in
+    // flight together (a dependent chain per link otherwise), summed in link order
     float acc[3] = {0.f, 0.f, 0.f};
     int cnt = 0;
-    for (int k = 0; k < Q; ++k) {
-      if (!(m & (1u << k))) continue;
-      const int i = LT::opp(k);
-      int yx = x + LT::cx(i), yy = y + LT::cy(i), yz = z + LT::cz(i);
-      wrap(L, 0, yx); wrap(L, 1, yy); if (D == 3) wrap(L, 2, yz);
-      const long long cy_ = cidx(L, yx, yy, yz);
-      const float q = phx / (phx - C.phi[fo + cy_]);
-      for (int a = 0; a < D; ++a)
-        acc[a] += (1.0f - q) * C.macro[(1 + a) * NF + fo + c] + q * C.macro[(1 + a) * NF + fo + cy_];
-      ++cnt;
+    uint32_t mm = m;
+    while (mm) {
+      constexpr int G = 4;
+      long long cy[G];
+      bool on[G];
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        on[j] = mm != 0;
+        cy[j] = fo + c;
+        if (!on[j]) continue;
+        const int k = __ffs(mm) - 1;
+        mm &= mm - 1u;
+        const int i = LT::opp(k);
+        int yx = x + LT::cx(i), yy = y + LT::cy(i), yz = z + LT::cz(i);
+        wrap(L, 0, yx); wrap(L, 1, yy); if (D == 3) wrap(L, 2, yz);
+        cy[j] = fo + cidx(L, yx, yy, yz);
+      }
+      float py[G], uy[G][3];
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        py[j] = C.phi[cy[j]];
+#pragma unroll
+        for (int a = 0; a < D; ++a) uy[j][a] = C.macro[(1 + a) * NF + cy[j]];
+      }
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        if (!on[j]) continue;
+        const float q = phx / (phx - py[j]);
+        for (int a = 0; a < D; ++a) acc[a] += (1.0f - q) * ux[a] + q * uy[j][a];
+        ++cnt;
+      }
     }
     for (int a = 0; a < D; ++a) C.ut0[a * NF + fo + c] = acc[a] / (float)cnt;
   }
@@ -813,9 +838,14 @@ __global__ void k_ext_first(Ctx C, BlockShape S, int glevel, const float *__rest
   LSB_GRID_WAIT();
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
   const long long NF = C.nfine;
+  // the next entry of the band list is loaded while this one is processed
+  const int4 *info = C.band_info + (long long)glevel * C.band_cap;
+  int4 next = blockIdx.x < nl ? __ldg(info + blockIdx.x) : make_int4(0, 0, 0, 0);
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
+    const int4 bi = next;
+    if (w + gridDim.x < nl) next = __ldg(info + w + gridDim.x);
     int x, y, z;
-    const LevelDev &L = band_cell(C, S, glevel, w, threadIdx.x, x, y, z);
+    const LevelDev &L = band_cell_at(C, S, bi, threadIdx.x, x, y, z);
     if (!L.ls_active) continue;
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const long long fo = L.fine_off;
@@ -880,9 +910,14 @@ __global__ void k_adv_mirror(Ctx C, BlockShape S, int glevel, int stage, const f
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
   const float *pin = stage == 1 ? C.phi : (stage == 2 ? C.p1 : C.p2);
   const long long NF = C.nfine;
+  // the next entry of the band list is loaded while this one is processed
+  const int4 *info = C.band_info + (long long)glevel * C.band_cap;
+  int4 next = blockIdx.x < nl ? __ldg(info + blockIdx.x) : make_int4(0, 0, 0, 0);
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
+    const int4 bi = next;
+    if (w + gridDim.x < nl) next = __ldg(info + w + gridDim.x);
     int x, y, z;
-    const LevelDev &L = band_cell(C, S, glevel, w, threadIdx.x, x, y, z);
+    const LevelDev &L = band_cell_at(C, S, bi, threadIdx.x, x, y, z);
     if (!L.ls_active) continue;
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const unsigned c = (unsigned)cidx(L, x, y, z);
@@ -923,9 +958,14 @@ __global__ void k_reinit_mirror(Ctx C, BlockShape S, int glevel, int stage, int 
   constexpr int D = LT::D;
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
   const float *pin = stage == 1 ? C.phi : (stage == 2 ? C.p1 : C.p2);
+  // the next entry of the band list is loaded while this one is processed
+  const int4 *info = C.band_info + (long long)glevel * C.band_cap;
+  int4 next = blockIdx.x < nl ? __ldg(info + blockIdx.x) : make_int4(0, 0, 0, 0);
   for (int w = blockIdx.x; w < nl; w += gridDim.x) {
+    const int4 bi = next;
+    if (w + gridDim.x < nl) next = __ldg(info + w + gridDim.x);
     int x, y, z;
-    const LevelDev &L = band_cell(C, S, glevel, w, threadIdx.x, x, y, z);
+    const LevelDev &L = band_cell_at(C, S, bi, threadIdx.x, x, y, z);
     if (!L.ls_active) continue;
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
     const unsigned cl = (unsigned)cidx(L, x, y, z);

@@ -75,6 +75,7 @@ def load():
     lib.lsb_record.argtypes = [vp, ctypes.c_int]
     lib.lsb_set_driver.argtypes = [vp, ctypes.c_int]
     lib.lsb_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+    lib.lsb_set_objective.argtypes = [vp, ctypes.c_double]
     lib.lsb_work_counts.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     lib.lsb_autotune.argtypes = [ctypes.c_int, ctypes.POINTER(GridDesc), ctypes.POINTER(Params),
                                  ctypes.POINTER(ctypes.c_void_p), vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -97,7 +98,7 @@ def load():
     lib.lsb_kernel_count.restype = ctypes.c_int
     for name in ("lsb_use_graphs", "lsb_get_fields_noalloc", "lsb_profile", "lsb_profile_read", "lsb_create_grid", "lsb_set_params", "lsb_step", "lsb_refine", "lsb_get_fields",
                  "lsb_observables", "lsb_cell_updates", "lsb_backward", "lsb_record", "lsb_autotune", "lsb_set_driver", "lsb_sync",
-                 "lsb_set_wait_limit", "lsb_work_counts"):
+                 "lsb_set_wait_limit", "lsb_work_counts", "lsb_set_objective"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -255,6 +256,10 @@ class Grid:
     def set_driver(self, mode):
         """0: one launch per level-set pass; 1: one persistent cooperative launch per finest step."""
         self._check(self.lib.lsb_set_driver(self.h, int(mode)))
+
+    def set_objective(self, eps=1.5):
+        """Gas indicator of volume, centroid and velocity: 0 sharp, > 0 smoothed H_eps (width eps)."""
+        self._check(self.lib.lsb_set_objective(self.h, float(eps)))
 
     def set_wait_limit(self, spins):
         """Iteration limit of the bounded device-side waits (~64 ns each; 0 gives up at once)."""
