@@ -92,7 +92,7 @@ struct lsb_grid {
   int2 *d_linkcell = nullptr;
   uint8_t *d_linkdir = nullptr;
   long long link_list_off[MAXL] = {0, 0, 0, 0};
-  int *d_counters = nullptr, *d_err = nullptr, *d_band = nullptr;
+  int *d_counters = nullptr, *d_err = nullptr, *d_band = nullptr, *d_check = nullptr;
   int4 *d_band_info = nullptr;
   unsigned *d_bar = nullptr;  // grid barrier of the persistent level-set kernel
   long long wait_limit = 1LL << 22;  // sleeps of ~64 ns before a device-side wait gives up
@@ -109,7 +109,6 @@ struct lsb_grid {
   WorkList cs[MAXL], rst[MAXL], ghost[MAXL], finest[MAXL], leaf, tags, sens, all_active;
   std::vector<int> tags_prev;
   CellList ghost_cells[MAXL], rl_cells[MAXL];
-  CellList ghost_par[MAXL];  // ghost cells grouped by coarse parent: {first cell, cells}
   int *d_count = nullptr;
   int par[MAXL] = {0, 0, 0, 0};
   long long fine_steps[MAXL] = {0, 0, 0, 0};
@@ -250,6 +249,7 @@ Ctx make_ctx(lsb_grid *g) {
   C.iface_list = g->d_iface;
   C.flip_list = g->d_flip;
   C.band_list = g->d_band;
+  C.check_list = g->d_check;
   C.band_info = g->d_band_info;
   C.list_cap = g->list_cap;
   C.band_cap = g->band_cap;
@@ -484,15 +484,22 @@ bool has_finest(const lsb_grid *g, int l) {
 // Classification of the finest level l: phases, flips, cut links, band; then geometry.
 lsb_status classify(lsb_grid *g, int l, int init) {
   if (!has_finest(g, l)) return LSB_OK;
-  CU(cudaMemsetAsync(g->d_counters + l * NCOUNT, 0, sizeof(int) * NCOUNT, g->stream));
+  // the band list the previous classification left is the set of blocks whose phases can
+  // change (phi moves on band cells only): keep its length, then clear the counters
+  int *cnt = g->d_counters + l * NCOUNT;
+  CU(cudaMemcpyAsync(cnt + 5, cnt + 3, sizeof(int), cudaMemcpyDeviceToDevice, g->stream));
+  CU(cudaMemsetAsync(cnt, 0, sizeof(int) * 5, g->stream));
   Ctx C = make_ctx(g);
   BlockShape S = shape(g);
   WorkList &F = g->finest[l];
   const int *fl = F.d;
   const int Q = g->Q, D = g->D, nt = g->nthreads;
-  RUN(8, 0, F.n, nt, run_classify_phase, Q, LN(g, F.n, nt), C, S, fl, F.n, l, init);
+  // after creation or a regrid every finest block; otherwise the previous band's blocks
+  // (and, for the cut links, the blocks next to a flipped cell), walked from the lists
+  const int nlist = init ? F.n : std::max(1, std::min(F.n, 152 * 8));
+  RUN(8, 0, F.n, nt, run_classify_phase, Q, LN(g, nlist, nt), C, S, fl, F.n, l, init);
   if (!init) RUN(9, 0, 1, 128, run_flip_mark, Q, LN(g, DYN_GRID / 4, 128), C, S, l);
-  RUN(9, 0, F.n, nt, run_classify_links, Q, LN(g, F.n, nt), C, S, fl, F.n, l, init);
+  RUN(9, 0, F.n, nt, run_classify_links, Q, LN(g, nlist, nt), C, S, fl, F.n, l, init);
   RUN(10, 0, F.n, 128, run_band, Q, LN(g, (F.n + 127) / 128, 128), C, S, fl, F.n, l);
   RUN(11, 0, 1, 128, run_geometry, D, LN(g, DYN_GRID, 128), C, l, 0);
   RUN(11, 0, 1, 128, run_geometry, D, LN(g, DYN_GRID, 128), C, l, 1);
@@ -641,9 +648,7 @@ lsb_status advance(lsb_grid *g, int l) {
       C = make_ctx(g);
       const float theta = sub == 0 ? 0.0f : 0.5f;
       const CellList &gc = g->ghost_cells[l + 1];
-      const CellList &gp = g->ghost_par[l + 1];
-      RUN(3, 0, gp.n, 128, run_ghost_parents, Q, st, LN(g, (gp.n + 127) / 128, 128), C, (const int2 *)gc.d,
-          (const int2 *)gp.d, gp.n, theta);
+      RUN(3, 0, gc.n, 128, run_ghost_cells, Q, st, LN(g, (gc.n + 127) / 128, 128), C, (const int2 *)gc.d, gc.n, theta);
       TRY(advance(g, l + 1));
     }
   }
@@ -1455,6 +1460,7 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
   ALLOC(g->d_iface, sizeof(int2) * MAXL * g->list_cap);
   ALLOC(g->d_flip, sizeof(int2) * MAXL * g->list_cap);
   ALLOC(g->d_band, sizeof(int) * MAXL * (size_t)std::max(1, g->band_cap));
+  ALLOC(g->d_check, sizeof(int) * MAXL * (size_t)std::max(1, g->band_cap));
   ALLOC(g->d_band_info, sizeof(int4) * MAXL * (size_t)std::max(1, g->band_cap));
   ALLOC(g->d_obs, sizeof(double) * n_cases * 16);
   ALLOC(g->d_sens, sizeof(float) * g->nblock_total);
@@ -2177,7 +2183,6 @@ lsb_status collect_cells(lsb_grid *g) {
       CellList &cl = kind == 0 ? g->ghost_cells[l] : g->rl_cells[l];
       const int bits = kind == 0 ? TAG_GHOST : TAG_RLAYER;
       cl.n = 0;
-      if (kind == 0) g->ghost_par[l].n = 0;
       if (bl.n == 0) continue;
       const int need = bl.n * g->nthreads;
       if (need > cl.cap) {
@@ -2192,16 +2197,6 @@ lsb_status collect_cells(lsb_grid *g) {
       CU(cudaMemcpyAsync(&n, g->d_count, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
       CU(cudaStreamSynchronize(g->stream));
       cl.n = std::min(n, cl.cap);
-      if (kind == 0 && cl.n == 1) {
-        const int2 one = make_int2(0, 1);
-        CellList &pl = g->ghost_par[l];
-        if (pl.cap < 1) {
-          TRY(dalloc(g, &pl.d, sizeof(int2)));
-          pl.cap = 1;
-        }
-        pl.n = 1;
-        CU(cudaMemcpy(pl.d, &one, sizeof(int2), cudaMemcpyHostToDevice));
-      }
       // the atomics append in arbitrary order: sort so that neighbouring threads work on
       // neighbouring cells.  Restriction cells: by (level, cell).  Ghost cells: by (level,
       // coarse parent, position in the parent), so that the up to 2^D fine cells
@@ -2218,18 +2213,6 @@ lsb_status collect_cells(lsb_grid *g) {
             return ((unsigned long long)a.x << 56) | (par << 3) | ((z & 1) << 2) | ((y & 1) << 1) | (x & 1);
           };
           std::sort(h.begin(), h.end(), [&](const int2 &a, const int2 &b) { return key(a) < key(b); });
-          // runs of cells with the same (level, parent): one entry per coarse parent
-          std::vector<int2> par;
-          for (int e = 0; e < cl.n; ++e)
-            if (e == 0 || (key(h[e]) >> 3) != (key(h[e - 1]) >> 3)) par.push_back(make_int2(e, 1));
-            else par.back().y++;
-          CellList &pl = g->ghost_par[l];
-          if ((int)par.size() > pl.cap) {
-            TRY(dalloc(g, &pl.d, sizeof(int2) * par.size()));
-            pl.cap = (int)par.size();
-          }
-          pl.n = (int)par.size();
-          CU(cudaMemcpy(pl.d, par.data(), sizeof(int2) * par.size(), cudaMemcpyHostToDevice));
         } else {
           std::sort(h.begin(), h.end(),
                     [](const int2 &a, const int2 &b) { return a.x != b.x ? a.x < b.x : a.y < b.y; });

@@ -204,6 +204,7 @@ struct Ctx {
   int *counters;           // per global level: [0] links, [1] iface cells, [2] flipped, [3] band blocks
   int2 *iface_list, *flip_list;   // (ld, cell)
   int *band_list;          // global block ids
+  int *check_list;         // blocks next to a flipped cell outside the previous band
   int4 *band_info;         // beside each band-list entry: its block coordinates (as blk_info)
   long long list_cap;      // capacity of iface/flip lists per global level
   int band_cap;
@@ -212,7 +213,10 @@ struct Ctx {
 };
 
 enum : int { ERR_LINK_OVF = 1, ERR_LIST_OVF = 2, ERR_NONFINITE = 4, ERR_BAND_OVF = 8, ERR_TIMEOUT = 16 };
-constexpr int NCOUNT = 4;
+// device counters per global level: [0] cut links, [1] interface cells, [2] flipped cells,
+// [3] band blocks, [4] blocks next to a flipped cell outside the previous band (check
+// list), [5] band blocks of the previous classification (the band list it left)
+constexpr int NCOUNT = 6;
 
 // ---------------------------------------------------------------- storage
 template <typename T> struct Store;

@@ -71,9 +71,6 @@ cudaError_t run_collect(Launch L, Ctx C, BlockShape S, const int *list, int n, i
                         int cap);
 cudaError_t run_restrict_cells(int Q, int st, Launch L, Ctx C, const int2 *cells, int n);
 cudaError_t run_ghost_cells(int Q, int st, Launch L, Ctx C, const int2 *cells, int n, float theta);
-// the ghost ring with one thread per coarse parent (parents: {first child in cells, children})
-cudaError_t run_ghost_parents(int Q, int st, Launch L, Ctx C, const int2 *cells, const int2 *parents, int n,
-                              float theta);
 cudaError_t run_observables(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, double *out,
                             int stride, float eps);
 cudaError_t run_export(int Q, int st, Launch L, Ctx C, int ld, int field, float *dst);

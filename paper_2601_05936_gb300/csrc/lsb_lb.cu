@@ -19,6 +19,25 @@
 #include "lsb_kernels.h"
 #include "lsb_tma.cuh"
 
+// CTAs of 128 threads per SM the ghost-ring and cut-link kernels are compiled for
+// (registers capped to fit; 0 leaves the compiler's choice)
+#ifndef LSB_GHOST_MINB
+#define LSB_GHOST_MINB 0
+#endif
+#ifndef LSB_LINK_MINB
+#define LSB_LINK_MINB 0
+#endif
+#if LSB_GHOST_MINB > 0
+#define LSB_GHOST_LB __launch_bounds__(128, LSB_GHOST_MINB)
+#else
+#define LSB_GHOST_LB
+#endif
+#if LSB_LINK_MINB > 0
+#define LSB_LINK_LB __launch_bounds__(128, LSB_LINK_MINB)
+#else
+#define LSB_LINK_LB
+#endif
+
 namespace lsb {
 
 // BGK collision with forcing (Eq. 1), in place on deviations f~ = f - w, written per pair
@@ -543,7 +562,7 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
 // i = opp(k) points from x (phase A) to x + c_i (phase B).  One thread per link
 // (the link list of the classification, in link-buffer order).
 template <int Q, typename T>
-__global__ void k_interface_bc(Ctx C, int glevel) {
+__global__ void LSB_LINK_LB k_interface_bc(Ctx C, int glevel) {
   LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
@@ -1005,7 +1024,7 @@ __global__ void k_restrict_cells(Ctx C, const int2 *cells, int n) {
 // interpolation at time weight theta, f^neq scaled by tau_f / (2 tau_c), a
 // fine-level collision, pushed into the fine leaves that stream from it.
 template <int Q, typename T>
-__global__ void k_ghost_cells(Ctx C, const int2 *cells, int n, float theta) {
+__global__ void LSB_GHOST_LB k_ghost_cells(Ctx C, const int2 *cells, int n, float theta) {
   LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
@@ -1046,109 +1065,6 @@ __global__ void k_ghost_cells(Ctx C, const int2 *cells, int n, float theta) {
       const long long ct = cidx(F, t[0], t[1], t[2]);
       if (C.tag[F.cell_off + ct] & TAG_LEAF)
         Store<T>::st(Bf + mirror_dir<Q>(i, mm) * F.ncell + ct, f[i], C.fp16_scale);
-    }
-  }
-}
-
-// The ghost ring grouped by coarse parent: one thread per parent, whose interpolation
-// sources (the parent and its 2D axis neighbours, blended in time) are loaded once and
-// serve every ghost child of that parent (a face of the ring holds 2^(D-1) children per
-// parent).  parents[e] = {first child in cells, number of children}; the children's
-// arithmetic is that of k_ghost_cells, in the same order.
-template <int Q, typename T>
-__global__ void k_ghost_parents(Ctx C, const int2 *cells, const int2 *parents, int n, float theta) {
-  LSB_GRID_WAIT();
-  using LT = Lat<Q>;
-  constexpr int D = LT::D;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    const int2 pr = parents[e];
-    const int2 it0 = cells[pr.x];
-    const LevelDev &F = C.lds[it0.x];
-    const LevelDev &Lc = C.lds[F.parent_ld];
-    int x0, y0, z0;
-    cell_xyz(F, it0.y, x0, y0, z0);
-    const int P[3] = {x0 >> 1, y0 >> 1, D == 3 ? (z0 >> 1) : 0};
-    const T *Ac = fA<T, Q>(C, Lc);
-    const T *Bc = fB<T, Q>(C, Lc);
-    auto load = [&](long long cc, float *dst) {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        float a = Store<T>::ld(Ac + i * Lc.ncell + cc, C.fp16_inv);
-        if (theta != 0.f) a = (1.0f - theta) * a + theta * Store<T>::ld(Bc + i * Lc.ncell + cc, C.fp16_inv);
-        dst[i] = a;
-      }
-    };
-    const long long cp = cidx(Lc, P[0], P[1], P[2]);
-    float fp[Q], gr[D][Q];
-    load(cp, fp);
-    bool any[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      int up[3] = {P[0], P[1], P[2]}, dn[3] = {P[0], P[1], P[2]};
-      up[a] += 1;
-      dn[a] -= 1;
-      bool upok = wrap(Lc, a, up[a]);
-      bool dnok = wrap(Lc, a, dn[a]);
-      long long cu = 0, cd = 0;
-      if (upok) {
-        cu = cidx(Lc, up[0], up[1], up[2]);
-        upok = (C.tag[Lc.cell_off + cu] & TAG_LEAF) != 0;
-      }
-      if (dnok) {
-        cd = cidx(Lc, dn[0], dn[1], dn[2]);
-        dnok = (C.tag[Lc.cell_off + cd] & TAG_LEAF) != 0;
-      }
-      any[a] = upok || dnok;
-      float fu[Q], fd[Q];
-      if (upok) load(cu, fu);
-      if (dnok) load(cd, fd);
-#pragma unroll
-      for (int i = 0; i < Q; ++i)
-        gr[a][i] = !any[a] ? 0.f : ((upok && dnok) ? 0.5f * (fu[i] - fd[i]) : (upok ? fu[i] - fp[i] : fp[i] - fd[i]));
-    }
-    const int ph = C.tag[Lc.cell_off + cp] & TAG_GAS;
-    const float fac = F.tau[ph] / (2.0f * Lc.tau[ph]);
-    const float acc[3] = {F.acc[ph][0], F.acc[ph][1], F.acc[ph][2]};
-    T *Bf = fB<T, Q>(C, F);
-    for (int j = 0; j < pr.y; ++j) {
-      const int2 it = cells[pr.x + j];
-      int x, y, z;
-      cell_xyz(F, it.y, x, y, z);
-      float f[Q];
-#pragma unroll
-      for (int i = 0; i < Q; ++i) f[i] = fp[i];
-      const int fcrd[3] = {x, y, z};
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        if (!any[a]) continue;
-        const float delta = ((fcrd[a] & 1) - 0.5f) * 0.5f;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) f[i] += delta * gr[a][i];
-      }
-      rescale_neq<Q>(f, fac);
-      float drho, u[3];
-      collide_phase<Q>(f, F.omega[ph], acc, drho, u, F.cumulant[ph]);
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        if (i == LT::REST) continue;
-        int t[3] = {x + LT::cx(i), y + LT::cy(i), z + LT::cz(i)};
-        const int o[3] = {x, y, z};
-        int mm = 0;
-        bool ok = true;
-        for (int a = 0; a < D; ++a)
-          if (!wrap(F, a, t[a])) {
-            if (F.slip[a]) {
-              t[a] = o[a];
-              mm |= 1 << a;
-            } else {
-              ok = false;
-            }
-          }
-        if (!ok) continue;
-        const long long ct = cidx(F, t[0], t[1], t[2]);
-        if (C.tag[F.cell_off + ct] & TAG_LEAF)
-          Store<T>::st(Bf + mirror_dir<Q>(i, mm) * F.ncell + ct, f[i], C.fp16_scale);
-      }
     }
   }
 }
@@ -1360,10 +1276,6 @@ cudaError_t run_restrict_cells(int Q, int st, Launch L, Ctx C, const int2 *cells
 }
 cudaError_t run_ghost_cells(int Q, int st, Launch L, Ctx C, const int2 *cells, int n, float theta) {
   LSB_QT(Q, st, (LK(k_ghost_cells)(C, cells, n, theta)));
-}
-cudaError_t run_ghost_parents(int Q, int st, Launch L, Ctx C, const int2 *cells, const int2 *parents, int n,
-                              float theta) {
-  LSB_QT(Q, st, (LK(k_ghost_parents)(C, cells, parents, n, theta)));
 }
 cudaError_t run_level_tags(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n) {
   if (Q == 9) launcher(k_level_tags<9>, L, 0)(C, S, list, n);

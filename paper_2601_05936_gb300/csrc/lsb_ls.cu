@@ -30,13 +30,15 @@ __device__ __forceinline__ bool in_band(const Ctx &C, const LevelDev &L, const B
 template <int Q>
 __global__ void k_classify_phase(Ctx C, BlockShape S, const int *list, int nlist, int glevel, int init) {
   LSB_GRID_WAIT();
+  // phi changes only on band cells, so outside the previous band no phase (and no stale
+  // flip bit: flips happen next to the interface, inside the band) can change: unless
+  // init, the blocks are those of the previous band list
+  if (!init) {
+    nlist = min(C.counters[glevel * NCOUNT + 5], C.band_cap);
+    list = C.band_list + (long long)glevel * C.band_cap;
+  }
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     const int gb = list[w];
-    // phi changes only on band cells, so outside the previous band no phase (and no
-    // stale flip bit: flips happen next to the interface, inside the band) can change
-    const bool band = (C.bflag[gb] & BF_BAND) != 0;
-    __syncthreads();  // every thread has read the flag before thread 0 rewrites it
-    if (!init && !band) continue;
     if (threadIdx.x == 0) C.bflag[gb] = init ? 0 : BF_OLDBAND;
     int x, y, z;
     const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
@@ -82,8 +84,20 @@ __global__ void k_flip_mark(Ctx C, BlockShape S, int glevel) {
       int sx = x + LT::cx(k), sy = y + LT::cy(k), sz = z + LT::cz(k);
       if (!(wrap(L, 0, sx) && wrap(L, 1, sy) && (D == 2 || wrap(L, 2, sz)))) continue;
       const int nb = L.block_off + block_of(L, sx, sy, sz, S);
-      const uint8_t f = C.bflag[nb];
-      if (!(f & (BF_OLDBAND | BF_CHECK))) C.bflag[nb] = f | BF_CHECK;  // byte store: only adds the bit
+      // set BF_CHECK once per block (compare-and-swap on the flag's word) and list it
+      unsigned *wp = reinterpret_cast<unsigned *>(C.bflag + (nb & ~3));
+      const int sh = (nb & 3) * 8;
+      unsigned old = *reinterpret_cast<volatile unsigned *>(wp);
+      while (!(((old >> sh) & 0xffu) & (BF_OLDBAND | BF_CHECK))) {
+        const unsigned prev = atomicCAS(wp, old, old | ((unsigned)BF_CHECK << sh));
+        if (prev == old) {
+          const int e = atomicAdd(&C.counters[glevel * NCOUNT + 4], 1);
+          if (e < C.band_cap) C.check_list[(long long)glevel * C.band_cap + e] = nb;
+          else atomicOr(C.err, ERR_BAND_OVF);
+          break;
+        }
+        old = prev;
+      }
     }
   }
 }
@@ -99,8 +113,17 @@ __global__ void k_classify_links(Ctx C, BlockShape S, const int *list, int nlist
   LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
+  // unless full: the previous band list, then the check list (every other block keeps
+  // flag 0 and an all-zero mask)
+  int nband = nlist;
+  if (!full) {
+    nband = min(C.counters[glevel * NCOUNT + 5], C.band_cap);
+    nlist = nband + min(C.counters[glevel * NCOUNT + 4], C.band_cap);
+    list = C.band_list + (long long)glevel * C.band_cap;
+  }
+  const int *chk = C.check_list + (long long)glevel * C.band_cap;
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
-    const int gb = list[w];
+    const int gb = w < nband ? list[w] : chk[w - nband];
     const bool work = full || (C.bflag[gb] & (BF_OLDBAND | BF_CHECK));
     __syncthreads();  // every thread has read the flags before thread 0 rewrites them
     if (!work) {
@@ -250,12 +273,24 @@ __global__ void k_geometry(Ctx C, int glevel, int which) {
     // fit to the closed-form solve; GB300 runs float64 at a small fraction of its
     // integer rate.
     long long iP = 0, isx[3] = {0, 0, 0}, isxx[3] = {0, 0, 0}, isxy[3] = {0, 0, 0};
+    // cells whose 3^D stencil lies inside the box read it at direct offsets
+    const bool inner = x >= 1 && x + 1 < L.n[0] && y >= 1 && y + 1 < L.n[1] && (D == 2 || (z >= 1 && z + 1 < L.n[2]));
+    const long long p0 = L.p[0], p01 = (long long)L.p[0] * L.p[1];
+#pragma unroll
     for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz)
+#pragma unroll
       for (int oy = -1; oy <= 1; ++oy)
+#pragma unroll
         for (int ox = -1; ox <= 1; ++ox) {
-          const int xx = clampwrap(L, 0, x + ox), yy = clampwrap(L, 1, y + oy);
-          const int zz = D == 3 ? clampwrap(L, 2, z + oz) : 0;
-          const long long v = __float2ll_rn(C.phi[L.fine_off + cidx(L, xx, yy, zz)] * 1073741824.0f);
+          long long cc;
+          if (inner) {
+            cc = c + ox + oy * p0 + oz * p01;
+          } else {
+            const int xx = clampwrap(L, 0, x + ox), yy = clampwrap(L, 1, y + oy);
+            const int zz = D == 3 ? clampwrap(L, 2, z + oz) : 0;
+            cc = cidx(L, xx, yy, zz);
+          }
+          const long long v = __float2ll_rn(C.phi[L.fine_off + cc] * 1073741824.0f);
           const int o[3] = {ox, oy, oz};
           iP += v;
           for (int a = 0; a < D; ++a) {
@@ -811,6 +846,12 @@ __global__ void k_reinit_stage(Ctx C, BlockShape S, int glevel, int stage) {
 // neighbours read.  The arithmetic and its order are those of the passes above,
 // so the results are the same bit for bit.
 
+// Resident CTAs of 512 threads per SM the mirrored stage kernels are compiled for (their
+// registers capped to fit): the passes are latency-bound, so more warps in flight pay.
+#ifndef LSB_LS_MINB
+#define LSB_LS_MINB 3
+#endif
+
 // seven values of the stage array along axis a at offsets -3..+3 (clamped or
 // wrapped at the box faces like gather7)
 __device__ __forceinline__ void gather7m(const LevelDev &L, const float *__restrict__ pinL, int x, int y, int z,
@@ -833,7 +874,7 @@ __device__ __forceinline__ void gather7m(const LevelDev &L, const float *__restr
 // First extension sweep of a step (mode 2 of d_ext_iter): sweep from uin = ut0 and
 // store the plan (S(phi) n, upwind sides, interface and box-boundary bits).
 template <int D>
-__global__ void k_ext_first(Ctx C, BlockShape S, int glevel, const float *__restrict__ uin,
+__global__ void __launch_bounds__(512, LSB_LS_MINB) k_ext_first(Ctx C, BlockShape S, int glevel, const float *__restrict__ uin,
                             float *__restrict__ uout) {
   LSB_GRID_WAIT();
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
@@ -905,7 +946,8 @@ __global__ void k_ext_first(Ctx C, BlockShape S, int glevel, const float *__rest
 // TVD-RK3 transport stage (as d_adv_stage).  Stage 1 takes u~ from the last
 // extension sweep (ufin) and commits it to ut0, ut1 and ut2 at the cell.
 template <int D>
-__global__ void k_adv_mirror(Ctx C, BlockShape S, int glevel, int stage, const float *__restrict__ ufin) {
+__global__ void __launch_bounds__(512, LSB_LS_MINB) k_adv_mirror(Ctx C, BlockShape S, int glevel, int stage,
+                                                                 const float *__restrict__ ufin) {
   LSB_GRID_WAIT();
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
   const float *pin = stage == 1 ? C.phi : (stage == 2 ? C.p1 : C.p2);
@@ -952,7 +994,8 @@ __global__ void k_adv_mirror(Ctx C, BlockShape S, int glevel, int stage, const f
 // pseudo step) it also finds the frozen cells and S(phi0) as d_reinit_prep does.
 // Frozen cells leave phi as it is and write it into the stage array of stages 1, 2.
 template <int Q>
-__global__ void k_reinit_mirror(Ctx C, BlockShape S, int glevel, int stage, int prep) {
+__global__ void __launch_bounds__(512, LSB_LS_MINB) k_reinit_mirror(Ctx C, BlockShape S, int glevel, int stage,
+                                                                    int prep) {
   LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
