@@ -1755,7 +1755,7 @@ lsb_status lsb_observables(lsb_grid *g, double *out_host, size_t n_doubles) {
   CU(cudaMemsetAsync(g->d_obs, 0, sizeof(double) * stride * g->ncase, g->stream));
   Ctx C = make_ctx(g);
   BlockShape S = shape(g);
-  const int og = std::min(g->leaf.n, 152 * 4);
+  const int og = std::min(g->leaf.n, 152 * 3);  // the resident CTAs of k_observables
   RUN(6, 0, g->leaf.n, g->nthreads, run_observables, g->Q, g->storage, LN(g, og, g->nthreads), C, S,
       (const int *)g->leaf.d, g->leaf.n, g->d_obs, stride, g->obj_eps);
   std::vector<double> h((size_t)stride * g->ncase);
@@ -1966,7 +1966,7 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
   Ctx C = make_ctx(g);
   BlockShape S = shape(g);
   CU(cudaMemsetAsync(g->d_obs, 0, sizeof(double) * stride * g->ncase, g->stream));
-  const int og = std::min(g->leaf.n, 152 * 4);
+  const int og = std::min(g->leaf.n, 152 * 3);  // the resident CTAs of k_observables
   RUN(6, 0, g->leaf.n, g->nthreads, run_observables, Q, g->storage, LN(g, og, g->nthreads), C, S,
       (const int *)g->leaf.d, g->leaf.n, g->d_obs, stride, g->obj_eps);
   // the objective's direct dependence on phi (smoothed indicator): into the level set's

@@ -855,8 +855,8 @@ __global__ void k_level_tags(Ctx C, BlockShape S, const int *list, int nlist) {
 template <int Q, typename T>
 // eps > 0: gas volume, centroid and velocity weighted by the smoothed indicator H_eps of
 // phi at the leaf's first finest child instead of the leaf's phase (masses stay phase sums)
-__global__ void k_observables(Ctx C, BlockShape S, const int *list, int nlist, double *out, int stride,
-                              float eps) {
+__global__ void __launch_bounds__(512, 3) k_observables(Ctx C, BlockShape S, const int *list, int nlist,
+                                                         double *out, int stride, float eps) {
   LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
@@ -886,15 +886,20 @@ __global__ void k_observables(Ctx C, BlockShape S, const int *list, int nlist, d
     }
     __syncthreads();
   };
+  // the next block's list entry and coordinates are loaded while this one is summed
+  int4 next = blockIdx.x < nlist ? __ldg(C.blk_info + __ldg(list + blockIdx.x)) : make_int4(0, 0, 0, 0);
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
-    const int gb = list[w];
-    const int case_id = C.lds[C.blk_info[gb].x].case_id;  // uniform over the CTA
+    const int4 bi = next;
+    if (w + gridDim.x < nlist) next = __ldg(C.blk_info + __ldg(list + w + gridDim.x));
+    const LevelDev &L = C.lds[bi.x];
+    const int case_id = L.case_id;  // uniform over the CTA
     if (case_id != cur_case) {
       if (cur_case >= 0) flush(cur_case);
       cur_case = case_id;
     }
-    int x, y, z;
-    const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
+    const int x = (bi.y << S.lg[0]) + (threadIdx.x & (S.bs[0] - 1));
+    const int y = (bi.z << S.lg[1]) + ((threadIdx.x >> S.lg[0]) & (S.bs[1] - 1));
+    const int z = (bi.w << S.lg[2]) + (threadIdx.x >> (S.lg[0] + S.lg[1]));
     if (x < L.n[0] && y < L.n[1] && z < L.n[2]) {
       const long long c = cidx(L, x, y, z);
       const uint8_t tg = C.tag[L.cell_off + c];
