@@ -134,6 +134,11 @@ struct lsb_grid {
   cudaGraphExec_t gexec[2][2] = {};  // [coarse steps per replay - 1][level-0 parity at the start]
   cudaStream_t side[MAXL] = {};        // per level: its collide-and-stream beside the first fine sub-step
   cudaEvent_t ev_fork[MAXL] = {}, ev_join[MAXL] = {};
+  // per level: its second sub-step's ghost ring, filled beside the first sub-step's
+  // interface, level-set, classification and refill passes
+  cudaStream_t side2[MAXL] = {};
+  cudaEvent_t ev_free[MAXL] = {}, ev_fill[MAXL] = {};
+  int early_fill = -1;  // level whose next ghost ring fills right after its collide
   uint64_t gnodes[2][2] = {};
   // adjoint of the frozen-interface step: recording and reverse sweep
   int rec_on = 0, rec_every = 0;
@@ -631,6 +636,28 @@ lsb_status advance(lsb_grid *g, int l) {
     RUN(collide_kid(l), cs_bytes, g->cs[l].n, nt, run_collide_stream, Q, st, LN(g, g->cs[l].n, nt), C, S, (const int *)g->cs[l].d,
         g->cs[l].n);
   }
+  if (g->early_fill == l) {
+    // the second sub-step's ghost ring (theta = 1/2): its pushes go to the buffer that
+    // sub-step streams into, which is this sub-step's A buffer (the collide has finished
+    // reading it, and the interface, level-set, classification and refill passes that
+    // follow touch only B); it reads the coarser level's A and B buffers, so it also waits
+    // for that level's collide on side[l - 1]
+    g->early_fill = -1;
+    if (!g->side2[l]) {
+      CU(cudaStreamCreateWithFlags(&g->side2[l], cudaStreamNonBlocking));
+      CU(cudaEventCreateWithFlags(&g->ev_free[l], cudaEventDisableTiming));
+      CU(cudaEventCreateWithFlags(&g->ev_fill[l], cudaEventDisableTiming));
+    }
+    CU(cudaEventRecord(g->ev_free[l], g->stream));
+    CU(cudaStreamWaitEvent(g->side2[l], g->ev_free[l], 0));
+    CU(cudaStreamWaitEvent(g->side2[l], g->ev_join[l - 1], 0));
+    Ctx C2 = make_ctx(g);
+    C2.par[l] ^= 1;  // the buffers of the next sub-step
+    const CellList &gc = g->ghost_cells[l];
+    RUN(3, 0, gc.n, 128, run_ghost_cells, Q, st, (Launch{(gc.n + 127) / 128, 128, g->side2[l]}), C2,
+        (const int2 *)gc.d, gc.n, 0.5f);
+    CU(cudaEventRecord(g->ev_fill[l], g->side2[l]));
+  }
   if (has_finest(g, l)) {
     RUN(1, 0, 1, 128, run_interface_bc, Q, st, LN(g, DYN_GRID, 128), C, l);
     if (ls_active_any(g, l)) {
@@ -643,13 +670,24 @@ lsb_status advance(lsb_grid *g, int l) {
   }
   if (call >= 0 && l + 1 < g->Lmax) TRY(copy_level(g, g->tape_new[call], (const float *)g->d_buf[1 - g->par[l]], l));
   if (l + 1 < g->Lmax) {
+    // with the next level the deepest (no sub-steps below it read its A buffer), its second
+    // ghost ring fills beside its first sub-step
+    const bool early = fork && l + 2 == g->Lmax;
     for (int sub = 0; sub < 2; ++sub) {
-      if (sub == 1 && fork) CU(cudaStreamWaitEvent(g->stream, g->ev_join[l], 0));  // theta = 1/2 reads B
-      C = make_ctx(g);
-      const float theta = sub == 0 ? 0.0f : 0.5f;
-      const CellList &gc = g->ghost_cells[l + 1];
-      RUN(3, 0, gc.n, 128, run_ghost_cells, Q, st, LN(g, (gc.n + 127) / 128, 128), C, (const int2 *)gc.d, gc.n, theta);
-      TRY(advance(g, l + 1));
+      if (sub == 1 && early) {
+        CU(cudaStreamWaitEvent(g->stream, g->ev_fill[l + 1], 0));  // after the coarse collide, too
+      } else {
+        if (sub == 1 && fork) CU(cudaStreamWaitEvent(g->stream, g->ev_join[l], 0));  // theta = 1/2 reads B
+        C = make_ctx(g);
+        const float theta = sub == 0 ? 0.0f : 0.5f;
+        const CellList &gc = g->ghost_cells[l + 1];
+        RUN(3, 0, gc.n, 128, run_ghost_cells, Q, st, LN(g, (gc.n + 127) / 128, 128), C, (const int2 *)gc.d, gc.n,
+            theta);
+      }
+      if (sub == 0 && early) g->early_fill = l + 1;
+      const lsb_status r = advance(g, l + 1);
+      g->early_fill = -1;
+      if (r != LSB_OK) return r;
     }
   }
   g->par[l] ^= 1;
@@ -2116,13 +2154,20 @@ void lsb_destroy(lsb_grid *g) {
   if (g->stream) cudaStreamSynchronize(g->stream);
   else cudaDeviceSynchronize();
   drop_graphs(g);
-  for (int l = 0; l < MAXL; ++l)
+  for (int l = 0; l < MAXL; ++l) {
+    if (g->side2[l]) {
+      cudaStreamSynchronize(g->side2[l]);
+      cudaStreamDestroy(g->side2[l]);
+      cudaEventDestroy(g->ev_free[l]);
+      cudaEventDestroy(g->ev_fill[l]);
+    }
     if (g->side[l]) {
       cudaStreamSynchronize(g->side[l]);
       cudaStreamDestroy(g->side[l]);
       cudaEventDestroy(g->ev_fork[l]);
       cudaEventDestroy(g->ev_join[l]);
     }
+  }
   for (void *p : g->allocs) cudaFree(p);
   if (g->d_lsa) cudaFree(g->d_lsa);
   if (g->d_seg) cudaFree(g->d_seg);

@@ -139,7 +139,7 @@ def test_autograd_initial_radius_gradient():
     Jo, dp_o, (lf, lphi, lut) = gradients(st, (sim.f[0].copy(), sim.phi.copy(), sim.ut.copy()), params_of(sim),
                                           steps, a)
     assert sim.stats["flipped"] == 0
-    assert abs(float(J) - Jo) < 1e-4
+    assert abs(float(J.detach()) - Jo) < 1e-4
     dR_o = float(lphi.sum())
     assert abs(float(dR) - dR_o) <= 1e-3 * abs(dR_o), (float(dR), dR_o)
     # central differences of the oracle in R (same phases, same initial populations)

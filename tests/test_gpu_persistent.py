@@ -103,14 +103,23 @@ def test_single_step_graph_replay_matches_eager():
     _same(ref2, got2)
 
 
-def test_side_stream_coarse_collide_matches_serial():
+@pytest.mark.parametrize("dim", [3, 2])
+def test_side_stream_coarse_collide_matches_serial(dim):
     """With a stream of its own and kernel timing off, a coarser level's collide-and-stream
-    runs on a side stream beside the first fine sub-step; with kernel timing on it runs in
-    line.  Both orders give the same state bit for bit (eager and graph replay)."""
+    runs on a side stream beside the first fine sub-step, and the deepest level's second
+    ghost ring fills on another beside the first sub-step's interface and level-set
+    passes; with kernel timing on both run in line.  Both orders give the same state bit
+    for bit (eager and graph replay; two levels in 3D, three in 2D, where the middle
+    level's collide and the deepest ring's fill both leave the main stream)."""
     import torch
 
     from paper_2601_05936_gb300 import lsb, workloads
-    case = workloads.rising_bubble_3d(scale=0.25)
+    if dim == 3:
+        case = workloads.rising_bubble_3d(scale=0.25)
+    else:
+        case = workloads.rising_bubble_2d(nx=64, ny=128, levels=3, radius_base=8.0)
+        case["regrid_every"] = 3
+    nl = case["n_levels"]
 
     def run(timed, graphs):
         st = torch.cuda.Stream()
@@ -122,7 +131,7 @@ def test_side_stream_coarse_collide_matches_serial():
         if timed:
             g.profile_read()
             g.profile(0)
-        out = [g.get(f, 0, l) for l in range(2) for f in ("rho", "u")] + [g.get("phi"), g.get("tag")]
+        out = [g.get(f, 0, l) for l in range(nl) for f in ("rho", "u")] + [g.get("phi"), g.get("tag")]
         g.close()
         return out
 
