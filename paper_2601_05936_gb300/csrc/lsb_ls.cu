@@ -303,49 +303,37 @@ __global__ void k_geometry(Ctx C, int glevel, int which) {
             isxy[2] += oy * oz > 0 ? v : (oy * oz < 0 ? -v : 0);
           }
         }
-    const double sc = 1.0 / 1073741824.0;
-    const double P = (double)iP * sc;
-    double sx[3], sxx[3], sxy[3];
-    for (int a = 0; a < 3; ++a) {
-      sx[a] = (double)isx[a] * sc;
-      sxx[a] = (double)isxx[a] * sc;
-      sxy[a] = (double)isxy[a] * sc;
-    }
-    double g[3] = {0, 0, 0}, H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    if (D == 2) {
-      // sums over 9 points: sum o^2 = 6, sum o_x^2 o_y^2 = 4, sum o^4 = 6
-      const double R = sxx[0] + sxx[1];
-      const double s = (3.0 * R - 4.0 * P) / 6.0;
-      const double a0 = (5.0 * P - 3.0 * R) / 9.0;
-      for (int a = 0; a < 2; ++a) {
-        g[a] = sx[a] / 6.0;
-        H[a][a] = 2.0 * (sxx[a] - 6.0 * a0 - 4.0 * s) / 2.0;
-      }
-      H[0][1] = H[1][0] = sxy[0] / 4.0;
-    } else {
-      // sums over 27 points: sum o^2 = 18, sum o_a^2 o_b^2 = 12, sum o^4 = 18
-      const double R = sxx[0] + sxx[1] + sxx[2];
-      const double s = (R - 2.0 * P) / 6.0;
-      const double a0 = (7.0 * P - 3.0 * R) / 27.0;
-      for (int a = 0; a < 3; ++a) {
-        g[a] = sx[a] / 18.0;
-        H[a][a] = 2.0 * (sxx[a] - 18.0 * a0 - 12.0 * s) / 6.0;
-      }
-      H[0][1] = H[1][0] = sxy[0] / 12.0;
-      H[0][2] = H[2][0] = sxy[1] / 12.0;
-      H[1][2] = H[2][1] = sxy[2] / 12.0;
-    }
-    double g2 = 0, tr = 0, gHg = 0;
+    // The fit's coefficients are fixed rational combinations of the stencil sums.  In 2D
+    // (9 points: sum o^2 = 6, sum o_x^2 o_y^2 = 4, sum o^4 = 6) g_a = S_a / 6, H_aa =
+    // (3 S_aa - 2 P) / 3, H_xy = S_xy / 4; in 3D (27 points: 18, 12, 18) g_a = S_a / 18,
+    // H_aa = (3 S_aa - 2 P) / 9, H_ab = S_ab / 12.  In the unit 1 / (12 * 2^30) (2D) or
+    // 1 / (36 * 2^30) (3D) both read g = 2 G and H = K with the integers G_a = S_a,
+    // K_aa = 4 (3 S_aa - 2 P), K_ab = 3 S_ab, and kappa, homogeneous of degree zero in
+    // (g, H), is (|G|^2 tr K - G.K.G) / (2 |G|^3): float64 from exact integers, one
+    // square root and two divisions.
+    double G[3] = {0, 0, 0}, K[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     for (int a = 0; a < D; ++a) {
-      g2 += g[a] * g[a];
-      tr += H[a][a];
-      for (int b = 0; b < D; ++b) gHg += g[a] * H[a][b] * g[b];
+      G[a] = (double)isx[a];
+      K[a][a] = (double)(4 * (3 * isxx[a] - 2 * iP));
+    }
+    K[0][1] = K[1][0] = (double)(3 * isxy[0]);
+    if (D == 3) {
+      K[0][2] = K[2][0] = (double)(3 * isxy[1]);
+      K[1][2] = K[2][1] = (double)(3 * isxy[2]);
+    }
+    double g2 = 0, tr = 0, gKg = 0;
+    for (int a = 0; a < D; ++a) {
+      g2 += G[a] * G[a];
+      tr += K[a][a];
+      for (int b = 0; b < D; ++b) gKg += G[a] * K[a][b] * G[b];
     }
     const double mag = sqrt(g2);
     const long long fc = L.fine_off + c;
-    if (mag > 1e-12) {
-      for (int a = 0; a < D; ++a) C.nvec[a * C.nfine + fc] = (float)(g[a] / mag);
-      C.kappa[fc] = (float)((g2 * tr - gHg) / (mag * mag * mag));
+    // |grad phi| = |G| / (6 or 18) / 2^30
+    if (mag > 1e-12 * (D == 2 ? 6.0 : 18.0) * 1073741824.0) {
+      const double inv = 1.0 / mag;
+      for (int a = 0; a < D; ++a) C.nvec[a * C.nfine + fc] = (float)(G[a] * inv);
+      C.kappa[fc] = (float)((g2 * tr - gKg) / (2.0 * g2 * mag));
     } else {
       for (int a = 0; a < D; ++a) C.nvec[a * C.nfine + fc] = 0.f;
       C.kappa[fc] = 0.f;
