@@ -734,15 +734,17 @@ __device__ __forceinline__ void interp_coarse(const Ctx &C, const LevelDev &Lc, 
   const T *Ac = fA<T, Q>(C, Lc);
   const T *Bc = fB<T, Q>(C, Lc);
   const int P[3] = {x >> 1, y >> 1, D == 3 ? (z >> 1) : 0};
-  auto load = [&](long long cc, float *dst) {
+  // Q x cells of a level stay below 2^32 (checked at creation): 32-bit offsets
+  const unsigned Nc = (unsigned)Lc.ncell;
+  auto load = [&](unsigned cc, float *dst) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      float a = Store<T>::ld(Ac + i * Lc.ncell + cc, C.fp16_inv);
-      if (theta != 0.f) a = (1.0f - theta) * a + theta * Store<T>::ld(Bc + i * Lc.ncell + cc, C.fp16_inv);
+      float a = Store<T>::ld(Ac + (i * Nc + cc), C.fp16_inv);
+      if (theta != 0.f) a = (1.0f - theta) * a + theta * Store<T>::ld(Bc + (i * Nc + cc), C.fp16_inv);
       dst[i] = a;
     }
   };
-  const long long cp = cidx(Lc, P[0], P[1], P[2]);
+  const unsigned cp = (unsigned)cidx(Lc, P[0], P[1], P[2]);
   float fp[Q];
   load(cp, fp);
 #pragma unroll
@@ -755,13 +757,13 @@ __device__ __forceinline__ void interp_coarse(const Ctx &C, const LevelDev &Lc, 
     dn[a] -= 1;
     bool upok = wrap(Lc, a, up[a]);
     bool dnok = wrap(Lc, a, dn[a]);
-    long long cu = 0, cd = 0;
+    unsigned cu = 0, cd = 0;
     if (upok) {
-      cu = cidx(Lc, up[0], up[1], up[2]);
+      cu = (unsigned)cidx(Lc, up[0], up[1], up[2]);
       upok = (C.tag[Lc.cell_off + cu] & TAG_LEAF) != 0;
     }
     if (dnok) {
-      cd = cidx(Lc, dn[0], dn[1], dn[2]);
+      cd = (unsigned)cidx(Lc, dn[0], dn[1], dn[2]);
       dnok = (C.tag[Lc.cell_off + cd] & TAG_LEAF) != 0;
     }
     if (!upok && !dnok) continue;
@@ -1049,6 +1051,19 @@ __global__ void LSB_GHOST_LB k_ghost_cells(Ctx C, const int2 *cells, int n, floa
     const float acc[3] = {F.acc[ph][0], F.acc[ph][1], F.acc[ph][2]};
     collide_phase<Q>(f, F.omega[ph], acc, drho, u, F.cumulant[ph]);
     T *Bf = fB<T, Q>(C, F);
+    const unsigned N = (unsigned)F.ncell;
+    const uint8_t *tagF = C.tag + F.cell_off;
+    if (x > 0 && x + 1 < F.n[0] && y > 0 && y + 1 < F.n[1] && (D == 2 || (z > 0 && z + 1 < F.n[2]))) {
+      // away from the box faces every target is c + c_i
+      const int p0 = F.p[0], p01 = F.p[0] * F.p[1];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if (i == LT::REST) continue;
+        const unsigned ct = (unsigned)((int)c + LT::cx(i) + LT::cy(i) * p0 + LT::cz(i) * p01);
+        if (tagF[ct] & TAG_LEAF) Store<T>::st(Bf + (i * N + ct), f[i], C.fp16_scale);
+      }
+      continue;
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if (i == LT::REST) continue;
