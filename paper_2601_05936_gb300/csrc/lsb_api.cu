@@ -597,8 +597,28 @@ lsb_status advance(lsb_grid *g, int l) {
   const int nt = g->nthreads;
   Ctx C = make_ctx(g);
   const int Q = g->Q, st = g->storage;
+  // A coarser level's collide-and-stream writes only its own B buffer, and the first fine
+  // sub-step reads only its A buffer at leaf cells (ghost ring at theta = 0): with no case
+  // finishing at this level, the restriction (it writes A at covered cells from the finer
+  // level's A, which that sub-step only reads) and the collide run on a side stream beside
+  // that sub-step (half the resident CTAs, so the sub-step's kernels find room), joined
+  // before anything of the second sub-step writes the finer A buffer or reads this B.
+  const bool fork = g->stream && g->prof_mode == 0 && !g->tape_on && l + 1 < g->Lmax && !has_finest(g, l) &&
+                    g->d_tmaps && !g->no_tma && !g->tma_a;
   const CellList &rc = g->rl_cells[l];
-  RUN(2, 0, rc.n, 128, run_restrict_cells, Q, st, LN(g, (rc.n + 127) / 128, 128), C, (const int2 *)rc.d, rc.n);
+  if (fork) {
+    if (!g->side[l]) {
+      CU(cudaStreamCreateWithFlags(&g->side[l], cudaStreamNonBlocking));
+      CU(cudaEventCreateWithFlags(&g->ev_fork[l], cudaEventDisableTiming));
+      CU(cudaEventCreateWithFlags(&g->ev_join[l], cudaEventDisableTiming));
+    }
+    CU(cudaEventRecord(g->ev_fork[l], g->stream));
+    CU(cudaStreamWaitEvent(g->side[l], g->ev_fork[l], 0));
+    RUN(2, 0, rc.n, 128, run_restrict_cells, Q, st, (Launch{(rc.n + 127) / 128, 128, g->side[l]}), C,
+        (const int2 *)rc.d, rc.n);
+  } else {
+    RUN(2, 0, rc.n, 128, run_restrict_cells, Q, st, LN(g, (rc.n + 127) / 128, 128), C, (const int2 *)rc.d, rc.n);
+  }
   const int call = g->tape_on ? g->tape_call++ : -1;
   if (call >= 0) TRY(copy_level(g, g->tape_old[call], (const float *)g->d_buf[g->par[l]], l));
   if (call >= 0 && g->rec_moving && l == g->Lmax - 1) {  // the level set at the finest sub-step's start
@@ -608,20 +628,7 @@ lsb_status advance(lsb_grid *g, int l) {
                        g->stream));
   }
   const double cs_bytes = 2.0 * g->Q * (g->storage == LSB_FP32 ? 4 : 2) * g->leaf_cells[l];
-  // A coarser level's collide-and-stream writes only its own B buffer, and the first fine
-  // sub-step reads only its A buffer (ghost ring at theta = 0): with no case finishing at
-  // this level, the collide runs on a side stream beside that sub-step (half the resident
-  // CTAs, so the sub-step's kernels find room) and is joined before the second sub-step.
-  const bool fork = g->stream && g->prof_mode == 0 && !g->tape_on && l + 1 < g->Lmax && !has_finest(g, l) &&
-                    g->d_tmaps && !g->no_tma && !g->tma_a;
   if (fork) {
-    if (!g->side[l]) {
-      CU(cudaStreamCreateWithFlags(&g->side[l], cudaStreamNonBlocking));
-      CU(cudaEventCreateWithFlags(&g->ev_fork[l], cudaEventDisableTiming));
-      CU(cudaEventCreateWithFlags(&g->ev_join[l], cudaEventDisableTiming));
-    }
-    CU(cudaEventRecord(g->ev_fork[l], g->stream));
-    CU(cudaStreamWaitEvent(g->side[l], g->ev_fork[l], 0));
     const int grid = std::min(g->cs[l].n, std::max(1, g->tma_grid / 2));
     const CUtensorMap *tm = (const CUtensorMap *)g->d_tmaps;
     RUN(collide_kid(l), cs_bytes, g->cs[l].n, nt, run_collide_stream_tma, Q, st, Launch{grid, nt, g->side[l]}, C, S,
