@@ -130,6 +130,7 @@ struct lsb_grid {
   // TMA tensor maps of every level's population buffers (2 per level descriptor)
   CUtensorMap *d_tmaps = nullptr;
   int tma_grid = 0;
+  int obs_tma_grid = 0;           // resident CTAs of the TMA-staged observables pass (0: not built)
   int tma_tags = 0;               // d_tmaps also holds one cell-tag map per level descriptor
   cudaGraphExec_t gexec[2][2] = {};  // [coarse steps per replay - 1][level-0 parity at the start]
   cudaStream_t side[MAXL] = {};        // per level: its collide-and-stream beside the first fine sub-step
@@ -834,6 +835,11 @@ lsb_status build_tensor_maps(lsb_grid *g) {
   CU(cudaMemcpy(g->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
   g->tma_grid = per_sm * nsm;
   g->tma_tags = tags;
+  int obs_sm = 0;
+  if (prepare_observables_tma(g->Q, g->storage, g->nthreads, &obs_sm) == cudaSuccess && obs_sm >= 1)
+    g->obs_tma_grid = obs_sm * nsm;
+  else
+    cudaGetLastError();
   g->encode_fn = fn;
   return LSB_OK;
 }
@@ -1793,6 +1799,19 @@ lsb_status lsb_get_fields(lsb_grid *g, int case_idx, int field, int level, void 
   return lsb_sync(g);
 }
 
+// The observables of every case into d_obs (zeroed by the caller): the TMA-staged pass
+// when the population maps are the plain ones, else per-thread loads.
+lsb_status observables_pass(lsb_grid *g, const Ctx &C, const BlockShape &S, int stride) {
+  const bool tma = g->obs_tma_grid > 0 && g->d_tmaps && !g->no_tma && !g->tma_a;
+  const CUtensorMap *tm = tma ? (const CUtensorMap *)g->d_tmaps : nullptr;
+  const CUtensorMap *tt = tma && g->tma_tags ? tm + 2 * g->lds.size() : nullptr;
+  // the resident CTAs of the kernel that runs
+  const int og = std::min(g->leaf.n, tma ? g->obs_tma_grid : 152 * LSB_OBS_MINB);
+  RUN(6, 0, g->leaf.n, g->nthreads, run_observables, g->Q, g->storage, LN(g, og, g->nthreads), C, S,
+      (const int *)g->leaf.d, g->leaf.n, g->d_obs, stride, g->obj_eps, tm, tt);
+  return LSB_OK;
+}
+
 lsb_status lsb_observables(lsb_grid *g, double *out_host, size_t n_doubles) {
   if (!g || !out_host) return LSB_EINVAL;
   const int stride = 4 + 2 * g->D;
@@ -1800,9 +1819,7 @@ lsb_status lsb_observables(lsb_grid *g, double *out_host, size_t n_doubles) {
   CU(cudaMemsetAsync(g->d_obs, 0, sizeof(double) * stride * g->ncase, g->stream));
   Ctx C = make_ctx(g);
   BlockShape S = shape(g);
-  const int og = std::min(g->leaf.n, 152 * 3);  // the resident CTAs of k_observables
-  RUN(6, 0, g->leaf.n, g->nthreads, run_observables, g->Q, g->storage, LN(g, og, g->nthreads), C, S,
-      (const int *)g->leaf.d, g->leaf.n, g->d_obs, stride, g->obj_eps);
+  TRY(observables_pass(g, C, S, stride));
   std::vector<double> h((size_t)stride * g->ncase);
   CU(cudaMemcpyAsync(h.data(), g->d_obs, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g->stream));
   lsb_status s = lsb_sync(g);
@@ -2011,9 +2028,7 @@ lsb_status lsb_backward(lsb_grid *g, const double *dJ_dobs, double *dJ_dparams, 
   Ctx C = make_ctx(g);
   BlockShape S = shape(g);
   CU(cudaMemsetAsync(g->d_obs, 0, sizeof(double) * stride * g->ncase, g->stream));
-  const int og = std::min(g->leaf.n, 152 * 3);  // the resident CTAs of k_observables
-  RUN(6, 0, g->leaf.n, g->nthreads, run_observables, Q, g->storage, LN(g, og, g->nthreads), C, S,
-      (const int *)g->leaf.d, g->leaf.n, g->d_obs, stride, g->obj_eps);
+  TRY(observables_pass(g, C, S, stride));
   // the objective's direct dependence on phi (smoothed indicator): into the level set's
   // adjoint at the end of the window (moving), or into dJ/dphi (frozen)
   float *lphi = g->obj_eps > 0.f ? (mv ? lsa_ptrs(g).LP[0] : (dJ_dphi0 ? g->d_gphi : nullptr)) : nullptr;

@@ -71,8 +71,14 @@ cudaError_t run_collect(Launch L, Ctx C, BlockShape S, const int *list, int n, i
                         int cap);
 cudaError_t run_restrict_cells(int Q, int st, Launch L, Ctx C, const int2 *cells, int n);
 cudaError_t run_ghost_cells(int Q, int st, Launch L, Ctx C, const int2 *cells, int n, float theta);
+#ifndef LSB_OBS_MINB
+#define LSB_OBS_MINB 2  // CTAs of 512 threads per SM k_observables is built for (its grid)
+#endif
+// tmaps (population maps as for the TMA-staged collide; tmaps_tag optional): the
+// TMA-staged kernel (grid at most its resident CTAs); nullptr: per-thread loads
 cudaError_t run_observables(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, double *out,
-                            int stride, float eps);
+                            int stride, float eps, const CUtensorMap *tmaps, const CUtensorMap *tmaps_tag);
+cudaError_t prepare_observables_tma(int Q, int st, int nthreads, int *ctas_per_sm);
 cudaError_t run_export(int Q, int st, Launch L, Ctx C, int ld, int field, float *dst);
 // Export into the file-scope staging array; *staged receives its device address.
 cudaError_t run_export_noalloc(int Q, int st, Launch L, Ctx C, int ld, int field, float **staged);

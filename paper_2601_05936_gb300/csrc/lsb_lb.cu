@@ -853,25 +853,54 @@ __global__ void k_level_tags(Ctx C, BlockShape S, const int *list, int nlist) {
 // velocity of the gas (sharp Heaviside, Sec. 3.2), lengths in finest cells.
 // Persistent CTAs accumulate in registers while the case stays the same, then
 // reduce through warp shuffles and shared memory: one set of atomics per CTA
-// and case run instead of one per warp and block.
-template <int Q, typename T>
-// eps > 0: gas volume, centroid and velocity weighted by the smoothed indicator H_eps of
-// phi at the leaf's first finest child instead of the leaf's phase (masses stay phase sums)
-__global__ void __launch_bounds__(512, 3) k_observables(Ctx C, BlockShape S, const int *list, int nlist,
-                                                         double *out, int stride, float eps) {
-  LSB_GRID_WAIT();
-  using LT = Lat<Q>;
-  constexpr int D = LT::D;
-  constexpr int NV = 4 + 2 * D;
-  __shared__ double red[32][NV];
-  // per-thread partials in FP32 over the thread's few cells, FP64 from the warp sum on:
-  // cell volumes, counts and centroid terms are integer-valued (exact in FP32 while a
-  // thread's sums stay below 2^24); mass is kept as volume + vol * drho with the small
-  // second part summed apart
-  float vol_l = 0.f, vol_g = 0.f, dm_l = 0.f, dm_g = 0.f, v[NV];  // per phase as scalars (registers)
-  for (int k = 0; k < NV; ++k) v[k] = 0.f;
+// and case run instead of one per warp and block.  eps > 0: gas volume, centroid
+// and velocity weighted by the smoothed indicator H_eps of phi at the leaf's first
+// finest child instead of the leaf's phase (masses stay phase sums).
+//
+// Per-thread partials are FP32 over the thread's few cells, FP64 from the warp sum on:
+// cell volumes, counts and centroid terms are integer-valued (exact in FP32 while a
+// thread's sums stay below 2^24); mass is kept as volume + vol * drho with the small
+// second part summed apart.
+template <int D>
+struct ObsAcc {
+  static constexpr int NV = 4 + 2 * D;
+  float vol_l = 0.f, vol_g = 0.f, dm_l = 0.f, dm_g = 0.f, v[NV];
   int cur_case = -1;
-  auto flush = [&](int case_id) {
+  __device__ ObsAcc() {
+    for (int k = 0; k < NV; ++k) v[k] = 0.f;
+  }
+  // one leaf cell with populations f
+  template <int Q>
+  __device__ __forceinline__ void cell(const Ctx &C, const LevelDev &L, int x, int y, int z, uint8_t tg,
+                                       const float *f, float eps) {
+    float drho, u[3];
+    lb_moments<Q>(f, drho, u);
+    float vol = 1.f;
+    for (int a = 0; a < D; ++a) vol *= (float)L.scale;
+    const int gas = tg & TAG_GAS;
+    if (gas) {
+      vol_g += vol;
+      dm_g += vol * drho;
+    } else {
+      vol_l += vol;
+      dm_l += vol * drho;
+    }
+    v[3] += 1.f;
+    const bool finite = isfinite(drho) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
+    if (!finite) atomicOr(C.err, ERR_NONFINITE);
+    const float h = eps > 0.f ? smooth_h(C.phi[corner_phi_index(C, L, x, y, z)], eps) : (gas ? 1.f : 0.f);
+    if (h != 0.f) {
+      const float vh = vol * h;
+      v[2] += vh;
+      const int crd[3] = {x, y, z};
+      for (int a = 0; a < D; ++a) {
+        v[4 + a] += vh * ((float)crd[a] + 0.5f) * (float)L.scale;
+        v[4 + D + a] += vh * u[a];
+      }
+    }
+  }
+  // the CTA's partials of case_id into out (every thread of the CTA calls this)
+  __device__ void flush(double *out, int stride, int case_id, double (*red)[NV]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     for (int k = 0; k < NV; ++k) {
       double s = k == 0 ? (double)vol_l + (double)dm_l : (k == 1 ? (double)vol_g + (double)dm_g : (double)v[k]);
@@ -887,58 +916,147 @@ __global__ void __launch_bounds__(512, 3) k_observables(Ctx C, BlockShape S, con
       if (s != 0.0) atomicAdd(out + (long long)case_id * stride + threadIdx.x, s);
     }
     __syncthreads();
-  };
+  }
+  // called with each block's case before its cells (uniform over the CTA)
+  __device__ __forceinline__ void enter(double *out, int stride, int case_id, double (*red)[NV]) {
+    if (case_id != cur_case) {
+      if (cur_case >= 0) flush(out, stride, cur_case, red);
+      cur_case = case_id;
+    }
+  }
+  __device__ __forceinline__ void finish(double *out, int stride, double (*red)[NV]) {
+    if (cur_case >= 0) flush(out, stride, cur_case, red);
+  }
+};
+
+template <int Q, typename T>
+__global__ void __launch_bounds__(512, LSB_OBS_MINB) k_observables(Ctx C, BlockShape S, const int *list, int nlist,
+                                                                   double *out, int stride, float eps) {
+  LSB_GRID_WAIT();
+  constexpr int D = Lat<Q>::D;
+  __shared__ double red[32][ObsAcc<D>::NV];
+  ObsAcc<D> acc;
   // the next block's list entry and coordinates are loaded while this one is summed
   int4 next = blockIdx.x < nlist ? __ldg(C.blk_info + __ldg(list + blockIdx.x)) : make_int4(0, 0, 0, 0);
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     const int4 bi = next;
     if (w + gridDim.x < nlist) next = __ldg(C.blk_info + __ldg(list + w + gridDim.x));
     const LevelDev &L = C.lds[bi.x];
-    const int case_id = L.case_id;  // uniform over the CTA
-    if (case_id != cur_case) {
-      if (cur_case >= 0) flush(cur_case);
-      cur_case = case_id;
-    }
+    acc.enter(out, stride, L.case_id, red);
     const int x = (bi.y << S.lg[0]) + (threadIdx.x & (S.bs[0] - 1));
     const int y = (bi.z << S.lg[1]) + ((threadIdx.x >> S.lg[0]) & (S.bs[1] - 1));
     const int z = (bi.w << S.lg[2]) + (threadIdx.x >> (S.lg[0] + S.lg[1]));
     if (x < L.n[0] && y < L.n[1] && z < L.n[2]) {
-      const long long c = cidx(L, x, y, z);
+      const unsigned c = (unsigned)cidx(L, x, y, z);
+      // the populations are loaded beside the cell's tag (every cell of a listed block
+      // holds them), so the two loads do not wait on each other
       const uint8_t tg = C.tag[L.cell_off + c];
-      if (tg & TAG_LEAF) {
-        const T *A = fA<T, Q>(C, L);
-        float f[Q];
+      const T *A = fA<T, Q>(C, L);
+      const unsigned N = (unsigned)L.ncell;
+      float f[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) f[i] = Store<T>::ld(A + i * L.ncell + c, C.fp16_inv);
-        float drho, u[3];
-        lb_moments<Q>(f, drho, u);
-        float vol = 1.f;
-        for (int a = 0; a < D; ++a) vol *= (float)L.scale;
-        const int gas = tg & TAG_GAS;
-        if (gas) {
-          vol_g += vol;
-          dm_g += vol * drho;
-        } else {
-          vol_l += vol;
-          dm_l += vol * drho;
-        }
-        v[3] += 1.f;
-        const bool finite = isfinite(drho) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
-        if (!finite) atomicOr(C.err, ERR_NONFINITE);
-        const float h = eps > 0.f ? smooth_h(C.phi[corner_phi_index(C, L, x, y, z)], eps) : (gas ? 1.f : 0.f);
-        if (h != 0.f) {
-          const float vh = vol * h;
-          v[2] += vh;
-          const int crd[3] = {x, y, z};
-          for (int a = 0; a < D; ++a) {
-            v[4 + a] += vh * ((float)crd[a] + 0.5f) * (float)L.scale;
-            v[4 + D + a] += vh * u[a];
-          }
-        }
-      }
+      for (int i = 0; i < Q; ++i) f[i] = Store<T>::ld(A + (i * N + c), C.fp16_inv);
+      if (tg & TAG_LEAF) acc.template cell<Q>(C, L, x, y, z, tg, f, eps);
     }
   }
-  if (cur_case >= 0) flush(cur_case);
+  acc.finish(out, stride, red);
+}
+
+// The same sums with each block's populations (and tags) brought into shared memory
+// by one TMA load, two stages per CTA as in the TMA-staged collide-and-stream: a
+// block's Q population planes arrive in one bulk copy instead of Q loads per thread,
+// so the pass streams at the copy rate instead of waiting on the loads each thread
+// keeps in flight.  The stage is refilled once every thread holds its populations;
+// waits are bounded (ERR_TIMEOUT, then a bounded wait for the other load in flight).
+struct ObsMeta {
+  int ld, x0, y0, z0;
+};
+template <int Q, typename T>
+__global__ void __launch_bounds__(512, 2) k_observables_tma(Ctx C, BlockShape S, const int *__restrict__ list,
+                                                            int nlist, double *out, int stride, float eps,
+                                                            const CUtensorMap *__restrict__ tmaps,
+                                                            const CUtensorMap *__restrict__ tmaps_tag) {
+  LSB_GRID_WAIT();
+  constexpr int D = Lat<Q>::D;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ ObsMeta meta[4];  // iteration it uses meta[it & 3]; two blocks are staged ahead
+  __shared__ double red[32][ObsAcc<D>::NV];
+  const int nt = blockDim.x;
+  const bool stag = tmaps_tag != nullptr;
+  const unsigned stage_bytes = (unsigned)(Q * nt * sizeof(T));
+  const unsigned tag_off = (stage_bytes + 127u) & ~127u;
+  const unsigned stage_stride = (tag_off + nt + 127u) & ~127u;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int w, int st, int ms) {
+    const int4 bi = __ldg(C.blk_info + __ldg(list + w));
+    const LevelDev &L = C.lds[bi.x];
+    ObsMeta &m = meta[ms];
+    m.ld = bi.x;
+    m.x0 = bi.y << S.lg[0];
+    m.y0 = bi.z << S.lg[1];
+    m.z0 = bi.w << S.lg[2];
+    const CUtensorMap *tm = tmaps + 2 * bi.x + C.par[L.level];
+    mbar_expect_tx(&bar[st], stage_bytes + (stag ? (unsigned)nt : 0u));
+    T *dst = reinterpret_cast<T *>(smem_raw + st * stage_stride);
+    if (D == 3) tma_load_4d(dst, tm, m.x0, m.y0, m.z0, 0, &bar[st]);
+    else tma_load_3d(dst, tm, m.x0, m.y0, 0, &bar[st]);
+    if (stag) {
+      unsigned char *tdst = smem_raw + st * stage_stride + tag_off;
+      if (D == 3) tma_load_3d(tdst, tmaps_tag + bi.x, m.x0, m.y0, m.z0, &bar[st]);
+      else tma_load_2d(tdst, tmaps_tag + bi.x, m.x0, m.y0, &bar[st]);
+    }
+  };
+  const int G = gridDim.x;
+  if (threadIdx.x == 0) {
+    if ((int)blockIdx.x < nlist) issue(blockIdx.x, 0, 0);
+    if ((int)blockIdx.x + G < nlist) issue(blockIdx.x + G, 1, 1);
+  }
+  auto wait_stage = [&](int j) {
+    for (unsigned spins = 0; !mbar_try_wait(&bar[j & 1], (j >> 1) & 1);)
+      if (++spins > kWaitLimit) return false;
+    return true;
+  };
+  ObsAcc<D> acc;
+  int it = 0;
+  for (int w = blockIdx.x; w < nlist; w += G, ++it) {
+    const int st = it & 1;
+    const bool ok = wait_stage(it);
+    const ObsMeta m = meta[it & 3];
+    const LevelDev &L = C.lds[m.ld];
+    const int t = threadIdx.x;
+    const int x = m.x0 + (t & (S.bs[0] - 1));
+    const int y = m.y0 + ((t >> S.lg[0]) & (S.bs[1] - 1));
+    const int z = m.z0 + (t >> (S.lg[0] + S.lg[1]));
+    bool act = ok && x < L.n[0] && y < L.n[1] && z < L.n[2];
+    uint8_t tg = 0;
+    if (act) {
+      tg = stag ? smem_raw[st * stage_stride + tag_off + t] : C.tag[L.cell_off + cidx(L, x, y, z)];
+      act = (tg & TAG_LEAF) != 0;
+    }
+    float f[Q];
+    if (act) {
+      const T *sp = reinterpret_cast<const T *>(smem_raw + st * stage_stride);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) f[i] = stage_ld<T>(sp + i * nt + t, C.fp16_inv);
+    }
+    if (__syncthreads_or(!ok)) {  // a load never arrived: drain the other one in flight, stop
+      if (t == 0) {
+        atomicOr(C.err, ERR_TIMEOUT);
+        if (w + G < nlist) wait_stage(it + 1);
+      }
+      return;
+    }
+    if (t == 0 && w + 2 * G < nlist) issue(w + 2 * G, st, (it + 2) & 3);
+    acc.enter(out, stride, L.case_id, red);
+    if (act) acc.template cell<Q>(C, L, x, y, z, tg, f, eps);
+  }
+  acc.finish(out, stride, red);
 }
 
 // ------------------------------------------------------------------ field export
@@ -1251,8 +1369,30 @@ cudaError_t run_prolong(int Q, int st, Launch L, Ctx C, BlockShape S, const int 
   LSB_QT(Q, st, (LK(k_prolong)(C, S, list, n)));
 }
 cudaError_t run_observables(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, double *out,
-                            int stride, float eps) {
+                            int stride, float eps, const CUtensorMap *tmaps, const CUtensorMap *tmaps_tag) {
+  if (tmaps) {
+    const size_t smem = tma_smem_bytes(Q, st, L.block);
+    LSB_QT(Q, st,
+           (launcher(k_observables_tma<Q_, T_>, L, smem)(C, S, list, n, out, stride, eps, tmaps, tmaps_tag)));
+  }
   LSB_QT(Q, st, (LK(k_observables)(C, S, list, n, out, stride, eps)));
+}
+// Raise the TMA-staged observables kernel's dynamic shared-memory limit (once, outside
+// any capture) and report how many CTAs of nthreads fit on one SM.
+cudaError_t prepare_observables_tma(int Q, int st, int nthreads, int *ctas_per_sm) {
+  const size_t smem = tma_smem_bytes(Q, st, nthreads);
+  cudaError_t e = cudaSuccess;
+  int nb = 0;
+  auto prep = [&](auto kern) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, nthreads, smem);
+  };
+  if (Q == 9) st == 0 ? prep(k_observables_tma<9, float>) : prep(k_observables_tma<9, __half>);
+  else if (Q == 19) st == 0 ? prep(k_observables_tma<19, float>) : prep(k_observables_tma<19, __half>);
+  else if (st == 0) prep(k_observables_tma<27, float>);
+  else e = cudaErrorInvalidValue;
+  *ctas_per_sm = nb;
+  return e;
 }
 cudaError_t run_export(int Q, int st, Launch L, Ctx C, int ld, int field, float *dst) {
   LSB_QT(Q, st, (LK(k_export)(C, ld, field, dst)));
