@@ -92,6 +92,10 @@ struct lsb_grid {
   int2 *d_linkcell = nullptr;
   uint8_t *d_linkdir = nullptr;
   long long link_list_off[MAXL] = {0, 0, 0, 0};
+  // pinned host words the synchronising calls read back into: the error word, then the
+  // observables of every case (allocated at the first use)
+  int *h_err = nullptr;
+  double *h_obs = nullptr;
   int *d_counters = nullptr, *d_err = nullptr, *d_band = nullptr, *d_check = nullptr;
   int4 *d_band_info = nullptr;
   unsigned *d_bar = nullptr;  // grid barrier of the persistent level-set kernel
@@ -703,6 +707,17 @@ lsb_status advance(lsb_grid *g, int l) {
 }
 
 lsb_status regrid(lsb_grid *g, bool initial);
+// Pinned read-back words (one allocation: the error word, then room for the observables).
+lsb_status pin_host(lsb_grid *g) {
+  if (g->h_err) return LSB_OK;
+  const size_t nobs = (size_t)(4 + 2 * g->D) * g->ncase;
+  void *p = nullptr;
+  CU(cudaMallocHost(&p, 16 + sizeof(double) * nobs));
+  g->h_err = static_cast<int *>(p);
+  g->h_obs = reinterpret_cast<double *>(static_cast<char *>(p) + 16);
+  return LSB_OK;
+}
+
 
 // Leaf cell updates of one coarse step: sum over levels of leaf cells x 2^level.
 double updates_per_step(const lsb_grid *g) {
@@ -1507,6 +1522,8 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
   }
   ALLOC(g->d_counters, sizeof(int) * MAXL * NCOUNT);
   ALLOC(g->d_err, sizeof(int));
+  s = pin_host(g);
+  if (s) { g_create_error = g->err; lsb_destroy(g); return s; }
   ALLOC(g->d_bar, 2 * sizeof(unsigned));
   ALLOC(g->d_iface, sizeof(int2) * MAXL * g->list_cap);
   ALLOC(g->d_flip, sizeof(int2) * MAXL * g->list_cap);
@@ -1684,9 +1701,11 @@ lsb_status lsb_refine(lsb_grid *g) {
 
 lsb_status lsb_sync(lsb_grid *g) {
   if (!g) return LSB_EINVAL;
+  TRY(pin_host(g));
+  // the error word comes back with the stream's work: one wait for both
+  CU(cudaMemcpyAsync(g->h_err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
   CU(cudaStreamSynchronize(g->stream));
-  int e = 0;
-  CU(cudaMemcpy(&e, g->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  const int e = *g->h_err;
   g->latched |= e;
   if (g->latched & (ERR_LINK_OVF | ERR_LIST_OVF | ERR_BAND_OVF))
     return fail(g, LSB_ENOMEM, "device work list overflow (flags %d)", g->latched);
@@ -1820,12 +1839,12 @@ lsb_status lsb_observables(lsb_grid *g, double *out_host, size_t n_doubles) {
   Ctx C = make_ctx(g);
   BlockShape S = shape(g);
   TRY(observables_pass(g, C, S, stride));
-  std::vector<double> h((size_t)stride * g->ncase);
-  CU(cudaMemcpyAsync(h.data(), g->d_obs, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g->stream));
+  TRY(pin_host(g));
+  CU(cudaMemcpyAsync(g->h_obs, g->d_obs, sizeof(double) * stride * g->ncase, cudaMemcpyDeviceToHost, g->stream));
   lsb_status s = lsb_sync(g);
   for (int c = 0; c < g->ncase; ++c) {
     double *o = out_host + (size_t)stride * c;
-    const double *v = h.data() + (size_t)stride * c;
+    const double *v = g->h_obs + (size_t)stride * c;
     o[0] = v[0];
     o[1] = v[1];
     o[2] = v[2];
@@ -2202,6 +2221,7 @@ void lsb_destroy(lsb_grid *g) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
+  if (g->h_err) cudaFreeHost(g->h_err);
   delete g;
 }
 
