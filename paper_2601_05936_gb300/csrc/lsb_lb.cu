@@ -993,8 +993,14 @@ __global__ void __launch_bounds__(512, 2) k_observables_tma(Ctx C, BlockShape S,
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  auto issue = [&](int w, int st, int ms) {
-    const int4 bi = __ldg(C.blk_info + __ldg(list + w));
+  // the issuing thread holds the coordinates of the next block it will load, fetched one
+  // load ahead, so an issue waits on no list lookup
+  int4 pre = make_int4(0, 0, 0, 0);
+  auto fetch = [&](int w) {
+    if (w < nlist) pre = __ldg(C.blk_info + __ldg(list + w));
+  };
+  auto issue = [&](int st, int ms) {
+    const int4 bi = pre;
     const LevelDev &L = C.lds[bi.x];
     ObsMeta &m = meta[ms];
     m.ld = bi.x;
@@ -1014,8 +1020,11 @@ __global__ void __launch_bounds__(512, 2) k_observables_tma(Ctx C, BlockShape S,
   };
   const int G = gridDim.x;
   if (threadIdx.x == 0) {
-    if ((int)blockIdx.x < nlist) issue(blockIdx.x, 0, 0);
-    if ((int)blockIdx.x + G < nlist) issue(blockIdx.x + G, 1, 1);
+    fetch(blockIdx.x);
+    if ((int)blockIdx.x < nlist) issue(0, 0);
+    fetch(blockIdx.x + G);
+    if ((int)blockIdx.x + G < nlist) issue(1, 1);
+    fetch(blockIdx.x + 2 * G);
   }
   auto wait_stage = [&](int j) {
     for (unsigned spins = 0; !mbar_try_wait(&bar[j & 1], (j >> 1) & 1);)
@@ -1052,7 +1061,10 @@ __global__ void __launch_bounds__(512, 2) k_observables_tma(Ctx C, BlockShape S,
       }
       return;
     }
-    if (t == 0 && w + 2 * G < nlist) issue(w + 2 * G, st, (it + 2) & 3);
+    if (t == 0 && w + 2 * G < nlist) {
+      issue(st, (it + 2) & 3);
+      fetch(w + 3 * G);
+    }
     acc.enter(out, stride, L.case_id, red);
     if (act) acc.template cell<Q>(C, L, x, y, z, tg, f, eps);
   }
