@@ -510,9 +510,9 @@ lsb_status classify(lsb_grid *g, int l, int init) {
   RUN(8, 0, F.n, nt, run_classify_phase, Q, LN(g, nlist, nt), C, S, fl, F.n, l, init);
   if (!init) RUN(9, 0, 1, 128, run_flip_mark, Q, LN(g, DYN_GRID / 4, 128), C, S, l);
   RUN(9, 0, F.n, nt, run_classify_links, Q, LN(g, nlist, nt), C, S, fl, F.n, l, init);
-  RUN(10, 0, F.n, 128, run_band, Q, LN(g, (F.n + 127) / 128, 128), C, S, fl, F.n, l);
-  RUN(11, 0, 1, 128, run_geometry, D, LN(g, DYN_GRID, 128), C, l, 0);
-  RUN(11, 0, 1, 128, run_geometry, D, LN(g, DYN_GRID, 128), C, l, 1);
+  RUN(10, 0, F.n, 128, run_band, Q, LN(g, (F.n + 3) / 4, 128), C, S, fl, F.n, l);  // a warp per block
+  // the curvature fit at the interface and the flipped cells, one launch
+  RUN(11, 0, 1, 128, run_geometry, D, LN(g, DYN_GRID, 128), C, l, 2);
   return LSB_OK;
 }
 

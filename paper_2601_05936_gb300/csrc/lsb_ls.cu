@@ -206,46 +206,42 @@ __global__ void k_classify_links(Ctx C, BlockShape S, const int *list, int nlist
 }
 
 // Pass 3: band flag of every active finest block (itself or a 3^D neighbour
-// holds an interface cell); band blocks are listed.
+// holds an interface cell); band blocks are listed.  One warp per block, lane k
+// reading the flags of neighbour k, so the 3^D loads are in flight together.
 template <int Q>
 __global__ void k_band(Ctx C, BlockShape S, const int *list, int nlist, int glevel) {
   LSB_GRID_WAIT();
   constexpr int D = Lat<Q>::D;
-  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nlist; w += gridDim.x * blockDim.x) {
+  constexpr int NN = D == 3 ? 27 : 9;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int w = blockIdx.x * wpb + (threadIdx.x >> 5); w < nlist; w += gridDim.x * wpb) {
     const int gb = list[w];
     const LevelDev &L = C.lds[C.blk_ld[gb]];
-    const int lb = gb - L.block_off;
-    const int b[3] = {lb % L.nb[0], (lb / L.nb[0]) % L.nb[1], lb / (L.nb[0] * L.nb[1])};
-    bool band = false;
-    for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); ++dz)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          int nb3[3] = {b[0] + dx, b[1] + dy, b[2] + dz};
-          const int d3[3] = {dx, dy, dz};
-          bool ok = true;
-          for (int a = 0; a < D; ++a) {
-            if (nb3[a] < 0 || nb3[a] >= L.nb[a]) {
-              if (L.per[a]) nb3[a] = (nb3[a] + L.nb[a]) % L.nb[a];
-              else ok = false;
-            }
-            (void)d3;
-          }
-          if (!ok) continue;
-          int nbid = L.block_off + nb3[0] + L.nb[0] * (nb3[1] + L.nb[1] * nb3[2]);
-          if (C.bflag[nbid] & BF_IFACE) band = true;
+    bool hot = false;
+    if (lane < NN) {
+      const int lb = gb - L.block_off;
+      int nb3[3] = {lb % L.nb[0] + lane % 3 - 1, (lb / L.nb[0]) % L.nb[1] + (lane / 3) % 3 - 1,
+                    lb / (L.nb[0] * L.nb[1]) + (D == 3 ? lane / 9 - 1 : 0)};
+      bool ok = true;
+      for (int a = 0; a < D; ++a) {
+        if (nb3[a] < 0 || nb3[a] >= L.nb[a]) {
+          if (L.per[a]) nb3[a] = (nb3[a] + L.nb[a]) % L.nb[a];
+          else ok = false;
         }
-    if (band && C.bstat[gb] == BLK_LEAF) {
+      }
+      if (ok) hot = (C.bflag[L.block_off + nb3[0] + L.nb[0] * (nb3[1] + L.nb[1] * nb3[2])] & BF_IFACE) != 0;
+    }
+    const bool band = __any_sync(0xffffffffu, hot);
+    if (lane == 0 && band && C.bstat[gb] == BLK_LEAF) {
       C.bflag[gb] = C.bflag[gb] | BF_BAND;
-      // one atomic per group of lanes that list a block together
-      cooperative_groups::coalesced_group grp = cooperative_groups::coalesced_threads();
-      int e0 = 0;
-      if (grp.thread_rank() == 0) e0 = atomicAdd(&C.counters[glevel * NCOUNT + 3], (int)grp.size());
-      const int e = grp.shfl(e0, 0) + (int)grp.thread_rank();
+      const int e = atomicAdd(&C.counters[glevel * NCOUNT + 3], 1);
       if (e < C.band_cap) {
         C.band_list[(long long)glevel * C.band_cap + e] = gb;
         C.band_info[(long long)glevel * C.band_cap + e] = C.blk_info[gb];
+      } else {
+        atomicOr(C.err, ERR_BAND_OVF);
       }
-      else atomicOr(C.err, ERR_BAND_OVF);
     }
   }
 }
@@ -256,13 +252,17 @@ __global__ void k_band(Ctx C, BlockShape S, const int *list, int nlist, int glev
 // H_ab = sum(o_a o_b phi)/sum(o_a^2 o_b^2) (a != b); the constant and pure
 // quadratic coefficients solve the 1 + D even normal equations in closed form.
 // n = g/|g|, kappa = (|g|^2 tr H - g.H.g)/|g|^3.
+// which: 0 the interface list, 1 the flip list, 2 both (one index space, interface
+// cells first; a cell on both lists gets the same values twice).
 template <int D>
 __global__ void k_geometry(Ctx C, int glevel, int which) {
   LSB_GRID_WAIT();
-  const int n = min(C.counters[glevel * NCOUNT + (which ? 2 : 1)], (int)C.list_cap);
-  const int2 *lst = (which ? C.flip_list : C.iface_list) + (long long)glevel * C.list_cap;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    const int2 it = lst[e];
+  const int ni = which == 1 ? 0 : min(C.counters[glevel * NCOUNT + 1], (int)C.list_cap);
+  const int nf = which == 0 ? 0 : min(C.counters[glevel * NCOUNT + 2], (int)C.list_cap);
+  const int2 *li = C.iface_list + (long long)glevel * C.list_cap;
+  const int2 *lf = C.flip_list + (long long)glevel * C.list_cap;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ni + nf; e += gridDim.x * blockDim.x) {
+    const int2 it = e < ni ? li[e] : lf[e - ni];
     const LevelDev &L = C.lds[it.x];
     const long long c = it.y;
     int x, y, z;
