@@ -531,14 +531,21 @@ __global__ void k_ext_iter(Ctx C, BlockShape S, int glevel, const float *uin, fl
   d_ext_iter<D>(C, S, glevel, uin, uout, mode);
 }
 
+#ifndef LSB_EXT_MINB
+#define LSB_EXT_MINB 3  // CTAs of 512 threads per SM the sweep is built for
+#endif
+#ifndef LSB_EXT_U
+#define LSB_EXT_U 1  // band blocks a thread carries at once
+#endif
 // The sweeps after the first (mode 3 of d_ext_iter: the same arithmetic in the same order)
 // as a lean kernel of its own.  Its chain of dependent loads (band list, block coordinates,
 // plan, values, upwind neighbours) is latency-bound and the band holds only a few blocks
-// per resident CTA, so each thread carries two blocks at once with their loads interleaved.
+// per resident CTA: one cell per thread (LSB_EXT_U blocks at once) at three CTAs per SM
+// measured faster than two blocks per thread at two CTAs per SM (more CTAs in flight).
 // MIRROR: the forward step's stage arrays equal ut0 outside the band, so every
 // upwind neighbour reads uin (no band bit of the plan consulted).
 template <int D, bool MIRROR = false>
-__global__ void __launch_bounds__(512, 2) k_ext_plan(Ctx C, BlockShape S, int glevel, const float *__restrict__ uin,
+__global__ void __launch_bounds__(512, LSB_EXT_MINB) k_ext_plan(Ctx C, BlockShape S, int glevel, const float *__restrict__ uin,
                                                      float *__restrict__ uout) {
   LSB_GRID_WAIT();
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
@@ -547,7 +554,7 @@ __global__ void __launch_bounds__(512, 2) k_ext_plan(Ctx C, BlockShape S, int gl
   const int G = gridDim.x;
   // each thread takes its cell in two band blocks per pass, with both blocks' dependent
   // loads (list entry, block coordinates, plan, neighbours) issued side by side
-  constexpr int U = 2;
+  constexpr int U = LSB_EXT_U;
   for (int w0 = blockIdx.x; w0 < nl; w0 += U * G) {
     int gb[U];
 #pragma unroll
