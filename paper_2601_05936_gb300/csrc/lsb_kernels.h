@@ -16,7 +16,8 @@ constexpr int kMaxDevices = 64;
 struct Launch {
   int grid, block;
   cudaStream_t stream;
-  int pdl = 0;  // programmatic dependent launch: may overlap the previous kernel's tail
+  int pdl = 0;   // programmatic dependent launch: may overlap the previous kernel's tail
+  int prio = 0;  // launch priority (0: the stream's; lower numbers are scheduled first)
 };
 
 // Launch kern on L's grid and stream.  With L.pdl the launch carries the
@@ -25,20 +26,27 @@ struct Launch {
 // memory) in LSB_GRID_WAIT at its start.
 template <typename... P, typename... A>
 inline void lsb_launch(void (*kern)(P...), const Launch &L, size_t smem, A... args) {
-  if (!L.pdl) {
+  if (!L.pdl && !L.prio) {
     kern<<<L.grid, L.block, smem, L.stream>>>(args...);
     return;
   }
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute at[2];
+  unsigned na = 0;
+  if (L.pdl) {
+    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[na++].val.programmaticStreamSerializationAllowed = 1;
+  }
+  if (L.prio) {
+    at[na].id = cudaLaunchAttributePriority;
+    at[na++].val.priority = L.prio;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)L.grid);
   cfg.blockDim = dim3((unsigned)L.block);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = L.stream;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = na;
   cudaLaunchKernelEx(&cfg, kern, args...);
 }
 template <typename K>
