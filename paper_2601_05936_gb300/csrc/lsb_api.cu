@@ -603,13 +603,39 @@ lsb_status restore(lsb_grid *g, const float *src) {
   return LSB_OK;
 }
 
-// One advance of global level l (recursive over finer levels).
 // The side stream's collide gets 1 / LSB_SIDE_DIV of the resident CTAs: all of them measured
 // fastest (0.8179 ms per step against 0.8257 at half and 0.94 at a quarter), the main
 // stream's kernels taking the slots it frees first by their priority.
 #ifndef LSB_SIDE_DIV
 #define LSB_SIDE_DIV 1
 #endif
+
+// Restriction and collide-and-stream of level l on its side stream, after the main
+// stream's work so far.
+lsb_status coarse_side(lsb_grid *g, int l) {
+  const BlockShape S = shape(g);
+  const Ctx C = make_ctx(g);
+  const int Q = g->Q, st = g->storage, nt = g->nthreads;
+  if (!g->side[l]) {
+    CU(cudaStreamCreateWithFlags(&g->side[l], cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&g->ev_fork[l], cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&g->ev_join[l], cudaEventDisableTiming));
+  }
+  CU(cudaEventRecord(g->ev_fork[l], g->stream));
+  CU(cudaStreamWaitEvent(g->side[l], g->ev_fork[l], 0));
+  const CellList &rc = g->rl_cells[l];
+  RUN(2, 0, rc.n, 128, run_restrict_cells, Q, st, (Launch{(rc.n + 127) / 128, 128, g->side[l]}), C,
+      (const int2 *)rc.d, rc.n);
+  const double cs_bytes = 2.0 * g->Q * (g->storage == LSB_FP32 ? 4 : 2) * g->leaf_cells[l];
+  const int grid = std::min(g->cs[l].n, std::max(1, g->tma_grid / LSB_SIDE_DIV));
+  const CUtensorMap *tm = (const CUtensorMap *)g->d_tmaps;
+  RUN(collide_kid(l), cs_bytes, g->cs[l].n, nt, run_collide_stream_tma, Q, st, Launch{grid, nt, g->side[l]}, C, S,
+      (const int *)g->cs[l].d, g->cs[l].n, tm, g->tma_tags ? tm + 2 * g->lds.size() : nullptr);
+  CU(cudaEventRecord(g->ev_join[l], g->side[l]));
+  return LSB_OK;
+}
+
+// One advance of global level l (recursive over finer levels).
 lsb_status advance(lsb_grid *g, int l) {
   BlockShape S = shape(g);
   const int nt = g->nthreads;
@@ -626,15 +652,7 @@ lsb_status advance(lsb_grid *g, int l) {
                     g->d_tmaps && !g->no_tma && !g->tma_a;
   const CellList &rc = g->rl_cells[l];
   if (fork) {
-    if (!g->side[l]) {
-      CU(cudaStreamCreateWithFlags(&g->side[l], cudaStreamNonBlocking));
-      CU(cudaEventCreateWithFlags(&g->ev_fork[l], cudaEventDisableTiming));
-      CU(cudaEventCreateWithFlags(&g->ev_join[l], cudaEventDisableTiming));
-    }
-    CU(cudaEventRecord(g->ev_fork[l], g->stream));
-    CU(cudaStreamWaitEvent(g->side[l], g->ev_fork[l], 0));
-    RUN(2, 0, rc.n, 128, run_restrict_cells, Q, st, (Launch{(rc.n + 127) / 128, 128, g->side[l]}), C,
-        (const int2 *)rc.d, rc.n);
+    TRY(coarse_side(g, l));
   } else {
     RUN(2, 0, rc.n, 128, run_restrict_cells, Q, st, LN(g, (rc.n + 127) / 128, 128), C, (const int2 *)rc.d, rc.n);
   }
@@ -648,11 +666,7 @@ lsb_status advance(lsb_grid *g, int l) {
   }
   const double cs_bytes = 2.0 * g->Q * (g->storage == LSB_FP32 ? 4 : 2) * g->leaf_cells[l];
   if (fork) {
-    const int grid = std::min(g->cs[l].n, std::max(1, g->tma_grid / LSB_SIDE_DIV));
-    const CUtensorMap *tm = (const CUtensorMap *)g->d_tmaps;
-    RUN(collide_kid(l), cs_bytes, g->cs[l].n, nt, run_collide_stream_tma, Q, st, Launch{grid, nt, g->side[l]}, C, S,
-        (const int *)g->cs[l].d, g->cs[l].n, tm, g->tma_tags ? tm + 2 * g->lds.size() : nullptr);
-    CU(cudaEventRecord(g->ev_join[l], g->side[l]));
+    // on the side stream (coarse_side, above)
   } else if (g->d_tmaps && !g->no_tma) {
     const int grid = std::min(g->cs[l].n, g->tma_grid);
     const CUtensorMap *tm = (const CUtensorMap *)g->d_tmaps;
