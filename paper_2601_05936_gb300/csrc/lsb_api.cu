@@ -145,6 +145,7 @@ struct lsb_grid {
   cudaStream_t side2[MAXL] = {};
   cudaEvent_t ev_free[MAXL] = {}, ev_fill[MAXL] = {};
   int early_fill = -1;  // level whose next ghost ring fills right after its collide
+  bool counters_turned[MAXL] = {};  // the level's classification counters already started
   uint64_t gnodes[2][2] = {};
   // adjoint of the frozen-interface step: recording and reverse sweep
   int rec_on = 0, rec_every = 0;
@@ -503,9 +504,14 @@ lsb_status classify(lsb_grid *g, int l, int init) {
   if (!has_finest(g, l)) return LSB_OK;
   // the band list the previous classification left is the set of blocks whose phases can
   // change (phi moves on band cells only): keep its length, then clear the counters
+  // (the first extension sweep of this sub-step did it already; the phase pass clears the
+  // band count)
   int *cnt = g->d_counters + l * NCOUNT;
-  CU(cudaMemcpyAsync(cnt + 5, cnt + 3, sizeof(int), cudaMemcpyDeviceToDevice, g->stream));
-  CU(cudaMemsetAsync(cnt, 0, sizeof(int) * 5, g->stream));
+  if (init || !g->counters_turned[l]) {
+    CU(cudaMemcpyAsync(cnt + 5, cnt + 3, sizeof(int), cudaMemcpyDeviceToDevice, g->stream));
+    CU(cudaMemsetAsync(cnt, 0, sizeof(int) * 5, g->stream));
+  }
+  g->counters_turned[l] = false;
   Ctx C = make_ctx(g);
   BlockShape S = shape(g);
   WorkList &F = g->finest[l];
@@ -559,7 +565,10 @@ lsb_status levelset(lsb_grid *g, int l) {
   const float *uin = g->d_ut[0];
   for (int it = 0; it < g->n_ext; ++it) {
     float *uout = g->d_ut[1 + (it & 1)];
-    if (it == 0) RUN(13, 0, nb, nt, run_ext_first, D, LN(g, nb, nt), C, S, l, uin, uout);
+    if (it == 0) {
+      RUN(13, 0, nb, nt, run_ext_first, D, LN(g, nb, nt), C, S, l, uin, uout, 1);
+      g->counters_turned[l] = true;  // the classification of this sub-step finds them started
+    }
     else RUN(13, 0, nb, nt, run_ext_sweep_mirror, D, LN(g, nb, nt), C, S, l, uin, uout);
     uin = uout;
   }

@@ -103,7 +103,8 @@ cudaError_t run_adv_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int 
 cudaError_t run_reinit_prep(int Q, Launch L, Ctx C, BlockShape S, int glevel);
 cudaError_t run_reinit_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage);
 // forward passes on mirrored stage arrays (no band lookups; see lsb_ls.cu)
-cudaError_t run_ext_first(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout);
+cudaError_t run_ext_first(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout,
+                          int turn);
 cudaError_t run_ext_sweep_mirror(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout);
 cudaError_t run_adv_mirror(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage, const float *ufin);
 cudaError_t run_reinit_mirror(int Q, Launch L, Ctx C, BlockShape S, int glevel, int stage, int prep);

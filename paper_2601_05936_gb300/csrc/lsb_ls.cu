@@ -36,6 +36,8 @@ __global__ void k_classify_phase(Ctx C, BlockShape S, const int *list, int nlist
   if (!init) {
     nlist = min(C.counters[glevel * NCOUNT + 5], C.band_cap);
     list = C.band_list + (long long)glevel * C.band_cap;
+    // the band count starts again for the band pass (no pass before it reads it)
+    if (blockIdx.x == 0 && threadIdx.x == 0) C.counters[glevel * NCOUNT + 3] = 0;
   }
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     const int gb = list[w];
@@ -869,10 +871,18 @@ __device__ __forceinline__ void gather7m(const LevelDev &L, const float *__restr
 // First extension sweep of a step (mode 2 of d_ext_iter): sweep from uin = ut0 and
 // store the plan (S(phi) n, upwind sides, interface and box-boundary bits).
 template <int D>
+// turn: also start the classification's counters (the band count into the previous-band
+// slot, the other slots but the band count to zero; no pass between here and the
+// classification reads them).
 __global__ void __launch_bounds__(512, LSB_LS_MINB) k_ext_first(Ctx C, BlockShape S, int glevel, const float *__restrict__ uin,
-                            float *__restrict__ uout) {
+                            float *__restrict__ uout, int turn) {
   LSB_GRID_WAIT();
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
+  if (turn && blockIdx.x == 0 && threadIdx.x == 0) {
+    int *cnt = C.counters + glevel * NCOUNT;
+    cnt[5] = cnt[3];
+    cnt[0] = cnt[1] = cnt[2] = cnt[4] = 0;
+  }
   const long long NF = C.nfine;
   // the next entry of the band list is loaded while this one is processed
   const int4 *info = C.band_info + (long long)glevel * C.band_cap;
@@ -1364,8 +1374,9 @@ cudaError_t run_ext_iter(int D, Launch L, Ctx C, BlockShape S, int glevel, const
 cudaError_t run_adv_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage) {
   LDP(k_adv_stage, C, S, glevel, stage);
 }
-cudaError_t run_ext_first(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout) {
-  LDP(k_ext_first, C, S, glevel, uin, uout);
+cudaError_t run_ext_first(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout,
+                          int turn) {
+  LDP(k_ext_first, C, S, glevel, uin, uout, turn);
 }
 cudaError_t run_ext_sweep_mirror(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout) {
   if (D == 2)
