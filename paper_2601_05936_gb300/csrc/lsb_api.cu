@@ -96,6 +96,7 @@ struct lsb_grid {
   // observables of every case (allocated at the first use)
   int *h_err = nullptr;
   double *h_obs = nullptr;
+  int *d_work = nullptr;  // per level: the collide-and-stream's block counters (next, finished)
   int *d_counters = nullptr, *d_err = nullptr, *d_band = nullptr, *d_check = nullptr;
   int4 *d_band_info = nullptr;
   unsigned *d_bar = nullptr;  // grid barrier of the persistent level-set kernel
@@ -619,6 +620,13 @@ lsb_status restore(lsb_grid *g, const float *src) {
 #define LSB_SIDE_DIV 1
 #endif
 
+// The collide-and-stream's block counters of level l (two words, zero between launches;
+// one launch of a level at a time), or none (static assignment).
+#ifndef LSB_DYN
+#define LSB_DYN 1
+#endif
+int *work_counters(lsb_grid *g, int l) { return LSB_DYN && g->d_work ? g->d_work + 2 * l : nullptr; }
+
 // Restriction and collide-and-stream of level l on its side stream, after the main
 // stream's work so far.
 lsb_status coarse_side(lsb_grid *g, int l) {
@@ -639,7 +647,7 @@ lsb_status coarse_side(lsb_grid *g, int l) {
   const int grid = std::min(g->cs[l].n, std::max(1, g->tma_grid / LSB_SIDE_DIV));
   const CUtensorMap *tm = (const CUtensorMap *)g->d_tmaps;
   RUN(collide_kid(l), cs_bytes, g->cs[l].n, nt, run_collide_stream_tma, Q, st, Launch{grid, nt, g->side[l]}, C, S,
-      (const int *)g->cs[l].d, g->cs[l].n, tm, g->tma_tags ? tm + 2 * g->lds.size() : nullptr);
+      (const int *)g->cs[l].d, g->cs[l].n, tm, g->tma_tags ? tm + 2 * g->lds.size() : nullptr, work_counters(g, l));
   CU(cudaEventRecord(g->ev_join[l], g->side[l]));
   return LSB_OK;
 }
@@ -679,8 +687,9 @@ lsb_status advance(lsb_grid *g, int l) {
   } else if (g->d_tmaps && !g->no_tma) {
     const int grid = std::min(g->cs[l].n, g->tma_grid);
     const CUtensorMap *tm = (const CUtensorMap *)g->d_tmaps;
-    RUN(collide_kid(l), cs_bytes, g->cs[l].n, nt, run_collide_stream_tma, Q, st, LN(g, grid, nt), C, S, (const int *)g->cs[l].d,
-        g->cs[l].n, g->tma_a ? g->tma_a : tm, g->tma_tags ? tm + 2 * g->lds.size() : nullptr);
+    RUN(collide_kid(l), cs_bytes, g->cs[l].n, nt, run_collide_stream_tma, Q, st, LN(g, grid, nt), C, S,
+        (const int *)g->cs[l].d, g->cs[l].n, g->tma_a ? g->tma_a : tm, g->tma_tags ? tm + 2 * g->lds.size() : nullptr,
+        work_counters(g, l));
   } else {
     RUN(collide_kid(l), cs_bytes, g->cs[l].n, nt, run_collide_stream, Q, st, LN(g, g->cs[l].n, nt), C, S, (const int *)g->cs[l].d,
         g->cs[l].n);
@@ -1559,6 +1568,7 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
   }
   ALLOC(g->d_counters, sizeof(int) * MAXL * NCOUNT);
   ALLOC(g->d_err, sizeof(int));
+  ALLOC(g->d_work, sizeof(int) * 2 * MAXL);
   s = pin_host(g);
   if (s) { g_create_error = g->err; lsb_destroy(g); return s; }
   {
@@ -1596,6 +1606,7 @@ lsb_status lsb_create_grid(int n_cases, const lsb_grid_desc *descs, const lsb_pa
       cuerr(cudaMemset(g->d_tag, 0, g->ncell_total), "tag") ||
       cuerr(cudaMemset(g->d_bflag, 0, g->nblock_total), "bflag") ||
       cuerr(cudaMemset(g->d_err, 0, sizeof(int)), "err") ||
+      cuerr(cudaMemset(g->d_work, 0, sizeof(int) * 2 * MAXL), "work") ||
       cuerr(cudaMemset(g->d_bar, 0, 2 * sizeof(unsigned)), "barrier") ||
       cuerr(cudaMemset(g->d_counters, 0, sizeof(int) * MAXL * NCOUNT), "counters") ||
       cuerr(cudaMemset(g->d_cmask, 0, 4 * nf), "cmask") ||

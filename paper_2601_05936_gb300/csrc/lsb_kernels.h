@@ -67,8 +67,9 @@ inline Launch with_grid(Launch L, int grid) {
 // lsb_lb.cu: lattice Boltzmann, interface bounce-back, level transfers
 cudaError_t run_init(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n);
 cudaError_t run_collide_stream(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n);
+// work: nullptr, or two zeroed counters of this launch's own (dynamic block taking)
 cudaError_t run_collide_stream_tma(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n,
-                                   const CUtensorMap *tmaps, const CUtensorMap *tmaps_tag);
+                                   const CUtensorMap *tmaps, const CUtensorMap *tmaps_tag, int *work);
 size_t tma_smem_bytes(int Q, int st, int nthreads);
 cudaError_t prepare_collide_stream_tma(int Q, int st, int nthreads, int *ctas_per_sm);
 cudaError_t run_interface_bc(int Q, int st, Launch L, Ctx C, int glevel);

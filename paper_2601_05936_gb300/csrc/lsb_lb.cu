@@ -371,9 +371,14 @@ struct BlockMeta {
 };
 
 template <int Q, typename T>
+// work (optional): two counters, zero at launch.  Then thread 0 takes each next list
+// index from work[0] instead of walking blockIdx.x + k gridDim.x, so that CTAs that become
+// resident late (beside another kernel) take fewer blocks; the last CTA to finish
+// (work[1]) sets both back to zero for the next launch.
 __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape S, const int *__restrict__ list,
                                                                int nlist, const CUtensorMap *__restrict__ tmaps,
-                                                               const CUtensorMap *__restrict__ tmaps_tag) {
+                                                               const CUtensorMap *__restrict__ tmaps_tag,
+                                                               int *work) {
   LSB_GRID_WAIT();
   using LT = Lat<Q>;
   constexpr int D = LT::D;
@@ -428,18 +433,40 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
     }
   };
   const int G = gridDim.x;
+  // the list index of this CTA's k-th block; meta[slot].gb = -1 marks an iteration with none
+  auto take = [&](int k) { return work ? atomicAdd(work, 1) : (int)blockIdx.x + k * G; };
+  __shared__ int more;  // thread 0: the list may still hold blocks for this CTA
+  auto issue_next = [&](int k, int st, int ms) {
+    const int w = more ? take(k) : nlist;
+    if (w < nlist) {
+      issue(w, st, ms);
+    } else {
+      more = 0;
+      meta[ms].gb = -1;
+    }
+  };
   if (threadIdx.x == 0) {
-    if ((int)blockIdx.x < nlist) issue(blockIdx.x, 0, 0);
-    if ((int)blockIdx.x + G < nlist) issue(blockIdx.x + G, 1, 1);
+    more = 1;
+    issue_next(0, 0, 0);
+    issue_next(1, 1, 1);
   }
+  __syncthreads();
   // bounded wait for the load of iteration j (stage j & 1, its (j >> 1)-th use)
   auto wait_stage = [&](int j) {
     for (unsigned spins = 0; !mbar_try_wait(&bar[j & 1], (j >> 1) & 1);)
       if (++spins > kWaitLimit) return false;
     return true;
   };
-  int it = 0;
-  for (int w = blockIdx.x; w < nlist; w += G, ++it) {
+  // the last CTA out resets the work counters (every CTA passes here once)
+  auto finish = [&]() {
+    if (work && threadIdx.x == 0 && atomicAdd(work + 1, 1) == (int)gridDim.x - 1) {
+      work[0] = 0;
+      work[1] = 0;
+    }
+  };
+  for (int it = 0;; ++it) {
+    // set by thread 0 two iterations ago, before a barrier every thread has passed since
+    if (meta[it & 3].gb < 0) break;
     const int st = it & 1;
     const bool ok = wait_stage(it);
     const BlockMeta &m = meta[it & 3];
@@ -471,11 +498,12 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
     if (__syncthreads_or(!ok)) {  // a load never arrived: drain the other one in flight, stop
       if (t == 0) {
         atomicOr(C.err, ERR_TIMEOUT);
-        if (w + G < nlist) wait_stage(it + 1);
+        if (meta[(it + 1) & 3].gb >= 0) wait_stage(it + 1);
       }
+      finish();
       return;
     }
-    if (t == 0 && w + 2 * G < nlist) issue(w + 2 * G, st, (it + 2) & 3);
+    if (t == 0) issue_next(it + 2, st, (it + 2) & 3);
     do {
       if (!act) break;
 
@@ -555,6 +583,7 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
       else push(std::false_type{});
     } while (false);
   }
+  finish();
 }
 
 // ------------------------------------------------------------------ interface post-pass
@@ -1366,10 +1395,10 @@ cudaError_t prepare_collide_stream_tma(int Q, int st, int nthreads, int *ctas_pe
   return e;
 }
 cudaError_t run_collide_stream_tma(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n,
-                                   const CUtensorMap *tmaps, const CUtensorMap *tmaps_tag) {
+                                   const CUtensorMap *tmaps, const CUtensorMap *tmaps_tag, int *work) {
   const size_t smem = tma_smem_bytes(Q, st, L.block);
   LSB_QT(Q, st,
-         (launcher(k_collide_stream_tma<Q_, T_>, L, smem)(C, S, list, n, tmaps, tmaps_tag)));
+         (launcher(k_collide_stream_tma<Q_, T_>, L, smem)(C, S, list, n, tmaps, tmaps_tag, work)));
 }
 cudaError_t run_interface_bc(int Q, int st, Launch L, Ctx C, int glevel) {
   LSB_QT(Q, st, (LK(k_interface_bc)(C, glevel)));
