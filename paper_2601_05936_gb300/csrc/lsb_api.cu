@@ -144,7 +144,7 @@ struct lsb_grid {
   // per level: its second sub-step's ghost ring, filled beside the first sub-step's
   // interface, level-set, classification and refill passes
   cudaStream_t side2[MAXL] = {};
-  cudaEvent_t ev_free[MAXL] = {}, ev_fill[MAXL] = {};
+  cudaEvent_t ev_free[MAXL] = {}, ev_fill[MAXL] = {}, ev_ring0[MAXL] = {}, ev_ring0_done[MAXL] = {};
   int early_fill = -1;  // level whose next ghost ring fills right after its collide
   bool counters_turned[MAXL] = {};  // the level's classification counters already started
   uint64_t gnodes[2][2] = {};
@@ -652,6 +652,12 @@ lsb_status coarse_side(lsb_grid *g, int l) {
   return LSB_OK;
 }
 
+// The first sub-step's ghost ring of the deepest level on its side stream beside that
+// sub-step's collide (which takes its blocks dynamically, so the ring's CTAs cost it only
+// their share): 0.803 -> 0.799 ms per step.
+#ifndef LSB_RING0_SIDE
+#define LSB_RING0_SIDE 1
+#endif
 // One advance of global level l (recursive over finer levels).
 lsb_status advance(lsb_grid *g, int l) {
   BlockShape S = shape(g);
@@ -700,13 +706,9 @@ lsb_status advance(lsb_grid *g, int l) {
     // reading it, and the interface, level-set, classification and refill passes that
     // follow touch only B); it reads the coarser level's A and B buffers, so it also waits
     // for that level's collide on side[l - 1]
-    g->early_fill = -1;
-    if (!g->side2[l]) {
-      CU(cudaStreamCreateWithFlags(&g->side2[l], cudaStreamNonBlocking));
-      CU(cudaEventCreateWithFlags(&g->ev_free[l], cudaEventDisableTiming));
-      CU(cudaEventCreateWithFlags(&g->ev_fill[l], cudaEventDisableTiming));
-    }
+    g->early_fill = -1;  // (the side stream and its events are made by the coarser level)
     CU(cudaEventRecord(g->ev_free[l], g->stream));
+    if (LSB_RING0_SIDE) CU(cudaStreamWaitEvent(g->stream, g->ev_ring0_done[l], 0));  // this sub-step's ring
     CU(cudaStreamWaitEvent(g->side2[l], g->ev_free[l], 0));
     CU(cudaStreamWaitEvent(g->side2[l], g->ev_join[l - 1], 0));
     Ctx C2 = make_ctx(g);
@@ -728,11 +730,28 @@ lsb_status advance(lsb_grid *g, int l) {
   }
   if (call >= 0 && l + 1 < g->Lmax) TRY(copy_level(g, g->tape_new[call], (const float *)g->d_buf[1 - g->par[l]], l));
   if (l + 1 < g->Lmax) {
-    // with the next level the deepest (no sub-steps below it read its A buffer), its second
-    // ghost ring fills beside its first sub-step
+    // with the next level the deepest (no sub-steps below it read its buffers), its ghost
+    // rings fill on a side stream: the first beside its first sub-step's collide, the
+    // second beside that sub-step's interface, level-set, classification and refill passes
     const bool early = fork && l + 2 == g->Lmax;
+    if (early && !g->side2[l + 1]) {
+      CU(cudaStreamCreateWithFlags(&g->side2[l + 1], cudaStreamNonBlocking));
+      for (cudaEvent_t *e : {&g->ev_free[l + 1], &g->ev_fill[l + 1], &g->ev_ring0[l + 1], &g->ev_ring0_done[l + 1]})
+        CU(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
     for (int sub = 0; sub < 2; ++sub) {
-      if (sub == 1 && early) {
+      if (sub == 0 && early && LSB_RING0_SIDE) {
+        // the first sub-step's ring (theta = 0) reads only the coarser level's A buffer at
+        // leaf cells and writes pushes into the finer B buffer that no leaf pushes to: it
+        // runs beside that sub-step's collide-and-stream, joined before its interface pass
+        CU(cudaEventRecord(g->ev_ring0[l + 1], g->stream));
+        CU(cudaStreamWaitEvent(g->side2[l + 1], g->ev_ring0[l + 1], 0));
+        C = make_ctx(g);
+        const CellList &gc = g->ghost_cells[l + 1];
+        RUN(3, 0, gc.n, 128, run_ghost_cells, Q, st, (Launch{(gc.n + 127) / 128, 128, g->side2[l + 1]}), C,
+            (const int2 *)gc.d, gc.n, 0.0f);
+        CU(cudaEventRecord(g->ev_ring0_done[l + 1], g->side2[l + 1]));
+      } else if (sub == 1 && early) {
         CU(cudaStreamWaitEvent(g->stream, g->ev_fill[l + 1], 0));  // after the coarse collide, too
       } else {
         if (sub == 1 && fork) CU(cudaStreamWaitEvent(g->stream, g->ev_join[l], 0));  // theta = 1/2 reads B
@@ -2254,6 +2273,8 @@ void lsb_destroy(lsb_grid *g) {
       cudaStreamDestroy(g->side2[l]);
       cudaEventDestroy(g->ev_free[l]);
       cudaEventDestroy(g->ev_fill[l]);
+      if (g->ev_ring0[l]) cudaEventDestroy(g->ev_ring0[l]);
+      if (g->ev_ring0_done[l]) cudaEventDestroy(g->ev_ring0_done[l]);
     }
     if (g->side[l]) {
       cudaStreamSynchronize(g->side[l]);
