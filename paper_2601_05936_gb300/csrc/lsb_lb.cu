@@ -435,18 +435,20 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
   const int G = gridDim.x;
   // the list index of this CTA's k-th block; meta[slot].gb = -1 marks an iteration with none
   auto take = [&](int k) { return work ? atomicAdd(work, 1) : (int)blockIdx.x + k * G; };
-  __shared__ int more;  // thread 0: the list may still hold blocks for this CTA
+  // thread 0 takes each index one load ahead of its use (nextw), so that the counter's
+  // round trip overlaps its block's collision instead of delaying the next load
+  int nextw = nlist;
   auto issue_next = [&](int k, int st, int ms) {
-    const int w = more ? take(k) : nlist;
+    const int w = nextw;
     if (w < nlist) {
       issue(w, st, ms);
+      nextw = take(k + 1);
     } else {
-      more = 0;
       meta[ms].gb = -1;
     }
   };
   if (threadIdx.x == 0) {
-    more = 1;
+    nextw = take(0);
     issue_next(0, 0, 0);
     issue_next(1, 1, 1);
   }
