@@ -341,8 +341,8 @@ __global__ void __launch_bounds__(512, (Q == 27 ? 1 : LSB_CS_MINB)) k_collide_st
 // bs0 x bs1 x bs2 cells x Q populations) into one of two stages.  When the
 // level's cell tags have a tensor map too (block rows of whole 16-byte units),
 // the block's tags come with the same stage, so no thread waits on a global
-// load before its collision.  Persistent CTAs walk the work list; one thread
-// issues the loads.  A stage is released as soon as every thread has copied its
+// load before its collision.  Persistent CTAs take blocks from the work list (in
+// turn, or from a counter: see the kernel); one thread issues the loads.  A stage is released as soon as every thread has copied its
 // populations into registers, and is refilled at once with the block after
 // next, so two loads per CTA are in flight while it collides and pushes.  Every
 // thread waits on the stage's mbarrier with an iteration limit; on expiry the

@@ -554,8 +554,8 @@ __global__ void __launch_bounds__(512, LSB_EXT_MINB) k_ext_plan(Ctx C, BlockShap
   const int *lst = C.band_list + (long long)glevel * C.band_cap;
   const long long NF = C.nfine;
   const int G = gridDim.x;
-  // each thread takes its cell in two band blocks per pass, with both blocks' dependent
-  // loads (list entry, block coordinates, plan, neighbours) issued side by side
+  // each thread takes its cell in U band blocks per pass, with the blocks' dependent loads
+  // (list entry, block coordinates, plan, neighbours) issued side by side
   constexpr int U = LSB_EXT_U;
   for (int w0 = blockIdx.x; w0 < nl; w0 += U * G) {
     int gb[U];
