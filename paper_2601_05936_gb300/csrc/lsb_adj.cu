@@ -380,6 +380,10 @@ __global__ void k_adj_links(Ctx C, int glevel, const float *__restrict__ F, floa
       if (sg[k] != 0.0) atomicAdd(grad + (long long)(k / 5) * NG_ADJ + (k % 5), sg[k]);
 }
 
+#ifndef LSB_ADJ_MINB
+#define LSB_ADJ_MINB 2  // CTAs of 512 threads per SM the adjoint collision is built for (64 registers,
+                        // some spills: 0.354 -> 0.371 of measured HBM against one CTA at 128)
+#endif
 // ------------------------------------------------------------------ streaming + collision
 // One thread per leaf cell.  lambda_c (adjoint of the post-collision values) is
 // the transpose of the forward push: population i of x went to x + c_i, to
@@ -390,7 +394,7 @@ __global__ void k_adj_links(Ctx C, int glevel, const float *__restrict__ F, floa
 // Pi_ab = sum c_a c_b (f - feq), with dPi_ab / df_j = c_ja c_jb - c_s^2 d_ab
 // + u_a u_b - c_ja u_b - u_a c_jb.
 template <int Q>
-__global__ void __launch_bounds__(512, 1) k_adj_collide(Ctx C, BlockShape S, const int *__restrict__ list, int nlist,
+__global__ void __launch_bounds__(512, LSB_ADJ_MINB) k_adj_collide(Ctx C, BlockShape S, const int *__restrict__ list, int nlist,
                                                       const float *__restrict__ F, const float *__restrict__ lamN,
                                                       float *__restrict__ lamO, const float *__restrict__ LA,
                                                       double *grad) {
