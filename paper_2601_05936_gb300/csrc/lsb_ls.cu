@@ -848,6 +848,15 @@ __global__ void k_reinit_stage(Ctx C, BlockShape S, int glevel, int stage) {
 #ifndef LSB_LS_MINB
 #define LSB_LS_MINB 3
 #endif
+#ifndef LSB_EF_MINB
+#define LSB_EF_MINB LSB_LS_MINB  // the first extension sweep
+#endif
+#ifndef LSB_ADV_MINB
+#define LSB_ADV_MINB LSB_LS_MINB  // the transport stages
+#endif
+#ifndef LSB_RE_MINB
+#define LSB_RE_MINB LSB_LS_MINB  // the reinitialisation stages
+#endif
 
 // seven values of the stage array along axis a at offsets -3..+3 (clamped or
 // wrapped at the box faces like gather7)
@@ -874,7 +883,7 @@ template <int D>
 // turn: also start the classification's counters (the band count into the previous-band
 // slot, the other slots but the band count to zero; no pass between here and the
 // classification reads them).
-__global__ void __launch_bounds__(512, LSB_LS_MINB) k_ext_first(Ctx C, BlockShape S, int glevel, const float *__restrict__ uin,
+__global__ void __launch_bounds__(512, LSB_EF_MINB) k_ext_first(Ctx C, BlockShape S, int glevel, const float *__restrict__ uin,
                             float *__restrict__ uout, int turn) {
   LSB_GRID_WAIT();
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
@@ -951,7 +960,7 @@ __global__ void __launch_bounds__(512, LSB_LS_MINB) k_ext_first(Ctx C, BlockShap
 // TVD-RK3 transport stage (as d_adv_stage).  Stage 1 takes u~ from the last
 // extension sweep (ufin) and commits it to ut0, ut1 and ut2 at the cell.
 template <int D>
-__global__ void __launch_bounds__(512, LSB_LS_MINB) k_adv_mirror(Ctx C, BlockShape S, int glevel, int stage,
+__global__ void __launch_bounds__(512, LSB_ADV_MINB) k_adv_mirror(Ctx C, BlockShape S, int glevel, int stage,
                                                                  const float *__restrict__ ufin) {
   LSB_GRID_WAIT();
   const int nl = min(C.counters[glevel * NCOUNT + 3], C.band_cap);
@@ -999,7 +1008,7 @@ __global__ void __launch_bounds__(512, LSB_LS_MINB) k_adv_mirror(Ctx C, BlockSha
 // pseudo step) it also finds the frozen cells and S(phi0) as d_reinit_prep does.
 // Frozen cells leave phi as it is and write it into the stage array of stages 1, 2.
 template <int Q>
-__global__ void __launch_bounds__(512, LSB_LS_MINB) k_reinit_mirror(Ctx C, BlockShape S, int glevel, int stage,
+__global__ void __launch_bounds__(512, LSB_RE_MINB) k_reinit_mirror(Ctx C, BlockShape S, int glevel, int stage,
                                                                     int prep) {
   LSB_GRID_WAIT();
   using LT = Lat<Q>;
