@@ -26,7 +26,7 @@ using namespace lsb;
 namespace {
 
 constexpr int MAXL = 4;
-const char *const KNAMES[] = {"k_collide_stream", "k_interface_bc", "k_restrict", "k_ghost", "k_prolong", "k_level_tags", "k_observables", "k_export", "k_classify_phase", "k_classify_links", "k_band", "k_geometry", "k_ext_init", "k_ext_iter", "k_adv_stage", "k_reinit_prep", "k_reinit_stage", "k_refill", "k_sensor", "k_init", "k_collect",
+const char *const KNAMES[] = {"k_collide_stream", "k_interface_bc", "k_restrict", "k_ghost", "k_prolong", "k_level_tags", "k_observables", "k_export", "k_classify_phase", "k_classify_links", "k_post_classify", "k_geometry", "k_ext_init", "k_ext_iter", "k_adv_stage", "k_reinit_prep", "k_reinit_stage", "k_refill", "k_sensor", "k_init", "k_collect",
                                "k_collide_stream_l1", "k_collide_stream_l2", "k_collide_stream_l3", "k_adj_seed",
                                "k_adj_links", "k_adj_collide", "k_adj_macro", "k_adj_geometry",
                                "k_levelset_persistent", "k_lsa", "k_adj_ghost", "k_adj_ghost_apply",
@@ -147,6 +147,7 @@ struct lsb_grid {
   cudaEvent_t ev_free[MAXL] = {}, ev_fill[MAXL] = {}, ev_ring0[MAXL] = {}, ev_ring0_done[MAXL] = {};
   int early_fill = -1;  // level whose next ghost ring fills right after its collide
   bool counters_turned[MAXL] = {};  // the level's classification counters already started
+  bool init_done[MAXL] = {};        // the level's interface u~ came with the interface pass
   uint64_t gnodes[2][2] = {};
   // adjoint of the frozen-interface step: recording and reverse sweep
   int rec_on = 0, rec_every = 0;
@@ -501,7 +502,9 @@ bool has_finest(const lsb_grid *g, int l) {
 }
 
 // Classification of the finest level l: phases, flips, cut links, band; then geometry.
-lsb_status classify(lsb_grid *g, int l, int init) {
+// refill: the step's classification, whose curvature-fit threads also refill the flipped
+// cells (the refill pass of the step); otherwise no refill runs here.
+lsb_status classify(lsb_grid *g, int l, int init, bool refill = false) {
   if (!has_finest(g, l)) return LSB_OK;
   // the band list the previous classification left is the set of blocks whose phases can
   // change (phi moves on band cells only): keep its length, then clear the counters
@@ -524,9 +527,12 @@ lsb_status classify(lsb_grid *g, int l, int init) {
   RUN(8, 0, F.n, nt, run_classify_phase, Q, LN(g, nlist, nt), C, S, fl, F.n, l, init);
   if (!init) RUN(9, 0, 1, 128, run_flip_mark, Q, LN(g, DYN_GRID / 4, 128), C, S, l);
   RUN(9, 0, F.n, nt, run_classify_links, Q, LN(g, nlist, nt), C, S, fl, F.n, l, init);
-  RUN(10, 0, F.n, 128, run_band, Q, LN(g, (F.n + 3) / 4, 128), C, S, fl, F.n, l);  // a warp per block
-  // the curvature fit at the interface and the flipped cells, one launch
-  RUN(11, 0, 1, 128, run_geometry, D, LN(g, DYN_GRID, 128), C, l, 2);
+  // the band pass (a warp per block) and the curvature fit at the interface and the
+  // flipped cells (and the refill of the flipped cells) share a launch
+  const int gband = (F.n + 3) / 4;
+  RUN(10, 0, F.n, 128, run_post_classify, Q, g->storage, LN(g, gband + DYN_GRID, 128), C, fl, F.n, l, gband,
+      refill ? 1 : 0);
+  (void)D;
   return LSB_OK;
 }
 
@@ -562,7 +568,8 @@ lsb_status levelset(lsb_grid *g, int l) {
   // passes on mirrored stage arrays: the first sweep stores the plan, the others reuse
   // it; the first transport stage commits u~; the first reinitialisation stage finds
   // the frozen cells
-  RUN(12, 0, 1, 128, run_ext_init, Q, LN(g, DYN_GRID, 128), C, l);
+  if (!g->init_done[l]) RUN(12, 0, 1, 128, run_ext_init, Q, LN(g, DYN_GRID, 128), C, l);
+  g->init_done[l] = false;
   const float *uin = g->d_ut[0];
   for (int it = 0; it < g->n_ext; ++it) {
     float *uout = g->d_ut[1 + (it & 1)];
@@ -719,12 +726,17 @@ lsb_status advance(lsb_grid *g, int l) {
     CU(cudaEventRecord(g->ev_fill[l], g->side2[l]));
   }
   if (has_finest(g, l)) {
-    RUN(1, 0, 1, 128, run_interface_bc, Q, st, LN(g, DYN_GRID, 128), C, l);
+    if (ls_active_any(g, l) && g->driver == 0) {
+      // the interface pass and the level set's first pass (u~ at the interface cells) share
+      // a launch; the level-set update then starts from its first extension sweep
+      RUN(1, 0, 1, 128, run_iface_init, Q, st, LN(g, 2 * DYN_GRID, 128), C, l, DYN_GRID);
+      g->init_done[l] = true;
+    } else {
+      RUN(1, 0, 1, 128, run_interface_bc, Q, st, LN(g, DYN_GRID, 128), C, l);
+    }
     if (ls_active_any(g, l)) {
       TRY(levelset(g, l));
-      TRY(classify(g, l, 0));
-      C = make_ctx(g);
-      RUN(17, 0, 1, 128, run_refill, Q, st, LN(g, DYN_GRID, 128), C, l);
+      TRY(classify(g, l, 0, true));  // with the refill of the flipped cells
     }  // a frozen level set leaves phases, cut links and geometry as they are
     g->fine_steps[l]++;
   }

@@ -294,7 +294,7 @@ __device__ __forceinline__ const LevelDev &blk_cell(const Ctx &C, const BlockSha
 }
 
 // Cell (x, y, z) of thread t in band-list entry w of global level glevel: the block
-// coordinates come from the copy k_band stores beside the list, so they do not wait
+// coordinates come from the copy the band pass stores beside the list, so they do not wait
 // on the list entry.
 __device__ __forceinline__ const LevelDev &band_cell(const Ctx &C, const BlockShape &S, int glevel, int w, int t,
                                                      int &x, int &y, int &z) {
@@ -358,6 +358,68 @@ __device__ __forceinline__ int clampwrap(const LevelDev &L, int a, int v) {
   int n = L.n[a];
   if (L.per[a]) return (v % n + n) % n;
   return v < 0 ? 0 : (v >= n ? n - 1 : v);
+}
+
+
+// ------------------------------------------------------------------ interface velocity
+// Interface cells: mean of u_I = (1-q) u(x) + q u(x + c_i) over their cut links, on the
+// CTAs [b0, b0 + nb) of the launch (the rest of a shared launch does other work).
+template <int Q>
+__device__ __forceinline__ void d_ext_init(const Ctx &C, int glevel, int b0, int nb) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  const int n = min(C.counters[glevel * NCOUNT + 1], (int)C.list_cap);
+  const int2 *lst = C.iface_list + (long long)glevel * C.list_cap;
+  for (int e = ((int)blockIdx.x - b0) * blockDim.x + threadIdx.x; e < n; e += nb * blockDim.x) {
+    const int2 it = lst[e];
+    const LevelDev &L = C.lds[it.x];
+    if (!L.ls_active) continue;  // frozen level set in this case
+    const long long c = it.y;
+    int x, y, z;
+    cell_xyz(L, c, x, y, z);
+    const long long fo = L.fine_off, NF = C.nfine;
+    const uint32_t m = C.cmask[fo + c];
+    const float phx = C.phi[fo + c];
+    float ux[3];
+    for (int a = 0; a < D; ++a) ux[a] = C.macro[(1 + a) * NF + fo + c];
+    // the cut links' partners, loaded in groups of four with every load of a group in
+    // flight together (a dependent chain per link otherwise), summed in link order
+    float acc[3] = {0.f, 0.f, 0.f};
+    int cnt = 0;
+    uint32_t mm = m;
+    while (mm) {
+      constexpr int G = 4;
+      long long cy[G];
+      bool on[G];
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        on[j] = mm != 0;
+        cy[j] = fo + c;
+        if (!on[j]) continue;
+        const int k = __ffs(mm) - 1;
+        mm &= mm - 1u;
+        const int i = LT::opp(k);
+        int yx = x + LT::cx(i), yy = y + LT::cy(i), yz = z + LT::cz(i);
+        wrap(L, 0, yx); wrap(L, 1, yy); if (D == 3) wrap(L, 2, yz);
+        cy[j] = fo + cidx(L, yx, yy, yz);
+      }
+      float py[G], uy[G][3];
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        py[j] = C.phi[cy[j]];
+#pragma unroll
+        for (int a = 0; a < D; ++a) uy[j][a] = C.macro[(1 + a) * NF + cy[j]];
+      }
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        if (!on[j]) continue;
+        const float q = phx / (phx - py[j]);
+        for (int a = 0; a < D; ++a) acc[a] += (1.0f - q) * ux[a] + q * uy[j][a];
+        ++cnt;
+      }
+    }
+    for (int a = 0; a < D; ++a) C.ut0[a * NF + fo + c] = acc[a] / (float)cnt;
+  }
 }
 
 }  // namespace lsb

@@ -592,13 +592,14 @@ __global__ void __launch_bounds__(512, 2) k_collide_stream_tma(Ctx C, BlockShape
 // For every cut link (x, k): Eq. bb with the momentum term of Eq. bb_cc;
 // i = opp(k) points from x (phase A) to x + c_i (phase B).  One thread per link
 // (the link list of the classification, in link-buffer order).
+// On the CTAs [b0, b0 + nb) of the launch.
 template <int Q, typename T>
-__global__ void LSB_LINK_LB k_interface_bc(Ctx C, int glevel) {
-  LSB_GRID_WAIT();
+__device__ __forceinline__ void d_interface_bc(const Ctx &C, int glevel, int b0, int nb) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   const long long n = min((long long)C.counters[glevel * NCOUNT + 0], C.link_cap);
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+  for (long long e = ((long long)blockIdx.x - b0) * blockDim.x + threadIdx.x; e < n;
+       e += (long long)nb * blockDim.x) {
     const int2 it = C.link_cell[C.link_list_off[glevel] + e];
     const int k = C.link_dir[C.link_list_off[glevel] + e];
     const LevelDev &L = C.lds[it.x];
@@ -697,6 +698,21 @@ __global__ void LSB_LINK_LB k_interface_bc(Ctx C, int glevel) {
       Store<T>::st(Bf + k * N + c, val, C.fp16_scale);
     }
   }
+}
+template <int Q, typename T>
+__global__ void LSB_LINK_LB k_interface_bc(Ctx C, int glevel) {
+  LSB_GRID_WAIT();
+  d_interface_bc<Q, T>(C, glevel, 0, gridDim.x);
+}
+// The interface pass and the interface cells' u~ (the level set's first pass) in one
+// launch: neither reads what the other writes (the pass writes populations, u~ comes
+// from the moments the collide stored), so CTAs [0, ga) take the cut links and the rest
+// the interface cells.
+template <int Q, typename T>
+__global__ void LSB_LINK_LB k_iface_init(Ctx C, int glevel, int ga) {
+  LSB_GRID_WAIT();
+  if ((int)blockIdx.x < ga) d_interface_bc<Q, T>(C, glevel, 0, ga);
+  else d_ext_init<Q>(C, glevel, ga, (int)gridDim.x - ga);
 }
 
 // ------------------------------------------------------------------ level transfers
@@ -1404,6 +1420,9 @@ cudaError_t run_collide_stream_tma(int Q, int st, Launch L, Ctx C, BlockShape S,
 }
 cudaError_t run_interface_bc(int Q, int st, Launch L, Ctx C, int glevel) {
   LSB_QT(Q, st, (LK(k_interface_bc)(C, glevel)));
+}
+cudaError_t run_iface_init(int Q, int st, Launch L, Ctx C, int glevel, int ga) {
+  LSB_QT(Q, st, (LK(k_iface_init)(C, glevel, ga)));
 }
 cudaError_t run_restrict(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, int all_cells) {
   LSB_QT(Q, st, (LK(k_restrict)(C, S, list, n, all_cells)));

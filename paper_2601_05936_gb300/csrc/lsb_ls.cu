@@ -210,14 +210,14 @@ __global__ void k_classify_links(Ctx C, BlockShape S, const int *list, int nlist
 // Pass 3: band flag of every active finest block (itself or a 3^D neighbour
 // holds an interface cell); band blocks are listed.  One warp per block, lane k
 // reading the flags of neighbour k, so the 3^D loads are in flight together.
+// On the CTAs [b0, b0 + nb) of the launch.
 template <int Q>
-__global__ void k_band(Ctx C, BlockShape S, const int *list, int nlist, int glevel) {
-  LSB_GRID_WAIT();
+__device__ __forceinline__ void d_band(const Ctx &C, const int *list, int nlist, int glevel, int b0, int nb) {
   constexpr int D = Lat<Q>::D;
   constexpr int NN = D == 3 ? 27 : 9;
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
-  for (int w = blockIdx.x * wpb + (threadIdx.x >> 5); w < nlist; w += gridDim.x * wpb) {
+  for (int w = ((int)blockIdx.x - b0) * wpb + (threadIdx.x >> 5); w < nlist; w += nb * wpb) {
     const int gb = list[w];
     const LevelDev &L = C.lds[C.blk_ld[gb]];
     bool hot = false;
@@ -256,14 +256,14 @@ __global__ void k_band(Ctx C, BlockShape S, const int *list, int nlist, int glev
 // n = g/|g|, kappa = (|g|^2 tr H - g.H.g)/|g|^3.
 // which: 0 the interface list, 1 the flip list, 2 both (one index space, interface
 // cells first; a cell on both lists gets the same values twice).
-template <int D>
-__global__ void k_geometry(Ctx C, int glevel, int which) {
-  LSB_GRID_WAIT();
+// On the CTAs [b0, b0 + nb) of the launch; post(it) runs after the fit of each flipped cell.
+template <int D, typename Post>
+__device__ __forceinline__ void d_geometry(const Ctx &C, int glevel, int which, int b0, int nb, Post post) {
   const int ni = which == 1 ? 0 : min(C.counters[glevel * NCOUNT + 1], (int)C.list_cap);
   const int nf = which == 0 ? 0 : min(C.counters[glevel * NCOUNT + 2], (int)C.list_cap);
   const int2 *li = C.iface_list + (long long)glevel * C.list_cap;
   const int2 *lf = C.flip_list + (long long)glevel * C.list_cap;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ni + nf; e += gridDim.x * blockDim.x) {
+  for (int e = ((int)blockIdx.x - b0) * blockDim.x + threadIdx.x; e < ni + nf; e += nb * blockDim.x) {
     const int2 it = e < ni ? li[e] : lf[e - ni];
     const LevelDev &L = C.lds[it.x];
     const long long c = it.y;
@@ -340,72 +340,22 @@ __global__ void k_geometry(Ctx C, int glevel, int which) {
       for (int a = 0; a < D; ++a) C.nvec[a * C.nfine + fc] = 0.f;
       C.kappa[fc] = 0.f;
     }
+    if (e >= ni) post(it);
   }
+}
+template <int D>
+__global__ void k_geometry(Ctx C, int glevel, int which) {
+  LSB_GRID_WAIT();
+  d_geometry<D>(C, glevel, which, 0, gridDim.x, [](int2) {});
 }
 
 // ------------------------------------------------------------------ velocity extension
-// Interface cells: mean of u_I = (1-q) u(x) + q u(x + c_i) over their cut links.
-template <int Q>
-__device__ __forceinline__ void d_ext_init(const Ctx &C, int glevel) {
-  using LT = Lat<Q>;
-  constexpr int D = LT::D;
-  const int n = min(C.counters[glevel * NCOUNT + 1], (int)C.list_cap);
-  const int2 *lst = C.iface_list + (long long)glevel * C.list_cap;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    const int2 it = lst[e];
-    const LevelDev &L = C.lds[it.x];
-    if (!L.ls_active) continue;  // frozen level set in this case
-    const long long c = it.y;
-    int x, y, z;
-    cell_xyz(L, c, x, y, z);
-    const long long fo = L.fine_off, NF = C.nfine;
-    const uint32_t m = C.cmask[fo + c];
-    const float phx = C.phi[fo + c];
-    float ux[3];
-    for (int a = 0; a < D; ++a) ux[a] = C.macro[(1 + a) * NF + fo + c];
-    // the cut links' partners, loaded in groups of four with every load of a group in
-    // flight together (a dependent chain per link otherwise), summed in link order
-    float acc[3] = {0.f, 0.f, 0.f};
-    int cnt = 0;
-    uint32_t mm = m;
-    while (mm) {
-      constexpr int G = 4;
-      long long cy[G];
-      bool on[G];
-#pragma unroll
-      for (int j = 0; j < G; ++j) {
-        on[j] = mm != 0;
-        cy[j] = fo + c;
-        if (!on[j]) continue;
-        const int k = __ffs(mm) - 1;
-        mm &= mm - 1u;
-        const int i = LT::opp(k);
-        int yx = x + LT::cx(i), yy = y + LT::cy(i), yz = z + LT::cz(i);
-        wrap(L, 0, yx); wrap(L, 1, yy); if (D == 3) wrap(L, 2, yz);
-        cy[j] = fo + cidx(L, yx, yy, yz);
-      }
-      float py[G], uy[G][3];
-#pragma unroll
-      for (int j = 0; j < G; ++j) {
-        py[j] = C.phi[cy[j]];
-#pragma unroll
-        for (int a = 0; a < D; ++a) uy[j][a] = C.macro[(1 + a) * NF + cy[j]];
-      }
-#pragma unroll
-      for (int j = 0; j < G; ++j) {
-        if (!on[j]) continue;
-        const float q = phx / (phx - py[j]);
-        for (int a = 0; a < D; ++a) acc[a] += (1.0f - q) * ux[a] + q * uy[j][a];
-        ++cnt;
-      }
-    }
-    for (int a = 0; a < D; ++a) C.ut0[a * NF + fo + c] = acc[a] / (float)cnt;
-  }
-}
+// (d_ext_init, the interface cells' u~, is in lsb_device.cuh: the interface pass shares
+// its launch)
 template <int Q>
 __global__ void k_ext_init(Ctx C, int glevel) {
   LSB_GRID_WAIT();
-  d_ext_init<Q>(C, glevel);
+  d_ext_init<Q>(C, glevel, 0, gridDim.x);
 }
 
 // One Jacobi sweep of first-order upwind extension on the band (interface cells
@@ -1125,7 +1075,7 @@ __global__ void k_levelset_persistent(Ctx C, BlockShape S, int glevel, int n_ext
                                       unsigned *bar, long long limit) {
   LSB_GRID_WAIT();
   constexpr int D = Lat<Q>::D;
-  d_ext_init<Q>(C, glevel);
+  d_ext_init<Q>(C, glevel, 0, gridDim.x);
   if (!grid_barrier(bar, C.err, limit)) return;
   const float *uin = C.ut0;
   for (int it = 0; it < n_ext; ++it) {
@@ -1177,15 +1127,12 @@ __device__ __forceinline__ float feq_q(int i, float drho, const float u[3]) {
   return LT::w(i) * (drho + (1.0f + drho) * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
 }
 
+// Refill of one flipped cell (its normal and curvature already fitted).
 template <int Q, typename T>
-__global__ void k_refill(Ctx C, int glevel) {
-  LSB_GRID_WAIT();
+__device__ __forceinline__ void refill_cell(const Ctx &C, int2 it) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
-  const int n = min(C.counters[glevel * NCOUNT + 2], (int)C.list_cap);
-  const int2 *lst = C.flip_list + (long long)glevel * C.list_cap;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    const int2 it = lst[e];
+  {
     const LevelDev &L = C.lds[it.x];
     const long long c = it.y;
     int x, y, z;
@@ -1220,7 +1167,7 @@ __global__ void k_refill(Ctx C, int glevel) {
     }
     if (best < 0) {
       for (int i = 0; i < Q; ++i) Store<T>::st(Bf + i * N + c, 0.0f, C.fp16_scale);
-      continue;
+      return;
     }
     const int ex = LT::cx(best), ey = LT::cy(best), ez = LT::cz(best);
     const float phr = C.phi[fo + c];
@@ -1269,6 +1216,24 @@ __global__ void k_refill(Ctx C, int glevel) {
       const float v = feq_q<Q>(i, rr, ur) + (f1[i] - feq_q<Q>(i, r1, u1));
       Store<T>::st(Bf + i * N + c, v, C.fp16_scale);
     }
+  }
+}
+
+// The classification's last passes in one launch: the band (CTAs [0, gband), a warp
+// per finest block) and the curvature fit of the interface and flipped cells (the rest),
+// which read nothing the band pass writes; with refill set, each flipped cell is refilled
+// by the thread that fitted it (the refill reads the fit at its own cell only, and
+// neighbours of the new phase that did not flip).
+template <int Q, typename T>
+__global__ void k_post_classify(Ctx C, const int *list, int nlist, int glevel, int gband, int refill) {
+  LSB_GRID_WAIT();
+  constexpr int D = Lat<Q>::D;
+  if ((int)blockIdx.x < gband) {
+    d_band<Q>(C, list, nlist, glevel, 0, gband);
+  } else if (refill) {
+    d_geometry<D>(C, glevel, 2, gband, (int)gridDim.x - gband, [&](int2 it) { refill_cell<Q, T>(C, it); });
+  } else {
+    d_geometry<D>(C, glevel, 2, gband, (int)gridDim.x - gband, [](int2) {});
   }
 }
 
@@ -1371,9 +1336,6 @@ cudaError_t run_classify_links(int Q, Launch L, Ctx C, BlockShape S, const int *
   LQ(k_classify_links, C, S, list, n, glevel, full);
 }
 cudaError_t run_flip_mark(int Q, Launch L, Ctx C, BlockShape S, int glevel) { LQ(k_flip_mark, C, S, glevel); }
-cudaError_t run_band(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, int glevel) {
-  LQ(k_band, C, S, list, n, glevel);
-}
 cudaError_t run_geometry(int D, Launch L, Ctx C, int glevel, int which) { LD(k_geometry, C, glevel, which); }
 cudaError_t run_ext_init(int Q, Launch L, Ctx C, int glevel) { LQ(k_ext_init, C, glevel); }
 cudaError_t run_ext_iter(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int mode) {
@@ -1406,16 +1368,17 @@ cudaError_t run_reinit_prep(int Q, Launch L, Ctx C, BlockShape S, int glevel) { 
 cudaError_t run_reinit_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage) {
   LDP(k_reinit_stage, C, S, glevel, stage);
 }
-cudaError_t run_refill(int Q, int st, Launch L, Ctx C, int glevel) {
+cudaError_t run_post_classify(int Q, int st, Launch L, Ctx C, const int *list, int n, int glevel, int gband,
+                              int refill) {
   if (Q == 9) {
-    if (st == 0) launcher(k_refill<9, float>, L, 0)(C, glevel);
-    else launcher(k_refill<9, __half>, L, 0)(C, glevel);
+    if (st == 0) launcher(k_post_classify<9, float>, L, 0)(C, list, n, glevel, gband, refill);
+    else launcher(k_post_classify<9, __half>, L, 0)(C, list, n, glevel, gband, refill);
   } else if (Q == 19) {
-    if (st == 0) launcher(k_refill<19, float>, L, 0)(C, glevel);
-    else launcher(k_refill<19, __half>, L, 0)(C, glevel);
+    if (st == 0) launcher(k_post_classify<19, float>, L, 0)(C, list, n, glevel, gband, refill);
+    else launcher(k_post_classify<19, __half>, L, 0)(C, list, n, glevel, gband, refill);
   } else {
     if (st != 0) return cudaErrorInvalidValue;  // D3Q27: FP32 storage only
-    launcher(k_refill<27, float>, L, 0)(C, glevel);
+    launcher(k_post_classify<27, float>, L, 0)(C, list, n, glevel, gband, refill);
   }
   return cudaGetLastError();
 }
