@@ -65,7 +65,9 @@ def build(force=False, verbose=False, extra=(), out=None):
         list(ex.map(comp, zip(SOURCES, objs)))
     target = LIB if out is None else out
     tmp = target + ".tmp"
-    r = subprocess.run([exe, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], capture_output=True, text=True)
+    # every symbol resolved at link time: a missing definition fails the build, not the load
+    r = subprocess.run([exe, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-Xlinker", "--no-undefined"],
+                       capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, target)

@@ -525,7 +525,6 @@ lsb_status classify(lsb_grid *g, int l, int init, bool refill = false) {
   // (and, for the cut links, the blocks next to a flipped cell), walked from the lists
   const int nlist = init ? F.n : std::max(1, std::min(F.n, 152 * 8));
   RUN(8, 0, F.n, nt, run_classify_phase, Q, LN(g, nlist, nt), C, S, fl, F.n, l, init);
-  if (!init) RUN(9, 0, 1, 128, run_flip_mark, Q, LN(g, DYN_GRID / 4, 128), C, S, l);
   RUN(9, 0, F.n, nt, run_classify_links, Q, LN(g, nlist, nt), C, S, fl, F.n, l, init);
   // the band pass (a warp per block) and the curvature fit at the interface and the
   // flipped cells (and the refill of the flipped cells) share a launch

@@ -145,9 +145,10 @@ enum : uint8_t {
 };
 
 // per-block flag bits (finest level)
-// BF_OLDBAND / BF_CHECK live only between the phase and link passes of a
-// classification: the previous band, and blocks next to a cell that flipped.
-enum : uint8_t { BF_IFACE = 1, BF_BAND = 2, BF_OLDBAND = 4, BF_CHECK = 8 };
+// BF_CHECK lives only between the phase and link passes of a classification: blocks
+// next to a cell that flipped outside the previous band (whose blocks still hold BF_BAND
+// until the link pass rewrites the flags).
+enum : uint8_t { BF_IFACE = 1, BF_BAND = 2, BF_CHECK = 8 };
 
 struct LevelDev {
   int case_id, level, n_levels, finest;

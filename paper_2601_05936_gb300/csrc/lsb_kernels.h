@@ -97,7 +97,6 @@ cudaError_t run_export_noalloc(int Q, int st, Launch L, Ctx C, int ld, int field
 // lsb_ls.cu: level set, classification, geometry, refill, sensor
 cudaError_t run_classify_phase(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, int glevel, int init);
 cudaError_t run_classify_links(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, int glevel, int full);
-cudaError_t run_flip_mark(int Q, Launch L, Ctx C, BlockShape S, int glevel);
 cudaError_t run_geometry(int D, Launch L, Ctx C, int glevel, int which);
 cudaError_t run_ext_init(int Q, Launch L, Ctx C, int glevel);
 cudaError_t run_ext_iter(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int mode);

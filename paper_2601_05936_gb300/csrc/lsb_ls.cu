@@ -25,11 +25,15 @@ __device__ __forceinline__ bool in_band(const Ctx &C, const LevelDev &L, const B
 // ------------------------------------------------------------------ classification
 // Pass 1: phase of every leaf cell from phi (liquid iff phi < 0); flipped cells
 // are listed.  init = 1 (after creation or regrid): all blocks, no flips,
-// previous = current.  Otherwise only blocks of the previous band, whose band
-// flag is kept as BF_OLDBAND (other blocks keep flag 0).
+// previous = current.  Otherwise only blocks of the previous band (they keep the band
+// flag the previous band pass set until the link pass rewrites the flags), and every
+// block next to a flipped cell (or holding one) that is not in that band gets BF_CHECK
+// and a place in the check list.
 template <int Q>
 __global__ void k_classify_phase(Ctx C, BlockShape S, const int *list, int nlist, int glevel, int init) {
   LSB_GRID_WAIT();
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
   // phi changes only on band cells, so outside the previous band no phase (and no stale
   // flip bit: flips happen next to the interface, inside the band) can change: unless
   // init, the blocks are those of the previous band list
@@ -41,7 +45,6 @@ __global__ void k_classify_phase(Ctx C, BlockShape S, const int *list, int nlist
   }
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     const int gb = list[w];
-    if (threadIdx.x == 0) C.bflag[gb] = init ? 0 : BF_OLDBAND;
     int x, y, z;
     const LevelDev &L = blk_cell(C, S, gb, threadIdx.x, x, y, z);
     if (x >= L.n[0] || y >= L.n[1] || z >= L.n[2]) continue;
@@ -63,42 +66,27 @@ __global__ void k_classify_phase(Ctx C, BlockShape S, const int *list, int nlist
       int e = atomicAdd(&C.counters[glevel * NCOUNT + 2], 1);
       if (e < C.list_cap) C.flip_list[(long long)glevel * C.list_cap + e] = make_int2(C.blk_ld[gb], (int)c);
       else atomicOr(C.err, ERR_LIST_OVF);
-    }
-  }
-}
-
-// Pass 1b: blocks next to a flipped cell (or holding one) that were not in the
-// previous band get BF_CHECK.
-template <int Q>
-__global__ void k_flip_mark(Ctx C, BlockShape S, int glevel) {
-  LSB_GRID_WAIT();
-  using LT = Lat<Q>;
-  constexpr int D = LT::D;
-  const int n = min(C.counters[glevel * NCOUNT + 2], (int)C.list_cap);
-  const int2 *lst = C.flip_list + (long long)glevel * C.list_cap;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    const int2 it = lst[e];
-    const LevelDev &L = C.lds[it.x];
-    const long long c = it.y;
-    int x, y, z;
-    cell_xyz(L, c, x, y, z);
-    for (int k = 0; k < Q; ++k) {
-      int sx = x + LT::cx(k), sy = y + LT::cy(k), sz = z + LT::cz(k);
-      if (!(wrap(L, 0, sx) && wrap(L, 1, sy) && (D == 2 || wrap(L, 2, sz)))) continue;
-      const int nb = L.block_off + block_of(L, sx, sy, sz, S);
-      // set BF_CHECK once per block (compare-and-swap on the flag's word) and list it
-      unsigned *wp = reinterpret_cast<unsigned *>(C.bflag + (nb & ~3));
-      const int sh = (nb & 3) * 8;
-      unsigned old = *reinterpret_cast<volatile unsigned *>(wp);
-      while (!(((old >> sh) & 0xffu) & (BF_OLDBAND | BF_CHECK))) {
-        const unsigned prev = atomicCAS(wp, old, old | ((unsigned)BF_CHECK << sh));
-        if (prev == old) {
-          const int e = atomicAdd(&C.counters[glevel * NCOUNT + 4], 1);
-          if (e < C.band_cap) C.check_list[(long long)glevel * C.band_cap + e] = nb;
-          else atomicOr(C.err, ERR_BAND_OVF);
-          break;
+      // the blocks around the flip that the previous band does not hold: the band flags
+      // tested here are those of the previous classification, which no thread of this pass
+      // changes
+      for (int k = 0; k < Q; ++k) {
+        int sx = x + LT::cx(k), sy = y + LT::cy(k), sz = z + LT::cz(k);
+        if (!(wrap(L, 0, sx) && wrap(L, 1, sy) && (D == 2 || wrap(L, 2, sz)))) continue;
+        const int nb = L.block_off + block_of(L, sx, sy, sz, S);
+        // set BF_CHECK once per block (compare-and-swap on the flag's word) and list it
+        unsigned *wp = reinterpret_cast<unsigned *>(C.bflag + (nb & ~3));
+        const int sh = (nb & 3) * 8;
+        unsigned old = *reinterpret_cast<volatile unsigned *>(wp);
+        while (!(((old >> sh) & 0xffu) & (BF_BAND | BF_CHECK))) {
+          const unsigned seen = atomicCAS(wp, old, old | ((unsigned)BF_CHECK << sh));
+          if (seen == old) {
+            const int slot = atomicAdd(&C.counters[glevel * NCOUNT + 4], 1);
+            if (slot < C.band_cap) C.check_list[(long long)glevel * C.band_cap + slot] = nb;
+            else atomicOr(C.err, ERR_BAND_OVF);
+            break;
+          }
+          old = seen;
         }
-        old = prev;
       }
     }
   }
@@ -126,7 +114,7 @@ __global__ void k_classify_links(Ctx C, BlockShape S, const int *list, int nlist
   const int *chk = C.check_list + (long long)glevel * C.band_cap;
   for (int w = blockIdx.x; w < nlist; w += gridDim.x) {
     const int gb = w < nband ? list[w] : chk[w - nband];
-    const bool work = full || (C.bflag[gb] & (BF_OLDBAND | BF_CHECK));
+    const bool work = full || (C.bflag[gb] & (BF_BAND | BF_CHECK));
     __syncthreads();  // every thread has read the flags before thread 0 rewrites them
     if (!work) {
       if (threadIdx.x == 0) C.bflag[gb] = 0;
@@ -1335,7 +1323,6 @@ cudaError_t run_classify_phase(int Q, Launch L, Ctx C, BlockShape S, const int *
 cudaError_t run_classify_links(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n, int glevel, int full) {
   LQ(k_classify_links, C, S, list, n, glevel, full);
 }
-cudaError_t run_flip_mark(int Q, Launch L, Ctx C, BlockShape S, int glevel) { LQ(k_flip_mark, C, S, glevel); }
 cudaError_t run_geometry(int D, Launch L, Ctx C, int glevel, int which) { LD(k_geometry, C, glevel, which); }
 cudaError_t run_ext_init(int Q, Launch L, Ctx C, int glevel) { LQ(k_ext_init, C, glevel); }
 cudaError_t run_ext_iter(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout, int mode) {
