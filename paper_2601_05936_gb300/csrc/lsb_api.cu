@@ -344,6 +344,14 @@ bool profiled(const lsb_grid *g, int kid) { return g->prof_mode == 2 || (g->prof
   } while (0)
 
 constexpr int DYN_GRID = 152 * 8;  // CTAs for kernels over device-sized lists
+// CTAs of a shared launch for the interface cells' u~ and for the curvature fit (of 128
+// threads; the cell lists are a few ten thousand long and loop beyond)
+#ifndef LSB_INIT_CTAS
+#define LSB_INIT_CTAS 512
+#endif
+#ifndef LSB_GEO_CTAS
+#define LSB_GEO_CTAS 512
+#endif
 
 #define TRY(x)                   \
   do {                           \
@@ -529,8 +537,8 @@ lsb_status classify(lsb_grid *g, int l, int init, bool refill = false) {
   // the band pass (a warp per block) and the curvature fit at the interface and the
   // flipped cells (and the refill of the flipped cells) share a launch
   const int gband = (F.n + 3) / 4;
-  RUN(10, 0, F.n, 128, run_post_classify, Q, g->storage, LN(g, gband + DYN_GRID, 128), C, fl, F.n, l, gband,
-      refill ? 1 : 0);
+  RUN(10, 0, F.n, 128, run_post_classify, Q, g->storage, LN(g, LSB_GEO_CTAS + gband, 128), C, fl, F.n, l,
+      LSB_GEO_CTAS, refill ? 1 : 0);
   (void)D;
   return LSB_OK;
 }
@@ -728,7 +736,7 @@ lsb_status advance(lsb_grid *g, int l) {
     if (ls_active_any(g, l) && g->driver == 0) {
       // the interface pass and the level set's first pass (u~ at the interface cells) share
       // a launch; the level-set update then starts from its first extension sweep
-      RUN(1, 0, 1, 128, run_iface_init, Q, st, LN(g, 2 * DYN_GRID, 128), C, l, DYN_GRID);
+      RUN(1, 0, 1, 128, run_iface_init, Q, st, LN(g, LSB_INIT_CTAS + DYN_GRID, 128), C, l, LSB_INIT_CTAS);
       g->init_done[l] = true;
     } else {
       RUN(1, 0, 1, 128, run_interface_bc, Q, st, LN(g, DYN_GRID, 128), C, l);

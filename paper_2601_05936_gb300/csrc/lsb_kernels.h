@@ -73,8 +73,8 @@ cudaError_t run_collide_stream_tma(int Q, int st, Launch L, Ctx C, BlockShape S,
 size_t tma_smem_bytes(int Q, int st, int nthreads);
 cudaError_t prepare_collide_stream_tma(int Q, int st, int nthreads, int *ctas_per_sm);
 cudaError_t run_interface_bc(int Q, int st, Launch L, Ctx C, int glevel);
-// the interface pass on CTAs [0, ga) and the interface cells' u~ on the rest, one launch
-cudaError_t run_iface_init(int Q, int st, Launch L, Ctx C, int glevel, int ga);
+// the interface cells' u~ on CTAs [0, gi) and the interface pass on the rest, one launch
+cudaError_t run_iface_init(int Q, int st, Launch L, Ctx C, int glevel, int gi);
 cudaError_t run_restrict(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, int all_cells);
 cudaError_t run_prolong(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n);
 cudaError_t run_level_tags(int Q, Launch L, Ctx C, BlockShape S, const int *list, int n);
@@ -109,9 +109,9 @@ cudaError_t run_ext_first(int D, Launch L, Ctx C, BlockShape S, int glevel, cons
 cudaError_t run_ext_sweep_mirror(int D, Launch L, Ctx C, BlockShape S, int glevel, const float *uin, float *uout);
 cudaError_t run_adv_mirror(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage, const float *ufin);
 cudaError_t run_reinit_mirror(int Q, Launch L, Ctx C, BlockShape S, int glevel, int stage, int prep);
-// the band pass on CTAs [0, gband) and the curvature fit of the interface and flipped cells
-// (each flipped cell then refilled when refill is set) on the rest, one launch
-cudaError_t run_post_classify(int Q, int st, Launch L, Ctx C, const int *list, int n, int glevel, int gband,
+// the curvature fit of the interface and flipped cells on CTAs [0, gg) (each flipped cell
+// then refilled when refill is set) and the band pass on the rest, one launch
+cudaError_t run_post_classify(int Q, int st, Launch L, Ctx C, const int *list, int n, int glevel, int gg,
                               int refill);
 cudaError_t run_levelset_persistent(int Q, Launch L, Ctx C, BlockShape S, int glevel, int n_ext, int reinit,
                                     int n_reinit, unsigned *bar, long long limit);

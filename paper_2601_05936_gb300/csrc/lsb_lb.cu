@@ -706,13 +706,13 @@ __global__ void LSB_LINK_LB k_interface_bc(Ctx C, int glevel) {
 }
 // The interface pass and the interface cells' u~ (the level set's first pass) in one
 // launch: neither reads what the other writes (the pass writes populations, u~ comes
-// from the moments the collide stored), so CTAs [0, ga) take the cut links and the rest
-// the interface cells.
+// from the moments the collide stored), so CTAs [0, gi) take the interface cells (the
+// longer chain per thread, so its CTAs are scheduled first) and the rest the cut links.
 template <int Q, typename T>
-__global__ void LSB_LINK_LB k_iface_init(Ctx C, int glevel, int ga) {
+__global__ void LSB_LINK_LB k_iface_init(Ctx C, int glevel, int gi) {
   LSB_GRID_WAIT();
-  if ((int)blockIdx.x < ga) d_interface_bc<Q, T>(C, glevel, 0, ga);
-  else d_ext_init<Q>(C, glevel, ga, (int)gridDim.x - ga);
+  if ((int)blockIdx.x < gi) d_ext_init<Q>(C, glevel, 0, gi);
+  else d_interface_bc<Q, T>(C, glevel, gi, (int)gridDim.x - gi);
 }
 
 // ------------------------------------------------------------------ level transfers
@@ -1421,8 +1421,8 @@ cudaError_t run_collide_stream_tma(int Q, int st, Launch L, Ctx C, BlockShape S,
 cudaError_t run_interface_bc(int Q, int st, Launch L, Ctx C, int glevel) {
   LSB_QT(Q, st, (LK(k_interface_bc)(C, glevel)));
 }
-cudaError_t run_iface_init(int Q, int st, Launch L, Ctx C, int glevel, int ga) {
-  LSB_QT(Q, st, (LK(k_iface_init)(C, glevel, ga)));
+cudaError_t run_iface_init(int Q, int st, Launch L, Ctx C, int glevel, int gi) {
+  LSB_QT(Q, st, (LK(k_iface_init)(C, glevel, gi)));
 }
 cudaError_t run_restrict(int Q, int st, Launch L, Ctx C, BlockShape S, const int *list, int n, int all_cells) {
   LSB_QT(Q, st, (LK(k_restrict)(C, S, list, n, all_cells)));

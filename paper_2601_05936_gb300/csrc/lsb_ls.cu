@@ -1207,21 +1207,21 @@ __device__ __forceinline__ void refill_cell(const Ctx &C, int2 it) {
   }
 }
 
-// The classification's last passes in one launch: the band (CTAs [0, gband), a warp
-// per finest block) and the curvature fit of the interface and flipped cells (the rest),
-// which read nothing the band pass writes; with refill set, each flipped cell is refilled
-// by the thread that fitted it (the refill reads the fit at its own cell only, and
-// neighbours of the new phase that did not flip).
+// The classification's last passes in one launch: the curvature fit of the interface and
+// flipped cells (CTAs [0, gg): the longer chain per thread, scheduled first) and the band
+// (the rest, a warp per finest block), which read nothing of each other's; with refill
+// set, each flipped cell is refilled by the thread that fitted it (the refill reads the
+// fit at its own cell only, and neighbours of the new phase that did not flip).
 template <int Q, typename T>
-__global__ void k_post_classify(Ctx C, const int *list, int nlist, int glevel, int gband, int refill) {
+__global__ void k_post_classify(Ctx C, const int *list, int nlist, int glevel, int gg, int refill) {
   LSB_GRID_WAIT();
   constexpr int D = Lat<Q>::D;
-  if ((int)blockIdx.x < gband) {
-    d_band<Q>(C, list, nlist, glevel, 0, gband);
+  if ((int)blockIdx.x >= gg) {
+    d_band<Q>(C, list, nlist, glevel, gg, (int)gridDim.x - gg);
   } else if (refill) {
-    d_geometry<D>(C, glevel, 2, gband, (int)gridDim.x - gband, [&](int2 it) { refill_cell<Q, T>(C, it); });
+    d_geometry<D>(C, glevel, 2, 0, gg, [&](int2 it) { refill_cell<Q, T>(C, it); });
   } else {
-    d_geometry<D>(C, glevel, 2, gband, (int)gridDim.x - gband, [](int2) {});
+    d_geometry<D>(C, glevel, 2, 0, gg, [](int2) {});
   }
 }
 
@@ -1355,17 +1355,17 @@ cudaError_t run_reinit_prep(int Q, Launch L, Ctx C, BlockShape S, int glevel) { 
 cudaError_t run_reinit_stage(int D, Launch L, Ctx C, BlockShape S, int glevel, int stage) {
   LDP(k_reinit_stage, C, S, glevel, stage);
 }
-cudaError_t run_post_classify(int Q, int st, Launch L, Ctx C, const int *list, int n, int glevel, int gband,
+cudaError_t run_post_classify(int Q, int st, Launch L, Ctx C, const int *list, int n, int glevel, int gg,
                               int refill) {
   if (Q == 9) {
-    if (st == 0) launcher(k_post_classify<9, float>, L, 0)(C, list, n, glevel, gband, refill);
-    else launcher(k_post_classify<9, __half>, L, 0)(C, list, n, glevel, gband, refill);
+    if (st == 0) launcher(k_post_classify<9, float>, L, 0)(C, list, n, glevel, gg, refill);
+    else launcher(k_post_classify<9, __half>, L, 0)(C, list, n, glevel, gg, refill);
   } else if (Q == 19) {
-    if (st == 0) launcher(k_post_classify<19, float>, L, 0)(C, list, n, glevel, gband, refill);
-    else launcher(k_post_classify<19, __half>, L, 0)(C, list, n, glevel, gband, refill);
+    if (st == 0) launcher(k_post_classify<19, float>, L, 0)(C, list, n, glevel, gg, refill);
+    else launcher(k_post_classify<19, __half>, L, 0)(C, list, n, glevel, gg, refill);
   } else {
     if (st != 0) return cudaErrorInvalidValue;  // D3Q27: FP32 storage only
-    launcher(k_post_classify<27, float>, L, 0)(C, list, n, glevel, gband, refill);
+    launcher(k_post_classify<27, float>, L, 0)(C, list, n, glevel, gg, refill);
   }
   return cudaGetLastError();
 }
