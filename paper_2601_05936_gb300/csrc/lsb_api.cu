@@ -512,6 +512,10 @@ bool has_finest(const lsb_grid *g, int l) {
 // Classification of the finest level l: phases, flips, cut links, band; then geometry.
 // refill: the step's classification, whose curvature-fit threads also refill the flipped
 // cells (the refill pass of the step); otherwise no refill runs here.
+#ifndef LSB_CLS_CTAS
+#define LSB_CLS_CTAS 32  // CTAs per SM (at most) of the phase and link passes: a CTA per listed block
+                         // (8: 0.769 ms per step, 16-32: 0.759)
+#endif
 lsb_status classify(lsb_grid *g, int l, int init, bool refill = false) {
   if (!has_finest(g, l)) return LSB_OK;
   // the band list the previous classification left is the set of blocks whose phases can
@@ -531,7 +535,7 @@ lsb_status classify(lsb_grid *g, int l, int init, bool refill = false) {
   const int Q = g->Q, D = g->D, nt = g->nthreads;
   // after creation or a regrid every finest block; otherwise the previous band's blocks
   // (and, for the cut links, the blocks next to a flipped cell), walked from the lists
-  const int nlist = init ? F.n : std::max(1, std::min(F.n, 152 * 8));
+  const int nlist = init ? F.n : std::max(1, std::min(F.n, 152 * LSB_CLS_CTAS));
   RUN(8, 0, F.n, nt, run_classify_phase, Q, LN(g, nlist, nt), C, S, fl, F.n, l, init);
   RUN(9, 0, F.n, nt, run_classify_links, Q, LN(g, nlist, nt), C, S, fl, F.n, l, init);
   // the band pass (a warp per block) and the curvature fit at the interface and the
