@@ -349,6 +349,9 @@ constexpr int DYN_GRID = 152 * 8;  // CTAs for kernels over device-sized lists
 #ifndef LSB_INIT_CTAS
 #define LSB_INIT_CTAS 512
 #endif
+#ifndef LSB_IFACE_CTAS
+#define LSB_IFACE_CTAS DYN_GRID  // and for the cut links of the interface pass beside them
+#endif
 #ifndef LSB_GEO_CTAS
 #define LSB_GEO_CTAS 512
 #endif
@@ -740,7 +743,7 @@ lsb_status advance(lsb_grid *g, int l) {
     if (ls_active_any(g, l) && g->driver == 0) {
       // the interface pass and the level set's first pass (u~ at the interface cells) share
       // a launch; the level-set update then starts from its first extension sweep
-      RUN(1, 0, 1, 128, run_iface_init, Q, st, LN(g, LSB_INIT_CTAS + DYN_GRID, 128), C, l, LSB_INIT_CTAS);
+      RUN(1, 0, 1, 128, run_iface_init, Q, st, LN(g, LSB_INIT_CTAS + LSB_IFACE_CTAS, 128), C, l, LSB_INIT_CTAS);
       g->init_done[l] = true;
     } else {
       RUN(1, 0, 1, 128, run_interface_bc, Q, st, LN(g, DYN_GRID, 128), C, l);
